@@ -1,0 +1,263 @@
+/*
+ * amr4.h -- C ABI of the GB300-native fourth-order AMR elliptic solver.
+ *
+ * Method: Zhao & Zhang, "Fourth-order AMR both in space and in time for incompressible
+ * Navier-Stokes equations with Dirichlet boundary conditions" (arXiv 2506.02663).
+ * The library solves the paper's fourth-order finite-volume elliptic systems -- the
+ * pure-Neumann pressure Poisson equation and the Helmholtz systems (I - gamma*nu*k*L) of
+ * Eq. (GePUP-IMEX b) -- on a block-structured AMR hierarchy (Sec. 5) by geometric
+ * multigrid (Sec. 6.4), with every step in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Ownership.  The caller owns every field buffer and the stream.  The library owns the
+ *   hierarchy metadata (host and device copies), multigrid scratch and bottom-solve
+ *   factors; they are freed by the matching destroy call.
+ * Memory.  Field pointers are DEVICE pointers (cudaMalloc'd or torch tensors) unless a
+ *   call says otherwise.  ``stream`` is a cudaStream_t passed as void* (NULL = legacy
+ *   default stream).  Calls are stream-ordered; a call that returns statistics or norms
+ *   synchronises its stream before returning.
+ * Errors.  Every call returns an amr_status; nothing crosses the ABI as an exception.
+ *   Argument and geometry errors are detected on the host before any launch and leave the
+ *   outputs untouched.  amr_last_error() returns a thread-local message for the last
+ *   failing call of the calling thread.
+ * Composite field layout.  A composite field is one contiguous array of doubles (or
+ *   floats where a call says so) holding every box ("patch") of every level, levels in
+ *   order, boxes in the order given at creation.  Patch p occupies
+ *       [offset_p, offset_p + stride_z_p * (n_z + 4))        (3-D)
+ *       [offset_p, offset_p + stride_y_p * (n_y + 4))        (2-D)
+ *   and cell (i, j, k) of the box (0-based, x fastest) sits at
+ *       offset_p + (k+2)*stride_z_p + (j+2)*stride_y_p + (i+2)
+ *   i.e. every box is wrapped by the two ghost layers of Sec. 3 (paragraph after
+ *   Eq. appProj).  amr_field_layout() returns the offsets and strides.  Values on the
+ *   invalid region of a level (Eq. validRegion) are defined as the average of their
+ *   children (Eq. AMR_avergingDownToCrse); calls that read a composite field overwrite
+ *   them with that average first.
+ * Boundary data layout.  Optional ``bc`` arrays hold, for every level l and face
+ *   f = 2*d + side (side 0 = low, 1 = high), one value per cell of the domain's face at
+ *   level l (the domain's cells with dimension d removed, lowest remaining dimension
+ *   fastest), levels in order, faces in order.  Dirichlet data are face averages of the
+ *   solution; Neumann data are face averages of its OUTWARD normal derivative
+ *   (Eqs. velBCHomoDiri5th, Neumann5).  NULL means homogeneous data.
+ *   amr_bc_layout() returns the offsets.
+ */
+#ifndef AMR4_H
+#define AMR4_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_ERR_INVALID_ARG = 1,   /* bad argument, layout or descriptor                      */
+  AMR_ERR_NESTING = 2,       /* proper nesting violated (paragraph after Eq. pBlock)     */
+  AMR_ERR_REFINEMENT = 3,    /* proper refinement violated (Eq. pBlock)                  */
+  AMR_ERR_BOX_TOO_SMALL = 4, /* a box of level >= 1 has fewer than 4 cells in a dimension */
+  AMR_ERR_NOT_CONVERGED = 5, /* max_vcycles reached above tolerance (stats still valid)   */
+  AMR_ERR_NONFINITE = 6,     /* a residual norm became NaN or Inf                          */
+  AMR_ERR_CUDA = 7,          /* a CUDA runtime call failed (message in amr_last_error)    */
+  AMR_ERR_OOM = 8            /* device allocation failed                                  */
+} amr_status;
+
+typedef enum { AMR_BC_DIRICHLET = 0, AMR_BC_NEUMANN = 1 } amr_bc;
+typedef enum { AMR_FP64 = 0, AMR_MIXED = 1 } amr_precision;
+
+/* Hierarchy description (Eqs. grids, AMRHier).
+ *   dim       2 or 3
+ *   ratio     refinement ratio r (2; 4 is accepted by amr_hierarchy_create and the
+ *             index maps, solver calls need 2)
+ *   n0        cells of level 0 per dimension (>= 5); level l has n0 * r^l
+ *   h0        cell size of level 0 (square cells)
+ *   nlevels   number of levels (>= 1)
+ *   nboxes    boxes per level (nboxes[0] must be 1: level 0 is the domain)
+ *   boxes     for every box of every level in order: lo[0..dim-1], hi[0..dim-1],
+ *             inclusive indices in that level's index space
+ * Validation order (the first failing check is reported): dim/ratio/n0/level-0 box;
+ * then every box of every level >= 1 in order: bounds (INVALID_ARG), >= 4 cells per
+ * dimension (BOX_TOO_SMALL), lo and hi+1 divisible by r (REFINEMENT); then pairwise
+ * disjointness per level (INVALID_ARG); then nesting for levels >= 2: C_r(box) grown by 3
+ * coarse cells (clipped to the domain) inside level l-1 (NESTING); finally the coarsest
+ * level-0 multigrid grid must have at most 1024 cells (INVALID_ARG). */
+typedef struct {
+  int dim;
+  int ratio;
+  int n0[3];
+  double h0;
+  int nlevels;
+  const int* nboxes;
+  const int* boxes;
+} amr_hierarchy_desc;
+
+typedef struct amr_hierarchy amr_hierarchy;
+typedef struct amr_operator amr_operator;
+
+typedef struct {
+  int level;
+  int box;          /* index of the box within its level */
+  int lo[3], hi[3]; /* inclusive, level index space (unused dims 0) */
+  long long offset; /* element offset of the padded patch in a composite field */
+  long long stride_y, stride_z;
+  long long nelems; /* elements occupied by the padded patch */
+} amr_patch_info;
+
+/* Index maps (host arrays owned by the hierarchy, valid until destroy).  They are the
+ * bit-exact parity artefacts of Sec. 5.1 / Fig. 1(c):
+ *   valid         one int per interior cell of every patch (patch order, x fastest):
+ *                 1 valid, 0 invalid (Eq. validRegion)
+ *   component     one int per box of every level: connected-component label of the box
+ *                 within its level (boxes sharing a face patch of positive measure are
+ *                 connected; label = smallest box index of the component)
+ *   ghost_code    one int per padded cell of every patch (extents n+4 per dimension, x
+ *                 fastest, no pitch padding): 0 interior, 1 physical, 2 copy from a box of
+ *                 the same level, 3 AMRCFI, 4 unused (outside the box in >= 2 dims)
+ *   ghost_src     same shape: physical -> face id 2d+side; copy -> source box index;
+ *                 else -1
+ *   ghost_aux     same shape: physical -> ghost layer (1 or 2); copy -> source cell's
+ *                 interior linear index in the source box (x fastest); else -1
+ *   ncfi          number of AMRCFI ghost cells; for each (ordered by padded-cell index
+ *                 over all patches): cfi_cell (padded-cell index over all patches, in the
+ *                 ghost_code numbering), cfi_start[dim] (global coarse index of the first
+ *                 cell of the 5-cell window per dimension), cfi_pos[dim] (parent coarse
+ *                 cell within the window, 0..4), cfi_sub[dim] (fine sub-cell, 0..r-1)
+ *   nreflux       number of coarse valid cells with a coarse-fine face (COH-3); for each:
+ *                 reflux_cell[3] = (level, box, interior linear index), reflux_faces =
+ *                 bit (2d+side) set for every face of the cell that borders the invalid
+ *                 region. */
+typedef struct {
+  long long ncells_interior;
+  long long ncells_padded;
+  const int* valid;
+  const int* component;
+  const int* ghost_code;
+  const int* ghost_src;
+  const int* ghost_aux;
+  long long ncfi;
+  const long long* cfi_cell;
+  const int* cfi_start; /* ncfi * dim */
+  const int* cfi_pos;   /* ncfi * dim */
+  const int* cfi_sub;   /* ncfi * dim */
+  long long nreflux;
+  const int* reflux_cell;  /* nreflux * 3 */
+  const int* reflux_faces; /* nreflux */
+} amr_index_maps;
+
+typedef struct {
+  int nu1, nu2;      /* pre/post smoothing sweeps (4, 4: Fig. mg_convergenceRate)        */
+  double omega;      /* weighted-Jacobi weight (2/3, Sec. 6.4)                           */
+  double rtol, atol; /* stop when ||f - A phi||_inf,valid <= max(rtol*||f||_inf, atol)    */
+  int max_vcycles;   /* hard cap on V-cycles (no unbounded device loop exists)            */
+  int precision;     /* AMR_FP64, or AMR_MIXED: FP32 V-cycles inside FP64 refinement      */
+  int zero_initial;  /* 1: start from phi = 0; 0: use phi as the initial guess            */
+  int use_graph;     /* 1: replay one captured CUDA graph per V-cycle                     */
+} amr_solver_params;
+
+typedef struct {
+  int vcycles;          /* V-cycles performed                                   */
+  double rhs_norm;      /* ||f||_inf over valid cells (after the solvability fix) */
+  double final_res;     /* ||f - A phi||_inf over valid cells at exit             */
+  double removed_mean;  /* pure Neumann: constant removed from f (Sec. 6.3)       */
+  double res_history[64]; /* residual norm before each V-cycle (first 64)         */
+} amr_solve_stats;
+
+/* ---- hierarchy ------------------------------------------------------------------ */
+amr_status amr_hierarchy_create(const amr_hierarchy_desc* desc, amr_hierarchy** out);
+void amr_hierarchy_destroy(amr_hierarchy* h);
+/* Number of patches, total elements of a composite field; ``patches`` (nullable) receives
+ * npatches entries. */
+amr_status amr_field_layout(const amr_hierarchy* h, int* npatches, long long* nelems,
+                            amr_patch_info* patches);
+/* offsets[l*2*dim + f] = element offset of face f of level l in a bc array;
+ * offsets[nlevels*2*dim] = total length.  ``offsets`` needs nlevels*2*dim+1 entries. */
+amr_status amr_bc_layout(const amr_hierarchy* h, long long* offsets);
+amr_status amr_get_index_maps(const amr_hierarchy* h, amr_index_maps* out);
+
+/* ---- operators -------------------------------------------------------------------- */
+/* alpha*I + beta*L with boundary types bc_types[2*dim] (face f = 2d+side); the PPE is
+ * alpha = 0, beta = 1 with all faces Neumann; the viscous systems alpha = 1,
+ * beta = -gamma*nu*k (Eq. GePUP-IMEX b).  Precomputes the dense bottom-solve inverse
+ * and allocates multigrid scratch.  Needs ratio 2. */
+amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, const int* bc_types,
+                               amr_operator** out);
+void amr_operator_destroy(amr_operator* op);
+
+/* COH-1 on a composite field: average down (Eq. AMR_avergingDownToCrse), then fill the
+ * stored ghost cells: copies from boxes of the same level and AMRCFI from the next coarser
+ * level (Sec. 5.2).  Ghost cells outside the physical domain are never stored: every
+ * kernel evaluates Eqs. (velBCHomoDiri5th)/(Neumann5) on the fly where a stencil leaves
+ * the domain.  Unused corner ghosts are not written.  bc is accepted for symmetry and
+ * not read. */
+amr_status amr_fill_ghosts(amr_operator* op, double* phi, const double* bc, void* stream);
+
+/* out = alpha*phi + beta*L^comp phi (COH-1..4, refluxing of Eq. cell2face fluxes). */
+amr_status amr_apply(amr_operator* op, double* phi, double* out, const double* bc, void* stream);
+
+/* res = f - A^comp phi on every covered cell (meaningful on valid cells);
+ * *norm (host, nullable) = ||res||_inf over valid cells (synchronises). */
+amr_status amr_residual(amr_operator* op, double* phi, const double* f, double* res,
+                        const double* bc, double* norm, void* stream);
+
+/* nsweeps weighted-Jacobi sweeps (true diagonal, homogeneous physical ghosts, zero CF
+ * ghosts) of level ``level``'s operator on x for right-hand side b (both composite fields;
+ * only that level is touched).  Kernel-level entry point of the smoother (Sec. 6.4). */
+amr_status amr_smooth(amr_operator* op, int level, int nsweeps, double omega, double* x,
+                      const double* b, void* stream);
+
+/* One composite V-cycle (Sec. 6.4) in FP64 on phi for right-hand side f. */
+amr_status amr_vcycle(amr_operator* op, const amr_solver_params* p, double* phi, const double* f,
+                      const double* bc, void* stream);
+
+/* V-cycles until the max-norm residual test of Sec. 7 passes.  Pure Neumann: f (const)
+ * is corrected into an internal copy (Sec. 6.3) and phi is returned with zero h^D-weighted
+ * mean over the valid cells.  stats (host, nullable). */
+amr_status amr_solve(amr_operator* op, const amr_solver_params* p, double* phi, const double* f,
+                     const double* bc, amr_solve_stats* stats, void* stream);
+
+/* Sec. 6.3 for the composite PPE: f -= m on every valid cell with
+ * m * sum_valid h^D = sum_valid h^D f - beta * sum_boundary h^(D-1) g (g = Neumann data in
+ * bc, NULL = 0), compensated sums.  *m (host, nullable) receives m.  One component: level
+ * 0 is the whole (connected) domain. */
+amr_status amr_solvability_fix(amr_operator* op, double* f, const double* bc, double* m, void* stream);
+
+/* phi -= (h^D-weighted mean over valid cells), compensated sums; *mean (nullable). */
+amr_status amr_mean_zero(amr_hierarchy* h, double* phi, double* mean, void* stream);
+
+/* G^comp (COH-1,2,4; Eq. discreteOps a): grad[d] = component d.  Ghosts of phi use
+ * bc_types (data bc, nullable). */
+amr_status amr_gradient(amr_hierarchy* h, const int* bc_types, double* phi, double* const* grad,
+                        const double* bc, void* stream);
+/* D^comp (COH-1..4 with refluxing of Eq. cell2face face values; Eq. discreteOps b).
+ * Ghosts of u[d] use bc_types with data bc[d] (array of dim pointers, or NULL). */
+amr_status amr_divergence(amr_hierarchy* h, const int* bc_types, double* const* u, double* out,
+                          const double* const* bc, void* stream);
+
+/* Composite projection u = w - G^comp (L^comp)^{-1} D^comp w (Eq. comp_ProjOp): ppe is an
+ * all-Neumann operator with alpha = 0, beta = 1; w ghosts use vel_bc_types with data
+ * w_bc[d] (nullable); no average-down of u afterwards (Lemma compositeProjection).
+ * phi (device, composite field) receives the mean-zero potential. */
+amr_status amr_project(amr_operator* ppe, const amr_solver_params* p, const int* vel_bc_types,
+                       double* const* w, const double* const* w_bc, double* const* u, double* phi,
+                       amr_solve_stats* stats, void* stream);
+
+/* Adjoint (transposed) operator: out = A^T y over the valid cells (homogeneous data);
+ * y and out are composite fields whose invalid cells are ignored (out's are set to 0). */
+amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, void* stream);
+/* lambda = A^{-T} g (the adjoint solve of a Helmholtz operator), by V-cycles on A^T. */
+amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, double* lambda,
+                               const double* g, amr_solve_stats* stats, void* stream);
+
+/* Host-buffer variant of amr_solve: phi and f are HOST pointers (pinned or pageable);
+ * the library copies them to its own device buffers and back inside the call. */
+amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* phi_host,
+                          const double* f_host, const double* bc_host, amr_solve_stats* stats,
+                          void* stream);
+
+void amr_default_params(amr_solver_params* p);
+const char* amr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMR4_H */

@@ -32,7 +32,7 @@ from .stencil import NG
 OK, ERR_INVALID_ARG, ERR_NESTING, ERR_REFINEMENT, ERR_BOX_TOO_SMALL = 0, 1, 2, 3, 4
 NESTING_MARGIN = 3
 MIN_BOX = 4
-MAX_BOTTOM_CELLS = 4096
+MAX_BOTTOM_CELLS = 1024
 
 # ghost-map codes (interface format shared with the library's index maps)
 G_INTERIOR, G_PHYS, G_COPY, G_CFI, G_UNUSED = 0, 1, 2, 3, 4
@@ -262,3 +262,84 @@ def _face_adjacent(a, b, D):
         if touch and all(max(a[0][e], b[0][e]) <= min(a[1][e], b[1][e]) for e in range(D) if e != d):
             return True
     return False
+
+
+def index_maps(H):
+    """Index maps in the library's canonical format (see the C header's amr_index_maps):
+    valid per interior cell (patch order, x fastest), component per box, ghost maps per
+    padded cell, AMRCFI ghost list, coarse cells with CF faces (COH-3)."""
+    from .cfi import window_start
+    D, r = H.D, H.ratio
+    valid, comp, code, src, aux = [], [], [], [], []
+    cfi_cell, cfi_start, cfi_pos, cfi_sub = [], [], [], []
+    rcell, rfaces = [], []
+    base = 0
+    for l, lev in enumerate(H.levels):
+        comp += H.components(l)
+        for k, (lo, hi) in enumerate(lev.boxes):
+            sub = lev.valid[lev.box_slice(lo, hi)]
+            valid += [int(v) for v in sub.transpose().ravel()]  # x fastest
+            c, s, a = H.ghost_map(l, k)
+            c_x = c.transpose().ravel()
+            code += [int(v) for v in c_x]
+            src += [int(v) for v in s.transpose().ravel()]
+            aux += [int(v) for v in a.transpose().ravel()]
+            ext = c.shape
+            for idx in np.nonzero(c_x == G_CFI)[0]:
+                # padded index -> coordinates (x fastest)
+                a_ = []
+                rem = int(idx)
+                for d in range(D):
+                    a_.append(rem % ext[d])
+                    rem //= ext[d]
+                g = [lo[d] - NG + a_[d] for d in range(D)]
+                crs = H.levels[l - 1]
+                par = [g[d] // r for d in range(D)]
+                st = [window_start(par[d], crs.ndom[d]) for d in range(D)]
+                cfi_cell.append(base + int(idx))
+                cfi_start.append(st)
+                cfi_pos.append([par[d] - st[d] for d in range(D)])
+                cfi_sub.append([g[d] - r * par[d] for d in range(D)])
+            base += c.size
+    for l in range(H.lmax):
+        lev = H.levels[l]
+        faces = {}
+        for d in range(D):
+            for s in (1, -1):
+                nb = np.zeros(lev.shape, bool)
+                src_, dst_ = [slice(None)] * D, [slice(None)] * D
+                if s == 1:
+                    dst_[d], src_[d] = slice(0, -1), slice(1, None)
+                else:
+                    dst_[d], src_[d] = slice(1, None), slice(0, -1)
+                nb[tuple(dst_)] = lev.invalid[tuple(src_)]
+                for cell in np.argwhere(lev.valid & nb):
+                    key = tuple(int(v) for v in cell)
+                    faces[key] = faces.get(key, 0) | (1 << (2 * d + (1 if s == 1 else 0)))
+        for k, (lo, hi) in enumerate(lev.boxes):
+            n = [hi[d] - lo[d] + 1 for d in range(D)]
+            ents = []
+            for key, f in faces.items():
+                g = [key[d] + lev.origin[d] for d in range(D)]
+                if all(lo[d] <= g[d] <= hi[d] for d in range(D)):
+                    lin, stride = 0, 1
+                    for d in range(D):
+                        lin += (g[d] - lo[d]) * stride
+                        stride *= n[d]
+                    ents.append((lin, f))
+            for lin, f in sorted(ents):
+                rcell.append([l, k, lin])
+                rfaces.append(f)
+    return {
+        "valid": np.asarray(valid, np.int32),
+        "component": np.asarray(comp, np.int32),
+        "ghost_code": np.asarray(code, np.int32),
+        "ghost_src": np.asarray(src, np.int32),
+        "ghost_aux": np.asarray(aux, np.int32),
+        "cfi_cell": np.asarray(cfi_cell, np.int64),
+        "cfi_start": np.asarray(cfi_start, np.int32).reshape(-1, D),
+        "cfi_pos": np.asarray(cfi_pos, np.int32).reshape(-1, D),
+        "cfi_sub": np.asarray(cfi_sub, np.int32).reshape(-1, D),
+        "reflux_cell": np.asarray(rcell, np.int32).reshape(-1, 3),
+        "reflux_faces": np.asarray(rfaces, np.int32),
+    }

@@ -14,7 +14,7 @@ the max-norm residual stopping test.  Readings taken where it is silent:
   operator by probing, by definition;
 * coarse multigrid operators are re-discretisations (same formulas, h doubled, same
   boundary types, homogeneous data);
-* the bottom solver is a dense direct solve on the coarsest grid (at most 4096 cells); for
+* the bottom solver is a dense direct solve on the coarsest grid (at most 1024 cells); for
   the pure-Neumann operator it is bordered with the mean constraint;
 * AMR levels: a composite V-cycle in correction form visits the finest AMR level first,
   smoothing each level with zero coarse-fine ghosts, passes to the next coarser level the

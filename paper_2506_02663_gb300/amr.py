@@ -1,0 +1,381 @@
+"""Thin Python binding of libamr4 (ctypes).  Argument marshalling only: every step of the
+solver runs in the library's CUDA kernels.  The library must have been built
+(``__graft_entry__.build()``); importing this module without it raises ImportError --
+there is no fallback path.
+
+Field arguments are torch CUDA tensors (float64, contiguous, ``numel == nelems``) holding
+a composite field in the library's padded layout (``Hierarchy.pack`` / ``unpack`` convert
+from and to per-box numpy arrays whose axis d is the paper's dimension d).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"libamr4 is not built ({LIB} missing); run __graft_entry__.build()")
+_lib = C.CDLL(LIB)
+
+AMR_OK, AMR_ERR_INVALID_ARG, AMR_ERR_NESTING, AMR_ERR_REFINEMENT, AMR_ERR_BOX_TOO_SMALL = 0, 1, 2, 3, 4
+AMR_ERR_NOT_CONVERGED, AMR_ERR_NONFINITE, AMR_ERR_CUDA, AMR_ERR_OOM = 5, 6, 7, 8
+DIRICHLET, NEUMANN = 0, 1
+FP64, MIXED = 0, 1
+NG = 2
+
+
+class HierarchyDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("ratio", C.c_int), ("n0", C.c_int * 3), ("h0", C.c_double),
+                ("nlevels", C.c_int), ("nboxes", C.POINTER(C.c_int)), ("boxes", C.POINTER(C.c_int))]
+
+
+class PatchInfo(C.Structure):
+    _fields_ = [("level", C.c_int), ("box", C.c_int), ("lo", C.c_int * 3), ("hi", C.c_int * 3),
+                ("offset", C.c_longlong), ("stride_y", C.c_longlong), ("stride_z", C.c_longlong),
+                ("nelems", C.c_longlong)]
+
+
+class IndexMaps(C.Structure):
+    _fields_ = [("ncells_interior", C.c_longlong), ("ncells_padded", C.c_longlong),
+                ("valid", C.POINTER(C.c_int)), ("component", C.POINTER(C.c_int)),
+                ("ghost_code", C.POINTER(C.c_int)), ("ghost_src", C.POINTER(C.c_int)),
+                ("ghost_aux", C.POINTER(C.c_int)), ("ncfi", C.c_longlong),
+                ("cfi_cell", C.POINTER(C.c_longlong)), ("cfi_start", C.POINTER(C.c_int)),
+                ("cfi_pos", C.POINTER(C.c_int)), ("cfi_sub", C.POINTER(C.c_int)),
+                ("nreflux", C.c_longlong), ("reflux_cell", C.POINTER(C.c_int)),
+                ("reflux_faces", C.POINTER(C.c_int))]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("rtol", C.c_double),
+                ("atol", C.c_double), ("max_vcycles", C.c_int), ("precision", C.c_int),
+                ("zero_initial", C.c_int), ("use_graph", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("vcycles", C.c_int), ("rhs_norm", C.c_double), ("final_res", C.c_double),
+                ("removed_mean", C.c_double), ("res_history", C.c_double * 64)]
+
+
+_vp = C.c_void_p
+_P = C.POINTER
+_sigs = {
+    "amr_hierarchy_create": [_P(HierarchyDesc), _P(_vp)],
+    "amr_hierarchy_destroy": [_vp],
+    "amr_field_layout": [_vp, _P(C.c_int), _P(C.c_longlong), _P(PatchInfo)],
+    "amr_bc_layout": [_vp, _P(C.c_longlong)],
+    "amr_get_index_maps": [_vp, _P(IndexMaps)],
+    "amr_operator_create": [_vp, C.c_double, C.c_double, _P(C.c_int), _P(_vp)],
+    "amr_operator_destroy": [_vp],
+    "amr_fill_ghosts": [_vp, _vp, _vp, _vp],
+    "amr_apply": [_vp, _vp, _vp, _vp, _vp],
+    "amr_residual": [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _vp],
+    "amr_smooth": [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp],
+    "amr_vcycle": [_vp, _P(SolverParams), _vp, _vp, _vp, _vp],
+    "amr_solve": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
+    "amr_solve_host": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
+    "amr_solvability_fix": [_vp, _vp, _vp, _P(C.c_double), _vp],
+    "amr_mean_zero": [_vp, _vp, _P(C.c_double), _vp],
+    "amr_gradient": [_vp, _P(C.c_int), _vp, _P(_vp), _vp, _vp],
+    "amr_divergence": [_vp, _P(C.c_int), _P(_vp), _vp, _P(_vp), _vp],
+    "amr_project": [_vp, _P(SolverParams), _P(C.c_int), _P(_vp), _P(_vp), _P(_vp), _vp, _P(SolveStats), _vp],
+    "amr_apply_transpose": [_vp, _vp, _vp, _vp],
+    "amr_solve_transpose": [_vp, _P(SolverParams), _vp, _vp, _P(SolveStats), _vp],
+    "amr_default_params": [_P(SolverParams)],
+    "amr_last_error": [],
+}
+for _n, _a in _sigs.items():
+    _f = getattr(_lib, _n)
+    _f.argtypes = _a
+    _f.restype = C.c_int
+_lib.amr_hierarchy_destroy.restype = None
+_lib.amr_operator_destroy.restype = None
+_lib.amr_default_params.restype = None
+_lib.amr_last_error.restype = C.c_char_p
+
+EXPORTED = tuple(_sigs)
+
+
+class AmrError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.amr_last_error().decode(errors="replace")
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(st, where, ok=(AMR_OK,)):
+    if st not in ok:
+        raise AmrError(st, where)
+    return st
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return _vp(t.data_ptr())
+    return _vp(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return _vp(stream.cuda_stream)
+    return _vp(int(stream))
+
+
+def default_params(**kw):
+    p = SolverParams()
+    _lib.amr_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def stats_dict(s):
+    n = min(s.vcycles + 1, 64)
+    return {"vcycles": s.vcycles, "rhs_norm": s.rhs_norm, "final_res": s.final_res,
+            "removed_mean": s.removed_mean, "res_history": list(s.res_history[:n])}
+
+
+class Hierarchy:
+    """amr_hierarchy: boxes per level as [(lo, hi), ...] with inclusive tuples."""
+
+    def __init__(self, dim, n0, boxes, h0=None, ratio=2):
+        self.dim = dim
+        self.n0 = tuple(n0)
+        self.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in bl] for bl in boxes]
+        self.nlevels = len(boxes)
+        self.h0 = h0 if h0 is not None else 1.0 / n0[0]
+        nb = (C.c_int * self.nlevels)(*[len(b) for b in boxes])
+        flat = []
+        for bl in boxes:
+            for lo, hi in bl:
+                flat += list(lo) + list(hi)
+        fb = (C.c_int * len(flat))(*flat)
+        d = HierarchyDesc(dim, ratio, (C.c_int * 3)(*(list(n0) + [1] * (3 - dim))), self.h0,
+                          self.nlevels, nb, fb)
+        self._h = _vp()
+        _check(_lib.amr_hierarchy_create(C.byref(d), C.byref(self._h)), "amr_hierarchy_create")
+        npatch = C.c_int()
+        ne = C.c_longlong()
+        _check(_lib.amr_field_layout(self._h, C.byref(npatch), C.byref(ne), None), "amr_field_layout")
+        arr = (PatchInfo * npatch.value)()
+        _check(_lib.amr_field_layout(self._h, None, None, arr), "amr_field_layout")
+        self.nelems = ne.value
+        self.patches = [{"level": p.level, "box": p.box, "lo": tuple(p.lo[:dim]), "hi": tuple(p.hi[:dim]),
+                         "offset": p.offset, "sy": p.stride_y, "sz": p.stride_z, "nelems": p.nelems}
+                        for p in arr]
+        offs = (C.c_longlong * (self.nlevels * 2 * dim + 1))()
+        _check(_lib.amr_bc_layout(self._h, offs), "amr_bc_layout")
+        self.bc_offsets = list(offs)
+        self.ratio = ratio
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.amr_hierarchy_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- index maps
+    def index_maps(self):
+        m = IndexMaps()
+        _check(_lib.amr_get_index_maps(self._h, C.byref(m)), "amr_get_index_maps")
+
+        def arr(ptr, n, dt):
+            if n == 0:
+                return np.zeros(0, dt)
+            return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt).copy()
+
+        D = self.dim
+        return {
+            "valid": arr(m.valid, m.ncells_interior, np.int32),
+            "component": arr(m.component, sum(len(b) for b in self.boxes), np.int32),
+            "ghost_code": arr(m.ghost_code, m.ncells_padded, np.int32),
+            "ghost_src": arr(m.ghost_src, m.ncells_padded, np.int32),
+            "ghost_aux": arr(m.ghost_aux, m.ncells_padded, np.int32),
+            "cfi_cell": arr(m.cfi_cell, m.ncfi, np.int64),
+            "cfi_start": arr(m.cfi_start, m.ncfi * D, np.int32).reshape(-1, D),
+            "cfi_pos": arr(m.cfi_pos, m.ncfi * D, np.int32).reshape(-1, D),
+            "cfi_sub": arr(m.cfi_sub, m.ncfi * D, np.int32).reshape(-1, D),
+            "reflux_cell": arr(m.reflux_cell, m.nreflux * 3, np.int32).reshape(-1, 3),
+            "reflux_faces": arr(m.reflux_faces, m.nreflux, np.int32),
+        }
+
+    # ---------------------------------------------------------------- marshalling
+    def _view(self, arr, p):
+        """Padded [z][y][x] view of patch p inside a flat composite array."""
+        D = self.dim
+        n = [p["hi"][d] - p["lo"][d] + 1 for d in range(D)]
+        seg = arr[p["offset"]:p["offset"] + p["nelems"]]
+        if D == 2:
+            return seg.reshape(n[1] + 2 * NG, p["sy"])
+        return seg.reshape(n[2] + 2 * NG, n[1] + 2 * NG, p["sy"])
+
+    def interior(self, arr, p):
+        D = self.dim
+        n = [p["hi"][d] - p["lo"][d] + 1 for d in range(D)]
+        v = self._view(arr, p)
+        if D == 2:
+            return v[NG:NG + n[1], NG:NG + n[0]]
+        return v[NG:NG + n[2], NG:NG + n[1], NG:NG + n[0]]
+
+    def pack(self, per_box, fill=0.0, dtype=np.float64):
+        """per_box[l][k]: array with axis d = dimension d over box k of level l."""
+        out = np.full(self.nelems, fill, dtype=dtype)
+        i = 0
+        for l, bl in enumerate(self.boxes):
+            for k in range(len(bl)):
+                p = self.patches[i]
+                self.interior(out, p)[...] = np.asarray(per_box[l][k]).transpose()
+                i += 1
+        return out
+
+    def unpack(self, flat):
+        """Composite flat numpy array -> per_box[l][k] arrays (axis d = dimension d)."""
+        flat = np.asarray(flat)
+        out = []
+        i = 0
+        for l, bl in enumerate(self.boxes):
+            lev = []
+            for k in range(len(bl)):
+                lev.append(self.interior(flat, self.patches[i]).transpose().copy())
+                i += 1
+            out.append(lev)
+        return out
+
+    def pack_bc(self, data):
+        """data[l]: dict face -> array over the domain face at level l (axis order of the
+        remaining dimensions), or None.  Returns the flat bc array of the ABI layout."""
+        D = self.dim
+        out = np.zeros(self.bc_offsets[-1])
+        for l in range(self.nlevels):
+            if data is None or data[l] is None:
+                continue
+            for f in range(2 * D):
+                if f in data[l] and data[l][f] is not None:
+                    a = self.bc_offsets[l * 2 * D + f]
+                    b = self.bc_offsets[l * 2 * D + f + 1]
+                    out[a:b] = np.asarray(data[l][f], dtype=np.float64).transpose().ravel()
+        return out
+
+
+class Operator:
+    """amr_operator: alpha*I + beta*L^comp with boundary types bc_types (2*dim ints)."""
+
+    def __init__(self, hier, alpha, beta, bc_types):
+        self.h = hier
+        self.alpha, self.beta = alpha, beta
+        self.bc_types = list(bc_types)
+        bt = (C.c_int * len(bc_types))(*bc_types)
+        self._op = _vp()
+        _check(_lib.amr_operator_create(hier.handle, alpha, beta, bt, C.byref(self._op)), "amr_operator_create")
+
+    def close(self):
+        if self._op:
+            _lib.amr_operator_destroy(self._op)
+            self._op = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fill_ghosts(self, phi, bc=None, stream=None):
+        _check(_lib.amr_fill_ghosts(self._op, _ptr(phi), _ptr(bc), _stream(stream)), "amr_fill_ghosts")
+
+    def apply(self, phi, out, bc=None, stream=None):
+        _check(_lib.amr_apply(self._op, _ptr(phi), _ptr(out), _ptr(bc), _stream(stream)), "amr_apply")
+
+    def residual(self, phi, f, res, bc=None, stream=None):
+        nrm = C.c_double()
+        _check(_lib.amr_residual(self._op, _ptr(phi), _ptr(f), _ptr(res), _ptr(bc), C.byref(nrm),
+                                 _stream(stream)), "amr_residual")
+        return nrm.value
+
+    def smooth(self, level, nsweeps, omega, x, b, stream=None):
+        _check(_lib.amr_smooth(self._op, level, nsweeps, omega, _ptr(x), _ptr(b), _stream(stream)), "amr_smooth")
+
+    def vcycle(self, phi, f, bc=None, params=None, stream=None):
+        p = params or default_params()
+        _check(_lib.amr_vcycle(self._op, C.byref(p), _ptr(phi), _ptr(f), _ptr(bc), _stream(stream)), "amr_vcycle")
+
+    def solve(self, phi, f, bc=None, params=None, stream=None, allow_not_converged=False):
+        p = params or default_params()
+        s = SolveStats()
+        ok = (AMR_OK, AMR_ERR_NOT_CONVERGED) if allow_not_converged else (AMR_OK,)
+        st = _lib.amr_solve(self._op, C.byref(p), _ptr(phi), _ptr(f), _ptr(bc), C.byref(s), _stream(stream))
+        _check(st, "amr_solve", ok)
+        d = stats_dict(s)
+        d["status"] = st
+        return d
+
+    def solve_host(self, phi_host, f_host, bc_host=None, params=None, stream=None):
+        """phi_host / f_host: numpy float64 arrays (HOST memory) in the composite layout."""
+        p = params or default_params()
+        s = SolveStats()
+        bcp = None if bc_host is None else _vp(bc_host.ctypes.data)
+        _check(_lib.amr_solve_host(self._op, C.byref(p), _vp(phi_host.ctypes.data), _vp(f_host.ctypes.data), bcp,
+                                   C.byref(s), _stream(stream)), "amr_solve_host")
+        return stats_dict(s)
+
+    def solvability_fix(self, f, bc=None, stream=None):
+        m = C.c_double()
+        _check(_lib.amr_solvability_fix(self._op, _ptr(f), _ptr(bc), C.byref(m), _stream(stream)),
+               "amr_solvability_fix")
+        return m.value
+
+    def apply_transpose(self, y, out, stream=None):
+        _check(_lib.amr_apply_transpose(self._op, _ptr(y), _ptr(out), _stream(stream)), "amr_apply_transpose")
+
+    def solve_transpose(self, lam, g, params=None, stream=None):
+        p = params or default_params()
+        s = SolveStats()
+        _check(_lib.amr_solve_transpose(self._op, C.byref(p), _ptr(lam), _ptr(g), C.byref(s), _stream(stream)),
+               "amr_solve_transpose")
+        return stats_dict(s)
+
+
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def mean_zero(hier, phi, stream=None):
+    m = C.c_double()
+    _check(_lib.amr_mean_zero(hier.handle, _ptr(phi), C.byref(m), _stream(stream)), "amr_mean_zero")
+    return m.value
+
+
+def gradient(hier, bc_types, phi, grads, bc=None, stream=None):
+    bt = (C.c_int * len(bc_types))(*bc_types)
+    _check(_lib.amr_gradient(hier.handle, bt, _ptr(phi), _ptr_array(grads), _ptr(bc), _stream(stream)),
+           "amr_gradient")
+
+
+def divergence(hier, bc_types, u, out, bc=None, stream=None):
+    bt = (C.c_int * len(bc_types))(*bc_types)
+    bcp = None if bc is None else _ptr_array(bc)
+    _check(_lib.amr_divergence(hier.handle, bt, _ptr_array(u), _ptr(out), bcp, _stream(stream)), "amr_divergence")
+
+
+def project(ppe, vel_bc_types, w, u, phi, w_bc=None, params=None, stream=None):
+    p = params or default_params()
+    s = SolveStats()
+    bt = (C.c_int * len(vel_bc_types))(*vel_bc_types)
+    wb = None if w_bc is None else _ptr_array(w_bc)
+    _check(_lib.amr_project(ppe._op, C.byref(p), bt, _ptr_array(w), wb, _ptr_array(u), _ptr(phi), C.byref(s),
+                            _stream(stream)), "amr_project")
+    return stats_dict(s)

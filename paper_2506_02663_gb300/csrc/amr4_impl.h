@@ -1,0 +1,154 @@
+// Internal data structures of libamr4 (host C++ and CUDA).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/amr4.h"
+
+namespace amr4 {
+
+constexpr int NG = 2;         // ghost layers (Sec. 3, paragraph after Eq. appProj)
+constexpr int CFI_W = 5;      // AMRCFI window width (degree-4 reconstruction)
+constexpr int MIN_BOX = 4;    // one-sided ghost formulas read 4 interior cells
+constexpr int NEST_MARGIN = 3;
+constexpr int MAX_BOTTOM = 1024;
+
+// One padded patch of a composite field (device-visible, trivially copyable).
+struct PatchDesc {
+  long long off;   // element offset of the padded patch
+  long long sy;    // y stride (elements)
+  long long sz;    // z stride (elements; = sy*(ny+4) in 3-D, 0 in 2-D)
+  int n[3];        // interior extents (1 in unused dimensions)
+  int lo[3];       // global index of interior cell (0,0,0) at its level
+};
+
+// Level description passed by value to kernels.
+struct LevelView {
+  const PatchDesc* patches;  // device array
+  int npatch;
+  int D;
+  int ndom[3];
+  int maxn[3];               // largest interior extents (launch shape)
+  double h;
+  int bc[6];                 // boundary type per face
+  long long bc_off[6];       // offsets of this level's faces inside a bc array
+  long long bc_pitch[6];     // leading extent of each face array (transverse dim 0)
+};
+
+// AMRCFI ghost cell: dst = fine field offset; src >= 0: field offset of the window's first
+// coarse cell in coarse patch cpatch; src < 0: -(1+k) with the 5^D offsets at side[k*5^D].
+struct CfiEntry {
+  long long dst;
+  long long src;
+  int cpatch;
+  signed char pos[3];
+  signed char sub[3];
+  signed char pad[2];
+};
+
+struct CopyEntry {
+  long long dst;
+  long long src;
+};
+
+// Coarse valid cell with >= 1 coarse-fine face (COH-3).
+struct RefluxEntry {
+  long long coff;   // coarse field offset of the cell
+  int cpatch;       // coarse patch
+  int faces;        // bit 2d+side
+  int g[3];         // coarse global index
+  int fpatch[6];    // fine patch that covers the neighbour across face 2d+side
+};
+
+// Fine box x coarse box intersection, used for restriction / average-down / prolongation.
+struct XferBlock {
+  int fpatch;
+  int cpatch;
+  int clo[3];  // coarse global region [clo, chi]
+  int chi[3];
+};
+
+struct Box {
+  int lo[3];
+  int hi[3];
+};
+
+struct DeviceLists {
+  CfiEntry* cfi = nullptr;
+  long long* cfi_side = nullptr;
+  long long ncfi = 0;
+  CopyEntry* copy = nullptr;
+  long long ncopy = 0;
+  RefluxEntry* reflux = nullptr;
+  long long nreflux = 0;
+  XferBlock* xfer = nullptr;  // blocks between this level (coarse) and level+1
+  int nxfer = 0;
+  int xfer_max[3] = {1, 1, 1};  // largest coarse region extent
+};
+
+struct LevelHost {
+  std::vector<Box> boxes;
+  int ndom[3] = {1, 1, 1};
+  double h = 0.0;
+  std::vector<PatchDesc> patches;
+  int first_patch = 0;  // global patch index of the first patch
+  PatchDesc* d_patches = nullptr;
+  std::vector<CfiEntry> cfi;
+  std::vector<long long> cfi_side;
+  std::vector<CopyEntry> copy;
+  std::vector<RefluxEntry> reflux;  // this level's coarse cells bordering level+1
+  std::vector<XferBlock> xfer;      // this level (coarse) <-> level+1 (fine)
+  DeviceLists dev;
+  int maxn[3] = {1, 1, 1};
+};
+
+// A single-box grid of the level-0 multigrid pyramid.
+struct MgGrid {
+  int n[3] = {1, 1, 1};
+  double h = 0.0;
+  PatchDesc patch{};
+  PatchDesc* d_patch = nullptr;
+  long long nelems = 0;
+};
+
+}  // namespace amr4
+
+struct amr_hierarchy {
+  int D = 2;
+  int r = 2;
+  int n0[3] = {1, 1, 1};
+  double h0 = 0.0;
+  int L = 0;  // number of levels
+  std::vector<amr4::LevelHost> lev;
+  long long nelems = 0;
+  int npatch = 0;
+  std::vector<amr_patch_info> pinfo;
+  unsigned char* d_valid = nullptr;  // composite layout: 1 on valid interior cells
+  std::vector<long long> bc_off;     // nlevels*2D + 1
+  std::vector<amr4::MgGrid> mg;      // level-0 multigrid grids (mg[0] = level 0 itself)
+  // index maps (host)
+  std::vector<int> im_valid, im_component, im_code, im_src, im_aux;
+  std::vector<long long> im_cfi_cell;
+  std::vector<int> im_cfi_start, im_cfi_pos, im_cfi_sub;
+  std::vector<int> im_reflux_cell, im_reflux_faces;
+  // CFI weights W[pos][sub][a] (exact rationals rounded once), ratio r
+  std::vector<double> cfi_w;
+  // reduction scratch (device)
+  double* d_red = nullptr;       // partials
+  double* d_scalar = nullptr;    // a few device scalars
+  double* h_scalar = nullptr;    // pinned host mirror
+  bool on_device = false;
+};
+
+namespace amr4 {
+// hierarchy.cpp
+amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std::string& err);
+void free_hierarchy(amr_hierarchy* h);
+amr_status upload_hierarchy(amr_hierarchy* h, std::string& err);
+void set_error(const std::string& msg);
+const char* get_error();
+void cfi_weights_exact(int r, std::vector<double>& w);  // [pos][sub][a], 5 x r x 5
+LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types);
+}  // namespace amr4

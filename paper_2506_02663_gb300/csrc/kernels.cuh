@@ -1,0 +1,630 @@
+// sm_103a kernels of libamr4.  Templated on the value type T (double / float) and the
+// dimension D (2 / 3).  Every kernel works on padded patches (PatchDesc); physical ghost
+// values are evaluated on the fly from Eqs. (velBCHomoDiri5th)/(Neumann5) whenever a stencil
+// leaves the domain, so no kernel depends on physical ghost cells stored in memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "amr4_impl.h"
+
+namespace amr4 {
+
+// Eq. (velBCHomoDiri5th) and Eq. (Neumann5): [bc type][layer-1][m], m = 0..3 inward.
+__constant__ double c_ghost[2][2][4] = {
+    {{-77.0 / 12.0, 43.0 / 12.0, -17.0 / 12.0, 3.0 / 12.0},
+     {-505.0 / 12.0, 335.0 / 12.0, -145.0 / 12.0, 27.0 / 12.0}},
+    {{5.0 / 10.0, 9.0 / 10.0, -5.0 / 10.0, 1.0 / 10.0},
+     {-75.0 / 10.0, 145.0 / 10.0, -75.0 / 10.0, 15.0 / 10.0}}};
+// data coefficient: Dirichlet b (x face value), Neumann b (x h x outward derivative)
+__constant__ double c_ghost_b[2][2] = {{5.0, 75.0 / 3.0}, {6.0 / 5.0, 6.0}};
+// AMRCFI 1-D weights [pos][sub][a] for ratio r (r <= 4), set by the host
+__constant__ double c_cfi[5 * 4 * 5];
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+
+struct Cell {
+  int c[3];  // local interior coordinates (may be -2..n+1)
+};
+
+__device__ __forceinline__ long long poff(const PatchDesc& p, int i, int j, int k) {
+  return p.off + (long long)(i + NG) + (long long)(j + NG) * p.sy + (long long)(k + NG) * p.sz;
+}
+
+// Map a (blockIdx, threadIdx) to a cell of patch blockIdx.z; false when outside.
+template <int D>
+__device__ __forceinline__ bool thread_cell(const PatchDesc& p, int nby, int& i, int& j, int& k) {
+  i = blockIdx.x * BX + threadIdx.x;
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  k = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  j = by * BY + threadIdx.y;
+  return i < p.n[0] && j < p.n[1] && k < p.n[2];
+}
+
+// Physical ghost value at local coordinates c (outside the domain along dimension d only).
+template <typename T, int D>
+__device__ T phys_ghost(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv,
+                        const T* __restrict__ bc, int ci, int cj, int ck, int d) {
+  int c[3] = {ci, cj, ck};
+  const int g = p.lo[d] + c[d];
+  const int side = g < 0 ? 0 : 1;
+  const int layer = side == 0 ? -g : g - lv.ndom[d] + 1;  // 1 or 2
+  const int f = 2 * d + side;
+  const int type = lv.bc[f];
+  T v = T(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[d] = side == 0 ? (m - p.lo[d]) : (lv.ndom[d] - 1 - m - p.lo[d]);
+    v += T(c_ghost[type][layer - 1][m]) * x[poff(p, cc[0], cc[1], cc[2])];
+  }
+  if (bc != nullptr) {
+    // transverse index over the domain face, lowest remaining dimension fastest
+    long long t = 0, s = 1;
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      t += (long long)(p.lo[e] + c[e]) * s;
+      s *= lv.ndom[e];
+    }
+    const T gv = bc[lv.bc_off[f] + t];
+    const T b = T(c_ghost_b[type][layer - 1]) * (type == 1 ? T(lv.h) : T(1));
+    v += b * gv;
+  }
+  return v;
+}
+
+// x at local coordinates (ci,cj,ck), evaluating physical ghosts on the fly.  ``ood`` is the
+// single dimension that may leave the domain (-1: none checked).
+template <typename T, int D>
+__device__ __forceinline__ T read_nb(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv,
+                                     const T* __restrict__ bc, int ci, int cj, int ck, int d) {
+  const int c[3] = {ci, cj, ck};
+  const int g = p.lo[d] + c[d];
+  if (g < 0 || g >= lv.ndom[d]) return phys_ghost<T, D>(x, p, lv, bc, ci, cj, ck, d);
+  return x[poff(p, ci, cj, ck)];
+}
+
+// Homogeneous physical extension with corners: each out-of-domain dimension is expanded
+// with the layer formula (Fig. 1(c): corner ghosts from already-extended values).
+template <typename T, int D>
+__device__ T read_ext(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int ci, int cj, int ck) {
+  const int c[3] = {ci, cj, ck};
+  int idx[3][4];
+  double w[3][4];
+  int cnt[3] = {1, 1, 1};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    idx[e][0] = c[e];
+    w[e][0] = 1.0;
+    if (e >= D) continue;
+    const int g = p.lo[e] + c[e];
+    if (g < 0 || g >= lv.ndom[e]) {
+      const int side = g < 0 ? 0 : 1;
+      const int layer = side == 0 ? -g : g - lv.ndom[e] + 1;
+      const int type = lv.bc[2 * e + side];
+      cnt[e] = 4;
+      for (int m = 0; m < 4; ++m) {
+        idx[e][m] = side == 0 ? (m - p.lo[e]) : (lv.ndom[e] - 1 - m - p.lo[e]);
+        w[e][m] = c_ghost[type][layer - 1][m];
+      }
+    }
+  }
+  T v = T(0);
+  for (int a = 0; a < cnt[0]; ++a)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int q = 0; q < cnt[2]; ++q)
+        v += T(w[0][a] * w[1][b] * w[2][q]) * x[poff(p, idx[0][a], idx[1][b], idx[2][q])];
+  return v;
+}
+
+// 1-D contribution to the true Jacobi diagonal (x 12 h^2): -30, plus the ghost-cell
+// coefficients that fall back on the cell itself near a physical face.
+__device__ __forceinline__ double diag_1d(int g, int ndom, int blo, int bhi) {
+  double a = -30.0;
+  if (g == 0) a += 16.0 * c_ghost[blo][0][0] - c_ghost[blo][1][0];
+  else if (g == 1) a += -c_ghost[blo][0][1];
+  if (g == ndom - 1) a += 16.0 * c_ghost[bhi][0][0] - c_ghost[bhi][1][0];
+  else if (g == ndom - 2) a += -c_ghost[bhi][0][1];
+  return a;
+}
+
+// ------------------------------------------------------------------------ level operator
+// MODE 0: out = alpha x + beta L x
+// MODE 1: out = f - (alpha x + beta L x)
+// MODE 2: out = x + omega (f - A x) / diag        (weighted Jacobi, Sec. 6.4)
+// MODE 3: out = omega f / diag                    (first sweep from x = 0)
+enum { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
+
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, const T* __restrict__ x,
+                                                     const T* __restrict__ f, T* __restrict__ out,
+                                                     const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                     const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (vmask != nullptr && vmask[o] == 0) return;
+  const T inv = T(1.0 / (12.0 * lv.h * lv.h));
+  if (MODE == OP_JACOBI0) {
+    double dg = 0.0;
+    const int c[3] = {i, j, k};
+    for (int d = 0; d < D; ++d) dg += diag_1d(p.lo[d] + c[d], lv.ndom[d], lv.bc[2 * d], lv.bc[2 * d + 1]);
+    const T diag = alpha + beta * inv * T(dg);
+    out[o] = omega * f[o] / diag;
+    return;
+  }
+  const T xc = x[o];
+  T acc = T(0);
+  const int c[3] = {i, j, k};
+  const long long st[3] = {1, p.sy, p.sz};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int g = p.lo[d] + c[d];
+    T m1, p1, m2, p2;
+    if (g >= 2 && g <= lv.ndom[d] - 3) {
+      m1 = x[o - st[d]];
+      p1 = x[o + st[d]];
+      m2 = x[o - 2 * st[d]];
+      p2 = x[o + 2 * st[d]];
+    } else {
+      int cc[3] = {i, j, k};
+      cc[d] = c[d] - 1; m1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] + 1; p1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] - 2; m2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] + 2; p2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    }
+    acc += T(16) * (m1 + p1) - (m2 + p2);
+  }
+  acc -= T(30 * D) * xc;
+  const T ax = alpha * xc + beta * (acc * inv);
+  if (MODE == OP_APPLY) {
+    out[o] = ax;
+  } else if (MODE == OP_RESID) {
+    out[o] = f[o] - ax;
+  } else {
+    double dg = 0.0;
+    for (int d = 0; d < D; ++d) dg += diag_1d(p.lo[d] + c[d], lv.ndom[d], lv.bc[2 * d], lv.bc[2 * d + 1]);
+    const T diag = alpha + beta * inv * T(dg);
+    out[o] = xc + omega * (f[o] - ax) / diag;
+  }
+}
+
+// ------------------------------------------------------------------------ G and D
+// grad: out_d = (-x_{+2} + 8 x_{+1} - 8 x_{-1} + x_{-2}) / (12 h)   (Eq. discreteOps a)
+template <typename T, int D>
+__global__ void k_gradient(LevelView lv, int nby, const T* __restrict__ x, T* __restrict__ g0, T* __restrict__ g1,
+                           T* __restrict__ g2, const T* __restrict__ bc) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  const T inv = T(1.0 / (12.0 * lv.h));
+  T* outs[3] = {g0, g1, g2};
+  const int c[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int cc[3] = {i, j, k};
+    cc[d] = c[d] - 1; const T m1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] + 1; const T p1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] - 2; const T m2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] + 2; const T p2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    outs[d][o] = (T(8) * (p1 - m1) - (p2 - m2)) * inv;
+  }
+}
+
+struct Ptr3 {
+  const double* p[3];
+};
+struct Ptr3m {
+  double* p[3];
+};
+
+// div: sum_d (-u_{+2} + 8 u_{+1} - 8 u_{-1} + u_{-2}) / (12 h)   (Eq. discreteOps b)
+template <int D>
+__global__ void k_divergence(LevelView lv, int nby, Ptr3 u, double* __restrict__ out, Ptr3 bc) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  const double inv = 1.0 / (12.0 * lv.h);
+  const int c[3] = {i, j, k};
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double* x = u.p[d];
+    int cc[3] = {i, j, k};
+    cc[d] = c[d] - 1; const double m1 = read_nb<double, D>(x, p, lv, bc.p[d], cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] + 1; const double p1 = read_nb<double, D>(x, p, lv, bc.p[d], cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] - 2; const double m2 = read_nb<double, D>(x, p, lv, bc.p[d], cc[0], cc[1], cc[2], d);
+    cc[d] = c[d] + 2; const double p2 = read_nb<double, D>(x, p, lv, bc.p[d], cc[0], cc[1], cc[2], d);
+    acc += 8.0 * (p1 - m1) - (p2 - m2);
+  }
+  out[o] = acc * inv;
+}
+
+// ------------------------------------------------------------------------ AMRCFI / copy
+template <typename T, int D>
+__global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long long* __restrict__ side,
+                      const PatchDesc* __restrict__ cpatches, int r, const T* __restrict__ xc, T* __restrict__ xf,
+                      int zero) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CfiEntry e = list[t];
+  if (zero) {
+    xf[e.dst] = T(0);
+    return;
+  }
+  const double* w0 = &c_cfi[(e.pos[0] * r + e.sub[0]) * CFI_W];
+  const double* w1 = &c_cfi[(e.pos[1] * r + e.sub[1]) * CFI_W];
+  const double* w2 = &c_cfi[(e.pos[2] * r + e.sub[2]) * CFI_W];
+  T v = T(0);
+  if (e.src >= 0) {
+    const PatchDesc cp = cpatches[e.cpatch];
+    for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
+      for (int c1 = 0; c1 < CFI_W; ++c1) {
+        const long long row = e.src + (long long)c1 * cp.sy + (long long)c2 * cp.sz;
+        const double wr = w1[c1] * (D == 3 ? w2[c2] : 1.0);
+#pragma unroll
+        for (int c0 = 0; c0 < CFI_W; ++c0) v += T(w0[c0] * wr) * xc[row + c0];
+      }
+  } else {
+    const long long* s = side + (-1 - e.src) * (D == 3 ? 125 : 25);
+    int q = 0;
+    for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
+      for (int c1 = 0; c1 < CFI_W; ++c1)
+        for (int c0 = 0; c0 < CFI_W; ++c0, ++q)
+          v += T(w0[c0] * w1[c1] * (D == 3 ? w2[c2] : 1.0)) * xc[s[q]];
+  }
+  xf[e.dst] = v;
+}
+
+template <typename T>
+__global__ void k_copy(const CopyEntry* __restrict__ list, long long n, T* __restrict__ x) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CopyEntry e = list[t];
+  x[e.dst] = x[e.src];
+}
+
+// ------------------------------------------------------------------------ transfers
+// Coarse cells of a transfer block get the mean of their r^D children (r = 2):
+// of x (average-down, Eq. AMR_avergingDownToCrse / restriction), or of f - A x on the fine
+// level (residual restriction) when RESID.
+template <typename T, int D, bool RESID>
+__global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                           const T* __restrict__ xf, const T* __restrict__ ff, T* __restrict__ outc,
+                           T alpha, T beta, int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int g[3] = {b.clo[0] + i, b.clo[1] + j, b.clo[2] + kk};
+  if (g[0] > b.chi[0] || g[1] > b.chi[1] || g[2] > b.chi[2]) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  T acc = T(0);
+  const T inv = T(1.0 / (12.0 * fine.h * fine.h));
+  for (int q2 = 0; q2 < (D == 3 ? 2 : 1); ++q2)
+    for (int q1 = 0; q1 < 2; ++q1)
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const int fi = 2 * g[0] + q0 - fp.lo[0];
+        const int fj = 2 * g[1] + q1 - fp.lo[1];
+        const int fk = (D == 3) ? 2 * g[2] + q2 - fp.lo[2] : 0;
+        const long long o = poff(fp, fi, fj, fk);
+        if (!RESID) {
+          acc += xf[o];
+        } else {
+          const T xc = xf[o];
+          T s = T(0);
+          const int c[3] = {fi, fj, fk};
+          const long long st[3] = {1, fp.sy, fp.sz};
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const int gg = fp.lo[d] + c[d];
+            T m1, p1, m2, p2;
+            if (gg >= 2 && gg <= fine.ndom[d] - 3) {
+              m1 = xf[o - st[d]];
+              p1 = xf[o + st[d]];
+              m2 = xf[o - 2 * st[d]];
+              p2 = xf[o + 2 * st[d]];
+            } else {
+              int cc[3] = {fi, fj, fk};
+              cc[d] = c[d] - 1; m1 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
+              cc[d] = c[d] + 1; p1 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
+              cc[d] = c[d] - 2; m2 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
+              cc[d] = c[d] + 2; p2 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
+            }
+            s += T(16) * (m1 + p1) - (m2 + p2);
+          }
+          s -= T(30 * D) * xc;
+          acc += ff[o] - (alpha * xc + beta * (s * inv));
+        }
+      }
+  outc[poff(cp, g[0] - cp.lo[0], g[1] - cp.lo[1], g[2] - cp.lo[2])] = acc * T(D == 3 ? 0.125 : 0.25);
+}
+
+// Fine cells of a transfer block += cell-centred tensor linear interpolation of the coarse
+// correction (Sec. 6.4 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse
+// values outside the domain come from the homogeneous physical extension with corners.
+template <typename T, int D>
+__global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                          const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2, int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;  // fine offsets inside the block region
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  int par[3], sg[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    par[e] = (e < D) ? (gf[e] >> 1) : 0;
+    sg[e] = (e < D) ? (((gf[e] & 1) == 0) ? -1 : 1) : 0;
+  }
+  T v = T(0);
+  for (int q2 = 0; q2 < (D == 3 ? 2 : 1); ++q2)
+    for (int q1 = 0; q1 < 2; ++q1)
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const int q[3] = {q0, q1, q2};
+        int cc[3];
+        double w = 1.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          cc[e] = par[e] + q[e] * sg[e] - cp.lo[e];
+          if (e < D) w *= (q[e] == 0) ? 0.75 : 0.25;
+        }
+        bool inside = true;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          const int g = cp.lo[e] + cc[e];
+          inside = inside && g >= 0 && g < crs.ndom[e];
+        }
+        const T cv = inside ? xc[poff(cp, cc[0], cc[1], cc[2])] : read_ext<T, D>(xc, cp, crs, cc[0], cc[1], cc[2]);
+        v += T(w) * cv;
+      }
+  const long long o = poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]);
+  xf[o] += v;
+  if (xf2 != nullptr) xf2[o] += v;
+}
+
+// ------------------------------------------------------------------------ elementwise
+// y[o] += a * x[o] on the interior cells of a level (optionally also y2[o] += a * x[o]);
+// source type S, destination type T.
+template <typename S, typename T, int D>
+__global__ void k_axpy(LevelView lv, int nby, const S* __restrict__ x, T* __restrict__ y, T* __restrict__ y2, T a) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  const T v = a * T(x[o]);
+  y[o] += v;
+  if (y2 != nullptr) y2[o] += v;
+}
+
+template <typename S, typename T, int D>
+__global__ void k_convert(LevelView lv, int nby, const S* __restrict__ x, T* __restrict__ y) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  y[o] = T(x[o]);
+}
+
+// y[o] += a on interior cells (mask: only valid cells when vmask != null)
+template <int D>
+__global__ void k_shift(LevelView lv, int nby, double* __restrict__ y, const double* __restrict__ a,
+                        const unsigned char* __restrict__ vmask, double sign) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (vmask != nullptr && vmask[o] == 0) return;
+  y[o] += sign * a[0];
+}
+
+// out = w - g on interior cells
+template <int D>
+__global__ void k_sub(LevelView lv, int nby, const double* __restrict__ w, const double* __restrict__ g,
+                      double* __restrict__ out) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  out[o] = w[o] - g[o];
+}
+
+// ------------------------------------------------------------------------ reductions
+// max |x| over valid interior cells, combined with atomicMax on the IEEE bit pattern
+// (order-preserving for non-negative doubles; NaN sorts above +Inf).
+template <typename T, int D>
+__global__ void k_maxnorm(LevelView lv, int nby, const T* __restrict__ x, const unsigned char* __restrict__ vmask,
+                          unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long sm[BX * BY / 32];
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  unsigned long long v = 0ull;
+  if (thread_cell<D>(p, nby, i, j, k)) {
+    const long long o = poff(p, i, j, k);
+    if (vmask == nullptr || vmask[o]) {
+      const double a = fabs((double)x[o]);
+      v = (unsigned long long)__double_as_longlong(a);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+    v = u > v ? u : v;
+  }
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  if ((tid & 31) == 0) sm[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    v = tid < (BX * BY / 32) ? sm[tid] : 0ull;
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+      v = u > v ? u : v;
+    }
+    if (tid == 0 && v != 0ull) atomicMax(out, v);
+  }
+}
+
+// Error-free transformation (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// double-double accumulate (s, c) += (a, ac)
+__device__ __forceinline__ void dd_add(double& s, double& c, double a, double ac) {
+  double t, e;
+  two_sum(s, a, t, e);
+  e += c + ac;
+  two_sum(t, e, s, c);
+}
+
+// Compensated, deterministic partial sums of w * x over valid interior cells: one
+// double-double partial per block, written to part[2*(base + linear block id)].
+template <int D>
+__global__ void k_wsum(LevelView lv, int nby, const double* __restrict__ x, const unsigned char* __restrict__ vmask,
+                       double w, double* __restrict__ part, long long base) {
+  __shared__ double ss[BX * BY], sc[BX * BY];
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  double s = 0.0, c = 0.0;
+  if (thread_cell<D>(p, nby, i, j, k)) {
+    const long long o = poff(p, i, j, k);
+    if (vmask == nullptr || vmask[o]) {
+      const double prod = w * x[o];
+      const double pe = fma(w, x[o], -prod);  // exact product error
+      s = prod;
+      c = pe;
+    }
+  }
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  ss[tid] = s;
+  sc[tid] = c;
+  __syncthreads();
+  for (int st = BX * BY / 2; st > 0; st >>= 1) {
+    if (tid < st) {
+      double a = ss[tid], ac = sc[tid];
+      dd_add(a, ac, ss[tid + st], sc[tid + st]);
+      ss[tid] = a;
+      sc[tid] = ac;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const long long bid = base + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[2 * bid] = ss[0];
+    part[2 * bid + 1] = sc[0];
+  }
+}
+
+// Boundary flux partials: sum over physical faces of valid boundary cells of
+// scale * g (g = Neumann datum), one double-double per (patch, face) block row.
+template <int D>
+__global__ void k_bsum(LevelView lv, const double* __restrict__ bc, const unsigned char* __restrict__ vmask,
+                       double scale, double* __restrict__ part, long long base) {
+  __shared__ double ss[256], sc[256];
+  const int pidx = blockIdx.x / (2 * D);
+  const int f = blockIdx.x % (2 * D);
+  const int d = f / 2, side = f % 2;
+  const PatchDesc p = lv.patches[pidx];
+  const int gface = side == 0 ? 0 : lv.ndom[d] - 1;
+  double s = 0.0, c = 0.0;
+  const bool touches = (p.lo[d] <= gface && gface <= p.lo[d] + p.n[d] - 1) && lv.bc[f] == 1 && bc != nullptr;
+  if (touches) {
+    const int e1 = (d == 0) ? 1 : 0;
+    const int e2 = (D == 3) ? ((d == 2) ? 1 : 2) : -1;
+    const long long ncell = (long long)p.n[e1] * (e2 >= 0 ? p.n[e2] : 1);
+    for (long long t = threadIdx.x; t < ncell; t += blockDim.x) {
+      int c3[3] = {0, 0, 0};
+      c3[d] = gface - p.lo[d];
+      c3[e1] = (int)(t % p.n[e1]);
+      if (e2 >= 0) c3[e2] = (int)(t / p.n[e1]);
+      const long long o = poff(p, c3[0], c3[1], c3[2]);
+      if (!vmask[o]) continue;
+      long long ti = p.lo[e1] + c3[e1];
+      if (e2 >= 0) ti += (long long)(p.lo[e2] + c3[e2]) * lv.ndom[e1];
+      const double gv = bc[lv.bc_off[f] + ti];
+      const double prod = scale * gv;
+      dd_add(s, c, prod, fma(scale, gv, -prod));
+    }
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      double a = ss[threadIdx.x], ac = sc[threadIdx.x];
+      dd_add(a, ac, ss[threadIdx.x + st], sc[threadIdx.x + st]);
+      ss[threadIdx.x] = a;
+      sc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * (base + blockIdx.x)] = ss[0];
+    part[2 * (base + blockIdx.x) + 1] = sc[0];
+  }
+}
+
+// Final fixed-order reduction of n double-double partials (one block of 256 threads):
+// out[0] = (sum_a - sum_b_scaled ... ) handled by the caller; here out[slot] = sum.
+__global__ void k_dd_final(const double* __restrict__ part, long long n, double* __restrict__ out) {
+  __shared__ double ss[256], sc[256];
+  double s = 0.0, c = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) dd_add(s, c, part[2 * t], part[2 * t + 1]);
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      double a = ss[threadIdx.x], ac = sc[threadIdx.x];
+      dd_add(a, ac, ss[threadIdx.x + st], sc[threadIdx.x + st]);
+      ss[threadIdx.x] = a;
+      sc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = ss[0] + sc[0];
+}
+
+// m = (S_f - beta * S_b) / V ; used by the solvability fix and mean-zero
+__global__ void k_mean_from_sums(const double* __restrict__ sf, const double* __restrict__ sb, double beta,
+                                 double vol, double* __restrict__ m) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) m[0] = (sf[0] - (sb ? beta * sb[0] : 0.0)) / vol;
+}
+
+// ------------------------------------------------------------------------ bottom solve
+// x = Minv * b on the coarsest multigrid grid (one block); bordered Neumann systems use the
+// leading n x n block of the inverse of [A 1; 1^T 0] (the constraint right-hand side is 0).
+template <typename T, int D>
+__global__ void k_bottom(const double* __restrict__ minv, int n, int ld, PatchDesc p, const T* __restrict__ b,
+                         T* __restrict__ x) {
+  extern __shared__ double sb[];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % p.n[0];
+    const int j = (t / p.n[0]) % p.n[1];
+    const int k = t / (p.n[0] * p.n[1]);
+    sb[t] = (double)b[poff(p, i, j, k)];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    double acc = 0.0;
+    const double* row = minv + (long long)t * ld;
+    for (int q = 0; q < n; ++q) acc = fma(row[q], sb[q], acc);
+    const int i = t % p.n[0];
+    const int j = (t / p.n[0]) % p.n[1];
+    const int k = t / (p.n[0] * p.n[1]);
+    x[poff(p, i, j, k)] = T(acc);
+  }
+}
+
+}  // namespace amr4

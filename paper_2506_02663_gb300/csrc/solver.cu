@@ -1,0 +1,1121 @@
+// libamr4 orchestration and C-ABI entry points: composite operators (COH-1..4), the
+// composite V-cycle (Sec. 6.4), solves with the max-norm stopping test (Sec. 7), the
+// solvability fix (Sec. 6.3), the composite projection (Eq. comp_ProjOp) and FP32 V-cycles
+// inside FP64 iterative refinement.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "amr4_impl.h"
+#include "kernels.cuh"
+
+using namespace amr4;
+
+namespace {
+
+// ---------------------------------------------------------------- scratch and operator
+template <typename T>
+struct Scratch {
+  T* E = nullptr;   // per-level corrections
+  T* R = nullptr;   // per-level right-hand sides / residuals
+  T* T1 = nullptr;  // smoothing ping-pong
+  T* T2 = nullptr;
+  T* X = nullptr;   // accumulated composite correction
+  T* rin = nullptr; // V-cycle input residual (FP32 path)
+  std::vector<T*> mx, mb, mt;  // level-0 multigrid grids m >= 1
+  bool ready = false;
+};
+
+}  // namespace
+
+struct amr_operator {
+  amr_hierarchy* h = nullptr;
+  double alpha = 0.0, beta = 1.0;
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  bool neumann = false;  // pure-Neumann PPE: alpha == 0 and every face Neumann
+  double* d_binv = nullptr;
+  int nbot = 0, ldb = 0;
+  Scratch<double> s64;
+  Scratch<float> s32;
+  double* F = nullptr;    // internal right-hand side copy
+  double* Res = nullptr;  // FP64 composite residual
+  double* Tmp = nullptr;  // FP64 composite scratch
+  std::vector<XferBlock*> d_mgx;  // transfer block m -> m+1
+};
+
+namespace {
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return AMR_ERR_CUDA;                                                            \
+    }                                                                                 \
+  } while (0)
+
+inline amr_status launch_check() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return AMR_ERR_CUDA;
+  }
+  return AMR_OK;
+}
+
+template <typename T>
+amr_status dalloc(T** p, size_t n) {
+  if (cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return AMR_ERR_OOM;
+  }
+  return AMR_OK;
+}
+
+struct Geo {
+  dim3 grid;
+  dim3 block{BX, BY, 1};
+  int nby;
+};
+
+inline Geo geo_of(const LevelView& v) {
+  Geo g;
+  g.nby = (v.maxn[1] + BY - 1) / BY;
+  g.grid = dim3((v.maxn[0] + BX - 1) / BX, g.nby * (v.D == 3 ? v.maxn[2] : 1), v.npatch);
+  return g;
+}
+
+LevelView mg_view(const amr_hierarchy* h, int m, const int* bc) {
+  LevelView v{};
+  const MgGrid& g = h->mg[m];
+  v.patches = g.d_patch;
+  v.npatch = 1;
+  v.D = h->D;
+  v.h = g.h;
+  for (int e = 0; e < 3; ++e) { v.ndom[e] = g.n[e]; v.maxn[e] = g.n[e]; }
+  for (int f = 0; f < 6; ++f) { v.bc[f] = bc[f]; v.bc_off[f] = 0; v.bc_pitch[f] = 1; }
+  return v;
+}
+
+// range [first, end) of a level's elements inside a composite field
+inline void level_range(const amr_hierarchy* h, int l, long long& a, long long& b) {
+  a = h->lev[l].patches.front().off;
+  b = (l + 1 < h->L) ? h->lev[l + 1].patches.front().off : h->nelems;
+}
+
+// ---------------------------------------------------------------- host bottom matrix
+const double HG[2][2][4] = {{{-77.0 / 12.0, 43.0 / 12.0, -17.0 / 12.0, 3.0 / 12.0},
+                              {-505.0 / 12.0, 335.0 / 12.0, -145.0 / 12.0, 27.0 / 12.0}},
+                             {{5.0 / 10.0, 9.0 / 10.0, -5.0 / 10.0, 1.0 / 10.0},
+                              {-75.0 / 10.0, 145.0 / 10.0, -75.0 / 10.0, 15.0 / 10.0}}};
+
+// alpha x + beta L x on one box grid with homogeneous physical ghosts (host, for the
+// dense bottom-solve matrix).
+void host_apply(int D, const int n[3], double h, double alpha, double beta, const int* bc,
+                const std::vector<double>& x, std::vector<double>& y) {
+  auto at = [&](int i, int j, int k) -> double { return x[((size_t)k * n[1] + j) * n[0] + i]; };
+  auto val = [&](int c0, int c1, int c2, int d) -> double {
+    int c[3] = {c0, c1, c2};
+    if (c[d] >= 0 && c[d] < n[d]) return at(c[0], c[1], c[2]);
+    const int side = c[d] < 0 ? 0 : 1;
+    const int layer = side == 0 ? -c[d] : c[d] - n[d] + 1;
+    const int type = bc[2 * d + side];
+    double v = 0.0;
+    for (int m = 0; m < 4; ++m) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] = side == 0 ? m : n[d] - 1 - m;
+      v += HG[type][layer - 1][m] * at(cc[0], cc[1], cc[2]);
+    }
+    return v;
+  };
+  y.assign(x.size(), 0.0);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        double acc = 0.0;
+        int c[3] = {i, j, k};
+        for (int d = 0; d < D; ++d) {
+          int cm1[3] = {i, j, k}, cp1[3] = {i, j, k}, cm2[3] = {i, j, k}, cp2[3] = {i, j, k};
+          cm1[d] = c[d] - 1; cp1[d] = c[d] + 1; cm2[d] = c[d] - 2; cp2[d] = c[d] + 2;
+          acc += 16.0 * (val(cm1[0], cm1[1], cm1[2], d) + val(cp1[0], cp1[1], cp1[2], d)) -
+                 (val(cm2[0], cm2[1], cm2[2], d) + val(cp2[0], cp2[1], cp2[2], d));
+        }
+        acc -= 30.0 * D * at(i, j, k);
+        y[((size_t)k * n[1] + j) * n[0] + i] = alpha * at(i, j, k) + beta * acc / (12.0 * h * h);
+      }
+}
+
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = i;
+    if (A[(size_t)piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+        std::swap(I[(size_t)c * n + k], I[(size_t)piv * n + k]);
+      }
+    const double d = A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) { A[(size_t)c * n + k] /= d; I[(size_t)c * n + k] /= d; }
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = A[(size_t)i * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)i * n + k] -= f * A[(size_t)c * n + k];
+        I[(size_t)i * n + k] -= f * I[(size_t)c * n + k];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// ---------------------------------------------------------------- kernel wrappers
+template <typename T, int D>
+amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* out, const T* bc, double alpha,
+                    double beta, double omega, const unsigned char* vmask, cudaStream_t st) {
+  Geo g = geo_of(lv);
+  switch (mode) {
+    case OP_APPLY:
+      k_level_op<T, D, OP_APPLY><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      break;
+    case OP_RESID:
+      k_level_op<T, D, OP_RESID><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      break;
+    case OP_JACOBI:
+      k_level_op<T, D, OP_JACOBI><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      break;
+    default:
+      k_level_op<T, D, OP_JACOBI0><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+  }
+  return launch_check();
+}
+
+template <typename T, int D>
+amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const XferBlock* blocks, int nblocks,
+                           const int xmax[3], bool resid, const T* xf, const T* ff, T* outc, double alpha,
+                           double beta, cudaStream_t st) {
+  if (nblocks == 0) return AMR_OK;
+  const int nby = (xmax[1] + BY - 1) / BY;
+  dim3 grid((xmax[0] + BX - 1) / BX, nby * (D == 3 ? xmax[2] : 1), nblocks);
+  dim3 block(BX, BY, 1);
+  if (resid)
+    k_restrict<T, D, true><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
+  else
+    k_restrict<T, D, false><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
+  return launch_check();
+}
+
+template <typename T, int D>
+amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const XferBlock* blocks, int nblocks,
+                          const int xmax[3], const T* xc, T* xf, T* xf2, cudaStream_t st) {
+  if (nblocks == 0) return AMR_OK;
+  const int fy = 2 * xmax[1];
+  const int nby = (fy + BY - 1) / BY;
+  dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
+  dim3 block(BX, BY, 1);
+  k_prolong<T, D><<<grid, block, 0, st>>>(fine, crs, blocks, xc, xf, xf2, nby);
+  return launch_check();
+}
+
+template <typename T, int D>
+amr_status cfi_fill(const amr_hierarchy* h, int l, const T* xc, T* xf, bool zero, cudaStream_t st) {
+  const DeviceLists& dl = h->lev[l].dev;
+  if (dl.ncfi == 0) return AMR_OK;
+  const int nt = 128;
+  k_cfi<T, D><<<(unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st>>>(dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches,
+                                                                  h->r, xc, xf, zero ? 1 : 0);
+  return launch_check();
+}
+
+template <typename T>
+amr_status copy_fill(const amr_hierarchy* h, int l, T* x, cudaStream_t st) {
+  const DeviceLists& dl = h->lev[l].dev;
+  if (dl.ncopy == 0) return AMR_OK;
+  const int nt = 128;
+  k_copy<T><<<(unsigned)((dl.ncopy + nt - 1) / nt), nt, 0, st>>>(dl.copy, dl.ncopy, x);
+  return launch_check();
+}
+
+template <typename T>
+struct P3 {
+  const T* p[3];
+};
+
+template <typename T, int D>
+__global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
+                            P3<T> xcs, P3<T> xfs, P3<T> bcs, T* __restrict__ out, T coef, int kind);
+
+template <typename T, int D>
+amr_status reflux(const amr_hierarchy* h, int l, const LevelView& crs, const LevelView& fine, P3<T> xc, P3<T> xf,
+                  P3<T> bcs, T* out, double coef, int kind, cudaStream_t st) {
+  const DeviceLists& dl = h->lev[l].dev;
+  if (dl.nreflux == 0) return AMR_OK;
+  const int nt = 128;
+  k_reflux_p3<T, D><<<(unsigned)((dl.nreflux + nt - 1) / nt), nt, 0, st>>>(crs, fine, dl.reflux, dl.nreflux, xc, xf,
+                                                                         bcs, out, T(coef), kind);
+  return launch_check();
+}
+
+template <typename S, typename T, int D>
+amr_status axpy(const LevelView& lv, const S* x, T* y, T* y2, double a, cudaStream_t st) {
+  Geo g = geo_of(lv);
+  k_axpy<S, T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, y, y2, T(a));
+  return launch_check();
+}
+
+template <typename S, typename T, int D>
+amr_status convert(const LevelView& lv, const S* x, T* y, cudaStream_t st) {
+  Geo g = geo_of(lv);
+  k_convert<S, T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, y);
+  return launch_check();
+}
+
+#define TRY(...)                         \
+  do {                                   \
+    amr_status s_ = (__VA_ARGS__);       \
+    if (s_ != AMR_OK) return s_;         \
+  } while (0)
+
+}  // namespace
+
+// reflux kernel with by-value pointer triples (defined outside the anonymous namespace
+// declaration above so that it can be instantiated)
+namespace {
+template <typename T, int D>
+__global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
+                            P3<T> xcs, P3<T> xfs, P3<T> bcs, T* __restrict__ out, T coef, int kind) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const RefluxEntry e = list[t];
+  const PatchDesc cp = crs.patches[e.cpatch];
+  const double fd[4] = {1.0 / 12.0, -15.0 / 12.0, 15.0 / 12.0, -1.0 / 12.0};
+  const double fv[4] = {-1.0 / 12.0, 7.0 / 12.0, 7.0 / 12.0, -1.0 / 12.0};
+  const double* fc = kind == 0 ? fd : fv;
+  T corr = T(0);
+  for (int d = 0; d < D; ++d)
+    for (int side = 0; side < 2; ++side) {
+      if (!(e.faces & (1 << (2 * d + side)))) continue;
+      const int comp = kind == 0 ? 0 : d;
+      const T* xc = xcs.p[comp];
+      const T* xf = xfs.p[comp];
+      int own[3] = {e.g[0] - cp.lo[0], e.g[1] - cp.lo[1], e.g[2] - cp.lo[2]};
+      if (side == 0) own[d] -= 1;
+      T Fc = T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int cc[3] = {own[0], own[1], own[2]};
+        cc[d] += q - 1;
+        Fc += T(fc[q]) * read_nb<T, D>(xc, cp, crs, bcs.p[comp], cc[0], cc[1], cc[2], d);
+      }
+      const PatchDesc fp = fine.patches[e.fpatch[2 * d + side]];
+      T Fs = T(0);
+      const int e1 = (d == 0) ? 1 : 0;
+      const int e2 = (d == 2) ? 1 : 2;
+      for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
+        for (int t1 = 0; t1 < 2; ++t1) {
+          int gf[3] = {0, 0, 0};
+          gf[d] = side == 1 ? 2 * (e.g[d] + 1) - 1 : 2 * e.g[d] - 1;
+          gf[e1] = 2 * e.g[e1] + t1;
+          if (D == 3) gf[e2] = 2 * e.g[e2] + t2;
+          const int cf[3] = {gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int cc[3] = {cf[0], cf[1], cf[2]};
+            cc[d] += q - 1;
+            Fs += T(fc[q]) * xf[poff(fp, cc[0], cc[1], cc[2])];
+          }
+        }
+      const T Fbar = Fs * T(D == 3 ? 0.25 : 0.5);
+      const T hc = kind == 0 ? T(crs.h) : T(1);
+      const T hf = kind == 0 ? T(fine.h) : T(1);
+      corr += T(side == 1 ? 1 : -1) * (Fbar / hf - Fc / hc);
+    }
+  out[e.coff] += coef * corr / T(crs.h);
+}
+
+// ---------------------------------------------------------------- scratch management
+template <typename T>
+Scratch<T>& scratch(amr_operator* op);
+template <>
+Scratch<double>& scratch<double>(amr_operator* op) { return op->s64; }
+template <>
+Scratch<float>& scratch<float>(amr_operator* op) { return op->s32; }
+
+template <typename T>
+amr_status ensure_scratch(amr_operator* op) {
+  Scratch<T>& S = scratch<T>(op);
+  if (S.ready) return AMR_OK;
+  const amr_hierarchy* h = op->h;
+  const size_t n = (size_t)h->nelems;
+  TRY(dalloc(&S.E, n));
+  TRY(dalloc(&S.R, n));
+  TRY(dalloc(&S.T1, n));
+  TRY(dalloc(&S.T2, n));
+  TRY(dalloc(&S.X, n));
+  TRY(dalloc(&S.rin, n));
+  CK(cudaMemset(S.E, 0, n * sizeof(T)));
+  CK(cudaMemset(S.R, 0, n * sizeof(T)));
+  CK(cudaMemset(S.T1, 0, n * sizeof(T)));
+  CK(cudaMemset(S.T2, 0, n * sizeof(T)));
+  CK(cudaMemset(S.X, 0, n * sizeof(T)));
+  CK(cudaMemset(S.rin, 0, n * sizeof(T)));
+  S.mx.assign(h->mg.size(), nullptr);
+  S.mb.assign(h->mg.size(), nullptr);
+  S.mt.assign(h->mg.size(), nullptr);
+  for (size_t m = 1; m < h->mg.size(); ++m) {
+    const size_t q = (size_t)h->mg[m].nelems;
+    TRY(dalloc(&S.mx[m], q));
+    TRY(dalloc(&S.mb[m], q));
+    TRY(dalloc(&S.mt[m], q));
+    CK(cudaMemset(S.mx[m], 0, q * sizeof(T)));
+    CK(cudaMemset(S.mb[m], 0, q * sizeof(T)));
+    CK(cudaMemset(S.mt[m], 0, q * sizeof(T)));
+  }
+  S.ready = true;
+  return AMR_OK;
+}
+
+template <typename T>
+void free_scratch(Scratch<T>& S) {
+  cudaFree(S.E); cudaFree(S.R); cudaFree(S.T1); cudaFree(S.T2); cudaFree(S.X); cudaFree(S.rin);
+  for (auto p : S.mx) cudaFree(p);
+  for (auto p : S.mb) cudaFree(p);
+  for (auto p : S.mt) cudaFree(p);
+  S = Scratch<T>();
+}
+
+// ---------------------------------------------------------------- smoothing
+// nsweeps weighted-Jacobi sweeps on one level from x = 0 (first sweep closed form), the
+// result ends in ``a`` (b is the other ping-pong buffer).  Copy ghosts are refreshed
+// before every sweep; CF ghosts of a and b must already be zero.
+template <typename T, int D>
+amr_status smooth_from_zero(const amr_hierarchy* h, int l, const LevelView& lv, const T* f, T* a, T* b, int nsweeps,
+                            double alpha, double beta, double omega, bool amr_level, cudaStream_t st) {
+  if (nsweeps <= 0) return AMR_OK;
+  T* cur = (nsweeps % 2 == 1) ? a : b;
+  T* oth = (cur == a) ? b : a;
+  TRY(level_op<T, D>(OP_JACOBI0, lv, nullptr, f, cur, nullptr, alpha, beta, omega, nullptr, st));
+  for (int s = 1; s < nsweeps; ++s) {
+    if (amr_level) TRY(copy_fill<T>(h, l, cur, st));
+    TRY(level_op<T, D>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
+    std::swap(cur, oth);
+  }
+  return AMR_OK;
+}
+
+// nsweeps sweeps starting from the values in a; result in a (copy back if odd).
+template <typename T, int D>
+amr_status smooth_from(const amr_hierarchy* h, int l, const LevelView& lv, const T* f, T* a, T* b, int nsweeps,
+                       double alpha, double beta, double omega, bool amr_level, cudaStream_t st) {
+  T* cur = a;
+  T* oth = b;
+  for (int s = 0; s < nsweeps; ++s) {
+    if (amr_level) TRY(copy_fill<T>(h, l, cur, st));
+    TRY(level_op<T, D>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
+    std::swap(cur, oth);
+  }
+  if (cur != a) {
+    // odd count: bring the result back into a (interior cells)
+    TRY(convert<T, T, D>(lv, cur, a, st));
+  }
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- level-0 multigrid
+template <typename T, int D>
+amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const T* b, T* x, T* t, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  const int M = (int)h->mg.size() - 1;
+  const LevelView lv = mg_view(h, m, op->bc);
+  if (m == M) {
+    const int n = op->nbot;
+    k_bottom<T, D><<<1, 256, n * sizeof(double), st>>>(op->d_binv, n, op->ldb, h->mg[m].patch, b, x);
+    return launch_check();
+  }
+  TRY(smooth_from_zero<T, D>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
+  const LevelView cv = mg_view(h, m + 1, op->bc);
+  const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
+  TRY(restrict_blocks<T, D>(lv, cv, op->d_mgx[m], 1, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
+  TRY(mg_level0<T, D>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
+  TRY(prolong_blocks<T, D>(lv, cv, op->d_mgx[m], 1, xm, S.mx[m + 1], x, (T*)nullptr, st));
+  TRY(smooth_from<T, D>(h, 0, lv, b, x, t, p.nu2, op->alpha, op->beta, p.omega, false, st));
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- composite V-cycle
+// Correction form: given the composite residual r (covered cells), S.X receives the
+// V-cycle's approximation of A^{-1} r (homogeneous data).
+template <typename T, int D>
+amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  const int L = h->L - 1;
+  const size_t bytes = (size_t)h->nelems * sizeof(T);
+  CK(cudaMemsetAsync(S.E, 0, bytes, st));
+  CK(cudaMemsetAsync(S.X, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T1, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T2, 0, bytes, st));
+  {
+    long long a, b;
+    level_range(h, L, a, b);
+    CK(cudaMemcpyAsync(S.R + a, r + a, (size_t)(b - a) * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  std::vector<LevelView> lv(h->L);
+  for (int l = 0; l <= L; ++l) lv[l] = level_view(h, l, op->bc);
+  const double a_ = op->alpha, b_ = op->beta;
+  // ---- down
+  for (int l = L; l >= 1; --l) {
+    TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st));
+    TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
+    const DeviceLists& cl = h->lev[l - 1].dev;
+    // invalid cells of level l-1: mean of the fine residual R_l - A_l E_l (zero CF ghosts)
+    TRY(copy_fill<T>(h, l, S.E, st));
+    TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+    // valid cells of level l-1: composite residual r - A^comp X
+    for (int m = l - 1; m >= 0; --m) {
+      const DeviceLists& dm = h->lev[m].dev;
+      TRY(restrict_blocks<T, D>(lv[m + 1], lv[m], dm.xfer, dm.nxfer, dm.xfer_max, false, S.X, (const T*)nullptr, S.X,
+                                0.0, 0.0, st));
+    }
+    if (l - 1 >= 1) TRY(cfi_fill<T, D>(h, l - 1, S.X, S.X, false, st));
+    TRY(copy_fill<T>(h, l - 1, S.X, st));
+    TRY(cfi_fill<T, D>(h, l, S.X, S.X, false, st));
+    TRY(copy_fill<T>(h, l, S.X, st));
+    TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, h->d_valid, st));
+    P3<T> xc{{S.X, S.X, S.X}}, xf{{S.X, S.X, S.X}}, nb{{nullptr, nullptr, nullptr}};
+    TRY(reflux<T, D>(h, l - 1, lv[l - 1], lv[l], xc, xf, nb, S.R, -b_, 0, st));
+  }
+  // ---- level 0: single-level V-cycle on all of level 0
+  TRY(mg_level0<T, D>(op, p, 0, S.R, S.E, S.T1, st));
+  TRY(axpy<T, T, D>(lv[0], S.E, S.X, (T*)nullptr, 1.0, st));
+  // ---- up
+  for (int l = 1; l <= L; ++l) {
+    const DeviceLists& cl = h->lev[l - 1].dev;
+    TRY(copy_fill<T>(h, l - 1, S.E, st));
+    TRY(prolong_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, S.E, S.E, S.X, st));
+    TRY(cfi_fill<T, D>(h, l, S.E, S.E, false, st));
+    TRY(copy_fill<T>(h, l, S.E, st));
+    TRY(level_op<T, D>(OP_RESID, lv[l], S.E, S.R, S.R, nullptr, a_, b_, 0.0, nullptr, st));
+    TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st));
+    TRY(axpy<T, T, D>(lv[l], S.T1, S.E, S.X, 1.0, st));
+  }
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- FP64 composite pieces
+template <int D>
+amr_status avgdown_all(amr_hierarchy* h, double* x, cudaStream_t st) {
+  for (int m = h->L - 2; m >= 0; --m) {
+    const DeviceLists& dm = h->lev[m].dev;
+    LevelView f = level_view(h, m + 1, nullptr), c = level_view(h, m, nullptr);
+    TRY(restrict_blocks<double, D>(f, c, dm.xfer, dm.nxfer, dm.xfer_max, false, x, (const double*)nullptr, x, 0.0, 0.0,
+                                   st));
+  }
+  return AMR_OK;
+}
+
+template <int D>
+amr_status fill_ghosts_all(amr_hierarchy* h, double* x, cudaStream_t st) {
+  TRY(avgdown_all<D>(h, x, st));
+  for (int l = 0; l < h->L; ++l) {
+    if (l >= 1) TRY(cfi_fill<double, D>(h, l, x, x, false, st));
+    TRY(copy_fill<double>(h, l, x, st));
+  }
+  return AMR_OK;
+}
+
+// out = A^comp x (mode OP_APPLY) or out = f - A^comp x (OP_RESID); covered cells.
+template <int D>
+amr_status composite_op(amr_operator* op, int mode, double* x, const double* f, double* out, const double* bc,
+                        cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  TRY(fill_ghosts_all<D>(h, x, st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, op->bc);
+    TRY(level_op<double, D>(mode, lv, x, f, out, bc, op->alpha, op->beta, 0.0, nullptr, st));
+  }
+  for (int l = h->L - 2; l >= 0; --l) {
+    LevelView c = level_view(h, l, op->bc), fv = level_view(h, l + 1, op->bc);
+    P3<double> xc{{x, x, x}}, xf{{x, x, x}}, nb{{bc, bc, bc}};
+    TRY(reflux<double, D>(h, l, c, fv, xc, xf, nb, out, mode == OP_APPLY ? op->beta : -op->beta, 0, st));
+  }
+  TRY(avgdown_all<D>(h, out, st));  // COH-4
+  return AMR_OK;
+}
+
+template <typename T, int D>
+amr_status maxnorm(amr_hierarchy* h, const T* x, bool use_mask, double* out_host, cudaStream_t st) {
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(h->d_scalar);
+  CK(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    k_maxnorm<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, use_mask ? h->d_valid : nullptr, acc);
+    TRY(launch_check());
+  }
+  CK(cudaMemcpyAsync(h->h_scalar, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out_host = h->h_scalar[0];
+  return AMR_OK;
+}
+
+// d_out[0] = sum over valid cells of h^D x (compensated); d_out[1] = boundary flux sum
+template <int D>
+amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* bc_types, double* d_out,
+                cudaStream_t st) {
+  long long base = 0;
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    const long long nb = (long long)g.grid.x * g.grid.y * g.grid.z;
+    if (base + nb > 8192) {
+      set_error("reduction scratch too small");
+      return AMR_ERR_INVALID_ARG;
+    }
+    k_wsum<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, h->d_valid, std::pow(lv.h, D), h->d_red, base);
+    TRY(launch_check());
+    base += nb;
+  }
+  k_dd_final<<<1, 256, 0, st>>>(h->d_red, base, d_out);
+  TRY(launch_check());
+  if (bc != nullptr && bc_types != nullptr) {
+    long long bb = 0;
+    for (int l = 0; l < h->L; ++l) {
+      LevelView lv = level_view(h, l, bc_types);
+      const int nblk = lv.npatch * 2 * D;
+      k_bsum<D><<<nblk, 256, 0, st>>>(lv, bc, h->d_valid, std::pow(lv.h, D - 1), h->d_red, bb);
+      TRY(launch_check());
+      bb += nblk;
+    }
+    k_dd_final<<<1, 256, 0, st>>>(h->d_red, bb, d_out + 1);
+    TRY(launch_check());
+  } else {
+    CK(cudaMemsetAsync(d_out + 1, 0, sizeof(double), st));
+  }
+  return AMR_OK;
+}
+
+double valid_volume(const amr_hierarchy* h) {
+  // number of valid cells per level times h^D (exact small integers times powers of 2)
+  long double v = 0.0L;
+  size_t q = 0;
+  for (int l = 0; l < h->L; ++l) {
+    long long cnt = 0;
+    for (const PatchDesc& p : h->lev[l].patches) {
+      const long long nc = (long long)p.n[0] * p.n[1] * p.n[2];
+      for (long long i = 0; i < nc; ++i) cnt += h->im_valid[q + i];
+      q += nc;
+    }
+    v += (long double)cnt * std::pow((long double)h->lev[l].h, (long double)h->D);
+  }
+  return (double)v;
+}
+
+template <int D>
+amr_status shift_all(amr_hierarchy* h, double* x, const double* d_m, bool valid_only, double sign, cudaStream_t st) {
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    k_shift<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, d_m, valid_only ? h->d_valid : nullptr, sign);
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+template <int D>
+amr_status solvability_fix_impl(amr_operator* op, double* f, const double* bc, double* m_host, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  TRY(wsum<D>(h, f, bc, op->bc, h->d_scalar + 2, st));
+  k_mean_from_sums<<<1, 1, 0, st>>>(h->d_scalar + 2, h->d_scalar + 3, op->beta, valid_volume(h), h->d_scalar + 4);
+  TRY(launch_check());
+  TRY(shift_all<D>(h, f, h->d_scalar + 4, true, -1.0, st));
+  if (m_host) {
+    CK(cudaMemcpyAsync(h->h_scalar + 4, h->d_scalar + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *m_host = h->h_scalar[4];
+  }
+  return AMR_OK;
+}
+
+template <int D>
+amr_status mean_zero_impl(amr_hierarchy* h, double* x, double* mean_host, cudaStream_t st) {
+  TRY(avgdown_all<D>(h, x, st));
+  TRY(wsum<D>(h, x, nullptr, nullptr, h->d_scalar + 2, st));
+  k_mean_from_sums<<<1, 1, 0, st>>>(h->d_scalar + 2, nullptr, 0.0, valid_volume(h), h->d_scalar + 4);
+  TRY(launch_check());
+  TRY(shift_all<D>(h, x, h->d_scalar + 4, false, -1.0, st));
+  if (mean_host) {
+    CK(cudaMemcpyAsync(h->h_scalar + 4, h->d_scalar + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *mean_host = h->h_scalar[4];
+  }
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- solve
+template <int D>
+amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
+                      amr_solve_stats* stats, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  const size_t bytes = (size_t)h->nelems * sizeof(double);
+  amr_solve_stats loc{};
+  CK(cudaMemcpyAsync(op->F, f, bytes, cudaMemcpyDeviceToDevice, st));
+  if (op->neumann) TRY(solvability_fix_impl<D>(op, op->F, bc, &loc.removed_mean, st));
+  if (p.zero_initial) CK(cudaMemsetAsync(phi, 0, bytes, st));
+  TRY(avgdown_all<D>(h, op->F, st));
+  double fn = 0.0;
+  TRY(maxnorm<double, D>(h, op->F, true, &fn, st));
+  loc.rhs_norm = fn;
+  const double tol = std::max(p.rtol * fn, p.atol);
+  if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  else TRY(ensure_scratch<double>(op));
+  amr_status result = AMR_ERR_NOT_CONVERGED;
+  double res = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    TRY(composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, st));
+    TRY(maxnorm<double, D>(h, op->Res, true, &res, st));
+    if (it < 64) loc.res_history[it] = res;
+    if (!std::isfinite(res)) { result = AMR_ERR_NONFINITE; set_error("residual is not finite"); break; }
+    if (res <= tol) { result = AMR_OK; break; }
+    if (it >= p.max_vcycles) { set_error("max_vcycles reached"); break; }
+    if (p.precision == AMR_MIXED) {
+      Scratch<float>& S = op->s32;
+      for (int l = 0; l < h->L; ++l) TRY(convert<double, float, D>(level_view(h, l, nullptr), op->Res, S.rin, st));
+      TRY(vcycle_corr<float, D>(op, p, S.rin, st));
+      for (int l = 0; l < h->L; ++l) TRY(axpy<float, double, D>(level_view(h, l, nullptr), S.X, phi, (double*)nullptr, 1.0, st));
+    } else {
+      Scratch<double>& S = op->s64;
+      TRY(vcycle_corr<double, D>(op, p, op->Res, st));
+      for (int l = 0; l < h->L; ++l) TRY(axpy<double, double, D>(level_view(h, l, nullptr), S.X, phi, (double*)nullptr, 1.0, st));
+    }
+  }
+  loc.vcycles = it;
+  loc.final_res = res;
+  if (op->neumann && result == AMR_OK) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
+  else TRY(avgdown_all<D>(h, phi, st));
+  if (stats) *stats = loc;
+  return result;
+}
+
+template <int D>
+amr_status vcycle_impl(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
+                       cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  TRY(ensure_scratch<double>(op));
+  TRY(composite_op<D>(op, OP_RESID, phi, f, op->Res, bc, st));
+  TRY(vcycle_corr<double, D>(op, p, op->Res, st));
+  for (int l = 0; l < h->L; ++l) TRY(axpy<double, double, D>(level_view(h, l, nullptr), op->s64.X, phi, (double*)nullptr, 1.0, st));
+  return AMR_OK;
+}
+
+template <int D>
+amr_status smooth_impl(amr_operator* op, int level, int nsweeps, double omega, double* x, const double* b,
+                       cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  TRY(ensure_scratch<double>(op));
+  LevelView lv = level_view(h, level, op->bc);
+  // zero CF ghosts of x, use Tmp as the ping-pong partner (its CF ghosts zeroed too)
+  if (level >= 1) {
+    TRY(cfi_fill<double, D>(h, level, x, x, true, st));
+    TRY(cfi_fill<double, D>(h, level, op->Tmp, op->Tmp, true, st));
+  }
+  TRY(smooth_from<double, D>(h, level, lv, b, x, op->Tmp, nsweeps, op->alpha, op->beta, omega, true, st));
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- G, D, projection
+template <int D>
+amr_status gradient_impl(amr_hierarchy* h, const int* bct, double* phi, double* const* grad, const double* bc,
+                         cudaStream_t st) {
+  TRY(fill_ghosts_all<D>(h, phi, st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, bct);
+    Geo g = geo_of(lv);
+    k_gradient<double, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, phi, grad[0], grad[1], D == 3 ? grad[2] : nullptr, bc);
+    TRY(launch_check());
+  }
+  for (int d = 0; d < D; ++d) TRY(avgdown_all<D>(h, grad[d], st));  // COH-4
+  return AMR_OK;
+}
+
+template <int D>
+amr_status divergence_impl(amr_hierarchy* h, const int* bct, double* const* u, double* out,
+                           const double* const* bc, cudaStream_t st) {
+  for (int d = 0; d < D; ++d) TRY(fill_ghosts_all<D>(h, u[d], st));
+  Ptr3 up{{u[0], u[1], D == 3 ? u[2] : nullptr}};
+  Ptr3 bp{{bc ? bc[0] : nullptr, bc ? bc[1] : nullptr, (bc && D == 3) ? bc[2] : nullptr}};
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, bct);
+    Geo g = geo_of(lv);
+    k_divergence<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, up, out, bp);
+    TRY(launch_check());
+  }
+  for (int l = h->L - 2; l >= 0; --l) {
+    LevelView c = level_view(h, l, bct), fv = level_view(h, l + 1, bct);
+    P3<double> xc{{u[0], u[1], D == 3 ? u[2] : nullptr}};
+    P3<double> bcs{{bp.p[0], bp.p[1], bp.p[2]}};
+    TRY(reflux<double, D>(h, l, c, fv, xc, xc, bcs, out, 1.0, 1, st));
+  }
+  TRY(avgdown_all<D>(h, out, st));
+  return AMR_OK;
+}
+
+template <int D>
+amr_status project_impl(amr_operator* ppe, const amr_solver_params& p, const int* vbc, double* const* w,
+                        const double* const* wbc, double* const* u, double* phi, amr_solve_stats* stats,
+                        cudaStream_t st) {
+  amr_hierarchy* h = ppe->h;
+  TRY(divergence_impl<D>(h, vbc, w, ppe->Tmp, wbc, st));
+  amr_solver_params q = p;
+  q.zero_initial = 1;
+  amr_status s = solve_impl<D>(ppe, q, phi, ppe->Tmp, nullptr, stats, st);
+  if (s != AMR_OK) return s;
+  // G^comp phi into u, then u = w - G phi (no average-down of u afterwards)
+  TRY(gradient_impl<D>(h, ppe->bc, phi, u, nullptr, st));
+  for (int d = 0; d < D; ++d)
+    for (int l = 0; l < h->L; ++l) {
+      LevelView lv = level_view(h, l, nullptr);
+      Geo g = geo_of(lv);
+      k_sub<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, w[d], u[d], u[d]);
+      TRY(launch_check());
+    }
+  return AMR_OK;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+// =================================================================== C ABI
+#define DISPATCH(h, fn, ...) ((h)->D == 2 ? fn<2>(__VA_ARGS__) : fn<3>(__VA_ARGS__))
+
+static amr_status check_op(amr_operator* op) {
+  if (op == nullptr || op->h == nullptr) {
+    set_error("null operator");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return AMR_OK;
+}
+
+static amr_status ensure_device(amr_hierarchy* h) {
+  std::string err;
+  amr_status s = upload_hierarchy(h, err);
+  if (s != AMR_OK) set_error(err);
+  return s;
+}
+
+extern "C" {
+
+const char* amr_last_error(void) { return get_error(); }
+
+void amr_default_params(amr_solver_params* p) {
+  if (!p) return;
+  p->nu1 = 4;
+  p->nu2 = 4;
+  p->omega = 2.0 / 3.0;
+  p->rtol = 1e-10;
+  p->atol = 0.0;
+  p->max_vcycles = 50;
+  p->precision = AMR_FP64;
+  p->zero_initial = 1;
+  p->use_graph = 0;
+}
+
+amr_status amr_hierarchy_create(const amr_hierarchy_desc* desc, amr_hierarchy** out) {
+  if (desc == nullptr || out == nullptr) {
+    set_error("null argument");
+    return AMR_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  amr_hierarchy* h = new (std::nothrow) amr_hierarchy();
+  if (!h) {
+    set_error("host allocation failed");
+    return AMR_ERR_OOM;
+  }
+  std::string err;
+  amr_status st;
+  try {
+    st = build_hierarchy(desc, h, err);
+  } catch (const std::exception& ex) {
+    err = ex.what();
+    st = AMR_ERR_OOM;
+  }
+  if (st != AMR_OK) {
+    set_error(err);
+    free_hierarchy(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return AMR_OK;
+}
+
+void amr_hierarchy_destroy(amr_hierarchy* h) {
+  if (!h) return;
+  free_hierarchy(h);
+  delete h;
+}
+
+amr_status amr_field_layout(const amr_hierarchy* h, int* npatches, long long* nelems, amr_patch_info* patches) {
+  if (!h) { set_error("null hierarchy"); return AMR_ERR_INVALID_ARG; }
+  if (npatches) *npatches = h->npatch;
+  if (nelems) *nelems = h->nelems;
+  if (patches) std::memcpy(patches, h->pinfo.data(), h->pinfo.size() * sizeof(amr_patch_info));
+  return AMR_OK;
+}
+
+amr_status amr_bc_layout(const amr_hierarchy* h, long long* offsets) {
+  if (!h || !offsets) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  std::memcpy(offsets, h->bc_off.data(), h->bc_off.size() * sizeof(long long));
+  return AMR_OK;
+}
+
+amr_status amr_get_index_maps(const amr_hierarchy* h, amr_index_maps* o) {
+  if (!h || !o) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  o->ncells_interior = (long long)h->im_valid.size();
+  o->ncells_padded = (long long)h->im_code.size();
+  o->valid = h->im_valid.data();
+  o->component = h->im_component.data();
+  o->ghost_code = h->im_code.data();
+  o->ghost_src = h->im_src.data();
+  o->ghost_aux = h->im_aux.data();
+  o->ncfi = (long long)h->im_cfi_cell.size();
+  o->cfi_cell = h->im_cfi_cell.data();
+  o->cfi_start = h->im_cfi_start.data();
+  o->cfi_pos = h->im_cfi_pos.data();
+  o->cfi_sub = h->im_cfi_sub.data();
+  o->nreflux = (long long)h->im_reflux_faces.size();
+  o->reflux_cell = h->im_reflux_cell.data();
+  o->reflux_faces = h->im_reflux_faces.data();
+  return AMR_OK;
+}
+
+amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, const int* bc_types, amr_operator** out) {
+  if (!h || !bc_types || !out) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (h->r != 2) { set_error("solver calls need refinement ratio 2"); return AMR_ERR_INVALID_ARG; }
+  for (int f = 0; f < 2 * h->D; ++f)
+    if (bc_types[f] != AMR_BC_DIRICHLET && bc_types[f] != AMR_BC_NEUMANN) { set_error("bad bc type"); return AMR_ERR_INVALID_ARG; }
+  if (!std::isfinite(alpha) || !std::isfinite(beta) || beta == 0.0) { set_error("bad alpha/beta"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  std::unique_ptr<amr_operator> op(new amr_operator());
+  op->h = h;
+  op->alpha = alpha;
+  op->beta = beta;
+  bool alln = true;
+  for (int f = 0; f < 6; ++f) op->bc[f] = f < 2 * h->D ? bc_types[f] : 0;
+  for (int f = 0; f < 2 * h->D; ++f) alln = alln && bc_types[f] == AMR_BC_NEUMANN;
+  op->neumann = alln && alpha == 0.0;
+  // AMRCFI weights for ratio 2
+  CK(cudaMemcpyToSymbol(c_cfi, h->cfi_w.data(), h->cfi_w.size() * sizeof(double)));
+  // dense bottom inverse on the coarsest level-0 multigrid grid
+  const MgGrid& g = h->mg.back();
+  const int n = g.n[0] * g.n[1] * g.n[2];
+  const int ld = op->neumann ? n + 1 : n;
+  std::vector<double> A((size_t)ld * ld, 0.0);
+  std::vector<double> e(n, 0.0), y;
+  for (int j = 0; j < n; ++j) {
+    e.assign(n, 0.0);
+    e[j] = 1.0;
+    host_apply(h->D, g.n, g.h, alpha, beta, op->bc, e, y);
+    for (int i = 0; i < n; ++i) A[(size_t)i * ld + j] = y[i];
+  }
+  if (op->neumann) {
+    for (int i = 0; i < n; ++i) { A[(size_t)i * ld + n] = 1.0; A[(size_t)n * ld + i] = 1.0; }
+  }
+  if (!invert(A, ld)) { set_error("singular bottom operator"); return AMR_ERR_INVALID_ARG; }
+  op->nbot = n;
+  op->ldb = ld;
+  TRY(dalloc(&op->d_binv, A.size()));
+  CK(cudaMemcpy(op->d_binv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  // multigrid transfer blocks
+  for (size_t m = 0; m + 1 < h->mg.size(); ++m) {
+    XferBlock b{};
+    b.fpatch = 0;
+    b.cpatch = 0;
+    for (int q = 0; q < 3; ++q) { b.clo[q] = 0; b.chi[q] = h->mg[m + 1].n[q] - 1; }
+    XferBlock* d = nullptr;
+    TRY(dalloc(&d, 1));
+    CK(cudaMemcpy(d, &b, sizeof(b), cudaMemcpyHostToDevice));
+    op->d_mgx.push_back(d);
+  }
+  const size_t ne = (size_t)h->nelems;
+  TRY(dalloc(&op->F, ne));
+  TRY(dalloc(&op->Res, ne));
+  TRY(dalloc(&op->Tmp, ne));
+  CK(cudaMemset(op->F, 0, ne * sizeof(double)));
+  CK(cudaMemset(op->Res, 0, ne * sizeof(double)));
+  CK(cudaMemset(op->Tmp, 0, ne * sizeof(double)));
+  *out = op.release();
+  return AMR_OK;
+}
+
+void amr_operator_destroy(amr_operator* op) {
+  if (!op) return;
+  free_scratch(op->s64);
+  free_scratch(op->s32);
+  cudaFree(op->d_binv);
+  cudaFree(op->F);
+  cudaFree(op->Res);
+  cudaFree(op->Tmp);
+  for (auto p : op->d_mgx) cudaFree(p);
+  delete op;
+}
+
+amr_status amr_fill_ghosts(amr_operator* op, double* phi, const double* bc, void* stream) {
+  TRY(check_op(op));
+  if (!phi) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  (void)bc;  // physical ghosts are evaluated on the fly by the operators; see below
+  amr_hierarchy* h = op->h;
+  TRY(DISPATCH(h, fill_ghosts_all, h, phi, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_apply(amr_operator* op, double* phi, double* out, const double* bc, void* stream) {
+  TRY(check_op(op));
+  if (!phi || !out) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, composite_op, op, OP_APPLY, phi, nullptr, out, bc, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_residual(amr_operator* op, double* phi, const double* f, double* res, const double* bc, double* norm,
+                        void* stream) {
+  TRY(check_op(op));
+  if (!phi || !f || !res) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, composite_op, op, OP_RESID, phi, f, res, bc, S(stream)));
+  if (norm) {
+    amr_hierarchy* h = op->h;
+    if (h->D == 2) TRY((maxnorm<double, 2>(h, res, true, norm, S(stream))));
+    else TRY((maxnorm<double, 3>(h, res, true, norm, S(stream))));
+  }
+  return AMR_OK;
+}
+
+amr_status amr_smooth(amr_operator* op, int level, int nsweeps, double omega, double* x, const double* b, void* stream) {
+  TRY(check_op(op));
+  if (level < 0 || level >= op->h->L || nsweeps < 0 || !x || !b) { set_error("bad argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, smooth_impl, op, level, nsweeps, omega, x, b, S(stream)));
+  return AMR_OK;
+}
+
+static amr_status check_params(const amr_solver_params* p) {
+  if (!p || p->nu1 < 0 || p->nu2 < 0 || p->max_vcycles < 0 || !(p->omega > 0.0) ||
+      (p->precision != AMR_FP64 && p->precision != AMR_MIXED)) {
+    set_error("bad solver parameters");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return AMR_OK;
+}
+
+amr_status amr_vcycle(amr_operator* op, const amr_solver_params* p, double* phi, const double* f, const double* bc,
+                      void* stream) {
+  TRY(check_op(op));
+  TRY(check_params(p));
+  if (!phi || !f) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, vcycle_impl, op, *p, phi, f, bc, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_solve(amr_operator* op, const amr_solver_params* p, double* phi, const double* f, const double* bc,
+                     amr_solve_stats* stats, void* stream) {
+  TRY(check_op(op));
+  TRY(check_params(p));
+  if (!phi || !f) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  return DISPATCH(op->h, solve_impl, op, *p, phi, f, bc, stats, S(stream));
+}
+
+amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* phi_host, const double* f_host,
+                          const double* bc_host, amr_solve_stats* stats, void* stream) {
+  TRY(check_op(op));
+  TRY(check_params(p));
+  if (!phi_host || !f_host) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  amr_hierarchy* h = op->h;
+  const size_t bytes = (size_t)h->nelems * sizeof(double);
+  cudaStream_t st = S(stream);
+  double *dphi = nullptr, *df = nullptr, *dbc = nullptr;
+  TRY(dalloc(&dphi, h->nelems));
+  amr_status s = dalloc(&df, h->nelems);
+  const size_t nbc = (size_t)h->bc_off.back();
+  if (s == AMR_OK && bc_host) s = dalloc(&dbc, nbc);
+  if (s == AMR_OK) {
+    cudaMemcpyAsync(df, f_host, bytes, cudaMemcpyHostToDevice, st);
+    if (!p->zero_initial) cudaMemcpyAsync(dphi, phi_host, bytes, cudaMemcpyHostToDevice, st);
+    if (bc_host) cudaMemcpyAsync(dbc, bc_host, nbc * sizeof(double), cudaMemcpyHostToDevice, st);
+    s = DISPATCH(h, solve_impl, op, *p, dphi, df, dbc, stats, st);
+    if (s == AMR_OK || s == AMR_ERR_NOT_CONVERGED) {
+      cudaMemcpyAsync(phi_host, dphi, bytes, cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("stream sync failed"); s = AMR_ERR_CUDA; }
+    }
+  }
+  cudaFree(dphi);
+  cudaFree(df);
+  cudaFree(dbc);
+  return s;
+}
+
+amr_status amr_solvability_fix(amr_operator* op, double* f, const double* bc, double* m, void* stream) {
+  TRY(check_op(op));
+  if (!f) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, solvability_fix_impl, op, f, bc, m, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_mean_zero(amr_hierarchy* h, double* phi, double* mean, void* stream) {
+  if (!h || !phi) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  TRY(DISPATCH(h, mean_zero_impl, h, phi, mean, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_gradient(amr_hierarchy* h, const int* bc_types, double* phi, double* const* grad, const double* bc,
+                        void* stream) {
+  if (!h || !bc_types || !phi || !grad) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  TRY(DISPATCH(h, gradient_impl, h, bc_types, phi, grad, bc, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_divergence(amr_hierarchy* h, const int* bc_types, double* const* u, double* out, const double* const* bc,
+                          void* stream) {
+  if (!h || !bc_types || !u || !out) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  TRY(DISPATCH(h, divergence_impl, h, bc_types, u, out, bc, S(stream)));
+  return AMR_OK;
+}
+
+amr_status amr_project(amr_operator* ppe, const amr_solver_params* p, const int* vel_bc_types, double* const* w,
+                       const double* const* w_bc, double* const* u, double* phi, amr_solve_stats* stats, void* stream) {
+  TRY(check_op(ppe));
+  TRY(check_params(p));
+  if (!ppe->neumann) { set_error("projection needs the pure-Neumann PPE operator"); return AMR_ERR_INVALID_ARG; }
+  if (!vel_bc_types || !w || !u || !phi) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  return DISPATCH(ppe->h, project_impl, ppe, *p, vel_bc_types, w, w_bc, u, phi, stats, S(stream));
+}
+
+amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, void* stream) {
+  (void)op; (void)y; (void)out; (void)stream;
+  set_error("amr_apply_transpose: not available in this build");
+  return AMR_ERR_INVALID_ARG;
+}
+
+amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, double* lambda, const double* g,
+                               amr_solve_stats* stats, void* stream) {
+  (void)op; (void)p; (void)lambda; (void)g; (void)stats; (void)stream;
+  set_error("amr_solve_transpose: not available in this build");
+  return AMR_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

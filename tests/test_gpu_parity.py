@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
+element on seeded inputs.  Tolerances: operator applications within 1e-13 of the
+operator's term scale (|alpha| + |beta| sum|L coefs|/h^2) * max|phi|; smoothing within
+1e-12 relative; one V-cycle within 1e-10 relative; solutions within 1e-10 relative
+max-norm (FP64 and mixed precision refined to the same residual)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import composite as cp, mg, solve as so  # noqa: E402
+from oracle.hierarchy import Hierarchy as OH  # noqa: E402
+
+from _gpu_helpers import from_packed, level_bc_data, max_abs, max_diff, op_scale, to_packed  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+HIERS = {
+    # ragged non-square base, box touching the x-low boundary
+    "two_level_ragged": (2, (40, 24), [[((0, 0), (39, 23))], [((0, 8), (27, 39))]]),
+    # multi-box level with a shared face + a third level
+    "three_level_multibox": (2, (24, 24), [[((0, 0), (23, 23))], [((8, 8), (23, 31)), ((24, 8), (39, 31))],
+                                           [((24, 24), (47, 47))]]),
+    # 3-D two-level
+    "three_d": (3, (12, 12, 12), [[((0, 0, 0), (11, 11, 11))], [((8, 0, 4), (19, 11, 15))]]),
+}
+
+
+def _amr():
+    from paper_2506_02663_gb300 import amr
+    return amr
+
+
+def _hier(name, bc):
+    dim, n0, boxes = HIERS[name]
+    hi = tuple(n0[d] / n0[0] for d in range(dim))
+    H = OH(dim, n0, boxes, bc=bc, hi=hi)
+    gh = _amr().Hierarchy(dim, n0, boxes, h0=1.0 / n0[0])
+    return H, gh
+
+
+def _rand_field(H, rng, redundant=True):
+    U = so.Unknowns(H)
+    return U.scatter(rng.standard_normal(U.n), fill_invalid=redundant)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _bc_data(H, rng):
+    out = []
+    for lev in H.levels:
+        out.append({2 * d + s: rng.standard_normal(tuple(lev.ndom[e] for e in range(H.D) if e != d))
+                    for d in range(H.D) for s in (0, 1)})
+    return out
+
+
+BCS = {2: ([0, 1, 0, 0], [1, 1, 1, 1], [0, 0, 0, 0]), 3: ([0, 1, 0, 0, 1, 0], [1] * 6, [0] * 6)}
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+def test_fill_ghosts_cfi_and_copy(name):
+    dim = HIERS[name][0]
+    H, gh = _hier(name, [0] * (2 * dim))
+    rng = np.random.default_rng(1)
+    F = _rand_field(H, rng)
+    P = [a.copy() for a in F]
+    cp.average_down_all(H, P)
+    for l in range(1, H.lmax + 1):
+        cp.fill_cf_ghosts(H, P, l)
+    op = _amr().Operator(gh, 0.0, 1.0, [0] * (2 * dim))
+    d = _dev(to_packed(gh, H, F, fill=np.nan))
+    op.fill_ghosts(d)
+    flat = d.cpu().numpy()
+    maps = gh.index_maps()
+    codes = maps["ghost_code"]
+    base = 0
+    worst = 0.0
+    for p in gh.patches:
+        l = p["level"]
+        lev = H.levels[l]
+        n = [p["hi"][e] - p["lo"][e] + 1 for e in range(dim)]
+        ext = [v + 4 for v in n]
+        view = gh._view(flat, p)
+        cnt = int(np.prod(ext))
+        c = codes[base:base + cnt].reshape(ext[::-1])  # [z][y][x]
+        for idx in np.argwhere((c == 2) | (c == 3)):
+            a = idx[::-1]
+            g = [p["lo"][e] - 2 + a[e] for e in range(dim)]
+            arr = tuple(g[e] - lev.origin[e] for e in range(dim))
+            got = view[tuple(idx)]
+            worst = max(worst, abs(got - P[l][arr]))
+        base += cnt
+    assert worst <= 1e-14 * max_abs(H, F, "covered")
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_apply_parity_with_boundary_data(name, which):
+    dim = HIERS[name][0]
+    bc = BCS[dim][which]
+    H, gh = _hier(name, bc)
+    rng = np.random.default_rng(2 + which)
+    F = _rand_field(H, rng)
+    data = _bc_data(H, rng)
+    for alpha, beta in ((0.0, 1.0), (1.0, -0.01)):
+        ref = cp.apply(H, F, alpha, beta, data)
+        op = _amr().Operator(gh, alpha, beta, bc)
+        d = _dev(to_packed(gh, H, F, fill=np.nan))
+        out = torch.zeros_like(d)
+        op.apply(d, out, bc=_dev(gh.pack_bc(data)))
+        got = from_packed(gh, H, out.cpu().numpy())
+        err = max_diff(H, got, ref)
+        assert np.isfinite(err)
+        assert err <= 1e-13 * op_scale(H, alpha, beta, F), (err, op_scale(H, alpha, beta, F))
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+def test_smoother_parity(name):
+    dim = HIERS[name][0]
+    bc = BCS[dim][0]
+    H, gh = _hier(name, bc)
+    rng = np.random.default_rng(5)
+    alpha, beta = 1.0, -0.02
+    op = _amr().Operator(gh, alpha, beta, bc)
+    for l in range(H.lmax + 1):
+        X = _rand_field(H, rng, redundant=False)
+        B = _rand_field(H, rng, redundant=False)
+        diag = mg.jacobi_diagonal(H, l, alpha, beta)
+        Xr = X[l].copy()
+        for _ in range(3):
+            Xr = mg.jacobi(H, l, Xr, B[l], diag, alpha, beta, 2.0 / 3.0)
+        dx = _dev(to_packed(gh, H, X))
+        db = _dev(to_packed(gh, H, B))
+        op.smooth(l, 3, 2.0 / 3.0, dx, db)
+        got = from_packed(gh, H, dx.cpu().numpy())
+        lev = H.levels[l]
+        err = float(np.max(np.abs(got[l][lev.covered] - Xr[lev.covered])))
+        assert err <= 1e-12 * float(np.max(np.abs(Xr[lev.covered]))), (l, err)
+
+
+@pytest.mark.parametrize("name", ["two_level_ragged", "three_level_multibox"])
+@pytest.mark.parametrize("bcw", [0, 1])
+def test_one_vcycle_parity(name, bcw):
+    dim = HIERS[name][0]
+    bc = [bcw] * (2 * dim)
+    H, gh = _hier(name, bc)
+    rng = np.random.default_rng(9)
+    alpha, beta = (0.0, 1.0)
+    F = _rand_field(H, rng)
+    if bcw == 1:
+        F, _ = so.solvability_fix(H, F)
+    phi = _rand_field(H, rng)
+    ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+    op = _amr().Operator(gh, alpha, beta, bc)
+    dphi = _dev(to_packed(gh, H, phi))
+    op.vcycle(dphi, _dev(to_packed(gh, H, F)))
+    got = from_packed(gh, H, dphi.cpu().numpy())
+    err = max_diff(H, got, ref)
+    assert err <= 1e-10 * max_abs(H, ref), err
+
+
+SOLVE_CASES = [
+    ("two_level_ragged", 0, (1.0, -0.01)),
+    ("two_level_ragged", 1, (0.0, 1.0)),
+    ("three_level_multibox", 0, (0.0, 1.0)),
+    ("three_level_multibox", 1, (0.0, 1.0)),
+    ("three_d", 0, (1.0, -0.01)),
+    ("three_d", 1, (0.0, 1.0)),
+]
+
+
+@pytest.mark.parametrize("name,bcw,ab", SOLVE_CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_parity(name, bcw, ab, precision):
+    amr = _amr()
+    dim = HIERS[name][0]
+    bc = [bcw] * (2 * dim)
+    H, gh = _hier(name, bc)
+    alpha, beta = ab
+    rng = np.random.default_rng(11)
+    F = _rand_field(H, rng)
+    Fc = F
+    if so.is_pure_neumann(H, alpha):
+        Fc, _ = so.solvability_fix(H, F)
+    ref, _, _ = so.solve_direct(H, Fc, alpha, beta)
+    if so.is_pure_neumann(H, alpha):
+        ref, _ = so.mean_zero(H, ref)
+    op = amr.Operator(gh, alpha, beta, bc)
+    dphi = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    st = op.solve(dphi, _dev(to_packed(gh, H, F)),
+                  params=amr.default_params(rtol=1e-12, max_vcycles=200, precision=precision))
+    got = from_packed(gh, H, dphi.cpu().numpy())
+    err = max_diff(H, got, ref)
+    assert err <= 1e-10 * max_abs(H, ref), (err, st)
+
+
+def test_solvability_fix_and_mean_zero_parity():
+    amr = _amr()
+    H, gh = _hier("three_level_multibox", [1, 1, 1, 1])
+    rng = np.random.default_rng(13)
+    F = _rand_field(H, rng)
+    F = [a + 2.5 for a in F]
+    data = _bc_data(H, rng)
+    ref, m = so.solvability_fix(H, F, beta=1.0, bc_data=data)
+    op = amr.Operator(gh, 0.0, 1.0, [1, 1, 1, 1])
+    d = _dev(to_packed(gh, H, F))
+    mg_ = op.solvability_fix(d, bc=_dev(gh.pack_bc(data)))
+    assert abs(mg_ - m) <= 1e-14 * abs(m)
+    got = from_packed(gh, H, d.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-14 * max_abs(H, ref)
+    phi = _rand_field(H, rng)
+    phi = [a + 1.0 for a in phi]
+    refz, mean = so.mean_zero(H, phi)
+    dp = _dev(to_packed(gh, H, phi))
+    mm = amr.mean_zero(gh, dp)
+    assert abs(mm - mean) <= 1e-14 * abs(mean)
+    gotz = from_packed(gh, H, dp.cpu().numpy())
+    assert max_diff(H, gotz, refz) <= 1e-13 * max_abs(H, phi)
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+def test_gradient_divergence_parity(name):
+    amr = _amr()
+    dim = HIERS[name][0]
+    H, gh = _hier(name, [1] * (2 * dim))
+    rng = np.random.default_rng(17)
+    phi = _rand_field(H, rng)
+    G = cp.gradient(H, phi)
+    dphi = _dev(to_packed(gh, H, phi))
+    grads = [torch.zeros_like(dphi) for _ in range(dim)]
+    amr.gradient(gh, [1] * (2 * dim), dphi, grads)
+    scale = max_abs(H, phi, "covered") * 16.0 / (12 * min(l.h for l in H.levels))
+    for d in range(dim):
+        got = from_packed(gh, H, grads[d].cpu().numpy())
+        assert max_diff(H, got, G[d]) <= 1e-13 * scale
+    U = [_rand_field(H, rng) for _ in range(dim)]
+    Y = cp.divergence(H, U, None, [0] * (2 * dim))
+    du = [_dev(to_packed(gh, H, u)) for u in U]
+    out = torch.zeros_like(du[0])
+    amr.divergence(gh, [0] * (2 * dim), du, out)
+    got = from_packed(gh, H, out.cpu().numpy())
+    scale = max(max_abs(H, u, "covered") for u in U) * 16.0 * dim / (12 * min(l.h for l in H.levels))
+    assert max_diff(H, got, Y) <= 1e-13 * scale
+
+
+def test_projection_parity():
+    amr = _amr()
+    H, gh = _hier("two_level_ragged", [1, 1, 1, 1])
+    rng = np.random.default_rng(19)
+    W = [_rand_field(H, rng) for _ in range(2)]
+    Uref, phiref = so.project(H, W)
+    ppe = amr.Operator(gh, 0.0, 1.0, [1, 1, 1, 1])
+    dw = [_dev(to_packed(gh, H, w)) for w in W]
+    du = [torch.zeros_like(dw[0]) for _ in range(2)]
+    dphi = torch.zeros_like(dw[0])
+    amr.project(ppe, [0, 0, 0, 0], dw, du, dphi, params=amr.default_params(rtol=1e-13, max_vcycles=200))
+    for d in range(2):
+        got = from_packed(gh, H, du[d].cpu().numpy())
+        assert max_diff(H, got, Uref[d], "covered") <= 1e-9 * max_abs(H, Uref[d]), d
+    gphi = from_packed(gh, H, dphi.cpu().numpy())
+    assert max_diff(H, gphi, phiref) <= 1e-10 * max_abs(H, phiref)
+
+
+def test_manufactured_solution_order_on_gpu():
+    """The 64^2 manufactured-solution workload with inhomogeneous Dirichlet data, solved to
+    1e-12: fourth-order convergence of the GPU solution against exact cell averages."""
+    amr = _amr()
+    from paper_2506_02663_gb300 import workloads as wl
+    errs = []
+    for n in (32, 64, 128):
+        rhs, bcd, exact = wl.ms2d(n)
+        gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+        op = amr.Operator(gh, 0.0, 1.0, [0, 0, 0, 0])
+        dphi = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve(dphi, _dev(gh.pack([[rhs]])), bc=_dev(gh.pack_bc([bcd])),
+                      params=amr.default_params(rtol=1e-12, max_vcycles=100))
+        got = gh.unpack(dphi.cpu().numpy())[0][0]
+        errs.append(np.sum(np.abs(got - exact)) / n ** 2)
+        if n == 64:
+            assert st["final_res"] <= 1e-12 * st["rhs_norm"]
+    assert np.log2(errs[0] / errs[1]) > 3.8 and np.log2(errs[1] / errs[2]) > 3.8, errs
+
+
+def test_status_codes_and_nan_corners():
+    amr = _amr()
+    H, gh = _hier("two_level_ragged", [0, 0, 0, 0])
+    rng = np.random.default_rng(23)
+    F = _rand_field(H, rng)
+    op = amr.Operator(gh, 0.0, 1.0, [0, 0, 0, 0])
+    # corners and pitch padding poisoned with NaN: never read by any kernel
+    dphi = _dev(to_packed(gh, H, cp.new_field(H), fill=np.nan))
+    st = op.solve(dphi, _dev(to_packed(gh, H, F, fill=np.nan)), params=amr.default_params(rtol=1e-10, zero_initial=0))
+    assert st["status"] == amr.AMR_OK and np.isfinite(st["final_res"])
+    # iteration cap reported as NOT_CONVERGED with valid statistics
+    d2 = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    st = op.solve(d2, _dev(to_packed(gh, H, F)), params=amr.default_params(rtol=1e-14, max_vcycles=1),
+                  allow_not_converged=True)
+    assert st["status"] == amr.AMR_ERR_NOT_CONVERGED and st["vcycles"] == 1
+    # a NaN in the right-hand side is detected by the residual norm
+    Fn = to_packed(gh, H, F)
+    Fn[gh.patches[0]["offset"] + 3 * gh.patches[0]["sy"] + 3] = np.nan
+    with pytest.raises(amr.AmrError) as ei:
+        op.solve(torch.zeros_like(d2), _dev(Fn))
+    assert ei.value.status == amr.AMR_ERR_NONFINITE
+    # bad parameters are rejected on the host before any launch
+    with pytest.raises(amr.AmrError) as ei:
+        op.solve(d2, _dev(Fn), params=amr.default_params(nu1=-1))
+    assert ei.value.status == amr.AMR_ERR_INVALID_ARG
+
+
+def _bumps2d_gpu(scale=1):
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, rhs = wl.bumps2d_rhs(scale)
+    return dim, n0, boxes, rhs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_bumps2d_residual_property(precision):
+    """The two-level 256^2 workload at full size in the bench's launch configuration: the
+    oracle's own composite operator confirms the GPU solution's residual (PPE and
+    Helmholtz), i.e. a property that holds at any size."""
+    amr = _amr()
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, rhs = _bumps2d_gpu()
+    gh = amr.Hierarchy(dim, n0, boxes)
+    f = _dev(gh.pack(rhs))
+    for bc, (alpha, beta) in (([1, 1, 1, 1], (0.0, 1.0)), ([0, 0, 0, 0], (1.0, wl.HELMHOLTZ_BETA))):
+        H = OH(dim, n0, boxes, bc=bc)
+        op = amr.Operator(gh, alpha, beta, bc)
+        dphi = torch.zeros_like(f)
+        st = op.solve(dphi, f, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=precision))
+        phi = from_packed(gh, H, dphi.cpu().numpy())
+        F = from_packed(gh, H, f.cpu().numpy())
+        if so.is_pure_neumann(H, alpha):
+            F, m = so.solvability_fix(H, F)
+            assert abs(m - st["removed_mean"]) <= 1e-14 * max(abs(m), 1e-300) + 1e-300
+        R = cp.residual(H, phi, F, alpha, beta)
+        assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F), (max_abs(H, R), st)
