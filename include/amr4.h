@@ -256,6 +256,17 @@ amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* 
 
 void amr_default_params(amr_solver_params* p);
 const char* amr_last_error(void);
+/* Number of CUDA kernels this library has launched in the process so far (a host-side
+ * counter; a replayed CUDA graph counts its kernel nodes). */
+long long amr_kernel_launches(void);
+/* Bench instrumentation.  amr_profile_enable(1) clears the record and makes the library
+ * bracket every launch of the instrumented kernel classes with CUDA events on the
+ * launching stream (0 stops recording).  amr_profile_read() synchronises on the recorded
+ * events and returns, for one class, the number of launches, the summed event intervals
+ * (ms) and the summed algorithmic bytes.  Classes: 0 weighted-Jacobi sweeps, 1 level
+ * residual / apply, 2 restriction and average-down, 3 prolongation. */
+amr_status amr_profile_enable(int on);
+amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes);
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,9 @@ _sigs = {
     "amr_solve_transpose": [_vp, _P(SolverParams), _vp, _vp, _P(SolveStats), _vp],
     "amr_default_params": [_P(SolverParams)],
     "amr_last_error": [],
+    "amr_kernel_launches": [],
+    "amr_profile_enable": [C.c_int],
+    "amr_profile_read": [C.c_int, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
 }
 for _n, _a in _sigs.items():
     _f = getattr(_lib, _n)
@@ -93,6 +96,26 @@ _lib.amr_hierarchy_destroy.restype = None
 _lib.amr_operator_destroy.restype = None
 _lib.amr_default_params.restype = None
 _lib.amr_last_error.restype = C.c_char_p
+_lib.amr_kernel_launches.restype = C.c_longlong
+
+
+def kernel_launches():
+    return int(_lib.amr_kernel_launches())
+
+
+KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG = 0, 1, 2, 3
+
+
+def profile_enable(on):
+    _check(_lib.amr_profile_enable(1 if on else 0), "amr_profile_enable")
+
+
+def profile_read(kernel_class):
+    n = C.c_longlong()
+    ms = C.c_double()
+    by = C.c_double()
+    _check(_lib.amr_profile_read(kernel_class, C.byref(n), C.byref(ms), C.byref(by)), "amr_profile_read")
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
 EXPORTED = tuple(_sigs)
 

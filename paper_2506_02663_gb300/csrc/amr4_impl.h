@@ -35,6 +35,7 @@ struct LevelView {
   int bc[6];                 // boundary type per face
   long long bc_off[6];       // offsets of this level's faces inside a bc array
   long long bc_pitch[6];     // leading extent of each face array (transverse dim 0)
+  double ncells;             // interior cells over all patches (host bookkeeping)
 };
 
 // AMRCFI ghost cell: dst = fine field offset; src >= 0: field offset of the window's first

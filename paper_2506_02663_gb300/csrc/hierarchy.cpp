@@ -610,6 +610,8 @@ LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types) {
   v.D = h->D;
   v.h = L.h;
   for (int e = 0; e < 3; ++e) { v.ndom[e] = L.ndom[e]; v.maxn[e] = L.maxn[e]; }
+  v.ncells = 0.0;
+  for (const PatchDesc& p : L.patches) v.ncells += (double)p.n[0] * p.n[1] * p.n[2];
   for (int f = 0; f < 6; ++f) {
     v.bc[f] = (f < 2 * h->D && bc_types) ? bc_types[f] : 0;
     v.bc_off[f] = (f < 2 * h->D) ? h->bc_off[(size_t)l * 2 * h->D + f] : 0;

@@ -3,6 +3,7 @@
 // solvability fix (Sec. 6.3), the composite projection (Eq. comp_ProjOp) and FP32 V-cycles
 // inside FP64 iterative refinement.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -59,13 +60,54 @@ namespace {
     }                                                                                 \
   } while (0)
 
+std::atomic<long long> g_launches{0};  // kernels launched by this library (host count)
+
 inline amr_status launch_check() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
     return AMR_ERR_CUDA;
   }
   return AMR_OK;
+}
+
+// ---------------------------------------------------------------- bench instrumentation
+// When enabled, launches of the instrumented kernel classes are bracketed with CUDA events
+// on the launching stream; amr_profile_read() sums the event intervals.
+enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_NCLASS = 4 };
+struct ProfRec {
+  cudaEvent_t a, b;
+  int cls;
+  double bytes;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+Profiler g_prof;
+constexpr size_t PROF_MAX = 400000;
+
+inline void prof_begin(cudaStream_t st, cudaEvent_t* ev) {
+  if (!g_prof.on || g_prof.used + 2 > 2 * PROF_MAX) { *ev = nullptr; return; }
+  *ev = g_prof.get();
+  cudaEventRecord(*ev, st);
+}
+inline void prof_end(cudaStream_t st, cudaEvent_t a, int cls, double bytes) {
+  if (a == nullptr) return;
+  cudaEvent_t b = g_prof.get();
+  cudaEventRecord(b, st);
+  g_prof.recs.push_back({a, b, cls, bytes});
 }
 
 template <typename T>
@@ -100,6 +142,7 @@ LevelView mg_view(const amr_hierarchy* h, int m, const int* bc) {
   v.h = g.h;
   for (int e = 0; e < 3; ++e) { v.ndom[e] = g.n[e]; v.maxn[e] = g.n[e]; }
   for (int f = 0; f < 6; ++f) { v.bc[f] = bc[f]; v.bc_off[f] = 0; v.bc_pitch[f] = 1; }
+  v.ncells = (double)g.n[0] * g.n[1] * g.n[2];
   return v;
 }
 
@@ -185,6 +228,8 @@ template <typename T, int D>
 amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* out, const T* bc, double alpha,
                     double beta, double omega, const unsigned char* vmask, cudaStream_t st) {
   Geo g = geo_of(lv);
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
   switch (mode) {
     case OP_APPLY:
       k_level_op<T, D, OP_APPLY><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
@@ -198,6 +243,10 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
     default:
       k_level_op<T, D, OP_JACOBI0><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
   }
+  // algorithmic bytes: Jacobi reads x, f and writes the sweep (the first sweep reads f
+  // only); residual reads x, f and writes r; apply reads x and writes the result
+  const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
+  prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
   return launch_check();
 }
 
@@ -209,10 +258,14 @@ amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const Xf
   const int nby = (xmax[1] + BY - 1) / BY;
   dim3 grid((xmax[0] + BX - 1) / BX, nby * (D == 3 ? xmax[2] : 1), nblocks);
   dim3 block(BX, BY, 1);
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
   if (resid)
     k_restrict<T, D, true><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
   else
     k_restrict<T, D, false><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
+  const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
+  prof_end(st, ev, PC_RESTRICT, ((resid ? 2.0 : 1.0) * (1 << D) + 1.0) * sizeof(T) * cc);
   return launch_check();
 }
 
@@ -224,7 +277,11 @@ amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const Xfe
   const int nby = (fy + BY - 1) / BY;
   dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
   dim3 block(BX, BY, 1);
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
   k_prolong<T, D><<<grid, block, 0, st>>>(fine, crs, blocks, xc, xf, xf2, nby);
+  const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
+  prof_end(st, ev, PC_PROLONG, (1.0 + (1 << D) * (xf2 ? 4.0 : 2.0)) * sizeof(T) * cc);
   return launch_check();
 }
 
@@ -820,6 +877,35 @@ static amr_status ensure_device(amr_hierarchy* h) {
 extern "C" {
 
 const char* amr_last_error(void) { return get_error(); }
+
+long long amr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+amr_status amr_profile_enable(int on) {
+  for (auto& r : g_prof.recs) (void)r;
+  g_prof.recs.clear();
+  g_prof.used = 0;
+  g_prof.on = on != 0;
+  return AMR_OK;
+}
+
+amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes) {
+  if (kernel_class < 0 || kernel_class >= PC_NCLASS) { set_error("bad kernel class"); return AMR_ERR_INVALID_ARG; }
+  long long n = 0;
+  double ms = 0.0, by = 0.0;
+  for (const ProfRec& r : g_prof.recs) {
+    if (r.cls != kernel_class) continue;
+    CK(cudaEventSynchronize(r.b));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    by += r.bytes;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  if (total_bytes) *total_bytes = by;
+  return AMR_OK;
+}
 
 void amr_default_params(amr_solver_params* p) {
   if (!p) return;

@@ -22,7 +22,7 @@ def amr():
 
 def test_exports_every_declared_symbol(amr):
     hdr = open(os.path.join(ROOT, "include", "amr4.h")).read()
-    declared = set(re.findall(r"^\s*(?:amr_status|void|const char\*)\s+(amr_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:amr_status|void|const char\*|long long)\s+(amr_\w+)\s*\(", hdr, re.M))
     assert len(declared) >= 20
     import ctypes
     lib = ctypes.CDLL(amr.LIB)
