@@ -1,0 +1,415 @@
+"""Benchmark of the hot path: composite geometric-multigrid solves of the fourth-order
+finite-volume elliptic systems on a two-level 2-D AMR hierarchy.
+
+Workload ``bumps2d``: base 256^2 on the unit square, one ratio-2 box over [0.25,0.75]^2
+(256^2 fine cells), right-hand side = exact cell averages of a seeded sum of 8 Gaussian
+bumps.  One step = one pass of the whole hot path: the pure-Neumann pressure Poisson
+equation (solvability fix, V-cycles to ||r||_inf <= 1e-10 ||f||_inf, mean-zero) and the
+viscous Helmholtz system (alpha = 1, beta = -gamma nu k, gamma = 0.25, nu = 1e-3,
+k = 1/256, Dirichlet) solved to the same tolerance.  Metric: V-cycle DOF/s = valid cells
+x V-cycles / time, summed over both systems and all ranks.
+
+``python bench.py [--gpus N --steps K --warmup W]``        this library (GB300)
+``python bench.py --impl reference ...``                    the CPU oracle on host cores
+Under torchrun (N > 1) every rank solves its own replica (the solve does not shard:
+replicas only) and rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle DOF/s & time-to-1e-10 residual; HBM GB/s vs 8 TB/s; mixed vs FP64"
+UNIT = "DOF*V-cycles/s"
+WORKLOAD = ("bumps2d: 2-D two-level AMR, base 256^2 on [0,1]^2 + ratio-2 box [0.25,0.75]^2 "
+            "(256^2 fine cells), RHS = cell averages of 8 seeded Gaussian bumps; per step: pure-Neumann "
+            "PPE + Helmholtz (gamma=0.25, nu=1e-3, k=1/256, Dirichlet), each to ||r||_inf <= 1e-10 ||f||_inf")
+RTOL = 1e-10
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the large-grid roofline")
+    ap.add_argument("--profile-case", choices=["none", "large"], default="none",
+                    help="run only one mixed-precision solve of the single-level 4096^2 case (for ncu)")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, rhs = wl.bumps2d_rhs()
+    systems = [("ppe", [1, 1, 1, 1], 0.0, 1.0), ("helmholtz", [0, 0, 0, 0], 1.0, wl.HELMHOLTZ_BETA)]
+    return dim, n0, boxes, rhs, systems
+
+
+def valid_dof(n0, boxes):
+    """Valid cells of a two-level hierarchy: level-0 cells minus the coarsened level-1
+    boxes, plus every level-1 cell (top level has no invalid region)."""
+    n = n0[0] * n0[1]
+    fine = 0
+    cover = 0
+    for lo, hi in boxes[1]:
+        c = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1)
+        fine += c
+        cover += c // 4
+    return n - cover + fine
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "solver.cu"):
+        with open(os.path.join(ROOT, "paper_2506_02663_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_class_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel_class_name)
+        if e and e.get("source_hash") == _kernel_source_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ============================================================================ oracle arm
+def _oracle_vcycles(seconds, max_cycles=None):
+    """Time oracle V-cycles (PPE and Helmholtz alternately, setup excluded) on the full
+    workload for about ``seconds``; returns (DOF*V-cycles per second, cycles, seconds)."""
+    import numpy as np
+    from oracle import composite as cp, mg, solve as so
+    from oracle.hierarchy import Hierarchy as OH
+    dim, n0, boxes, rhs, systems = _workload()
+    dof = valid_dof(n0, boxes)
+    runs = []
+    for name, bc, alpha, beta in systems:
+        H = OH(dim, n0, boxes, bc=bc)
+        F = cp.new_field(H)
+        for l, lev in enumerate(H.levels):
+            for k, (lo, hi) in enumerate(lev.boxes):
+                F[l][lev.box_slice(lo, hi)] = rhs[l][k]
+        if so.is_pure_neumann(H, alpha):
+            F, _ = so.solvability_fix(H, F)
+        runs.append((H, mg.CompositeMG(H, alpha, beta), F))
+    phis = [cp.new_field(H) for H, _, _ in runs]
+    cycles = 0
+    t0 = time.perf_counter()
+    while True:
+        for i, (H, m, F) in enumerate(runs):
+            phis[i] = m.vcycle(phis[i], F)
+            cycles += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_cycles and cycles >= max_cycles):
+            break
+    return dof * cycles / el, cycles, el
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    # each step: one oracle V-cycle of each system on the full workload
+    vals = []
+    for _ in range(args.warmup):
+        _oracle_vcycles(0.0, max_cycles=2)
+    t_all = 0.0
+    dofv = 0.0
+    for _ in range(args.steps):
+        v, c, el = _oracle_vcycles(0.0, max_cycles=2)
+        vals.append(v)
+        t_all += el
+        dofv += v * el
+    value = dofv / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "arm": "FP64 numpy oracle, one V-cycle per system per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x (1 PPE + 1 Helmholtz oracle V-cycle) on the full workload, setup excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ============================================================================ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2506_02663_gb300 import amr
+    dim, n0, boxes, rhs, systems = _workload()
+    dof = valid_dof(n0, boxes)
+    gh = amr.Hierarchy(dim, n0, boxes)
+    f_host = gh.pack(rhs)
+    f = torch.from_numpy(f_host).cuda()
+    ops = [amr.Operator(gh, a, b, bc) for _, bc, a, b in systems]
+    phis = [torch.zeros_like(f) for _ in systems]
+    prec = amr.MIXED if args.precision == "mixed" else amr.FP64
+    params = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(p):
+        vc = []
+        for op, phi in zip(ops, phis):
+            st = op.solve(phi, f, params=p)
+            vc.append(st["vcycles"])
+        return vc
+
+    def timed(p, k):
+        ts, vcs = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vcs.append(step(p))
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts, vcs
+
+    for _ in range(args.warmup):
+        step(params)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = amr.kernel_launches()
+    ts, vcs = timed(params, args.steps)
+    launches = amr.kernel_launches() - l0
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    total_ms = sum(ts)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    dofv_rank = sum(dof * sum(v) for v in vcs)
+    value = ws * dofv_rank / (tmax * 1e-3)
+    vc_per_system = [statistics.mean(v[i] for v in vcs) for i in range(len(systems))]
+
+    # ---------------- end to end through the C ABI with host buffers
+    import torch as _t
+    fh = _t.from_numpy(f_host).pin_memory().numpy()
+    ph = _t.zeros(gh.nelems, dtype=_t.float64).pin_memory().numpy()
+    e2e_v = 0
+    for op in ops:
+        op.solve_host(ph, fh, params=params)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        for op in ops:
+            st = op.solve_host(ph, fh, params=params)
+            e2e_v += st["vcycles"]
+    te = time.perf_counter() - te
+    e2e = {"value": ws * dof * e2e_v / te if te > 0 else None, "unit": UNIT,
+           "h2d_bytes_per_step": len(systems) * gh.nelems * 8, "d2h_bytes_per_step": len(systems) * gh.nelems * 8,
+           "ms_per_step": 1e3 * te / args.steps}
+
+    # ---------------- roofline of the dominant kernel (weighted-Jacobi sweeps), live
+    peak, peak_kind = _peaks()
+    amr.profile_enable(True)
+    timed(params, max(1, min(args.steps, 5)))
+    amr.profile_enable(False)
+    jac = amr.profile_read(amr.KC_JACOBI)
+    achieved = jac["bytes"] / (jac["ms"] * 1e-3) / 1e9 if jac["ms"] > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": _traffic("jacobi_bumps2d"),
+                "kernel": "k_level_op<float,2,JACOBI> + first-sweep variant (all levels)",
+                "launches": jac["launches"], "avg_launch_us": 1e3 * jac["ms"] / max(jac["launches"], 1),
+                "bytes_per_launch": jac["bytes"] / max(jac["launches"], 1), "peak_source": f"{peak_kind} hbm_gbs"}
+    others = {}
+    for name, kc in (("residual", amr.KC_RESID), ("restrict", amr.KC_RESTRICT), ("prolong", amr.KC_PROLONG)):
+        r = amr.profile_read(kc)
+        others[name] = {"launches": r["launches"], "ms": r["ms"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 V-cycles in f64 refinement" if prec == amr.MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dof_per_system": dof, "systems": [s[0] for s in systems],
+                   "precision": args.precision, "rtol": RTOL, "vcycles_per_system": vc_per_system,
+                   "l2": "flushed (256 MB write) before every timed step; the working set fits in L2",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "roofline": roofline,
+        "kernel_classes_ms": others,
+    }
+
+    if not args.no_extras and rank == 0:
+        p64 = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.FP64 if prec == amr.MIXED else amr.MIXED)
+        step(p64)
+        ts2, vcs2 = timed(p64, args.steps)
+        v2 = dof * sum(sum(v) for v in vcs2) / (sum(ts2) * 1e-3)
+        key = "fp64" if prec == amr.MIXED else "mixed"
+        line[key] = {"value": v2, "ms_per_step": sum(ts2) / args.steps,
+                     "vcycles_per_system": [statistics.mean(v[i] for v in vcs2) for i in range(len(systems))]}
+        line["large_grid_roofline"] = _large_grid_roofline(amr, torch, peak, peak_kind)
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, c, el = _oracle_vcycles(12.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{c} FP64 numpy-oracle V-cycles (PPE and Helmholtz alternating) on the full "
+                                          f"workload in {el:.1f} s, setup excluded; numpy element-wise ops use one core"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _large_grid_roofline(amr, torch, peak, peak_kind, n=4096):
+    """Same Jacobi kernel on a single-level n^2 Helmholtz solve (fields >> L2): the HBM
+    efficiency of the smoother when it is not launch-bound."""
+    from paper_2506_02663_gb300 import workloads as wl
+    gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+    op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA * 16.0, [0, 0, 0, 0])
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    f = torch.randn(gh.nelems, dtype=torch.float64, device="cuda", generator=g)
+    phi = torch.zeros_like(f)
+    p = amr.default_params(rtol=1e-10, max_vcycles=40, precision=amr.MIXED)
+    op.solve(phi, f, params=p)
+    amr.profile_enable(True)
+    st = op.solve(phi, f, params=p)
+    amr.profile_enable(False)
+    jac = amr.profile_read(amr.KC_JACOBI)
+    ach = jac["bytes"] / (jac["ms"] * 1e-3) / 1e9
+    op.close()
+    gh.close()
+    return {"workload": f"single-level {n}^2 Helmholtz, mixed precision, {st['vcycles']} V-cycles",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "launches": jac["launches"], "peak_source": f"{peak_kind} hbm_gbs"}
+
+
+def _profile_case():
+    import torch
+    from paper_2506_02663_gb300 import amr
+    from paper_2506_02663_gb300 import workloads as wl
+    n = 4096
+    gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+    op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA * 16.0, [0, 0, 0, 0])
+    f = torch.ones(gh.nelems, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(f)
+    st = op.solve(phi, f, params=amr.default_params(rtol=1e-10, max_vcycles=40, precision=amr.MIXED))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "large", "vcycles": st["vcycles"], "final_res": st["final_res"]}))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.profile_case == "large":
+        return _profile_case()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

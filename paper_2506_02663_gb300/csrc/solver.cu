@@ -47,6 +47,9 @@ struct amr_operator {
   double* Res = nullptr;  // FP64 composite residual
   double* Tmp = nullptr;  // FP64 composite scratch
   std::vector<XferBlock*> d_mgx;  // transfer block m -> m+1
+  double* hphi = nullptr;  // device staging for the host-buffer solve (allocated once)
+  double* hf = nullptr;
+  double* hbc = nullptr;
 };
 
 namespace {
@@ -1058,6 +1061,9 @@ void amr_operator_destroy(amr_operator* op) {
   cudaFree(op->Res);
   cudaFree(op->Tmp);
   for (auto p : op->d_mgx) cudaFree(p);
+  cudaFree(op->hphi);
+  cudaFree(op->hf);
+  cudaFree(op->hbc);
   delete op;
 }
 
@@ -1131,24 +1137,18 @@ amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* 
   amr_hierarchy* h = op->h;
   const size_t bytes = (size_t)h->nelems * sizeof(double);
   cudaStream_t st = S(stream);
-  double *dphi = nullptr, *df = nullptr, *dbc = nullptr;
-  TRY(dalloc(&dphi, h->nelems));
-  amr_status s = dalloc(&df, h->nelems);
   const size_t nbc = (size_t)h->bc_off.back();
-  if (s == AMR_OK && bc_host) s = dalloc(&dbc, nbc);
-  if (s == AMR_OK) {
-    cudaMemcpyAsync(df, f_host, bytes, cudaMemcpyHostToDevice, st);
-    if (!p->zero_initial) cudaMemcpyAsync(dphi, phi_host, bytes, cudaMemcpyHostToDevice, st);
-    if (bc_host) cudaMemcpyAsync(dbc, bc_host, nbc * sizeof(double), cudaMemcpyHostToDevice, st);
-    s = DISPATCH(h, solve_impl, op, *p, dphi, df, dbc, stats, st);
-    if (s == AMR_OK || s == AMR_ERR_NOT_CONVERGED) {
-      cudaMemcpyAsync(phi_host, dphi, bytes, cudaMemcpyDeviceToHost, st);
-      if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("stream sync failed"); s = AMR_ERR_CUDA; }
-    }
+  if (!op->hphi) TRY(dalloc(&op->hphi, h->nelems));
+  if (!op->hf) TRY(dalloc(&op->hf, h->nelems));
+  if (bc_host && !op->hbc) TRY(dalloc(&op->hbc, nbc));
+  CK(cudaMemcpyAsync(op->hf, f_host, bytes, cudaMemcpyHostToDevice, st));
+  if (!p->zero_initial) CK(cudaMemcpyAsync(op->hphi, phi_host, bytes, cudaMemcpyHostToDevice, st));
+  if (bc_host) CK(cudaMemcpyAsync(op->hbc, bc_host, nbc * sizeof(double), cudaMemcpyHostToDevice, st));
+  amr_status s = DISPATCH(h, solve_impl, op, *p, op->hphi, op->hf, bc_host ? op->hbc : nullptr, stats, st);
+  if (s == AMR_OK || s == AMR_ERR_NOT_CONVERGED) {
+    CK(cudaMemcpyAsync(phi_host, op->hphi, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
   }
-  cudaFree(dphi);
-  cudaFree(df);
-  cudaFree(dbc);
   return s;
 }
 
