@@ -36,7 +36,15 @@ struct LevelView {
   long long bc_off[6];       // offsets of this level's faces inside a bc array
   long long bc_pitch[6];     // leading extent of each face array (transverse dim 0)
   double ncells;             // interior cells over all patches (host bookkeeping)
+  // per-level constants precomputed on the host, in both precisions, so that FP32 kernels
+  // execute no FP64 instruction per cell
+  double hd, inv12h2, inv12h;
+  float hf, inv12h2_f, inv12h_f;
+  double dcorr[6][2];        // Jacobi diagonal correction (x 12 h^2) at distance 0 / 1 from face f
+  float dcorr_f[6][2];
 };
+
+void finish_view(LevelView& v);  // fills the precomputed constants from h and bc
 
 // AMRCFI ghost cell: dst = fine field offset; src >= 0: field offset of the window's first
 // coarse cell in coarse patch cpatch; src < 0: -(1+k) with the 5^D offsets at side[k*5^D].

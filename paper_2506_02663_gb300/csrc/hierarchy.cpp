@@ -602,6 +602,30 @@ void free_hierarchy(amr_hierarchy* h) {
   if (h->h_scalar) cudaFreeHost(h->h_scalar);
 }
 
+// Eqs. (velBCHomoDiri5th), (Neumann5): coefficient of interior cell m in ghost layer 1 / 2
+static const double GC[2][2][4] = {{{-77.0 / 12.0, 43.0 / 12.0, -17.0 / 12.0, 3.0 / 12.0},
+                                    {-505.0 / 12.0, 335.0 / 12.0, -145.0 / 12.0, 27.0 / 12.0}},
+                                   {{5.0 / 10.0, 9.0 / 10.0, -5.0 / 10.0, 1.0 / 10.0},
+                                    {-75.0 / 10.0, 145.0 / 10.0, -75.0 / 10.0, 15.0 / 10.0}}};
+
+void finish_view(LevelView& v) {
+  v.hd = v.h;
+  v.hf = (float)v.h;
+  v.inv12h2 = 1.0 / (12.0 * v.h * v.h);
+  v.inv12h = 1.0 / (12.0 * v.h);
+  v.inv12h2_f = (float)v.inv12h2;
+  v.inv12h_f = (float)v.inv12h;
+  for (int f = 0; f < 6; ++f) {
+    const int t = v.bc[f] == 1 ? 1 : 0;
+    // the cell owning the face reads ghost 1 with weight 16 and ghost 2 with weight -1; the
+    // next cell reads ghost 1 with weight -1 (Eq. discreteOps c)
+    v.dcorr[f][0] = 16.0 * GC[t][0][0] - GC[t][1][0];
+    v.dcorr[f][1] = -GC[t][0][1];
+    v.dcorr_f[f][0] = (float)v.dcorr[f][0];
+    v.dcorr_f[f][1] = (float)v.dcorr[f][1];
+  }
+}
+
 LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types) {
   LevelView v{};
   const LevelHost& L = h->lev[l];
@@ -621,6 +645,7 @@ LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types) {
       if (e != d) { lead = e; break; }
     v.bc_pitch[f] = (f < 2 * h->D && lead >= 0) ? L.ndom[lead] : 1;
   }
+  finish_view(v);
   return v;
 }
 

@@ -19,8 +19,33 @@ __constant__ double c_ghost[2][2][4] = {
      {-75.0 / 10.0, 145.0 / 10.0, -75.0 / 10.0, 15.0 / 10.0}}};
 // data coefficient: Dirichlet b (x face value), Neumann b (x h x outward derivative)
 __constant__ double c_ghost_b[2][2] = {{5.0, 75.0 / 3.0}, {6.0 / 5.0, 6.0}};
+__constant__ float c_ghost_f[2][2][4] = {
+    {{-77.0f / 12.0f, 43.0f / 12.0f, -17.0f / 12.0f, 3.0f / 12.0f},
+     {-505.0f / 12.0f, 335.0f / 12.0f, -145.0f / 12.0f, 27.0f / 12.0f}},
+    {{5.0f / 10.0f, 9.0f / 10.0f, -5.0f / 10.0f, 1.0f / 10.0f},
+     {-75.0f / 10.0f, 145.0f / 10.0f, -75.0f / 10.0f, 15.0f / 10.0f}}};
+__constant__ float c_ghost_b_f[2][2] = {{5.0f, 75.0f / 3.0f}, {6.0f / 5.0f, 6.0f}};
 // AMRCFI 1-D weights [pos][sub][a] for ratio r (r <= 4), set by the host
 __constant__ double c_cfi[5 * 4 * 5];
+__constant__ float c_cfi_f[5 * 4 * 5];
+
+// Select the double or float copy of a precomputed constant (FP32 kernels never touch the
+// FP64 pipe per cell; GB300's FP64 rate is a small fraction of its FP32 rate).
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+template <typename T>
+__device__ __forceinline__ T gcoef(int type, int layer, int m) {
+  return pick<T>(c_ghost[type][layer][m], c_ghost_f[type][layer][m]);
+}
+template <typename T>
+__device__ __forceinline__ T cfiw(int i) {
+  return pick<T>(c_cfi[i], c_cfi_f[i]);
+}
 
 constexpr int BX = 32;
 constexpr int BY = 8;
@@ -58,7 +83,7 @@ __device__ T phys_ghost(const T* __restrict__ x, const PatchDesc& p, const Level
   for (int m = 0; m < 4; ++m) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[d] = side == 0 ? (m - p.lo[d]) : (lv.ndom[d] - 1 - m - p.lo[d]);
-    v += T(c_ghost[type][layer - 1][m]) * x[poff(p, cc[0], cc[1], cc[2])];
+    v += gcoef<T>(type, layer - 1, m) * x[poff(p, cc[0], cc[1], cc[2])];
   }
   if (bc != nullptr) {
     // transverse index over the domain face, lowest remaining dimension fastest
@@ -69,7 +94,8 @@ __device__ T phys_ghost(const T* __restrict__ x, const PatchDesc& p, const Level
       s *= lv.ndom[e];
     }
     const T gv = bc[lv.bc_off[f] + t];
-    const T b = T(c_ghost_b[type][layer - 1]) * (type == 1 ? T(lv.h) : T(1));
+    const T b = pick<T>(c_ghost_b[type][layer - 1], c_ghost_b_f[type][layer - 1]) *
+                (type == 1 ? pick<T>(lv.hd, lv.hf) : T(1));
     v += b * gv;
   }
   return v;
@@ -92,12 +118,12 @@ template <typename T, int D>
 __device__ T read_ext(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int ci, int cj, int ck) {
   const int c[3] = {ci, cj, ck};
   int idx[3][4];
-  double w[3][4];
+  T w[3][4];
   int cnt[3] = {1, 1, 1};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     idx[e][0] = c[e];
-    w[e][0] = 1.0;
+    w[e][0] = T(1);
     if (e >= D) continue;
     const int g = p.lo[e] + c[e];
     if (g < 0 || g >= lv.ndom[e]) {
@@ -107,7 +133,7 @@ __device__ T read_ext(const T* __restrict__ x, const PatchDesc& p, const LevelVi
       cnt[e] = 4;
       for (int m = 0; m < 4; ++m) {
         idx[e][m] = side == 0 ? (m - p.lo[e]) : (lv.ndom[e] - 1 - m - p.lo[e]);
-        w[e][m] = c_ghost[type][layer - 1][m];
+        w[e][m] = gcoef<T>(type, layer - 1, m);
       }
     }
   }
@@ -115,18 +141,24 @@ __device__ T read_ext(const T* __restrict__ x, const PatchDesc& p, const LevelVi
   for (int a = 0; a < cnt[0]; ++a)
     for (int b = 0; b < cnt[1]; ++b)
       for (int q = 0; q < cnt[2]; ++q)
-        v += T(w[0][a] * w[1][b] * w[2][q]) * x[poff(p, idx[0][a], idx[1][b], idx[2][q])];
+        v += w[0][a] * w[1][b] * w[2][q] * x[poff(p, idx[0][a], idx[1][b], idx[2][q])];
   return v;
 }
 
-// 1-D contribution to the true Jacobi diagonal (x 12 h^2): -30, plus the ghost-cell
-// coefficients that fall back on the cell itself near a physical face.
-__device__ __forceinline__ double diag_1d(int g, int ndom, int blo, int bhi) {
-  double a = -30.0;
-  if (g == 0) a += 16.0 * c_ghost[blo][0][0] - c_ghost[blo][1][0];
-  else if (g == 1) a += -c_ghost[blo][0][1];
-  if (g == ndom - 1) a += 16.0 * c_ghost[bhi][0][0] - c_ghost[bhi][1][0];
-  else if (g == ndom - 2) a += -c_ghost[bhi][0][1];
+// True Jacobi diagonal (x 12 h^2): -30 per dimension, plus the ghost-cell coefficients
+// that fall back on the cell itself within two cells of a physical face (precomputed per
+// face in LevelView::dcorr).
+template <typename T, int D>
+__device__ __forceinline__ T diag_sum(const LevelView& lv, const PatchDesc& p, const int c[3]) {
+  T a = T(-30 * D);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int g = p.lo[d] + c[d];
+    if (g == 0) a += pick<T>(lv.dcorr[2 * d][0], lv.dcorr_f[2 * d][0]);
+    else if (g == 1) a += pick<T>(lv.dcorr[2 * d][1], lv.dcorr_f[2 * d][1]);
+    if (g == lv.ndom[d] - 1) a += pick<T>(lv.dcorr[2 * d + 1][0], lv.dcorr_f[2 * d + 1][0]);
+    else if (g == lv.ndom[d] - 2) a += pick<T>(lv.dcorr[2 * d + 1][1], lv.dcorr_f[2 * d + 1][1]);
+  }
   return a;
 }
 
@@ -147,12 +179,10 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
   if (vmask != nullptr && vmask[o] == 0) return;
-  const T inv = T(1.0 / (12.0 * lv.h * lv.h));
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   if (MODE == OP_JACOBI0) {
-    double dg = 0.0;
     const int c[3] = {i, j, k};
-    for (int d = 0; d < D; ++d) dg += diag_1d(p.lo[d] + c[d], lv.ndom[d], lv.bc[2 * d], lv.bc[2 * d + 1]);
-    const T diag = alpha + beta * inv * T(dg);
+    const T diag = alpha + beta * inv * diag_sum<T, D>(lv, p, c);
     out[o] = omega * f[o] / diag;
     return;
   }
@@ -185,9 +215,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
   } else if (MODE == OP_RESID) {
     out[o] = f[o] - ax;
   } else {
-    double dg = 0.0;
-    for (int d = 0; d < D; ++d) dg += diag_1d(p.lo[d] + c[d], lv.ndom[d], lv.bc[2 * d], lv.bc[2 * d + 1]);
-    const T diag = alpha + beta * inv * T(dg);
+    const T diag = alpha + beta * inv * diag_sum<T, D>(lv, p, c);
     out[o] = xc + omega * (f[o] - ax) / diag;
   }
 }
@@ -201,7 +229,7 @@ __global__ void k_gradient(LevelView lv, int nby, const T* __restrict__ x, T* __
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
-  const T inv = T(1.0 / (12.0 * lv.h));
+  const T inv = pick<T>(lv.inv12h, lv.inv12h_f);
   T* outs[3] = {g0, g1, g2};
   const int c[3] = {i, j, k};
 #pragma unroll
@@ -229,7 +257,7 @@ __global__ void k_divergence(LevelView lv, int nby, Ptr3 u, double* __restrict__
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
-  const double inv = 1.0 / (12.0 * lv.h);
+  const double inv = lv.inv12h;
   const int c[3] = {i, j, k};
   double acc = 0.0;
 #pragma unroll
@@ -257,18 +285,18 @@ __global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long
     xf[e.dst] = T(0);
     return;
   }
-  const double* w0 = &c_cfi[(e.pos[0] * r + e.sub[0]) * CFI_W];
-  const double* w1 = &c_cfi[(e.pos[1] * r + e.sub[1]) * CFI_W];
-  const double* w2 = &c_cfi[(e.pos[2] * r + e.sub[2]) * CFI_W];
+  const int b0 = (e.pos[0] * r + e.sub[0]) * CFI_W;
+  const int b1 = (e.pos[1] * r + e.sub[1]) * CFI_W;
+  const int b2 = (e.pos[2] * r + e.sub[2]) * CFI_W;
   T v = T(0);
   if (e.src >= 0) {
     const PatchDesc cp = cpatches[e.cpatch];
     for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
       for (int c1 = 0; c1 < CFI_W; ++c1) {
         const long long row = e.src + (long long)c1 * cp.sy + (long long)c2 * cp.sz;
-        const double wr = w1[c1] * (D == 3 ? w2[c2] : 1.0);
+        const T wr = cfiw<T>(b1 + c1) * (D == 3 ? cfiw<T>(b2 + c2) : T(1));
 #pragma unroll
-        for (int c0 = 0; c0 < CFI_W; ++c0) v += T(w0[c0] * wr) * xc[row + c0];
+        for (int c0 = 0; c0 < CFI_W; ++c0) v += cfiw<T>(b0 + c0) * wr * xc[row + c0];
       }
   } else {
     const long long* s = side + (-1 - e.src) * (D == 3 ? 125 : 25);
@@ -276,7 +304,7 @@ __global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long
     for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
       for (int c1 = 0; c1 < CFI_W; ++c1)
         for (int c0 = 0; c0 < CFI_W; ++c0, ++q)
-          v += T(w0[c0] * w1[c1] * (D == 3 ? w2[c2] : 1.0)) * xc[s[q]];
+          v += cfiw<T>(b0 + c0) * cfiw<T>(b1 + c1) * (D == 3 ? cfiw<T>(b2 + c2) : T(1)) * xc[s[q]];
   }
   xf[e.dst] = v;
 }
@@ -307,7 +335,7 @@ __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __res
   const PatchDesc cp = crs.patches[b.cpatch];
   const PatchDesc fp = fine.patches[b.fpatch];
   T acc = T(0);
-  const T inv = T(1.0 / (12.0 * fine.h * fine.h));
+  const T inv = pick<T>(fine.inv12h2, fine.inv12h2_f);
   for (int q2 = 0; q2 < (D == 3 ? 2 : 1); ++q2)
     for (int q1 = 0; q1 < 2; ++q1)
       for (int q0 = 0; q0 < 2; ++q0) {
@@ -374,11 +402,11 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
       for (int q0 = 0; q0 < 2; ++q0) {
         const int q[3] = {q0, q1, q2};
         int cc[3];
-        double w = 1.0;
+        T w = T(1);
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
           cc[e] = par[e] + q[e] * sg[e] - cp.lo[e];
-          if (e < D) w *= (q[e] == 0) ? 0.75 : 0.25;
+          if (e < D) w *= (q[e] == 0) ? T(0.75) : T(0.25);
         }
         bool inside = true;
 #pragma unroll
@@ -387,7 +415,7 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
           inside = inside && g >= 0 && g < crs.ndom[e];
         }
         const T cv = inside ? xc[poff(cp, cc[0], cc[1], cc[2])] : read_ext<T, D>(xc, cp, crs, cc[0], cc[1], cc[2]);
-        v += T(w) * cv;
+        v += w * cv;
       }
   const long long o = poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]);
   xf[o] += v;

@@ -50,6 +50,24 @@ struct amr_operator {
   double* hphi = nullptr;  // device staging for the host-buffer solve (allocated once)
   double* hf = nullptr;
   double* hbc = nullptr;
+  // captured solve (use_graph): one graph = prologue + device-side while loop over V-cycles
+  struct DevStats* d_stats = nullptr;
+  struct DevStats* h_stats = nullptr;  // pinned
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* g_phi = nullptr;
+  const void* g_bc = nullptr;
+  int g_prec = -1, g_nu1 = -1, g_nu2 = -1, g_maxv = -1;
+  double g_omega = 0.0, g_rtol = -1.0, g_atol = -1.0;
+  long long launches_pre = 0, launches_body = 0;
+  int g_straight = 0;
+};
+
+struct DevStats {
+  int iter;    // V-cycles performed
+  int status;  // 0 converged, 1 max_vcycles reached, 2 non-finite residual, 3 running
+  double hist[64];
 };
 
 namespace {
@@ -146,6 +164,7 @@ LevelView mg_view(const amr_hierarchy* h, int m, const int* bc) {
   for (int e = 0; e < 3; ++e) { v.ndom[e] = g.n[e]; v.maxn[e] = g.n[e]; }
   for (int f = 0; f < 6; ++f) { v.bc[f] = bc[f]; v.bc_off[f] = 0; v.bc_pitch[f] = 1; }
   v.ncells = (double)g.n[0] * g.n[1] * g.n[2];
+  finish_view(v);
   return v;
 }
 
@@ -359,9 +378,9 @@ __global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __
   if (t >= n) return;
   const RefluxEntry e = list[t];
   const PatchDesc cp = crs.patches[e.cpatch];
-  const double fd[4] = {1.0 / 12.0, -15.0 / 12.0, 15.0 / 12.0, -1.0 / 12.0};
-  const double fv[4] = {-1.0 / 12.0, 7.0 / 12.0, 7.0 / 12.0, -1.0 / 12.0};
-  const double* fc = kind == 0 ? fd : fv;
+  const T fd[4] = {T(1.0 / 12.0), T(-15.0 / 12.0), T(15.0 / 12.0), T(-1.0 / 12.0)};
+  const T fv[4] = {T(-1.0 / 12.0), T(7.0 / 12.0), T(7.0 / 12.0), T(-1.0 / 12.0)};
+  const T* fc = kind == 0 ? fd : fv;
   T corr = T(0);
   for (int d = 0; d < D; ++d)
     for (int side = 0; side < 2; ++side) {
@@ -376,7 +395,7 @@ __global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __
       for (int q = 0; q < 4; ++q) {
         int cc[3] = {own[0], own[1], own[2]};
         cc[d] += q - 1;
-        Fc += T(fc[q]) * read_nb<T, D>(xc, cp, crs, bcs.p[comp], cc[0], cc[1], cc[2], d);
+        Fc += fc[q] * read_nb<T, D>(xc, cp, crs, bcs.p[comp], cc[0], cc[1], cc[2], d);
       }
       const PatchDesc fp = fine.patches[e.fpatch[2 * d + side]];
       T Fs = T(0);
@@ -393,15 +412,15 @@ __global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __
           for (int q = 0; q < 4; ++q) {
             int cc[3] = {cf[0], cf[1], cf[2]};
             cc[d] += q - 1;
-            Fs += T(fc[q]) * xf[poff(fp, cc[0], cc[1], cc[2])];
+            Fs += fc[q] * xf[poff(fp, cc[0], cc[1], cc[2])];
           }
         }
       const T Fbar = Fs * T(D == 3 ? 0.25 : 0.5);
-      const T hc = kind == 0 ? T(crs.h) : T(1);
-      const T hf = kind == 0 ? T(fine.h) : T(1);
+      const T hc = kind == 0 ? pick<T>(crs.hd, crs.hf) : T(1);
+      const T hf = kind == 0 ? pick<T>(fine.hd, fine.hf) : T(1);
       corr += T(side == 1 ? 1 : -1) * (Fbar / hf - Fc / hc);
     }
-  out[e.coff] += coef * corr / T(crs.h);
+  out[e.coff] += coef * corr / pick<T>(crs.hd, crs.hf);
 }
 
 // ---------------------------------------------------------------- scratch management
@@ -724,10 +743,50 @@ amr_status mean_zero_impl(amr_hierarchy* h, double* x, double* mean_host, cudaSt
   return AMR_OK;
 }
 
+// max-norm over valid cells into *out (IEEE bits, atomicMax); no host readback
+template <typename T, int D>
+amr_status maxnorm_dev(amr_hierarchy* h, const T* x, unsigned long long* out, cudaStream_t st) {
+  CK(cudaMemsetAsync(out, 0, sizeof(unsigned long long), st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    k_maxnorm<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, h->d_valid, out);
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+// Stopping test of Sec. 7 on the device: records the residual norm, decides whether the
+// while-loop of the captured solve runs another V-cycle.
+__global__ void k_check(cudaGraphConditionalHandle handle, int use_cond, const unsigned long long* __restrict__ rbits,
+                        const unsigned long long* __restrict__ fbits, double rtol, double atol, int maxv,
+                        DevStats* __restrict__ s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r = __longlong_as_double((long long)*rbits);
+  const double fn = __longlong_as_double((long long)*fbits);
+  const int it = s->iter;
+  if (it < 64) s->hist[it] = r;
+  const double tol = fmax(rtol * fn, atol);
+  unsigned int cont = 0;
+  if (!isfinite(r)) s->status = 2;
+  else if (r <= tol) s->status = 0;
+  else if (it >= maxv) s->status = 1;
+  else {
+    cont = 1;
+    s->iter = it + 1;
+  }
+  if (use_cond) cudaGraphSetConditional(handle, cont);
+}
+
 // ---------------------------------------------------------------- solve
+template <int D>
+amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
+                       amr_solve_stats* stats, cudaStream_t st);
+
 template <int D>
 amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
                       amr_solve_stats* stats, cudaStream_t st) {
+  if (p.use_graph) return solve_graph<D>(op, p, phi, f, bc, stats, st);
   amr_hierarchy* h = op->h;
   const size_t bytes = (size_t)h->nelems * sizeof(double);
   amr_solve_stats loc{};
@@ -768,6 +827,183 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
   else TRY(avgdown_all<D>(h, phi, st));
   if (stats) *stats = loc;
   return result;
+}
+
+// One V-cycle iteration of the solve loop (V-cycle on op->Res, phi += correction, new
+// residual and its norm), all stream-ordered on st; used inside the captured while-body.
+template <int D>
+amr_status iteration_body(amr_operator* op, int prec, const amr_solver_params& p, double* phi, const double* bc,
+                          cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  if (prec == AMR_MIXED) {
+    Scratch<float>& Sf = op->s32;
+    for (int l = 0; l < h->L; ++l) TRY(convert<double, float, D>(level_view(h, l, nullptr), op->Res, Sf.rin, st));
+    TRY(vcycle_corr<float, D>(op, p, Sf.rin, st));
+    for (int l = 0; l < h->L; ++l) TRY(axpy<float, double, D>(level_view(h, l, nullptr), Sf.X, phi, (double*)nullptr, 1.0, st));
+  } else {
+    Scratch<double>& Sd = op->s64;
+    TRY(vcycle_corr<double, D>(op, p, op->Res, st));
+    for (int l = 0; l < h->L; ++l) TRY(axpy<double, double, D>(level_view(h, l, nullptr), Sd.X, phi, (double*)nullptr, 1.0, st));
+  }
+  TRY(composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, st));
+  TRY(maxnorm_dev<double, D>(h, op->Res, reinterpret_cast<unsigned long long*>(h->d_scalar), st));
+  return AMR_OK;
+}
+
+template <int D>
+amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* bc) {
+  amr_hierarchy* h = op->h;
+  if (op->exec) { cudaGraphExecDestroy(op->exec); op->exec = nullptr; }
+  if (op->graph) { cudaGraphDestroy(op->graph); op->graph = nullptr; }
+  if (!op->cap_stream) CK(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
+  if (!op->body_stream) CK(cudaStreamCreateWithFlags(&op->body_stream, cudaStreamNonBlocking));
+  const bool prof = g_prof.on;
+  cudaStream_t cs = op->cap_stream, bs = op->body_stream;
+  unsigned long long* rb0 = reinterpret_cast<unsigned long long*>(h->d_scalar);
+  unsigned long long* fb0 = reinterpret_cast<unsigned long long*>(h->d_scalar + 5);
+  if (prof) {
+    // instrumented variant: a straight-line graph of exactly max_vcycles iterations with
+    // event-record nodes around the instrumented kernels (events are not allowed inside
+    // conditional bodies)
+    amr_status r = AMR_OK;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = g_launches.load();
+    cudaMemsetAsync(op->d_stats, 0, sizeof(DevStats), cs);
+    r = composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, cs);
+    if (r == AMR_OK) r = maxnorm_dev<double, D>(h, op->Res, rb0, cs);
+    if (r == AMR_OK) {
+      k_check<<<1, 1, 0, cs>>>(cudaGraphConditionalHandle{}, 0, rb0, fb0, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+      r = launch_check();
+    }
+    for (int it = 0; r == AMR_OK && it < p.max_vcycles; ++it) {
+      r = iteration_body<D>(op, p.precision, p, phi, bc, cs);
+      if (r == AMR_OK) {
+        k_check<<<1, 1, 0, cs>>>(cudaGraphConditionalHandle{}, 0, rb0, fb0, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+        r = launch_check();
+      }
+    }
+    op->launches_pre = g_launches.load() - l0;
+    op->launches_body = 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    g_launches.store(l0);
+    if (r != AMR_OK) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return r; }
+    if (e != cudaSuccess) { set_error(std::string("capture: ") + cudaGetErrorString(e)); return AMR_ERR_CUDA; }
+    op->graph = g;
+    CK(cudaGraphInstantiate(&op->exec, g, 0));
+    op->g_phi = phi; op->g_bc = bc; op->g_prec = p.precision; op->g_nu1 = p.nu1; op->g_nu2 = p.nu2;
+    op->g_maxv = p.max_vcycles; op->g_omega = p.omega; op->g_rtol = p.rtol; op->g_atol = p.atol;
+    op->g_straight = 1;
+    return AMR_OK;
+  }
+  unsigned long long* rbits = reinterpret_cast<unsigned long long*>(h->d_scalar);
+  unsigned long long* fbits = reinterpret_cast<unsigned long long*>(h->d_scalar + 5);
+  amr_status result = AMR_OK;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const long long l0 = g_launches.load();
+  do {
+    cudaMemsetAsync(op->d_stats, 0, sizeof(DevStats), cs);
+    if ((result = composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, cs)) != AMR_OK) break;
+    if ((result = maxnorm_dev<double, D>(h, op->Res, rbits, cs)) != AMR_OK) break;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, cg, 0, 0) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    k_check<<<1, 1, 0, cs>>>(handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+    if ((result = launch_check()) != AMR_OK) break;
+    op->launches_pre = g_launches.load() - l0;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &edata, &ndeps) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, cg, deps, edata, ndeps, &cp) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      result = AMR_ERR_CUDA;
+      break;
+    }
+    const long long l1 = g_launches.load();
+    amr_status rb = iteration_body<D>(op, p.precision, p, phi, bc, bs);
+    if (rb == AMR_OK) {
+      k_check<<<1, 1, 0, bs>>>(handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+      rb = launch_check();
+    }
+    op->launches_body = g_launches.load() - l1;
+    cudaGraph_t bout = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(bs, &bout);
+    if (rb != AMR_OK) { result = rb; break; }
+    if (e1 != cudaSuccess) { set_error(std::string("body capture: ") + cudaGetErrorString(e1)); result = AMR_ERR_CUDA; break; }
+    if (cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) {
+      result = AMR_ERR_CUDA;
+      break;
+    }
+  } while (false);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  g_launches.store(l0);  // captured launches are counted when the graph runs
+  if (result != AMR_OK) {
+    if (g) cudaGraphDestroy(g);
+    if (std::string(get_error()).empty()) set_error("graph capture failed");
+    cudaGetLastError();
+    return result;
+  }
+  if (e2 != cudaSuccess) { set_error(std::string("capture: ") + cudaGetErrorString(e2)); return AMR_ERR_CUDA; }
+  op->graph = g;
+  CK(cudaGraphInstantiate(&op->exec, g, 0));
+  op->g_phi = phi; op->g_bc = bc; op->g_prec = p.precision; op->g_nu1 = p.nu1; op->g_nu2 = p.nu2;
+  op->g_maxv = p.max_vcycles; op->g_omega = p.omega; op->g_rtol = p.rtol; op->g_atol = p.atol;
+  op->g_straight = 0;
+  return AMR_OK;
+}
+
+template <int D>
+amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
+                       amr_solve_stats* stats, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  const size_t bytes = (size_t)h->nelems * sizeof(double);
+  if (!op->d_stats) {
+    TRY(dalloc(&op->d_stats, 1));
+    CK(cudaMallocHost(&op->h_stats, sizeof(DevStats)));
+  }
+  if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  else TRY(ensure_scratch<double>(op));
+  // set-up outside the graph: internal RHS copy, solvability fix, ||f||
+  CK(cudaMemcpyAsync(op->F, f, bytes, cudaMemcpyDeviceToDevice, st));
+  if (op->neumann) TRY(solvability_fix_impl<D>(op, op->F, bc, nullptr, st));
+  if (p.zero_initial) CK(cudaMemsetAsync(phi, 0, bytes, st));
+  TRY(avgdown_all<D>(h, op->F, st));
+  TRY(maxnorm_dev<double, D>(h, op->F, reinterpret_cast<unsigned long long*>(h->d_scalar + 5), st));
+  const bool hit = op->exec && op->g_phi == phi && op->g_bc == bc && op->g_prec == p.precision &&
+                   op->g_nu1 == p.nu1 && op->g_nu2 == p.nu2 && op->g_maxv == p.max_vcycles &&
+                   op->g_omega == p.omega && op->g_rtol == p.rtol && op->g_atol == p.atol &&
+                   op->g_straight == (g_prof.on ? 1 : 0);
+  if (!hit) TRY(build_solve_graph<D>(op, p, phi, bc));
+  CK(cudaGraphLaunch(op->exec, st));
+  if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
+  else TRY(avgdown_all<D>(h, phi, st));
+  CK(cudaMemcpyAsync(op->h_stats, op->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const DevStats& ds = *op->h_stats;
+  g_launches.fetch_add(op->launches_pre + (long long)ds.iter * op->launches_body);
+  amr_solve_stats loc{};
+  loc.vcycles = ds.iter;
+  for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
+  loc.final_res = ds.hist[std::min(ds.iter, 63)];
+  loc.rhs_norm = h->h_scalar[5];
+  loc.removed_mean = op->neumann ? h->h_scalar[4] : 0.0;
+  if (stats) *stats = loc;
+  if (ds.status == 0) return AMR_OK;
+  if (ds.status == 2) { set_error("residual is not finite"); return AMR_ERR_NONFINITE; }
+  set_error("max_vcycles reached");
+  return AMR_ERR_NOT_CONVERGED;
 }
 
 template <int D>
@@ -884,9 +1120,10 @@ const char* amr_last_error(void) { return get_error(); }
 long long amr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 amr_status amr_profile_enable(int on) {
-  for (auto& r : g_prof.recs) (void)r;
-  g_prof.recs.clear();
-  g_prof.used = 0;
+  if (on) {
+    g_prof.recs.clear();
+    g_prof.used = 0;
+  }
   g_prof.on = on != 0;
   return AMR_OK;
 }
@@ -1010,6 +1247,10 @@ amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, cons
   op->neumann = alln && alpha == 0.0;
   // AMRCFI weights for ratio 2
   CK(cudaMemcpyToSymbol(c_cfi, h->cfi_w.data(), h->cfi_w.size() * sizeof(double)));
+  {
+    std::vector<float> wf(h->cfi_w.begin(), h->cfi_w.end());
+    CK(cudaMemcpyToSymbol(c_cfi_f, wf.data(), wf.size() * sizeof(float)));
+  }
   // dense bottom inverse on the coarsest level-0 multigrid grid
   const MgGrid& g = h->mg.back();
   const int n = g.n[0] * g.n[1] * g.n[2];
@@ -1064,6 +1305,12 @@ void amr_operator_destroy(amr_operator* op) {
   cudaFree(op->hphi);
   cudaFree(op->hf);
   cudaFree(op->hbc);
+  if (op->exec) cudaGraphExecDestroy(op->exec);
+  if (op->graph) cudaGraphDestroy(op->graph);
+  if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
+  if (op->body_stream) cudaStreamDestroy(op->body_stream);
+  cudaFree(op->d_stats);
+  if (op->h_stats) cudaFreeHost(op->h_stats);
   delete op;
 }
 

@@ -338,3 +338,38 @@ def test_full_size_bumps2d_residual_property(precision):
             assert abs(m - st["removed_mean"]) <= 1e-14 * max(abs(m), 1e-300) + 1e-300
         R = cp.residual(H, phi, F, alpha, beta)
         assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F), (max_abs(H, R), st)
+
+
+@pytest.mark.parametrize("name,bcw,ab", [("two_level_ragged", 1, (0.0, 1.0)), ("three_level_multibox", 0, (1.0, -0.01)),
+                                         ("three_d", 1, (0.0, 1.0))])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_solve_matches_host_loop(name, bcw, ab, precision):
+    """The captured solve (one CUDA graph with a device-side while loop over V-cycles)
+    performs the same V-cycles as the host-driven loop: same count, same residual history
+    to rounding, same solution; relaunching the cached graph reproduces it."""
+    amr = _amr()
+    dim = HIERS[name][0]
+    bc = [bcw] * (2 * dim)
+    H, gh = _hier(name, bc)
+    alpha, beta = ab
+    rng = np.random.default_rng(29)
+    F = _rand_field(H, rng)
+    op = amr.Operator(gh, alpha, beta, bc)
+    f = _dev(to_packed(gh, H, F))
+    p0 = amr.default_params(rtol=1e-11, max_vcycles=100, precision=precision)
+    p1 = amr.default_params(rtol=1e-11, max_vcycles=100, precision=precision, use_graph=1)
+    a = torch.zeros_like(f)
+    s0 = op.solve(a, f, params=p0)
+    for _ in range(2):
+        b = torch.zeros_like(f)
+        s1 = op.solve(b, f, params=p1)
+        assert s1["vcycles"] == s0["vcycles"], (s0, s1)
+        for x, y in zip(s0["res_history"], s1["res_history"]):
+            assert abs(x - y) <= 1e-6 * abs(x) + 1e-300
+        ga = from_packed(gh, H, a.cpu().numpy())
+        gb = from_packed(gh, H, b.cpu().numpy())
+        assert max_diff(H, ga, gb) <= 1e-12 * max_abs(H, ga)
+    # the iteration cap is reported the same way through the graph
+    s2 = op.solve(torch.zeros_like(f), f, params=amr.default_params(rtol=1e-15, max_vcycles=2, use_graph=1,
+                                                                   precision=precision), allow_not_converged=True)
+    assert s2["status"] == amr.AMR_ERR_NOT_CONVERGED and s2["vcycles"] == 2
