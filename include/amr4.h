@@ -224,6 +224,28 @@ amr_status amr_solvability_fix(amr_operator* op, double* f, const double* bc, do
 /* phi -= (h^D-weighted mean over valid cells), compensated sums; *mean (nullable). */
 amr_status amr_mean_zero(amr_hierarchy* h, double* phi, double* mean, void* stream);
 
+/* Allocation-free variant of amr_mean_zero.  The paper has no counterpart: this exists for
+ * callers that must not allocate device memory at the point of the call -- code running
+ * while device memory is fully held by another allocator (a framework's caching pool), or
+ * inside a timing- or latency-critical loop where cudaMalloc's implicit device-wide
+ * synchronisation is not acceptable.  Same result as amr_mean_zero (same kernels, same
+ * fixed-order compensated sums), but its reduction scratch is a fixed file-scope device
+ * array inside the library (8192 block partials plus a few scalars, about 128 KiB per GPU
+ * that loads the library, held until the process exits) instead of hierarchy-owned memory,
+ * and it calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - The hierarchy must already have its device copy (any earlier device call on it, e.g.
+ *     amr_operator_create, makes it); otherwise AMR_ERR_INVALID_ARG.
+ *   - Hierarchies whose reduction needs more than 8192 blocks are rejected with
+ *     AMR_ERR_INVALID_ARG and a message giving the count (nothing is launched).
+ *   - The first call on a device looks up the array's device address with that device
+ *     current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents; each call
+ *     writes every slot it reads before reading it.  Calls that overlap on the GPU (on
+ *     different streams, or from different threads on the same device) race on the array
+ *     and must be serialised by the caller.
+ *   - *mean (host, nullable) receives the removed mean and then the call synchronises. */
+amr_status amr_mean_zero_noalloc(amr_hierarchy* h, double* phi, double* mean, void* stream);
+
 /* G^comp (COH-1,2,4; Eq. discreteOps a): grad[d] = component d.  Ghosts of phi use
  * bc_types (data bc, nullable). */
 amr_status amr_gradient(amr_hierarchy* h, const int* bc_types, double* phi, double* const* grad,

@@ -77,6 +77,7 @@ _sigs = {
     "amr_solve_host": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
     "amr_solvability_fix": [_vp, _vp, _vp, _P(C.c_double), _vp],
     "amr_mean_zero": [_vp, _vp, _P(C.c_double), _vp],
+    "amr_mean_zero_noalloc": [_vp, _vp, _P(C.c_double), _vp],
     "amr_gradient": [_vp, _P(C.c_int), _vp, _P(_vp), _vp, _vp],
     "amr_divergence": [_vp, _P(C.c_int), _P(_vp), _vp, _P(_vp), _vp],
     "amr_project": [_vp, _P(SolverParams), _P(C.c_int), _P(_vp), _P(_vp), _P(_vp), _vp, _P(SolveStats), _vp],
@@ -379,6 +380,14 @@ def _ptr_array(ts):
 def mean_zero(hier, phi, stream=None):
     m = C.c_double()
     _check(_lib.amr_mean_zero(hier.handle, _ptr(phi), C.byref(m), _stream(stream)), "amr_mean_zero")
+    return m.value
+
+
+def mean_zero_noalloc(hier, phi, stream=None):
+    """amr_mean_zero_noalloc: the same result as mean_zero for callers that must not allocate
+    device memory during the call (scratch is a fixed array inside the library)."""
+    m = C.c_double()
+    _check(_lib.amr_mean_zero_noalloc(hier.handle, _ptr(phi), C.byref(m), _stream(stream)), "amr_mean_zero_noalloc")
     return m.value
 
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1095,6 +1096,81 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+// =================================================================== allocation-free mean-zero
+// Scratch for amr_mean_zero_noalloc: the block partial sums (one double-double per block) and
+// three scalars live in this file-scope device array instead of hierarchy-owned memory, so
+// the entry point never allocates.  Every GPU that loads the library holds it until exit.
+namespace {
+constexpr long long NOALLOC_MAX_PARTIALS = 8192;  // largest number of reduction blocks
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_PARTIALS + 8];
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device
+// with that device current (the host-side name is only a stand-in for the device symbol).
+amr_status noalloc_scratch(double** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_error("amr_mean_zero_noalloc: device index out of range");
+    return AMR_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error(std::string("amr_mean_zero_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return AMR_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return AMR_OK;
+}
+
+template <int D>
+amr_status mean_zero_noalloc_impl(amr_hierarchy* h, double* x, double* mean_host, cudaStream_t st) {
+  // size check before anything is launched
+  long long nblocks = 0;
+  for (int l = 0; l < h->L; ++l) {
+    Geo g = geo_of(level_view(h, l, nullptr));
+    nblocks += (long long)g.grid.x * g.grid.y * g.grid.z;
+  }
+  if (nblocks > NOALLOC_MAX_PARTIALS) {
+    set_error("amr_mean_zero_noalloc: hierarchy needs " + std::to_string(nblocks) +
+              " reduction blocks, more than the fixed scratch holds (" + std::to_string(NOALLOC_MAX_PARTIALS) + ")");
+    return AMR_ERR_INVALID_ARG;
+  }
+  double* scratch = nullptr;
+  TRY(noalloc_scratch(&scratch));
+  double* part = scratch;
+  double* sums = scratch + 2 * NOALLOC_MAX_PARTIALS;  // [0] weighted sum, [2] mean
+  TRY(avgdown_all<D>(h, x, st));
+  long long base = 0;
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    // every block writes its own partial slot, so no slot needs clearing first
+    k_wsum<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, h->d_valid, std::pow(lv.h, D), part, base);
+    TRY(launch_check());
+    base += (long long)g.grid.x * g.grid.y * g.grid.z;
+  }
+  k_dd_final<<<1, 256, 0, st>>>(part, base, sums);
+  TRY(launch_check());
+  k_mean_from_sums<<<1, 1, 0, st>>>(sums, nullptr, 0.0, valid_volume(h), sums + 2);
+  TRY(launch_check());
+  TRY(shift_all<D>(h, x, sums + 2, false, -1.0, st));
+  if (mean_host) {
+    CK(cudaMemcpyAsync(h->h_scalar + 8, sums + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *mean_host = h->h_scalar[8];
+  }
+  return AMR_OK;
+}
+}  // namespace
+
 // =================================================================== C ABI
 #define DISPATCH(h, fn, ...) ((h)->D == 2 ? fn<2>(__VA_ARGS__) : fn<3>(__VA_ARGS__))
 
@@ -1411,6 +1487,16 @@ amr_status amr_mean_zero(amr_hierarchy* h, double* phi, double* mean, void* stre
   TRY(ensure_device(h));
   TRY(DISPATCH(h, mean_zero_impl, h, phi, mean, S(stream)));
   return AMR_OK;
+}
+
+amr_status amr_mean_zero_noalloc(amr_hierarchy* h, double* phi, double* mean, void* stream) {
+  if (!h || !phi) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  if (!h->on_device) {
+    set_error("amr_mean_zero_noalloc: the hierarchy has no device copy yet (create an operator or call another "
+              "device entry point once beforehand)");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return DISPATCH(h, mean_zero_noalloc_impl, h, phi, mean, S(stream));
 }
 
 amr_status amr_gradient(amr_hierarchy* h, const int* bc_types, double* phi, double* const* grad, const double* bc,
