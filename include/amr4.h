@@ -151,7 +151,10 @@ typedef struct {
   int max_vcycles;   /* hard cap on V-cycles (no unbounded device loop exists)            */
   int precision;     /* AMR_FP64, or AMR_MIXED: FP32 V-cycles inside FP64 refinement      */
   int zero_initial;  /* 1: start from phi = 0; 0: use phi as the initial guess            */
-  int use_graph;     /* 1: replay one captured CUDA graph per V-cycle                     */
+  int use_graph;     /* 1: capture the whole solve as one CUDA graph (device-side loop over
+                        V-cycles, no host round trip per V-cycle) and replay it              */
+  int fuse_coarse;   /* 1: run the coarse end of the level-0 V-cycle in one shared-memory
+                        block (same arithmetic as the per-grid kernels)                      */
 } amr_solver_params;
 
 typedef struct {

@@ -170,25 +170,20 @@ __device__ __forceinline__ T diag_sum(const LevelView& lv, const PatchDesc& p, c
 enum { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
 
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, const T* __restrict__ x,
-                                                     const T* __restrict__ f, T* __restrict__ out,
-                                                     const T* __restrict__ bc, T alpha, T beta, T omega,
-                                                     const unsigned char* __restrict__ vmask) {
-  const PatchDesc p = lv.patches[blockIdx.z];
-  int i, j, k;
-  if (!thread_cell<D>(p, nby, i, j, k)) return;
+__device__ __forceinline__ void cell_level_op(const LevelView& lv, const PatchDesc& p, int i, int j, int k,
+                                              const T* __restrict__ x, const T* __restrict__ f,
+                                              T* __restrict__ out, const T* __restrict__ bc, T alpha, T beta,
+                                              T omega) {
   const long long o = poff(p, i, j, k);
-  if (vmask != nullptr && vmask[o] == 0) return;
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  const int c[3] = {i, j, k};
   if (MODE == OP_JACOBI0) {
-    const int c[3] = {i, j, k};
     const T diag = alpha + beta * inv * diag_sum<T, D>(lv, p, c);
     out[o] = omega * f[o] / diag;
     return;
   }
   const T xc = x[o];
   T acc = T(0);
-  const int c[3] = {i, j, k};
   const long long st[3] = {1, p.sy, p.sz};
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -218,6 +213,18 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
     const T diag = alpha + beta * inv * diag_sum<T, D>(lv, p, c);
     out[o] = xc + omega * (f[o] - ax) / diag;
   }
+}
+
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, const T* __restrict__ x,
+                                                     const T* __restrict__ f, T* __restrict__ out,
+                                                     const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                     const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) return;
+  cell_level_op<T, D, MODE>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
 }
 
 // ------------------------------------------------------------------------ G and D
@@ -318,22 +325,13 @@ __global__ void k_copy(const CopyEntry* __restrict__ list, long long n, T* __res
 }
 
 // ------------------------------------------------------------------------ transfers
-// Coarse cells of a transfer block get the mean of their r^D children (r = 2):
-// of x (average-down, Eq. AMR_avergingDownToCrse / restriction), or of f - A x on the fine
-// level (residual restriction) when RESID.
+// Coarse cell g gets the mean of its r^D children (r = 2): of x (average-down,
+// Eq. AMR_avergingDownToCrse / restriction), or of f - A x on the fine level (residual
+// restriction) when RESID.
 template <typename T, int D, bool RESID>
-__global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
-                           const T* __restrict__ xf, const T* __restrict__ ff, T* __restrict__ outc,
-                           T alpha, T beta, int nby) {
-  const XferBlock b = blocks[blockIdx.z];
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
-  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
-  const int j = by * BY + threadIdx.y;
-  const int g[3] = {b.clo[0] + i, b.clo[1] + j, b.clo[2] + kk};
-  if (g[0] > b.chi[0] || g[1] > b.chi[1] || g[2] > b.chi[2]) return;
-  const PatchDesc cp = crs.patches[b.cpatch];
-  const PatchDesc fp = fine.patches[b.fpatch];
+__device__ __forceinline__ void cell_restrict(const LevelView& fine, const PatchDesc& fp, const PatchDesc& cp,
+                                              const int g[3], const T* __restrict__ xf, const T* __restrict__ ff,
+                                              T* __restrict__ outc, T alpha, T beta) {
   T acc = T(0);
   const T inv = pick<T>(fine.inv12h2, fine.inv12h2_f);
   for (int q2 = 0; q2 < (D == 3 ? 2 : 1); ++q2)
@@ -375,21 +373,27 @@ __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __res
   outc[poff(cp, g[0] - cp.lo[0], g[1] - cp.lo[1], g[2] - cp.lo[2])] = acc * T(D == 3 ? 0.125 : 0.25);
 }
 
-// Fine cells of a transfer block += cell-centred tensor linear interpolation of the coarse
-// correction (Sec. 6.4 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse
-// values outside the domain come from the homogeneous physical extension with corners.
-template <typename T, int D>
-__global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
-                          const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2, int nby) {
+template <typename T, int D, bool RESID>
+__global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                           const T* __restrict__ xf, const T* __restrict__ ff, T* __restrict__ outc,
+                           T alpha, T beta, int nby) {
   const XferBlock b = blocks[blockIdx.z];
-  const int i = blockIdx.x * BX + threadIdx.x;  // fine offsets inside the block region
+  const int i = blockIdx.x * BX + threadIdx.x;
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
   const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
   const int j = by * BY + threadIdx.y;
-  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
-  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
-  const PatchDesc cp = crs.patches[b.cpatch];
-  const PatchDesc fp = fine.patches[b.fpatch];
+  const int g[3] = {b.clo[0] + i, b.clo[1] + j, b.clo[2] + kk};
+  if (g[0] > b.chi[0] || g[1] > b.chi[1] || g[2] > b.chi[2]) return;
+  cell_restrict<T, D, RESID>(fine, fine.patches[b.fpatch], crs.patches[b.cpatch], g, xf, ff, outc, alpha, beta);
+}
+
+// Fine cell gf += cell-centred tensor linear interpolation of the coarse correction
+// (Sec. 6.4 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse values outside
+// the domain come from the homogeneous physical extension with corners.
+template <typename T, int D>
+__device__ __forceinline__ void cell_prolong(const LevelView& crs, const PatchDesc& fp, const PatchDesc& cp,
+                                             const int gf[3], const T* __restrict__ xc, T* __restrict__ xf,
+                                             T* __restrict__ xf2) {
   int par[3], sg[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -420,6 +424,136 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
   const long long o = poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]);
   xf[o] += v;
   if (xf2 != nullptr) xf2[o] += v;
+}
+
+template <typename T, int D>
+__global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                          const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2, int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;  // fine offsets inside the block region
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
+  cell_prolong<T, D>(crs, fine.patches[b.fpatch], crs.patches[b.cpatch], gf, xc, xf, xf2);
+}
+
+// ------------------------------------------------------------------------ fused coarse V-cycle
+// The coarse end of the level-0 multigrid pyramid (every grid from m0 down to the coarsest,
+// whose arrays fit in shared memory together) runs as ONE block: the same per-cell
+// smoothing / residual-restriction / prolongation functions as the standalone kernels, with
+// __syncthreads() between phases, and the dense bottom solve at the end of the descent.
+constexpr int CMG_MAX = 10;
+struct CoarseMG {
+  int ng;                      // grids handled, index 0 = m0, ng-1 = coarsest
+  int nu1, nu2;
+  int nbot, ldb;
+  const double* minv;          // bottom inverse (global)
+  PatchDesc gp;                // global layout of grid m0 (right-hand side in, correction out)
+  LevelView lv[CMG_MAX];       // per-grid constants (patches pointer unused)
+  PatchDesc sp[CMG_MAX];       // shared-memory layout of each grid's arrays (off = 0)
+  int offx[CMG_MAX], offb[CMG_MAX], offt[CMG_MAX];  // element offsets in dynamic shared memory
+};
+
+__device__ __forceinline__ void cell_of(const PatchDesc& p, int t, int& i, int& j, int& k) {
+  i = t % p.n[0];
+  j = (t / p.n[0]) % p.n[1];
+  k = t / (p.n[0] * p.n[1]);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __restrict__ bglob, T* __restrict__ xglob,
+                                                    T alpha, T beta, T omega) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  auto ncell = [&](int m) { return cm.sp[m].n[0] * cm.sp[m].n[1] * cm.sp[m].n[2]; };
+  int i, j, k;
+  for (int t = tid; t < ncell(0); t += nth) {
+    cell_of(cm.sp[0], t, i, j, k);
+    sm[cm.offb[0] + poff(cm.sp[0], i, j, k)] = bglob[poff(cm.gp, i, j, k)];
+  }
+  __syncthreads();
+  for (int m = 0; m + 1 < cm.ng; ++m) {
+    T* x = sm + cm.offx[m];
+    T* tb = sm + cm.offt[m];
+    const T* b = sm + cm.offb[m];
+    T* cur = (cm.nu1 % 2 == 1) ? x : tb;
+    T* oth = (cur == x) ? tb : x;
+    for (int t = tid; t < ncell(m); t += nth) {
+      cell_of(cm.sp[m], t, i, j, k);
+      cell_level_op<T, D, OP_JACOBI0>(cm.lv[m], cm.sp[m], i, j, k, nullptr, b, cur, nullptr, alpha, beta, omega);
+    }
+    __syncthreads();
+    for (int s = 1; s < cm.nu1; ++s) {
+      for (int t = tid; t < ncell(m); t += nth) {
+        cell_of(cm.sp[m], t, i, j, k);
+        cell_level_op<T, D, OP_JACOBI>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
+      }
+      __syncthreads();
+      T* sw = cur;
+      cur = oth;
+      oth = sw;
+    }
+    for (int t = tid; t < ncell(m + 1); t += nth) {
+      cell_of(cm.sp[m + 1], t, i, j, k);
+      const int g[3] = {i, j, k};
+      cell_restrict<T, D, true>(cm.lv[m], cm.sp[m], cm.sp[m + 1], g, x, b, sm + cm.offb[m + 1], alpha, beta);
+    }
+    __syncthreads();
+  }
+  {
+    const int M = cm.ng - 1;
+    const T* b = sm + cm.offb[M];
+    T* x = sm + cm.offx[M];
+    for (int r = tid; r < cm.nbot; r += nth) {
+      double acc = 0.0;
+      const double* row = cm.minv + (long long)r * cm.ldb;
+      for (int q = 0; q < cm.nbot; ++q) {
+        cell_of(cm.sp[M], q, i, j, k);
+        acc = fma(row[q], (double)b[poff(cm.sp[M], i, j, k)], acc);
+      }
+      cell_of(cm.sp[M], r, i, j, k);
+      x[poff(cm.sp[M], i, j, k)] = T(acc);
+    }
+    __syncthreads();
+  }
+  for (int m = cm.ng - 2; m >= 0; --m) {
+    T* x = sm + cm.offx[m];
+    T* tb = sm + cm.offt[m];
+    const T* b = sm + cm.offb[m];
+    for (int t = tid; t < ncell(m); t += nth) {
+      cell_of(cm.sp[m], t, i, j, k);
+      const int gf[3] = {i, j, k};
+      cell_prolong<T, D>(cm.lv[m + 1], cm.sp[m], cm.sp[m + 1], gf, sm + cm.offx[m + 1], x, (T*)nullptr);
+    }
+    __syncthreads();
+    T* cur = x;
+    T* oth = tb;
+    for (int s = 0; s < cm.nu2; ++s) {
+      for (int t = tid; t < ncell(m); t += nth) {
+        cell_of(cm.sp[m], t, i, j, k);
+        cell_level_op<T, D, OP_JACOBI>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
+      }
+      __syncthreads();
+      T* sw = cur;
+      cur = oth;
+      oth = sw;
+    }
+    if (cur != x) {
+      for (int t = tid; t < ncell(m); t += nth) {
+        cell_of(cm.sp[m], t, i, j, k);
+        const long long o = poff(cm.sp[m], i, j, k);
+        x[o] = cur[o];
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = tid; t < ncell(0); t += nth) {
+    cell_of(cm.sp[0], t, i, j, k);
+    xglob[poff(cm.gp, i, j, k)] = sm[cm.offx[0] + poff(cm.sp[0], i, j, k)];
+  }
 }
 
 // ------------------------------------------------------------------------ elementwise
