@@ -47,8 +47,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven V-cycle loop instead of the captured solve")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the large-grid roofline")
-    ap.add_argument("--profile-case", choices=["none", "large"], default="none",
-                    help="run only one mixed-precision solve of the single-level 4096^2 case (for ncu)")
+    ap.add_argument("--profile-case", choices=["none", "large", "bench"], default="none",
+                    help="large: one mixed-precision solve of the single-level 4096^2 case; bench: one warm-up "
+                         "and one timed step of the bench workload and nothing else (both for ncu)")
     return ap.parse_args()
 
 
@@ -412,10 +413,30 @@ def _profile_case():
     return 0
 
 
+def _profile_bench(args):
+    """One warm-up step and one step of the bench workload (graph mode), for launch lists."""
+    import torch
+    from paper_2506_02663_gb300 import amr
+    dim, n0, boxes, rhs, systems = _workload()
+    gh = amr.Hierarchy(dim, n0, boxes)
+    f = torch.from_numpy(gh.pack(rhs)).cuda()
+    ops = [amr.Operator(gh, a, b, bc) for _, bc, a, b in systems]
+    prec = amr.MIXED if args.precision == "mixed" else amr.FP64
+    p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=0 if args.no_graph else 1)
+    for _ in range(2):
+        l0 = amr.kernel_launches()
+        vc = [op.solve(torch.zeros_like(f), f, params=p)["vcycles"] for op in ops]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "bench", "vcycles": vc, "launches": amr.kernel_launches() - l0}))
+    return 0
+
+
 def main():
     args = _args()
     if args.profile_case == "large":
         return _profile_case()
+    if args.profile_case == "bench":
+        return _profile_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -154,7 +154,8 @@ typedef struct {
   int use_graph;     /* 1: capture the whole solve as one CUDA graph (device-side loop over
                         V-cycles, no host round trip per V-cycle) and replay it              */
   int fuse_coarse;   /* 1: run the coarse end of the level-0 V-cycle in one shared-memory
-                        block (same arithmetic as the per-grid kernels)                      */
+                        block (same arithmetic as the per-grid kernels); default 0: on GB300
+                        one block is slower than the graph's per-grid launches              */
 } amr_solver_params;
 
 typedef struct {

@@ -54,7 +54,9 @@ struct CfiEntry {
   int cpatch;
   signed char pos[3];
   signed char sub[3];
-  signed char pad[2];
+  signed char dir;    // dimension along which the ghost lies outside its fine patch
+  signed char layer;  // -L: L cells below the patch's low side, +L: above its high side
+  int fpatch;         // fine patch (index within its level)
 };
 
 struct CopyEntry {

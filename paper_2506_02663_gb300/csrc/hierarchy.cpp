@@ -385,6 +385,9 @@ amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std
                   const LevelHost& C = h->lev[l - 1];
                   CfiEntry ce{};
                   ce.dst = p.off + (long long)ax + (long long)ay * p.sy + (long long)az * p.sz;
+                  ce.dir = (signed char)d;
+                  ce.layer = (signed char)(g[d] < p.lo[d] ? -(p.lo[d] - g[d]) : (g[d] - (p.lo[d] + p.n[d] - 1)));
+                  ce.fpatch = (int)k;
                   int start[3] = {0, 0, 0};
                   for (int e = 0; e < 3; ++e) { ce.pos[e] = 0; ce.sub[e] = 0; }
                   for (int e = 0; e < D; ++e) {

@@ -169,7 +169,67 @@ __device__ __forceinline__ T diag_sum(const LevelView& lv, const PatchDesc& p, c
 // MODE 3: out = omega f / diag                    (first sweep from x = 0)
 enum { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
 
-template <typename T, int D, int MODE>
+// 12 h^2 (L x) at one cell (TR = false), or 12 h^2 (L^T x) with the level operator's
+// transpose (TR = true): the interior stencil is symmetric; outside the domain there is no
+// row, so the transpose reads 0 there and instead gathers the ghost-formula coefficients of
+// Eqs. (velBCHomoDiri5th)/(Neumann5) from the two rows that read the physical ghosts
+// (ghost 1 is read by the face cell with weight 16 and the next cell with weight -1,
+// ghost 2 by the face cell with weight -1).  Zero-CF semantics in both directions: stored
+// CF ghost values are used as they are (zero in smoothing buffers).
+template <typename T, int D, bool TR>
+__device__ __forceinline__ T cell_Lx(const LevelView& lv, const PatchDesc& p, int i, int j, int k,
+                                     const T* __restrict__ x, const T* __restrict__ bc) {
+  const long long o = poff(p, i, j, k);
+  const T xc = x[o];
+  T acc = T(0);
+  const int c[3] = {i, j, k};
+  const long long st[3] = {1, p.sy, p.sz};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int g = p.lo[d] + c[d];
+    T m1, p1, m2, p2;
+    if (g >= 2 && g <= lv.ndom[d] - 3) {
+      m1 = x[o - st[d]];
+      p1 = x[o + st[d]];
+      m2 = x[o - 2 * st[d]];
+      p2 = x[o + 2 * st[d]];
+    } else if (!TR) {
+      int cc[3] = {i, j, k};
+      cc[d] = c[d] - 1; m1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] + 1; p1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] - 2; m2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+      cc[d] = c[d] + 2; p2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
+    } else {
+      m1 = (g - 1 >= 0) ? x[o - st[d]] : T(0);
+      m2 = (g - 2 >= 0) ? x[o - 2 * st[d]] : T(0);
+      p1 = (g + 1 < lv.ndom[d]) ? x[o + st[d]] : T(0);
+      p2 = (g + 2 < lv.ndom[d]) ? x[o + 2 * st[d]] : T(0);
+    }
+    acc += T(16) * (m1 + p1) - (m2 + p2);
+    if (TR) {
+      // low face: this cell is interior cell m = g of the rows' ghost formulas
+      if (g <= 3 && p.lo[d] == 0) {
+        const int t = lv.bc[2 * d];
+        const long long o0 = o - (long long)c[d] * st[d];  // local index 0 along d
+        const T w1 = T(16) * x[o0] - x[o0 + st[d]];
+        const T w2 = -x[o0];
+        acc += gcoef<T>(t, 0, g) * w1 + gcoef<T>(t, 1, g) * w2;
+      }
+      const int m = lv.ndom[d] - 1 - g;
+      if (m <= 3 && p.lo[d] + p.n[d] == lv.ndom[d]) {
+        const int t = lv.bc[2 * d + 1];
+        const long long o0 = o + (long long)(p.n[d] - 1 - c[d]) * st[d];  // last cell along d
+        const T w1 = T(16) * x[o0] - x[o0 - st[d]];
+        const T w2 = -x[o0];
+        acc += gcoef<T>(t, 0, m) * w1 + gcoef<T>(t, 1, m) * w2;
+      }
+    }
+  }
+  acc -= T(30 * D) * xc;
+  return acc;
+}
+
+template <typename T, int D, int MODE, bool TR = false>
 __device__ __forceinline__ void cell_level_op(const LevelView& lv, const PatchDesc& p, int i, int j, int k,
                                               const T* __restrict__ x, const T* __restrict__ f,
                                               T* __restrict__ out, const T* __restrict__ bc, T alpha, T beta,
@@ -183,28 +243,7 @@ __device__ __forceinline__ void cell_level_op(const LevelView& lv, const PatchDe
     return;
   }
   const T xc = x[o];
-  T acc = T(0);
-  const long long st[3] = {1, p.sy, p.sz};
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int g = p.lo[d] + c[d];
-    T m1, p1, m2, p2;
-    if (g >= 2 && g <= lv.ndom[d] - 3) {
-      m1 = x[o - st[d]];
-      p1 = x[o + st[d]];
-      m2 = x[o - 2 * st[d]];
-      p2 = x[o + 2 * st[d]];
-    } else {
-      int cc[3] = {i, j, k};
-      cc[d] = c[d] - 1; m1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
-      cc[d] = c[d] + 1; p1 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
-      cc[d] = c[d] - 2; m2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
-      cc[d] = c[d] + 2; p2 = read_nb<T, D>(x, p, lv, bc, cc[0], cc[1], cc[2], d);
-    }
-    acc += T(16) * (m1 + p1) - (m2 + p2);
-  }
-  acc -= T(30 * D) * xc;
-  const T ax = alpha * xc + beta * (acc * inv);
+  const T ax = alpha * xc + beta * (cell_Lx<T, D, TR>(lv, p, i, j, k, x, bc) * inv);
   if (MODE == OP_APPLY) {
     out[o] = ax;
   } else if (MODE == OP_RESID) {
@@ -215,7 +254,7 @@ __device__ __forceinline__ void cell_level_op(const LevelView& lv, const PatchDe
   }
 }
 
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, bool TR = false>
 __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, const T* __restrict__ x,
                                                      const T* __restrict__ f, T* __restrict__ out,
                                                      const T* __restrict__ bc, T alpha, T beta, T omega,
@@ -224,7 +263,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) return;
-  cell_level_op<T, D, MODE>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
+  cell_level_op<T, D, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
 }
 
 // ------------------------------------------------------------------------ G and D
@@ -328,7 +367,7 @@ __global__ void k_copy(const CopyEntry* __restrict__ list, long long n, T* __res
 // Coarse cell g gets the mean of its r^D children (r = 2): of x (average-down,
 // Eq. AMR_avergingDownToCrse / restriction), or of f - A x on the fine level (residual
 // restriction) when RESID.
-template <typename T, int D, bool RESID>
+template <typename T, int D, bool RESID, bool TR = false>
 __device__ __forceinline__ void cell_restrict(const LevelView& fine, const PatchDesc& fp, const PatchDesc& cp,
                                               const int g[3], const T* __restrict__ xf, const T* __restrict__ ff,
                                               T* __restrict__ outc, T alpha, T beta) {
@@ -345,35 +384,14 @@ __device__ __forceinline__ void cell_restrict(const LevelView& fine, const Patch
           acc += xf[o];
         } else {
           const T xc = xf[o];
-          T s = T(0);
-          const int c[3] = {fi, fj, fk};
-          const long long st[3] = {1, fp.sy, fp.sz};
-#pragma unroll
-          for (int d = 0; d < D; ++d) {
-            const int gg = fp.lo[d] + c[d];
-            T m1, p1, m2, p2;
-            if (gg >= 2 && gg <= fine.ndom[d] - 3) {
-              m1 = xf[o - st[d]];
-              p1 = xf[o + st[d]];
-              m2 = xf[o - 2 * st[d]];
-              p2 = xf[o + 2 * st[d]];
-            } else {
-              int cc[3] = {fi, fj, fk};
-              cc[d] = c[d] - 1; m1 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
-              cc[d] = c[d] + 1; p1 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
-              cc[d] = c[d] - 2; m2 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
-              cc[d] = c[d] + 2; p2 = read_nb<T, D>(xf, fp, fine, nullptr, cc[0], cc[1], cc[2], d);
-            }
-            s += T(16) * (m1 + p1) - (m2 + p2);
-          }
-          s -= T(30 * D) * xc;
+          const T s = cell_Lx<T, D, TR>(fine, fp, fi, fj, fk, xf, (const T*)nullptr);
           acc += ff[o] - (alpha * xc + beta * (s * inv));
         }
       }
   outc[poff(cp, g[0] - cp.lo[0], g[1] - cp.lo[1], g[2] - cp.lo[2])] = acc * T(D == 3 ? 0.125 : 0.25);
 }
 
-template <typename T, int D, bool RESID>
+template <typename T, int D, bool RESID, bool TR = false>
 __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                            const T* __restrict__ xf, const T* __restrict__ ff, T* __restrict__ outc,
                            T alpha, T beta, int nby) {
@@ -384,7 +402,7 @@ __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __res
   const int j = by * BY + threadIdx.y;
   const int g[3] = {b.clo[0] + i, b.clo[1] + j, b.clo[2] + kk};
   if (g[0] > b.chi[0] || g[1] > b.chi[1] || g[2] > b.chi[2]) return;
-  cell_restrict<T, D, RESID>(fine, fine.patches[b.fpatch], crs.patches[b.cpatch], g, xf, ff, outc, alpha, beta);
+  cell_restrict<T, D, RESID, TR>(fine, fine.patches[b.fpatch], crs.patches[b.cpatch], g, xf, ff, outc, alpha, beta);
 }
 
 // Fine cell gf += cell-centred tensor linear interpolation of the coarse correction
@@ -462,7 +480,7 @@ __device__ __forceinline__ void cell_of(const PatchDesc& p, int t, int& i, int& 
   k = t / (p.n[0] * p.n[1]);
 }
 
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __restrict__ bglob, T* __restrict__ xglob,
                                                     T alpha, T beta, T omega) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -483,13 +501,13 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __rest
     T* oth = (cur == x) ? tb : x;
     for (int t = tid; t < ncell(m); t += nth) {
       cell_of(cm.sp[m], t, i, j, k);
-      cell_level_op<T, D, OP_JACOBI0>(cm.lv[m], cm.sp[m], i, j, k, nullptr, b, cur, nullptr, alpha, beta, omega);
+      cell_level_op<T, D, OP_JACOBI0, TR>(cm.lv[m], cm.sp[m], i, j, k, nullptr, b, cur, nullptr, alpha, beta, omega);
     }
     __syncthreads();
     for (int s = 1; s < cm.nu1; ++s) {
       for (int t = tid; t < ncell(m); t += nth) {
         cell_of(cm.sp[m], t, i, j, k);
-        cell_level_op<T, D, OP_JACOBI>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
+        cell_level_op<T, D, OP_JACOBI, TR>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
       }
       __syncthreads();
       T* sw = cur;
@@ -499,7 +517,7 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __rest
     for (int t = tid; t < ncell(m + 1); t += nth) {
       cell_of(cm.sp[m + 1], t, i, j, k);
       const int g[3] = {i, j, k};
-      cell_restrict<T, D, true>(cm.lv[m], cm.sp[m], cm.sp[m + 1], g, x, b, sm + cm.offb[m + 1], alpha, beta);
+      cell_restrict<T, D, true, TR>(cm.lv[m], cm.sp[m], cm.sp[m + 1], g, x, b, sm + cm.offb[m + 1], alpha, beta);
     }
     __syncthreads();
   }
@@ -534,7 +552,7 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __rest
     for (int s = 0; s < cm.nu2; ++s) {
       for (int t = tid; t < ncell(m); t += nth) {
         cell_of(cm.sp[m], t, i, j, k);
-        cell_level_op<T, D, OP_JACOBI>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
+        cell_level_op<T, D, OP_JACOBI, TR>(cm.lv[m], cm.sp[m], i, j, k, cur, b, oth, nullptr, alpha, beta, omega);
       }
       __syncthreads();
       T* sw = cur;
@@ -554,6 +572,147 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __rest
     cell_of(cm.sp[0], t, i, j, k);
     xglob[poff(cm.gp, i, j, k)] = sm[cm.offx[0] + poff(cm.sp[0], i, j, k)];
   }
+}
+
+// ------------------------------------------------------------------------ composite transpose
+// Pieces of (A^comp)^T z beyond the per-level transposed stencil (which also covers the
+// physical-ghost coefficients and same-level copies through the copy ghosts of z):
+//   k_reflux_T   transposed refluxing (COH-3): scatters each coarse row's weight onto the
+//                coarse and fine cells its flux difference reads (atomic adds); coarse reads
+//                outside the domain go through the physical ghost coefficients;
+//   k_cfi_T      transposed AMRCFI: the weight that fine rows put on a CF ghost (its
+//                stencil reads plus any refluxing weight stored in the ghost slot) goes to
+//                the ghost's 5^D coarse window with the interpolation weights (atomic adds);
+//   k_avgdown_T  transposed average-down: invalid coarse cells hand 1/2^D of their weight
+//                to each child (applied coarse to fine).
+template <typename T, int D>
+__global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
+                           const T* __restrict__ z, T* __restrict__ W, T beta) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const RefluxEntry e = list[t];
+  const T zc = z[e.coff];
+  if (zc == T(0)) return;
+  const PatchDesc cp = crs.patches[e.cpatch];
+  const T fd[4] = {T(1.0 / 12.0), T(-15.0 / 12.0), T(15.0 / 12.0), T(-1.0 / 12.0)};
+  const T hc = pick<T>(crs.hd, crs.hf), hf = pick<T>(fine.hd, fine.hf);
+  const long long st[3] = {1, cp.sy, cp.sz};
+  for (int d = 0; d < D; ++d)
+    for (int side = 0; side < 2; ++side) {
+      if (!(e.faces & (1 << (2 * d + side)))) continue;
+      const T s = T(side == 1 ? 1 : -1);
+      int own[3] = {e.g[0] - cp.lo[0], e.g[1] - cp.lo[1], e.g[2] - cp.lo[2]};
+      if (side == 0) own[d] -= 1;
+      for (int q = 0; q < 4; ++q) {
+        int cc[3] = {own[0], own[1], own[2]};
+        cc[d] += q - 1;
+        const T wgt = -beta * s * fd[q] * zc / (hc * hc);
+        const int g = cp.lo[d] + cc[d];
+        if (g >= 0 && g < crs.ndom[d]) {
+          atomicAdd(&W[poff(cp, cc[0], cc[1], cc[2])], wgt);
+        } else {
+          const int gs = g < 0 ? 0 : 1;
+          const int layer = gs == 0 ? -g : g - crs.ndom[d] + 1;
+          const int type = crs.bc[2 * d + gs];
+          for (int m = 0; m < 4; ++m) {
+            int c2[3] = {cc[0], cc[1], cc[2]};
+            c2[d] = gs == 0 ? (m - cp.lo[d]) : (crs.ndom[d] - 1 - m - cp.lo[d]);
+            atomicAdd(&W[poff(cp, c2[0], c2[1], c2[2])], gcoef<T>(type, layer - 1, m) * wgt);
+          }
+        }
+      }
+      const PatchDesc fp = fine.patches[e.fpatch[2 * d + side]];
+      const int e1 = (d == 0) ? 1 : 0;
+      const int e2 = (d == 2) ? 1 : 2;
+      const T fw = beta * s * zc / (T(D == 3 ? 4 : 2) * hf * hc);
+      for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
+        for (int t1 = 0; t1 < 2; ++t1) {
+          int gf[3] = {0, 0, 0};
+          gf[d] = side == 1 ? 2 * (e.g[d] + 1) - 1 : 2 * e.g[d] - 1;
+          gf[e1] = 2 * e.g[e1] + t1;
+          if (D == 3) gf[e2] = 2 * e.g[e2] + t2;
+          for (int q = 0; q < 4; ++q) {
+            int cc[3] = {gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]};
+            cc[d] += q - 1;
+            atomicAdd(&W[poff(fp, cc[0], cc[1], cc[2])], fd[q] * fw);
+          }
+        }
+      (void)st;
+    }
+}
+
+template <typename T, int D>
+__global__ void k_cfi_T(const CfiEntry* __restrict__ list, long long n, const long long* __restrict__ side,
+                        const PatchDesc* __restrict__ cpatches, const PatchDesc* __restrict__ fpatches, int r,
+                        const T* __restrict__ z, T* __restrict__ W, T beta_inv12h2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CfiEntry e = list[t];
+  const PatchDesc fp = fpatches[e.fpatch];
+  const long long st[3] = {1, fp.sy, fp.sz};
+  const long long step = (e.layer > 0 ? -1 : 1) * st[e.dir];  // towards the interior
+  const int L = e.layer > 0 ? e.layer : -e.layer;
+  T wg = (L == 1) ? T(16) * z[e.dst + step] - z[e.dst + 2 * step] : -z[e.dst + 2 * step];
+  wg = wg * beta_inv12h2 + W[e.dst];
+  if (wg == T(0)) return;
+  const int b0 = (e.pos[0] * r + e.sub[0]) * CFI_W;
+  const int b1 = (e.pos[1] * r + e.sub[1]) * CFI_W;
+  const int b2 = (e.pos[2] * r + e.sub[2]) * CFI_W;
+  if (e.src >= 0) {
+    const PatchDesc cp = cpatches[e.cpatch];
+    for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
+      for (int c1 = 0; c1 < CFI_W; ++c1) {
+        const long long row = e.src + (long long)c1 * cp.sy + (long long)c2 * cp.sz;
+        const T wr = cfiw<T>(b1 + c1) * (D == 3 ? cfiw<T>(b2 + c2) : T(1)) * wg;
+        for (int c0 = 0; c0 < CFI_W; ++c0) atomicAdd(&W[row + c0], cfiw<T>(b0 + c0) * wr);
+      }
+  } else {
+    const long long* sd = side + (-1 - e.src) * (D == 3 ? 125 : 25);
+    int q = 0;
+    for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
+      for (int c1 = 0; c1 < CFI_W; ++c1)
+        for (int c0 = 0; c0 < CFI_W; ++c0, ++q)
+          atomicAdd(&W[sd[q]], cfiw<T>(b0 + c0) * cfiw<T>(b1 + c1) * (D == 3 ? cfiw<T>(b2 + c2) : T(1)) * wg);
+  }
+}
+
+template <typename T, int D>
+__global__ void k_avgdown_T(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks, T* __restrict__ W,
+                            int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  const T wc = W[poff(cp, (gf[0] >> 1) - cp.lo[0], (gf[1] >> 1) - cp.lo[1], (D == 3 ? (gf[2] >> 1) : 0) - cp.lo[2])];
+  W[poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2])] += wc * T(D == 3 ? 0.125 : 0.25);
+}
+
+// out = vmask ? (f ? f - w : w) : 0 on interior cells (composite transpose epilogue; also
+// used to copy the valid part of a field)
+template <typename T, int D>
+__global__ void k_valid_out(LevelView lv, int nby, const T* __restrict__ w, const T* __restrict__ f, T* __restrict__ out,
+                            const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  out[o] = vmask[o] ? (f != nullptr ? f[o] - w[o] : w[o]) : T(0);
+}
+
+// out = f - w on valid interior cells only (other cells untouched)
+template <typename T, int D>
+__global__ void k_level_op_masked_copy(LevelView lv, int nby, const T* __restrict__ w, const T* __restrict__ f,
+                                       T* __restrict__ out, const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (vmask[o]) out[o] = f[o] - w[o];
 }
 
 // ------------------------------------------------------------------------ elementwise

