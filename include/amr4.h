@@ -270,9 +270,27 @@ amr_status amr_project(amr_operator* ppe, const amr_solver_params* p, const int*
 /* Adjoint (transposed) operator: out = A^T y over the valid cells (homogeneous data);
  * y and out are composite fields whose invalid cells are ignored (out's are set to 0). */
 amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, void* stream);
-/* lambda = A^{-T} g (the adjoint solve of a Helmholtz operator), by V-cycles on A^T. */
+/* lambda = A^{-T} g over the valid cells (the adjoint solve), by V-cycles on A^T: every
+ * level operator replaced by its transpose (interior stencil, physical-ghost coefficients),
+ * exact composite transposes (refluxing, AMRCFI, average-down) for the residuals passed
+ * between levels, FP64 outer residual (precision as in amr_solve).  Values of g on invalid
+ * cells are first handed to their children (transposed average-down), so that a gradient
+ * with respect to a composite field whose invalid cells are averages is propagated
+ * correctly; ghost cells of g are ignored; lambda's invalid cells are set to 0.  Not
+ * provided for the singular pure-Neumann operator (AMR_ERR_INVALID_ARG). */
 amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, double* lambda,
                                const double* g, amr_solve_stats* stats, void* stream);
+
+/* Batched solves: n independent problems (each with its own operator; hierarchies may
+ * differ, e.g. the uneven sizes of a batch of single-level Helmholtz problems), each solved
+ * by its captured CUDA graph (p->use_graph is forced to 1, boundary data homogeneous).  The
+ * graphs are launched concurrently on a pool of internal streams forked from ``stream`` and
+ * joined back to it; problems that share a hierarchy run one after another on the same
+ * stream because they share its reduction scratch.  The call synchronises ``stream``.
+ * stats and status (host arrays of n entries, nullable) receive each problem's statistics
+ * and status; the return value is the first non-OK status (AMR_OK if all converged). */
+amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
+                           const double* const* f, amr_solve_stats* stats, int* status, void* stream);
 
 /* Host-buffer variant of amr_solve: phi and f are HOST pointers (pinned or pageable);
  * the library copies them to its own device buffers and back inside the call. */

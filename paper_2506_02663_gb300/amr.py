@@ -75,6 +75,7 @@ _sigs = {
     "amr_vcycle": [_vp, _P(SolverParams), _vp, _vp, _vp, _vp],
     "amr_solve": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
     "amr_solve_host": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
+    "amr_batch_solve": [_P(_vp), C.c_int, _P(SolverParams), _P(_vp), _P(_vp), _P(SolveStats), _P(C.c_int), _vp],
     "amr_solvability_fix": [_vp, _vp, _vp, _P(C.c_double), _vp],
     "amr_mean_zero": [_vp, _vp, _P(C.c_double), _vp],
     "amr_mean_zero_noalloc": [_vp, _vp, _P(C.c_double), _vp],
@@ -371,6 +372,18 @@ class Operator:
         _check(_lib.amr_solve_transpose(self._op, C.byref(p), _ptr(lam), _ptr(g), C.byref(s), _stream(stream)),
                "amr_solve_transpose")
         return stats_dict(s)
+
+
+def batch_solve(ops, phis, fs, params=None, stream=None):
+    """amr_batch_solve: returns (list of stats dicts, list of statuses)."""
+    n = len(ops)
+    p = params or default_params()
+    oa = (_vp * n)(*[op._op.value for op in ops])
+    st = (SolveStats * n)()
+    sc = (C.c_int * n)()
+    rc = _lib.amr_batch_solve(oa, n, C.byref(p), _ptr_array(phis), _ptr_array(fs), st, sc, _stream(stream))
+    _check(rc, "amr_batch_solve", (AMR_OK, AMR_ERR_NOT_CONVERGED))
+    return [stats_dict(st[k]) for k in range(n)], list(sc)
 
 
 def _ptr_array(ts):

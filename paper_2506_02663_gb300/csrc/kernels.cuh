@@ -644,7 +644,8 @@ __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __r
 template <typename T, int D>
 __global__ void k_cfi_T(const CfiEntry* __restrict__ list, long long n, const long long* __restrict__ side,
                         const PatchDesc* __restrict__ cpatches, const PatchDesc* __restrict__ fpatches, int r,
-                        const T* __restrict__ z, T* __restrict__ W, T beta_inv12h2) {
+                        const T* __restrict__ z, const T* __restrict__ wghost, T* __restrict__ W, T beta_inv12h2,
+                        T sign) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CfiEntry e = list[t];
@@ -653,7 +654,7 @@ __global__ void k_cfi_T(const CfiEntry* __restrict__ list, long long n, const lo
   const long long step = (e.layer > 0 ? -1 : 1) * st[e.dir];  // towards the interior
   const int L = e.layer > 0 ? e.layer : -e.layer;
   T wg = (L == 1) ? T(16) * z[e.dst + step] - z[e.dst + 2 * step] : -z[e.dst + 2 * step];
-  wg = wg * beta_inv12h2 + W[e.dst];
+  wg = sign * (wg * beta_inv12h2 + (wghost != nullptr ? wghost[e.dst] : T(0)));
   if (wg == T(0)) return;
   const int b0 = (e.pos[0] * r + e.sub[0]) * CFI_W;
   const int b1 = (e.pos[1] * r + e.sub[1]) * CFI_W;
@@ -692,6 +693,20 @@ __global__ void k_avgdown_T(LevelView fine, LevelView crs, const XferBlock* __re
   W[poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2])] += wc * T(D == 3 ? 0.125 : 0.25);
 }
 
+// Transposed same-level copy: weight accumulated in a copy-ghost slot (by refluxing
+// transposes) belongs to the sibling cell the ghost copies.
+template <typename T>
+__global__ void k_copy_T(const CopyEntry* __restrict__ list, long long n, T* __restrict__ W) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CopyEntry e = list[t];
+  const T v = W[e.dst];
+  if (v != T(0)) {
+    atomicAdd(&W[e.src], v);
+    W[e.dst] = T(0);
+  }
+}
+
 // out = vmask ? (f ? f - w : w) : 0 on interior cells (composite transpose epilogue; also
 // used to copy the valid part of a field)
 template <typename T, int D>
@@ -702,6 +717,98 @@ __global__ void k_valid_out(LevelView lv, int nby, const T* __restrict__ w, cons
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
   out[o] = vmask[o] ? (f != nullptr ? f[o] - w[o] : w[o]) : T(0);
+}
+
+// Transposed prolongation (Sec. 6.4 linear interpolation): every fine cell hands
+// w * (y1 + y2) to each coarse cell its interpolation reads (atomic adds); coarse positions
+// outside the domain pass their weight on through the homogeneous extension.
+template <typename T, int D>
+__global__ void k_prolong_T(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                            const T* __restrict__ y1, const T* __restrict__ y2, T* __restrict__ out, int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  const long long of = poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]);
+  const T v = y1[of] + (y2 != nullptr ? y2[of] : T(0));
+  if (v == T(0)) return;
+  int par[3], sg[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    par[e] = (e < D) ? (gf[e] >> 1) : 0;
+    sg[e] = (e < D) ? (((gf[e] & 1) == 0) ? -1 : 1) : 0;
+  }
+  for (int q2 = 0; q2 < (D == 3 ? 2 : 1); ++q2)
+    for (int q1 = 0; q1 < 2; ++q1)
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const int q[3] = {q0, q1, q2};
+        int cc[3];
+        T w = T(1);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          cc[e] = par[e] + q[e] * sg[e] - cp.lo[e];
+          if (e < D) w *= (q[e] == 0) ? T(0.75) : T(0.25);
+        }
+        // tensor expansion of the out-of-domain dimensions (as in read_ext), scattered
+        int idx[3][4];
+        T ww[3][4];
+        int cnt[3] = {1, 1, 1};
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          idx[e][0] = cc[e];
+          ww[e][0] = T(1);
+          if (e >= D) continue;
+          const int g = cp.lo[e] + cc[e];
+          if (g < 0 || g >= crs.ndom[e]) {
+            const int side = g < 0 ? 0 : 1;
+            const int layer = side == 0 ? -g : g - crs.ndom[e] + 1;
+            const int type = crs.bc[2 * e + side];
+            cnt[e] = 4;
+            for (int m = 0; m < 4; ++m) {
+              idx[e][m] = side == 0 ? (m - cp.lo[e]) : (crs.ndom[e] - 1 - m - cp.lo[e]);
+              ww[e][m] = gcoef<T>(type, layer - 1, m);
+            }
+          }
+        }
+        for (int a0 = 0; a0 < cnt[0]; ++a0)
+          for (int a1 = 0; a1 < cnt[1]; ++a1)
+            for (int a2 = 0; a2 < cnt[2]; ++a2)
+              atomicAdd(&out[poff(cp, idx[0][a0], idx[1][a1], idx[2][a2])], w * ww[0][a0] * ww[1][a1] * ww[2][a2] * v);
+      }
+}
+
+// y += a * x on valid interior cells (x is read as 0 elsewhere)
+template <typename T, int D>
+__global__ void k_axpy_valid(LevelView lv, int nby, const T* __restrict__ x, T* __restrict__ y, T a,
+                             const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (vmask[o]) y[o] += a * x[o];
+}
+
+// Transposed average-down from one coarse buffer into a fine buffer: y_f += y_c / 2^D for
+// every fine cell of the transfer blocks (the coarse cells are the invalid ones).
+template <typename T, int D>
+__global__ void k_avgdown_T2(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                             const T* __restrict__ yc, T* __restrict__ yf, int nby) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
+  const int kk = (D == 3) ? (int)(blockIdx.y / nby) : 0;
+  const int j = by * BY + threadIdx.y;
+  const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  const T wc = yc[poff(cp, (gf[0] >> 1) - cp.lo[0], (gf[1] >> 1) - cp.lo[1], (D == 3 ? (gf[2] >> 1) : 0) - cp.lo[2])];
+  yf[poff(fp, gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2])] += wc * T(D == 3 ? 0.125 : 0.25);
 }
 
 // out = f - w on valid interior cells only (other cells untouched)

@@ -31,6 +31,7 @@ struct Scratch {
   T* rin = nullptr; // V-cycle input residual (FP32 path)
   T* Z = nullptr;   // composite transpose: masked input
   T* W = nullptr;   // composite transpose: accumulated result
+  T* Y = nullptr;   // adjoint V-cycle temporary
   std::vector<T*> mx, mb, mt;  // level-0 multigrid grids m >= 1
   bool ready = false;
 };
@@ -57,6 +58,7 @@ struct amr_operator {
   // captured solve (use_graph): one graph = prologue + device-side while loop over V-cycles
   struct DevStats* d_stats = nullptr;
   struct DevStats* h_stats = nullptr;  // pinned
+  double* h_scal = nullptr;            // pinned copy of the hierarchy's device scalars
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -451,6 +453,8 @@ amr_status ensure_scratch(amr_operator* op) {
   TRY(dalloc(&S.rin, n));
   TRY(dalloc(&S.Z, n));
   TRY(dalloc(&S.W, n));
+  TRY(dalloc(&S.Y, n));
+  CK(cudaMemset(S.Y, 0, n * sizeof(T)));
   CK(cudaMemset(S.Z, 0, n * sizeof(T)));
   CK(cudaMemset(S.W, 0, n * sizeof(T)));
   CK(cudaMemset(S.E, 0, n * sizeof(T)));
@@ -478,7 +482,7 @@ amr_status ensure_scratch(amr_operator* op) {
 template <typename T>
 void free_scratch(Scratch<T>& S) {
   cudaFree(S.E); cudaFree(S.R); cudaFree(S.T1); cudaFree(S.T2); cudaFree(S.X); cudaFree(S.rin);
-  cudaFree(S.Z); cudaFree(S.W);
+  cudaFree(S.Z); cudaFree(S.W); cudaFree(S.Y);
   for (auto p : S.mx) cudaFree(p);
   for (auto p : S.mb) cudaFree(p);
   for (auto p : S.mt) cudaFree(p);
@@ -627,13 +631,14 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
 // per-level transposed stencil (physical-ghost coefficients included), transposed
 // refluxing, transposed AMRCFI, transposed average-down (coarse to fine).
 template <typename T, int D>
-amr_status composite_AT(amr_operator* op, const T* x, cudaStream_t st) {
+amr_status composite_AT(amr_operator* op, const T* x, cudaStream_t st, int only_level = -1) {
   amr_hierarchy* h = op->h;
   Scratch<T>& S = scratch<T>(op);
   const size_t bytes = (size_t)h->nelems * sizeof(T);
   CK(cudaMemsetAsync(S.Z, 0, bytes, st));
   CK(cudaMemsetAsync(S.W, 0, bytes, st));
   for (int l = 0; l < h->L; ++l) {
+    if (only_level >= 0 && l != only_level) continue;
     LevelView lv = level_view(h, l, op->bc);
     Geo g = geo_of(lv);
     k_valid_out<T, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, (const T*)nullptr, S.Z, h->d_valid);
@@ -652,13 +657,19 @@ amr_status composite_AT(amr_operator* op, const T* x, cudaStream_t st) {
         level_view(h, l, op->bc), level_view(h, l + 1, op->bc), dl.reflux, dl.nreflux, S.Z, S.W, T(op->beta));
     TRY(launch_check());
   }
+  for (int l = 0; l < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.ncopy == 0) continue;
+    k_copy_T<T><<<(unsigned)((dl.ncopy + nt - 1) / nt), nt, 0, st>>>(dl.copy, dl.ncopy, S.W);
+    TRY(launch_check());
+  }
   for (int l = h->L - 1; l >= 1; --l) {
     const DeviceLists& dl = h->lev[l].dev;
     if (dl.ncfi == 0) continue;
     const LevelView fv = level_view(h, l, op->bc);
     k_cfi_T<T, D><<<(unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st>>>(
-        dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches, h->lev[l].d_patches, h->r, S.Z, S.W,
-        T(op->beta * fv.inv12h2));
+        dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches, h->lev[l].d_patches, h->r, S.Z, S.W, S.W,
+        T(op->beta * fv.inv12h2), T(1));
     TRY(launch_check());
   }
   for (int l = 0; l + 1 < h->L; ++l) {
@@ -695,49 +706,131 @@ amr_status transpose_residual(amr_operator* op, int l, const T* f, T* out, cudaS
   return AMR_OK;
 }
 
-// Adjoint V-cycle: the V-cycle of vcycle_corr with every level operator replaced by its
-// transpose; the residuals handed between AMR levels are the exact composite ones,
-// r - (A^comp)^T X.
+template <typename T, int D>
+Geo xfer_geo(const DeviceLists& dl, bool fine_cells, int& nby) {
+  Geo g;
+  const int fy = (fine_cells ? 2 : 1) * dl.xfer_max[1];
+  nby = (fy + BY - 1) / BY;
+  g.nby = nby;
+  g.grid = dim3(((fine_cells ? 2 : 1) * dl.xfer_max[0] + BX - 1) / BX,
+                nby * (D == 3 ? (fine_cells ? 2 : 1) * dl.xfer_max[2] : 1), dl.nxfer);
+  return g;
+}
+
+// Adjoint V-cycle: the exact transpose of vcycle_corr's AMR part (the forward program run
+// backwards, every step transposed; the transpose of weighted-Jacobi sweeps from zero on A
+// is the same number of sweeps from zero on A^T), with a V-cycle on A^T for all of level
+// 0.  Input: r (valid cells); output S.X = M^T r where M is the forward V-cycle's AMR part.
 template <typename T, int D>
 amr_status vcycle_corr_T(amr_operator* op, const amr_solver_params& p, const T* r, cudaStream_t st) {
   amr_hierarchy* h = op->h;
   Scratch<T>& S = scratch<T>(op);
   const int L = h->L - 1;
   const size_t bytes = (size_t)h->nelems * sizeof(T);
-  CK(cudaMemsetAsync(S.E, 0, bytes, st));
-  CK(cudaMemsetAsync(S.X, 0, bytes, st));
-  CK(cudaMemsetAsync(S.T1, 0, bytes, st));
-  CK(cudaMemsetAsync(S.T2, 0, bytes, st));
-  {
-    long long a, b;
-    level_range(h, L, a, b);
-    CK(cudaMemcpyAsync(S.R + a, r + a, (size_t)(b - a) * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  // adjoint buffers: Xb = S.X (adjoint of X), Eb = S.E, Rb = S.R, rb = S.rin (output), tmp = S.Y
+  T* Xb = S.X;
+  T* Eb = S.E;
+  T* Rb = S.R;
+  T* rb = S.rin;
+  T* tmp = S.Y;
+  if (r == rb) {
+    CK(cudaMemcpyAsync(S.Y, r, bytes, cudaMemcpyDeviceToDevice, st));  // mixed precision: input lives in rin
+    r = S.Y;
   }
+  CK(cudaMemsetAsync(Xb, 0, bytes, st));
   std::vector<LevelView> lv(h->L);
   for (int l = 0; l <= L; ++l) lv[l] = level_view(h, l, op->bc);
-  const double a_ = op->alpha, b_ = op->beta;
-  for (int l = L; l >= 1; --l) {
-    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st)));
-    TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
-    const DeviceLists& cl = h->lev[l - 1].dev;
-    TRY(copy_fill<T>(h, l, S.E, st));
-    TRY((restrict_blocks<T, D, true>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st)));
-    TRY((composite_AT<T, D>(op, S.X, st)));
-    TRY((transpose_residual<T, D>(op, l - 1, r, S.R, st)));
+  for (int l = 0; l <= L; ++l) {
+    Geo g = geo_of(lv[l]);
+    k_axpy_valid<T, D><<<g.grid, g.block, 0, st>>>(lv[l], g.nby, r, Xb, T(1), h->d_valid);
+    TRY(launch_check());
   }
-  TRY((mg_level0<T, D, true>(op, p, 0, S.R, S.E, S.T1, st)));
-  TRY(axpy<T, T, D>(lv[0], S.E, S.X, (T*)nullptr, 1.0, st));
+  CK(cudaMemsetAsync(Eb, 0, bytes, st));
+  CK(cudaMemsetAsync(Rb, 0, bytes, st));
+  CK(cudaMemsetAsync(rb, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T1, 0, bytes, st));
+  CK(cudaMemsetAsync(S.T2, 0, bytes, st));
+  const double a_ = op->alpha, b_ = op->beta;
+  const int nt = 128;
+  // ---- reverse of the up-leg, finest level first
+  for (int l = L; l >= 1; --l) {
+    const DeviceLists& cl = h->lev[l - 1].dev;
+    // U4^T: delta_bar = Eb_l + Xb_l (into tmp, level l)
+    CK(cudaMemsetAsync(tmp, 0, bytes, st));
+    TRY((axpy<T, T, D>(lv[l], Eb, tmp, (T*)nullptr, 1.0, st)));
+    TRY((axpy<T, T, D>(lv[l], Xb, tmp, (T*)nullptr, 1.0, st)));
+    // U3^T: Rb_l += S'^T delta_bar (nu2 sweeps from zero on A_l^T)
+    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], tmp, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st)));
+    TRY((axpy<T, T, D>(lv[l], S.T1, Rb, (T*)nullptr, 1.0, st)));
+    // U2^T: Eb_l -= A_l^T Rb_l ; Eb_{l-1} -= A_fc^T Rb_l
+    TRY(copy_fill<T>(h, l, Rb, st));
+    TRY((level_op<T, D, true>(OP_RESID, lv[l], Rb, Eb, Eb, nullptr, a_, b_, 0.0, nullptr, st)));
+    {
+      const DeviceLists& dl = h->lev[l].dev;
+      if (dl.ncfi) {
+        k_cfi_T<T, D><<<(unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st>>>(
+            dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches, h->lev[l].d_patches, h->r, Rb, (const T*)nullptr,
+            Eb, T(b_ * lv[l].inv12h2), T(-1));
+        TRY(launch_check());
+      }
+    }
+    // U1^T: Eb_{l-1} += P^T (Eb_l + Xb_l)
+    if (cl.nxfer) {
+      int nby;
+      Geo g = xfer_geo<T, D>(cl, true, nby);
+      k_prolong_T<T, D><<<g.grid, dim3(BX, BY, 1), 0, st>>>(lv[l], lv[l - 1], cl.xfer, Eb, Xb, Eb, nby);
+      TRY(launch_check());
+    }
+    // the forward prolongation read sibling values through copy ghosts of level l-1
+    if (cl.ncopy) {
+      k_copy_T<T><<<(unsigned)((cl.ncopy + nt - 1) / nt), nt, 0, st>>>(cl.copy, cl.ncopy, Eb);
+      TRY(launch_check());
+    }
+  }
+  // ---- level 0: Eb_0 += Xb_0 ; Rb_0 += MG0^T(Eb_0)
+  TRY((axpy<T, T, D>(lv[0], Xb, Eb, (T*)nullptr, 1.0, st)));
+  CK(cudaMemsetAsync(tmp, 0, bytes, st));
+  TRY((mg_level0<T, D, true>(op, p, 0, Eb, tmp, S.T1, st)));
+  TRY((axpy<T, T, D>(lv[0], tmp, Rb, (T*)nullptr, 1.0, st)));
+  // ---- reverse of the down-leg, coarsest level first
   for (int l = 1; l <= L; ++l) {
     const DeviceLists& cl = h->lev[l - 1].dev;
-    TRY(copy_fill<T>(h, l - 1, S.E, st));
-    TRY(prolong_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, S.E, S.E, S.X, st));
-    TRY(copy_fill<T>(h, l, S.E, st));
-    TRY((level_op<T, D, true>(OP_RESID, lv[l], S.E, S.R, S.R, nullptr, a_, b_, 0.0, nullptr, st)));
-    TRY((composite_AT<T, D>(op, S.X, st)));
-    TRY((transpose_residual<T, D>(op, l, r, S.R, st)));
-    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], S.R, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st)));
-    TRY(axpy<T, T, D>(lv[l], S.T1, S.E, S.X, 1.0, st));
+    // D4^T: rb_{l-1} += Rb_{l-1} (valid) ; Xb -= valid part of A^T (Rb_{l-1} on level l-1 valid cells)
+    {
+      Geo g = geo_of(lv[l - 1]);
+      k_axpy_valid<T, D><<<g.grid, g.block, 0, st>>>(lv[l - 1], g.nby, Rb, rb, T(1), h->d_valid);
+      TRY(launch_check());
+    }
+    TRY((composite_AT<T, D>(op, Rb, st, l - 1)));
+    for (int m = l; m <= L; ++m) {
+      Geo g = geo_of(lv[m]);
+      k_axpy_valid<T, D><<<g.grid, g.block, 0, st>>>(lv[m], g.nby, S.W, Xb, T(-1), h->d_valid);
+      TRY(launch_check());
+    }
+    // D3^T: tmp_l = Avg^T (Rb_{l-1} on invalid cells) ; Rb_l += tmp_l ; Eb_l -= A_l^T tmp_l
+    CK(cudaMemsetAsync(tmp, 0, bytes, st));
+    if (cl.nxfer) {
+      int nby;
+      Geo g = xfer_geo<T, D>(cl, true, nby);
+      k_avgdown_T2<T, D><<<g.grid, dim3(BX, BY, 1), 0, st>>>(lv[l], lv[l - 1], cl.xfer, Rb, tmp, nby);
+      TRY(launch_check());
+    }
+    TRY((axpy<T, T, D>(lv[l], tmp, Rb, (T*)nullptr, 1.0, st)));
+    TRY(copy_fill<T>(h, l, tmp, st));
+    TRY((level_op<T, D, true>(OP_RESID, lv[l], tmp, Eb, Eb, nullptr, a_, b_, 0.0, nullptr, st)));
+    // D2^T: Eb_l += Xb_l
+    TRY((axpy<T, T, D>(lv[l], Xb, Eb, (T*)nullptr, 1.0, st)));
+    // D1^T: Rb_l += S^T Eb_l
+    TRY((smooth_from_zero<T, D, true>(h, l, lv[l], Eb, S.T1, S.T2, p.nu1, a_, b_, p.omega, true, st)));
+    TRY((axpy<T, T, D>(lv[l], S.T1, Rb, (T*)nullptr, 1.0, st)));
   }
+  // R_L = r_L: rb_L += Rb_L (valid cells)
+  {
+    Geo g = geo_of(lv[L]);
+    k_axpy_valid<T, D><<<g.grid, g.block, 0, st>>>(lv[L], g.nby, Rb, rb, T(1), h->d_valid);
+    TRY(launch_check());
+  }
+  CK(cudaMemcpyAsync(S.X, rb, bytes, cudaMemcpyDeviceToDevice, st));
   return AMR_OK;
 }
 
@@ -1152,18 +1245,20 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
   return AMR_OK;
 }
 
+// Captured solve, asynchronous part: set-up, graph launch, epilogue and the stats copy to
+// pinned host memory, all on st; solve_graph_finish() reads the stats after a sync.
 template <int D>
-amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
-                       amr_solve_stats* stats, cudaStream_t st) {
+amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, double* phi, const double* f,
+                              const double* bc, cudaStream_t st) {
   amr_hierarchy* h = op->h;
   const size_t bytes = (size_t)h->nelems * sizeof(double);
   if (!op->d_stats) {
     TRY(dalloc(&op->d_stats, 1));
     CK(cudaMallocHost(&op->h_stats, sizeof(DevStats)));
+    CK(cudaMallocHost(&op->h_scal, 8 * sizeof(double)));
   }
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
   else TRY(ensure_scratch<double>(op));
-  // set-up outside the graph: internal RHS copy, solvability fix, ||f||
   CK(cudaMemcpyAsync(op->F, f, bytes, cudaMemcpyDeviceToDevice, st));
   if (op->neumann) TRY(solvability_fix_impl<D>(op, op->F, bc, nullptr, st));
   if (p.zero_initial) CK(cudaMemsetAsync(phi, 0, bytes, st));
@@ -1178,21 +1273,32 @@ amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi
   if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
   else TRY(avgdown_all<D>(h, phi, st));
   CK(cudaMemcpyAsync(op->h_stats, op->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(op->h_scal, h->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return AMR_OK;
+}
+
+amr_status solve_graph_finish(amr_operator* op, amr_solve_stats* stats) {
   const DevStats& ds = *op->h_stats;
   g_launches.fetch_add(op->launches_pre + (long long)ds.iter * op->launches_body);
   amr_solve_stats loc{};
   loc.vcycles = ds.iter;
   for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
   loc.final_res = ds.hist[std::min(ds.iter, 63)];
-  loc.rhs_norm = h->h_scalar[5];
-  loc.removed_mean = op->neumann ? h->h_scalar[4] : 0.0;
+  loc.rhs_norm = op->h_scal[5];
+  loc.removed_mean = op->neumann ? op->h_scal[4] : 0.0;
   if (stats) *stats = loc;
   if (ds.status == 0) return AMR_OK;
   if (ds.status == 2) { set_error("residual is not finite"); return AMR_ERR_NONFINITE; }
   set_error("max_vcycles reached");
   return AMR_ERR_NOT_CONVERGED;
+}
+
+template <int D>
+amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
+                       amr_solve_stats* stats, cudaStream_t st) {
+  TRY(solve_graph_launch<D>(op, p, phi, f, bc, st));
+  CK(cudaStreamSynchronize(st));
+  return solve_graph_finish(op, stats);
 }
 
 template <int D>
@@ -1212,6 +1318,20 @@ amr_status solve_transpose_impl(amr_operator* op, const amr_solver_params& p, do
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
   amr_solve_stats loc{};
   if (p.zero_initial) CK(cudaMemsetAsync(lam, 0, bytes, st));
+  // right-hand side: weight on invalid cells (derived data, the average of their children)
+  // is handed to the children by the transposed average-down, coarse to fine
+  CK(cudaMemcpyAsync(op->F, g, bytes, cudaMemcpyDeviceToDevice, st));
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.nxfer == 0) continue;
+    const int fy = 2 * dl.xfer_max[1];
+    const int nby = (fy + BY - 1) / BY;
+    dim3 grid((2 * dl.xfer_max[0] + BX - 1) / BX, nby * (D == 3 ? 2 * dl.xfer_max[2] : 1), dl.nxfer);
+    k_avgdown_T<double, D><<<grid, dim3(BX, BY, 1), 0, st>>>(level_view(h, l + 1, nullptr), level_view(h, l, nullptr),
+                                                           dl.xfer, op->F, nby);
+    TRY(launch_check());
+  }
+  g = op->F;
   double gn = 0.0;
   TRY((maxnorm<double, D>(h, g, true, &gn, st)));
   loc.rhs_norm = gn;
@@ -1637,6 +1757,7 @@ void amr_operator_destroy(amr_operator* op) {
   if (op->body_stream) cudaStreamDestroy(op->body_stream);
   cudaFree(op->d_stats);
   if (op->h_stats) cudaFreeHost(op->h_stats);
+  if (op->h_scal) cudaFreeHost(op->h_scal);
   delete op;
 }
 
@@ -1723,6 +1844,57 @@ amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* 
     CK(cudaStreamSynchronize(st));
   }
   return s;
+}
+
+amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
+                           const double* const* f, amr_solve_stats* stats, int* status, void* stream) {
+  if (!ops || n < 0 || !phi || !f) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(check_params(p));
+  for (int k = 0; k < n; ++k) {
+    TRY(check_op(ops[k]));
+    if (!phi[k] || !f[k]) { set_error("null field in batch"); return AMR_ERR_INVALID_ARG; }
+  }
+  static std::mutex mu;
+  static std::vector<cudaStream_t> pool;
+  static std::vector<cudaEvent_t> ev;
+  std::lock_guard<std::mutex> lock(mu);
+  constexpr int NSTREAM = 16;
+  if (pool.empty()) {
+    pool.resize(NSTREAM);
+    ev.resize(NSTREAM + 1);
+    for (int i = 0; i < NSTREAM; ++i) CK(cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking));
+    for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t st = S(stream);
+  amr_solver_params q = *p;
+  q.use_graph = 1;
+  // problems that share a hierarchy share its reduction scratch: same stream, in order
+  std::vector<const amr_hierarchy*> hs;
+  std::vector<int> sid(n);
+  for (int k = 0; k < n; ++k) {
+    auto it = std::find(hs.begin(), hs.end(), ops[k]->h);
+    const int hidx = (int)(it - hs.begin());
+    if (it == hs.end()) hs.push_back(ops[k]->h);
+    sid[k] = hidx % NSTREAM;
+  }
+  CK(cudaEventRecord(ev[NSTREAM], st));
+  for (int i = 0; i < NSTREAM; ++i) CK(cudaStreamWaitEvent(pool[i], ev[NSTREAM], 0));
+  for (int k = 0; k < n; ++k) {
+    amr_operator* op = ops[k];
+    TRY(DISPATCH(op->h, solve_graph_launch, op, q, phi[k], f[k], nullptr, pool[sid[k]]));
+  }
+  for (int i = 0; i < NSTREAM; ++i) {
+    CK(cudaEventRecord(ev[i], pool[i]));
+    CK(cudaStreamWaitEvent(st, ev[i], 0));
+  }
+  CK(cudaStreamSynchronize(st));
+  amr_status worst = AMR_OK;
+  for (int k = 0; k < n; ++k) {
+    amr_status sk = solve_graph_finish(ops[k], stats ? &stats[k] : nullptr);
+    if (status) status[k] = sk;
+    if (sk != AMR_OK && worst == AMR_OK) worst = sk;
+  }
+  return worst;
 }
 
 amr_status amr_solvability_fix(amr_operator* op, double* f, const double* bc, double* m, void* stream) {
