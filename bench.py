@@ -361,6 +361,7 @@ def run_ours(args):
         line[key] = {"value": v2, "ms_per_step": sum(ts2) / args.steps,
                      "vcycles_per_system": [statistics.mean(v[i] for v in vcs2) for i in range(len(systems))]}
         line["large_grid_roofline"] = _large_grid_roofline(amr, torch, peak, peak_kind)
+        line["batch"] = _batch_measure(amr, torch)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, c, el = _oracle_vcycles(12.0)
@@ -372,6 +373,61 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def _batch_measure(amr, torch, reps=3):
+    """The batch workload: 96 independent single-level Helmholtz problems of uneven sizes
+    N in {64,...,512} (seeded), mixed precision to 1e-10, all solved by one amr_batch_solve
+    call (concurrent captured solves); compared with the same solves one after another and
+    with FP64 V-cycles."""
+    from paper_2506_02663_gb300 import workloads as wl
+    probs = wl.batch2d_problems()
+    hs, ops, fs, phis = [], [], [], []
+    dof = 0
+    for pr in probs:
+        n = pr["n"]
+        gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+        hs.append(gh)
+        ops.append(amr.Operator(gh, pr["alpha"], pr["beta"], [0, 0, 0, 0]))
+        fs.append(torch.from_numpy(gh.pack([[pr["rhs"]]])).cuda())
+        phis.append(torch.zeros_like(fs[-1]))
+        dof += n * n
+    out = {"workload": "batch2d: 96 single-level 2-D Helmholtz problems, N in {64,96,128,192,256,384,512} (seeded), "
+                       "alpha=1, beta=-0.25*nu/256, nu log-uniform [1e-4,1e-2], Fourier RHS |k|<=16",
+           "dof": dof}
+    stream = torch.cuda.current_stream()
+    for name, prec in (("mixed", amr.MIXED), ("fp64", amr.FP64)):
+        p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
+        amr.batch_solve(ops, phis, fs, params=p)  # warm-up: captures every graph
+        ts, vcs = [], []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st, status = amr.batch_solve(ops, phis, fs, params=p)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            vcs.append(sum(pr["n"] ** 2 * s["vcycles"] for pr, s in zip(probs, st)))
+        out[name] = {"ms_per_batch": statistics.median(ts), "value": statistics.mean(vcs) / (statistics.median(ts) * 1e-3),
+                     "unit": UNIT, "all_converged": all(x == 0 for x in status)}
+    # one after another on one stream
+    p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.MIXED, use_graph=1)
+    for op, x, f in zip(ops, phis, fs):
+        op.solve(x, f, params=p)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for op, x, f in zip(ops, phis, fs):
+        op.solve(x, f, params=p)
+    b.record(stream)
+    b.synchronize()
+    out["sequential_mixed_ms"] = a.elapsed_time(b)
+    for op in ops:
+        op.close()
+    for gh in hs:
+        gh.close()
+    return out
 
 
 def _large_grid_roofline(amr, torch, peak, peak_kind, n=4096):

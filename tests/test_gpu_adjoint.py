@@ -71,7 +71,9 @@ def test_solve_transpose_matches_direct(name, precision):
     bc = BCS[dim][0]
     H, gh = _hier(name, bc)
     rng = np.random.default_rng(47)
-    G = _rand_field(H, rng)
+    # zero on invalid cells: the ABI hands invalid-cell weight to the children first
+    # (transposed average-down), which the oracle's plain A^{-T} g does not do
+    G = _rand_field(H, rng, redundant=False)
     for alpha, beta in ((1.0, -0.01), (0.0, 1.0)):
         ref, A, U = so.solve_transpose_direct(H, G, alpha, beta)
         op = amr.Operator(gh, alpha, beta, bc)
@@ -85,6 +87,30 @@ def test_solve_transpose_matches_direct(name, precision):
 def _valid_mask_tensor(gh, H):
     m = [lev.valid.astype(np.float64) for lev in H.levels]
     return _dev(to_packed(gh, H, m, fill=0.0))
+
+
+def test_solve_transpose_hands_invalid_weight_to_children():
+    """g with weight on invalid cells: the ABI solves A^T lambda = E^T g (E = the map from
+    unknowns to composite data whose invalid cells are averages), checked against the oracle
+    with E^T applied by hand."""
+    amr = _amr()
+    from oracle import composite as cp
+    H, gh = _hier("three_level_multibox", [0, 0, 0, 0])
+    rng = np.random.default_rng(59)
+    G = _rand_field(H, rng)  # invalid cells hold the average of their children
+    Et = [a.copy() for a in G]
+    for l in range(H.lmax):
+        lev, fine = H.levels[l], H.levels[l + 1]
+        for lo, hi in fine.boxes:
+            fs = fine.box_slice(lo, hi)
+            par = np.repeat(np.repeat(Et[l][lev.box_slice(tuple(v // 2 for v in lo), tuple(v // 2 for v in hi))], 2, 0), 2, 1)
+            Et[l + 1][fs] = Et[l + 1][fs] + par / 4.0
+    ref, _, _ = so.solve_transpose_direct(H, Et, 1.0, -0.01)
+    op = amr.Operator(gh, 1.0, -0.01, [0, 0, 0, 0])
+    lam = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    op.solve_transpose(lam, _dev(to_packed(gh, H, G)), params=amr.default_params(rtol=1e-12, max_vcycles=200))
+    got = from_packed(gh, H, lam.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref)
 
 
 @pytest.mark.parametrize("name", ["two_level_ragged", "three_level_multibox", "three_d"])
