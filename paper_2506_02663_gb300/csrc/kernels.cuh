@@ -181,7 +181,7 @@ __device__ __forceinline__ T cell_Lx(const LevelView& lv, const PatchDesc& p, in
                                      const T* __restrict__ x, const T* __restrict__ bc) {
   const long long o = poff(p, i, j, k);
   const T xc = x[o];
-  T acc = T(0);
+  T s1 = T(0), s2 = T(0), extra = T(0);
   const int c[3] = {i, j, k};
   const long long st[3] = {1, p.sy, p.sz};
 #pragma unroll
@@ -205,7 +205,8 @@ __device__ __forceinline__ T cell_Lx(const LevelView& lv, const PatchDesc& p, in
       p1 = (g + 1 < lv.ndom[d]) ? x[o + st[d]] : T(0);
       p2 = (g + 2 < lv.ndom[d]) ? x[o + 2 * st[d]] : T(0);
     }
-    acc += T(16) * (m1 + p1) - (m2 + p2);
+    s1 += m1 + p1;
+    s2 += m2 + p2;
     if (TR) {
       // low face: this cell is interior cell m = g of the rows' ghost formulas
       if (g <= 3 && p.lo[d] == 0) {
@@ -213,7 +214,7 @@ __device__ __forceinline__ T cell_Lx(const LevelView& lv, const PatchDesc& p, in
         const long long o0 = o - (long long)c[d] * st[d];  // local index 0 along d
         const T w1 = T(16) * x[o0] - x[o0 + st[d]];
         const T w2 = -x[o0];
-        acc += gcoef<T>(t, 0, g) * w1 + gcoef<T>(t, 1, g) * w2;
+        extra += gcoef<T>(t, 0, g) * w1 + gcoef<T>(t, 1, g) * w2;
       }
       const int m = lv.ndom[d] - 1 - g;
       if (m <= 3 && p.lo[d] + p.n[d] == lv.ndom[d]) {
@@ -221,12 +222,11 @@ __device__ __forceinline__ T cell_Lx(const LevelView& lv, const PatchDesc& p, in
         const long long o0 = o + (long long)(p.n[d] - 1 - c[d]) * st[d];  // last cell along d
         const T w1 = T(16) * x[o0] - x[o0 - st[d]];
         const T w2 = -x[o0];
-        acc += gcoef<T>(t, 0, m) * w1 + gcoef<T>(t, 1, m) * w2;
+        extra += gcoef<T>(t, 0, m) * w1 + gcoef<T>(t, 1, m) * w2;
       }
     }
   }
-  acc -= T(30 * D) * xc;
-  return acc;
+  return (T(16) * s1 - s2 - T(30 * D) * xc) + extra;
 }
 
 template <typename T, int D, int MODE, bool TR = false>
@@ -264,6 +264,64 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) return;
   cell_level_op<T, D, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
+}
+
+// 2-D level operator, tiled: each thread computes ROWS consecutive cells of one column
+// with 32-bit patch-local offsets and reuses the column loads.  A block whose whole tile
+// (plus the two-cell stencil reach) lies inside the domain takes the fast path with the
+// constant interior diagonal (omega / diag precomputed); any other block runs the generic
+// per-cell code.  Both paths sum in the same order (bit-identical results).
+constexpr int ROWS = 4;
+
+template <typename T, int MODE, bool TR>
+__global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const T* __restrict__ x,
+                                                             const T* __restrict__ f, T* __restrict__ out,
+                                                             const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                             T omega_over_diag, const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j0 = (blockIdx.y * BY + threadIdx.y) * ROWS;
+  const int ti0 = blockIdx.x * BX, tj0 = blockIdx.y * BY * ROWS;
+  const bool full = ti0 + BX <= p.n[0] && tj0 + BY * ROWS <= p.n[1];
+  // the transpose also gathers ghost coefficients at distance 2 and 3 from a physical face
+  constexpr int M = TR ? 4 : 2;
+  const bool inside = p.lo[0] + ti0 >= M && p.lo[0] + ti0 + BX - 1 <= lv.ndom[0] - 1 - M && p.lo[1] + tj0 >= M &&
+                      p.lo[1] + tj0 + BY * ROWS - 1 <= lv.ndom[1] - 1 - M;
+  if (!(full && inside && vmask == nullptr)) {
+    if (i >= p.n[0]) return;
+    for (int r = 0; r < ROWS; ++r) {
+      const int j = j0 + r;
+      if (j >= p.n[1]) return;
+      if (vmask != nullptr && vmask[poff(p, i, j, 0)] == 0) continue;
+      cell_level_op<T, 2, MODE, TR>(lv, p, i, j, 0, x, f, out, bc, alpha, beta, omega);
+    }
+    return;
+  }
+  const T* __restrict__ xb = x + p.off;
+  const int sy = (int)p.sy;
+  const int o = (j0 + NG) * sy + (i + NG);
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  if (MODE == OP_JACOBI0) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) out[p.off + o + r * sy] = omega_over_diag * f[p.off + o + r * sy];
+    return;
+  }
+  T col[ROWS + 4];
+#pragma unroll
+  for (int q = 0; q < ROWS + 4; ++q) col[q] = xb[o + (q - 2) * sy];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int orr = o + r * sy;
+    const T xc = col[r + 2];
+    const T s1 = (xb[orr - 1] + xb[orr + 1]) + (col[r + 1] + col[r + 3]);
+    const T s2 = (xb[orr - 2] + xb[orr + 2]) + (col[r] + col[r + 4]);
+    const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
+    const T ax = alpha * xc + beta * (lap * inv);
+    const long long og = p.off + orr;
+    if (MODE == OP_APPLY) out[og] = ax;
+    else if (MODE == OP_RESID) out[og] = f[og] - ax;
+    else out[og] = xc + omega_over_diag * (f[og] - ax);
+  }
 }
 
 // ------------------------------------------------------------------------ G and D

@@ -101,6 +101,13 @@ inline amr_status launch_check() {
   return AMR_OK;
 }
 
+template <typename T>
+inline T pick_host(double d, float f);
+template <>
+inline double pick_host<double>(double d, float) { return d; }
+template <>
+inline float pick_host<float>(double, float f) { return f; }
+
 // ---------------------------------------------------------------- bench instrumentation
 // When enabled, launches of the instrumented kernel classes are bracketed with CUDA events
 // on the launching stream; amr_profile_read() sums the event intervals.
@@ -260,6 +267,29 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
   Geo g = geo_of(lv);
   cudaEvent_t ev;
   prof_begin(st, &ev);
+  if (D == 2) {
+    // tiled 2-D path; omega / (interior diagonal) computed once here in the value type
+    const T diag = T(alpha) + T(beta) * pick_host<T>(lv.inv12h2, lv.inv12h2_f) * T(-60);
+    const T ood = T(omega) / diag;
+    dim3 grid((lv.maxn[0] + BX - 1) / BX, (lv.maxn[1] + BY * ROWS - 1) / (BY * ROWS), lv.npatch);
+    dim3 block(BX, BY, 1);
+    switch (mode) {
+      case OP_APPLY:
+        k_level_op2d_tiled<T, OP_APPLY, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
+        break;
+      case OP_RESID:
+        k_level_op2d_tiled<T, OP_RESID, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
+        break;
+      case OP_JACOBI:
+        k_level_op2d_tiled<T, OP_JACOBI, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
+        break;
+      default:
+        k_level_op2d_tiled<T, OP_JACOBI0, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
+    }
+    const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    return launch_check();
+  }
   switch (mode) {
     case OP_APPLY:
       k_level_op<T, D, OP_APPLY, TR><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
