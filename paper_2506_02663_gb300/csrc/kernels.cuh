@@ -266,14 +266,13 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
   cell_level_op<T, D, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
 }
 
-// 2-D level operator, tiled: each thread computes ROWS consecutive cells of one column
+// 2-D level operator, tiled: each thread computes ROWS (1, 2 or 4; chosen per grid by the
+// autotuner) consecutive cells of one column
 // with 32-bit patch-local offsets and reuses the column loads.  A block whose whole tile
 // (plus the two-cell stencil reach) lies inside the domain takes the fast path with the
 // constant interior diagonal (omega / diag precomputed); any other block runs the generic
 // per-cell code.  Both paths sum in the same order (bit-identical results).
-constexpr int ROWS = 4;
-
-template <typename T, int MODE, bool TR>
+template <typename T, int MODE, bool TR, int ROWS>
 __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const T* __restrict__ x,
                                                              const T* __restrict__ f, T* __restrict__ out,
                                                              const T* __restrict__ bc, T alpha, T beta, T omega,
@@ -463,6 +462,69 @@ __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __res
   cell_restrict<T, D, RESID, TR>(fine, fine.patches[b.fpatch], crs.patches[b.cpatch], g, xf, ff, outc, alpha, beta);
 }
 
+// 2-D residual restriction, one thread per coarse cell: the four children's residuals
+// f - A x from one plus-shaped load of the fine neighbourhood (32-bit offsets) when the
+// block's children and their two-cell reach lie inside the domain; generic code otherwise.
+// Same summation order as cell_restrict / cell_Lx.
+template <typename T, bool TR>
+__global__ void __launch_bounds__(BX* BY) k_restrict2d_resid(LevelView fine, LevelView crs,
+                                                             const XferBlock* __restrict__ blocks,
+                                                             const T* __restrict__ xf, const T* __restrict__ ff,
+                                                             T* __restrict__ outc, T alpha, T beta) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  const int g[3] = {b.clo[0] + i, b.clo[1] + j, 0};
+  constexpr int M = TR ? 4 : 2;
+  const int c0 = b.clo[0] + blockIdx.x * BX, c1 = b.clo[1] + blockIdx.y * BY;
+  const bool full = c0 + BX - 1 <= b.chi[0] && c1 + BY - 1 <= b.chi[1];
+  const bool inside = 2 * c0 >= M && 2 * (c0 + BX) - 1 <= fine.ndom[0] - 1 - M && 2 * c1 >= M &&
+                      2 * (c1 + BY) - 1 <= fine.ndom[1] - 1 - M;
+  if (!(full && inside)) {
+    if (g[0] > b.chi[0] || g[1] > b.chi[1]) return;
+    cell_restrict<T, 2, true, TR>(fine, fp, cp, g, xf, ff, outc, alpha, beta);
+    return;
+  }
+  const T inv = pick<T>(fine.inv12h2, fine.inv12h2_f);
+  const T* __restrict__ xb = xf + fp.off;
+  const T* __restrict__ fb = ff + fp.off;
+  const int sy = (int)fp.sy;
+  const int o = (2 * g[1] - fp.lo[1] + NG) * sy + (2 * g[0] - fp.lo[0] + NG);
+  // rows 0 and 1 of the 2x2 block: columns -2..3 ; columns 0 and 1: rows -2, -1, 2, 3
+  T r0[6], r1[6], cu[2][2], cd[2][2];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    r0[q] = xb[o + q - 2];
+    r1[q] = xb[o + sy + q - 2];
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    cd[0][q] = xb[o - 2 * sy + q];
+    cd[1][q] = xb[o - sy + q];
+    cu[0][q] = xb[o + 2 * sy + q];
+    cu[1][q] = xb[o + 3 * sy + q];
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+    for (int q0 = 0; q0 < 2; ++q0) {
+      const T* row = q1 == 0 ? r0 : r1;
+      const T xc = row[q0 + 2];
+      const T ym1 = q1 == 0 ? cd[1][q0] : r0[q0 + 2];
+      const T yp1 = q1 == 0 ? r1[q0 + 2] : cu[0][q0];
+      const T ym2 = q1 == 0 ? cd[0][q0] : cd[1][q0];
+      const T yp2 = q1 == 0 ? cu[0][q0] : cu[1][q0];
+      const T s1 = (row[q0 + 1] + row[q0 + 3]) + (ym1 + yp1);
+      const T s2 = (row[q0] + row[q0 + 4]) + (ym2 + yp2);
+      const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
+      acc += fb[o + q1 * sy + q0] - (alpha * xc + beta * (lap * inv));
+    }
+  outc[poff(cp, g[0] - cp.lo[0], g[1] - cp.lo[1], 0)] = acc * T(0.25);
+}
+
 // Fine cell gf += cell-centred tensor linear interpolation of the coarse correction
 // (Sec. 6.4 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse values outside
 // the domain come from the homogeneous physical extension with corners.
@@ -513,6 +575,56 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
   const int gf[3] = {2 * b.clo[0] + i, 2 * b.clo[1] + j, D == 3 ? 2 * b.clo[2] + kk : 0};
   if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || (D == 3 && gf[2] > 2 * b.chi[2] + 1)) return;
   cell_prolong<T, D>(crs, fine.patches[b.fpatch], crs.patches[b.cpatch], gf, xc, xf, xf2);
+}
+
+// 2-D prolongation, one thread per coarse cell: its four children += linear interpolation
+// from the 3x3 coarse neighbourhood (32-bit offsets) when the neighbourhood lies inside the
+// domain and the patch; generic per-fine-cell code otherwise (same arithmetic).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong2d(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                                                      const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2) {
+  const XferBlock b = blocks[blockIdx.z];
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int g0 = b.clo[0] + i, g1 = b.clo[1] + j;
+  if (g0 > b.chi[0] || g1 > b.chi[1]) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  const bool inside = g0 - 1 >= cp.lo[0] && g0 + 1 <= cp.lo[0] + cp.n[0] - 1 && g1 - 1 >= cp.lo[1] &&
+                      g1 + 1 <= cp.lo[1] + cp.n[1] - 1;
+  if (!inside) {
+    for (int q1 = 0; q1 < 2; ++q1)
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const int gf[3] = {2 * g0 + q0, 2 * g1 + q1, 0};
+        cell_prolong<T, 2>(crs, fp, cp, gf, xc, xf, xf2);
+      }
+    return;
+  }
+  const T* __restrict__ cb = xc + cp.off;
+  const int csy = (int)cp.sy;
+  const int oc = (g1 - cp.lo[1] + NG) * csy + (g0 - cp.lo[0] + NG);
+  T c[3][3];
+#pragma unroll
+  for (int a1 = 0; a1 < 3; ++a1)
+#pragma unroll
+    for (int a0 = 0; a0 < 3; ++a0) c[a1][a0] = cb[oc + (a1 - 1) * csy + (a0 - 1)];
+  const int fsy = (int)fp.sy;
+  const long long of = fp.off + (long long)((2 * g1 - fp.lo[1] + NG) * fsy + (2 * g0 - fp.lo[0] + NG));
+#pragma unroll
+  for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+    for (int q0 = 0; q0 < 2; ++q0) {
+      const int s0 = q0 == 0 ? -1 : 1, s1 = q1 == 0 ? -1 : 1;
+      // corners in the generic order: (q0, q1) = (0,0), (1,0), (0,1), (1,1) over the parent
+      T v = T(0);
+      v += (T(0.75) * T(0.75)) * c[1][1];
+      v += (T(0.25) * T(0.75)) * c[1][1 + s0];
+      v += (T(0.75) * T(0.25)) * c[1 + s1][1];
+      v += (T(0.25) * T(0.25)) * c[1 + s1][1 + s0];
+      const long long o = of + q1 * fsy + q0;
+      xf[o] += v;
+      if (xf2 != nullptr) xf2[o] += v;
+    }
 }
 
 // ------------------------------------------------------------------------ fused coarse V-cycle
@@ -1009,6 +1121,46 @@ __global__ void k_wsum(LevelView lv, int nby, const double* __restrict__ x, cons
     const long long bid = base + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     part[2 * bid] = ss[0];
     part[2 * bid + 1] = sc[0];
+  }
+}
+
+// Grid-stride variant with a fixed number of blocks per level (deterministic: the cell
+// each thread visits depends only on the launch shape): partial part[2*(base+block)].
+template <int D>
+__global__ void __launch_bounds__(256) k_wsum_gs(LevelView lv, const double* __restrict__ x,
+                                                 const unsigned char* __restrict__ vmask, double w,
+                                                 double* __restrict__ part, long long base) {
+  __shared__ double ss[256], sc[256];
+  double s = 0.0, c = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int pi = 0; pi < lv.npatch; ++pi) {
+    const PatchDesc p = lv.patches[pi];
+    const long long n = (long long)p.n[0] * p.n[1] * p.n[2];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+      const int i = (int)(t % p.n[0]);
+      const int j = (int)((t / p.n[0]) % p.n[1]);
+      const int k = (int)(t / ((long long)p.n[0] * p.n[1]));
+      const long long o = poff(p, i, j, k);
+      if (vmask != nullptr && !vmask[o]) continue;
+      const double prod = w * x[o];
+      dd_add(s, c, prod, fma(w, x[o], -prod));
+    }
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      double a = ss[threadIdx.x], ac = sc[threadIdx.x];
+      dd_add(a, ac, ss[threadIdx.x + st], sc[threadIdx.x + st]);
+      ss[threadIdx.x] = a;
+      sc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * (base + blockIdx.x)] = ss[0];
+    part[2 * (base + blockIdx.x) + 1] = sc[0];
   }
 }
 

@@ -101,6 +101,23 @@ inline amr_status launch_check() {
   return AMR_OK;
 }
 
+// ---------------------------------------------------------------- tile autotuner
+// Rows per thread of the tiled 2-D kernel, per (grid cells, value size): filled by
+// autotune_tiles() (CUDA-event timing of each variant on the operator's own buffers), with
+// a size-based default before tuning.
+std::mutex g_tile_mu;
+std::vector<std::pair<long long, int>> g_tile_table;  // key = ncells * 16 + sizeof(T)
+
+inline int tile_rows_for(const LevelView& lv, size_t tsize) {
+  const long long key = (long long)lv.ncells * 16 + (long long)tsize;
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    for (const auto& e : g_tile_table)
+      if (e.first == key) return e.second;
+  }
+  return lv.ncells >= 1024.0 * 1024.0 ? 4 : 1;
+}
+
 template <typename T>
 inline T pick_host(double d, float f);
 template <>
@@ -268,24 +285,27 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
   cudaEvent_t ev;
   prof_begin(st, &ev);
   if (D == 2) {
-    // tiled 2-D path; omega / (interior diagonal) computed once here in the value type
+    // tiled 2-D path; omega / (interior diagonal) computed once here in the value type;
+    // rows per thread from the autotuner's table (keyed by grid size), default by size
     const T diag = T(alpha) + T(beta) * pick_host<T>(lv.inv12h2, lv.inv12h2_f) * T(-60);
     const T ood = T(omega) / diag;
-    dim3 grid((lv.maxn[0] + BX - 1) / BX, (lv.maxn[1] + BY * ROWS - 1) / (BY * ROWS), lv.npatch);
+    const int rows = tile_rows_for(lv, sizeof(T));
+    dim3 grid((lv.maxn[0] + BX - 1) / BX, (lv.maxn[1] + BY * rows - 1) / (BY * rows), lv.npatch);
     dim3 block(BX, BY, 1);
+    const T A = T(alpha), B = T(beta), O = T(omega);
+#define LAUNCH_TILED(M)                                                                                     \
+  do {                                                                                                      \
+    if (rows == 4) k_level_op2d_tiled<T, M, TR, 4><<<grid, block, 0, st>>>(lv, x, f, out, bc, A, B, O, ood, vmask); \
+    else if (rows == 2) k_level_op2d_tiled<T, M, TR, 2><<<grid, block, 0, st>>>(lv, x, f, out, bc, A, B, O, ood, vmask); \
+    else k_level_op2d_tiled<T, M, TR, 1><<<grid, block, 0, st>>>(lv, x, f, out, bc, A, B, O, ood, vmask); \
+  } while (0)
     switch (mode) {
-      case OP_APPLY:
-        k_level_op2d_tiled<T, OP_APPLY, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
-        break;
-      case OP_RESID:
-        k_level_op2d_tiled<T, OP_RESID, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
-        break;
-      case OP_JACOBI:
-        k_level_op2d_tiled<T, OP_JACOBI, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
-        break;
-      default:
-        k_level_op2d_tiled<T, OP_JACOBI0, TR><<<grid, block, 0, st>>>(lv, x, f, out, bc, T(alpha), T(beta), T(omega), ood, vmask);
+      case OP_APPLY: LAUNCH_TILED(OP_APPLY); break;
+      case OP_RESID: LAUNCH_TILED(OP_RESID); break;
+      case OP_JACOBI: LAUNCH_TILED(OP_JACOBI); break;
+      default: LAUNCH_TILED(OP_JACOBI0);
     }
+#undef LAUNCH_TILED
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
     prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
     return launch_check();
@@ -320,7 +340,9 @@ amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const Xf
   dim3 block(BX, BY, 1);
   cudaEvent_t ev;
   prof_begin(st, &ev);
-  if (resid)
+  if (resid && D == 2)
+    k_restrict2d_resid<T, TR><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta));
+  else if (resid)
     k_restrict<T, D, true, TR><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
   else
     k_restrict<T, D, false><<<grid, block, 0, st>>>(fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
@@ -333,13 +355,17 @@ template <typename T, int D>
 amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const XferBlock* blocks, int nblocks,
                           const int xmax[3], const T* xc, T* xf, T* xf2, cudaStream_t st) {
   if (nblocks == 0) return AMR_OK;
-  const int fy = 2 * xmax[1];
-  const int nby = (fy + BY - 1) / BY;
-  dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
-  dim3 block(BX, BY, 1);
   cudaEvent_t ev;
   prof_begin(st, &ev);
-  k_prolong<T, D><<<grid, block, 0, st>>>(fine, crs, blocks, xc, xf, xf2, nby);
+  if (D == 2) {
+    dim3 grid((xmax[0] + BX - 1) / BX, (xmax[1] + BY - 1) / BY, nblocks);
+    k_prolong2d<T><<<grid, dim3(BX, BY, 1), 0, st>>>(fine, crs, blocks, xc, xf, xf2);
+  } else {
+    const int fy = 2 * xmax[1];
+    const int nby = (fy + BY - 1) / BY;
+    dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
+    k_prolong<T, D><<<grid, dim3(BX, BY, 1), 0, st>>>(fine, crs, blocks, xc, xf, xf2, nby);
+  }
   const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
   prof_end(st, ev, PC_PROLONG, (1.0 + (1 << D) * (xf2 ? 4.0 : 2.0)) * sizeof(T) * cc);
   return launch_check();
@@ -469,6 +495,9 @@ Scratch<double>& scratch<double>(amr_operator* op) { return op->s64; }
 template <>
 Scratch<float>& scratch<float>(amr_operator* op) { return op->s32; }
 
+template <typename T, int D>
+amr_status autotune_tiles(amr_operator* op, cudaStream_t st);
+
 template <typename T>
 amr_status ensure_scratch(amr_operator* op) {
   Scratch<T>& S = scratch<T>(op);
@@ -506,6 +535,8 @@ amr_status ensure_scratch(amr_operator* op) {
     CK(cudaMemset(S.mt[m], 0, q * sizeof(T)));
   }
   S.ready = true;
+  // choose the tiled kernel's rows per thread for every grid this operator smooths
+  if (op->h->D == 2) TRY((autotune_tiles<T, 2>(op, 0)));
   return AMR_OK;
 }
 
@@ -517,6 +548,57 @@ void free_scratch(Scratch<T>& S) {
   for (auto p : S.mb) cudaFree(p);
   for (auto p : S.mt) cudaFree(p);
   S = Scratch<T>();
+}
+
+template <typename T, int D>
+amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
+  if (D != 2) return AMR_OK;
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  std::vector<std::pair<LevelView, std::pair<T*, T*>>> cases;
+  for (int l = 0; l < h->L; ++l) cases.push_back({level_view(h, l, op->bc), {S.T1, S.T2}});
+  for (size_t m = 1; m < h->mg.size(); ++m) cases.push_back({mg_view(h, (int)m, op->bc), {S.mx[m], S.mt[m]}});
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (auto& c : cases) {
+    const LevelView& lv = c.first;
+    const long long key = (long long)lv.ncells * 16 + (long long)sizeof(T);
+    {
+      std::lock_guard<std::mutex> lock(g_tile_mu);
+      bool known = false;
+      for (const auto& e : g_tile_table) known = known || e.first == key;
+      if (known) continue;
+    }
+    float best = 1e30f;
+    int best_rows = 1;
+    for (int rows : {1, 2, 4}) {
+      {
+        std::lock_guard<std::mutex> lock(g_tile_mu);
+        g_tile_table.push_back({key, rows});
+      }
+      for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
+        CK(cudaEventRecord(a, st));
+        for (int it = 0; it < 4; ++it)
+          TRY((level_op<T, D>(OP_JACOBI, lv, c.second.first, c.second.first, c.second.second, nullptr, op->alpha,
+                              op->beta, 2.0 / 3.0, nullptr, st)));
+        CK(cudaEventRecord(b, st));
+      }
+      CK(cudaEventSynchronize(b));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      {
+        std::lock_guard<std::mutex> lock(g_tile_mu);
+        g_tile_table.pop_back();
+      }
+      if (ms < best) { best = ms; best_rows = rows; }
+    }
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tile_table.push_back({key, best_rows});
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return AMR_OK;
 }
 
 // ---------------------------------------------------------------- smoothing
@@ -988,13 +1070,12 @@ amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* 
   long long base = 0;
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, nullptr);
-    Geo g = geo_of(lv);
-    const long long nb = (long long)g.grid.x * g.grid.y * g.grid.z;
+    const long long nb = std::min<long long>(512, std::max<long long>(1, ((long long)lv.ncells + 255) / 256));
     if (base + nb > 8192) {
       set_error("reduction scratch too small");
       return AMR_ERR_INVALID_ARG;
     }
-    k_wsum<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, h->d_valid, std::pow(lv.h, D), h->d_red, base);
+    k_wsum_gs<D><<<(unsigned)nb, 256, 0, st>>>(lv, x, h->d_valid, std::pow(lv.h, D), h->d_red, base);
     TRY(launch_check());
     base += nb;
   }
