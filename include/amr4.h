@@ -276,10 +276,37 @@ amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, v
  * between levels, FP64 outer residual (precision as in amr_solve).  Values of g on invalid
  * cells are first handed to their children (transposed average-down), so that a gradient
  * with respect to a composite field whose invalid cells are averages is propagated
- * correctly; ghost cells of g are ignored; lambda's invalid cells are set to 0.  Not
- * provided for the singular pure-Neumann operator (AMR_ERR_INVALID_ARG). */
+ * correctly; ghost cells of g are ignored; lambda's invalid cells are set to 0.
+ * Pure-Neumann operator (alpha = 0, every face Neumann): the adjoint of the whole solve map
+ * of amr_solve (Sec. 6.3 solvability correction, solve, h^D-weighted mean zero).  With
+ * w = h^D on the valid cells it returns the lambda with A^T lambda = g - w (1^T g)/(1^T w)
+ * and 1^T lambda = 0 (the null vectors of A are 1 on the right and w on the left);
+ * stats->removed_mean receives (1^T g)/(1^T w). */
 amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, double* lambda,
                                const double* g, amr_solve_stats* stats, void* stream);
+
+/* out = (G^comp)^T y: the adjoint of amr_gradient's linear part (homogeneous boundary data,
+ * ghosts of types bc_types).  y: dim device composite fields; weight on their invalid cells
+ * (where G^comp's output is the average of the children, COH-4) is handed to the children
+ * first.  out (device composite field) receives values on the valid cells and 0 on the
+ * invalid cells; its ghost cells are scratch.  Uses a hierarchy-owned scratch of three
+ * fields (allocated on the first call): calls on one hierarchy must not overlap. */
+amr_status amr_gradient_transpose(amr_hierarchy* h, const int* bc_types, const double* const* y, double* out,
+                                  void* stream);
+/* out[d] = the component-d part of (D^comp)^T y (adjoint of amr_divergence's linear part,
+ * including the transposed refluxing of the face values of Eq. cell2face).  Same
+ * conventions as amr_gradient_transpose. */
+amr_status amr_divergence_transpose(amr_hierarchy* h, const int* bc_types, const double* y, double* const* out,
+                                    void* stream);
+/* out = P^T v: the adjoint of amr_project's linear map w -> u (homogeneous w_bc), as a map
+ * on the covered cells of every level of each of the dim components: u_d reads w_d itself
+ * on every cell and, on the valid cells, through G^comp (L^comp)^{-1} D^comp.  Hence
+ * out_d = v_d - (D^comp)^T lambda with lambda = M^T (G^comp)^T v, M the pure-Neumann solve
+ * map (amr_solve_transpose).  lambda (device composite field) receives that adjoint
+ * potential.  ppe as for amr_project; p controls the adjoint solve. */
+amr_status amr_project_transpose(amr_operator* ppe, const amr_solver_params* p, const int* vel_bc_types,
+                                 const double* const* v, double* const* out, double* lambda,
+                                 amr_solve_stats* stats, void* stream);
 
 /* Batched solves: n independent problems (each with its own operator; hierarchies may
  * differ, e.g. the uneven sizes of a batch of single-level Helmholtz problems), each solved

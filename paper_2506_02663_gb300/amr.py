@@ -84,6 +84,9 @@ _sigs = {
     "amr_project": [_vp, _P(SolverParams), _P(C.c_int), _P(_vp), _P(_vp), _P(_vp), _vp, _P(SolveStats), _vp],
     "amr_apply_transpose": [_vp, _vp, _vp, _vp],
     "amr_solve_transpose": [_vp, _P(SolverParams), _vp, _vp, _P(SolveStats), _vp],
+    "amr_gradient_transpose": [_vp, _P(C.c_int), _P(_vp), _vp, _vp],
+    "amr_divergence_transpose": [_vp, _P(C.c_int), _vp, _P(_vp), _vp],
+    "amr_project_transpose": [_vp, _P(SolverParams), _P(C.c_int), _P(_vp), _P(_vp), _vp, _P(SolveStats), _vp],
     "amr_default_params": [_P(SolverParams)],
     "amr_last_error": [],
     "amr_kernel_launches": [],
@@ -414,6 +417,30 @@ def divergence(hier, bc_types, u, out, bc=None, stream=None):
     bt = (C.c_int * len(bc_types))(*bc_types)
     bcp = None if bc is None else _ptr_array(bc)
     _check(_lib.amr_divergence(hier.handle, bt, _ptr_array(u), _ptr(out), bcp, _stream(stream)), "amr_divergence")
+
+
+def gradient_transpose(hier, bc_types, y, out, stream=None):
+    """amr_gradient_transpose: out = (G^comp)^T y (y: dim fields)."""
+    bt = (C.c_int * len(bc_types))(*bc_types)
+    _check(_lib.amr_gradient_transpose(hier.handle, bt, _ptr_array(y), _ptr(out), _stream(stream)),
+           "amr_gradient_transpose")
+
+
+def divergence_transpose(hier, bc_types, y, out, stream=None):
+    """amr_divergence_transpose: out[d] = component d of (D^comp)^T y."""
+    bt = (C.c_int * len(bc_types))(*bc_types)
+    _check(_lib.amr_divergence_transpose(hier.handle, bt, _ptr(y), _ptr_array(out), _stream(stream)),
+           "amr_divergence_transpose")
+
+
+def project_transpose(ppe, vel_bc_types, v, out, lam, params=None, stream=None):
+    """amr_project_transpose: out = P^T v; lam receives the adjoint potential."""
+    p = params or default_params()
+    s = SolveStats()
+    bt = (C.c_int * len(vel_bc_types))(*vel_bc_types)
+    _check(_lib.amr_project_transpose(ppe._op, C.byref(p), bt, _ptr_array(v), _ptr_array(out), _ptr(lam),
+                                      C.byref(s), _stream(stream)), "amr_project_transpose")
+    return stats_dict(s)
 
 
 def project(ppe, vel_bc_types, w, u, phi, w_bc=None, params=None, stream=None):

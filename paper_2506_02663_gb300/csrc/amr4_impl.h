@@ -150,6 +150,8 @@ struct amr_hierarchy {
   double* d_red = nullptr;       // partials
   double* d_scalar = nullptr;    // a few device scalars
   double* h_scalar = nullptr;    // pinned host mirror
+  double* d_tz = nullptr;        // G/D transposes: 3 composite fields (allocated on first use)
+  bool cfi_const_ready = false;  // AMRCFI weights copied to the device constant banks
   bool on_device = false;
 };
 

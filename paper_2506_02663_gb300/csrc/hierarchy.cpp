@@ -602,6 +602,7 @@ void free_hierarchy(amr_hierarchy* h) {
   cudaFree(h->d_valid);
   cudaFree(h->d_red);
   cudaFree(h->d_scalar);
+  cudaFree(h->d_tz);
   if (h->h_scalar) cudaFreeHost(h->h_scalar);
 }
 

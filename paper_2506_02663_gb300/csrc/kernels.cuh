@@ -755,9 +755,45 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __rest
 //                the ghost's 5^D coarse window with the interpolation weights (atomic adds);
 //   k_avgdown_T  transposed average-down: invalid coarse cells hand 1/2^D of their weight
 //                to each child (applied coarse to fine).
+template <typename T>
+struct Out3 {
+  T* p[3];
+};
+template <typename T>
+struct P3c {
+  const T* p[3];
+};
+
+// W[x] += wgt for a read of x at patch-local cell c by a stencil along d.  A read outside the
+// domain was a physical ghost (Eqs. velBCHomoDiri5th / Neumann5, homogeneous part): its
+// weight goes to the four interior cells the ghost formula combines.  Reads of copy or CF
+// ghost slots land in those slots (moved on by k_copy_T / k_cfi_T).
+template <typename T, int D>
+__device__ __forceinline__ void scatter_read(T* __restrict__ W, const PatchDesc& p, const LevelView& lv, const int* c,
+                                             int d, T wgt) {
+  const int g = p.lo[d] + c[d];
+  if (g >= 0 && g < lv.ndom[d]) {
+    atomicAdd(&W[poff(p, c[0], c[1], c[2])], wgt);
+    return;
+  }
+  const int gs = g < 0 ? 0 : 1;
+  const int layer = gs == 0 ? -g : g - lv.ndom[d] + 1;
+  const int type = lv.bc[2 * d + gs];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    int c2[3] = {c[0], c[1], c[2]};
+    c2[d] = gs == 0 ? (m - p.lo[d]) : (lv.ndom[d] - 1 - m - p.lo[d]);
+    atomicAdd(&W[poff(p, c2[0], c2[1], c2[2])], gcoef<T>(type, layer - 1, m) * wgt);
+  }
+}
+
+// Transposed refluxing (COH-3).  kind 0: Laplacian fluxes (face derivative, one field, all
+// W.p[] equal); kind 1: divergence fluxes (face values of component d into W.p[d]).  The
+// forward correction is out[c] += coef/hc * sum_faces s (Fbar/hf' - Fc/hc') with hf' = hf,
+// hc' = hc for derivatives and 1 for values.
 template <typename T, int D>
 __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
-                           const T* __restrict__ z, T* __restrict__ W, T beta) {
+                           const T* __restrict__ z, Out3<T> W, T coef, int kind) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const RefluxEntry e = list[t];
@@ -765,36 +801,27 @@ __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __r
   if (zc == T(0)) return;
   const PatchDesc cp = crs.patches[e.cpatch];
   const T fd[4] = {T(1.0 / 12.0), T(-15.0 / 12.0), T(15.0 / 12.0), T(-1.0 / 12.0)};
+  const T fv[4] = {T(-1.0 / 12.0), T(7.0 / 12.0), T(7.0 / 12.0), T(-1.0 / 12.0)};
+  const T* fc = kind == 0 ? fd : fv;
   const T hc = pick<T>(crs.hd, crs.hf), hf = pick<T>(fine.hd, fine.hf);
-  const long long st[3] = {1, cp.sy, cp.sz};
+  const T a = coef * zc / hc;
+  const T hck = kind == 0 ? hc : T(1), hfk = kind == 0 ? hf : T(1);
   for (int d = 0; d < D; ++d)
     for (int side = 0; side < 2; ++side) {
       if (!(e.faces & (1 << (2 * d + side)))) continue;
+      T* Wd = W.p[kind == 0 ? 0 : d];
       const T s = T(side == 1 ? 1 : -1);
       int own[3] = {e.g[0] - cp.lo[0], e.g[1] - cp.lo[1], e.g[2] - cp.lo[2]};
       if (side == 0) own[d] -= 1;
       for (int q = 0; q < 4; ++q) {
         int cc[3] = {own[0], own[1], own[2]};
         cc[d] += q - 1;
-        const T wgt = -beta * s * fd[q] * zc / (hc * hc);
-        const int g = cp.lo[d] + cc[d];
-        if (g >= 0 && g < crs.ndom[d]) {
-          atomicAdd(&W[poff(cp, cc[0], cc[1], cc[2])], wgt);
-        } else {
-          const int gs = g < 0 ? 0 : 1;
-          const int layer = gs == 0 ? -g : g - crs.ndom[d] + 1;
-          const int type = crs.bc[2 * d + gs];
-          for (int m = 0; m < 4; ++m) {
-            int c2[3] = {cc[0], cc[1], cc[2]};
-            c2[d] = gs == 0 ? (m - cp.lo[d]) : (crs.ndom[d] - 1 - m - cp.lo[d]);
-            atomicAdd(&W[poff(cp, c2[0], c2[1], c2[2])], gcoef<T>(type, layer - 1, m) * wgt);
-          }
-        }
+        scatter_read<T, D>(Wd, cp, crs, cc, d, -a * s * fc[q] / hck);
       }
       const PatchDesc fp = fine.patches[e.fpatch[2 * d + side]];
       const int e1 = (d == 0) ? 1 : 0;
       const int e2 = (d == 2) ? 1 : 2;
-      const T fw = beta * s * zc / (T(D == 3 ? 4 : 2) * hf * hc);
+      const T fw = a * s / (T(D == 3 ? 4 : 2) * hfk);
       for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
         for (int t1 = 0; t1 < 2; ++t1) {
           int gf[3] = {0, 0, 0};
@@ -804,10 +831,59 @@ __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __r
           for (int q = 0; q < 4; ++q) {
             int cc[3] = {gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]};
             cc[d] += q - 1;
-            atomicAdd(&W[poff(fp, cc[0], cc[1], cc[2])], fd[q] * fw);
+            atomicAdd(&Wd[poff(fp, cc[0], cc[1], cc[2])], fc[q] * fw);
           }
         }
-      (void)st;
+    }
+}
+
+// Transposed G^comp stencil (Eq. discreteOps a): each valid cell o hands z_d[o]/(12h) times
+// the weights (+1, -8, +8, -1) at offsets (-2, -1, +1, +2) along d to the cells it read.
+template <typename T, int D>
+__global__ void k_gradient_T(LevelView lv, int nby, P3c<T> z, const unsigned char* __restrict__ vmask,
+                             T* __restrict__ W) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (!vmask[o]) return;
+  const T inv = pick<T>(lv.inv12h, lv.inv12h_f);
+  const int c[3] = {i, j, k};
+  const T wq[4] = {T(1), T(-8), T(8), T(-1)};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const T a = z.p[d][o] * inv;
+    if (a == T(0)) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] += q < 2 ? q - 2 : q - 1;
+      scatter_read<T, D>(W, p, lv, cc, d, wq[q] * a);
+    }
+  }
+}
+
+// Transposed D^comp stencil (Eq. discreteOps b): each valid cell hands z[o]/(12h) times the
+// same weights to component d's cells along d.
+template <typename T, int D>
+__global__ void k_divergence_T(LevelView lv, int nby, const T* __restrict__ z, const unsigned char* __restrict__ vmask,
+                               Out3<T> W) {
+  const PatchDesc p = lv.patches[blockIdx.z];
+  int i, j, k;
+  if (!thread_cell<D>(p, nby, i, j, k)) return;
+  const long long o = poff(p, i, j, k);
+  if (!vmask[o]) return;
+  const T a = z[o] * pick<T>(lv.inv12h, lv.inv12h_f);
+  if (a == T(0)) return;
+  const int c[3] = {i, j, k};
+  const T wq[4] = {T(1), T(-8), T(8), T(-1)};
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] += q < 2 ? q - 2 : q - 1;
+      scatter_read<T, D>(W.p[d], p, lv, cc, d, wq[q] * a);
     }
 }
 

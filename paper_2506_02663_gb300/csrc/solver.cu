@@ -766,7 +766,8 @@ amr_status composite_AT(amr_operator* op, const T* x, cudaStream_t st, int only_
     const DeviceLists& dl = h->lev[l].dev;
     if (dl.nreflux == 0) continue;
     k_reflux_T<T, D><<<(unsigned)((dl.nreflux + nt - 1) / nt), nt, 0, st>>>(
-        level_view(h, l, op->bc), level_view(h, l + 1, op->bc), dl.reflux, dl.nreflux, S.Z, S.W, T(op->beta));
+        level_view(h, l, op->bc), level_view(h, l + 1, op->bc), dl.reflux, dl.nreflux, S.Z, Out3<T>{{S.W, S.W, S.W}},
+        T(op->beta), 0);
     TRY(launch_check());
   }
   for (int l = 0; l < h->L; ++l) {
@@ -1066,7 +1067,7 @@ amr_status maxnorm(amr_hierarchy* h, const T* x, bool use_mask, double* out_host
 // d_out[0] = sum over valid cells of h^D x (compensated); d_out[1] = boundary flux sum
 template <int D>
 amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* bc_types, double* d_out,
-                cudaStream_t st) {
+                cudaStream_t st, bool unweighted = false) {
   long long base = 0;
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, nullptr);
@@ -1075,7 +1076,7 @@ amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* 
       set_error("reduction scratch too small");
       return AMR_ERR_INVALID_ARG;
     }
-    k_wsum_gs<D><<<(unsigned)nb, 256, 0, st>>>(lv, x, h->d_valid, std::pow(lv.h, D), h->d_red, base);
+    k_wsum_gs<D><<<(unsigned)nb, 256, 0, st>>>(lv, x, h->d_valid, unweighted ? 1.0 : std::pow(lv.h, D), h->d_red, base);
     TRY(launch_check());
     base += nb;
   }
@@ -1151,6 +1152,28 @@ amr_status mean_zero_impl(amr_hierarchy* h, double* x, double* mean_host, cudaSt
     CK(cudaMemcpyAsync(h->h_scalar + 4, h->d_scalar + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *mean_host = h->h_scalar[4];
+  }
+  return AMR_OK;
+}
+
+// Transpose of the pure-Neumann projector F = I - 1 w^T/(w^T 1) (w = h^D on valid cells; F
+// is both the solvability correction of Sec. 6.3 with homogeneous data and the mean-zero
+// step): x <- x - w (1^T x)/(1^T w) on the valid cells.
+template <int D>
+amr_status neumann_fix_T(amr_hierarchy* h, double* x, double* m_host, cudaStream_t st) {
+  TRY(wsum<D>(h, x, nullptr, nullptr, h->d_scalar + 2, st, true));
+  k_mean_from_sums<<<1, 1, 0, st>>>(h->d_scalar + 2, nullptr, 0.0, valid_volume(h), h->d_scalar + 4);
+  TRY(launch_check());
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    k_shift<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, x, h->d_scalar + 4, h->d_valid, -std::pow(lv.h, D));
+    TRY(launch_check());
+  }
+  if (m_host) {
+    CK(cudaMemcpyAsync(h->h_scalar + 4, h->d_scalar + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *m_host = h->h_scalar[4];
   }
   return AMR_OK;
 }
@@ -1443,6 +1466,9 @@ amr_status solve_transpose_impl(amr_operator* op, const amr_solver_params& p, do
     TRY(launch_check());
   }
   g = op->F;
+  // pure Neumann: lambda = B^T g with B the bordered solve (solvability correction, solve,
+  // mean zero); A^T lambda = F^T g and 1^T lambda = 0 (F^T again at the end)
+  if (op->neumann) TRY(neumann_fix_T<D>(h, op->F, &loc.removed_mean, st));
   double gn = 0.0;
   TRY((maxnorm<double, D>(h, g, true, &gn, st)));
   loc.rhs_norm = gn;
@@ -1468,6 +1494,7 @@ amr_status solve_transpose_impl(amr_operator* op, const amr_solver_params& p, do
       for (int l = 0; l < h->L; ++l) TRY((axpy<double, double, D>(level_view(h, l, nullptr), op->s64.X, lam, (double*)nullptr, 1.0, st)));
     }
   }
+  if (op->neumann) TRY(neumann_fix_T<D>(h, lam, nullptr, st));
   // the adjoint unknowns live on valid cells: zero the invalid ones
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, nullptr);
@@ -1566,6 +1593,132 @@ amr_status project_impl(amr_operator* ppe, const amr_solver_params& p, const int
   return AMR_OK;
 }
 
+// ---------------------------------------------------------------- adjoints of G, D, projection
+template <int D>
+amr_status ensure_tz(amr_hierarchy* h) {
+  if (h->d_tz) return AMR_OK;
+  return dalloc(&h->d_tz, (size_t)3 * h->nelems);
+}
+
+// Weight on invalid cells of x (outputs of maps that end with an average-down) handed to the
+// children, coarse to fine: x <- E^T x in place (invalid entries keep their value).
+template <int D>
+amr_status avgdown_T_all(amr_hierarchy* h, double* x, cudaStream_t st) {
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.nxfer == 0) continue;
+    int nby;
+    Geo g = xfer_geo<double, D>(dl, true, nby);
+    k_avgdown_T<double, D><<<g.grid, dim3(BX, BY, 1), 0, st>>>(level_view(h, l + 1, nullptr), level_view(h, l, nullptr),
+                                                             dl.xfer, x, nby);
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+// Adjoints of the ghost fill (COH-1) on a weight field W whose ghost slots hold the weight
+// that stencils put on ghost values: copy ghosts -> their sibling cells, CF ghosts -> their
+// AMRCFI windows (fine to coarse), then invalid cells -> children (the average-down that
+// precedes the ghost fill), then W <- 0 on invalid cells.
+template <int D>
+amr_status ghost_fill_T(amr_hierarchy* h, double* W, cudaStream_t st) {
+  const int nt = 128;
+  for (int l = 0; l < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.ncopy == 0) continue;
+    k_copy_T<double><<<(unsigned)((dl.ncopy + nt - 1) / nt), nt, 0, st>>>(dl.copy, dl.ncopy, W);
+    TRY(launch_check());
+  }
+  for (int l = h->L - 1; l >= 1; --l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.ncfi == 0) continue;
+    k_cfi_T<double, D><<<(unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st>>>(
+        dl.cfi, dl.ncfi, dl.cfi_side, h->lev[l - 1].d_patches, h->lev[l].d_patches, h->r, W, W, W, 0.0, 1.0);
+    TRY(launch_check());
+  }
+  TRY(avgdown_T_all<D>(h, W, st));
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, nullptr);
+    Geo g = geo_of(lv);
+    k_valid_out<double, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, W, (const double*)nullptr, W, h->d_valid);
+    TRY(launch_check());
+  }
+  return AMR_OK;
+}
+
+// out = (G^comp)^T y (sum over components; y's invalid weights handed to children first)
+template <int D>
+amr_status gradient_T_impl(amr_hierarchy* h, const int* bct, const double* const* y, double* out, cudaStream_t st) {
+  TRY(ensure_tz<D>(h));
+  const size_t n = (size_t)h->nelems;
+  double* Z[3] = {h->d_tz, h->d_tz + n, h->d_tz + 2 * n};
+  for (int d = 0; d < D; ++d) {
+    CK(cudaMemcpyAsync(Z[d], y[d], n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(avgdown_T_all<D>(h, Z[d], st));
+  }
+  CK(cudaMemsetAsync(out, 0, n * sizeof(double), st));
+  P3c<double> zp{{Z[0], Z[1], Z[2]}};
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, bct);
+    Geo g = geo_of(lv);
+    k_gradient_T<double, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, zp, h->d_valid, out);
+    TRY(launch_check());
+  }
+  return ghost_fill_T<D>(h, out, st);
+}
+
+// out[d] = (D^comp)^T y restricted to component d (y's invalid weights handed down first)
+template <int D>
+amr_status divergence_T_impl(amr_hierarchy* h, const int* bct, const double* y, double* const* out, cudaStream_t st) {
+  TRY(ensure_tz<D>(h));
+  const size_t n = (size_t)h->nelems;
+  double* Z = h->d_tz;
+  CK(cudaMemcpyAsync(Z, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(avgdown_T_all<D>(h, Z, st));
+  for (int d = 0; d < D; ++d) CK(cudaMemsetAsync(out[d], 0, n * sizeof(double), st));
+  Out3<double> W{{out[0], out[1], D == 3 ? out[2] : out[1]}};
+  for (int l = 0; l < h->L; ++l) {
+    LevelView lv = level_view(h, l, bct);
+    Geo g = geo_of(lv);
+    k_divergence_T<double, D><<<g.grid, g.block, 0, st>>>(lv, g.nby, Z, h->d_valid, W);
+    TRY(launch_check());
+  }
+  const int nt = 128;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DeviceLists& dl = h->lev[l].dev;
+    if (dl.nreflux == 0) continue;
+    k_reflux_T<double, D><<<(unsigned)((dl.nreflux + nt - 1) / nt), nt, 0, st>>>(
+        level_view(h, l, bct), level_view(h, l + 1, bct), dl.reflux, dl.nreflux, Z, W, 1.0, 1);
+    TRY(launch_check());
+  }
+  for (int d = 0; d < D; ++d) TRY(ghost_fill_T<D>(h, out[d], st));
+  return AMR_OK;
+}
+
+// out = P^T v for the composite projection u = w - G^comp phi, phi = M D^comp w:
+// s = G^T v, lambda = M^T s (adjoint pure-Neumann solve), out_d = v_d - (D^T lambda)_d
+// (D^T lambda is 0 on invalid cells, where u_d reads w_d directly).
+template <int D>
+amr_status project_T_impl(amr_operator* ppe, const amr_solver_params& p, const int* vbc, const double* const* v,
+                          double* const* out, double* lam, amr_solve_stats* stats, cudaStream_t st) {
+  amr_hierarchy* h = ppe->h;
+  TRY(ensure_scratch<double>(ppe));
+  TRY(gradient_T_impl<D>(h, ppe->bc, v, ppe->Tmp, st));
+  amr_solver_params q = p;
+  q.zero_initial = 1;
+  amr_status s = solve_transpose_impl<D>(ppe, q, lam, ppe->Tmp, stats, st);
+  if (s != AMR_OK) return s;
+  TRY(divergence_T_impl<D>(h, vbc, lam, out, st));
+  for (int d = 0; d < D; ++d)
+    for (int l = 0; l < h->L; ++l) {
+      LevelView lv = level_view(h, l, nullptr);
+      Geo g = geo_of(lv);
+      k_sub<D><<<g.grid, g.block, 0, st>>>(lv, g.nby, v[d], out[d], out[d]);
+      TRY(launch_check());
+    }
+  return AMR_OK;
+}
+
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
@@ -1659,8 +1812,19 @@ static amr_status check_op(amr_operator* op) {
 static amr_status ensure_device(amr_hierarchy* h) {
   std::string err;
   amr_status s = upload_hierarchy(h, err);
-  if (s != AMR_OK) set_error(err);
-  return s;
+  if (s != AMR_OK) {
+    set_error(err);
+    return s;
+  }
+  if (!h->cfi_const_ready) {
+    // AMRCFI weights (ratio 2) into this device's constant banks: every entry point that
+    // fills CF ghosts (operators, G, D and their transposes) comes through here first
+    CK(cudaMemcpyToSymbol(c_cfi, h->cfi_w.data(), h->cfi_w.size() * sizeof(double)));
+    std::vector<float> wf(h->cfi_w.begin(), h->cfi_w.end());
+    CK(cudaMemcpyToSymbol(c_cfi_f, wf.data(), wf.size() * sizeof(float)));
+    h->cfi_const_ready = true;
+  }
+  return AMR_OK;
 }
 
 extern "C" {
@@ -1794,12 +1958,6 @@ amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, cons
   for (int f = 0; f < 6; ++f) op->bc[f] = f < 2 * h->D ? bc_types[f] : 0;
   for (int f = 0; f < 2 * h->D; ++f) alln = alln && bc_types[f] == AMR_BC_NEUMANN;
   op->neumann = alln && alpha == 0.0;
-  // AMRCFI weights for ratio 2
-  CK(cudaMemcpyToSymbol(c_cfi, h->cfi_w.data(), h->cfi_w.size() * sizeof(double)));
-  {
-    std::vector<float> wf(h->cfi_w.begin(), h->cfi_w.end());
-    CK(cudaMemcpyToSymbol(c_cfi_f, wf.data(), wf.size() * sizeof(float)));
-  }
   // dense bottom inverse on the coarsest level-0 multigrid grid
   const MgGrid& g = h->mg.back();
   const int n = g.n[0] * g.n[1] * g.n[2];
@@ -2069,11 +2227,37 @@ amr_status amr_solve_transpose(amr_operator* op, const amr_solver_params* p, dou
   TRY(check_op(op));
   TRY(check_params(p));
   if (!lambda || !g) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
-  if (op->neumann) {
-    set_error("amr_solve_transpose: the pure-Neumann operator is singular; its adjoint solve is not provided");
-    return AMR_ERR_INVALID_ARG;
-  }
   return DISPATCH(op->h, solve_transpose_impl, op, *p, lambda, g, stats, S(stream));
+}
+
+amr_status amr_gradient_transpose(amr_hierarchy* h, const int* bc_types, const double* const* y, double* out,
+                                  void* stream) {
+  if (!h || !bc_types || !y || !out) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  for (int d = 0; d < h->D; ++d)
+    if (!y[d]) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  return DISPATCH(h, gradient_T_impl, h, bc_types, y, out, S(stream));
+}
+
+amr_status amr_divergence_transpose(amr_hierarchy* h, const int* bc_types, const double* y, double* const* out,
+                                    void* stream) {
+  if (!h || !bc_types || !y || !out) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  for (int d = 0; d < h->D; ++d)
+    if (!out[d]) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  return DISPATCH(h, divergence_T_impl, h, bc_types, y, out, S(stream));
+}
+
+amr_status amr_project_transpose(amr_operator* ppe, const amr_solver_params* p, const int* vel_bc_types,
+                                 const double* const* v, double* const* out, double* lambda, amr_solve_stats* stats,
+                                 void* stream) {
+  TRY(check_op(ppe));
+  TRY(check_params(p));
+  if (!ppe->neumann) { set_error("projection needs the pure-Neumann PPE operator"); return AMR_ERR_INVALID_ARG; }
+  if (!vel_bc_types || !v || !out || !lambda) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  for (int d = 0; d < ppe->h->D; ++d)
+    if (!v[d] || !out[d]) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
+  return DISPATCH(ppe->h, project_T_impl, ppe, *p, vel_bc_types, v, out, lambda, stats, S(stream));
 }
 
 }  // extern "C"
