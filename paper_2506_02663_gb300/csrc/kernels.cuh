@@ -627,6 +627,171 @@ __global__ void __launch_bounds__(BX* BY) k_prolong2d(LevelView fine, LevelView 
     }
 }
 
+// ------------------------------------------------------------------------ temporally blocked 2-D smoothing
+// One block owns a tile of a single-patch 2-D grid and keeps a region (the tile plus a halo,
+// clipped to the patch) in shared memory with the global patch's own index map (interior
+// plus two ghost layers, lo = the region's global origin).  The per-cell code is the same as
+// the standalone kernels' (cell_level_op, cell_restrict, cell_prolong): physical ghosts are
+// evaluated from the region's own cells (the region reaches the domain face whenever a
+// stencil does), and reads past a region edge that is not a domain face see the zeroed ghost
+// slots.  At a patch edge that is not a domain face those zeros are exactly the zero CF
+// ghosts of correction smoothing; at an edge interior to the patch the values they spoil
+// move inward two cells per sweep, and the halo keeps them out of the tile: 2 nu cells for nu
+// sweeps, 2 more for the residual.  Sweep s (from 1) updates the region shrunk by 2 s on
+// every side that is not a patch face.
+struct TileGeom {
+  int i0, j0;      // tile origin (patch-local)
+  int tw, th;      // tile extents
+  int r0, r1;      // region origin (patch-local)
+  int rw, rh;      // region extents
+  int fl0, fh0, fl1, fh1;  // 1 where the region side is a patch face (does not shrink)
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, int tx, int ty, int halo) {
+  TileGeom t;
+  t.i0 = blockIdx.x * tx;
+  t.j0 = blockIdx.y * ty;
+  t.tw = min(tx, gp.n[0] - t.i0);
+  t.th = min(ty, gp.n[1] - t.j0);
+  t.r0 = max(t.i0 - halo, 0);
+  t.r1 = max(t.j0 - halo, 0);
+  const int e0 = min(t.i0 + t.tw + halo, gp.n[0]);
+  const int e1 = min(t.j0 + t.th + halo, gp.n[1]);
+  t.rw = e0 - t.r0;
+  t.rh = e1 - t.r1;
+  t.fl0 = t.r0 == 0;
+  t.fl1 = t.r1 == 0;
+  t.fh0 = e0 == gp.n[0];
+  t.fh1 = e1 == gp.n[1];
+  return t;
+}
+
+__device__ __forceinline__ PatchDesc region_desc(const PatchDesc& gp, const TileGeom& t) {
+  PatchDesc sp;
+  sp.off = 0;
+  sp.sy = t.rw + 2 * NG;
+  sp.sz = 0;
+  sp.n[0] = t.rw;
+  sp.n[1] = t.rh;
+  sp.n[2] = 1;
+  sp.lo[0] = gp.lo[0] + t.r0;
+  sp.lo[1] = gp.lo[1] + t.r1;
+  sp.lo[2] = 0;
+  return sp;
+}
+
+// region cells updated by sweep s (shrunk by 2 s on non-face sides)
+__device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int& b0, int& a1, int& b1) {
+  a0 = t.fl0 ? 0 : 2 * s;
+  b0 = t.fh0 ? t.rw : t.rw - 2 * s;
+  a1 = t.fl1 ? 0 : 2 * s;
+  b1 = t.fh1 ? t.rh : t.rh - 2 * s;
+}
+
+template <typename T, bool TR>
+__device__ __forceinline__ T* smooth_region(const LevelView& lv, const PatchDesc& sp, const TileGeom& tg, T* cur, T* oth,
+                                            const T* sb, int s_first, int nu, bool from_zero, T alpha, T beta,
+                                            T omega) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int s = s_first; s < s_first + nu; ++s) {
+    int a0, b0, a1, b1;
+    sweep_box(tg, s, a0, b0, a1, b1);
+    const int w = b0 - a0, cnt = w * (b1 - a1);
+    for (int q = tid; q < cnt; q += nth) {
+      const int i = a0 + q % w, j = a1 + q / w;
+      if (from_zero && s == s_first)
+        cell_level_op<T, 2, OP_JACOBI0, TR>(lv, sp, i, j, 0, nullptr, sb, oth, nullptr, alpha, beta, omega);
+      else
+        cell_level_op<T, 2, OP_JACOBI, TR>(lv, sp, i, j, 0, cur, sb, oth, nullptr, alpha, beta, omega);
+    }
+    __syncthreads();
+    T* sw = cur;
+    cur = oth;
+    oth = sw;
+  }
+  return cur;
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_region(T* a, long long n) {
+  for (long long q = threadIdx.x; q < n; q += blockDim.x) a[q] = T(0);
+}
+
+// Down leg of one multigrid level: nu weighted-Jacobi sweeps (from zero when FROM_ZERO,
+// else from x), the smoothed x written back, and the residual f - A x restricted (2x2
+// average) into the next grid's right-hand side bcn.  halo = 2 nu + 2.
+template <typename T, bool TR, bool FROM_ZERO>
+__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
+                                                   int nu, const T* __restrict__ b, T* __restrict__ x,
+                                                   T* __restrict__ bcn, T alpha, T beta, T omega) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileGeom tg = tile_geom(gp, tx, ty, halo);
+  const PatchDesc sp = region_desc(gp, tg);
+  const long long E = sp.sy * (tg.rh + 2 * NG);
+  T* sx = reinterpret_cast<T*>(smraw);
+  T* st = sx + E;
+  T* sb = st + E;
+  zero_region(sx, 3 * E);
+  __syncthreads();
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int cnt = tg.rw * tg.rh;
+  for (int q = tid; q < cnt; q += nth) {
+    const int i = q % tg.rw, j = q / tg.rw;
+    const long long og = poff(gp, tg.r0 + i, tg.r1 + j, 0);
+    const long long os = poff(sp, i, j, 0);
+    sb[os] = b[og];
+    if (!FROM_ZERO) sx[os] = x[og];
+  }
+  __syncthreads();
+  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, 1, nu, FROM_ZERO, alpha, beta, omega);
+  const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
+  for (int q = tid; q < tg.tw * tg.th; q += nth) {
+    const int i = q % tg.tw, j = q / tg.tw;
+    x[poff(gp, tg.i0 + i, tg.j0 + j, 0)] = cur[poff(sp, ti + i, tj + j, 0)];
+  }
+  const int cw = tg.tw / 2, ch = tg.th / 2;
+  for (int q = tid; q < cw * ch; q += nth) {
+    const int g[3] = {(gp.lo[0] + tg.i0) / 2 + q % cw, (gp.lo[1] + tg.j0) / 2 + q / cw, 0};
+    cell_restrict<T, 2, true, TR>(lv, sp, gcp, g, cur, sb, bcn, alpha, beta);
+  }
+}
+
+// Up leg of one multigrid level: x += linear prolongation of the coarse correction xc,
+// then nu weighted-Jacobi sweeps; halo = 2 nu.
+template <typename T, bool TR>
+__global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+                                                 int ty, int halo, int nu, const T* __restrict__ xc,
+                                                 const T* __restrict__ b, T* __restrict__ x, T alpha, T beta,
+                                                 T omega) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileGeom tg = tile_geom(gp, tx, ty, halo);
+  const PatchDesc sp = region_desc(gp, tg);
+  const long long E = sp.sy * (tg.rh + 2 * NG);
+  T* sx = reinterpret_cast<T*>(smraw);
+  T* st = sx + E;
+  T* sb = st + E;
+  zero_region(sx, 3 * E);
+  __syncthreads();
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int cnt = tg.rw * tg.rh;
+  for (int q = tid; q < cnt; q += nth) {
+    const int i = q % tg.rw, j = q / tg.rw;
+    const long long og = poff(gp, tg.r0 + i, tg.r1 + j, 0);
+    const long long os = poff(sp, i, j, 0);
+    sb[os] = b[og];
+    sx[os] = x[og];
+    const int gf[3] = {sp.lo[0] + i, sp.lo[1] + j, 0};
+    cell_prolong<T, 2>(cv, sp, gcp, gf, xc, sx, (T*)nullptr);
+  }
+  __syncthreads();
+  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, 1, nu, false, alpha, beta, omega);
+  const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
+  for (int q = tid; q < tg.tw * tg.th; q += nth) {
+    const int i = q % tg.tw, j = q / tg.tw;
+    x[poff(gp, tg.i0 + i, tg.j0 + j, 0)] = cur[poff(sp, ti + i, tj + j, 0)];
+  }
+}
+
 // ------------------------------------------------------------------------ fused coarse V-cycle
 // The coarse end of the level-0 multigrid pyramid (every grid from m0 down to the coarsest,
 // whose arrays fit in shared memory together) runs as ONE block: the same per-cell

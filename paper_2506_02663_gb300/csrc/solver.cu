@@ -68,6 +68,7 @@ struct amr_operator {
   double g_omega = 0.0, g_rtol = -1.0, g_atol = -1.0;
   long long launches_pre = 0, launches_body = 0;
   int g_fuse = -1;
+  int g_blk = -1;
   int cmg_m0[2][2] = {{-1, -1}, {-1, -1}};  // [transpose][precision 0 = FP32, 1 = FP64]; -1: unset
   size_t cmg_bytes[2][2] = {{0, 0}, {0, 0}};
 };
@@ -497,6 +498,8 @@ Scratch<float>& scratch<float>(amr_operator* op) { return op->s32; }
 
 template <typename T, int D>
 amr_status autotune_tiles(amr_operator* op, cudaStream_t st);
+template <typename T>
+amr_status blk_attrs();
 
 template <typename T>
 amr_status ensure_scratch(amr_operator* op) {
@@ -536,7 +539,10 @@ amr_status ensure_scratch(amr_operator* op) {
   }
   S.ready = true;
   // choose the tiled kernel's rows per thread for every grid this operator smooths
-  if (op->h->D == 2) TRY((autotune_tiles<T, 2>(op, 0)));
+  if (op->h->D == 2) {
+    TRY(blk_attrs<T>());
+    TRY((autotune_tiles<T, 2>(op, 0)));
+  }
   return AMR_OK;
 }
 
@@ -709,6 +715,30 @@ amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, si
   return launch_check();
 }
 
+// ---------------------------------------------------------------- temporally blocked legs
+constexpr int BLK_TX = 32, BLK_TY = 16, BLK_MAX_NU = 6;
+
+// dynamic shared memory of a blocked leg: three region arrays with two ghost layers
+template <typename T>
+size_t blk_smem(const MgGrid& g, int halo) {
+  const long long w = std::min(BLK_TX + 2 * halo, g.n[0]) + 2 * NG;
+  const long long hh = std::min(BLK_TY + 2 * halo, g.n[1]) + 2 * NG;
+  return (size_t)(3 * w * hh) * sizeof(T);
+}
+
+template <typename T>
+amr_status blk_attrs() {
+  static bool done = false;
+  if (done) return AMR_OK;
+  const int bytes = 200 * 1024;
+  CK(cudaFuncSetAttribute(k_mg_down2d<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_down2d<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_up2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_up2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+  return AMR_OK;
+}
+
 // ---------------------------------------------------------------- level-0 multigrid
 template <typename T, int D, bool TR = false>
 amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const T* b, T* x, T* t, cudaStream_t st) {
@@ -727,8 +757,23 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     k_bottom<T, D><<<1, 256, n * sizeof(double), st>>>(TR ? op->d_binvT : op->d_binv, n, op->ldb, h->mg[m].patch, b, x);
     return launch_check();
   }
-  TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const LevelView cv = mg_view(h, m + 1, op->bc);
+  if (D == 2 && p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
+    // temporally blocked legs: one launch for {nu1 sweeps, residual, restriction} and one
+    // for {prolongation, nu2 sweeps}
+    const MgGrid& g = h->mg[m];
+    const MgGrid& gc = h->mg[m + 1];
+    dim3 grid((g.n[0] + BLK_TX - 1) / BLK_TX, (g.n[1] + BLK_TY - 1) / BLK_TY, 1);
+    const int hd = 2 * p.nu1 + 2, hu = 2 * p.nu2;
+    k_mg_down2d<T, TR, true><<<grid, 256, blk_smem<T>(g, hd), st>>>(lv, g.patch, gc.patch, BLK_TX, BLK_TY, hd, p.nu1, b, x,
+                                                                   S.mb[m + 1], T(op->alpha), T(op->beta), T(p.omega));
+    TRY(launch_check());
+    TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
+    k_mg_up2d<T, TR><<<grid, 256, blk_smem<T>(g, hu), st>>>(lv, cv, g.patch, gc.patch, BLK_TX, BLK_TY, hu, p.nu2, S.mx[m + 1],
+                                                          b, x, T(op->alpha), T(op->beta), T(p.omega));
+    return launch_check();
+  }
+  TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
   TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], 1, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
   TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
@@ -1376,6 +1421,7 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
   op->g_phi = phi; op->g_bc = bc; op->g_prec = p.precision; op->g_nu1 = p.nu1; op->g_nu2 = p.nu2;
   op->g_maxv = p.max_vcycles; op->g_omega = p.omega; op->g_rtol = p.rtol; op->g_atol = p.atol;
   op->g_fuse = p.fuse_coarse;
+  op->g_blk = p.temporal_blocking;
   return AMR_OK;
 }
 
@@ -1401,7 +1447,7 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   const bool hit = op->exec && op->g_phi == phi && op->g_bc == bc && op->g_prec == p.precision &&
                    op->g_nu1 == p.nu1 && op->g_nu2 == p.nu2 && op->g_maxv == p.max_vcycles &&
                    op->g_omega == p.omega && op->g_rtol == p.rtol && op->g_atol == p.atol &&
-                   op->g_fuse == p.fuse_coarse;
+                   op->g_fuse == p.fuse_coarse && op->g_blk == p.temporal_blocking;
   if (!hit) TRY(build_solve_graph<D>(op, p, phi, bc));
   CK(cudaGraphLaunch(op->exec, st));
   if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
@@ -1871,6 +1917,7 @@ void amr_default_params(amr_solver_params* p) {
   p->zero_initial = 1;
   p->use_graph = 0;
   p->fuse_coarse = 0;
+  p->temporal_blocking = 1;
 }
 
 amr_status amr_hierarchy_create(const amr_hierarchy_desc* desc, amr_hierarchy** out) {
