@@ -319,18 +319,10 @@ def run_ours(args):
     amr.profile_enable(True)
     timed(prof_params, max(1, min(args.steps, 5)))
     amr.profile_enable(False)
-    jac = amr.profile_read(amr.KC_JACOBI)
-    achieved = jac["bytes"] / (jac["ms"] * 1e-3) / 1e9 if jac["ms"] > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "traffic": _traffic("jacobi_bumps2d"),
-                "kernel": "k_level_op<float,2,JACOBI> + first-sweep variant (grids outside the fused coarse block)",
-                "launches": jac["launches"], "avg_launch_us": 1e3 * jac["ms"] / max(jac["launches"], 1),
-                "bytes_per_launch": jac["bytes"] / max(jac["launches"], 1), "peak_source": f"{peak_kind} hbm_gbs"}
-    others = {}
-    for name, kc in (("residual", amr.KC_RESID), ("restrict", amr.KC_RESTRICT), ("prolong", amr.KC_PROLONG)):
-        r = amr.profile_read(kc)
-        others[name] = {"launches": r["launches"], "ms": r["ms"]}
+    classes = _class_table(amr)
+    dom = _dominant(classes)
+    roofline = _roofline_entry(classes, dom, peak, peak_kind, "bumps2d")
+    others = {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in classes.items() if k != dom}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -362,6 +354,7 @@ def run_ours(args):
                      "vcycles_per_system": [statistics.mean(v[i] for v in vcs2) for i in range(len(systems))]}
         line["large_grid_roofline"] = _large_grid_roofline(amr, torch, peak, peak_kind)
         line["batch"] = _batch_measure(amr, torch)
+        line["adjoint"] = _adjoint_measure(amr, torch)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, c, el = _oracle_vcycles(12.0)
@@ -373,6 +366,43 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+KERNEL_CLASSES = {
+    "jacobi": ("KC_JACOBI", "k_level_op2d_tiled<float,JACOBI> / k_level_op<float,*,JACOBI>: one weighted-Jacobi sweep"),
+    "residual": ("KC_RESID", "k_level_op*<*,RESID/APPLY>: level residual or operator"),
+    "restrict": ("KC_RESTRICT", "k_restrict2d_resid / k_restrict: residual restriction and average-down"),
+    "prolong": ("KC_PROLONG", "k_prolong2d / k_prolong: linear prolongation + correction"),
+    "down_leg": ("KC_DOWN", "k_mg_down2d<float>: nu1 sweeps + residual + restriction, one launch per grid"),
+    "up_leg": ("KC_UP", "k_mg_up2d<float>: prolongation + nu2 sweeps, one launch per grid"),
+}
+
+
+def _class_table(amr):
+    out = {}
+    for name, (kc, _) in KERNEL_CLASSES.items():
+        r = amr.profile_read(getattr(amr, kc))
+        if r["launches"]:
+            out[name] = r
+    return out
+
+
+def _dominant(classes):
+    return max(classes, key=lambda k: classes[k]["ms"]) if classes else None
+
+
+def _roofline_entry(classes, dom, peak, peak_kind, workload):
+    if dom is None:
+        return {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
+    c = classes[dom]
+    achieved = c["bytes"] / (c["ms"] * 1e-3) / 1e9 if c["ms"] > 0 else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": _traffic(f"{dom}_{workload}"),
+            "kernel": KERNEL_CLASSES[dom][1], "class": dom,
+            "launches": c["launches"], "avg_launch_us": 1e3 * c["ms"] / max(c["launches"], 1),
+            "bytes_per_launch": c["bytes"] / max(c["launches"], 1), "peak_source": f"{peak_kind} hbm_gbs",
+            "share_of_instrumented_ms": c["ms"] / sum(v["ms"] for v in classes.values())}
 
 
 def _batch_measure(amr, torch, reps=3):
@@ -431,8 +461,8 @@ def _batch_measure(amr, torch, reps=3):
 
 
 def _large_grid_roofline(amr, torch, peak, peak_kind, n=4096):
-    """Same Jacobi kernel on a single-level n^2 Helmholtz solve (fields >> L2): the HBM
-    efficiency of the smoother when it is not launch-bound."""
+    """The same kernels on a single-level n^2 Helmholtz solve (fields >> L2): the HBM
+    efficiency of the smoothing kernels when they are not launch-bound."""
     from paper_2506_02663_gb300 import workloads as wl
     gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
     op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA * 16.0, [0, 0, 0, 0])
@@ -445,13 +475,72 @@ def _large_grid_roofline(amr, torch, peak, peak_kind, n=4096):
     amr.profile_enable(True)
     st = op.solve(phi, f, params=p)
     amr.profile_enable(False)
-    jac = amr.profile_read(amr.KC_JACOBI)
-    ach = jac["bytes"] / (jac["ms"] * 1e-3) / 1e9 if jac["ms"] > 0 else None
+    classes = _class_table(amr)
+    dom = _dominant(classes)
+    out = _roofline_entry(classes, dom, peak, peak_kind, f"single{n}")
+    out["workload"] = f"single-level {n}^2 Helmholtz, mixed precision, {st['vcycles']} V-cycles"
+    out["classes"] = {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
+                      for k, v in classes.items()}
     op.close()
     gh.close()
-    return {"workload": f"single-level {n}^2 Helmholtz, mixed precision, {st['vcycles']} V-cycles",
-            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None,
-            "launches": jac["launches"], "peak_source": f"{peak_kind} hbm_gbs"}
+    return out
+
+
+def _adjoint_measure(amr, torch, reps=3):
+    """The adjoint2d workload (base 256^2, boxes [0.2,0.8]^2 -> 308^2 and [0.35,0.65]^2 ->
+    308^2 fine cells, two smoothed N(0,1) forcing components): forward = two Helmholtz solves
+    and the composite projection; backward = the projection's adjoint and two adjoint
+    Helmholtz solves, FP64 to 1e-12 (the accuracy the finite-difference check needs)."""
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, comps = wl.adjoint2d_forcing()
+    gh = amr.Hierarchy(dim, n0, boxes, h0=1.0 / n0[0])
+    helm = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA, [0] * 4)
+    ppe = amr.Operator(gh, 0.0, 1.0, [1] * 4)
+    p = amr.default_params(rtol=1e-12, max_vcycles=200, precision=amr.FP64, use_graph=1)
+    g = [torch.from_numpy(gh.pack(comps[d])).cuda() for d in range(dim)]
+    w = [torch.zeros_like(g[0]) for _ in range(dim)]
+    u = [torch.zeros_like(g[0]) for _ in range(dim)]
+    v = [torch.zeros_like(g[0]) for _ in range(dim)]
+    lam = [torch.zeros_like(g[0]) for _ in range(dim)]
+    phi = torch.zeros_like(g[0])
+    psi = torch.zeros_like(g[0])
+    stream = torch.cuda.current_stream()
+
+    def forward():
+        vc = 0
+        for d in range(dim):
+            vc += helm.solve(w[d], g[d], params=p)["vcycles"]
+        vc += amr.project(ppe, [0] * 4, w, u, phi, params=p)["vcycles"]
+        return vc
+
+    def backward():
+        vc = amr.project_transpose(ppe, [0] * 4, u, v, psi, params=p)["vcycles"]
+        for d in range(dim):
+            vc += helm.solve_transpose(lam[d], v[d], params=p)["vcycles"]
+        return vc
+
+    def timeit(fn):
+        fn()
+        ts, vcs = [], []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vcs.append(fn())
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), vcs[-1]
+    tf, vf = timeit(forward)
+    tb, vb = timeit(backward)
+    ppe.close()
+    helm.close()
+    gh.close()
+    return {"workload": "adjoint2d: three-level 2-D AMR (256^2 base, 308^2 + 308^2 fine), two components; "
+                        "forward = 2 Helmholtz solves + composite projection, backward = adjoint projection + "
+                        "2 adjoint Helmholtz solves, FP64 to 1e-12",
+            "forward_ms": tf, "backward_ms": tb, "backward_over_forward": tb / tf,
+            "vcycles_forward": vf, "vcycles_backward": vb}
 
 
 def _profile_case():

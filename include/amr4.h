@@ -156,10 +156,10 @@ typedef struct {
   int fuse_coarse;   /* 1: run the coarse end of the level-0 V-cycle in one shared-memory
                         block (same arithmetic as the per-grid kernels); default 0: on GB300
                         one block is slower than the graph's per-grid launches              */
-  int temporal_blocking; /* 1 (default): on 2-D level-0 multigrid grids, each down leg (nu1
-                        sweeps, residual, restriction) and each up leg (prolongation, nu2
-                        sweeps) is one launch over shared-memory tiles with halos (same
-                        per-cell arithmetic); 0: one launch per sweep                        */
+  int temporal_blocking; /* 1 (default): in FP32 V-cycles on 2-D level-0 multigrid grids,
+                        each down leg (nu1 sweeps, residual, restriction) and each up leg
+                        (prolongation, nu2 sweeps) is one launch over shared-memory tiles
+                        with halos (same per-cell arithmetic); 0: one launch per sweep    */
 } amr_solver_params;
 
 typedef struct {
@@ -339,7 +339,9 @@ long long amr_kernel_launches(void);
  * launching stream (0 stops recording).  amr_profile_read() synchronises on the recorded
  * events and returns, for one class, the number of launches, the summed event intervals
  * (ms) and the summed algorithmic bytes.  Classes: 0 weighted-Jacobi sweeps, 1 level
- * residual / apply, 2 restriction and average-down, 3 prolongation. */
+ * residual / apply, 2 restriction and average-down, 3 prolongation, 4 temporally blocked
+ * down legs (f read, x and the coarse f written once), 5 temporally blocked up legs (x, f
+ * and the coarse correction read once, x written once). */
 amr_status amr_profile_enable(int on);
 amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes);
 

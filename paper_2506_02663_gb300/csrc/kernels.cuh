@@ -688,22 +688,50 @@ __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int
   b1 = t.fh1 ? t.rh : t.rh - 2 * s;
 }
 
+// One weighted-Jacobi sweep over the box [a0,b0) x [a1,b1) of a shared-memory region: cells
+// whose stencil (and, for the transpose, the ghost-coefficient gathers) stays inside the
+// domain take the interior form with the constant diagonal (ood = omega / diag); the others
+// run cell_level_op.  Same summation order as cell_Lx.
+template <typename T, bool TR, bool ZERO>
+__device__ __forceinline__ void sweep_box_cells(const LevelView& lv, const PatchDesc& sp, const T* __restrict__ cur,
+                                                T* __restrict__ oth, const T* __restrict__ sb, int a0, int b0, int a1,
+                                                int b1, T alpha, T beta, T omega, T ood) {
+  constexpr int M = TR ? 4 : 2;
+  const int sy = (int)sp.sy;
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  for (int j = a1 + (int)threadIdx.y; j < b1; j += (int)blockDim.y)
+    for (int i = a0 + (int)threadIdx.x; i < b0; i += (int)blockDim.x) {
+      const int g0 = sp.lo[0] + i, g1 = sp.lo[1] + j;
+      if (g0 >= M && g0 <= lv.ndom[0] - 1 - M && g1 >= M && g1 <= lv.ndom[1] - 1 - M) {
+        const int o = (j + NG) * sy + (i + NG);
+        if (ZERO) {
+          oth[o] = ood * sb[o];
+        } else {
+          const T xc = cur[o];
+          const T s1 = (cur[o - 1] + cur[o + 1]) + (cur[o - sy] + cur[o + sy]);
+          const T s2 = (cur[o - 2] + cur[o + 2]) + (cur[o - 2 * sy] + cur[o + 2 * sy]);
+          const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
+          const T ax = alpha * xc + beta * (lap * inv);
+          oth[o] = xc + ood * (sb[o] - ax);
+        }
+      } else if (ZERO) {
+        cell_level_op<T, 2, OP_JACOBI0, TR>(lv, sp, i, j, 0, nullptr, sb, oth, nullptr, alpha, beta, omega);
+      } else {
+        cell_level_op<T, 2, OP_JACOBI, TR>(lv, sp, i, j, 0, cur, sb, oth, nullptr, alpha, beta, omega);
+      }
+    }
+}
+
 template <typename T, bool TR>
 __device__ __forceinline__ T* smooth_region(const LevelView& lv, const PatchDesc& sp, const TileGeom& tg, T* cur, T* oth,
-                                            const T* sb, int s_first, int nu, bool from_zero, T alpha, T beta,
-                                            T omega) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int s = s_first; s < s_first + nu; ++s) {
+                                            const T* sb, int nu, bool from_zero, T alpha, T beta, T omega, T ood) {
+  for (int s = 1; s <= nu; ++s) {
     int a0, b0, a1, b1;
     sweep_box(tg, s, a0, b0, a1, b1);
-    const int w = b0 - a0, cnt = w * (b1 - a1);
-    for (int q = tid; q < cnt; q += nth) {
-      const int i = a0 + q % w, j = a1 + q / w;
-      if (from_zero && s == s_first)
-        cell_level_op<T, 2, OP_JACOBI0, TR>(lv, sp, i, j, 0, nullptr, sb, oth, nullptr, alpha, beta, omega);
-      else
-        cell_level_op<T, 2, OP_JACOBI, TR>(lv, sp, i, j, 0, cur, sb, oth, nullptr, alpha, beta, omega);
-    }
+    if (from_zero && s == 1)
+      sweep_box_cells<T, TR, true>(lv, sp, cur, oth, sb, a0, b0, a1, b1, alpha, beta, omega, ood);
+    else
+      sweep_box_cells<T, TR, false>(lv, sp, cur, oth, sb, a0, b0, a1, b1, alpha, beta, omega, ood);
     __syncthreads();
     T* sw = cur;
     cur = oth;
@@ -712,84 +740,121 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const PatchDesc
   return cur;
 }
 
+__device__ __forceinline__ int blk_tid() { return (int)(threadIdx.y * blockDim.x + threadIdx.x); }
+__device__ __forceinline__ int blk_nth() { return (int)(blockDim.x * blockDim.y); }
+
 template <typename T>
-__device__ __forceinline__ void zero_region(T* a, long long n) {
-  for (long long q = threadIdx.x; q < n; q += blockDim.x) a[q] = T(0);
+__device__ __forceinline__ void zero_region(T* a, int n) {
+  for (int q = blk_tid(); q < n; q += blk_nth()) a[q] = T(0);
 }
 
-// Down leg of one multigrid level: nu weighted-Jacobi sweeps (from zero when FROM_ZERO,
-// else from x), the smoothed x written back, and the residual f - A x restricted (2x2
-// average) into the next grid's right-hand side bcn.  halo = 2 nu + 2.
-template <typename T, bool TR, bool FROM_ZERO>
-__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
-                                                   int nu, const T* __restrict__ b, T* __restrict__ x,
-                                                   T* __restrict__ bcn, T alpha, T beta, T omega) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const TileGeom tg = tile_geom(gp, tx, ty, halo);
-  const PatchDesc sp = region_desc(gp, tg);
-  const long long E = sp.sy * (tg.rh + 2 * NG);
-  T* sx = reinterpret_cast<T*>(smraw);
-  T* st = sx + E;
-  T* sb = st + E;
-  zero_region(sx, 3 * E);
-  __syncthreads();
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int cnt = tg.rw * tg.rh;
-  for (int q = tid; q < cnt; q += nth) {
-    const int i = q % tg.rw, j = q / tg.rw;
-    const long long og = poff(gp, tg.r0 + i, tg.r1 + j, 0);
-    const long long os = poff(sp, i, j, 0);
-    sb[os] = b[og];
-    if (!FROM_ZERO) sx[os] = x[og];
-  }
-  __syncthreads();
-  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, 1, nu, FROM_ZERO, alpha, beta, omega);
-  const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
-  for (int q = tid; q < tg.tw * tg.th; q += nth) {
-    const int i = q % tg.tw, j = q / tg.tw;
-    x[poff(gp, tg.i0 + i, tg.j0 + j, 0)] = cur[poff(sp, ti + i, tj + j, 0)];
-  }
-  const int cw = tg.tw / 2, ch = tg.th / 2;
-  for (int q = tid; q < cw * ch; q += nth) {
-    const int g[3] = {(gp.lo[0] + tg.i0) / 2 + q % cw, (gp.lo[1] + tg.j0) / 2 + q / cw, 0};
-    cell_restrict<T, 2, true, TR>(lv, sp, gcp, g, cur, sb, bcn, alpha, beta);
-  }
-}
-
-// Up leg of one multigrid level: x += linear prolongation of the coarse correction xc,
-// then nu weighted-Jacobi sweeps; halo = 2 nu.
+// Down leg of one multigrid level: nu weighted-Jacobi sweeps from zero, the smoothed x
+// written to xo, and the residual f - A x restricted (2x2 average) into the next grid's
+// right-hand side bcn.  halo = 2 nu + 2.  xo is not read (no block reads another's tile).
 template <typename T, bool TR>
-__global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
-                                                 int ty, int halo, int nu, const T* __restrict__ xc,
-                                                 const T* __restrict__ b, T* __restrict__ x, T alpha, T beta,
-                                                 T omega) {
+__global__ void __launch_bounds__(512) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
+                                                   int nu, const T* __restrict__ b, T* __restrict__ xo,
+                                                   T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, tx, ty, halo);
   const PatchDesc sp = region_desc(gp, tg);
-  const long long E = sp.sy * (tg.rh + 2 * NG);
+  const int sy = (int)sp.sy;
+  const int E = sy * (tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
   zero_region(sx, 3 * E);
   __syncthreads();
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int cnt = tg.rw * tg.rh;
-  for (int q = tid; q < cnt; q += nth) {
-    const int i = q % tg.rw, j = q / tg.rw;
-    const long long og = poff(gp, tg.r0 + i, tg.r1 + j, 0);
-    const long long os = poff(sp, i, j, 0);
-    sb[os] = b[og];
-    sx[os] = x[og];
-    const int gf[3] = {sp.lo[0] + i, sp.lo[1] + j, 0};
-    cell_prolong<T, 2>(cv, sp, gcp, gf, xc, sx, (T*)nullptr);
-  }
+  const T* __restrict__ bg = b + gp.off;
+  const int gsy = (int)gp.sy;
+  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
+      sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
   __syncthreads();
-  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, 1, nu, false, alpha, beta, omega);
+  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, nu, true, alpha, beta, omega, ood);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
-  for (int q = tid; q < tg.tw * tg.th; q += nth) {
-    const int i = q % tg.tw, j = q / tg.tw;
-    x[poff(gp, tg.i0 + i, tg.j0 + j, 0)] = cur[poff(sp, ti + i, tj + j, 0)];
-  }
+  T* __restrict__ xg = xo + gp.off;
+  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x)
+      xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
+  // residual restriction: interior children in the fast form, the others through cell_restrict
+  constexpr int M = TR ? 4 : 2;
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  const int cw = tg.tw / 2, ch = tg.th / 2;
+  for (int cj = (int)threadIdx.y; cj < ch; cj += (int)blockDim.y)
+    for (int ci = (int)threadIdx.x; ci < cw; ci += (int)blockDim.x) {
+      const int g[3] = {(gp.lo[0] + tg.i0) / 2 + ci, (gp.lo[1] + tg.j0) / 2 + cj, 0};
+      if (2 * g[0] >= M && 2 * g[0] + 1 <= lv.ndom[0] - 1 - M && 2 * g[1] >= M && 2 * g[1] + 1 <= lv.ndom[1] - 1 - M) {
+        T acc = T(0);
+#pragma unroll
+        for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+          for (int q0 = 0; q0 < 2; ++q0) {
+            const int o = (2 * g[1] + q1 - sp.lo[1] + NG) * sy + (2 * g[0] + q0 - sp.lo[0] + NG);
+            const T xc = cur[o];
+            const T s1 = (cur[o - 1] + cur[o + 1]) + (cur[o - sy] + cur[o + sy]);
+            const T s2 = (cur[o - 2] + cur[o + 2]) + (cur[o - 2 * sy] + cur[o + 2 * sy]);
+            const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
+            acc += sb[o] - (alpha * xc + beta * (lap * inv));
+          }
+        bcn[poff(gcp, g[0] - gcp.lo[0], g[1] - gcp.lo[1], 0)] = acc * T(0.25);
+      } else {
+        cell_restrict<T, 2, true, TR>(lv, sp, gcp, g, cur, sb, bcn, alpha, beta);
+      }
+    }
+}
+
+// Up leg of one multigrid level: x = xi + linear prolongation of the coarse correction xc,
+// then nu weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
+// halo = 2 nu.
+template <typename T, bool TR>
+__global__ void __launch_bounds__(512) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+                                                 int ty, int halo, int nu, const T* __restrict__ xc,
+                                                 const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
+                                                 T alpha, T beta, T omega, T ood) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileGeom tg = tile_geom(gp, tx, ty, halo);
+  const PatchDesc sp = region_desc(gp, tg);
+  const int sy = (int)sp.sy;
+  const int E = sy * (tg.rh + 2 * NG);
+  T* sx = reinterpret_cast<T*>(smraw);
+  T* st = sx + E;
+  T* sb = st + E;
+  zero_region(sx, 3 * E);
+  __syncthreads();
+  const int gsy = (int)gp.sy, csy = (int)gcp.sy;
+  const T* __restrict__ bg = b + gp.off;
+  const T* __restrict__ xg = xi + gp.off;
+  const T* __restrict__ cg = xc + gcp.off;
+  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x) {
+      const int og = (tg.r1 + j + NG) * gsy + tg.r0 + i + NG;
+      const int os = (j + NG) * sy + i + NG;
+      sb[os] = bg[og];
+      const int gf0 = sp.lo[0] + i, gf1 = sp.lo[1] + j;
+      const int p0 = gf0 >> 1, p1 = gf1 >> 1;
+      const int s0 = (gf0 & 1) ? 1 : -1, s1 = (gf1 & 1) ? 1 : -1;
+      if (p0 + s0 >= 0 && p0 + s0 < cv.ndom[0] && p1 + s1 >= 0 && p1 + s1 < cv.ndom[1]) {
+        const int oc = (p1 - gcp.lo[1] + NG) * csy + (p0 - gcp.lo[0] + NG);
+        T v = T(0);
+        v += (T(0.75) * T(0.75)) * cg[oc];
+        v += (T(0.25) * T(0.75)) * cg[oc + s0];
+        v += (T(0.75) * T(0.25)) * cg[oc + s1 * csy];
+        v += (T(0.25) * T(0.25)) * cg[oc + s1 * csy + s0];
+        sx[os] = xg[og] + v;
+      } else {
+        sx[os] = xg[og];
+        const int gf[3] = {gf0, gf1, 0};
+        cell_prolong<T, 2>(cv, sp, gcp, gf, xc, sx, (T*)nullptr);
+      }
+    }
+  __syncthreads();
+  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, nu, false, alpha, beta, omega, ood);
+  const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
+  T* __restrict__ xw = xo + gp.off;
+  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x)
+      xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
 }
 
 // ------------------------------------------------------------------------ fused coarse V-cycle

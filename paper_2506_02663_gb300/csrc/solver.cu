@@ -129,7 +129,7 @@ inline float pick_host<float>(double, float f) { return f; }
 // ---------------------------------------------------------------- bench instrumentation
 // When enabled, launches of the instrumented kernel classes are bracketed with CUDA events
 // on the launching stream; amr_profile_read() sums the event intervals.
-enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_NCLASS = 4 };
+enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_DOWN = 4, PC_UP = 5, PC_NCLASS = 6 };
 struct ProfRec {
   cudaEvent_t a, b;
   int cls;
@@ -540,7 +540,7 @@ amr_status ensure_scratch(amr_operator* op) {
   S.ready = true;
   // choose the tiled kernel's rows per thread for every grid this operator smooths
   if (op->h->D == 2) {
-    TRY(blk_attrs<T>());
+    if constexpr (sizeof(T) == 4) TRY(blk_attrs<T>());
     TRY((autotune_tiles<T, 2>(op, 0)));
   }
   return AMR_OK;
@@ -731,8 +731,8 @@ amr_status blk_attrs() {
   static bool done = false;
   if (done) return AMR_OK;
   const int bytes = 200 * 1024;
-  CK(cudaFuncSetAttribute(k_mg_down2d<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_mg_down2d<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_down2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_down2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_up2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_up2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done = true;
@@ -758,20 +758,32 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     return launch_check();
   }
   const LevelView cv = mg_view(h, m + 1, op->bc);
-  if (D == 2 && p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
-    // temporally blocked legs: one launch for {nu1 sweeps, residual, restriction} and one
-    // for {prolongation, nu2 sweeps}
+  if constexpr (D == 2 && sizeof(T) == 4) if (p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
+    // temporally blocked legs (FP32 V-cycles only: FP64 arithmetic is scarce on this part
+    // and the halo recomputation would cost more than the launches it saves): one launch
+    // for {nu1 sweeps, residual, restriction} into t, one for {prolongation, nu2 sweeps}
+    // from t into x
     const MgGrid& g = h->mg[m];
     const MgGrid& gc = h->mg[m + 1];
     dim3 grid((g.n[0] + BLK_TX - 1) / BLK_TX, (g.n[1] + BLK_TY - 1) / BLK_TY, 1);
+    const dim3 blk(32, 16, 1);
     const int hd = 2 * p.nu1 + 2, hu = 2 * p.nu2;
-    k_mg_down2d<T, TR, true><<<grid, 256, blk_smem<T>(g, hd), st>>>(lv, g.patch, gc.patch, BLK_TX, BLK_TY, hd, p.nu1, b, x,
-                                                                   S.mb[m + 1], T(op->alpha), T(op->beta), T(p.omega));
+    const double dint = op->alpha - 60.0 * op->beta * lv.inv12h2;  // interior diagonal
+    const T ood = T(p.omega / dint);
+    const double cells = (double)g.n[0] * g.n[1];
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    k_mg_down2d<T, TR><<<grid, blk, blk_smem<T>(g, hd), st>>>(lv, g.patch, gc.patch, BLK_TX, BLK_TY, hd, p.nu1, b, t,
+                                                             S.mb[m + 1], T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
+    prof_end(st, ev, PC_DOWN, (2.0 + 0.25) * sizeof(T) * cells);  // read f, write x, write coarse f
     TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
-    k_mg_up2d<T, TR><<<grid, 256, blk_smem<T>(g, hu), st>>>(lv, cv, g.patch, gc.patch, BLK_TX, BLK_TY, hu, p.nu2, S.mx[m + 1],
-                                                          b, x, T(op->alpha), T(op->beta), T(p.omega));
-    return launch_check();
+    prof_begin(st, &ev);
+    k_mg_up2d<T, TR><<<grid, blk, blk_smem<T>(g, hu), st>>>(lv, cv, g.patch, gc.patch, BLK_TX, BLK_TY, hu, p.nu2,
+                                                           S.mx[m + 1], b, t, x, T(op->alpha), T(op->beta), T(p.omega), ood);
+    TRY(launch_check());
+    prof_end(st, ev, PC_UP, (3.0 + 0.25) * sizeof(T) * cells);  // read x, f, coarse x; write x
+    return AMR_OK;
   }
   TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
