@@ -552,7 +552,8 @@ def _profile_case():
     op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA * 16.0, [0, 0, 0, 0])
     f = torch.ones(gh.nelems, dtype=torch.float64, device="cuda")
     phi = torch.zeros_like(f)
-    st = op.solve(phi, f, params=amr.default_params(rtol=1e-10, max_vcycles=40, precision=amr.MIXED))
+    # host-driven loop: kernels inside a graph's conditional body cannot be profiled
+    st = op.solve(phi, f, params=amr.default_params(rtol=1e-10, max_vcycles=40, precision=amr.MIXED, use_graph=0))
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "large", "vcycles": st["vcycles"], "final_res": st["final_res"]}))
     return 0
