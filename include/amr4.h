@@ -156,7 +156,7 @@ typedef struct {
   int fuse_coarse;   /* 1: run the coarse end of the level-0 V-cycle in one shared-memory
                         block (same arithmetic as the per-grid kernels); default 0: on GB300
                         one block is slower than the graph's per-grid launches              */
-  int temporal_blocking; /* 1 (default): in FP32 V-cycles on 2-D level-0 multigrid grids,
+  int temporal_blocking; /* 1 (default): in forward FP32 V-cycles on 2-D level-0 multigrid grids,
                         each down leg (nu1 sweeps, residual, restriction) and each up leg
                         (prolongation, nu2 sweeps) is one launch over shared-memory tiles
                         with halos (same per-cell arithmetic); 0: one launch per sweep    */

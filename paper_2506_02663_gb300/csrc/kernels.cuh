@@ -628,23 +628,22 @@ __global__ void __launch_bounds__(BX* BY) k_prolong2d(LevelView fine, LevelView 
 }
 
 // ------------------------------------------------------------------------ temporally blocked 2-D smoothing
-// One block owns a tile of a single-patch 2-D grid and keeps a region (the tile plus a halo,
-// clipped to the patch) in shared memory with the global patch's own index map (interior
-// plus two ghost layers, lo = the region's global origin).  The per-cell code is the same as
-// the standalone kernels' (cell_level_op, cell_restrict, cell_prolong): physical ghosts are
-// evaluated from the region's own cells (the region reaches the domain face whenever a
-// stencil does), and reads past a region edge that is not a domain face see the zeroed ghost
-// slots.  At a patch edge that is not a domain face those zeros are exactly the zero CF
-// ghosts of correction smoothing; at an edge interior to the patch the values they spoil
-// move inward two cells per sweep, and the halo keeps them out of the tile: 2 nu cells for nu
-// sweeps, 2 more for the residual.  Sweep s (from 1) updates the region shrunk by 2 s on
-// every side that is not a patch face.
+// One block owns a tile of a single-patch 2-D multigrid grid (the patch is the whole
+// domain) and keeps a region -- the tile plus a halo, clipped to the domain -- in shared
+// memory, laid out with two ghost layers like the global patch.  Before every sweep the
+// physical ghost layers of the domain faces the region touches are materialised from the
+// current iterate (homogeneous Eqs. velBCHomoDiri5th / Neumann5), so that every cell runs
+// the same interior stencil; only the Jacobi diagonal differs within two cells of a face
+// (the ghost formulas put weight back on the cell itself).  Sweep s (from 1) updates the
+// region shrunk by 2 s on every side that is not a domain face; that region never reads
+// past what sweep s-1 produced, so no value from outside the region is ever used, and the
+// halo (2 nu, plus 2 for a residual) keeps the shrinkage out of the tile.
 struct TileGeom {
-  int i0, j0;      // tile origin (patch-local)
+  int i0, j0;      // tile origin (patch-local = global)
   int tw, th;      // tile extents
-  int r0, r1;      // region origin (patch-local)
+  int r0, r1;      // region origin
   int rw, rh;      // region extents
-  int fl0, fh0, fl1, fh1;  // 1 where the region side is a patch face (does not shrink)
+  int fl0, fh0, fl1, fh1;  // 1 where the region side is a domain face (does not shrink)
 };
 
 __device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, int tx, int ty, int halo) {
@@ -666,20 +665,6 @@ __device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, int tx, int t
   return t;
 }
 
-__device__ __forceinline__ PatchDesc region_desc(const PatchDesc& gp, const TileGeom& t) {
-  PatchDesc sp;
-  sp.off = 0;
-  sp.sy = t.rw + 2 * NG;
-  sp.sz = 0;
-  sp.n[0] = t.rw;
-  sp.n[1] = t.rh;
-  sp.n[2] = 1;
-  sp.lo[0] = gp.lo[0] + t.r0;
-  sp.lo[1] = gp.lo[1] + t.r1;
-  sp.lo[2] = 0;
-  return sp;
-}
-
 // region cells updated by sweep s (shrunk by 2 s on non-face sides)
 __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int& b0, int& a1, int& b1) {
   a0 = t.fl0 ? 0 : 2 * s;
@@ -688,50 +673,92 @@ __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int
   b1 = t.fh1 ? t.rh : t.rh - 2 * s;
 }
 
-// One weighted-Jacobi sweep over the box [a0,b0) x [a1,b1) of a shared-memory region: cells
-// whose stencil (and, for the transpose, the ghost-coefficient gathers) stays inside the
-// domain take the interior form with the constant diagonal (ood = omega / diag); the others
-// run cell_level_op.  Same summation order as cell_Lx.
-template <typename T, bool TR, bool ZERO>
-__device__ __forceinline__ void sweep_box_cells(const LevelView& lv, const PatchDesc& sp, const T* __restrict__ cur,
-                                                T* __restrict__ oth, const T* __restrict__ sb, int a0, int b0, int a1,
-                                                int b1, T alpha, T beta, T omega, T ood) {
-  constexpr int M = TR ? 4 : 2;
-  const int sy = (int)sp.sy;
-  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
-  for (int j = a1 + (int)threadIdx.y; j < b1; j += (int)blockDim.y)
-    for (int i = a0 + (int)threadIdx.x; i < b0; i += (int)blockDim.x) {
-      const int g0 = sp.lo[0] + i, g1 = sp.lo[1] + j;
-      if (g0 >= M && g0 <= lv.ndom[0] - 1 - M && g1 >= M && g1 <= lv.ndom[1] - 1 - M) {
-        const int o = (j + NG) * sy + (i + NG);
-        if (ZERO) {
-          oth[o] = ood * sb[o];
-        } else {
-          const T xc = cur[o];
-          const T s1 = (cur[o - 1] + cur[o + 1]) + (cur[o - sy] + cur[o + sy]);
-          const T s2 = (cur[o - 2] + cur[o + 2]) + (cur[o - 2 * sy] + cur[o + 2 * sy]);
-          const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
-          const T ax = alpha * xc + beta * (lap * inv);
-          oth[o] = xc + ood * (sb[o] - ax);
-        }
-      } else if (ZERO) {
-        cell_level_op<T, 2, OP_JACOBI0, TR>(lv, sp, i, j, 0, nullptr, sb, oth, nullptr, alpha, beta, omega);
-      } else {
-        cell_level_op<T, 2, OP_JACOBI, TR>(lv, sp, i, j, 0, cur, sb, oth, nullptr, alpha, beta, omega);
-      }
+__device__ __forceinline__ int blk_tid() { return (int)(threadIdx.y * blockDim.x + threadIdx.x); }
+__device__ __forceinline__ int blk_nth() { return (int)(blockDim.x * blockDim.y); }
+
+// Physical ghost layers of the region's domain faces for rows [a1,b1) / columns [a0,b0).
+template <typename T>
+__device__ __forceinline__ void region_ghosts(const LevelView& lv, const TileGeom& tg, T* __restrict__ a, int sy, int a0,
+                                              int b0, int a1, int b1) {
+  const int tid = blk_tid(), nth = blk_nth();
+  const int nr = b1 - a1, nc = b0 - a0;
+  // x faces: 2 sides x 2 layers x nr rows; y faces: 2 x 2 x nc columns
+  const int nx = 4 * nr, ny = 4 * nc;
+  for (int q = tid; q < nx + ny; q += nth) {
+    if (q < nx) {
+      const int side = q / (2 * nr), layer = (q / nr) % 2, j = a1 + q % nr;
+      if (side == 0 ? !tg.fl0 : !tg.fh0) continue;
+      const int type = lv.bc[side];
+      const int row = (j + NG) * sy + NG;
+      T v = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[row + (side == 0 ? m : tg.rw - 1 - m)];
+      a[row + (side == 0 ? -1 - layer : tg.rw + layer)] = v;
+    } else {
+      const int q2 = q - nx;
+      const int side = q2 / (2 * nc), layer = (q2 / nc) % 2, i = a0 + q2 % nc;
+      if (side == 0 ? !tg.fl1 : !tg.fh1) continue;
+      const int type = lv.bc[2 + side];
+      const int col = NG + i;
+      T v = T(0);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[(NG + (side == 0 ? m : tg.rh - 1 - m)) * sy + col];
+      a[(NG + (side == 0 ? -1 - layer : tg.rh + layer)) * sy + col] = v;
     }
+  }
 }
 
-template <typename T, bool TR>
-__device__ __forceinline__ T* smooth_region(const LevelView& lv, const PatchDesc& sp, const TileGeom& tg, T* cur, T* oth,
-                                            const T* sb, int nu, bool from_zero, T alpha, T beta, T omega, T ood) {
+// Jacobi diagonal correction (x 12 h^2) of a cell at global index g along one dimension
+template <typename T>
+__device__ __forceinline__ T dcorr_1d(const LevelView& lv, int d, int g) {
+  if (g == 0) return pick<T>(lv.dcorr[2 * d][0], lv.dcorr_f[2 * d][0]);
+  if (g == 1) return pick<T>(lv.dcorr[2 * d][1], lv.dcorr_f[2 * d][1]);
+  if (g == lv.ndom[d] - 1) return pick<T>(lv.dcorr[2 * d + 1][0], lv.dcorr_f[2 * d + 1][0]);
+  if (g == lv.ndom[d] - 2) return pick<T>(lv.dcorr[2 * d + 1][1], lv.dcorr_f[2 * d + 1][1]);
+  return T(0);
+}
+
+// 12 h^2 L x at smem offset o (interior stencil; ghosts materialised), cell_Lx's order
+template <typename T>
+__device__ __forceinline__ T lap_smem(const T* __restrict__ a, int o, int sy) {
+  const T xc = a[o];
+  const T s1 = (a[o - 1] + a[o + 1]) + (a[o - sy] + a[o + sy]);
+  const T s2 = (a[o - 2] + a[o + 2]) + (a[o - 2 * sy] + a[o + 2 * sy]);
+  return (T(16) * s1 - s2 - T(60) * xc) + T(0);
+}
+
+// nu weighted-Jacobi sweeps on the region; returns the buffer holding the result
+template <typename T, bool ZERO>
+__device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, int sy, T* cur, T* oth,
+                                            const T* __restrict__ sb, int nu, T alpha, T beta, T omega, T ood) {
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  const int base0 = tg.r0, base1 = tg.r1;
   for (int s = 1; s <= nu; ++s) {
     int a0, b0, a1, b1;
     sweep_box(tg, s, a0, b0, a1, b1);
-    if (from_zero && s == 1)
-      sweep_box_cells<T, TR, true>(lv, sp, cur, oth, sb, a0, b0, a1, b1, alpha, beta, omega, ood);
-    else
-      sweep_box_cells<T, TR, false>(lv, sp, cur, oth, sb, a0, b0, a1, b1, alpha, beta, omega, ood);
+    const bool zero = ZERO && s == 1;
+    if (!zero) {
+      // ghosts of the current iterate for the rows / columns this sweep reads
+      int c0, d0, c1, d1;
+      sweep_box(tg, s - 1, c0, d0, c1, d1);
+      region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1);
+      __syncthreads();
+    }
+    for (int j = a1 + (int)threadIdx.y; j < b1; j += (int)blockDim.y) {
+      const T cy = dcorr_1d<T>(lv, 1, base1 + j);
+      for (int i = a0 + (int)threadIdx.x; i < b0; i += (int)blockDim.x) {
+        const int o = (j + NG) * sy + (i + NG);
+        const T cx = dcorr_1d<T>(lv, 0, base0 + i);
+        const T w = (cx == T(0) && cy == T(0)) ? ood : omega / (alpha + beta * inv * ((T(-60) + cx) + cy));
+        if (zero) {
+          oth[o] = w * sb[o];
+        } else {
+          const T xc = cur[o];
+          const T ax = alpha * xc + beta * (lap_smem(cur, o, sy) * inv);
+          oth[o] = xc + w * (sb[o] - ax);
+        }
+      }
+    }
     __syncthreads();
     T* sw = cur;
     cur = oth;
@@ -740,102 +767,96 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const PatchDesc
   return cur;
 }
 
-__device__ __forceinline__ int blk_tid() { return (int)(threadIdx.y * blockDim.x + threadIdx.x); }
-__device__ __forceinline__ int blk_nth() { return (int)(blockDim.x * blockDim.y); }
-
-template <typename T>
-__device__ __forceinline__ void zero_region(T* a, int n) {
-  for (int q = blk_tid(); q < n; q += blk_nth()) a[q] = T(0);
-}
-
 // Down leg of one multigrid level: nu weighted-Jacobi sweeps from zero, the smoothed x
 // written to xo, and the residual f - A x restricted (2x2 average) into the next grid's
-// right-hand side bcn.  halo = 2 nu + 2.  xo is not read (no block reads another's tile).
-template <typename T, bool TR>
-__global__ void __launch_bounds__(512) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
+// right-hand side bcn.  halo = 2 nu + 2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
                                                    int nu, const T* __restrict__ b, T* __restrict__ xo,
                                                    T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, tx, ty, halo);
-  const PatchDesc sp = region_desc(gp, tg);
-  const int sy = (int)sp.sy;
+  const int sy = tg.rw + 2 * NG;
   const int E = sy * (tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
-  zero_region(sx, 3 * E);
-  __syncthreads();
   const T* __restrict__ bg = b + gp.off;
   const int gsy = (int)gp.sy;
   for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
       sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
   __syncthreads();
-  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, nu, true, alpha, beta, omega, ood);
+  T* cur = smooth_region<T, true>(lv, tg, sy, sx, st, sb, nu, alpha, beta, omega, ood);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x)
       xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
-  // residual restriction: interior children in the fast form, the others through cell_restrict
-  constexpr int M = TR ? 4 : 2;
+  // residual of the tile's cells (ghosts of the final iterate first), restricted
+  int c0, d0, c1, d1;
+  sweep_box(tg, nu, c0, d0, c1, d1);
+  region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1);
+  __syncthreads();
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   const int cw = tg.tw / 2, ch = tg.th / 2;
+  const int csy = (int)gcp.sy;
+  T* __restrict__ cg = bcn + gcp.off;
   for (int cj = (int)threadIdx.y; cj < ch; cj += (int)blockDim.y)
     for (int ci = (int)threadIdx.x; ci < cw; ci += (int)blockDim.x) {
-      const int g[3] = {(gp.lo[0] + tg.i0) / 2 + ci, (gp.lo[1] + tg.j0) / 2 + cj, 0};
-      if (2 * g[0] >= M && 2 * g[0] + 1 <= lv.ndom[0] - 1 - M && 2 * g[1] >= M && 2 * g[1] + 1 <= lv.ndom[1] - 1 - M) {
-        T acc = T(0);
+      T acc = T(0);
 #pragma unroll
-        for (int q1 = 0; q1 < 2; ++q1)
+      for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
-          for (int q0 = 0; q0 < 2; ++q0) {
-            const int o = (2 * g[1] + q1 - sp.lo[1] + NG) * sy + (2 * g[0] + q0 - sp.lo[0] + NG);
-            const T xc = cur[o];
-            const T s1 = (cur[o - 1] + cur[o + 1]) + (cur[o - sy] + cur[o + sy]);
-            const T s2 = (cur[o - 2] + cur[o + 2]) + (cur[o - 2 * sy] + cur[o + 2 * sy]);
-            const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
-            acc += sb[o] - (alpha * xc + beta * (lap * inv));
-          }
-        bcn[poff(gcp, g[0] - gcp.lo[0], g[1] - gcp.lo[1], 0)] = acc * T(0.25);
-      } else {
-        cell_restrict<T, 2, true, TR>(lv, sp, gcp, g, cur, sb, bcn, alpha, beta);
-      }
+        for (int q0 = 0; q0 < 2; ++q0) {
+          const int o = (tj + 2 * cj + q1 + NG) * sy + (ti + 2 * ci + q0 + NG);
+          const T xc = cur[o];
+          acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
+        }
+      cg[((tg.j0 >> 1) + cj + NG) * csy + (tg.i0 >> 1) + ci + NG] = acc * T(0.25);
     }
 }
 
-// Up leg of one multigrid level: x = xi + linear prolongation of the coarse correction xc,
-// then nu weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
+// Up leg of one multigrid level: x = xi + linear prolongation of the coarse correction xc
+// (coarse values outside the domain from the homogeneous extension with corners), then nu
+// weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
 // halo = 2 nu.
-template <typename T, bool TR>
-__global__ void __launch_bounds__(512) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
                                                  int ty, int halo, int nu, const T* __restrict__ xc,
                                                  const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
                                                  T alpha, T beta, T omega, T ood) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, tx, ty, halo);
-  const PatchDesc sp = region_desc(gp, tg);
-  const int sy = (int)sp.sy;
+  const int sy = tg.rw + 2 * NG;
   const int E = sy * (tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
-  zero_region(sx, 3 * E);
-  __syncthreads();
   const int gsy = (int)gp.sy, csy = (int)gcp.sy;
   const T* __restrict__ bg = b + gp.off;
   const T* __restrict__ xg = xi + gp.off;
   const T* __restrict__ cg = xc + gcp.off;
+  PatchDesc sp;  // region in the global patch's index map form, for the generic prolongation
+  sp.off = 0;
+  sp.sy = sy;
+  sp.sz = 0;
+  sp.n[0] = tg.rw;
+  sp.n[1] = tg.rh;
+  sp.n[2] = 1;
+  sp.lo[0] = tg.r0;
+  sp.lo[1] = tg.r1;
+  sp.lo[2] = 0;
   for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x) {
       const int og = (tg.r1 + j + NG) * gsy + tg.r0 + i + NG;
       const int os = (j + NG) * sy + i + NG;
       sb[os] = bg[og];
-      const int gf0 = sp.lo[0] + i, gf1 = sp.lo[1] + j;
+      const int gf0 = tg.r0 + i, gf1 = tg.r1 + j;
       const int p0 = gf0 >> 1, p1 = gf1 >> 1;
       const int s0 = (gf0 & 1) ? 1 : -1, s1 = (gf1 & 1) ? 1 : -1;
       if (p0 + s0 >= 0 && p0 + s0 < cv.ndom[0] && p1 + s1 >= 0 && p1 + s1 < cv.ndom[1]) {
-        const int oc = (p1 - gcp.lo[1] + NG) * csy + (p0 - gcp.lo[0] + NG);
+        const int oc = (p1 + NG) * csy + (p0 + NG);
         T v = T(0);
         v += (T(0.75) * T(0.75)) * cg[oc];
         v += (T(0.25) * T(0.75)) * cg[oc + s0];
@@ -849,7 +870,7 @@ __global__ void __launch_bounds__(512) k_mg_up2d(LevelView lv, LevelView cv, Pat
       }
     }
   __syncthreads();
-  const T* cur = smooth_region<T, TR>(lv, sp, tg, sx, st, sb, nu, false, alpha, beta, omega, ood);
+  const T* cur = smooth_region<T, false>(lv, tg, sy, sx, st, sb, nu, alpha, beta, omega, ood);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xw = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)

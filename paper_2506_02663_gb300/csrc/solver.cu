@@ -716,13 +716,17 @@ amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, si
 }
 
 // ---------------------------------------------------------------- temporally blocked legs
-constexpr int BLK_TX = 32, BLK_TY = 16, BLK_MAX_NU = 6;
+constexpr int BLK_MAX_NU = 6;
+
+// tile edge: small grids need many blocks, large grids a small halo share
+inline int blk_tile(const MgGrid& g) { return (long long)g.n[0] * g.n[1] >= 1024LL * 1024 ? 32 : 16; }
 
 // dynamic shared memory of a blocked leg: three region arrays with two ghost layers
 template <typename T>
 size_t blk_smem(const MgGrid& g, int halo) {
-  const long long w = std::min(BLK_TX + 2 * halo, g.n[0]) + 2 * NG;
-  const long long hh = std::min(BLK_TY + 2 * halo, g.n[1]) + 2 * NG;
+  const int t = blk_tile(g);
+  const long long w = std::min(t + 2 * halo, g.n[0]) + 2 * NG;
+  const long long hh = std::min(t + 2 * halo, g.n[1]) + 2 * NG;
   return (size_t)(3 * w * hh) * sizeof(T);
 }
 
@@ -731,10 +735,8 @@ amr_status blk_attrs() {
   static bool done = false;
   if (done) return AMR_OK;
   const int bytes = 200 * 1024;
-  CK(cudaFuncSetAttribute(k_mg_down2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_mg_down2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_mg_up2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_mg_up2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_down2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_up2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done = true;
   return AMR_OK;
 }
@@ -758,29 +760,30 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     return launch_check();
   }
   const LevelView cv = mg_view(h, m + 1, op->bc);
-  if constexpr (D == 2 && sizeof(T) == 4) if (p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
-    // temporally blocked legs (FP32 V-cycles only: FP64 arithmetic is scarce on this part
-    // and the halo recomputation would cost more than the launches it saves): one launch
-    // for {nu1 sweeps, residual, restriction} into t, one for {prolongation, nu2 sweeps}
-    // from t into x
+  if constexpr (D == 2 && sizeof(T) == 4 && !TR) if (p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
+    // temporally blocked legs (FP32 forward V-cycles: FP64 arithmetic is scarce on this
+    // part and the halo recomputation would cost more than the launches it saves): one
+    // launch for {nu1 sweeps, residual, restriction} into t, one for {prolongation, nu2
+    // sweeps} from t into x
     const MgGrid& g = h->mg[m];
     const MgGrid& gc = h->mg[m + 1];
-    dim3 grid((g.n[0] + BLK_TX - 1) / BLK_TX, (g.n[1] + BLK_TY - 1) / BLK_TY, 1);
-    const dim3 blk(32, 16, 1);
+    const int tt = blk_tile(g);
+    dim3 grid((g.n[0] + tt - 1) / tt, (g.n[1] + tt - 1) / tt, 1);
+    const dim3 blk(32, 8, 1);
     const int hd = 2 * p.nu1 + 2, hu = 2 * p.nu2;
     const double dint = op->alpha - 60.0 * op->beta * lv.inv12h2;  // interior diagonal
     const T ood = T(p.omega / dint);
     const double cells = (double)g.n[0] * g.n[1];
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    k_mg_down2d<T, TR><<<grid, blk, blk_smem<T>(g, hd), st>>>(lv, g.patch, gc.patch, BLK_TX, BLK_TY, hd, p.nu1, b, t,
-                                                             S.mb[m + 1], T(op->alpha), T(op->beta), T(p.omega), ood);
+    k_mg_down2d<T><<<grid, blk, blk_smem<T>(g, hd), st>>>(lv, g.patch, gc.patch, tt, tt, hd, p.nu1, b, t, S.mb[m + 1],
+                                                         T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_DOWN, (2.0 + 0.25) * sizeof(T) * cells);  // read f, write x, write coarse f
     TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
     prof_begin(st, &ev);
-    k_mg_up2d<T, TR><<<grid, blk, blk_smem<T>(g, hu), st>>>(lv, cv, g.patch, gc.patch, BLK_TX, BLK_TY, hu, p.nu2,
-                                                           S.mx[m + 1], b, t, x, T(op->alpha), T(op->beta), T(p.omega), ood);
+    k_mg_up2d<T><<<grid, blk, blk_smem<T>(g, hu), st>>>(lv, cv, g.patch, gc.patch, tt, tt, hu, p.nu2, S.mx[m + 1], b, t,
+                                                       x, T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_UP, (3.0 + 0.25) * sizeof(T) * cells);  // read x, f, coarse x; write x
     return AMR_OK;
