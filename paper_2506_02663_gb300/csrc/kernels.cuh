@@ -708,14 +708,44 @@ __device__ __forceinline__ void region_ghosts(const LevelView& lv, const TileGeo
   }
 }
 
-// Jacobi diagonal correction (x 12 h^2) of a cell at global index g along one dimension
+// Weighted-Jacobi factors omega / diag of a region, table driven: the diagonal differs from
+// the interior one only within two cells of a domain face (the ghost formulas put weight back
+// on the cell itself), so a cell's factor is wt[kx[i] + 5 ky[j]] with kx, ky in 0..4 (0:
+// interior, 1, 2: first, second cell from the low face, 3, 4: from the high face).
+constexpr int BLK_MAX_REGION = 64;
+struct JacobiTable {
+  float wf[25];
+  double wd[25];
+  unsigned char kx[BLK_MAX_REGION], ky[BLK_MAX_REGION];
+};
+
 template <typename T>
-__device__ __forceinline__ T dcorr_1d(const LevelView& lv, int d, int g) {
-  if (g == 0) return pick<T>(lv.dcorr[2 * d][0], lv.dcorr_f[2 * d][0]);
-  if (g == 1) return pick<T>(lv.dcorr[2 * d][1], lv.dcorr_f[2 * d][1]);
-  if (g == lv.ndom[d] - 1) return pick<T>(lv.dcorr[2 * d + 1][0], lv.dcorr_f[2 * d + 1][0]);
-  if (g == lv.ndom[d] - 2) return pick<T>(lv.dcorr[2 * d + 1][1], lv.dcorr_f[2 * d + 1][1]);
-  return T(0);
+__device__ __forceinline__ T jt_get(const JacobiTable& t, int k);
+template <>
+__device__ __forceinline__ float jt_get<float>(const JacobiTable& t, int k) { return t.wf[k]; }
+template <>
+__device__ __forceinline__ double jt_get<double>(const JacobiTable& t, int k) { return t.wd[k]; }
+
+__device__ __forceinline__ int face_class(int g, int n) {
+  return g == 0 ? 1 : g == 1 ? 2 : g == n - 1 ? 3 : g == n - 2 ? 4 : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void build_jacobi_table(JacobiTable& jt, const LevelView& lv, const TileGeom& tg, T alpha,
+                                                   T beta, T omega, T ood) {
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  const int tid = blk_tid(), nth = blk_nth();
+  for (int q = tid; q < 25; q += nth) {
+    const int a = q % 5, b = q / 5;
+    // diag_sum's order: -30 D, then the x correction, then the y correction
+    const T cx = a == 0 ? T(0) : pick<T>(lv.dcorr[(a - 1) / 2][(a - 1) % 2], lv.dcorr_f[(a - 1) / 2][(a - 1) % 2]);
+    const T cy = b == 0 ? T(0) : pick<T>(lv.dcorr[2 + (b - 1) / 2][(b - 1) % 2], lv.dcorr_f[2 + (b - 1) / 2][(b - 1) % 2]);
+    const T w = q == 0 ? ood : omega / (alpha + beta * inv * ((T(-60) + cx) + cy));
+    if (sizeof(T) == 4) jt.wf[q] = (float)w;
+    else jt.wd[q] = (double)w;
+  }
+  for (int q = tid; q < tg.rw; q += nth) jt.kx[q] = (unsigned char)face_class(tg.r0 + q, lv.ndom[0]);
+  for (int q = tid; q < tg.rh; q += nth) jt.ky[q] = (unsigned char)face_class(tg.r1 + q, lv.ndom[1]);
 }
 
 // 12 h^2 L x at smem offset o (interior stencil; ghosts materialised), cell_Lx's order
@@ -729,10 +759,9 @@ __device__ __forceinline__ T lap_smem(const T* __restrict__ a, int o, int sy) {
 
 // nu weighted-Jacobi sweeps on the region; returns the buffer holding the result
 template <typename T, bool ZERO>
-__device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, int sy, T* cur, T* oth,
-                                            const T* __restrict__ sb, int nu, T alpha, T beta, T omega, T ood) {
+__device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, const JacobiTable& jt, int sy,
+                                            T* cur, T* oth, const T* __restrict__ sb, int nu, T alpha, T beta) {
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
-  const int base0 = tg.r0, base1 = tg.r1;
   for (int s = 1; s <= nu; ++s) {
     int a0, b0, a1, b1;
     sweep_box(tg, s, a0, b0, a1, b1);
@@ -745,11 +774,10 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
       __syncthreads();
     }
     for (int j = a1 + (int)threadIdx.y; j < b1; j += (int)blockDim.y) {
-      const T cy = dcorr_1d<T>(lv, 1, base1 + j);
+      const int ky5 = 5 * jt.ky[j];
       for (int i = a0 + (int)threadIdx.x; i < b0; i += (int)blockDim.x) {
         const int o = (j + NG) * sy + (i + NG);
-        const T cx = dcorr_1d<T>(lv, 0, base0 + i);
-        const T w = (cx == T(0) && cy == T(0)) ? ood : omega / (alpha + beta * inv * ((T(-60) + cx) + cy));
+        const T w = jt_get<T>(jt, jt.kx[i] + ky5);
         if (zero) {
           oth[o] = w * sb[o];
         } else {
@@ -781,13 +809,15 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
+  __shared__ JacobiTable jt;
+  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood);
   const T* __restrict__ bg = b + gp.off;
   const int gsy = (int)gp.sy;
   for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
       sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
   __syncthreads();
-  T* cur = smooth_region<T, true>(lv, tg, sy, sx, st, sb, nu, alpha, beta, omega, ood);
+  T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
@@ -837,6 +867,7 @@ __global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, Pat
   const T* __restrict__ bg = b + gp.off;
   const T* __restrict__ xg = xi + gp.off;
   const T* __restrict__ cg = xc + gcp.off;
+  __shared__ JacobiTable jt;
   PatchDesc sp;  // region in the global patch's index map form, for the generic prolongation
   sp.off = 0;
   sp.sy = sy;
@@ -869,8 +900,9 @@ __global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, Pat
         cell_prolong<T, 2>(cv, sp, gcp, gf, xc, sx, (T*)nullptr);
       }
     }
+  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood);
   __syncthreads();
-  const T* cur = smooth_region<T, false>(lv, tg, sy, sx, st, sb, nu, alpha, beta, omega, ood);
+  const T* cur = smooth_region<T, false>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xw = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
