@@ -676,34 +676,36 @@ __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int
 __device__ __forceinline__ int blk_tid() { return (int)(threadIdx.y * blockDim.x + threadIdx.x); }
 __device__ __forceinline__ int blk_nth() { return (int)(blockDim.x * blockDim.y); }
 
-// Physical ghost layers of the region's domain faces for rows [a1,b1) / columns [a0,b0).
+// Physical ghost layers of the region's domain faces for rows [a1,b1) / columns [a0,b0)
+// (only blocks whose region touches a face do any work here).
 template <typename T>
 __device__ __forceinline__ void region_ghosts(const LevelView& lv, const TileGeom& tg, T* __restrict__ a, int sy, int a0,
                                               int b0, int a1, int b1) {
+  if (!(tg.fl0 | tg.fh0 | tg.fl1 | tg.fh1)) return;
   const int tid = blk_tid(), nth = blk_nth();
   const int nr = b1 - a1, nc = b0 - a0;
-  // x faces: 2 sides x 2 layers x nr rows; y faces: 2 x 2 x nc columns
-  const int nx = 4 * nr, ny = 4 * nc;
-  for (int q = tid; q < nx + ny; q += nth) {
-    if (q < nx) {
-      const int side = q / (2 * nr), layer = (q / nr) % 2, j = a1 + q % nr;
-      if (side == 0 ? !tg.fl0 : !tg.fh0) continue;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? tg.fl0 : tg.fh0) {
       const int type = lv.bc[side];
-      const int row = (j + NG) * sy + NG;
-      T v = T(0);
+      for (int q = tid; q < 2 * nr; q += nth) {
+        const int layer = q & 1, j = a1 + (q >> 1);
+        const int row = (j + NG) * sy + NG;
+        T v = T(0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[row + (side == 0 ? m : tg.rw - 1 - m)];
-      a[row + (side == 0 ? -1 - layer : tg.rw + layer)] = v;
-    } else {
-      const int q2 = q - nx;
-      const int side = q2 / (2 * nc), layer = (q2 / nc) % 2, i = a0 + q2 % nc;
-      if (side == 0 ? !tg.fl1 : !tg.fh1) continue;
+        for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[row + (side == 0 ? m : tg.rw - 1 - m)];
+        a[row + (side == 0 ? -1 - layer : tg.rw + layer)] = v;
+      }
+    }
+    if (side == 0 ? tg.fl1 : tg.fh1) {
       const int type = lv.bc[2 + side];
-      const int col = NG + i;
-      T v = T(0);
+      for (int q = tid; q < 2 * nc; q += nth) {
+        const int layer = q & 1, col = NG + a0 + (q >> 1);
+        T v = T(0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[(NG + (side == 0 ? m : tg.rh - 1 - m)) * sy + col];
-      a[(NG + (side == 0 ? -1 - layer : tg.rh + layer)) * sy + col] = v;
+        for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[(NG + (side == 0 ? m : tg.rh - 1 - m)) * sy + col];
+        a[(NG + (side == 0 ? -1 - layer : tg.rh + layer)) * sy + col] = v;
+      }
     }
   }
 }
@@ -847,12 +849,51 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
     }
 }
 
+// Coarse value at (c0, c1) of a single-patch 2-D grid, at most one cell outside the domain
+// in each dimension: the homogeneous physical extension (layer-1 ghost formula), applied
+// dimension after dimension at corners (Fig. 1(c) order, as read_ext does).
+template <typename T>
+__device__ __forceinline__ T coarse_ext2d(const T* __restrict__ cg, int csy, const LevelView& cv, int c0, int c1) {
+  const int n0 = cv.ndom[0], n1 = cv.ndom[1];
+  const bool o0 = c0 < 0 || c0 >= n0, o1 = c1 < 0 || c1 >= n1;
+  if (!o0 && !o1) return cg[(c1 + NG) * csy + c0 + NG];
+  int ix[4], iy[4];
+  T wx[4], wy[4];
+  int cx = 1, cyc = 1;
+  ix[0] = c0;
+  wx[0] = T(1);
+  iy[0] = c1;
+  wy[0] = T(1);
+  if (o0) {
+    const int side = c0 < 0 ? 0 : 1, type = cv.bc[side];
+    cx = 4;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ix[m] = side == 0 ? m : n0 - 1 - m;
+      wx[m] = gcoef<T>(type, 0, m);
+    }
+  }
+  if (o1) {
+    const int side = c1 < 0 ? 0 : 1, type = cv.bc[2 + side];
+    cyc = 4;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      iy[m] = side == 0 ? m : n1 - 1 - m;
+      wy[m] = gcoef<T>(type, 0, m);
+    }
+  }
+  T v = T(0);
+  for (int a = 0; a < cx; ++a)
+    for (int b = 0; b < cyc; ++b) v += wx[a] * wy[b] * cg[(iy[b] + NG) * csy + ix[a] + NG];
+  return v;
+}
+
 // Up leg of one multigrid level: x = xi + linear prolongation of the coarse correction xc
 // (coarse values outside the domain from the homogeneous extension with corners), then nu
 // weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
 // halo = 2 nu.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+__global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
                                                  int ty, int halo, int nu, const T* __restrict__ xc,
                                                  const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
                                                  T alpha, T beta, T omega, T ood) {
@@ -868,16 +909,6 @@ __global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, Pat
   const T* __restrict__ xg = xi + gp.off;
   const T* __restrict__ cg = xc + gcp.off;
   __shared__ JacobiTable jt;
-  PatchDesc sp;  // region in the global patch's index map form, for the generic prolongation
-  sp.off = 0;
-  sp.sy = sy;
-  sp.sz = 0;
-  sp.n[0] = tg.rw;
-  sp.n[1] = tg.rh;
-  sp.n[2] = 1;
-  sp.lo[0] = tg.r0;
-  sp.lo[1] = tg.r1;
-  sp.lo[2] = 0;
   for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x) {
       const int og = (tg.r1 + j + NG) * gsy + tg.r0 + i + NG;
@@ -886,19 +917,25 @@ __global__ void __launch_bounds__(256) k_mg_up2d(LevelView lv, LevelView cv, Pat
       const int gf0 = tg.r0 + i, gf1 = tg.r1 + j;
       const int p0 = gf0 >> 1, p1 = gf1 >> 1;
       const int s0 = (gf0 & 1) ? 1 : -1, s1 = (gf1 & 1) ? 1 : -1;
+      T c01, c10, c11;
+      const T c00 = cg[(p1 + NG) * csy + (p0 + NG)];
       if (p0 + s0 >= 0 && p0 + s0 < cv.ndom[0] && p1 + s1 >= 0 && p1 + s1 < cv.ndom[1]) {
         const int oc = (p1 + NG) * csy + (p0 + NG);
-        T v = T(0);
-        v += (T(0.75) * T(0.75)) * cg[oc];
-        v += (T(0.25) * T(0.75)) * cg[oc + s0];
-        v += (T(0.75) * T(0.25)) * cg[oc + s1 * csy];
-        v += (T(0.25) * T(0.25)) * cg[oc + s1 * csy + s0];
-        sx[os] = xg[og] + v;
+        c10 = cg[oc + s0];
+        c01 = cg[oc + s1 * csy];
+        c11 = cg[oc + s1 * csy + s0];
       } else {
-        sx[os] = xg[og];
-        const int gf[3] = {gf0, gf1, 0};
-        cell_prolong<T, 2>(cv, sp, gcp, gf, xc, sx, (T*)nullptr);
+        c10 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1);
+        c01 = coarse_ext2d<T>(cg, csy, cv, p0, p1 + s1);
+        c11 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1 + s1);
       }
+      // cell_prolong's order: (q0, q1) = (0,0), (1,0), (0,1), (1,1)
+      T v = T(0);
+      v += (T(0.75) * T(0.75)) * c00;
+      v += (T(0.25) * T(0.75)) * c10;
+      v += (T(0.75) * T(0.25)) * c01;
+      v += (T(0.25) * T(0.25)) * c11;
+      sx[os] = xg[og] + v;
     }
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood);
   __syncthreads();
