@@ -375,6 +375,7 @@ KERNEL_CLASSES = {
     "prolong": ("KC_PROLONG", "k_prolong2d / k_prolong: linear prolongation + correction"),
     "down_leg": ("KC_DOWN", "k_mg_down2d<float>: nu1 sweeps + residual + restriction, one launch per grid"),
     "up_leg": ("KC_UP", "k_mg_up2d<float>: prolongation + nu2 sweeps, one launch per grid"),
+    "coarse_block": ("KC_COARSE", "k_mg_coarse2d<float>: the V-cycle on the grids <= 64^2, one block"),
 }
 
 

@@ -341,7 +341,8 @@ long long amr_kernel_launches(void);
  * (ms) and the summed algorithmic bytes.  Classes: 0 weighted-Jacobi sweeps, 1 level
  * residual / apply, 2 restriction and average-down, 3 prolongation, 4 temporally blocked
  * down legs (f read, x and the coarse f written once), 5 temporally blocked up legs (x, f
- * and the coarse correction read once, x written once). */
+ * and the coarse correction read once, x written once), 6 one-block coarse V-cycles (f
+ * read, x written once). */
 amr_status amr_profile_enable(int on);
 amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes);
 

@@ -109,7 +109,7 @@ def kernel_launches():
     return int(_lib.amr_kernel_launches())
 
 
-KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG, KC_DOWN, KC_UP = 0, 1, 2, 3, 4, 5
+KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG, KC_DOWN, KC_UP, KC_COARSE = 0, 1, 2, 3, 4, 5, 6
 
 
 def profile_enable(on):

@@ -947,6 +947,136 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
       xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
 }
 
+// Coarse end of the 2-D level-0 multigrid in one block: every grid from m0 (at most 64 cells
+// per dimension) down to the coarsest lives in shared memory; the legs use the same region
+// sweeps as k_mg_down2d / k_mg_up2d with the whole grid as the region (every side a domain
+// face, nothing shrinks), and the dense bottom solve runs between the legs.
+constexpr int CB_MAX = 8;
+struct CoarseBlock2D {
+  int ng;                         // grids m0 .. coarsest
+  int nu1, nu2;
+  int nbot, ldb;
+  const double* minv;             // bottom inverse
+  PatchDesc gp;                   // global layout of grid m0 (right-hand side in, correction out)
+  int offx[CB_MAX], offt[CB_MAX], offb[CB_MAX];  // element offsets in dynamic shared memory
+  double ood[CB_MAX];             // omega / interior diagonal per grid
+  LevelView lv[CB_MAX];
+};
+
+__device__ __forceinline__ TileGeom whole_grid(const LevelView& lv) {
+  TileGeom t;
+  t.i0 = t.j0 = t.r0 = t.r1 = 0;
+  t.tw = t.rw = lv.ndom[0];
+  t.th = t.rh = lv.ndom[1];
+  t.fl0 = t.fh0 = t.fl1 = t.fh1 = 1;
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
+                                                      T alpha, T beta, T omega) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ JacobiTable jts[CB_MAX];
+  __shared__ double bot[1024];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int tid = blk_tid(), nth = blk_nth();
+  T* xs[CB_MAX];
+  for (int q = 0; q < cb.ng; ++q) {
+    build_jacobi_table<T>(jts[q], cb.lv[q], whole_grid(cb.lv[q]), alpha, beta, omega, T(cb.ood[q]));
+    xs[q] = sm + cb.offx[q];
+  }
+  {
+    const int n0 = cb.lv[0].ndom[0], n1 = cb.lv[0].ndom[1], sy = n0 + 2 * NG;
+    const T* __restrict__ bg = b + cb.gp.off;
+    const int gsy = (int)cb.gp.sy;
+    for (int t = tid; t < n0 * n1; t += nth) {
+      const int i = t % n0, j = t / n0;
+      sm[cb.offb[0] + (j + NG) * sy + i + NG] = bg[(j + NG) * gsy + i + NG];
+    }
+  }
+  __syncthreads();
+  const int M = cb.ng - 1;
+  for (int q = 0; q < M; ++q) {
+    const LevelView& lv = cb.lv[q];
+    const TileGeom tg = whole_grid(lv);
+    const int sy = tg.rw + 2 * NG;
+    T* sb = sm + cb.offb[q];
+    T* cur = smooth_region<T, true>(lv, tg, jts[q], sy, sm + cb.offx[q], sm + cb.offt[q], sb, cb.nu1, alpha, beta);
+    xs[q] = cur;
+    region_ghosts(lv, tg, cur, sy, 0, tg.rw, 0, tg.rh);
+    __syncthreads();
+    const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+    const int cw = tg.rw / 2, ch = tg.rh / 2, csy = cw + 2 * NG;
+    T* bc = sm + cb.offb[q + 1];
+    for (int t = tid; t < cw * ch; t += nth) {
+      const int ci = t % cw, cj = t / cw;
+      T acc = T(0);
+#pragma unroll
+      for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+        for (int q0 = 0; q0 < 2; ++q0) {
+          const int o = (2 * cj + q1 + NG) * sy + (2 * ci + q0 + NG);
+          const T xc = cur[o];
+          acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
+        }
+      bc[(cj + NG) * csy + ci + NG] = acc * T(0.25);
+    }
+    __syncthreads();
+  }
+  {
+    // dense bottom solve (FP64 accumulation), cell order x fastest
+    const int n0 = cb.lv[M].ndom[0], sy = n0 + 2 * NG;
+    const T* bm = sm + cb.offb[M];
+    for (int t = tid; t < cb.nbot; t += nth) bot[t] = (double)bm[(t / n0 + NG) * sy + t % n0 + NG];
+    __syncthreads();
+    T* xm = sm + cb.offx[M];
+    for (int t = tid; t < cb.nbot; t += nth) {
+      double acc = 0.0;
+      const double* row = cb.minv + (long long)t * cb.ldb;
+      for (int k = 0; k < cb.nbot; ++k) acc = fma(row[k], bot[k], acc);
+      xm[(t / n0 + NG) * sy + t % n0 + NG] = T(acc);
+    }
+    xs[M] = xm;
+    __syncthreads();
+  }
+  for (int q = M - 1; q >= 0; --q) {
+    const LevelView& lv = cb.lv[q];
+    const LevelView& cv = cb.lv[q + 1];
+    const TileGeom tg = whole_grid(lv);
+    const int sy = tg.rw + 2 * NG, csy = cv.ndom[0] + 2 * NG;
+    T* xq = xs[q];
+    const T* cg = xs[q + 1];
+    for (int t = tid; t < tg.rw * tg.rh; t += nth) {
+      const int i = t % tg.rw, j = t / tg.rw;
+      const int p0 = i >> 1, p1 = j >> 1;
+      const int s0 = (i & 1) ? 1 : -1, s1 = (j & 1) ? 1 : -1;
+      const T c00 = cg[(p1 + NG) * csy + p0 + NG];
+      const T c10 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1);
+      const T c01 = coarse_ext2d<T>(cg, csy, cv, p0, p1 + s1);
+      const T c11 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1 + s1);
+      T v = T(0);
+      v += (T(0.75) * T(0.75)) * c00;
+      v += (T(0.25) * T(0.75)) * c10;
+      v += (T(0.75) * T(0.25)) * c01;
+      v += (T(0.25) * T(0.25)) * c11;
+      xq[(j + NG) * sy + i + NG] += v;
+    }
+    __syncthreads();
+    T* oth = (xq == sm + cb.offx[q]) ? sm + cb.offt[q] : sm + cb.offx[q];
+    xs[q] = smooth_region<T, false>(lv, tg, jts[q], sy, xq, oth, sm + cb.offb[q], cb.nu2, alpha, beta);
+  }
+  {
+    const int n0 = cb.lv[0].ndom[0], n1 = cb.lv[0].ndom[1], sy = n0 + 2 * NG;
+    T* __restrict__ xg = x + cb.gp.off;
+    const int gsy = (int)cb.gp.sy;
+    const T* x0 = xs[0];
+    for (int t = tid; t < n0 * n1; t += nth) {
+      const int i = t % n0, j = t / n0;
+      xg[(j + NG) * gsy + i + NG] = x0[(j + NG) * sy + i + NG];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------ fused coarse V-cycle
 // The coarse end of the level-0 multigrid pyramid (every grid from m0 down to the coarsest,
 // whose arrays fit in shared memory together) runs as ONE block: the same per-cell

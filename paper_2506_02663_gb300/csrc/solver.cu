@@ -129,7 +129,7 @@ inline float pick_host<float>(double, float f) { return f; }
 // ---------------------------------------------------------------- bench instrumentation
 // When enabled, launches of the instrumented kernel classes are bracketed with CUDA events
 // on the launching stream; amr_profile_read() sums the event intervals.
-enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_DOWN = 4, PC_UP = 5, PC_NCLASS = 6 };
+enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_DOWN = 4, PC_UP = 5, PC_COARSE = 6, PC_NCLASS = 7 };
 struct ProfRec {
   cudaEvent_t a, b;
   int cls;
@@ -737,7 +737,57 @@ amr_status blk_attrs() {
   const int bytes = 200 * 1024;
   CK(cudaFuncSetAttribute(k_mg_down2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_up2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_coarse2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done = true;
+  return AMR_OK;
+}
+
+// first grid of the one-block coarse V-cycle: every grid from it down fits a block (at most
+// 64 cells per dimension, CB_MAX grids, shared-memory budget); -1 when none below the top
+inline int coarse_block_m0(const amr_hierarchy* h, size_t& bytes) {
+  const int M = (int)h->mg.size() - 1;
+  int m0 = -1;
+  size_t acc = 0;
+  for (int m = M; m >= 0 && M - m + 1 <= CB_MAX; --m) {
+    const MgGrid& g = h->mg[m];
+    if (g.n[0] > BLK_MAX_REGION || g.n[1] > BLK_MAX_REGION) break;
+    const size_t need = acc + 3 * (size_t)(g.n[0] + 2 * NG) * (g.n[1] + 2 * NG) * sizeof(float);
+    if (need > 200 * 1024) break;
+    acc = need;
+    m0 = m;
+  }
+  bytes = acc;
+  return m0 < M ? m0 : -1;
+}
+
+template <typename T, int D>
+amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, size_t bytes, const T* b, T* x,
+                        cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  const int M = (int)h->mg.size() - 1;
+  CoarseBlock2D cb{};
+  cb.ng = M - m0 + 1;
+  cb.nu1 = p.nu1;
+  cb.nu2 = p.nu2;
+  cb.nbot = op->nbot;
+  cb.ldb = op->ldb;
+  cb.minv = op->d_binv;
+  cb.gp = h->mg[m0].patch;
+  int off = 0;
+  for (int q = 0; q < cb.ng; ++q) {
+    const MgGrid& g = h->mg[m0 + q];
+    const int e = (g.n[0] + 2 * NG) * (g.n[1] + 2 * NG);
+    cb.offx[q] = off; off += e;
+    cb.offt[q] = off; off += e;
+    cb.offb[q] = off; off += e;
+    cb.lv[q] = mg_view(h, m0 + q, op->bc);
+    cb.ood[q] = p.omega / (op->alpha - 60.0 * op->beta * cb.lv[q].inv12h2);
+  }
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
+  k_mg_coarse2d<T><<<1, dim3(32, 32, 1), bytes, st>>>(cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
+  TRY(launch_check());
+  prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * (double)h->mg[m0].n[0] * h->mg[m0].n[1]);  // read f, write x
   return AMR_OK;
 }
 
@@ -761,6 +811,8 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   }
   const LevelView cv = mg_view(h, m + 1, op->bc);
   if constexpr (D == 2 && sizeof(T) == 4 && !TR) if (p.temporal_blocking && p.nu1 >= 1 && p.nu1 <= BLK_MAX_NU && p.nu2 <= BLK_MAX_NU) {
+    size_t cbytes = 0;
+    if (m == coarse_block_m0(h, cbytes)) return coarse_block<T, D>(op, p, m, cbytes, b, x, st);
     // temporally blocked legs (FP32 forward V-cycles: FP64 arithmetic is scarce on this
     // part and the halo recomputation would cost more than the launches it saves): one
     // launch for {nu1 sweeps, residual, restriction} into t, one for {prolongation, nu2
