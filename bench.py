@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven V-cycle loop instead of the captured solve")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the large-grid roofline")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D workload in the extras")
     ap.add_argument("--profile-case", choices=["none", "large", "bench"], default="none",
                     help="large: one mixed-precision solve of the single-level 4096^2 case; bench: one warm-up "
                          "and one timed step of the bench workload and nothing else (both for ncu)")
@@ -70,13 +71,18 @@ def _workload():
 def valid_dof(n0, boxes):
     """Valid cells of a two-level hierarchy: level-0 cells minus the coarsened level-1
     boxes, plus every level-1 cell (top level has no invalid region)."""
-    n = n0[0] * n0[1]
+    D = len(n0)
+    n = 1
+    for v in n0:
+        n *= v
     fine = 0
     cover = 0
     for lo, hi in boxes[1]:
-        c = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1)
+        c = 1
+        for d in range(D):
+            c *= hi[d] - lo[d] + 1
         fine += c
-        cover += c // 4
+        cover += c // 2 ** D
     return n - cover + fine
 
 
@@ -355,6 +361,8 @@ def run_ours(args):
         line["large_grid_roofline"] = _large_grid_roofline(amr, torch, peak, peak_kind)
         line["batch"] = _batch_measure(amr, torch)
         line["adjoint"] = _adjoint_measure(amr, torch)
+        if not args.no_3d:
+            line["bumps3d"] = _bumps3d_measure(amr, torch, peak, peak_kind)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, c, el = _oracle_vcycles(12.0)
@@ -483,6 +491,62 @@ def _large_grid_roofline(amr, torch, peak, peak_kind, n=4096):
     out["classes"] = {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
                       for k, v in classes.items()}
     op.close()
+    gh.close()
+    return out
+
+
+def _bumps3d_measure(amr, torch, peak, peak_kind, reps=2):
+    """The 3-D workload: base 256^3 on [0,1]^3 plus a ratio-2 box over [0.375,0.625]^3
+    (128^3 fine cells); RHS = cell averages of seeded Gaussian bumps; one pure-Neumann PPE and
+    three Helmholtz solves (gamma=0.25, nu=1e-3, k=1/256, Dirichlet) per step, mixed
+    precision to 1e-10.  The fields (about 150 MB each in FP64) are larger than L2."""
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, rhs = wl.bumps3d_rhs()
+    gh = amr.Hierarchy(dim, n0, boxes)
+    dof = valid_dof(n0, boxes)
+    f = torch.from_numpy(gh.pack(rhs)).cuda()
+    ppe = amr.Operator(gh, 0.0, 1.0, [1] * 6)
+    helm = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA, [0] * 6)
+    phis = [torch.zeros_like(f) for _ in range(4)]
+    stream = torch.cuda.current_stream()
+    out = {"workload": "bumps3d: 3-D two-level AMR, base 256^3 + ratio-2 box [0.375,0.625]^3 (128^3 fine cells), "
+                       "Gaussian-bump RHS; per step: pure-Neumann PPE + 3 Helmholtz (gamma=0.25, nu=1e-3, k=1/256), "
+                       "each to ||r||_inf <= 1e-10 ||f||_inf",
+           "dof_per_system": dof}
+    for name, prec in (("mixed", amr.MIXED), ("fp64", amr.FP64)):
+        p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
+
+        def step():
+            vc = [ppe.solve(phis[0], f, params=p)["vcycles"]]
+            for c in range(3):
+                vc.append(helm.solve(phis[1 + c], f, params=p)["vcycles"])
+            return vc
+        step()
+        ts, vcs = [], []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vcs.append(step())
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        out[name] = {"ms_per_step": ms, "vcycles_per_system": vcs[-1],
+                     "value": dof * sum(vcs[-1]) / (ms * 1e-3), "unit": UNIT}
+    # kernel classes of one instrumented mixed step (host-driven loop)
+    pp = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.MIXED, use_graph=0)
+    amr.profile_enable(True)
+    ppe.solve(phis[0], f, params=pp)
+    helm.solve(phis[1], f, params=pp)
+    amr.profile_enable(False)
+    classes = _class_table(amr)
+    dom = _dominant(classes)
+    out["roofline"] = _roofline_entry(classes, dom, peak, peak_kind, "bumps3d")
+    out["classes"] = {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
+                      for k, v in classes.items()}
+    ppe.close()
+    helm.close()
     gh.close()
     return out
 

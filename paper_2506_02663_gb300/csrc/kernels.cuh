@@ -973,7 +973,7 @@ __device__ __forceinline__ TileGeom whole_grid(const LevelView& lv) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
+__global__ void __launch_bounds__(256) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
                                                       T alpha, T beta, T omega) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ JacobiTable jts[CB_MAX];

@@ -785,7 +785,7 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
   }
   cudaEvent_t ev;
   prof_begin(st, &ev);
-  k_mg_coarse2d<T><<<1, dim3(32, 32, 1), bytes, st>>>(cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
+  k_mg_coarse2d<T><<<1, dim3(32, 8, 1), bytes, st>>>(cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
   TRY(launch_check());
   prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * (double)h->mg[m0].n[0] * h->mg[m0].n[1]);  // read f, write x
   return AMR_OK;
