@@ -323,6 +323,63 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   }
 }
 
+// 3-D level operator, tiled: a 32 x 8 block of (x, y) columns, each thread ROWS consecutive
+// cells along z with the z-column held in registers (x and y neighbours from the caches),
+// 32-bit patch-local offsets.  A block whose cells and their two-cell reach lie inside the
+// domain and the patch takes the constant-interior-diagonal form; any other block runs the
+// generic per-cell code.  Same summation order as cell_Lx.
+template <typename T, int MODE, bool TR, int ROWS>
+__global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int nzs, const T* __restrict__ x,
+                                                             const T* __restrict__ f, T* __restrict__ out,
+                                                             const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                             T omega_over_diag, const unsigned char* __restrict__ vmask) {
+  const int pz = blockIdx.z / nzs, zs = blockIdx.z % nzs;
+  const PatchDesc p = lv.patches[pz];
+  const int ti0 = blockIdx.x * BX, tj0 = blockIdx.y * BY, k0 = zs * ROWS;
+  const int i = ti0 + threadIdx.x, j = tj0 + threadIdx.y;
+  const bool full = ti0 + BX <= p.n[0] && tj0 + BY <= p.n[1] && k0 + ROWS <= p.n[2];
+  constexpr int M = TR ? 4 : 2;
+  const bool inside = p.lo[0] + ti0 >= M && p.lo[0] + ti0 + BX - 1 <= lv.ndom[0] - 1 - M && p.lo[1] + tj0 >= M &&
+                      p.lo[1] + tj0 + BY - 1 <= lv.ndom[1] - 1 - M && p.lo[2] + k0 >= M &&
+                      p.lo[2] + k0 + ROWS - 1 <= lv.ndom[2] - 1 - M;
+  if (!(full && inside && vmask == nullptr)) {
+    if (i >= p.n[0] || j >= p.n[1]) return;
+    for (int r = 0; r < ROWS; ++r) {
+      const int k = k0 + r;
+      if (k >= p.n[2]) return;
+      if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) continue;
+      cell_level_op<T, 3, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
+    }
+    return;
+  }
+  const T* __restrict__ xb = x + p.off;
+  const T* __restrict__ fb = f + p.off;
+  T* __restrict__ ob = out + p.off;
+  const int sy = (int)p.sy, sz = (int)p.sz;
+  const int o = (k0 + NG) * sz + (j + NG) * sy + (i + NG);
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  if (MODE == OP_JACOBI0) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) ob[o + r * sz] = omega_over_diag * fb[o + r * sz];
+    return;
+  }
+  T col[ROWS + 4];
+#pragma unroll
+  for (int q = 0; q < ROWS + 4; ++q) col[q] = xb[o + (q - 2) * sz];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int orr = o + r * sz;
+    const T xc = col[r + 2];
+    const T s1 = ((xb[orr - 1] + xb[orr + 1]) + (xb[orr - sy] + xb[orr + sy])) + (col[r + 1] + col[r + 3]);
+    const T s2 = ((xb[orr - 2] + xb[orr + 2]) + (xb[orr - 2 * sy] + xb[orr + 2 * sy])) + (col[r] + col[r + 4]);
+    const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
+    const T ax = alpha * xc + beta * (lap * inv);
+    if (MODE == OP_APPLY) ob[orr] = ax;
+    else if (MODE == OP_RESID) ob[orr] = fb[orr] - ax;
+    else ob[orr] = xc + omega_over_diag * (fb[orr] - ax);
+  }
+}
+
 // ------------------------------------------------------------------------ G and D
 // grad: out_d = (-x_{+2} + 8 x_{+1} - 8 x_{-1} + x_{-2}) / (12 h)   (Eq. discreteOps a)
 template <typename T, int D>
@@ -973,7 +1030,7 @@ __device__ __forceinline__ TileGeom whole_grid(const LevelView& lv) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
+__global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
                                                       T alpha, T beta, T omega) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ JacobiTable jts[CB_MAX];

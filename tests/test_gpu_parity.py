@@ -430,3 +430,34 @@ def test_temporal_blocking_matches_per_sweep_legs(name, bcw, ab):
             res.append((from_packed(gh, H, x.cpu().numpy()), st["vcycles"]))
         assert abs(res[0][1] - res[1][1]) <= (0 if precision == amr.FP64 else 1)
         assert max_diff(H, res[0][0], res[1][0]) <= 1e-9 * max_abs(H, res[0][0])
+
+
+def test_3d_tiled_kernels_parity():
+    """A 72^3 single-level grid, large enough for the tiled 3-D level operator's interior
+    blocks (32 x 8 columns x 4 cells along z, two cells from every face): three FP64
+    weighted-Jacobi sweeps and the operator with boundary data against the oracle."""
+    amr = _amr()
+    n = 72
+    bc = [0, 1, 0, 0, 1, 0]
+    H = OH(3, (n, n, n), [[((0, 0, 0), (n - 1, n - 1, n - 1))]], bc=bc)
+    gh = amr.Hierarchy(3, (n, n, n), [[((0, 0, 0), (n - 1, n - 1, n - 1))]], h0=1.0 / n)
+    rng = np.random.default_rng(61)
+    alpha, beta = 1.0, -0.02
+    op = amr.Operator(gh, alpha, beta, bc)
+    X = _rand_field(H, rng, redundant=False)
+    B = _rand_field(H, rng, redundant=False)
+    diag = mg.jacobi_diagonal(H, 0, alpha, beta)
+    Xr = X[0].copy()
+    for _ in range(3):
+        Xr = mg.jacobi(H, 0, Xr, B[0], diag, alpha, beta, 2.0 / 3.0)
+    dx = _dev(to_packed(gh, H, X))
+    op.smooth(0, 3, 2.0 / 3.0, dx, _dev(to_packed(gh, H, B)))
+    got = from_packed(gh, H, dx.cpu().numpy())
+    cov = H.levels[0].covered
+    assert float(np.max(np.abs(got[0][cov] - Xr[cov]))) <= 1e-12 * float(np.max(np.abs(Xr[cov])))
+    data = _bc_data(H, rng)
+    ref = cp.apply(H, X, alpha, beta, data)
+    out = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    op.apply(_dev(to_packed(gh, H, X)), out, bc=_dev(gh.pack_bc(data)))
+    got = from_packed(gh, H, out.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-13 * op_scale(H, alpha, beta, X)
