@@ -267,11 +267,11 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
 }
 
 // 2-D level operator, tiled: each thread computes ROWS (1, 2 or 4; chosen per grid by the
-// autotuner) consecutive cells of one column
-// with 32-bit patch-local offsets and reuses the column loads.  A block whose whole tile
-// (plus the two-cell stencil reach) lies inside the domain takes the fast path with the
-// constant interior diagonal (omega / diag precomputed); any other block runs the generic
-// per-cell code.  Both paths sum in the same order (bit-identical results).
+// autotuner) consecutive cells of one column with 32-bit patch-local offsets and reuses the
+// column loads.  A thread whose cells (plus the two-cell stencil reach) lie inside the
+// domain and the patch takes the fast path with the constant interior diagonal (omega /
+// diag precomputed); the others run the generic per-cell code.  Both paths sum the
+// stencil in the same order as cell_Lx.
 template <typename T, int MODE, bool TR, int ROWS>
 __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const T* __restrict__ x,
                                                              const T* __restrict__ f, T* __restrict__ out,
@@ -280,13 +280,13 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   const PatchDesc p = lv.patches[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j0 = (blockIdx.y * BY + threadIdx.y) * ROWS;
-  const int ti0 = blockIdx.x * BX, tj0 = blockIdx.y * BY * ROWS;
-  const bool full = ti0 + BX <= p.n[0] && tj0 + BY * ROWS <= p.n[1];
-  // the transpose also gathers ghost coefficients at distance 2 and 3 from a physical face
+  // per thread: its column strip and the two-cell reach inside the patch and the domain
+  // (the transpose also gathers ghost coefficients at distance 2 and 3 from a physical face)
+  const bool full = i < p.n[0] && j0 + ROWS <= p.n[1];
   constexpr int M = TR ? 4 : 2;
-  const bool inside = p.lo[0] + ti0 >= M && p.lo[0] + ti0 + BX - 1 <= lv.ndom[0] - 1 - M && p.lo[1] + tj0 >= M &&
-                      p.lo[1] + tj0 + BY * ROWS - 1 <= lv.ndom[1] - 1 - M;
-  if (!(full && inside && vmask == nullptr)) {
+  const int g0 = p.lo[0] + i, g1 = p.lo[1] + j0;
+  const bool inside = g0 >= M && g0 <= lv.ndom[0] - 1 - M && g1 >= M && g1 + ROWS - 1 <= lv.ndom[1] - 1 - M;
+  if (!(full && inside)) {
     if (i >= p.n[0]) return;
     for (int r = 0; r < ROWS; ++r) {
       const int j = j0 + r;
@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   if (MODE == OP_JACOBI0) {
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) out[p.off + o + r * sy] = omega_over_diag * f[p.off + o + r * sy];
+    for (int r = 0; r < ROWS; ++r)
+      if (vmask == nullptr || vmask[p.off + o + r * sy]) out[p.off + o + r * sy] = omega_over_diag * f[p.off + o + r * sy];
     return;
   }
   T col[ROWS + 4];
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
     const int orr = o + r * sy;
+    if (vmask != nullptr && !vmask[p.off + orr]) continue;
     const T xc = col[r + 2];
     const T s1 = (xb[orr - 1] + xb[orr + 1]) + (col[r + 1] + col[r + 3]);
     const T s2 = (xb[orr - 2] + xb[orr + 2]) + (col[r] + col[r + 4]);
@@ -325,8 +327,8 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
 
 // 3-D level operator, tiled: a 32 x 8 block of (x, y) columns, each thread ROWS consecutive
 // cells along z with the z-column held in registers (x and y neighbours from the caches),
-// 32-bit patch-local offsets.  A block whose cells and their two-cell reach lie inside the
-// domain and the patch takes the constant-interior-diagonal form; any other block runs the
+// 32-bit patch-local offsets.  A thread whose cells and their two-cell reach lie inside the
+// domain and the patch takes the constant-interior-diagonal form; the others run the
 // generic per-cell code.  Same summation order as cell_Lx.
 template <typename T, int MODE, bool TR, int ROWS>
 __global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int nzs, const T* __restrict__ x,
@@ -335,14 +337,15 @@ __global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int n
                                                              T omega_over_diag, const unsigned char* __restrict__ vmask) {
   const int pz = blockIdx.z / nzs, zs = blockIdx.z % nzs;
   const PatchDesc p = lv.patches[pz];
-  const int ti0 = blockIdx.x * BX, tj0 = blockIdx.y * BY, k0 = zs * ROWS;
-  const int i = ti0 + threadIdx.x, j = tj0 + threadIdx.y;
-  const bool full = ti0 + BX <= p.n[0] && tj0 + BY <= p.n[1] && k0 + ROWS <= p.n[2];
+  const int k0 = zs * ROWS;
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  // per thread: its z strip and the two-cell reach inside the patch and the domain
+  const bool full = i < p.n[0] && j < p.n[1] && k0 + ROWS <= p.n[2];
   constexpr int M = TR ? 4 : 2;
-  const bool inside = p.lo[0] + ti0 >= M && p.lo[0] + ti0 + BX - 1 <= lv.ndom[0] - 1 - M && p.lo[1] + tj0 >= M &&
-                      p.lo[1] + tj0 + BY - 1 <= lv.ndom[1] - 1 - M && p.lo[2] + k0 >= M &&
-                      p.lo[2] + k0 + ROWS - 1 <= lv.ndom[2] - 1 - M;
-  if (!(full && inside && vmask == nullptr)) {
+  const int g0 = p.lo[0] + i, g1 = p.lo[1] + j, g2 = p.lo[2] + k0;
+  const bool inside = g0 >= M && g0 <= lv.ndom[0] - 1 - M && g1 >= M && g1 <= lv.ndom[1] - 1 - M && g2 >= M &&
+                      g2 + ROWS - 1 <= lv.ndom[2] - 1 - M;
+  if (!(full && inside)) {
     if (i >= p.n[0] || j >= p.n[1]) return;
     for (int r = 0; r < ROWS; ++r) {
       const int k = k0 + r;
@@ -358,9 +361,11 @@ __global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int n
   const int sy = (int)p.sy, sz = (int)p.sz;
   const int o = (k0 + NG) * sz + (j + NG) * sy + (i + NG);
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  const unsigned char* __restrict__ vm = vmask != nullptr ? vmask + p.off : nullptr;
   if (MODE == OP_JACOBI0) {
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) ob[o + r * sz] = omega_over_diag * fb[o + r * sz];
+    for (int r = 0; r < ROWS; ++r)
+      if (vm == nullptr || vm[o + r * sz]) ob[o + r * sz] = omega_over_diag * fb[o + r * sz];
     return;
   }
   T col[ROWS + 4];
@@ -369,6 +374,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int n
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
     const int orr = o + r * sz;
+    if (vm != nullptr && !vm[orr]) continue;
     const T xc = col[r + 2];
     const T s1 = ((xb[orr - 1] + xb[orr + 1]) + (xb[orr - sy] + xb[orr + sy])) + (col[r + 1] + col[r + 3]);
     const T s2 = ((xb[orr - 2] + xb[orr + 2]) + (xb[orr - 2 * sy] + xb[orr + 2 * sy])) + (col[r] + col[r + 4]);
