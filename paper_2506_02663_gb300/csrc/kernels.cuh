@@ -325,13 +325,28 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   }
 }
 
+// Generic cells of the tiled 3-D kernel (near faces, ragged strips, masked cells), kept out
+// of line so that their register demand does not limit the fast path's occupancy.
+template <typename T, int MODE, bool TR, int ROWS>
+__device__ __noinline__ void strip3d_generic(const LevelView& lv, const PatchDesc& p, int i, int j, int k0,
+                                             const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ out,
+                                             const T* __restrict__ bc, T alpha, T beta, T omega,
+                                             const unsigned char* __restrict__ vmask) {
+  for (int r = 0; r < ROWS; ++r) {
+    const int k = k0 + r;
+    if (k >= p.n[2]) return;
+    if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) continue;
+    cell_level_op<T, 3, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
+  }
+}
+
 // 3-D level operator, tiled: a 32 x 8 block of (x, y) columns, each thread ROWS consecutive
 // cells along z with the z-column held in registers (x and y neighbours from the caches),
 // 32-bit patch-local offsets.  A thread whose cells and their two-cell reach lie inside the
 // domain and the patch takes the constant-interior-diagonal form; the others run the
 // generic per-cell code.  Same summation order as cell_Lx.
 template <typename T, int MODE, bool TR, int ROWS>
-__global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int nzs, const T* __restrict__ x,
+__global__ void __launch_bounds__(BX* BY, 4) k_level_op3d_tiled(LevelView lv, int nzs, const T* __restrict__ x,
                                                              const T* __restrict__ f, T* __restrict__ out,
                                                              const T* __restrict__ bc, T alpha, T beta, T omega,
                                                              T omega_over_diag, const unsigned char* __restrict__ vmask) {
@@ -347,12 +362,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op3d_tiled(LevelView lv, int n
                       g2 + ROWS - 1 <= lv.ndom[2] - 1 - M;
   if (!(full && inside)) {
     if (i >= p.n[0] || j >= p.n[1]) return;
-    for (int r = 0; r < ROWS; ++r) {
-      const int k = k0 + r;
-      if (k >= p.n[2]) return;
-      if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) continue;
-      cell_level_op<T, 3, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
-    }
+    strip3d_generic<T, MODE, TR, ROWS>(lv, p, i, j, k0, x, f, out, bc, alpha, beta, omega, vmask);
     return;
   }
   const T* __restrict__ xb = x + p.off;
