@@ -325,77 +325,6 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   }
 }
 
-// Generic cells of the tiled 3-D kernel (near faces, ragged strips, masked cells), kept out
-// of line so that their register demand does not limit the fast path's occupancy.
-template <typename T, int MODE, bool TR, int ROWS>
-__device__ __noinline__ void strip3d_generic(const LevelView& lv, const PatchDesc& p, int i, int j, int k0,
-                                             const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ out,
-                                             const T* __restrict__ bc, T alpha, T beta, T omega,
-                                             const unsigned char* __restrict__ vmask) {
-  for (int r = 0; r < ROWS; ++r) {
-    const int k = k0 + r;
-    if (k >= p.n[2]) return;
-    if (vmask != nullptr && vmask[poff(p, i, j, k)] == 0) continue;
-    cell_level_op<T, 3, MODE, TR>(lv, p, i, j, k, x, f, out, bc, alpha, beta, omega);
-  }
-}
-
-// 3-D level operator, tiled: a 32 x 8 block of (x, y) columns, each thread ROWS consecutive
-// cells along z with the z-column held in registers (x and y neighbours from the caches),
-// 32-bit patch-local offsets.  A thread whose cells and their two-cell reach lie inside the
-// domain and the patch takes the constant-interior-diagonal form; the others run the
-// generic per-cell code.  Same summation order as cell_Lx.
-template <typename T, int MODE, bool TR, int ROWS>
-__global__ void __launch_bounds__(BX* BY, 4) k_level_op3d_tiled(LevelView lv, int nzs, const T* __restrict__ x,
-                                                             const T* __restrict__ f, T* __restrict__ out,
-                                                             const T* __restrict__ bc, T alpha, T beta, T omega,
-                                                             T omega_over_diag, const unsigned char* __restrict__ vmask) {
-  const int pz = blockIdx.z / nzs, zs = blockIdx.z % nzs;
-  const PatchDesc p = lv.patches[pz];
-  const int k0 = zs * ROWS;
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  // per thread: its z strip and the two-cell reach inside the patch and the domain
-  const bool full = i < p.n[0] && j < p.n[1] && k0 + ROWS <= p.n[2];
-  constexpr int M = TR ? 4 : 2;
-  const int g0 = p.lo[0] + i, g1 = p.lo[1] + j, g2 = p.lo[2] + k0;
-  const bool inside = g0 >= M && g0 <= lv.ndom[0] - 1 - M && g1 >= M && g1 <= lv.ndom[1] - 1 - M && g2 >= M &&
-                      g2 + ROWS - 1 <= lv.ndom[2] - 1 - M;
-  if (!(full && inside)) {
-    if (i >= p.n[0] || j >= p.n[1]) return;
-    strip3d_generic<T, MODE, TR, ROWS>(lv, p, i, j, k0, x, f, out, bc, alpha, beta, omega, vmask);
-    return;
-  }
-  const T* __restrict__ xb = x + p.off;
-  const T* __restrict__ fb = f + p.off;
-  T* __restrict__ ob = out + p.off;
-  const int sy = (int)p.sy, sz = (int)p.sz;
-  const int o = (k0 + NG) * sz + (j + NG) * sy + (i + NG);
-  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
-  const unsigned char* __restrict__ vm = vmask != nullptr ? vmask + p.off : nullptr;
-  if (MODE == OP_JACOBI0) {
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      if (vm == nullptr || vm[o + r * sz]) ob[o + r * sz] = omega_over_diag * fb[o + r * sz];
-    return;
-  }
-  T col[ROWS + 4];
-#pragma unroll
-  for (int q = 0; q < ROWS + 4; ++q) col[q] = xb[o + (q - 2) * sz];
-#pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    const int orr = o + r * sz;
-    if (vm != nullptr && !vm[orr]) continue;
-    const T xc = col[r + 2];
-    const T s1 = ((xb[orr - 1] + xb[orr + 1]) + (xb[orr - sy] + xb[orr + sy])) + (col[r + 1] + col[r + 3]);
-    const T s2 = ((xb[orr - 2] + xb[orr + 2]) + (xb[orr - 2 * sy] + xb[orr + 2 * sy])) + (col[r] + col[r + 4]);
-    const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
-    const T ax = alpha * xc + beta * (lap * inv);
-    if (MODE == OP_APPLY) ob[orr] = ax;
-    else if (MODE == OP_RESID) ob[orr] = fb[orr] - ax;
-    else ob[orr] = xc + omega_over_diag * (fb[orr] - ax);
-  }
-}
-
 // ------------------------------------------------------------------------ G and D
 // grad: out_d = (-x_{+2} + 8 x_{+1} - 8 x_{-1} + x_{-2}) / (12 h)   (Eq. discreteOps a)
 template <typename T, int D>

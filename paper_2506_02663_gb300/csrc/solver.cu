@@ -279,12 +279,6 @@ bool invert(std::vector<double>& A, int n) {
 }
 
 // ---------------------------------------------------------------- kernel wrappers
-// elements of the largest padded patch of a level (32-bit offsets inside the tiled kernels)
-inline long long max_patch_elems(const LevelView& lv) {
-  const long long e0 = lv.maxn[0] + 2 * NG, e1 = lv.maxn[1] + 2 * NG, e2 = lv.maxn[2] + 2 * NG;
-  return (e0 + 3) * e1 * e2;  // the x pitch is rounded up to a multiple of 4
-}
-
 template <typename T, int D, bool TR = false>
 amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* out, const T* bc, double alpha,
                     double beta, double omega, const unsigned char* vmask, cudaStream_t st) {
@@ -313,25 +307,6 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
       default: LAUNCH_TILED(OP_JACOBI0);
     }
 #undef LAUNCH_TILED
-    const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
-    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
-    return launch_check();
-  }
-  if (D == 3 && lv.maxn[2] >= 8 && max_patch_elems(lv) < (1LL << 31)) {
-    // tiled 3-D path: z strips of 4 cells per thread
-    constexpr int R3 = 4;
-    const T diag = T(alpha) + T(beta) * pick_host<T>(lv.inv12h2, lv.inv12h2_f) * T(-90);
-    const T ood = T(omega) / diag;
-    const int nzs = (lv.maxn[2] + R3 - 1) / R3;
-    dim3 grid((lv.maxn[0] + BX - 1) / BX, (lv.maxn[1] + BY - 1) / BY, nzs * lv.npatch);
-    dim3 block(BX, BY, 1);
-    const T A = T(alpha), B = T(beta), O = T(omega);
-    switch (mode) {
-      case OP_APPLY: k_level_op3d_tiled<T, OP_APPLY, TR, R3><<<grid, block, 0, st>>>(lv, nzs, x, f, out, bc, A, B, O, ood, vmask); break;
-      case OP_RESID: k_level_op3d_tiled<T, OP_RESID, TR, R3><<<grid, block, 0, st>>>(lv, nzs, x, f, out, bc, A, B, O, ood, vmask); break;
-      case OP_JACOBI: k_level_op3d_tiled<T, OP_JACOBI, TR, R3><<<grid, block, 0, st>>>(lv, nzs, x, f, out, bc, A, B, O, ood, vmask); break;
-      default: k_level_op3d_tiled<T, OP_JACOBI0, TR, R3><<<grid, block, 0, st>>>(lv, nzs, x, f, out, bc, A, B, O, ood, vmask);
-    }
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
     prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
     return launch_check();

@@ -432,10 +432,9 @@ def test_temporal_blocking_matches_per_sweep_legs(name, bcw, ab):
         assert max_diff(H, res[0][0], res[1][0]) <= 1e-9 * max_abs(H, res[0][0])
 
 
-def test_3d_tiled_kernels_parity():
-    """A 72^3 single-level grid, large enough for the tiled 3-D level operator's interior
-    blocks (32 x 8 columns x 4 cells along z, two cells from every face): three FP64
-    weighted-Jacobi sweeps and the operator with boundary data against the oracle."""
+def test_3d_large_grid_smoother_and_apply_parity():
+    """A 72^3 single-level grid (blocks far from every face as well as face blocks): three
+    FP64 weighted-Jacobi sweeps and the operator with boundary data against the oracle."""
     amr = _amr()
     n = 72
     bc = [0, 1, 0, 0, 1, 0]
