@@ -47,6 +47,13 @@ __device__ __forceinline__ T cfiw(int i) {
   return pick<T>(c_cfi[i], c_cfi_f[i]);
 }
 
+// Programmatic dependent launch: every kernel of the library is launched with programmatic
+// stream serialisation, so its blocks may be scheduled while the previous kernel on the
+// stream drains; each kernel therefore waits here, before touching any global data, until
+// the grids it depends on have completed and their memory is visible.  Without the launch
+// attribute the instruction returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr int BX = 32;
 constexpr int BY = 8;
 
@@ -259,6 +266,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
                                                      const T* __restrict__ f, T* __restrict__ out,
                                                      const T* __restrict__ bc, T alpha, T beta, T omega,
                                                      const unsigned char* __restrict__ vmask) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -277,6 +285,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
                                                              const T* __restrict__ f, T* __restrict__ out,
                                                              const T* __restrict__ bc, T alpha, T beta, T omega,
                                                              T omega_over_diag, const unsigned char* __restrict__ vmask) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j0 = (blockIdx.y * BY + threadIdx.y) * ROWS;
@@ -330,6 +339,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
 template <typename T, int D>
 __global__ void k_gradient(LevelView lv, int nby, const T* __restrict__ x, T* __restrict__ g0, T* __restrict__ g1,
                            T* __restrict__ g2, const T* __restrict__ bc) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -358,6 +368,7 @@ struct Ptr3m {
 // div: sum_d (-u_{+2} + 8 u_{+1} - 8 u_{-1} + u_{-2}) / (12 h)   (Eq. discreteOps b)
 template <int D>
 __global__ void k_divergence(LevelView lv, int nby, Ptr3 u, double* __restrict__ out, Ptr3 bc) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -383,6 +394,7 @@ template <typename T, int D>
 __global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long long* __restrict__ side,
                       const PatchDesc* __restrict__ cpatches, int r, const T* __restrict__ xc, T* __restrict__ xf,
                       int zero) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CfiEntry e = list[t];
@@ -416,6 +428,7 @@ __global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long
 
 template <typename T>
 __global__ void k_copy(const CopyEntry* __restrict__ list, long long n, T* __restrict__ x) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CopyEntry e = list[t];
@@ -454,6 +467,7 @@ template <typename T, int D, bool RESID, bool TR = false>
 __global__ void k_restrict(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                            const T* __restrict__ xf, const T* __restrict__ ff, T* __restrict__ outc,
                            T alpha, T beta, int nby) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
@@ -473,6 +487,7 @@ __global__ void __launch_bounds__(BX* BY) k_restrict2d_resid(LevelView fine, Lev
                                                              const XferBlock* __restrict__ blocks,
                                                              const T* __restrict__ xf, const T* __restrict__ ff,
                                                              T* __restrict__ outc, T alpha, T beta) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -569,6 +584,7 @@ __device__ __forceinline__ void cell_prolong(const LevelView& crs, const PatchDe
 template <typename T, int D>
 __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                           const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2, int nby) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;  // fine offsets inside the block region
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
@@ -585,6 +601,7 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
 template <typename T>
 __global__ void __launch_bounds__(BX* BY) k_prolong2d(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                                                       const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
@@ -806,6 +823,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
                                                    int nu, const T* __restrict__ b, T* __restrict__ xo,
                                                    T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, tx, ty, halo);
   const int sy = tg.rw + 2 * NG;
@@ -899,6 +917,7 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
                                                  int ty, int halo, int nu, const T* __restrict__ xc,
                                                  const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
                                                  T alpha, T beta, T omega, T ood) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, tx, ty, halo);
   const int sy = tg.rw + 2 * NG;
@@ -977,6 +996,7 @@ __device__ __forceinline__ TileGeom whole_grid(const LevelView& lv) {
 template <typename T>
 __global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
                                                       T alpha, T beta, T omega) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ JacobiTable jts[CB_MAX];
   __shared__ double bot[1024];
@@ -1105,6 +1125,7 @@ __device__ __forceinline__ void cell_of(const PatchDesc& p, int t, int& i, int& 
 template <typename T, int D, bool TR = false>
 __global__ void __launch_bounds__(1024) k_coarse_mg(CoarseMG cm, const T* __restrict__ bglob, T* __restrict__ xglob,
                                                     T alpha, T beta, T omega) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -1246,6 +1267,7 @@ __device__ __forceinline__ void scatter_read(T* __restrict__ W, const PatchDesc&
 template <typename T, int D>
 __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
                            const T* __restrict__ z, Out3<T> W, T coef, int kind) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const RefluxEntry e = list[t];
@@ -1294,6 +1316,7 @@ __global__ void k_reflux_T(LevelView crs, LevelView fine, const RefluxEntry* __r
 template <typename T, int D>
 __global__ void k_gradient_T(LevelView lv, int nby, P3c<T> z, const unsigned char* __restrict__ vmask,
                              T* __restrict__ W) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1320,6 +1343,7 @@ __global__ void k_gradient_T(LevelView lv, int nby, P3c<T> z, const unsigned cha
 template <typename T, int D>
 __global__ void k_divergence_T(LevelView lv, int nby, const T* __restrict__ z, const unsigned char* __restrict__ vmask,
                                Out3<T> W) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1344,6 +1368,7 @@ __global__ void k_cfi_T(const CfiEntry* __restrict__ list, long long n, const lo
                         const PatchDesc* __restrict__ cpatches, const PatchDesc* __restrict__ fpatches, int r,
                         const T* __restrict__ z, const T* __restrict__ wghost, T* __restrict__ W, T beta_inv12h2,
                         T sign) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CfiEntry e = list[t];
@@ -1378,6 +1403,7 @@ __global__ void k_cfi_T(const CfiEntry* __restrict__ list, long long n, const lo
 template <typename T, int D>
 __global__ void k_avgdown_T(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks, T* __restrict__ W,
                             int nby) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
@@ -1395,6 +1421,7 @@ __global__ void k_avgdown_T(LevelView fine, LevelView crs, const XferBlock* __re
 // transposes) belongs to the sibling cell the ghost copies.
 template <typename T>
 __global__ void k_copy_T(const CopyEntry* __restrict__ list, long long n, T* __restrict__ W) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CopyEntry e = list[t];
@@ -1410,6 +1437,7 @@ __global__ void k_copy_T(const CopyEntry* __restrict__ list, long long n, T* __r
 template <typename T, int D>
 __global__ void k_valid_out(LevelView lv, int nby, const T* __restrict__ w, const T* __restrict__ f, T* __restrict__ out,
                             const unsigned char* __restrict__ vmask) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1423,6 +1451,7 @@ __global__ void k_valid_out(LevelView lv, int nby, const T* __restrict__ w, cons
 template <typename T, int D>
 __global__ void k_prolong_T(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                             const T* __restrict__ y1, const T* __restrict__ y2, T* __restrict__ out, int nby) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
@@ -1484,6 +1513,7 @@ __global__ void k_prolong_T(LevelView fine, LevelView crs, const XferBlock* __re
 template <typename T, int D>
 __global__ void k_axpy_valid(LevelView lv, int nby, const T* __restrict__ x, T* __restrict__ y, T a,
                              const unsigned char* __restrict__ vmask) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1496,6 +1526,7 @@ __global__ void k_axpy_valid(LevelView lv, int nby, const T* __restrict__ x, T* 
 template <typename T, int D>
 __global__ void k_avgdown_T2(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
                              const T* __restrict__ yc, T* __restrict__ yf, int nby) {
+  pdl_wait();
   const XferBlock b = blocks[blockIdx.z];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int by = (D == 3) ? (int)(blockIdx.y % nby) : (int)blockIdx.y;
@@ -1513,6 +1544,7 @@ __global__ void k_avgdown_T2(LevelView fine, LevelView crs, const XferBlock* __r
 template <typename T, int D>
 __global__ void k_level_op_masked_copy(LevelView lv, int nby, const T* __restrict__ w, const T* __restrict__ f,
                                        T* __restrict__ out, const unsigned char* __restrict__ vmask) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1525,6 +1557,7 @@ __global__ void k_level_op_masked_copy(LevelView lv, int nby, const T* __restric
 // source type S, destination type T.
 template <typename S, typename T, int D>
 __global__ void k_axpy(LevelView lv, int nby, const S* __restrict__ x, T* __restrict__ y, T* __restrict__ y2, T a) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1536,6 +1569,7 @@ __global__ void k_axpy(LevelView lv, int nby, const S* __restrict__ x, T* __rest
 
 template <typename S, typename T, int D>
 __global__ void k_convert(LevelView lv, int nby, const S* __restrict__ x, T* __restrict__ y) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1547,6 +1581,7 @@ __global__ void k_convert(LevelView lv, int nby, const S* __restrict__ x, T* __r
 template <int D>
 __global__ void k_shift(LevelView lv, int nby, double* __restrict__ y, const double* __restrict__ a,
                         const unsigned char* __restrict__ vmask, double sign) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1559,6 +1594,7 @@ __global__ void k_shift(LevelView lv, int nby, double* __restrict__ y, const dou
 template <int D>
 __global__ void k_sub(LevelView lv, int nby, const double* __restrict__ w, const double* __restrict__ g,
                       double* __restrict__ out) {
+  pdl_wait();
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
@@ -1572,6 +1608,7 @@ __global__ void k_sub(LevelView lv, int nby, const double* __restrict__ w, const
 template <typename T, int D>
 __global__ void k_maxnorm(LevelView lv, int nby, const T* __restrict__ x, const unsigned char* __restrict__ vmask,
                           unsigned long long* __restrict__ out) {
+  pdl_wait();
   __shared__ unsigned long long sm[BX * BY / 32];
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
@@ -1619,6 +1656,7 @@ __device__ __forceinline__ void dd_add(double& s, double& c, double a, double ac
 template <int D>
 __global__ void k_wsum(LevelView lv, int nby, const double* __restrict__ x, const unsigned char* __restrict__ vmask,
                        double w, double* __restrict__ part, long long base) {
+  pdl_wait();
   __shared__ double ss[BX * BY], sc[BX * BY];
   const PatchDesc p = lv.patches[blockIdx.z];
   int i, j, k;
@@ -1658,6 +1696,7 @@ template <int D>
 __global__ void __launch_bounds__(256) k_wsum_gs(LevelView lv, const double* __restrict__ x,
                                                  const unsigned char* __restrict__ vmask, double w,
                                                  double* __restrict__ part, long long base) {
+  pdl_wait();
   __shared__ double ss[256], sc[256];
   double s = 0.0, c = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1697,6 +1736,7 @@ __global__ void __launch_bounds__(256) k_wsum_gs(LevelView lv, const double* __r
 template <int D>
 __global__ void k_bsum(LevelView lv, const double* __restrict__ bc, const unsigned char* __restrict__ vmask,
                        double scale, double* __restrict__ part, long long base) {
+  pdl_wait();
   __shared__ double ss[256], sc[256];
   const int pidx = blockIdx.x / (2 * D);
   const int f = blockIdx.x % (2 * D);
@@ -1744,6 +1784,7 @@ __global__ void k_bsum(LevelView lv, const double* __restrict__ bc, const unsign
 // Final fixed-order reduction of n double-double partials (one block of 256 threads):
 // out[0] = (sum_a - sum_b_scaled ... ) handled by the caller; here out[slot] = sum.
 __global__ void k_dd_final(const double* __restrict__ part, long long n, double* __restrict__ out) {
+  pdl_wait();
   __shared__ double ss[256], sc[256];
   double s = 0.0, c = 0.0;
   for (long long t = threadIdx.x; t < n; t += blockDim.x) dd_add(s, c, part[2 * t], part[2 * t + 1]);
@@ -1765,6 +1806,7 @@ __global__ void k_dd_final(const double* __restrict__ part, long long n, double*
 // m = (S_f - beta * S_b) / V ; used by the solvability fix and mean-zero
 __global__ void k_mean_from_sums(const double* __restrict__ sf, const double* __restrict__ sb, double beta,
                                  double vol, double* __restrict__ m) {
+  pdl_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) m[0] = (sf[0] - (sb ? beta * sb[0] : 0.0)) / vol;
 }
 
@@ -1774,6 +1816,7 @@ __global__ void k_mean_from_sums(const double* __restrict__ sf, const double* __
 template <typename T, int D>
 __global__ void k_bottom(const double* __restrict__ minv, int n, int ld, PatchDesc p, const T* __restrict__ b,
                          T* __restrict__ x) {
+  pdl_wait();
   extern __shared__ double sb[];
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const int i = t % p.n[0];
