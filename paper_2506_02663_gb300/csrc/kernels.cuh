@@ -695,13 +695,47 @@ __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int
 __device__ __forceinline__ int blk_tid() { return (int)(threadIdx.y * blockDim.x + threadIdx.x); }
 __device__ __forceinline__ int blk_nth() { return (int)(blockDim.x * blockDim.y); }
 
+// The threads that work on a region: the whole block (rows of 32 threads, __syncthreads), or
+// its first nth threads (whole warps) synchronised by named barrier 1, so that a small grid
+// keeps only the warps it needs busy while the others wait at the block's next barrier.
+struct Team {
+  int tid, nth;   // linear id and size
+  int tx, ty;     // position in rows of 32
+  int nty;        // rows
+  bool named;
+  __device__ __forceinline__ void sync() const {
+    if (named) asm volatile("bar.sync 1, %0;" ::"r"(nth) : "memory");
+    else __syncthreads();
+  }
+};
+__device__ __forceinline__ Team block_team() {  // blockDim.x == 32
+  Team t;
+  t.tid = blk_tid();
+  t.nth = blk_nth();
+  t.tx = (int)threadIdx.x;
+  t.ty = (int)threadIdx.y;
+  t.nty = (int)blockDim.y;
+  t.named = false;
+  return t;
+}
+__device__ __forceinline__ Team sub_team(int cells) {  // enough whole warps for ``cells``
+  Team t;
+  t.tid = blk_tid();
+  t.nth = min(blk_nth(), (cells + 31) / 32 * 32);
+  t.tx = t.tid & 31;
+  t.ty = t.tid >> 5;
+  t.nty = t.nth >> 5;
+  t.named = t.nth < blk_nth();
+  return t;
+}
+
 // Physical ghost layers of the region's domain faces for rows [a1,b1) / columns [a0,b0)
 // (only blocks whose region touches a face do any work here).
 template <typename T>
 __device__ __forceinline__ void region_ghosts(const LevelView& lv, const TileGeom& tg, T* __restrict__ a, int sy, int a0,
-                                              int b0, int a1, int b1) {
+                                              int b0, int a1, int b1, const Team& tm) {
   if (!(tg.fl0 | tg.fh0 | tg.fl1 | tg.fh1)) return;
-  const int tid = blk_tid(), nth = blk_nth();
+  const int tid = tm.tid, nth = tm.nth;
   const int nr = b1 - a1, nc = b0 - a0;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -753,9 +787,9 @@ __device__ __forceinline__ int face_class(int g, int n) {
 
 template <typename T>
 __device__ __forceinline__ void build_jacobi_table(JacobiTable& jt, const LevelView& lv, const TileGeom& tg, T alpha,
-                                                   T beta, T omega, T ood) {
+                                                   T beta, T omega, T ood, const Team& tm) {
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
-  const int tid = blk_tid(), nth = blk_nth();
+  const int tid = tm.tid, nth = tm.nth;
   for (int q = tid; q < 25; q += nth) {
     const int a = q % 5, b = q / 5;
     // diag_sum's order: -30 D, then the x correction, then the y correction
@@ -781,7 +815,8 @@ __device__ __forceinline__ T lap_smem(const T* __restrict__ a, int o, int sy) {
 // nu weighted-Jacobi sweeps on the region; returns the buffer holding the result
 template <typename T, bool ZERO>
 __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, const JacobiTable& jt, int sy,
-                                            T* cur, T* oth, const T* __restrict__ sb, int nu, T alpha, T beta) {
+                                            T* cur, T* oth, const T* __restrict__ sb, int nu, T alpha, T beta,
+                                            const Team& tm) {
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   for (int s = 1; s <= nu; ++s) {
     int a0, b0, a1, b1;
@@ -791,12 +826,12 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
       // ghosts of the current iterate for the rows / columns this sweep reads
       int c0, d0, c1, d1;
       sweep_box(tg, s - 1, c0, d0, c1, d1);
-      region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1);
-      __syncthreads();
+      region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1, tm);
+      tm.sync();
     }
-    for (int j = a1 + (int)threadIdx.y; j < b1; j += (int)blockDim.y) {
+    for (int j = a1 + tm.ty; j < b1; j += tm.nty) {
       const int ky5 = 5 * jt.ky[j];
-      for (int i = a0 + (int)threadIdx.x; i < b0; i += (int)blockDim.x) {
+      for (int i = a0 + tm.tx; i < b0; i += 32) {
         const int o = (j + NG) * sy + (i + NG);
         const T w = jt_get<T>(jt, jt.kx[i] + ky5);
         if (zero) {
@@ -808,7 +843,7 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
         }
       }
     }
-    __syncthreads();
+    tm.sync();
     T* sw = cur;
     cur = oth;
     oth = sw;
@@ -831,15 +866,16 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
+  const Team tm = block_team();
   __shared__ JacobiTable jt;
-  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood);
+  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   const T* __restrict__ bg = b + gp.off;
   const int gsy = (int)gp.sy;
   for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
     for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
       sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
   __syncthreads();
-  T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta);
+  T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
@@ -848,7 +884,7 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   // residual of the tile's cells (ghosts of the final iterate first), restricted
   int c0, d0, c1, d1;
   sweep_box(tg, nu, c0, d0, c1, d1);
-  region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1);
+  region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1, tm);
   __syncthreads();
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   const int cw = tg.tw / 2, ch = tg.th / 2;
@@ -958,9 +994,10 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
       v += (T(0.25) * T(0.25)) * c11;
       sx[os] = xg[og] + v;
     }
-  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood);
+  const Team tm = block_team();
+  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   __syncthreads();
-  const T* cur = smooth_region<T, false>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta);
+  const T* cur = smooth_region<T, false>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xw = xo + gp.off;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
@@ -1001,47 +1038,49 @@ __global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T*
   __shared__ JacobiTable jts[CB_MAX];
   __shared__ double bot[1024];
   T* sm = reinterpret_cast<T*>(smraw);
-  const int tid = blk_tid(), nth = blk_nth();
-  T* xs[CB_MAX];
-  for (int q = 0; q < cb.ng; ++q) {
-    build_jacobi_table<T>(jts[q], cb.lv[q], whole_grid(cb.lv[q]), alpha, beta, omega, T(cb.ood[q]));
-    xs[q] = sm + cb.offx[q];
-  }
+  const Team all = block_team();
+  const int M = cb.ng - 1;
+  for (int q = 0; q < cb.ng; ++q)
+    build_jacobi_table<T>(jts[q], cb.lv[q], whole_grid(cb.lv[q]), alpha, beta, omega, T(cb.ood[q]), all);
   {
     const int n0 = cb.lv[0].ndom[0], n1 = cb.lv[0].ndom[1], sy = n0 + 2 * NG;
     const T* __restrict__ bg = b + cb.gp.off;
     const int gsy = (int)cb.gp.sy;
-    for (int t = tid; t < n0 * n1; t += nth) {
+    for (int t = all.tid; t < n0 * n1; t += all.nth) {
       const int i = t % n0, j = t / n0;
       sm[cb.offb[0] + (j + NG) * sy + i + NG] = bg[(j + NG) * gsy + i + NG];
     }
   }
   __syncthreads();
-  const int M = cb.ng - 1;
+  // buffer holding each grid's iterate after its down leg: nu1 sweeps from zero starting in
+  // the x array end in x for an even count, in the t array for an odd one
+  const bool down_in_t = (cb.nu1 & 1) != 0, up_swaps = (cb.nu2 & 1) != 0;
   for (int q = 0; q < M; ++q) {
     const LevelView& lv = cb.lv[q];
     const TileGeom tg = whole_grid(lv);
-    const int sy = tg.rw + 2 * NG;
-    T* sb = sm + cb.offb[q];
-    T* cur = smooth_region<T, true>(lv, tg, jts[q], sy, sm + cb.offx[q], sm + cb.offt[q], sb, cb.nu1, alpha, beta);
-    xs[q] = cur;
-    region_ghosts(lv, tg, cur, sy, 0, tg.rw, 0, tg.rh);
-    __syncthreads();
-    const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
-    const int cw = tg.rw / 2, ch = tg.rh / 2, csy = cw + 2 * NG;
-    T* bc = sm + cb.offb[q + 1];
-    for (int t = tid; t < cw * ch; t += nth) {
-      const int ci = t % cw, cj = t / cw;
-      T acc = T(0);
+    const Team tm = sub_team(tg.rw * tg.rh);
+    if (tm.tid < tm.nth) {
+      const int sy = tg.rw + 2 * NG;
+      T* sb = sm + cb.offb[q];
+      T* cur = smooth_region<T, true>(lv, tg, jts[q], sy, sm + cb.offx[q], sm + cb.offt[q], sb, cb.nu1, alpha, beta, tm);
+      region_ghosts(lv, tg, cur, sy, 0, tg.rw, 0, tg.rh, tm);
+      tm.sync();
+      const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+      const int cw = tg.rw / 2, ch = tg.rh / 2, csy = cw + 2 * NG;
+      T* bc = sm + cb.offb[q + 1];
+      for (int t = tm.tid; t < cw * ch; t += tm.nth) {
+        const int ci = t % cw, cj = t / cw;
+        T acc = T(0);
 #pragma unroll
-      for (int q1 = 0; q1 < 2; ++q1)
+        for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
-        for (int q0 = 0; q0 < 2; ++q0) {
-          const int o = (2 * cj + q1 + NG) * sy + (2 * ci + q0 + NG);
-          const T xc = cur[o];
-          acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
-        }
-      bc[(cj + NG) * csy + ci + NG] = acc * T(0.25);
+          for (int q0 = 0; q0 < 2; ++q0) {
+            const int o = (2 * cj + q1 + NG) * sy + (2 * ci + q0 + NG);
+            const T xc = cur[o];
+            acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
+          }
+        bc[(cj + NG) * csy + ci + NG] = acc * T(0.25);
+      }
     }
     __syncthreads();
   }
@@ -1049,50 +1088,55 @@ __global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T*
     // dense bottom solve (FP64 accumulation), cell order x fastest
     const int n0 = cb.lv[M].ndom[0], sy = n0 + 2 * NG;
     const T* bm = sm + cb.offb[M];
-    for (int t = tid; t < cb.nbot; t += nth) bot[t] = (double)bm[(t / n0 + NG) * sy + t % n0 + NG];
+    for (int t = all.tid; t < cb.nbot; t += all.nth) bot[t] = (double)bm[(t / n0 + NG) * sy + t % n0 + NG];
     __syncthreads();
     T* xm = sm + cb.offx[M];
-    for (int t = tid; t < cb.nbot; t += nth) {
+    for (int t = all.tid; t < cb.nbot; t += all.nth) {
       double acc = 0.0;
       const double* row = cb.minv + (long long)t * cb.ldb;
       for (int k = 0; k < cb.nbot; ++k) acc = fma(row[k], bot[k], acc);
       xm[(t / n0 + NG) * sy + t % n0 + NG] = T(acc);
     }
-    xs[M] = xm;
     __syncthreads();
   }
   for (int q = M - 1; q >= 0; --q) {
     const LevelView& lv = cb.lv[q];
     const LevelView& cv = cb.lv[q + 1];
     const TileGeom tg = whole_grid(lv);
-    const int sy = tg.rw + 2 * NG, csy = cv.ndom[0] + 2 * NG;
-    T* xq = xs[q];
-    const T* cg = xs[q + 1];
-    for (int t = tid; t < tg.rw * tg.rh; t += nth) {
-      const int i = t % tg.rw, j = t / tg.rw;
-      const int p0 = i >> 1, p1 = j >> 1;
-      const int s0 = (i & 1) ? 1 : -1, s1 = (j & 1) ? 1 : -1;
-      const T c00 = cg[(p1 + NG) * csy + p0 + NG];
-      const T c10 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1);
-      const T c01 = coarse_ext2d<T>(cg, csy, cv, p0, p1 + s1);
-      const T c11 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1 + s1);
-      T v = T(0);
-      v += (T(0.75) * T(0.75)) * c00;
-      v += (T(0.25) * T(0.75)) * c10;
-      v += (T(0.75) * T(0.25)) * c01;
-      v += (T(0.25) * T(0.25)) * c11;
-      xq[(j + NG) * sy + i + NG] += v;
+    const Team tm = sub_team(tg.rw * tg.rh);
+    if (tm.tid < tm.nth) {
+      const int sy = tg.rw + 2 * NG, csy = cv.ndom[0] + 2 * NG;
+      T* xq = down_in_t ? sm + cb.offt[q] : sm + cb.offx[q];
+      T* oth = down_in_t ? sm + cb.offx[q] : sm + cb.offt[q];
+      // the coarser grid's final iterate: its down-leg buffer, swapped by an odd nu2
+      const bool cin_t = (q + 1 == M) ? false : (down_in_t != up_swaps);
+      const T* cg = cin_t ? sm + cb.offt[q + 1] : sm + cb.offx[q + 1];
+      for (int t = tm.tid; t < tg.rw * tg.rh; t += tm.nth) {
+        const int i = t % tg.rw, j = t / tg.rw;
+        const int p0 = i >> 1, p1 = j >> 1;
+        const int s0 = (i & 1) ? 1 : -1, s1 = (j & 1) ? 1 : -1;
+        const T c00 = cg[(p1 + NG) * csy + p0 + NG];
+        const T c10 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1);
+        const T c01 = coarse_ext2d<T>(cg, csy, cv, p0, p1 + s1);
+        const T c11 = coarse_ext2d<T>(cg, csy, cv, p0 + s0, p1 + s1);
+        T v = T(0);
+        v += (T(0.75) * T(0.75)) * c00;
+        v += (T(0.25) * T(0.75)) * c10;
+        v += (T(0.75) * T(0.25)) * c01;
+        v += (T(0.25) * T(0.25)) * c11;
+        xq[(j + NG) * sy + i + NG] += v;
+      }
+      tm.sync();
+      smooth_region<T, false>(lv, tg, jts[q], sy, xq, oth, sm + cb.offb[q], cb.nu2, alpha, beta, tm);
     }
     __syncthreads();
-    T* oth = (xq == sm + cb.offx[q]) ? sm + cb.offt[q] : sm + cb.offx[q];
-    xs[q] = smooth_region<T, false>(lv, tg, jts[q], sy, xq, oth, sm + cb.offb[q], cb.nu2, alpha, beta);
   }
   {
     const int n0 = cb.lv[0].ndom[0], n1 = cb.lv[0].ndom[1], sy = n0 + 2 * NG;
     T* __restrict__ xg = x + cb.gp.off;
     const int gsy = (int)cb.gp.sy;
-    const T* x0 = xs[0];
-    for (int t = tid; t < n0 * n1; t += nth) {
+    const T* x0 = (down_in_t != up_swaps) ? sm + cb.offt[0] : sm + cb.offx[0];
+    for (int t = all.tid; t < n0 * n1; t += all.nth) {
       const int i = t % n0, j = t / n0;
       xg[(j + NG) * gsy + i + NG] = x0[(j + NG) * sy + i + NG];
     }
