@@ -1681,6 +1681,55 @@ __global__ void k_maxnorm(LevelView lv, int nby, const T* __restrict__ x, const 
   }
 }
 
+// Whole-array passes of the refinement loop (one launch for every level):
+//   k_norm_convert  valid-cell max-norm of r into *acc (IEEE bits, atomicMax; a NaN wins)
+//                   and, when rin is given, r rounded to FP32 over the whole array (the
+//                   next FP32 V-cycle's right-hand side; ghost entries are never read);
+//   k_update_valid  phi += X on the valid cells (invalid cells are recomputed by the
+//                   average-down that starts the next composite residual), and clears the
+//                   norm accumulator for that residual.
+__global__ void __launch_bounds__(256) k_norm_convert(long long n, const double* __restrict__ r,
+                                                      const unsigned char* __restrict__ vmask, float* __restrict__ rin,
+                                                      unsigned long long* __restrict__ acc) {
+  pdl_wait();
+  __shared__ unsigned long long sm[8];
+  unsigned long long v = 0ull;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double x = r[e];
+    if (rin != nullptr) rin[e] = (float)x;
+    if (vmask[e]) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x));
+      v = b > v ? b : v;
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+    v = u > v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < 8 ? sm[threadIdx.x] : 0ull;
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+      v = u > v ? u : v;
+    }
+    if (threadIdx.x == 0 && v != 0ull) atomicMax(acc, v);
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_update_valid(long long n, const S* __restrict__ x, double* __restrict__ phi,
+                                                      const unsigned char* __restrict__ vmask,
+                                                      unsigned long long* __restrict__ acc_clear) {
+  pdl_wait();
+  if (acc_clear != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *acc_clear = 0ull;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    if (vmask[e]) phi[e] += (double)x[e];
+}
+
 // Error-free transformation (Knuth's TwoSum).
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
   s = a + b;

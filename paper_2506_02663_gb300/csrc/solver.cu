@@ -1423,23 +1423,40 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
 
 // One V-cycle iteration of the solve loop (V-cycle on op->Res, phi += correction, new
 // residual and its norm), all stream-ordered on st; used inside the captured while-body.
+// grid of the whole-array passes: grid-stride, a few blocks per SM
+inline unsigned flat_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8); }
+
+// valid-cell max-norm of op->Res into *acc, and (mixed precision) its FP32 copy into rin
+inline amr_status norm_convert(amr_operator* op, int prec, unsigned long long* acc, cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  float* rin = prec == AMR_MIXED ? op->s32.rin : nullptr;
+  launch(k_norm_convert, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const double*)op->Res,
+         (const unsigned char*)h->d_valid, rin, acc);
+  return launch_check();
+}
+
+// One V-cycle iteration of the captured solve loop: V-cycle on the residual (FP32 copy made
+// by the previous norm pass in mixed precision), phi += correction on the valid cells, new
+// composite residual, its norm (and FP32 copy), all stream-ordered on st.
 template <int D>
 amr_status iteration_body(amr_operator* op, int prec, const amr_solver_params& p, double* phi, const double* bc,
                           cudaStream_t st) {
   amr_hierarchy* h = op->h;
+  unsigned long long* rbits = reinterpret_cast<unsigned long long*>(h->d_scalar);
   if (prec == AMR_MIXED) {
     Scratch<float>& Sf = op->s32;
-    for (int l = 0; l < h->L; ++l) TRY(convert<double, float, D>(level_view(h, l, nullptr), op->Res, Sf.rin, st));
     TRY(vcycle_corr<float, D>(op, p, Sf.rin, st));
-    for (int l = 0; l < h->L; ++l) TRY(axpy<float, double, D>(level_view(h, l, nullptr), Sf.X, phi, (double*)nullptr, 1.0, st));
+    launch(k_update_valid<float>, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const float*)Sf.X, phi,
+           (const unsigned char*)h->d_valid, rbits);
   } else {
     Scratch<double>& Sd = op->s64;
     TRY(vcycle_corr<double, D>(op, p, op->Res, st));
-    for (int l = 0; l < h->L; ++l) TRY(axpy<double, double, D>(level_view(h, l, nullptr), Sd.X, phi, (double*)nullptr, 1.0, st));
+    launch(k_update_valid<double>, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const double*)Sd.X, phi,
+           (const unsigned char*)h->d_valid, rbits);
   }
+  TRY(launch_check());
   TRY(composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, st));
-  TRY(maxnorm_dev<double, D>(h, op->Res, reinterpret_cast<unsigned long long*>(h->d_scalar), st));
-  return AMR_OK;
+  return norm_convert(op, prec, rbits, st);
 }
 
 template <int D>
@@ -1457,8 +1474,9 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
   const long long l0 = g_launches.load();
   do {
     cudaMemsetAsync(op->d_stats, 0, sizeof(DevStats), cs);
+    cudaMemsetAsync(rbits, 0, sizeof(unsigned long long), cs);
     if ((result = composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, cs)) != AMR_OK) break;
-    if ((result = maxnorm_dev<double, D>(h, op->Res, rbits, cs)) != AMR_OK) break;
+    if ((result = norm_convert(op, p.precision, rbits, cs)) != AMR_OK) break;
     cudaStreamCaptureStatus cst;
     cudaGraph_t cg = nullptr;
     if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
