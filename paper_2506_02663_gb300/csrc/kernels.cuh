@@ -658,14 +658,17 @@ __global__ void __launch_bounds__(BX* BY) k_prolong2d(LevelView fine, LevelView 
 // past what sweep s-1 produced, so no value from outside the region is ever used, and the
 // halo (2 nu, plus 2 for a residual) keeps the shrinkage out of the tile.
 struct TileGeom {
-  int i0, j0;      // tile origin (patch-local = global)
+  int i0, j0;      // tile origin (patch-local)
   int tw, th;      // tile extents
-  int r0, r1;      // region origin
+  int r0, r1;      // region origin (patch-local)
   int rw, rh;      // region extents
-  int fl0, fh0, fl1, fh1;  // 1 where the region side is a domain face (does not shrink)
+  int fl0, fh0, fl1, fh1;  // 1 where the region side is a patch edge (closed: does not shrink)
+  int pl0, ph0, pl1, ph1;  // 1 where that edge is a domain face (physical ghosts; else a CF
+                           // edge whose ghosts are zero in correction smoothing)
+  int g0, g1;              // global index of the region's first cell
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, int tx, int ty, int halo) {
+__device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, const LevelView& lv, int tx, int ty, int halo) {
   TileGeom t;
   t.i0 = blockIdx.x * tx;
   t.j0 = blockIdx.y * ty;
@@ -681,10 +684,16 @@ __device__ __forceinline__ TileGeom tile_geom(const PatchDesc& gp, int tx, int t
   t.fl1 = t.r1 == 0;
   t.fh0 = e0 == gp.n[0];
   t.fh1 = e1 == gp.n[1];
+  t.pl0 = t.fl0 && gp.lo[0] == 0;
+  t.pl1 = t.fl1 && gp.lo[1] == 0;
+  t.ph0 = t.fh0 && gp.lo[0] + gp.n[0] == lv.ndom[0];
+  t.ph1 = t.fh1 && gp.lo[1] + gp.n[1] == lv.ndom[1];
+  t.g0 = gp.lo[0] + t.r0;
+  t.g1 = gp.lo[1] + t.r1;
   return t;
 }
 
-// region cells updated by sweep s (shrunk by 2 s on non-face sides)
+// region cells updated by sweep s (shrunk by 2 s on the open sides)
 __device__ __forceinline__ void sweep_box(const TileGeom& t, int s, int& a0, int& b0, int& a1, int& b1) {
   a0 = t.fl0 ? 0 : 2 * s;
   b0 = t.fh0 ? t.rw : t.rw - 2 * s;
@@ -740,23 +749,29 @@ __device__ __forceinline__ void region_ghosts(const LevelView& lv, const TileGeo
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     if (side == 0 ? tg.fl0 : tg.fh0) {
+      const bool phys = side == 0 ? tg.pl0 : tg.ph0;
       const int type = lv.bc[side];
       for (int q = tid; q < 2 * nr; q += nth) {
         const int layer = q & 1, j = a1 + (q >> 1);
         const int row = (j + NG) * sy + NG;
         T v = T(0);
+        if (phys) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[row + (side == 0 ? m : tg.rw - 1 - m)];
+          for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[row + (side == 0 ? m : tg.rw - 1 - m)];
+        }
         a[row + (side == 0 ? -1 - layer : tg.rw + layer)] = v;
       }
     }
     if (side == 0 ? tg.fl1 : tg.fh1) {
+      const bool phys = side == 0 ? tg.pl1 : tg.ph1;
       const int type = lv.bc[2 + side];
       for (int q = tid; q < 2 * nc; q += nth) {
         const int layer = q & 1, col = NG + a0 + (q >> 1);
         T v = T(0);
+        if (phys) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[(NG + (side == 0 ? m : tg.rh - 1 - m)) * sy + col];
+          for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer, m) * a[(NG + (side == 0 ? m : tg.rh - 1 - m)) * sy + col];
+        }
         a[(NG + (side == 0 ? -1 - layer : tg.rh + layer)) * sy + col] = v;
       }
     }
@@ -799,8 +814,8 @@ __device__ __forceinline__ void build_jacobi_table(JacobiTable& jt, const LevelV
     if (sizeof(T) == 4) jt.wf[q] = (float)w;
     else jt.wd[q] = (double)w;
   }
-  for (int q = tid; q < tg.rw; q += nth) jt.kx[q] = (unsigned char)face_class(tg.r0 + q, lv.ndom[0]);
-  for (int q = tid; q < tg.rh; q += nth) jt.ky[q] = (unsigned char)face_class(tg.r1 + q, lv.ndom[1]);
+  for (int q = tid; q < tg.rw; q += nth) jt.kx[q] = (unsigned char)face_class(tg.g0 + q, lv.ndom[0]);
+  for (int q = tid; q < tg.rh; q += nth) jt.ky[q] = (unsigned char)face_class(tg.g1 + q, lv.ndom[1]);
 }
 
 // 12 h^2 L x at smem offset o (interior stencil; ghosts materialised), cell_Lx's order
@@ -851,16 +866,18 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
   return cur;
 }
 
-// Down leg of one multigrid level: nu weighted-Jacobi sweeps from zero, the smoothed x
-// written to xo, and the residual f - A x restricted (2x2 average) into the next grid's
-// right-hand side bcn.  halo = 2 nu + 2.
+// Down leg of one multigrid level (a level-0 grid, or a single-box AMR level with zero CF
+// ghosts): nu weighted-Jacobi sweeps from zero, the smoothed x written to xo (and added to
+// xo2 when given), and the residual f - A x restricted (2x2 average) into the coarse
+// right-hand side bcn over the covered coarse cells.  halo = 2 nu + 2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
                                                    int nu, const T* __restrict__ b, T* __restrict__ xo,
-                                                   T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
+                                                   T* __restrict__ xo2, T* __restrict__ bcn, T alpha, T beta, T omega,
+                                                   T ood) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
-  const TileGeom tg = tile_geom(gp, tx, ty, halo);
+  const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
   const int sy = tg.rw + 2 * NG;
   const int E = sy * (tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
@@ -878,9 +895,13 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
+  T* __restrict__ xg2 = xo2 != nullptr ? xo2 + gp.off : nullptr;
   for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x)
-      xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
+    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x) {
+      const T v = cur[(tj + j + NG) * sy + ti + i + NG];
+      xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = v;
+      if (xg2 != nullptr) xg2[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] += v;
+    }
   // residual of the tile's cells (ghosts of the final iterate first), restricted
   int c0, d0, c1, d1;
   sweep_box(tg, nu, c0, d0, c1, d1);
@@ -901,7 +922,8 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
           const T xc = cur[o];
           acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
         }
-      cg[((tg.j0 >> 1) + cj + NG) * csy + (tg.i0 >> 1) + ci + NG] = acc * T(0.25);
+      cg[(((gp.lo[1] + tg.j0) >> 1) - gcp.lo[1] + cj + NG) * csy + ((gp.lo[0] + tg.i0) >> 1) - gcp.lo[0] + ci + NG] =
+          acc * T(0.25);
     }
 }
 
@@ -955,7 +977,7 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
                                                  T alpha, T beta, T omega, T ood) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
-  const TileGeom tg = tile_geom(gp, tx, ty, halo);
+  const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
   const int sy = tg.rw + 2 * NG;
   const int E = sy * (tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
@@ -1005,6 +1027,45 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
       xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
 }
 
+// Post-smoothing of a single-box AMR level (the correction form's up step): nu weighted-
+// Jacobi sweeps from zero on r (the residual already updated with the prolonged coarse
+// correction), zero CF ghosts and physical ghosts by formula, and the result t added to the
+// level's correction e and to the accumulated correction x on the tile.  Only the tile's
+// own e and x cells are read and written (no halo reads of them).  halo = 2 nu.
+template <typename T>
+__global__ void __launch_bounds__(256) k_amr_post2d(LevelView lv, PatchDesc gp, int tx, int ty, int halo, int nu,
+                                                    const T* __restrict__ r, T* __restrict__ e, T* __restrict__ x,
+                                                    T alpha, T beta, T omega, T ood) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
+  const int sy = tg.rw + 2 * NG;
+  const int E = sy * (tg.rh + 2 * NG);
+  T* sx = reinterpret_cast<T*>(smraw);
+  T* st = sx + E;
+  T* sb = st + E;
+  const Team tm = block_team();
+  __shared__ JacobiTable jt;
+  build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
+  const T* __restrict__ rg = r + gp.off;
+  const int gsy = (int)gp.sy;
+  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
+      sb[(j + NG) * sy + i + NG] = rg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
+  __syncthreads();
+  const T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
+  T* __restrict__ eg = e + gp.off;
+  T* __restrict__ xg = x + gp.off;
+  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
+    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x) {
+      const T v = cur[(tj + j + NG) * sy + ti + i + NG];
+      const int og = (tg.j0 + j + NG) * gsy + tg.i0 + i + NG;
+      eg[og] += v;
+      xg[og] += v;
+    }
+}
+
 // Coarse end of the 2-D level-0 multigrid in one block: every grid from m0 (at most 64 cells
 // per dimension) down to the coarsest lives in shared memory; the legs use the same region
 // sweeps as k_mg_down2d / k_mg_up2d with the whole grid as the region (every side a domain
@@ -1027,6 +1088,8 @@ __device__ __forceinline__ TileGeom whole_grid(const LevelView& lv) {
   t.tw = t.rw = lv.ndom[0];
   t.th = t.rh = lv.ndom[1];
   t.fl0 = t.fh0 = t.fl1 = t.fh1 = 1;
+  t.pl0 = t.ph0 = t.pl1 = t.ph1 = 1;
+  t.g0 = t.g1 = 0;
   return t;
 }
 

@@ -743,14 +743,14 @@ amr_status fused_coarse(amr_operator* op, const amr_solver_params& p, int m0, si
 constexpr int BLK_MAX_NU = 6;
 
 // tile edge: small grids need many blocks, large grids a small halo share
-inline int blk_tile(const MgGrid& g) { return (long long)g.n[0] * g.n[1] >= 1024LL * 1024 ? 32 : 16; }
+inline int blk_tile(const int* n) { return (long long)n[0] * n[1] >= 1024LL * 1024 ? 32 : 16; }
 
 // dynamic shared memory of a blocked leg: three region arrays with two ghost layers
 template <typename T>
-size_t blk_smem(const MgGrid& g, int halo) {
-  const int t = blk_tile(g);
-  const long long w = std::min(t + 2 * halo, g.n[0]) + 2 * NG;
-  const long long hh = std::min(t + 2 * halo, g.n[1]) + 2 * NG;
+size_t blk_smem(const int* n, int halo) {
+  const int t = blk_tile(n);
+  const long long w = std::min(t + 2 * halo, n[0]) + 2 * NG;
+  const long long hh = std::min(t + 2 * halo, n[1]) + 2 * NG;
   return (size_t)(3 * w * hh) * sizeof(T);
 }
 
@@ -761,6 +761,7 @@ amr_status blk_attrs() {
   const int bytes = 200 * 1024;
   CK(cudaFuncSetAttribute(k_mg_down2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_up2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_amr_post2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_coarse2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done = true;
   return AMR_OK;
@@ -843,7 +844,7 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     // sweeps} from t into x
     const MgGrid& g = h->mg[m];
     const MgGrid& gc = h->mg[m + 1];
-    const int tt = blk_tile(g);
+    const int tt = blk_tile(g.n);
     dim3 grid((g.n[0] + tt - 1) / tt, (g.n[1] + tt - 1) / tt, 1);
     const dim3 blk(32, 8, 1);
     const int hd = 2 * p.nu1 + 2, hu = 2 * p.nu2;
@@ -852,13 +853,14 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     const double cells = (double)g.n[0] * g.n[1];
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    launch(k_mg_down2d<T>, grid, blk, blk_smem<T>(g, hd), st, lv, g.patch, gc.patch, tt, tt, hd, p.nu1, b, t, S.mb[m + 1],
+    launch(k_mg_down2d<T>, grid, blk, blk_smem<T>(g.n, hd), st, lv, g.patch, gc.patch, tt, tt, hd, p.nu1, b, t, (T*)nullptr,
+           S.mb[m + 1],
                                                          T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_DOWN, (2.0 + 0.25) * sizeof(T) * cells);  // read f, write x, write coarse f
     TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
     prof_begin(st, &ev);
-    launch(k_mg_up2d<T>, grid, blk, blk_smem<T>(g, hu), st, lv, cv, g.patch, gc.patch, tt, tt, hu, p.nu2, S.mx[m + 1], b, t,
+    launch(k_mg_up2d<T>, grid, blk, blk_smem<T>(g.n, hu), st, lv, cv, g.patch, gc.patch, tt, tt, hu, p.nu2, S.mx[m + 1], b, t,
                                                        x, T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_UP, (3.0 + 0.25) * sizeof(T) * cells);  // read x, f, coarse x; write x
@@ -1086,6 +1088,22 @@ amr_status vcycle_corr_T(amr_operator* op, const amr_solver_params& p, const T* 
 // ---------------------------------------------------------------- composite V-cycle
 // Correction form: given the composite residual r (covered cells), S.X receives the
 // V-cycle's approximation of A^{-1} r (homogeneous data).
+// Whether AMR level l's smoothing runs as temporally blocked launches: FP32 forward V-cycles
+// in 2-D, a single box, whose coarsened cells lie in one coarse box, sweep counts within
+// the halo budget, and a box small enough for the region table.
+template <typename T, int D>
+bool blocked_amr_level(const amr_operator* op, const amr_solver_params& p, int l) {
+  if (D != 2 || sizeof(T) != 4 || !p.temporal_blocking) return false;
+  if (p.nu1 < 1 || p.nu1 > BLK_MAX_NU || p.nu2 > BLK_MAX_NU) return false;
+  const amr_hierarchy* h = op->h;
+  if (h->lev[l].patches.size() != 1 || h->lev[l - 1].xfer.size() != 1) return false;
+  const PatchDesc& fp = h->lev[l].patches[0];
+  const XferBlock& xb = h->lev[l - 1].xfer[0];
+  for (int d = 0; d < 2; ++d)
+    if (xb.clo[d] * 2 != fp.lo[d] || (xb.chi[d] + 1) * 2 != fp.lo[d] + fp.n[d]) return false;
+  return true;
+}
+
 template <typename T, int D>
 amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r, cudaStream_t st) {
   amr_hierarchy* h = op->h;
@@ -1106,12 +1124,28 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
   const double a_ = op->alpha, b_ = op->beta;
   // ---- down
   for (int l = L; l >= 1; --l) {
-    TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st));
-    TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
     const DeviceLists& cl = h->lev[l - 1].dev;
-    // invalid cells of level l-1: mean of the fine residual R_l - A_l E_l (zero CF ghosts)
-    TRY(copy_fill<T>(h, l, S.E, st));
-    TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+    if (blocked_amr_level<T, D>(op, p, l)) {
+      // one launch: nu1 sweeps from zero (zero CF ghosts) into E_l, X_l += E_l, and the
+      // mean of the fine residual R_l - A_l E_l into R_{l-1} on the covered cells
+      const PatchDesc& fp = h->lev[l].patches[0];
+      const PatchDesc& cpd = h->lev[l - 1].patches[h->lev[l - 1].xfer[0].cpatch];
+      const int tt = blk_tile(fp.n), hd = 2 * p.nu1 + 2;
+      const T ood = T(p.omega / (a_ - 60.0 * b_ * lv[l].inv12h2));
+      dim3 grid((fp.n[0] + tt - 1) / tt, (fp.n[1] + tt - 1) / tt, 1);
+      cudaEvent_t ev;
+      prof_begin(st, &ev);
+      launch(k_mg_down2d<T>, grid, dim3(32, 8, 1), blk_smem<T>(fp.n, hd), st, lv[l], fp, cpd, tt, tt, hd, p.nu1,
+             (const T*)S.R, S.E, S.X, S.R, T(a_), T(b_), T(p.omega), ood);
+      TRY(launch_check());
+      prof_end(st, ev, PC_DOWN, (3.0 + 0.25) * sizeof(T) * (double)fp.n[0] * fp.n[1]);  // f in; e, x, coarse f out
+    } else {
+      TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st));
+      TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
+      // invalid cells of level l-1: mean of the fine residual R_l - A_l E_l (zero CF ghosts)
+      TRY(copy_fill<T>(h, l, S.E, st));
+      TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+    }
     // valid cells of level l-1: composite residual r - A^comp X
     for (int m = l - 1; m >= 0; --m) {
       const DeviceLists& dm = h->lev[m].dev;
@@ -1137,8 +1171,22 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
     TRY(cfi_fill<T, D>(h, l, S.E, S.E, false, st));
     TRY(copy_fill<T>(h, l, S.E, st));
     TRY(level_op<T, D>(OP_RESID, lv[l], S.E, S.R, S.R, nullptr, a_, b_, 0.0, nullptr, st));
-    TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st));
-    TRY(axpy<T, T, D>(lv[l], S.T1, S.E, S.X, 1.0, st));
+    if (blocked_amr_level<T, D>(op, p, l) && p.nu2 >= 1) {
+      // one launch: nu2 sweeps from zero on R_l (zero CF ghosts), added to E_l and X_l
+      const PatchDesc& fp = h->lev[l].patches[0];
+      const int tt = blk_tile(fp.n), hu = 2 * p.nu2;
+      const T ood = T(p.omega / (a_ - 60.0 * b_ * lv[l].inv12h2));
+      dim3 grid((fp.n[0] + tt - 1) / tt, (fp.n[1] + tt - 1) / tt, 1);
+      cudaEvent_t ev;
+      prof_begin(st, &ev);
+      launch(k_amr_post2d<T>, grid, dim3(32, 8, 1), blk_smem<T>(fp.n, hu), st, lv[l], fp, tt, tt, hu, p.nu2,
+             (const T*)S.R, S.E, S.X, T(a_), T(b_), T(p.omega), ood);
+      TRY(launch_check());
+      prof_end(st, ev, PC_UP, 5.0 * sizeof(T) * (double)fp.n[0] * fp.n[1]);  // r in; e, x read and written
+    } else {
+      TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.T1, S.T2, p.nu2, a_, b_, p.omega, true, st));
+      TRY(axpy<T, T, D>(lv[l], S.T1, S.E, S.X, 1.0, st));
+    }
   }
   return AMR_OK;
 }
