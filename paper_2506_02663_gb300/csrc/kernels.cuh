@@ -334,6 +334,159 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
   }
 }
 
+// 3-D level operator, marching in z (homogeneous physical data, forward operator): a block
+// owns a 32 x 8 tile of (x, y) columns and walks a range of z planes.  Each thread keeps its
+// column's five z values in registers; the current plane of the tile plus a two-cell halo
+// sits in shared memory (double-buffered, one barrier per plane).  Halo cells inside the
+// domain come from global memory (patch interior or its stored CF / copy ghosts); cells
+// outside the domain are the ghost formulas of Eqs. (velBCHomoDiri5th)/(Neumann5) evaluated
+// from the column or row they extend; the Jacobi factor omega / diag comes from a 125-entry
+// table indexed by the cell's distance class to the x, y and z faces.  Same summation order
+// as cell_Lx.
+// distance class of global index g to the faces of an n-cell dimension: 0 interior, 1 and 2
+// the first and second cell from the low face, 3 and 4 from the high face
+__device__ __forceinline__ int face_class(int g, int n) {
+  return g == 0 ? 1 : g == 1 ? 2 : g == n - 1 ? 3 : g == n - 2 ? 4 : 0;
+}
+
+constexpr int MZ_TX = 32, MZ_TY = 8, MZ_W = MZ_TX + 4, MZ_H = MZ_TY + 4;
+
+template <typename T>
+__device__ __forceinline__ T mz_column(const T* __restrict__ xb, long long base, long long stride, int g, int n, int lo,
+                                       const LevelView& lv, int d) {
+  // value at global index g along d (base = offset of local index 0), ghost formula outside
+  if (g >= 0 && g < n) return xb[base + (long long)(g - lo) * stride];
+  const int side = g < 0 ? 0 : 1, layer = side == 0 ? -g : g - n + 1, type = lv.bc[2 * d + side];
+  T v = T(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer - 1, m) * xb[base + (long long)((side == 0 ? m : n - 1 - m) - lo) * stride];
+  return v;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv, int nzc, int kz, const T* __restrict__ x,
+                                                                 const T* __restrict__ f, T* __restrict__ out, T alpha,
+                                                                 T beta, T omega,
+                                                                 const unsigned char* __restrict__ vmask) {
+  pdl_wait();
+  __shared__ T sp[2][MZ_H * MZ_W];
+  __shared__ T wt[125];
+  const int pz = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+  const PatchDesc p = lv.patches[pz];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MZ_TX + tx;
+  const int i0 = blockIdx.x * MZ_TX, j0 = blockIdx.y * MZ_TY;
+  const int i = i0 + tx, j = j0 + ty;
+  const int k0 = zc * kz, k1 = min(k0 + kz, p.n[2]);
+  if (i0 >= p.n[0] || j0 >= p.n[1] || k0 >= k1) return;
+  const bool active = i < p.n[0] && j < p.n[1];
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  if (MODE == OP_JACOBI || MODE == OP_JACOBI0) {
+    for (int q = tid; q < 125; q += MZ_TX * MZ_TY) {
+      const int a = q % 5, b = (q / 5) % 5, c = q / 25;
+      const int cls[3] = {a, b, c};
+      T acc = T(-90);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (cls[d]) acc += pick<T>(lv.dcorr[2 * d + (cls[d] - 1) / 2][(cls[d] - 1) % 2],
+                                   lv.dcorr_f[2 * d + (cls[d] - 1) / 2][(cls[d] - 1) % 2]);
+      wt[q] = omega / (alpha + beta * inv * acc);
+    }
+  }
+  const long long sy = p.sy, sz = p.sz;
+  const int gi = p.lo[0] + i, gj = p.lo[1] + j;
+  // the halo cell this thread loads (tile-local coordinates; 176 cells, threads 0..175)
+  int hx = -100, hy = -100;
+  {
+    int q = tid;
+    if (q < 2 * MZ_W) {  // two rows below the tile
+      hy = -2 + q / MZ_W;
+      hx = q % MZ_W - 2;
+    } else if ((q -= 2 * MZ_W) < 2 * MZ_W) {  // two rows above
+      hy = MZ_TY + q / MZ_W;
+      hx = q % MZ_W - 2;
+    } else if ((q -= 2 * MZ_W) < 4 * MZ_TY) {  // two columns left and right of the tile rows
+      hy = q % MZ_TY;
+      const int c = q / MZ_TY;  // 0, 1: left (-2, -1); 2, 3: right (TX, TX + 1)
+      hx = c < 2 ? c - 2 : MZ_TX + c - 2;
+    }
+    // corners of the halo are never read by the axis-aligned stencil
+    if ((hx < 0 || hx >= MZ_TX) && (hy < 0 || hy >= MZ_TY)) hx = hy = -100;
+  }
+  const bool has_halo = hx > -100;
+  const int hgi = p.lo[0] + i0 + hx, hgj = p.lo[1] + j0 + hy;
+  const bool h_out_x = has_halo && (hgi < 0 || hgi >= lv.ndom[0]);
+  const bool h_out_y = has_halo && (hgj < 0 || hgj >= lv.ndom[1]);
+  // halo positions outside the patch's stored ghost layers (ragged tiles) are never read
+  const bool h_ok = has_halo && i0 + hx >= -NG && i0 + hx < p.n[0] + NG && j0 + hy >= -NG && j0 + hy < p.n[1] + NG;
+  // column base offsets (local index 0 along z)
+  const long long colc = p.off + (long long)(i + NG) + (long long)(j + NG) * sy + (long long)NG * sz;
+  const long long colh = p.off + (long long)(i0 + hx + NG) + (long long)(j0 + hy + NG) * sy + (long long)NG * sz;
+  const int nzd = lv.ndom[2], lz = p.lo[2];
+  const int kxc = face_class(gi, lv.ndom[0]), kyc = face_class(gj, lv.ndom[1]);
+  // register queue of the column: x at planes k-2 .. k+2
+  T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0), q4 = T(0);
+  if (active && MODE != OP_JACOBI0) {
+    q0 = mz_column<T>(x, colc, sz, lz + k0 - 2, nzd, lz, lv, 2);
+    q1 = mz_column<T>(x, colc, sz, lz + k0 - 1, nzd, lz, lv, 2);
+    q2 = x[colc + (long long)k0 * sz];
+    q3 = mz_column<T>(x, colc, sz, lz + k0 + 1, nzd, lz, lv, 2);
+    q4 = mz_column<T>(x, colc, sz, lz + k0 + 2, nzd, lz, lv, 2);
+  }
+  __syncthreads();  // weight table
+  for (int k = k0, buf = 0; k < k1; ++k, buf ^= 1) {
+    const long long oc = colc + (long long)k * sz;
+    if (MODE != OP_JACOBI0) {
+      T* s = sp[buf];
+      s[(ty + 2) * MZ_W + tx + 2] = active ? q2 : T(0);
+      if (h_ok) {
+        T hv;
+        if (h_out_x) {
+          // x ghost of row (hgj, k): formula from the row's first / last four cells
+          const int side = hgi < 0 ? 0 : 1, layer = side == 0 ? -hgi : hgi - lv.ndom[0] + 1, type = lv.bc[side];
+          const long long rb = p.off + (long long)(j0 + hy + NG) * sy + (long long)(k + NG) * sz + NG;
+          hv = T(0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) hv += gcoef<T>(type, layer - 1, m) * x[rb + ((side == 0 ? m : lv.ndom[0] - 1 - m) - p.lo[0])];
+        } else if (h_out_y) {
+          const int side = hgj < 0 ? 0 : 1, layer = side == 0 ? -hgj : hgj - lv.ndom[1] + 1, type = lv.bc[2 + side];
+          const long long cb = p.off + (long long)(i0 + hx + NG) + (long long)(k + NG) * sz + (long long)NG * sy;
+          hv = T(0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) hv += gcoef<T>(type, layer - 1, m) * x[cb + (long long)((side == 0 ? m : lv.ndom[1] - 1 - m) - p.lo[1]) * sy];
+        } else {
+          hv = x[colh + (long long)k * sz];
+        }
+        s[(hy + 2) * MZ_W + hx + 2] = hv;
+      }
+      __syncthreads();
+    }
+    if (active && (vmask == nullptr || vmask[oc])) {
+      const int kzc = face_class(lz + k, nzd);
+      if (MODE == OP_JACOBI0) {
+        out[oc] = wt[kxc + 5 * kyc + 25 * kzc] * f[oc];
+      } else {
+        const T* s = sp[buf];
+        const int c = (ty + 2) * MZ_W + tx + 2;
+        const T xc = q2;
+        const T s1 = ((s[c - 1] + s[c + 1]) + (s[c - MZ_W] + s[c + MZ_W])) + (q1 + q3);
+        const T s2 = ((s[c - 2] + s[c + 2]) + (s[c - 2 * MZ_W] + s[c + 2 * MZ_W])) + (q0 + q4);
+        const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
+        const T ax = alpha * xc + beta * (lap * inv);
+        if (MODE == OP_APPLY) out[oc] = ax;
+        else if (MODE == OP_RESID) out[oc] = f[oc] - ax;
+        else out[oc] = xc + wt[kxc + 5 * kyc + 25 * kzc] * (f[oc] - ax);
+      }
+    }
+    if (MODE != OP_JACOBI0 && active) {
+      q0 = q1;
+      q1 = q2;
+      q2 = q3;
+      q3 = q4;
+      if (k + 1 < k1) q4 = mz_column<T>(x, colc, sz, lz + k + 3, nzd, lz, lv, 2);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------ G and D
 // grad: out_d = (-x_{+2} + 8 x_{+1} - 8 x_{-1} + x_{-2}) / (12 h)   (Eq. discreteOps a)
 template <typename T, int D>
@@ -796,9 +949,6 @@ __device__ __forceinline__ float jt_get<float>(const JacobiTable& t, int k) { re
 template <>
 __device__ __forceinline__ double jt_get<double>(const JacobiTable& t, int k) { return t.wd[k]; }
 
-__device__ __forceinline__ int face_class(int g, int n) {
-  return g == 0 ? 1 : g == 1 ? 2 : g == n - 1 ? 3 : g == n - 2 ? 4 : 0;
-}
 
 template <typename T>
 __device__ __forceinline__ void build_jacobi_table(JacobiTable& jt, const LevelView& lv, const TileGeom& tg, T alpha,

@@ -334,6 +334,26 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
     prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
     return launch_check();
   }
+  if (D == 3 && !TR && bc == nullptr) {
+    // z-marching 3-D path (homogeneous physical data)
+    const int tx = (lv.maxn[0] + MZ_TX - 1) / MZ_TX, ty = (lv.maxn[1] + MZ_TY - 1) / MZ_TY;
+    const int nz = lv.maxn[2];
+    int nzc = std::max(1, std::min((2048 + tx * ty - 1) / (tx * ty), std::max(1, nz / 4)));
+    const int kz = (nz + nzc - 1) / nzc;
+    nzc = (nz + kz - 1) / kz;
+    dim3 grid(tx, ty, nzc * lv.npatch);
+    dim3 block(MZ_TX, MZ_TY, 1);
+    const T A = T(alpha), B = T(beta), O = T(omega);
+    switch (mode) {
+      case OP_APPLY: launch(k_level_op3d_march<T, OP_APPLY>, grid, block, 0, st, lv, nzc, kz, x, f, out, A, B, O, vmask); break;
+      case OP_RESID: launch(k_level_op3d_march<T, OP_RESID>, grid, block, 0, st, lv, nzc, kz, x, f, out, A, B, O, vmask); break;
+      case OP_JACOBI: launch(k_level_op3d_march<T, OP_JACOBI>, grid, block, 0, st, lv, nzc, kz, x, f, out, A, B, O, vmask); break;
+      default: launch(k_level_op3d_march<T, OP_JACOBI0>, grid, block, 0, st, lv, nzc, kz, x, f, out, A, B, O, vmask);
+    }
+    const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    return launch_check();
+  }
   switch (mode) {
     case OP_APPLY:
       launch(k_level_op<T, D, OP_APPLY, TR>, g.grid, g.block, 0, st, lv, g.nby, x, f, out, bc, T(alpha), T(beta), T(omega), vmask);
