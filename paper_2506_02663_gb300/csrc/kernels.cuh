@@ -363,6 +363,33 @@ __device__ __forceinline__ T mz_column(const T* __restrict__ xb, long long base,
   return v;
 }
 
+// x at patch-local (li, lj) of plane k as the stencil sees it: stored values (interior, or
+// CF / copy ghosts) inside the domain, the ghost formula outside; 0 at positions no stencil of
+// an interior cell reads (corners, beyond the stored ghost layers)
+template <typename T>
+__device__ __forceinline__ T mz_plane_value(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int li, int lj,
+                                           int k) {
+  const int gi = p.lo[0] + li, gj = p.lo[1] + lj;
+  const bool ox = gi < 0 || gi >= lv.ndom[0], oy = gj < 0 || gj >= lv.ndom[1];
+  if (ox && oy) return T(0);
+  if (li < -NG || li >= p.n[0] + NG || lj < -NG || lj >= p.n[1] + NG) return T(0);
+  if (ox) {
+    const int side = gi < 0 ? 0 : 1, layer = side == 0 ? -gi : gi - lv.ndom[0] + 1, type = lv.bc[side];
+    T v = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer - 1, m) * x[poff(p, (side == 0 ? m : lv.ndom[0] - 1 - m) - p.lo[0], lj, k)];
+    return v;
+  }
+  if (oy) {
+    const int side = gj < 0 ? 0 : 1, layer = side == 0 ? -gj : gj - lv.ndom[1] + 1, type = lv.bc[2 + side];
+    T v = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer - 1, m) * x[poff(p, li, (side == 0 ? m : lv.ndom[1] - 1 - m) - p.lo[1], k)];
+    return v;
+  }
+  return x[poff(p, li, lj, k)];
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv, int nzc, int kz, const T* __restrict__ x,
                                                                  const T* __restrict__ f, T* __restrict__ out, T alpha,
@@ -413,14 +440,8 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv,
     if ((hx < 0 || hx >= MZ_TX) && (hy < 0 || hy >= MZ_TY)) hx = hy = -100;
   }
   const bool has_halo = hx > -100;
-  const int hgi = p.lo[0] + i0 + hx, hgj = p.lo[1] + j0 + hy;
-  const bool h_out_x = has_halo && (hgi < 0 || hgi >= lv.ndom[0]);
-  const bool h_out_y = has_halo && (hgj < 0 || hgj >= lv.ndom[1]);
-  // halo positions outside the patch's stored ghost layers (ragged tiles) are never read
-  const bool h_ok = has_halo && i0 + hx >= -NG && i0 + hx < p.n[0] + NG && j0 + hy >= -NG && j0 + hy < p.n[1] + NG;
   // column base offsets (local index 0 along z)
   const long long colc = p.off + (long long)(i + NG) + (long long)(j + NG) * sy + (long long)NG * sz;
-  const long long colh = p.off + (long long)(i0 + hx + NG) + (long long)(j0 + hy + NG) * sy + (long long)NG * sz;
   const int nzd = lv.ndom[2], lz = p.lo[2];
   const int kxc = face_class(gi, lv.ndom[0]), kyc = face_class(gj, lv.ndom[1]);
   // register queue of the column: x at planes k-2 .. k+2
@@ -437,27 +458,9 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv,
     const long long oc = colc + (long long)k * sz;
     if (MODE != OP_JACOBI0) {
       T* s = sp[buf];
-      s[(ty + 2) * MZ_W + tx + 2] = active ? q2 : T(0);
-      if (h_ok) {
-        T hv;
-        if (h_out_x) {
-          // x ghost of row (hgj, k): formula from the row's first / last four cells
-          const int side = hgi < 0 ? 0 : 1, layer = side == 0 ? -hgi : hgi - lv.ndom[0] + 1, type = lv.bc[side];
-          const long long rb = p.off + (long long)(j0 + hy + NG) * sy + (long long)(k + NG) * sz + NG;
-          hv = T(0);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) hv += gcoef<T>(type, layer - 1, m) * x[rb + ((side == 0 ? m : lv.ndom[0] - 1 - m) - p.lo[0])];
-        } else if (h_out_y) {
-          const int side = hgj < 0 ? 0 : 1, layer = side == 0 ? -hgj : hgj - lv.ndom[1] + 1, type = lv.bc[2 + side];
-          const long long cb = p.off + (long long)(i0 + hx + NG) + (long long)(k + NG) * sz + (long long)NG * sy;
-          hv = T(0);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) hv += gcoef<T>(type, layer - 1, m) * x[cb + (long long)((side == 0 ? m : lv.ndom[1] - 1 - m) - p.lo[1]) * sy];
-        } else {
-          hv = x[colh + (long long)k * sz];
-        }
-        s[(hy + 2) * MZ_W + hx + 2] = hv;
-      }
+      // tile cells outside the patch (ragged tiles) hold the ghost values next to it
+      s[(ty + 2) * MZ_W + tx + 2] = active ? q2 : mz_plane_value<T>(x, p, lv, i, j, k);
+      if (has_halo) s[(hy + 2) * MZ_W + hx + 2] = mz_plane_value<T>(x, p, lv, i0 + hx, j0 + hy, k);
       __syncthreads();
     }
     if (active && (vmask == nullptr || vmask[oc])) {
