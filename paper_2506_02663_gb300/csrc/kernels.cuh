@@ -365,10 +365,11 @@ __device__ __forceinline__ T mz_column(const T* __restrict__ xb, long long base,
 
 // x at patch-local (li, lj) of plane k as the stencil sees it: stored values (interior, or
 // CF / copy ghosts) inside the domain, the ghost formula outside; 0 at positions no stencil of
-// an interior cell reads (corners, beyond the stored ghost layers)
+// an interior cell reads (corners, beyond the stored ghost layers).  The formula cases are
+// rare and kept out of line.
 template <typename T>
-__device__ __forceinline__ T mz_plane_value(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int li, int lj,
-                                           int k) {
+__device__ __noinline__ T mz_plane_value_slow(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int li,
+                                              int lj, int k) {
   const int gi = p.lo[0] + li, gj = p.lo[1] + lj;
   const bool ox = gi < 0 || gi >= lv.ndom[0], oy = gj < 0 || gj >= lv.ndom[1];
   if (ox && oy) return T(0);
@@ -390,8 +391,18 @@ __device__ __forceinline__ T mz_plane_value(const T* __restrict__ x, const Patch
   return x[poff(p, li, lj, k)];
 }
 
+template <typename T>
+__device__ __forceinline__ T mz_plane_value(const T* __restrict__ x, const PatchDesc& p, const LevelView& lv, int li, int lj,
+                                           int k) {
+  const int gi = p.lo[0] + li, gj = p.lo[1] + lj;
+  if (gi >= 0 && gi < lv.ndom[0] && gj >= 0 && gj < lv.ndom[1] && li >= -NG && li < p.n[0] + NG && lj >= -NG &&
+      lj < p.n[1] + NG)
+    return x[poff(p, li, lj, k)];
+  return mz_plane_value_slow<T>(x, p, lv, li, lj, k);
+}
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv, int nzc, int kz, const T* __restrict__ x,
+__global__ void __launch_bounds__(MZ_TX* MZ_TY, 4) k_level_op3d_march(LevelView lv, int nzc, int kz, const T* __restrict__ x,
                                                                  const T* __restrict__ f, T* __restrict__ out, T alpha,
                                                                  T beta, T omega,
                                                                  const unsigned char* __restrict__ vmask) {
@@ -453,20 +464,34 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv,
     q3 = mz_column<T>(x, colc, sz, lz + k0 + 1, nzd, lz, lv, 2);
     q4 = mz_column<T>(x, colc, sz, lz + k0 + 2, nzd, lz, lv, 2);
   }
+  // software pipeline: the plane-k loads (halo, the centre of an inactive tile cell, f) are
+  // issued one plane ahead, so their latency overlaps the barrier and the arithmetic
+  T hnext = T(0), cnext = T(0), fnext = T(0);
+  if (MODE != OP_JACOBI0) {
+    if (has_halo) hnext = mz_plane_value<T>(x, p, lv, i0 + hx, j0 + hy, k0);
+    if (!active) cnext = mz_plane_value<T>(x, p, lv, i, j, k0);
+  }
+  if (active && MODE != OP_APPLY) fnext = f[colc + (long long)k0 * sz];
   __syncthreads();  // weight table
   for (int k = k0, buf = 0; k < k1; ++k, buf ^= 1) {
     const long long oc = colc + (long long)k * sz;
+    const T fk = fnext;
     if (MODE != OP_JACOBI0) {
       T* s = sp[buf];
       // tile cells outside the patch (ragged tiles) hold the ghost values next to it
-      s[(ty + 2) * MZ_W + tx + 2] = active ? q2 : mz_plane_value<T>(x, p, lv, i, j, k);
-      if (has_halo) s[(hy + 2) * MZ_W + hx + 2] = mz_plane_value<T>(x, p, lv, i0 + hx, j0 + hy, k);
-      __syncthreads();
+      s[(ty + 2) * MZ_W + tx + 2] = active ? q2 : cnext;
+      if (has_halo) s[(hy + 2) * MZ_W + hx + 2] = hnext;
+      if (k + 1 < k1) {
+        if (has_halo) hnext = mz_plane_value<T>(x, p, lv, i0 + hx, j0 + hy, k + 1);
+        if (!active) cnext = mz_plane_value<T>(x, p, lv, i, j, k + 1);
+      }
     }
+    if (active && MODE != OP_APPLY && k + 1 < k1) fnext = f[oc + sz];
+    if (MODE != OP_JACOBI0) __syncthreads();
     if (active && (vmask == nullptr || vmask[oc])) {
       const int kzc = face_class(lz + k, nzd);
       if (MODE == OP_JACOBI0) {
-        out[oc] = wt[kxc + 5 * kyc + 25 * kzc] * f[oc];
+        out[oc] = wt[kxc + 5 * kyc + 25 * kzc] * fk;
       } else {
         const T* s = sp[buf];
         const int c = (ty + 2) * MZ_W + tx + 2;
@@ -476,8 +501,8 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY) k_level_op3d_march(LevelView lv,
         const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
         const T ax = alpha * xc + beta * (lap * inv);
         if (MODE == OP_APPLY) out[oc] = ax;
-        else if (MODE == OP_RESID) out[oc] = f[oc] - ax;
-        else out[oc] = xc + wt[kxc + 5 * kyc + 25 * kzc] * (f[oc] - ax);
+        else if (MODE == OP_RESID) out[oc] = fk - ax;
+        else out[oc] = xc + wt[kxc + 5 * kyc + 25 * kzc] * (fk - ax);
       }
     }
     if (MODE != OP_JACOBI0 && active) {
