@@ -48,9 +48,10 @@ def _args():
     ap.add_argument("--no-graph", action="store_true", help="host-driven V-cycle loop instead of the captured solve")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and the large-grid roofline")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D workload in the extras")
-    ap.add_argument("--profile-case", choices=["none", "large", "bench"], default="none",
+    ap.add_argument("--profile-case", choices=["none", "large", "bench", "single3d"], default="none",
                     help="large: one mixed-precision solve of the single-level 4096^2 case; bench: one warm-up "
-                         "and one timed step of the bench workload and nothing else (both for ncu)")
+                         "and one timed step of the bench workload and nothing else; single3d: two mixed-precision "
+                         "V-cycles of a single-level 256^3 Helmholtz problem (all for ncu)")
     return ap.parse_args()
 
 
@@ -624,6 +625,24 @@ def _profile_case():
     return 0
 
 
+def _profile_single3d(n=256):
+    """Two mixed-precision V-cycles (host-driven loop) of a single-level n^3 Helmholtz problem
+    with homogeneous Dirichlet data: the 3-D level-operator kernels on a grid whose fields
+    exceed L2 (67 MB per FP32 field at 256^3)."""
+    import torch
+    from paper_2506_02663_gb300 import amr
+    from paper_2506_02663_gb300 import workloads as wl
+    gh = amr.Hierarchy(3, (n, n, n), [[((0, 0, 0), (n - 1, n - 1, n - 1))]])
+    op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA, [0] * 6)
+    f = torch.ones(gh.nelems, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(f)
+    st = op.solve(phi, f, params=amr.default_params(rtol=1e-30, max_vcycles=2, precision=amr.MIXED, use_graph=0),
+                  allow_not_converged=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "single3d", "vcycles": st["vcycles"], "final_res": st["final_res"]}))
+    return 0
+
+
 def _profile_bench(args):
     """One warm-up step and one step of the bench workload (graph mode), for launch lists."""
     import torch
@@ -648,6 +667,8 @@ def main():
         return _profile_case()
     if args.profile_case == "bench":
         return _profile_bench(args)
+    if args.profile_case == "single3d":
+        return _profile_single3d()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
