@@ -345,6 +345,12 @@ long long amr_kernel_launches(void);
  * read, x written once). */
 amr_status amr_profile_enable(int on);
 amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes);
+/* Tile shape of the tiled level-operator kernels (not in the paper: a tuning and testing
+ * control).  rows = 0 (the default) uses the autotuner's choice per grid; rows = 1, 2 or 4
+ * forces that many cells per thread along y in the 2-D kernel, rows = 2 or 4 in the 3-D
+ * z-chunked kernel (a 3-D grid whose y extent is not a multiple of 8 rows takes 2; rows = 1
+ * counts as 2 there).  Process-wide; AMR_ERR_INVALID_ARG for any other value. */
+amr_status amr_set_tile_rows(int rows);
 
 #ifdef __cplusplus
 }

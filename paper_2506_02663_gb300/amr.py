@@ -92,6 +92,7 @@ _sigs = {
     "amr_last_error": [],
     "amr_kernel_launches": [],
     "amr_profile_enable": [C.c_int],
+    "amr_set_tile_rows": [C.c_int],
     "amr_profile_read": [C.c_int, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
 }
 for _n, _a in _sigs.items():
@@ -110,6 +111,12 @@ def kernel_launches():
 
 
 KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG, KC_DOWN, KC_UP, KC_COARSE = 0, 1, 2, 3, 4, 5, 6
+
+
+def set_tile_rows(rows):
+    """0: autotuned tile shape per grid; 1, 2, 4: cells per thread along y forced in the tiled
+    level-operator kernels (3-D: 2 or 4)."""
+    _check(_lib.amr_set_tile_rows(int(rows)), "amr_set_tile_rows")
 
 
 def profile_enable(on):

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "amr4_impl.h"
 
 namespace amr4 {
@@ -512,6 +514,226 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY, 4) k_level_op3d_march(LevelView 
       q3 = q4;
       if (k + 1 < k1) q4 = mz_column<T>(x, colc, sz, lz + k + 3, nzd, lz, lv, 2);
     }
+  }
+}
+
+// ------------------------------------------------------------------------ z-chunked 3-D marching operator
+// Level operator on a single-patch 3-D level whose x and y extents are multiples of the
+// 32 x 8R tile (R = 2 or 4 rows per thread, chosen per grid by the tile autotuner).  Block b
+// marches up z through chunk b / ntiles of tile column b % ntiles; the host sizes the chunks
+// so that the grid fits one wave, and since neighbouring tiles carry consecutive block
+// indices they march side by side and a tile's halo rows come from L2 where the neighbour
+// has just brought them in.  Thread (tx, ty) owns the columns (i0 + tx, j0 + ty + 8 r),
+// r < R: x at planes k-2..k+2 of each sits in registers, the plane k with its two-cell halo
+// in shared memory (double-buffered, one barrier per plane).  Every load of x, f and the
+// halo is issued two planes before its use (two register slots used alternately, so no
+// register with a load in flight is ever copied), and offsets inside the patch are 32-bit.
+// Physical ghost values outside the domain come from the same formulas as everywhere else,
+// the Jacobi factor from the 125-entry distance-class table; the summation order is cell_Lx's.
+constexpr int ZC_TX = 32, ZC_TY = 8, ZC_W = ZC_TX + 4;
+
+template <int R>
+struct ZcGeom {
+  static constexpr int TH = ZC_TY * R;                   // tile rows
+  static constexpr int SH = TH + 4;                      // shared-plane rows
+  static constexpr int NH = 2 * 2 * ZC_TX + 2 * 2 * TH;  // halo cells the stencil reads
+};
+
+// x of column ``col`` at patch-local plane k: stored values inside the domain, outside it in
+// z Eq. (velBCHomoDiri5th) / Eq. (Neumann5) with homogeneous data from the four planes next
+// to the face (a block-uniform branch, taken only by chunks at a z face)
+template <typename T>
+__device__ __forceinline__ T zc_zval(const T* __restrict__ xb, int col, int sz, int k, int lz, int nzd,
+                                     const LevelView& lv) {
+  const int g = lz + k;
+  if (g >= 0 && g < nzd) return xb[col + (k + NG) * sz];
+  const int side = g < 0 ? 0 : 1, layer = side == 0 ? -g : g - nzd + 1, type = lv.bc[4 + side];
+  const int k0 = (side == 0 ? 0 : nzd - 1) - lz + NG, dk = side == 0 ? sz : -sz;
+  T v = T(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) v += gcoef<T>(type, layer - 1, m) * xb[col + k0 * sz + m * dk];
+  return v;
+}
+
+template <int I>
+using zc_slot = std::integral_constant<int, I>;
+
+template <typename T, int MODE, int R>
+__global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
+    k_level_op3d_zc(LevelView lv, int ntx, int ntiles, int kc, const T* __restrict__ x, const T* __restrict__ f,
+                    T* __restrict__ out, T alpha, T beta, T omega, const unsigned char* __restrict__ vmask) {
+  using G = ZcGeom<R>;
+  pdl_wait();
+  __shared__ T sp[2][G::SH * ZC_W];
+  __shared__ T wt[125];
+  const PatchDesc p = lv.patches[0];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZC_TX + tx;
+  const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  if (MODE == OP_JACOBI || MODE == OP_JACOBI0) {
+    for (int q = tid; q < 125; q += ZC_TX * ZC_TY) {
+      const int a = q % 5, b = (q / 5) % 5, c = q / 25;
+      const int cls[3] = {a, b, c};
+      T acc = T(-90);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (cls[d]) acc += pick<T>(lv.dcorr[2 * d + (cls[d] - 1) / 2][(cls[d] - 1) % 2],
+                                   lv.dcorr_f[2 * d + (cls[d] - 1) / 2][(cls[d] - 1) % 2]);
+      wt[q] = omega / (alpha + beta * inv * acc);
+    }
+  }
+  const int sy = (int)p.sy, sz = (int)p.sz, nz = p.n[2];
+  const int nzd = lv.ndom[2], lz = p.lo[2];
+  const T* __restrict__ xb = x + p.off;
+  const T* __restrict__ fb = f + p.off;
+  T* __restrict__ ob = out + p.off;
+  // valid mask: only residuals are masked
+  const unsigned char* __restrict__ vb = (MODE == OP_RESID && vmask) ? vmask + p.off : nullptr;
+  // this thread's halo cell (tile-local): warps 0-1 the two rows below the tile, 2-3 the two
+  // rows above, the next ones the two columns on each side (lane pairs share a row)
+  int hx = 0, hy = 0;
+  const bool has_halo = tid < G::NH;
+  {
+    const int q = tid;
+    if (q < 2 * ZC_TX) {
+      hy = -2 + q / ZC_TX;
+      hx = q % ZC_TX;
+    } else if (q < 4 * ZC_TX) {
+      hy = G::TH + (q - 2 * ZC_TX) / ZC_TX;
+      hx = q % ZC_TX;
+    } else if (q < G::NH) {
+      const int r = q - 4 * ZC_TX, side = r / (2 * G::TH), c = r & 1;
+      hy = (r % (2 * G::TH)) >> 1;
+      hx = side == 0 ? c - 2 : ZC_TX + c;
+    }
+  }
+  const int hs = (hy + 2) * ZC_W + hx + 2;
+  const int c0 = (ty + 2) * ZC_W + tx + 2;  // shared index of row r: c0 + r * ZC_TY * ZC_W
+  const int tile = blockIdx.x % ntiles, ka = (blockIdx.x / ntiles) * kc, kb = min(nz, ka + kc);
+  __syncthreads();  // weight table
+  if (ka >= kb) return;
+  const int i0 = (tile % ntx) * ZC_TX, j0 = (tile / ntx) * G::TH;
+  const int i = i0 + tx;
+  const int col0 = (i + NG) + (j0 + ty + NG) * sy;  // column of row r: col0 + r * ZC_TY * sy
+  const int kx = face_class(p.lo[0] + i, lv.ndom[0]);
+  int wxy[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) wxy[r] = kx + 5 * face_class(p.lo[1] + j0 + ty + r * ZC_TY, lv.ndom[1]);
+  // halo cell: stored value inside the domain (interior, CF or copy ghost); outside it the
+  // ghost formula along the face normal from the four cells next to the face, whose first
+  // column and step are fixed here (corners of the halo are never read)
+  const int hli = i0 + hx, hlj = j0 + hy;
+  int hcol = (hli + NG) + (hlj + NG) * sy, hstep = 0, htype = 0, hlayer = 0;
+  {
+    const int hgi = p.lo[0] + hli, hgj = p.lo[1] + hlj;
+    const int d = (hgi < 0 || hgi >= lv.ndom[0]) ? 0 : ((hgj < 0 || hgj >= lv.ndom[1]) ? 1 : -1);
+    if (d >= 0) {
+      const int g = d == 0 ? hgi : hgj, n = lv.ndom[d], side = g < 0 ? 0 : 1;
+      hlayer = (side == 0 ? -g : g - n + 1) - 1;
+      htype = lv.bc[2 * d + side];
+      const int st = d == 0 ? 1 : sy;
+      const int first = (side == 0 ? 0 : n - 1) - p.lo[d] + NG;  // padded index of the face cell
+      hcol = d == 0 ? first + (hlj + NG) * sy : (hli + NG) + first * sy;
+      hstep = side == 0 ? st : -st;
+    }
+  }
+  auto halo = [&](int k) -> T {
+    const int o = hcol + (k + NG) * sz;
+    if (hstep == 0) return xb[o];
+    T v = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v += gcoef<T>(htype, hlayer, m) * xb[o + m * hstep];
+    return v;
+  };
+  constexpr int RS = ZC_TY;  // row step of a thread's columns (rows)
+  T q[R][5];                 // x of each column at planes k-2..k+2
+  T xs[2][R], fs[2][R], hv[2];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) q[r][m] = T(0);
+    xs[0][r] = xs[1][r] = fs[0][r] = fs[1][r] = T(0);
+  }
+  hv[0] = hv[1] = T(0);
+  if (MODE != OP_JACOBI0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int col = col0 + r * RS * sy;
+      q[r][0] = zc_zval<T>(xb, col, sz, ka - 2, lz, nzd, lv);
+      q[r][1] = zc_zval<T>(xb, col, sz, ka - 1, lz, nzd, lv);
+      q[r][2] = xb[col + (ka + NG) * sz];
+      q[r][3] = zc_zval<T>(xb, col, sz, ka + 1, lz, nzd, lv);
+      q[r][4] = zc_zval<T>(xb, col, sz, ka + 2, lz, nzd, lv);
+      if (ka + 1 < kb) xs[0][r] = zc_zval<T>(xb, col, sz, ka + 3, lz, nzd, lv);  // q4 of plane ka+1
+      if (ka + 2 < kb) xs[1][r] = zc_zval<T>(xb, col, sz, ka + 4, lz, nzd, lv);  // q4 of plane ka+2
+    }
+    if (has_halo) {
+      hv[0] = halo(ka);
+      if (ka + 1 < kb) hv[1] = halo(ka + 1);
+    }
+  }
+  if (MODE != OP_APPLY) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int col = col0 + r * RS * sy;
+      fs[0][r] = fb[col + (ka + NG) * sz];
+      if (ka + 1 < kb) fs[1][r] = fb[col + (ka + 1 + NG) * sz];
+    }
+  }
+  // one plane: stage, refill the consumed slots with plane k+2, barrier, compute, advance
+  // the queues (q4 from the slot loaded two planes ago, then the slot reloaded)
+  auto step = [&](int k, auto slot) {
+    constexpr int S = decltype(slot)::value;
+    T* __restrict__ s = sp[S];
+    T fk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) fk[r] = fs[S][r];
+    if (MODE != OP_JACOBI0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[c0 + r * RS * ZC_W] = q[r][2];
+      if (has_halo) {
+        s[hs] = hv[S];
+        if (k + 2 < kb) hv[S] = halo(k + 2);
+      }
+    }
+    if (MODE != OP_APPLY && k + 2 < kb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) fs[S][r] = fb[col0 + r * RS * sy + (k + 2 + NG) * sz];
+    }
+    if (MODE != OP_JACOBI0) __syncthreads();
+    const int kz25 = 25 * face_class(lz + k, nzd);
+    const int pk = col0 + (k + NG) * sz;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int P = pk + r * RS * sy;
+      if (MODE == OP_JACOBI0) {
+        ob[P] = wt[wxy[r] + kz25] * fk[r];
+      } else {
+        const int C = c0 + r * RS * ZC_W;
+        const T xc = q[r][2];
+        const T s1 = ((s[C - 1] + s[C + 1]) + (s[C - ZC_W] + s[C + ZC_W])) + (q[r][1] + q[r][3]);
+        const T s2 = ((s[C - 2] + s[C + 2]) + (s[C - 2 * ZC_W] + s[C + 2 * ZC_W])) + (q[r][0] + q[r][4]);
+        const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
+        const T ax = alpha * xc + beta * (lap * inv);
+        if (MODE == OP_APPLY) ob[P] = ax;
+        else if (MODE == OP_RESID) { if (vb == nullptr || vb[P]) ob[P] = fk[r] - ax; }
+        else ob[P] = xc + wt[wxy[r] + kz25] * (fk[r] - ax);
+      }
+    }
+    if (MODE != OP_JACOBI0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        q[r][0] = q[r][1];
+        q[r][1] = q[r][2];
+        q[r][2] = q[r][3];
+        q[r][3] = q[r][4];
+        q[r][4] = xs[S][r];
+        if (k + 3 < kb) xs[S][r] = zc_zval<T>(xb, col0 + r * RS * sy, sz, k + 5, lz, nzd, lv);  // q4 of plane k+3
+      }
+    }
+  };
+  for (int k = ka; k < kb; k += 2) {
+    step(k, zc_slot<0>{});
+    if (k + 1 < kb) step(k + 1, zc_slot<1>{});
   }
 }
 

@@ -126,19 +126,28 @@ inline amr_status launch_check() {
 }
 
 // ---------------------------------------------------------------- tile autotuner
-// Rows per thread of the tiled 2-D kernel, per (grid cells, value size): filled by
-// autotune_tiles() (CUDA-event timing of each variant on the operator's own buffers), with
-// a size-based default before tuning.
+// Rows per thread of the tiled 2-D kernel and of the z-chunked 3-D kernel, per (dimension,
+// grid cells, value size): filled by autotune_tiles() (CUDA-event timing of each variant on
+// the operator's own buffers), with a size-based default before tuning.
 std::mutex g_tile_mu;
-std::vector<std::pair<long long, int>> g_tile_table;  // key = ncells * 16 + sizeof(T)
+std::vector<std::pair<long long, int>> g_tile_table;
+
+inline long long tile_key(const LevelView& lv, size_t tsize) {
+  return ((long long)lv.ncells * 4 + lv.D) * 16 + (long long)tsize;
+}
+
+std::atomic<int> g_tile_force{0};  // amr_set_tile_rows: 0 = autotuned
 
 inline int tile_rows_for(const LevelView& lv, size_t tsize) {
-  const long long key = (long long)lv.ncells * 16 + (long long)tsize;
+  const int forced = g_tile_force.load(std::memory_order_relaxed);
+  if (forced) return lv.D == 3 ? std::max(2, forced) : forced;
+  const long long key = tile_key(lv, tsize);
   {
     std::lock_guard<std::mutex> lock(g_tile_mu);
     for (const auto& e : g_tile_table)
       if (e.first == key) return e.second;
   }
+  if (lv.D == 3) return 2;
   return lv.ncells >= 1024.0 * 1024.0 ? 4 : 1;
 }
 
@@ -302,6 +311,40 @@ bool invert(std::vector<double>& A, int n) {
 }
 
 // ---------------------------------------------------------------- kernel wrappers
+// The z-chunked 3-D operator runs on single-patch levels whose x / y extents are multiples of
+// its 32 x 8R tile and whose padded patch has fewer than 2^31 elements (32-bit offsets).
+inline bool zc_eligible(const LevelView& lv, int R) {
+  if (lv.D != 3 || lv.npatch != 1 || lv.maxn[0] % ZC_TX != 0 || lv.maxn[1] % (ZC_TY * R) != 0 || lv.maxn[2] < MIN_BOX)
+    return false;
+  const long long px = ((lv.maxn[0] + 2 * NG) + 3) / 4 * 4;
+  return px * (lv.maxn[1] + 2 * NG) * (lv.maxn[2] + 2 * NG) < (1LL << 31);
+}
+
+// one full wave of the z-chunked 3-D kernel: resident blocks per SM x SMs (queried once)
+template <typename T, int M, int R>
+int zc_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_level_op3d_zc<T, M, R>, ZC_TX * ZC_TY, 0);
+    blocks = std::max(1, nsm * std::max(1, per));
+  }
+  return blocks;
+}
+
+// z chunks of the 3-D kernel: as many as one wave holds, at least 4 planes each
+template <typename T, int M, int R>
+void launch_zc(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T O, const unsigned char* vmask,
+               cudaStream_t st) {
+  const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * R)), nz = lv.maxn[2];
+  const int nch = std::max(1, std::min(zc_blocks<T, M, R>() / ntiles, nz / 4));
+  const int kc = (nz + nch - 1) / nch;
+  const int G = ntiles * ((nz + kc - 1) / kc);
+  launch(k_level_op3d_zc<T, M, R>, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, A, B, O, vmask);
+}
+
 template <typename T, int D, bool TR = false>
 amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* out, const T* bc, double alpha,
                     double beta, double omega, const unsigned char* vmask, cudaStream_t st) {
@@ -330,6 +373,26 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
       default: LAUNCH_TILED(OP_JACOBI0);
     }
 #undef LAUNCH_TILED
+    const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    return launch_check();
+  }
+  if (D == 3 && !TR && bc == nullptr && (vmask == nullptr || mode == OP_RESID) && zc_eligible(lv, 2)) {
+    // z-chunked marching path; rows per thread from the autotuner's table
+    const int R = (tile_rows_for(lv, sizeof(T)) == 4 && zc_eligible(lv, 4)) ? 4 : 2;
+    const T A = T(alpha), B = T(beta), O = T(omega);
+#define LAUNCH_ZC(M)                                                                                    \
+  do {                                                                                                  \
+    if (R == 4) launch_zc<T, M, 4>(lv, x, f, out, A, B, O, vmask, st);                                  \
+    else launch_zc<T, M, 2>(lv, x, f, out, A, B, O, vmask, st);                                         \
+  } while (0)
+    switch (mode) {
+      case OP_APPLY: LAUNCH_ZC(OP_APPLY); break;
+      case OP_RESID: LAUNCH_ZC(OP_RESID); break;
+      case OP_JACOBI: LAUNCH_ZC(OP_JACOBI); break;
+      default: LAUNCH_ZC(OP_JACOBI0);
+    }
+#undef LAUNCH_ZC
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
     prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
     return launch_check();
@@ -582,10 +645,12 @@ amr_status ensure_scratch(amr_operator* op) {
     CK(cudaMemset(S.mt[m], 0, q * sizeof(T)));
   }
   S.ready = true;
-  // choose the tiled kernel's rows per thread for every grid this operator smooths
+  // choose the tiled kernels' rows per thread for every grid this operator smooths
   if (op->h->D == 2) {
     if constexpr (sizeof(T) == 4) TRY(blk_attrs<T>());
     TRY((autotune_tiles<T, 2>(op, 0)));
+  } else {
+    TRY((autotune_tiles<T, 3>(op, 0)));
   }
   return AMR_OK;
 }
@@ -602,7 +667,6 @@ void free_scratch(Scratch<T>& S) {
 
 template <typename T, int D>
 amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
-  if (D != 2) return AMR_OK;
   amr_hierarchy* h = op->h;
   Scratch<T>& S = scratch<T>(op);
   std::vector<std::pair<LevelView, std::pair<T*, T*>>> cases;
@@ -613,7 +677,8 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
   CK(cudaEventCreate(&b));
   for (auto& c : cases) {
     const LevelView& lv = c.first;
-    const long long key = (long long)lv.ncells * 16 + (long long)sizeof(T);
+    if (D == 3 && !zc_eligible(lv, 4)) continue;  // only the 2-row 3-D variant applies
+    const long long key = tile_key(lv, sizeof(T));
     {
       std::lock_guard<std::mutex> lock(g_tile_mu);
       bool known = false;
@@ -621,8 +686,9 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
       if (known) continue;
     }
     float best = 1e30f;
-    int best_rows = 1;
-    for (int rows : {1, 2, 4}) {
+    int best_rows = D == 3 ? 2 : 1;
+    const std::vector<int> variants = D == 3 ? std::vector<int>{2, 4} : std::vector<int>{1, 2, 4};
+    for (int rows : variants) {
       {
         std::lock_guard<std::mutex> lock(g_tile_mu);
         g_tile_table.push_back({key, rows});
@@ -2057,6 +2123,12 @@ extern "C" {
 const char* amr_last_error(void) { return get_error(); }
 
 long long amr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+amr_status amr_set_tile_rows(int rows) {
+  if (rows != 0 && rows != 1 && rows != 2 && rows != 4) { set_error("tile rows must be 0, 1, 2 or 4"); return AMR_ERR_INVALID_ARG; }
+  g_tile_force.store(rows, std::memory_order_relaxed);
+  return AMR_OK;
+}
 
 amr_status amr_profile_enable(int on) {
   // events are never reused: a cached instrumented graph keeps recording into its own

@@ -88,3 +88,11 @@ def test_layout_alignment_and_bc_layout(amr):
     for l in range(len(per)):
         for k in range(len(per[l])):
             assert np.array_equal(back[l][k], per[l][k])
+
+
+def test_set_tile_rows_validates(amr):
+    """The tile-shape control accepts 0 (autotuned), 1, 2 and 4 and rejects the rest on the
+    host, without touching a GPU."""
+    with pytest.raises(Exception):
+        amr.set_tile_rows(3)
+    amr.set_tile_rows(0)

@@ -460,3 +460,86 @@ def test_3d_large_grid_smoother_and_apply_parity():
     op.apply(_dev(to_packed(gh, H, X)), out, bc=_dev(gh.pack_bc(data)))
     got = from_packed(gh, H, out.cpu().numpy())
     assert max_diff(H, got, ref) <= 1e-13 * op_scale(H, alpha, beta, X)
+
+
+@pytest.fixture
+def tile_rows():
+    amr = _amr()
+    yield amr.set_tile_rows
+    amr.set_tile_rows(0)
+
+
+@pytest.mark.parametrize("n", [(64, 48, 40), (64, 64, 40)])
+@pytest.mark.parametrize("rows", [2, 4])
+def test_3d_zchunk_operator_parity(n, rows, tile_rows):
+    """Single-level grids whose x, y extents are multiples of the z-chunked kernel's tile
+    (32 x 16 with two rows per thread, 32 x 32 with four; 48 rows fall back to two), so
+    blocks sit at every face and z chunks end inside the grid: three FP64 weighted-Jacobi
+    sweeps, the homogeneous operator and the residual against the oracle."""
+    amr = _amr()
+    tile_rows(rows)
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    bc = [0, 1, 0, 0, 1, 0]
+    H = OH(3, n, box, bc=bc, hi=tuple(v / n[0] for v in n))
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    rng = np.random.default_rng(67)
+    alpha, beta = 1.0, -0.02
+    op = amr.Operator(gh, alpha, beta, bc)
+    X = _rand_field(H, rng, redundant=False)
+    B = _rand_field(H, rng, redundant=False)
+    diag = mg.jacobi_diagonal(H, 0, alpha, beta)
+    Xr = X[0].copy()
+    for _ in range(3):
+        Xr = mg.jacobi(H, 0, Xr, B[0], diag, alpha, beta, 2.0 / 3.0)
+    dx = _dev(to_packed(gh, H, X))
+    op.smooth(0, 3, 2.0 / 3.0, dx, _dev(to_packed(gh, H, B)))
+    got = from_packed(gh, H, dx.cpu().numpy())
+    cov = H.levels[0].covered
+    assert float(np.max(np.abs(got[0][cov] - Xr[cov]))) <= 1e-12 * float(np.max(np.abs(Xr[cov])))
+    ref = cp.apply(H, X, alpha, beta, None)
+    out = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    op.apply(_dev(to_packed(gh, H, X)), out)
+    got = from_packed(gh, H, out.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-13 * op_scale(H, alpha, beta, X)
+    res = torch.zeros_like(out)
+    op.residual(_dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B)), res)
+    got = from_packed(gh, H, res.cpu().numpy())
+    refr = [B[l] - ref[l] for l in range(len(ref))]
+    assert max_diff(H, got, refr) <= 1e-13 * op_scale(H, alpha, beta, X)
+
+
+@pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
+@pytest.mark.parametrize("rows", [2, 4])
+def test_3d_zchunk_two_level_vcycle_and_solve(bcw, ab, rows, tile_rows):
+    """Two-level 3-D hierarchy whose levels both run the z-chunked kernel (base 32 x 32 x 16,
+    one ratio-2 box of 32 x 16 x 16 fine cells, covered cells on the base): one FP64 V-cycle
+    against the oracle's, and mixed- and FP64 solves to 1e-10 whose residual, recomputed by
+    the oracle, meets the tolerance."""
+    amr = _amr()
+    tile_rows(rows)
+    n0 = (32, 32, 16)
+    boxes = [[((0, 0, 0), (31, 31, 15))], [((16, 16, 8), (47, 31, 23))]]
+    bc = [bcw] * 6
+    alpha, beta = ab
+    H = OH(3, n0, boxes, bc=bc, hi=tuple(v / n0[0] for v in n0))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / n0[0])
+    rng = np.random.default_rng(71)
+    F = _rand_field(H, rng)
+    if so.is_pure_neumann(H, alpha):
+        F, _ = so.solvability_fix(H, F)
+    phi = _rand_field(H, rng)
+    ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+    op = amr.Operator(gh, alpha, beta, bc)
+    dphi = _dev(to_packed(gh, H, phi))
+    op.vcycle(dphi, _dev(to_packed(gh, H, F)))
+    got = from_packed(gh, H, dphi.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref)
+    for precision in (amr.FP64, amr.MIXED):
+        x = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve(x, _dev(to_packed(gh, H, F)),
+                      params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=precision))
+        sol = from_packed(gh, H, x.cpu().numpy())
+        r = cp.residual(H, sol, F, alpha, beta)
+        fmax = max_abs(H, F)
+        rmax = max(float(np.max(np.abs(r[l][lev.valid]))) for l, lev in enumerate(H.levels))
+        assert rmax <= 1.5e-10 * fmax, (precision, rmax / fmax, st)
