@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(MZ_TX* MZ_TY, 4) k_level_op3d_march(LevelView 
 // halo is issued two planes before its use (two register slots used alternately, so no
 // register with a load in flight is ever copied), and offsets inside the patch are 32-bit.
 // Physical ghost values outside the domain come from the same formulas as everywhere else,
-// the Jacobi factor from the 125-entry distance-class table; the summation order is cell_Lx's.
+// the Jacobi factor from the 125-entry distance-class table.
 constexpr int ZC_TX = 32, ZC_TY = 8, ZC_W = ZC_TX + 4;
 
 template <int R>
@@ -586,6 +586,10 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
   const T* __restrict__ xb = x + p.off;
   const T* __restrict__ fb = f + p.off;
   T* __restrict__ ob = out + p.off;
+  // alpha x + beta L x = kc0 x + kc1 s1 - kc2 s2 with s1, s2 the sums of the six distance-1 and
+  // distance-2 neighbours (Eq. discreteOps: 12 h^2 L x = 16 s1 - s2 - 90 x): three multiply-adds
+  // after the sums, which matters most in FP64, whose rate on this part is a small fraction of FP32's
+  const T kc2 = beta * inv, kc1 = T(16) * kc2, kc0 = alpha - T(90) * kc2;
   // valid mask: only residuals are masked
   const unsigned char* __restrict__ vb = (MODE == OP_RESID && vmask) ? vmask + p.off : nullptr;
   // this thread's halo cell (tile-local): warps 0-1 the two rows below the tile, 2-3 the two
@@ -712,11 +716,13 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
         const T xc = q[r][2];
         const T s1 = ((s[C - 1] + s[C + 1]) + (s[C - ZC_W] + s[C + ZC_W])) + (q[r][1] + q[r][3]);
         const T s2 = ((s[C - 2] + s[C + 2]) + (s[C - 2 * ZC_W] + s[C + 2 * ZC_W])) + (q[r][0] + q[r][4]);
-        const T lap = (T(16) * s1 - s2 - T(90) * xc) + T(0);
-        const T ax = alpha * xc + beta * (lap * inv);
-        if (MODE == OP_APPLY) ob[P] = ax;
-        else if (MODE == OP_RESID) { if (vb == nullptr || vb[P]) ob[P] = fk[r] - ax; }
-        else ob[P] = xc + wt[wxy[r] + kz25] * (fk[r] - ax);
+        if (MODE == OP_APPLY) {
+          ob[P] = kc0 * xc + (kc1 * s1 - kc2 * s2);
+        } else {
+          const T res = fma(kc2, s2, fma(-kc1, s1, fma(-kc0, xc, fk[r])));
+          if (MODE == OP_RESID) { if (vb == nullptr || vb[P]) ob[P] = res; }
+          else ob[P] = fma(wt[wxy[r] + kz25], res, xc);
+        }
       }
     }
     if (MODE != OP_JACOBI0) {
@@ -1602,6 +1608,300 @@ __global__ void __launch_bounds__(1024) k_mg_coarse2d(CoarseBlock2D cb, const T*
     for (int t = all.tid; t < n0 * n1; t += all.nth) {
       const int i = t % n0, j = t / n0;
       xg[(j + NG) * gsy + i + NG] = x0[(j + NG) * sy + i + NG];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ square coarse V-cycle
+// The coarse end of the 2-D level-0 multigrid for the common case of a square pyramid
+// N0, N0/2, ... down to the bottom grid (N0 = 64: bottom 4; N0 = 48: bottom 6), every size a
+// compile-time constant, so that every loop over a grid's cells has a fixed trip count and
+// every stencil offset is an immediate.  Same V-cycle as k_mg_coarse2d (weighted-Jacobi legs,
+// residual restriction, linear prolongation with the homogeneous extension, dense bottom
+// solve); the physical ghost layers of an array are written by one pass over its four sides
+// (one warp per side) before a sweep reads them.
+constexpr int SQ_NT = 1024;  // threads of the block
+
+template <int N>
+struct Sq {
+  static constexpr int S = N + 4;  // row pitch (two ghost layers each side)
+  static constexpr int E = S * S;
+  static constexpr bool bottom = (N % 2 != 0) || (N / 2 < MIN_BOX);
+};
+// element offset of grid N's three arrays (x, t, b) in shared memory
+template <int N0, int N>
+__host__ __device__ constexpr int sq_off() {
+  if constexpr (N >= N0) return 0;
+  else return sq_off<N0, 2 * N>() + 3 * Sq<2 * N>::E;
+}
+template <int N0, int N>
+__host__ __device__ constexpr int sq_total() {
+  if constexpr (Sq<N>::bottom) return sq_off<N0, N>() + 3 * Sq<N>::E;
+  else return sq_total<N0, N / 2>();
+}
+template <int N0, int N>
+__host__ __device__ constexpr int sq_bottom() {
+  if constexpr (Sq<N>::bottom) return N;
+  else return sq_bottom<N0, N / 2>();
+}
+template <int N0, int N>
+__host__ __device__ constexpr int sq_depth() {  // grid index of N (0 = N0)
+  if constexpr (N >= N0) return 0;
+  else return 1 + sq_depth<N0, 2 * N>();
+}
+
+struct SqCtx {
+  float alpha, beta, omega;
+  int bcm;  // boundary type of face f (0 Dirichlet, 1 Neumann) in bit f
+  int nu1, nu2;
+  __device__ __forceinline__ int bc(int f) const { return (bcm >> f) & 1; }
+};
+
+template <typename T, int N>
+__device__ __forceinline__ T sq_ax(const T* __restrict__ a, int i, int j, T alpha, T binv) {
+  constexpr int S = Sq<N>::S;
+  const int o = (j + 2) * S + i + 2;
+  const T xc = a[o];
+  const T s1 = (a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]);
+  const T s2 = (a[o - 2] + a[o + 2]) + (a[o - 2 * S] + a[o + 2 * S]);
+  return alpha * xc + binv * ((T(16) * s1 - s2 - T(60) * xc) + T(0));
+}
+
+// Jacobi factor omega / diag of (i, j): table entry kx + 5 ky by distance class to the faces
+template <int N>
+__device__ __forceinline__ int sq_class(int i, int j) {
+  return face_class(i, N) + 5 * face_class(j, N);
+}
+
+template <typename T, int N0>
+struct SqVcycle {
+  T* sm;                 // dynamic shared memory
+  const float* wt;       // per grid 25 Jacobi factors (shared)
+  const double* minv;    // bottom inverse
+  int nbot, ldb;
+  double* bot;           // bottom right-hand side (shared, FP64)
+  const float* binv;     // beta / (12 h^2) per grid (shared)
+  SqCtx c;
+
+  template <int N> __device__ T* X() const { return sm + sq_off<N0, N>(); }
+  template <int N> __device__ T* Tt() const { return sm + sq_off<N0, N>() + Sq<N>::E; }
+  template <int N> __device__ T* B() const { return sm + sq_off<N0, N>() + 2 * Sq<N>::E; }
+
+  // physical ghost layers 1 and 2 of array a on grid N (Eqs. (velBCHomoDiri5th)/(Neumann5),
+  // homogeneous), entry e = side x (2N) + 2 position + layer; with corners, also the four
+  // layer-1 corner ghosts as the x extension of the y extension
+  template <int N>
+  __device__ void ghosts(T* a, bool corners) const {
+    constexpr int S = Sq<N>::S, NE = 8 * N, IT = (NE + SQ_NT - 1) / SQ_NT;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+      const int e = tid + q * SQ_NT;
+      if (NE % SQ_NT == 0 || e < NE) {
+        const int f = e / (2 * N), pos = (e % (2 * N)) >> 1, layer = e & 1;
+        const int side = f & 1, t = c.bc(f);
+        T v = T(0);
+        if (f < 2) {
+          const int row = (pos + 2) * S + 2;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) v += gcoef<T>(t, layer, m) * a[row + (side == 0 ? m : N - 1 - m)];
+          a[row + (side == 0 ? -1 - layer : N + layer)] = v;
+        } else {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) v += gcoef<T>(t, layer, m) * a[((side == 0 ? m : N - 1 - m) + 2) * S + pos + 2];
+          a[((side == 0 ? -1 - layer : N + layer) + 2) * S + pos + 2] = v;
+        }
+      }
+    }
+    if (corners && tid < 4) {
+      const int sx = tid & 1, sy = tid >> 1, tx = c.bc(sx), ty = c.bc(2 + sy);
+      T v = T(0);
+#pragma unroll
+      for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 4; ++ib)
+          v += gcoef<T>(tx, 0, ia) * gcoef<T>(ty, 0, ib) *
+               a[((sy == 0 ? ib : N - 1 - ib) + 2) * S + (sx == 0 ? ia : N - 1 - ia) + 2];
+      a[((sy == 0 ? -1 : N) + 2) * S + (sx == 0 ? -1 : N) + 2] = v;
+    }
+    __syncthreads();
+  }
+
+  // nu weighted-Jacobi sweeps on grid N; zero: the first one starts from x = 0 and writes a.
+  // Returns the array holding the result.
+  template <int N>
+  __device__ T* smooth(T* a, T* o, int nu, bool zero) const {
+    constexpr int S = Sq<N>::S, NC = N * N, IT = (NC + SQ_NT - 1) / SQ_NT;
+    const T* b = B<N>();
+    const float* w = wt + 25 * sq_depth<N0, N>();
+    const T bi = T(binv[sq_depth<N0, N>()]);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int s = 0; s < nu; ++s) {
+      const bool z = zero && s == 0;
+      if (!z) ghosts<N>(a, false);
+#pragma unroll
+      for (int q = 0; q < IT; ++q) {
+        const int cidx = tid + q * SQ_NT;
+        if (NC % SQ_NT == 0 || cidx < NC) {
+          const int i = cidx % N, j = cidx / N;
+          const int oc = (j + 2) * S + i + 2;
+          const T wc = T(w[sq_class<N>(i, j)]);
+          if (z) a[oc] = wc * b[oc];
+          else o[oc] = a[oc] + wc * (b[oc] - sq_ax<T, N>(a, i, j, T(c.alpha), bi));
+        }
+      }
+      __syncthreads();
+      if (!z) { T* sw = a; a = o; o = sw; }
+    }
+    return a;
+  }
+
+  // residual of grid N restricted (2 x 2 average) into the right-hand side of grid N/2
+  template <int N>
+  __device__ void restrict_residual(const T* a) const {
+    constexpr int M = N / 2, MS = Sq<M>::S, NC = M * M, IT = (NC + SQ_NT - 1) / SQ_NT;
+    constexpr int S = Sq<N>::S;
+    const T* b = B<N>();
+    T* bc = B<M>();
+    const T bi = T(binv[sq_depth<N0, N>()]);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    ghosts<N>(const_cast<T*>(a), false);
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+      const int cidx = tid + q * SQ_NT;
+      if (NC % SQ_NT == 0 || cidx < NC) {
+        const int ci = cidx % M, cj = cidx / M;
+        T acc = T(0);
+#pragma unroll
+        for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+          for (int q0 = 0; q0 < 2; ++q0) {
+            const int i = 2 * ci + q0, j = 2 * cj + q1;
+            acc += b[(j + 2) * S + i + 2] - sq_ax<T, N>(a, i, j, T(c.alpha), bi);
+          }
+        bc[(cj + 2) * MS + ci + 2] = acc * T(0.25);
+      }
+    }
+    __syncthreads();
+  }
+
+  // x_N += linear prolongation of the grid-N/2 correction cg (coarse values outside the
+  // domain: the homogeneous layer-1 extension, corners included)
+  template <int N>
+  __device__ void prolong(T* a, T* cg) const {
+    constexpr int M = N / 2, S = Sq<N>::S, NC = N * N, IT = (NC + SQ_NT - 1) / SQ_NT;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    ghosts<M>(cg, true);
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+      const int cidx = tid + q * SQ_NT;
+      if (NC % SQ_NT == 0 || cidx < NC) {
+        const int i = cidx % N, j = cidx / N;
+        const int p0 = i >> 1, p1 = j >> 1;
+        const int s0 = (i & 1) ? 1 : -1, s1 = (j & 1) ? 1 : -1;
+        const int oc = (p1 + 2) * Sq<M>::S + p0 + 2;
+        const T c00 = cg[oc];
+        const T c10 = cg[oc + s0];
+        const T c01 = cg[oc + s1 * Sq<M>::S];
+        const T c11 = cg[oc + s1 * Sq<M>::S + s0];
+        T v = T(0);
+        v += (T(0.75) * T(0.75)) * c00;
+        v += (T(0.25) * T(0.75)) * c10;
+        v += (T(0.75) * T(0.25)) * c01;
+        v += (T(0.25) * T(0.25)) * c11;
+        a[(j + 2) * S + i + 2] += v;
+      }
+    }
+    __syncthreads();
+  }
+
+  // dense bottom solve on grid N (FP64 accumulation), result in X<N>
+  template <int N>
+  __device__ void bottom() const {
+    constexpr int S = Sq<N>::S;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const T* b = B<N>();
+    for (int t = tid; t < nbot; t += SQ_NT) bot[t] = (double)b[(t / N + 2) * S + t % N + 2];
+    __syncthreads();
+    T* x = X<N>();
+    for (int t = tid; t < nbot; t += SQ_NT) {
+      double acc = 0.0;
+      const double* row = minv + (long long)t * ldb;
+      for (int k = 0; k < nbot; ++k) acc = fma(row[k], bot[k], acc);
+      x[(t / N + 2) * S + t % N + 2] = T(acc);
+    }
+    __syncthreads();
+  }
+
+  // V-cycle from grid N down (its right-hand side in B<N>); returns the array with the result
+  template <int N>
+  __device__ T* cycle() const {
+    if constexpr (Sq<N>::bottom) {
+      bottom<N>();
+      return X<N>();
+    } else {
+      T* cur = smooth<N>(X<N>(), Tt<N>(), c.nu1, true);
+      restrict_residual<N>(cur);
+      T* cg = cycle<N / 2>();
+      prolong<N>(cur, cg);
+      return smooth<N>(cur, cur == X<N>() ? Tt<N>() : X<N>(), c.nu2, false);
+    }
+  }
+};
+
+template <typename T, int N0>
+__global__ void __launch_bounds__(SQ_NT) k_mg_coarse2d_sq(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
+                                                          T alpha, T beta, T omega) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ float wt[25 * CB_MAX];
+  __shared__ double bot[1024];
+  __shared__ float sbinv[CB_MAX];
+  SqVcycle<T, N0> v;
+  v.sm = reinterpret_cast<T*>(smraw);
+  v.wt = wt;
+  v.minv = cb.minv;
+  v.nbot = cb.nbot;
+  v.ldb = cb.ldb;
+  v.bot = bot;
+  v.binv = sbinv;
+  v.c.alpha = (float)alpha;
+  v.c.beta = (float)beta;
+  v.c.omega = (float)omega;
+  v.c.bcm = 0;
+  for (int f = 0; f < 4; ++f) v.c.bcm |= (cb.lv[0].bc[f] & 1) << f;
+  v.c.nu1 = cb.nu1;
+  v.c.nu2 = cb.nu2;
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  for (int q = tid; q < cb.ng; q += SQ_NT) sbinv[q] = beta * cb.lv[q].inv12h2_f;
+  // Jacobi factors per grid (the diagonal differs from the interior one within two cells of a
+  // face: diag_sum's order, -60 then the x correction, then the y correction)
+  for (int e = tid; e < 25 * cb.ng; e += SQ_NT) {
+    const int q = e / 25, k = e % 25, a = k % 5, bb = k / 5;
+    const LevelView& lv = cb.lv[q];
+    const float cx = a == 0 ? 0.f : lv.dcorr_f[(a - 1) / 2][(a - 1) % 2];
+    const float cy = bb == 0 ? 0.f : lv.dcorr_f[2 + (bb - 1) / 2][(bb - 1) % 2];
+    wt[e] = k == 0 ? (float)cb.ood[q] : (float)(omega / (alpha + beta * lv.inv12h2_f * ((T(-60) + cx) + cy)));
+  }
+  {
+    constexpr int S = Sq<N0>::S;
+    const T* __restrict__ bg = b + cb.gp.off;
+    const int gsy = (int)cb.gp.sy;
+    T* bs = v.template B<N0>();
+    for (int t = tid; t < N0 * N0; t += SQ_NT) {
+      const int i = t % N0, j = t / N0;
+      bs[(j + 2) * S + i + 2] = bg[(j + NG) * gsy + i + NG];
+    }
+  }
+  __syncthreads();
+  const T* res = v.template cycle<N0>();
+  {
+    constexpr int S = Sq<N0>::S;
+    T* __restrict__ xg = x + cb.gp.off;
+    const int gsy = (int)cb.gp.sy;
+    for (int t = tid; t < N0 * N0; t += SQ_NT) {
+      const int i = t % N0, j = t / N0;
+      xg[(j + NG) * gsy + i + NG] = res[(j + 2) * S + i + 2];
     }
   }
 }

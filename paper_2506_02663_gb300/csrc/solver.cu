@@ -849,6 +849,8 @@ amr_status blk_attrs() {
   CK(cudaFuncSetAttribute(k_mg_up2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_amr_post2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(cudaFuncSetAttribute(k_mg_coarse2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_coarse2d_sq<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_mg_coarse2d_sq<T, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done = true;
   return AMR_OK;
 }
@@ -894,9 +896,28 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
     cb.lv[q] = mg_view(h, m0 + q, op->bc);
     cb.ood[q] = p.omega / (op->alpha - 60.0 * op->beta * cb.lv[q].inv12h2);
   }
+  // square pyramids N0, N0/2, ... with N0 = 64 or 48 take the compile-time-size kernel
+  int sq = 0;
+  for (int n0 : {64, 48}) {
+    bool ok = true;
+    for (int q = 0; q < cb.ng && ok; ++q) {
+      const MgGrid& g = h->mg[m0 + q];
+      ok = g.n[0] == (n0 >> q) && g.n[1] == (n0 >> q);
+    }
+    const int nb = n0 == 64 ? sq_bottom<64, 64>() : sq_bottom<48, 48>();
+    const int ngr = 1 + (n0 == 64 ? sq_depth<64, sq_bottom<64, 64>()>() : sq_depth<48, sq_bottom<48, 48>()>());
+    if (ok && cb.ng == ngr && op->nbot == nb * nb) { sq = n0; break; }
+  }
   cudaEvent_t ev;
   prof_begin(st, &ev);
-  launch(k_mg_coarse2d<T>, 1, dim3(32, 32, 1), bytes, st, cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
+  if (sq == 64)
+    launch(k_mg_coarse2d_sq<T, 64>, 1, dim3(32, 32, 1), sizeof(T) * sq_total<64, 64>(), st, cb, b, x, T(op->alpha),
+           T(op->beta), T(p.omega));
+  else if (sq == 48)
+    launch(k_mg_coarse2d_sq<T, 48>, 1, dim3(32, 32, 1), sizeof(T) * sq_total<48, 48>(), st, cb, b, x, T(op->alpha),
+           T(op->beta), T(p.omega));
+  else
+    launch(k_mg_coarse2d<T>, 1, dim3(32, 32, 1), bytes, st, cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
   TRY(launch_check());
   prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * (double)h->mg[m0].n[0] * h->mg[m0].n[1]);  // read f, write x
   return AMR_OK;

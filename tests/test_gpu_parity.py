@@ -543,3 +543,46 @@ def test_3d_zchunk_two_level_vcycle_and_solve(bcw, ab, rows, tile_rows):
         fmax = max_abs(H, F)
         rmax = max(float(np.max(np.abs(r[l][lev.valid]))) for l, lev in enumerate(H.levels))
         assert rmax <= 1.5e-10 * fmax, (precision, rmax / fmax, st)
+
+
+SQUARE_CASES = {
+    # level-0 pyramid 64, 32, 16, 8, 4: the whole level-0 V-cycle in the one-block kernel
+    "single64": (2, (64, 64), [[((0, 0), (63, 63))]]),
+    # 96, then 48, 24, 12, 6 in the one-block kernel
+    "single96": (2, (96, 96), [[((0, 0), (95, 95))]]),
+    # two levels over a 64^2 base
+    "two_level64": (2, (64, 64), [[((0, 0), (63, 63))], [((32, 40), (87, 95))]]),
+}
+
+
+@pytest.mark.parametrize("name", list(SQUARE_CASES))
+@pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
+def test_square_coarse_block_solves(name, bcw, ab):
+    """Square level-0 pyramids run the compile-time-size one-block coarse V-cycle (ghost values
+    evaluated where the stencil reads them): mixed-precision solves reach the oracle's direct
+    solution to 1e-10 and take the same number of V-cycles (+-1) as the per-sweep kernels."""
+    amr = _amr()
+    dim, n0, boxes = SQUARE_CASES[name]
+    bc = [bcw] * (2 * dim)
+    alpha, beta = ab
+    H = OH(dim, n0, boxes, bc=bc, hi=(1.0, 1.0))
+    gh = amr.Hierarchy(dim, n0, boxes, h0=1.0 / n0[0])
+    rng = np.random.default_rng(73)
+    F = _rand_field(H, rng)
+    Fc = F
+    if so.is_pure_neumann(H, alpha):
+        Fc, _ = so.solvability_fix(H, F)
+    ref, _, _ = so.solve_direct(H, Fc, alpha, beta)
+    if so.is_pure_neumann(H, alpha):
+        ref, _ = so.mean_zero(H, ref)
+    op = amr.Operator(gh, alpha, beta, bc)
+    f = _dev(to_packed(gh, H, F))
+    counts = []
+    for blk in (1, 0):
+        x = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve(x, f, params=amr.default_params(rtol=1e-12, max_vcycles=200, precision=amr.MIXED,
+                                                      temporal_blocking=blk))
+        got = from_packed(gh, H, x.cpu().numpy())
+        assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref), (blk, st)
+        counts.append(st["vcycles"])
+    assert abs(counts[0] - counts[1]) <= 1, counts
