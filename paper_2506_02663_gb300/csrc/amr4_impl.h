@@ -38,8 +38,8 @@ struct LevelView {
   double ncells;             // interior cells over all patches (host bookkeeping)
   // per-level constants precomputed on the host, in both precisions, so that FP32 kernels
   // execute no FP64 instruction per cell
-  double hd, inv12h2, inv12h;
-  float hf, inv12h2_f, inv12h_f;
+  double hd, inv12h2, inv12h, invh;
+  float hf, inv12h2_f, inv12h_f, invh_f;
   double dcorr[6][2];        // Jacobi diagonal correction (x 12 h^2) at distance 0 / 1 from face f
   float dcorr_f[6][2];
 };

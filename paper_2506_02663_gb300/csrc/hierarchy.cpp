@@ -619,6 +619,8 @@ void finish_view(LevelView& v) {
   v.inv12h = 1.0 / (12.0 * v.h);
   v.inv12h2_f = (float)v.inv12h2;
   v.inv12h_f = (float)v.inv12h;
+  v.invh = 1.0 / v.h;
+  v.invh_f = (float)v.invh;
   for (int f = 0; f < 6; ++f) {
     const int t = v.bc[f] == 1 ? 1 : 0;
     // the cell owning the face reads ghost 1 with weight 16 and ghost 2 with weight -1; the

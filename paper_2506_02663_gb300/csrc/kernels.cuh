@@ -1233,12 +1233,69 @@ __device__ __forceinline__ T lap_smem(const T* __restrict__ a, int o, int sy) {
   return (T(16) * s1 - s2 - T(60) * xc) + T(0);
 }
 
-// nu weighted-Jacobi sweeps on the region; returns the buffer holding the result
-template <typename T, bool ZERO>
+// f(i, j) for every cell of a w x h box of a block (32 x 8 threads).  RM = 0: rows of 32
+// threads stride over the box; RM > 0 (w, h <= RM, a compile-time bound): one linear pass
+// over RM x RM positions with a fixed trip count, positions outside the box skipped.
+template <int RM, typename F>
+__device__ __forceinline__ void for_cells(int w, int h, F&& f) {
+  if constexpr (RM == 0) {
+    for (int j = (int)threadIdx.y; j < h; j += (int)blockDim.y)
+      for (int i = (int)threadIdx.x; i < w; i += (int)blockDim.x) f(i, j);
+  } else {
+    constexpr int NC = RM * RM, IT = (NC + 255) / 256;
+    const int tid = (int)(threadIdx.x + 32 * threadIdx.y);
+#pragma unroll 2
+    for (int k = 0; k < IT; ++k) {
+      const int c = tid + 256 * k;
+      if (NC % 256 == 0 || c < NC) {
+        const int i = c % RM, j = c / RM;
+        if (i < w && j < h) f(i, j);
+      }
+    }
+  }
+}
+
+// nu weighted-Jacobi sweeps on the region; returns the buffer holding the result.  RM > 0:
+// the region is at most RM x RM (a compile-time bound, shared-memory pitch sy = RM + 4), cell
+// loops have fixed trip counts, and blocks whose region touches no domain face skip the
+// ghost pass and its barrier.
+template <typename T, bool ZERO, int RM = 0>
 __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, const JacobiTable& jt, int sy,
                                             T* cur, T* oth, const T* __restrict__ sb, int nu, T alpha, T beta,
                                             const Team& tm) {
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
+  if constexpr (RM > 0) {
+    constexpr int SY = RM + 2 * NG;
+    const bool face = tg.fl0 | tg.fh0 | tg.fl1 | tg.fh1;
+    for (int s = 1; s <= nu; ++s) {
+      int a0, b0, a1, b1;
+      sweep_box(tg, s, a0, b0, a1, b1);
+      const bool zero = ZERO && s == 1;
+      if (!zero && face) {
+        int c0, d0, c1, d1;
+        sweep_box(tg, s - 1, c0, d0, c1, d1);
+        region_ghosts(lv, tg, cur, SY, c0, d0, c1, d1, tm);
+        __syncthreads();
+      }
+      for_cells<RM>(b0, b1, [&](int i, int j) {
+        if (i < a0 || j < a1) return;
+        const int o = (j + NG) * SY + (i + NG);
+        const T w = jt_get<T>(jt, jt.kx[i] + 5 * jt.ky[j]);
+        if (zero) {
+          oth[o] = w * sb[o];
+        } else {
+          const T xc = cur[o];
+          const T ax = alpha * xc + beta * (lap_smem(cur, o, SY) * inv);
+          oth[o] = xc + w * (sb[o] - ax);
+        }
+      });
+      __syncthreads();
+      T* sw = cur;
+      cur = oth;
+      oth = sw;
+    }
+    return cur;
+  }
   for (int s = 1; s <= nu; ++s) {
     int a0, b0, a1, b1;
     sweep_box(tg, s, a0, b0, a1, b1);
@@ -1276,7 +1333,7 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
 // ghosts): nu weighted-Jacobi sweeps from zero, the smoothed x written to xo (and added to
 // xo2 when given), and the residual f - A x restricted (2x2 average) into the coarse
 // right-hand side bcn over the covered coarse cells.  halo = 2 nu + 2.
-template <typename T>
+template <typename T, int RM = 0, int TILE = 0>
 __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
                                                    int nu, const T* __restrict__ b, T* __restrict__ xo,
                                                    T* __restrict__ xo2, T* __restrict__ bcn, T alpha, T beta, T omega,
@@ -1284,8 +1341,10 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
-  const int sy = tg.rw + 2 * NG;
-  const int E = sy * (tg.rh + 2 * NG);
+  const int sy = RM > 0 ? RM + 2 * NG : tg.rw + 2 * NG;
+  const int E = sy * (RM > 0 ? RM + 2 * NG : tg.rh + 2 * NG);
+  constexpr int TM = TILE;      // bound of the tile loops (0: runtime loops)
+  constexpr int CM = TILE / 2;  // bound of the coarse-cell loops
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
@@ -1294,43 +1353,41 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   const T* __restrict__ bg = b + gp.off;
   const int gsy = (int)gp.sy;
-  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
-      sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
+  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
   __syncthreads();
-  T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  T* cur = smooth_region<T, true, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
   T* __restrict__ xg2 = xo2 != nullptr ? xo2 + gp.off : nullptr;
-  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x) {
-      const T v = cur[(tj + j + NG) * sy + ti + i + NG];
-      xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = v;
-      if (xg2 != nullptr) xg2[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] += v;
-    }
+  for_cells<TM>(tg.tw, tg.th, [&](int i, int j) {
+    const T v = cur[(tj + j + NG) * sy + ti + i + NG];
+    xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = v;
+    if (xg2 != nullptr) xg2[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] += v;
+  });
   // residual of the tile's cells (ghosts of the final iterate first), restricted
   int c0, d0, c1, d1;
   sweep_box(tg, nu, c0, d0, c1, d1);
-  region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1, tm);
-  __syncthreads();
+  if (RM == 0 || (tg.fl0 | tg.fh0 | tg.fl1 | tg.fh1)) {
+    region_ghosts(lv, tg, cur, sy, c0, d0, c1, d1, tm);
+    __syncthreads();
+  }
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   const int cw = tg.tw / 2, ch = tg.th / 2;
   const int csy = (int)gcp.sy;
   T* __restrict__ cg = bcn + gcp.off;
-  for (int cj = (int)threadIdx.y; cj < ch; cj += (int)blockDim.y)
-    for (int ci = (int)threadIdx.x; ci < cw; ci += (int)blockDim.x) {
-      T acc = T(0);
+  for_cells<CM>(cw, ch, [&](int ci, int cj) {
+    T acc = T(0);
 #pragma unroll
-      for (int q1 = 0; q1 < 2; ++q1)
+    for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
-        for (int q0 = 0; q0 < 2; ++q0) {
-          const int o = (tj + 2 * cj + q1 + NG) * sy + (ti + 2 * ci + q0 + NG);
-          const T xc = cur[o];
-          acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
-        }
-      cg[(((gp.lo[1] + tg.j0) >> 1) - gcp.lo[1] + cj + NG) * csy + ((gp.lo[0] + tg.i0) >> 1) - gcp.lo[0] + ci + NG] =
-          acc * T(0.25);
-    }
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const int o = (tj + 2 * cj + q1 + NG) * sy + (ti + 2 * ci + q0 + NG);
+        const T xc = cur[o];
+        acc += sb[o] - (alpha * xc + beta * (lap_smem(cur, o, sy) * inv));
+      }
+    cg[(((gp.lo[1] + tg.j0) >> 1) - gcp.lo[1] + cj + NG) * csy + ((gp.lo[0] + tg.i0) >> 1) - gcp.lo[0] + ci + NG] =
+        acc * T(0.25);
+  });
 }
 
 // Coarse value at (c0, c1) of a single-patch 2-D grid, at most one cell outside the domain
@@ -1376,7 +1433,7 @@ __device__ __forceinline__ T coarse_ext2d(const T* __restrict__ cg, int csy, con
 // (coarse values outside the domain from the homogeneous extension with corners), then nu
 // weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
 // halo = 2 nu.
-template <typename T>
+template <typename T, int RM = 0, int TILE = 0>
 __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
                                                  int ty, int halo, int nu, const T* __restrict__ xc,
                                                  const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
@@ -1384,8 +1441,8 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
-  const int sy = tg.rw + 2 * NG;
-  const int E = sy * (tg.rh + 2 * NG);
+  const int sy = RM > 0 ? RM + 2 * NG : tg.rw + 2 * NG;
+  const int E = sy * (RM > 0 ? RM + 2 * NG : tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
@@ -1394,8 +1451,7 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
   const T* __restrict__ xg = xi + gp.off;
   const T* __restrict__ cg = xc + gcp.off;
   __shared__ JacobiTable jt;
-  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x) {
+  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) {
       const int og = (tg.r1 + j + NG) * gsy + tg.r0 + i + NG;
       const int os = (j + NG) * sy + i + NG;
       sb[os] = bg[og];
@@ -1421,16 +1477,16 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
       v += (T(0.75) * T(0.25)) * c01;
       v += (T(0.25) * T(0.25)) * c11;
       sx[os] = xg[og] + v;
-    }
+  });
   const Team tm = block_team();
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   __syncthreads();
-  const T* cur = smooth_region<T, false>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  const T* cur = smooth_region<T, false, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xw = xo + gp.off;
-  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x)
-      xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
+  for_cells<TILE>(tg.tw, tg.th, [&](int i, int j) {
+    xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
+  });
 }
 
 // Post-smoothing of a single-box AMR level (the correction form's up step): nu weighted-
@@ -1438,15 +1494,15 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
 // correction), zero CF ghosts and physical ghosts by formula, and the result t added to the
 // level's correction e and to the accumulated correction x on the tile.  Only the tile's
 // own e and x cells are read and written (no halo reads of them).  halo = 2 nu.
-template <typename T>
+template <typename T, int RM = 0, int TILE = 0>
 __global__ void __launch_bounds__(256) k_amr_post2d(LevelView lv, PatchDesc gp, int tx, int ty, int halo, int nu,
                                                     const T* __restrict__ r, T* __restrict__ e, T* __restrict__ x,
                                                     T alpha, T beta, T omega, T ood) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
-  const int sy = tg.rw + 2 * NG;
-  const int E = sy * (tg.rh + 2 * NG);
+  const int sy = RM > 0 ? RM + 2 * NG : tg.rw + 2 * NG;
+  const int E = sy * (RM > 0 ? RM + 2 * NG : tg.rh + 2 * NG);
   T* sx = reinterpret_cast<T*>(smraw);
   T* st = sx + E;
   T* sb = st + E;
@@ -1455,21 +1511,18 @@ __global__ void __launch_bounds__(256) k_amr_post2d(LevelView lv, PatchDesc gp, 
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   const T* __restrict__ rg = r + gp.off;
   const int gsy = (int)gp.sy;
-  for (int j = (int)threadIdx.y; j < tg.rh; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.rw; i += (int)blockDim.x)
-      sb[(j + NG) * sy + i + NG] = rg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG];
+  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = rg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
   __syncthreads();
-  const T* cur = smooth_region<T, true>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  const T* cur = smooth_region<T, true, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ eg = e + gp.off;
   T* __restrict__ xg = x + gp.off;
-  for (int j = (int)threadIdx.y; j < tg.th; j += (int)blockDim.y)
-    for (int i = (int)threadIdx.x; i < tg.tw; i += (int)blockDim.x) {
-      const T v = cur[(tj + j + NG) * sy + ti + i + NG];
-      const int og = (tg.j0 + j + NG) * gsy + tg.i0 + i + NG;
-      eg[og] += v;
-      xg[og] += v;
-    }
+  for_cells<TILE>(tg.tw, tg.th, [&](int i, int j) {
+    const T v = cur[(tj + j + NG) * sy + ti + i + NG];
+    const int og = (tg.j0 + j + NG) * gsy + tg.i0 + i + NG;
+    eg[og] += v;
+    xg[og] += v;
+  });
 }
 
 // Coarse end of the 2-D level-0 multigrid in one block: every grid from m0 (at most 64 cells

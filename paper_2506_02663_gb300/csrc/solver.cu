@@ -542,22 +542,26 @@ amr_status convert(const LevelView& lv, const S* x, T* y, cudaStream_t st) {
 // reflux kernel with by-value pointer triples (defined outside the anonymous namespace
 // declaration above so that it can be instantiated)
 namespace {
-template <typename T, int D>
-__global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
-                            P3<T> xcs, P3<T> xfs, P3<T> bcs, T* __restrict__ out, T coef, int kind) {
-  pdl_wait();
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const RefluxEntry e = list[t];
+// Refluxing (COH-3) of one coarse cell: its flux through every coarse-fine face replaced by
+// the mean of the fine fluxes.  KIND 0: the derivative flux of L (1/12, -15/12, 15/12, -1/12
+// divided by h); KIND 1: the face value of D (-1/12, 7/12, 7/12, -1/12).  Reciprocals of h
+// instead of divisions: FP64 division is slow on this part.
+template <typename T, int D, int KIND>
+__device__ __forceinline__ void reflux_cell(const LevelView& crs, const LevelView& fine, const RefluxEntry& e,
+                                            const P3<T>& xcs, const P3<T>& xfs, const P3<T>& bcs, T* __restrict__ out,
+                                            T coef) {
+  constexpr double FC[2][4] = {{1.0 / 12.0, -15.0 / 12.0, 15.0 / 12.0, -1.0 / 12.0},
+                               {-1.0 / 12.0, 7.0 / 12.0, 7.0 / 12.0, -1.0 / 12.0}};
   const PatchDesc cp = crs.patches[e.cpatch];
-  const T fd[4] = {T(1.0 / 12.0), T(-15.0 / 12.0), T(15.0 / 12.0), T(-1.0 / 12.0)};
-  const T fv[4] = {T(-1.0 / 12.0), T(7.0 / 12.0), T(7.0 / 12.0), T(-1.0 / 12.0)};
-  const T* fc = kind == 0 ? fd : fv;
+  const T ihc = KIND == 0 ? pick<T>(crs.invh, crs.invh_f) : T(1);
+  const T ihf = KIND == 0 ? pick<T>(fine.invh, fine.invh_f) : T(1);
   T corr = T(0);
+#pragma unroll
   for (int d = 0; d < D; ++d)
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
       if (!(e.faces & (1 << (2 * d + side)))) continue;
-      const int comp = kind == 0 ? 0 : d;
+      const int comp = KIND == 0 ? 0 : d;
       const T* xc = xcs.p[comp];
       const T* xf = xfs.p[comp];
       int own[3] = {e.g[0] - cp.lo[0], e.g[1] - cp.lo[1], e.g[2] - cp.lo[2]};
@@ -567,32 +571,43 @@ __global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __
       for (int q = 0; q < 4; ++q) {
         int cc[3] = {own[0], own[1], own[2]};
         cc[d] += q - 1;
-        Fc += fc[q] * read_nb<T, D>(xc, cp, crs, bcs.p[comp], cc[0], cc[1], cc[2], d);
+        Fc += T(FC[KIND][q]) * read_nb<T, D>(xc, cp, crs, bcs.p[comp], cc[0], cc[1], cc[2], d);
       }
       const PatchDesc fp = fine.patches[e.fpatch[2 * d + side]];
       T Fs = T(0);
-      const int e1 = (d == 0) ? 1 : 0;
-      const int e2 = (d == 2) ? 1 : 2;
+      const int t1d = (d == 0) ? 1 : 0;
+      const int t2d = (d == 2) ? 1 : 2;
+#pragma unroll
       for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
+#pragma unroll
         for (int t1 = 0; t1 < 2; ++t1) {
           int gf[3] = {0, 0, 0};
           gf[d] = side == 1 ? 2 * (e.g[d] + 1) - 1 : 2 * e.g[d] - 1;
-          gf[e1] = 2 * e.g[e1] + t1;
-          if (D == 3) gf[e2] = 2 * e.g[e2] + t2;
+          gf[t1d] = 2 * e.g[t1d] + t1;
+          if (D == 3) gf[t2d] = 2 * e.g[t2d] + t2;
           const int cf[3] = {gf[0] - fp.lo[0], gf[1] - fp.lo[1], gf[2] - fp.lo[2]};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             int cc[3] = {cf[0], cf[1], cf[2]};
             cc[d] += q - 1;
-            Fs += fc[q] * xf[poff(fp, cc[0], cc[1], cc[2])];
+            Fs += T(FC[KIND][q]) * xf[poff(fp, cc[0], cc[1], cc[2])];
           }
         }
       const T Fbar = Fs * T(D == 3 ? 0.25 : 0.5);
-      const T hc = kind == 0 ? pick<T>(crs.hd, crs.hf) : T(1);
-      const T hf = kind == 0 ? pick<T>(fine.hd, fine.hf) : T(1);
-      corr += T(side == 1 ? 1 : -1) * (Fbar / hf - Fc / hc);
+      corr += T(side == 1 ? 1 : -1) * (Fbar * ihf - Fc * ihc);
     }
-  out[e.coff] += coef * corr / pick<T>(crs.hd, crs.hf);
+  out[e.coff] += coef * corr * pick<T>(crs.invh, crs.invh_f);
+}
+
+template <typename T, int D>
+__global__ void k_reflux_p3(LevelView crs, LevelView fine, const RefluxEntry* __restrict__ list, long long n,
+                            P3<T> xcs, P3<T> xfs, P3<T> bcs, T* __restrict__ out, T coef, int kind) {
+  pdl_wait();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const RefluxEntry e = list[t];
+  if (kind == 0) reflux_cell<T, D, 0>(crs, fine, e, xcs, xfs, bcs, out, coef);
+  else reflux_cell<T, D, 1>(crs, fine, e, xcs, xfs, bcs, out, coef);
 }
 
 // ---------------------------------------------------------------- scratch management
@@ -840,6 +855,37 @@ size_t blk_smem(const int* n, int halo) {
   return (size_t)(3 * w * hh) * sizeof(T);
 }
 
+// Blocked legs with compile-time region bounds (nu <= 4, tiles of 16 or 32): the down leg's
+// region is the tile plus 2 nu + 2 cells per side, the up leg's and the post-smoothing's the
+// tile plus 2 nu; other shapes take the runtime-bounded kernels.
+constexpr int BLK_FX_NU = 4;
+template <typename T, typename... A>
+void launch_down2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_down2d<T, 16 + 4 * BLK_FX_NU + 4, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  else if (nu <= BLK_FX_NU && tt == 32) launch(k_mg_down2d<T, 32 + 4 * BLK_FX_NU + 4, 32>, grid, dim3(32, 8, 1), smem, st, a...);
+  else launch(k_mg_down2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
+}
+template <typename T, typename... A>
+void launch_up2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_up2d<T, 16 + 4 * BLK_FX_NU, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  else if (nu <= BLK_FX_NU && tt == 32) launch(k_mg_up2d<T, 32 + 4 * BLK_FX_NU, 32>, grid, dim3(32, 8, 1), smem, st, a...);
+  else launch(k_mg_up2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
+}
+template <typename T, typename... A>
+void launch_post2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_amr_post2d<T, 16 + 4 * BLK_FX_NU, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  else if (nu <= BLK_FX_NU && tt == 32) launch(k_amr_post2d<T, 32 + 4 * BLK_FX_NU, 32>, grid, dim3(32, 8, 1), smem, st, a...);
+  else launch(k_amr_post2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
+}
+// shared memory of a blocked launch: the compile-time region bound when that kernel runs
+template <typename T>
+size_t blk_smem_fx(const int* n, int nu, bool down) {
+  const int tt = blk_tile(n);
+  if (nu > BLK_FX_NU) return blk_smem<T>(n, down ? 2 * nu + 2 : 2 * nu);
+  const int rm = tt + (down ? 4 * BLK_FX_NU + 4 : 4 * BLK_FX_NU) + 2 * NG;
+  return (size_t)3 * rm * rm * sizeof(T);
+}
+
 template <typename T>
 amr_status blk_attrs() {
   static bool done = false;
@@ -960,15 +1006,15 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     const double cells = (double)g.n[0] * g.n[1];
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    launch(k_mg_down2d<T>, grid, blk, blk_smem<T>(g.n, hd), st, lv, g.patch, gc.patch, tt, tt, hd, p.nu1, b, t, (T*)nullptr,
-           S.mb[m + 1],
-                                                         T(op->alpha), T(op->beta), T(p.omega), ood);
+    (void)blk;
+    launch_down2d<T>(tt, p.nu1, grid, blk_smem_fx<T>(g.n, p.nu1, true), st, lv, g.patch, gc.patch, tt, tt, hd, p.nu1, b, t,
+                     (T*)nullptr, S.mb[m + 1], T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_DOWN, (2.0 + 0.25) * sizeof(T) * cells);  // read f, write x, write coarse f
     TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
     prof_begin(st, &ev);
-    launch(k_mg_up2d<T>, grid, blk, blk_smem<T>(g.n, hu), st, lv, cv, g.patch, gc.patch, tt, tt, hu, p.nu2, S.mx[m + 1], b, t,
-                                                       x, T(op->alpha), T(op->beta), T(p.omega), ood);
+    launch_up2d<T>(tt, p.nu2, grid, blk_smem_fx<T>(g.n, p.nu2, false), st, lv, cv, g.patch, gc.patch, tt, tt, hu, p.nu2,
+                   (const T*)S.mx[m + 1], (const T*)b, (const T*)t, x, T(op->alpha), T(op->beta), T(p.omega), ood);
     TRY(launch_check());
     prof_end(st, ev, PC_UP, (3.0 + 0.25) * sizeof(T) * cells);  // read x, f, coarse x; write x
     return AMR_OK;
@@ -1242,8 +1288,8 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
       dim3 grid((fp.n[0] + tt - 1) / tt, (fp.n[1] + tt - 1) / tt, 1);
       cudaEvent_t ev;
       prof_begin(st, &ev);
-      launch(k_mg_down2d<T>, grid, dim3(32, 8, 1), blk_smem<T>(fp.n, hd), st, lv[l], fp, cpd, tt, tt, hd, p.nu1,
-             (const T*)S.R, S.E, S.X, S.R, T(a_), T(b_), T(p.omega), ood);
+      launch_down2d<T>(tt, p.nu1, grid, blk_smem_fx<T>(fp.n, p.nu1, true), st, lv[l], fp, cpd, tt, tt, hd, p.nu1,
+                       (const T*)S.R, S.E, S.X, S.R, T(a_), T(b_), T(p.omega), ood);
       TRY(launch_check());
       prof_end(st, ev, PC_DOWN, (3.0 + 0.25) * sizeof(T) * (double)fp.n[0] * fp.n[1]);  // f in; e, x, coarse f out
     } else {
@@ -1286,8 +1332,8 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
       dim3 grid((fp.n[0] + tt - 1) / tt, (fp.n[1] + tt - 1) / tt, 1);
       cudaEvent_t ev;
       prof_begin(st, &ev);
-      launch(k_amr_post2d<T>, grid, dim3(32, 8, 1), blk_smem<T>(fp.n, hu), st, lv[l], fp, tt, tt, hu, p.nu2,
-             (const T*)S.R, S.E, S.X, T(a_), T(b_), T(p.omega), ood);
+      launch_post2d<T>(tt, p.nu2, grid, blk_smem_fx<T>(fp.n, p.nu2, false), st, lv[l], fp, tt, tt, hu, p.nu2,
+                       (const T*)S.R, S.E, S.X, T(a_), T(b_), T(p.omega), ood);
       TRY(launch_check());
       prof_end(st, ev, PC_UP, 5.0 * sizeof(T) * (double)fp.n[0] * fp.n[1]);  // r in; e, x read and written
     } else {

@@ -586,3 +586,35 @@ def test_square_coarse_block_solves(name, bcw, ab):
         assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref), (blk, st)
         counts.append(st["vcycles"])
     assert abs(counts[0] - counts[1]) <= 1, counts
+
+
+@pytest.mark.parametrize("bcw,ab", [(0, (1.0, -1e-4)), (1, (0.0, 1.0))])
+def test_blocked_legs_large_tiles(bcw, ab):
+    """A 1024^2 single level takes the blocked legs with 32^2 tiles: mixed-precision solves
+    with and without temporal blocking take the same V-cycles (+-1) and agree to 1e-9, and
+    the oracle's residual of the blocked solution meets the tolerance."""
+    amr = _amr()
+    n = 1024
+    box = [[((0, 0), (n - 1, n - 1))]]
+    bc = [bcw] * 4
+    alpha, beta = ab
+    H = OH(2, (n, n), box, bc=bc, hi=(1.0, 1.0))
+    gh = amr.Hierarchy(2, (n, n), box, h0=1.0 / n)
+    rng = np.random.default_rng(79)
+    F = _rand_field(H, rng)
+    if so.is_pure_neumann(H, alpha):
+        F, _ = so.solvability_fix(H, F)
+    op = amr.Operator(gh, alpha, beta, bc)
+    f = _dev(to_packed(gh, H, F))
+    sols, counts = [], []
+    for blk in (1, 0):
+        x = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve(x, f, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=amr.MIXED,
+                                                      temporal_blocking=blk))
+        sols.append(from_packed(gh, H, x.cpu().numpy()))
+        counts.append(st["vcycles"])
+    assert abs(counts[0] - counts[1]) <= 1, counts
+    assert max_diff(H, sols[0], sols[1]) <= 1e-9 * max_abs(H, sols[1])
+    r = cp.residual(H, sols[0], F, alpha, beta)
+    rmax = float(np.max(np.abs(r[0][H.levels[0].valid])))
+    assert rmax <= 1.5e-10 * max_abs(H, F), rmax / max_abs(H, F)
