@@ -1004,6 +1004,93 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
   cell_prolong<T, D>(crs, fine.patches[b.fpatch], crs.patches[b.cpatch], gf, xc, xf, xf2);
 }
 
+// 3-D prolongation, one thread per fine cell: += trilinear interpolation of its 2x2x2 coarse
+// stencil, read with 32-bit offsets (cells outside the coarse patch are its stored ghost
+// layers).  In the outermost fine layer, where the stencil leaves the domain, the homogeneous
+// extension enters through per-dimension weights (no per-cell ghost evaluation), so boundary
+// lanes cost a few more loads instead of the generic path.  Interior: cell_prolong's order.
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong3d(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                                                      int nz, const T* __restrict__ xc, T* __restrict__ xf,
+                                                      T* __restrict__ xf2) {
+  pdl_wait();
+  const XferBlock b = blocks[blockIdx.z / nz];
+  const int gf[3] = {2 * b.clo[0] + (int)(blockIdx.x * BX + threadIdx.x), 2 * b.clo[1] + (int)(blockIdx.y * BY + threadIdx.y),
+                     2 * b.clo[2] + (int)(blockIdx.z % nz)};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || gf[2] > 2 * b.chi[2] + 1) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  int par[3], sg[3];
+  bool inside = true;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    par[e] = gf[e] >> 1;
+    sg[e] = (gf[e] & 1) ? 1 : -1;
+    inside = inside && par[e] + sg[e] >= 0 && par[e] + sg[e] < crs.ndom[e];
+  }
+  const T* __restrict__ cb = xc + cp.off;
+  const int csy = (int)cp.sy, csz = (int)cp.sz;
+  if (!inside) {
+    // tensor product of per-dimension weights: inside the domain the pair (parent 3/4, next
+    // 1/4); where the next coarse cell is outside, the homogeneous layer-1 extension folded
+    // into four inward points from the face (3/4 on the face cell + 1/4 of the ghost formula)
+    int ix[3][4];
+    T wx[3][4];
+    int nx[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int lo = e == 0 ? cp.lo[0] : (e == 1 ? cp.lo[1] : cp.lo[2]);
+      const int g2 = par[e] + sg[e];
+      if (g2 >= 0 && g2 < crs.ndom[e]) {
+        nx[e] = 2;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          ix[e][m] = par[e] - lo + (m == 1 ? sg[e] : 0);
+          wx[e][m] = m == 0 ? T(0.75) : (m == 1 ? T(0.25) : T(0));
+        }
+      } else {
+        nx[e] = 4;
+        const int side = g2 < 0 ? 0 : 1, type = crs.bc[2 * e + side];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          ix[e][m] = (side == 0 ? m : crs.ndom[e] - 1 - m) - lo;
+          wx[e][m] = T(0.25) * gcoef<T>(type, 0, m) + (m == 0 ? T(0.75) : T(0));
+        }
+      }
+    }
+    T v = T(0);
+#pragma unroll
+    for (int c2 = 0; c2 < 4; ++c2)
+#pragma unroll
+      for (int c1 = 0; c1 < 4; ++c1)
+#pragma unroll
+        for (int c0 = 0; c0 < 4; ++c0)
+          if (c0 < nx[0] && c1 < nx[1] && c2 < nx[2])
+            v += (wx[0][c0] * wx[1][c1] * wx[2][c2]) *
+                 cb[(ix[2][c2] + NG) * csz + (ix[1][c1] + NG) * csy + (ix[0][c0] + NG)];
+    const int of = (gf[2] - fp.lo[2] + NG) * (int)fp.sz + (gf[1] - fp.lo[1] + NG) * (int)fp.sy + (gf[0] - fp.lo[0] + NG);
+    xf[fp.off + of] += v;
+    if (xf2 != nullptr) xf2[fp.off + of] += v;
+    return;
+  }
+  const int oc = (par[2] - cp.lo[2] + NG) * csz + (par[1] - cp.lo[1] + NG) * csy + (par[0] - cp.lo[0] + NG);
+  const int d0 = sg[0], d1 = sg[1] * csy, d2 = sg[2] * csz;
+  T v = T(0);
+#pragma unroll
+  for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+      for (int q0 = 0; q0 < 2; ++q0) {
+        const T w = ((T(1) * (q0 == 0 ? T(0.75) : T(0.25))) * (q1 == 0 ? T(0.75) : T(0.25))) *
+                    (q2 == 0 ? T(0.75) : T(0.25));
+        v += w * cb[oc + q2 * d2 + q1 * d1 + q0 * d0];
+      }
+  const int of = (gf[2] - fp.lo[2] + NG) * (int)fp.sz + (gf[1] - fp.lo[1] + NG) * (int)fp.sy + (gf[0] - fp.lo[0] + NG);
+  xf[fp.off + of] += v;
+  if (xf2 != nullptr) xf2[fp.off + of] += v;
+}
+
 // 2-D prolongation, one thread per coarse cell: its four children += linear interpolation
 // from the 3x3 coarse neighbourhood (32-bit offsets) when the neighbourhood lies inside the
 // domain and the patch; generic per-fine-cell code otherwise (same arithmetic).

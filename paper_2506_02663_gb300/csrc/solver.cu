@@ -468,10 +468,18 @@ amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const Xfe
     dim3 grid((xmax[0] + BX - 1) / BX, (xmax[1] + BY - 1) / BY, nblocks);
     launch(k_prolong2d<T>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, xc, xf, xf2);
   } else {
-    const int fy = 2 * xmax[1];
-    const int nby = (fy + BY - 1) / BY;
-    dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
-    launch(k_prolong<T, D>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, xc, xf, xf2, nby);
+    // 32-bit offsets inside the padded patches (a 3-D patch beyond 2^31 elements takes the
+    // generic kernel)
+    const long long fel = (long long)(fine.maxn[0] + 2 * NG + 3) * (fine.maxn[1] + 2 * NG) * (fine.maxn[2] + 2 * NG);
+    if (fel < (1LL << 31) && 2LL * xmax[2] * nblocks <= 65535) {
+      dim3 grid((2 * xmax[0] + BX - 1) / BX, (2 * xmax[1] + BY - 1) / BY, 2 * xmax[2] * nblocks);
+      launch(k_prolong3d<T>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, 2 * xmax[2], xc, xf, xf2);
+    } else {
+      const int fy = 2 * xmax[1];
+      const int nby = (fy + BY - 1) / BY;
+      dim3 grid((2 * xmax[0] + BX - 1) / BX, nby * (D == 3 ? 2 * xmax[2] : 1), nblocks);
+      launch(k_prolong<T, D>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, xc, xf, xf2, nby);
+    }
   }
   const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
   prof_end(st, ev, PC_PROLONG, (1.0 + (1 << D) * (xf2 ? 4.0 : 2.0)) * sizeof(T) * cc);
@@ -684,14 +692,20 @@ template <typename T, int D>
 amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
   amr_hierarchy* h = op->h;
   Scratch<T>& S = scratch<T>(op);
-  std::vector<std::pair<LevelView, std::pair<T*, T*>>> cases;
-  for (int l = 0; l < h->L; ++l) cases.push_back({level_view(h, l, op->bc), {S.T1, S.T2}});
-  for (size_t m = 1; m < h->mg.size(); ++m) cases.push_back({mg_view(h, (int)m, op->bc), {S.mx[m], S.mt[m]}});
+  // (grid, x, f, out): three distinct buffers, so that the timed sweeps move the bytes a real
+  // sweep moves (a grid whose fields exceed L2 must not be timed from L2)
+  struct Case {
+    LevelView lv;
+    T *x, *f, *o;
+  };
+  std::vector<Case> cases;
+  for (int l = 0; l < h->L; ++l) cases.push_back({level_view(h, l, op->bc), S.T1, S.R, S.T2});
+  for (size_t m = 1; m < h->mg.size(); ++m) cases.push_back({mg_view(h, (int)m, op->bc), S.mx[m], S.mb[m], S.mt[m]});
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   for (auto& c : cases) {
-    const LevelView& lv = c.first;
+    const LevelView& lv = c.lv;
     if (D == 3 && !zc_eligible(lv, 4)) continue;  // only the 2-row 3-D variant applies
     const long long key = tile_key(lv, sizeof(T));
     {
@@ -711,8 +725,7 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
       for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
         CK(cudaEventRecord(a, st));
         for (int it = 0; it < 4; ++it)
-          TRY((level_op<T, D>(OP_JACOBI, lv, c.second.first, c.second.first, c.second.second, nullptr, op->alpha,
-                              op->beta, 2.0 / 3.0, nullptr, st)));
+          TRY((level_op<T, D>(OP_JACOBI, lv, c.x, c.f, c.o, nullptr, op->alpha, op->beta, 2.0 / 3.0, nullptr, st)));
         CK(cudaEventRecord(b, st));
       }
       CK(cudaEventSynchronize(b));
