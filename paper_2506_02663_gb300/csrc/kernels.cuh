@@ -622,32 +622,32 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
   int wxy[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) wxy[r] = kx + 5 * face_class(p.lo[1] + j0 + ty + r * ZC_TY, lv.ndom[1]);
-  // halo cell: stored value inside the domain (interior, CF or copy ghost); outside it the
-  // ghost formula along the face normal from the four cells next to the face, whose first
-  // column and step are fixed here (corners of the halo are never read)
+  // halo cell: stored value inside the domain (interior, CF or copy ghost).  Outside it (the
+  // tile then touches that domain face) the ghost formula along the face normal, evaluated in
+  // shared memory from the four staged cells next to the face, after the plane is staged;
+  // hsrc / hstep give the face cell's shared index and the inward step (corners of the halo
+  // are never read).
   const int hli = i0 + hx, hlj = j0 + hy;
-  int hcol = (hli + NG) + (hlj + NG) * sy, hstep = 0, htype = 0, hlayer = 0;
+  const int hcol = (hli + NG) + (hlj + NG) * sy;
+  int hsrc = 0, hstep = 0, htype = 0, hlayer = 0;
   {
     const int hgi = p.lo[0] + hli, hgj = p.lo[1] + hlj;
     const int d = (hgi < 0 || hgi >= lv.ndom[0]) ? 0 : ((hgj < 0 || hgj >= lv.ndom[1]) ? 1 : -1);
-    if (d >= 0) {
+    if (has_halo && d >= 0) {
       const int g = d == 0 ? hgi : hgj, n = lv.ndom[d], side = g < 0 ? 0 : 1;
       hlayer = (side == 0 ? -g : g - n + 1) - 1;
       htype = lv.bc[2 * d + side];
-      const int st = d == 0 ? 1 : sy;
-      const int first = (side == 0 ? 0 : n - 1) - p.lo[d] + NG;  // padded index of the face cell
-      hcol = d == 0 ? first + (hlj + NG) * sy : (hli + NG) + first * sy;
+      const int face = (side == 0 ? 0 : n - 1) - p.lo[d] - (d == 0 ? i0 : j0);  // tile-local
+      hsrc = d == 0 ? (hy + 2) * ZC_W + face + 2 : (face + 2) * ZC_W + hx + 2;
+      const int st = d == 0 ? 1 : ZC_W;
       hstep = side == 0 ? st : -st;
     }
   }
-  auto halo = [&](int k) -> T {
-    const int o = hcol + (k + NG) * sz;
-    if (hstep == 0) return xb[o];
-    T v = T(0);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) v += gcoef<T>(htype, hlayer, m) * xb[o + m * hstep];
-    return v;
-  };
+  const bool hload = has_halo && hstep == 0;
+  // blocks whose halo leaves the domain fill it after staging (block-uniform)
+  const bool face_tile = p.lo[0] + i0 == 0 || p.lo[0] + i0 + ZC_TX == lv.ndom[0] || p.lo[1] + j0 == 0 ||
+                         p.lo[1] + j0 + G::TH == lv.ndom[1];
+  auto halo = [&](int k) -> T { return hload ? xb[hcol + (k + NG) * sz] : T(0); };
   constexpr int RS = ZC_TY;  // row step of a thread's columns (rows)
   T q[R][5];                 // x of each column at planes k-2..k+2
   T xs[2][R], fs[2][R], hv[2];
@@ -685,8 +685,9 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
   }
   // one plane: stage, refill the consumed slots with plane k+2, barrier, compute, advance
   // the queues (q4 from the slot loaded two planes ago, then the slot reloaded)
-  auto step = [&](int k, auto slot) {
+  auto step = [&](int k, auto slot, auto safe) {
     constexpr int S = decltype(slot)::value;
+    constexpr bool SAFE = decltype(safe)::value;  // planes up to k+5 inside the domain
     T* __restrict__ s = sp[S];
     T fk[R];
 #pragma unroll
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
     if (MODE != OP_JACOBI0) {
 #pragma unroll
       for (int r = 0; r < R; ++r) s[c0 + r * RS * ZC_W] = q[r][2];
-      if (has_halo) {
+      if (hload) {
         s[hs] = hv[S];
         if (k + 2 < kb) hv[S] = halo(k + 2);
       }
@@ -703,7 +704,18 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
 #pragma unroll
       for (int r = 0; r < R; ++r) fs[S][r] = fb[col0 + r * RS * sy + (k + 2 + NG) * sz];
     }
-    if (MODE != OP_JACOBI0) __syncthreads();
+    if (MODE != OP_JACOBI0) {
+      __syncthreads();
+      if (face_tile) {
+        if (hstep != 0) {
+          T v = T(0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) v += gcoef<T>(htype, hlayer, m) * s[hsrc + m * hstep];
+          s[hs] = v;
+        }
+        __syncthreads();
+      }
+    }
     const int kz25 = 25 * face_class(lz + k, nzd);
     const int pk = col0 + (k + NG) * sz;
 #pragma unroll
@@ -733,13 +745,21 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
         q[r][2] = q[r][3];
         q[r][3] = q[r][4];
         q[r][4] = xs[S][r];
-        if (k + 3 < kb) xs[S][r] = zc_zval<T>(xb, col0 + r * RS * sy, sz, k + 5, lz, nzd, lv);  // q4 of plane k+3
+        if (k + 3 < kb) {  // q4 of plane k+3
+          if (SAFE) xs[S][r] = xb[col0 + r * RS * sy + (k + 5 + NG) * sz];
+          else xs[S][r] = zc_zval<T>(xb, col0 + r * RS * sy, sz, k + 5, lz, nzd, lv);
+        }
       }
     }
   };
   for (int k = ka; k < kb; k += 2) {
-    step(k, zc_slot<0>{});
-    if (k + 1 < kb) step(k + 1, zc_slot<1>{});
+    if (lz + k + 6 < nzd) {
+      step(k, zc_slot<0>{}, std::true_type{});
+      if (k + 1 < kb) step(k + 1, zc_slot<1>{}, std::true_type{});
+    } else {
+      step(k, zc_slot<0>{}, std::false_type{});
+      if (k + 1 < kb) step(k + 1, zc_slot<1>{}, std::false_type{});
+    }
   }
 }
 
