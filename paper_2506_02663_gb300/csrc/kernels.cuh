@@ -283,12 +283,11 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(LevelView lv, int nby, cons
 // diag precomputed); the others run the generic per-cell code.  Both paths sum the
 // stencil in the same order as cell_Lx.
 template <typename T, int MODE, bool TR, int ROWS>
-__global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const T* __restrict__ x,
-                                                             const T* __restrict__ f, T* __restrict__ out,
-                                                             const T* __restrict__ bc, T alpha, T beta, T omega,
-                                                             T omega_over_diag, const unsigned char* __restrict__ vmask) {
-  pdl_wait();
-  const PatchDesc p = lv.patches[blockIdx.z];
+__device__ __forceinline__ void level_op2d_tiled_body(const LevelView& lv, int pz, const T* __restrict__ x,
+                                                      const T* __restrict__ f, T* __restrict__ out,
+                                                      const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                      T omega_over_diag, const unsigned char* __restrict__ vmask) {
+  const PatchDesc p = lv.patches[pz];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j0 = (blockIdx.y * BY + threadIdx.y) * ROWS;
   // per thread: its column strip and the two-cell reach inside the patch and the domain
@@ -327,13 +326,35 @@ __global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const
     const T xc = col[r + 2];
     const T s1 = (xb[orr - 1] + xb[orr + 1]) + (col[r + 1] + col[r + 3]);
     const T s2 = (xb[orr - 2] + xb[orr + 2]) + (col[r] + col[r + 4]);
-    const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
-    const T ax = alpha * xc + beta * (lap * inv);
     const long long og = p.off + orr;
-    if (MODE == OP_APPLY) out[og] = ax;
-    else if (MODE == OP_RESID) out[og] = f[og] - ax;
-    else out[og] = xc + omega_over_diag * (f[og] - ax);
+    if constexpr (sizeof(T) == 8) {
+      // FP64: alpha x + beta L x = kc0 x + kc1 s1 - kc2 s2, three multiply-adds after the sums
+      // (FP64 arithmetic, not memory, bounds these passes on this part)
+      const T kc2 = beta * inv, kc1 = T(16) * kc2, kc0 = alpha - T(60) * kc2;
+      if (MODE == OP_APPLY) {
+        out[og] = kc0 * xc + (kc1 * s1 - kc2 * s2);
+      } else {
+        const T res = fma(kc2, s2, fma(-kc1, s1, fma(-kc0, xc, f[og])));
+        if (MODE == OP_RESID) out[og] = res;
+        else out[og] = fma(omega_over_diag, res, xc);
+      }
+    } else {
+      const T lap = (T(16) * s1 - s2 - T(60) * xc) + T(0);
+      const T ax = alpha * xc + beta * (lap * inv);
+      if (MODE == OP_APPLY) out[og] = ax;
+      else if (MODE == OP_RESID) out[og] = f[og] - ax;
+      else out[og] = xc + omega_over_diag * (f[og] - ax);
+    }
   }
+}
+
+template <typename T, int MODE, bool TR, int ROWS>
+__global__ void __launch_bounds__(BX* BY) k_level_op2d_tiled(LevelView lv, const T* __restrict__ x,
+                                                             const T* __restrict__ f, T* __restrict__ out,
+                                                             const T* __restrict__ bc, T alpha, T beta, T omega,
+                                                             T omega_over_diag, const unsigned char* __restrict__ vmask) {
+  pdl_wait();
+  level_op2d_tiled_body<T, MODE, TR, ROWS>(lv, blockIdx.z, x, f, out, bc, alpha, beta, omega, omega_over_diag, vmask);
 }
 
 // 3-D level operator, marching in z (homogeneous physical data, forward operator): a block
@@ -1441,11 +1462,9 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
 // xo2 when given), and the residual f - A x restricted (2x2 average) into the coarse
 // right-hand side bcn over the covered coarse cells.  halo = 2 nu + 2.
 template <typename T, int RM = 0, int TILE = 0>
-__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
-                                                   int nu, const T* __restrict__ b, T* __restrict__ xo,
-                                                   T* __restrict__ xo2, T* __restrict__ bcn, T alpha, T beta, T omega,
-                                                   T ood) {
-  pdl_wait();
+__device__ __forceinline__ void mg_down2d_body(const LevelView& lv, const PatchDesc& gp, const PatchDesc& gcp, int tx, int ty, int halo,
+                                               int nu, const T* __restrict__ b, T* __restrict__ xo, T* __restrict__ xo2,
+                                               T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
   const int sy = RM > 0 ? RM + 2 * NG : tg.rw + 2 * NG;
@@ -1497,6 +1516,15 @@ __global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, P
   });
 }
 
+template <typename T, int RM = 0, int TILE = 0>
+__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
+                                                   int nu, const T* __restrict__ b, T* __restrict__ xo,
+                                                   T* __restrict__ xo2, T* __restrict__ bcn, T alpha, T beta, T omega,
+                                                   T ood) {
+  pdl_wait();
+  mg_down2d_body<T, RM, TILE>(lv, gp, gcp, tx, ty, halo, nu, b, xo, xo2, bcn, alpha, beta, omega, ood);
+}
+
 // Coarse value at (c0, c1) of a single-patch 2-D grid, at most one cell outside the domain
 // in each dimension: the homogeneous physical extension (layer-1 ghost formula), applied
 // dimension after dimension at corners (Fig. 1(c) order, as read_ext does).
@@ -1541,11 +1569,10 @@ __device__ __forceinline__ T coarse_ext2d(const T* __restrict__ cg, int csy, con
 // weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
 // halo = 2 nu.
 template <typename T, int RM = 0, int TILE = 0>
-__global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
-                                                 int ty, int halo, int nu, const T* __restrict__ xc,
-                                                 const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
-                                                 T alpha, T beta, T omega, T ood) {
-  pdl_wait();
+__device__ __forceinline__ void mg_up2d_body(const LevelView& lv, const LevelView& cv, const PatchDesc& gp, const PatchDesc& gcp,
+                                             int tx, int ty, int halo, int nu, const T* __restrict__ xc,
+                                             const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
+                                             T alpha, T beta, T omega, T ood) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TileGeom tg = tile_geom(gp, lv, tx, ty, halo);
   const int sy = RM > 0 ? RM + 2 * NG : tg.rw + 2 * NG;
@@ -1594,6 +1621,15 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
   for_cells<TILE>(tg.tw, tg.th, [&](int i, int j) {
     xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
   });
+}
+
+template <typename T, int RM = 0, int TILE = 0>
+__global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+                                                 int ty, int halo, int nu, const T* __restrict__ xc,
+                                                 const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
+                                                 T alpha, T beta, T omega, T ood) {
+  pdl_wait();
+  mg_up2d_body<T, RM, TILE>(lv, cv, gp, gcp, tx, ty, halo, nu, xc, b, xi, xo, alpha, beta, omega, ood);
 }
 
 // Post-smoothing of a single-box AMR level (the correction form's up step): nu weighted-
@@ -2010,9 +2046,8 @@ struct SqVcycle {
 };
 
 template <typename T, int N0>
-__global__ void __launch_bounds__(SQ_NT) k_mg_coarse2d_sq(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
-                                                          T alpha, T beta, T omega) {
-  pdl_wait();
+__device__ __forceinline__ void mg_coarse2d_sq_body(const CoarseBlock2D& cb, const T* __restrict__ b, T* __restrict__ x,
+                                                    T alpha, T beta, T omega) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ float wt[25 * CB_MAX];
   __shared__ double bot[1024];
@@ -2064,6 +2099,166 @@ __global__ void __launch_bounds__(SQ_NT) k_mg_coarse2d_sq(CoarseBlock2D cb, cons
       xg[(j + NG) * gsy + i + NG] = res[(j + 2) * S + i + 2];
     }
   }
+}
+
+template <typename T, int N0>
+__global__ void __launch_bounds__(SQ_NT) k_mg_coarse2d_sq(CoarseBlock2D cb, const T* __restrict__ b, T* __restrict__ x,
+                                                          T alpha, T beta, T omega) {
+  pdl_wait();
+  mg_coarse2d_sq_body<T, N0>(cb, b, x, alpha, beta, omega);
+}
+
+// ------------------------------------------------------------------------ work-list batches
+// A batch of independent single-level 2-D problems solved together: every phase of the
+// mixed-precision iteration is one launch over a list of descriptors (problem, grid) in
+// device memory, blockIdx.z (or blockIdx.x) selecting the entry; entries of problems that
+// have converged (active[p] == 0) return at once.  The bodies are the single-problem
+// kernels' bodies.
+struct BDown {  // down leg of grid m of problem p
+  int p, tiles_x, tiles_y, tt, halo, nu;
+  LevelView lv;
+  PatchDesc gp, gcp;
+  const float* b;
+  float* xo;
+  float* bcn;
+  float alpha, beta, omega, ood;
+};
+struct BUp {  // up leg of grid m of problem p
+  int p, tiles_x, tiles_y, tt, halo, nu;
+  LevelView lv, cv;
+  PatchDesc gp, gcp;
+  const float* xc;
+  const float* b;
+  const float* xi;
+  float* xo;
+  float alpha, beta, omega, ood;
+};
+struct BCoarse {  // one-block coarse V-cycle of problem p (square pyramid from n0)
+  int p, n0;
+  CoarseBlock2D cb;
+  const float* b;
+  float* x;
+  float alpha, beta, omega;
+};
+struct BResid {  // FP64 residual of problem p's level: out = f - (alpha x + beta L x)
+  int p, tiles_x, tiles_y;
+  LevelView lv;
+  const double* x;
+  const double* f;
+  double* out;
+  double alpha, beta;
+};
+struct BFlat {  // whole-array passes of problem p
+  int p;
+  long long n;
+  const unsigned char* vmask;
+  double* phi;      // update: phi += e on valid cells
+  const float* e;
+  const double* r;  // norm: valid max-norm of r into acc[p], rin = (float) r
+  float* rin;
+  const double* f;  // init: F = f, phi = 0 (zero), fnorm
+  double* F;
+};
+
+template <int RM, int TILE>
+__global__ void __launch_bounds__(256) k_mg_down2d_b(const BDown* __restrict__ d, const int* __restrict__ active) {
+  pdl_wait();
+  const BDown& e = d[blockIdx.z];
+  if (!active[e.p] || (int)blockIdx.x >= e.tiles_x || (int)blockIdx.y >= e.tiles_y) return;
+  mg_down2d_body<float, RM, TILE>(e.lv, e.gp, e.gcp, e.tt, e.tt, e.halo, e.nu, e.b, e.xo, nullptr, e.bcn, e.alpha,
+                                  e.beta, e.omega, e.ood);
+}
+
+template <int RM, int TILE>
+__global__ void __launch_bounds__(256, 4) k_mg_up2d_b(const BUp* __restrict__ d, const int* __restrict__ active) {
+  pdl_wait();
+  const BUp& e = d[blockIdx.z];
+  if (!active[e.p] || (int)blockIdx.x >= e.tiles_x || (int)blockIdx.y >= e.tiles_y) return;
+  mg_up2d_body<float, RM, TILE>(e.lv, e.cv, e.gp, e.gcp, e.tt, e.tt, e.halo, e.nu, e.xc, e.b, e.xi, e.xo, e.alpha,
+                                e.beta, e.omega, e.ood);
+}
+
+__global__ void __launch_bounds__(SQ_NT) k_mg_coarse2d_sq_b(const BCoarse* __restrict__ d, const int* __restrict__ active) {
+  pdl_wait();
+  const BCoarse& e = d[blockIdx.x];
+  if (!active[e.p]) return;
+  if (e.n0 == 64) mg_coarse2d_sq_body<float, 64>(e.cb, e.b, e.x, e.alpha, e.beta, e.omega);
+  else mg_coarse2d_sq_body<float, 48>(e.cb, e.b, e.x, e.alpha, e.beta, e.omega);
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(BX* BY) k_resid2d_b(const BResid* __restrict__ d, const int* __restrict__ active) {
+  pdl_wait();
+  const BResid& e = d[blockIdx.z];
+  if (!active[e.p] || (int)blockIdx.x >= e.tiles_x || (int)blockIdx.y >= e.tiles_y) return;
+  level_op2d_tiled_body<double, OP_RESID, false, ROWS>(e.lv, 0, e.x, e.f, e.out, nullptr, e.alpha, e.beta, 0.0, 0.0,
+                                                       nullptr);
+}
+
+// block-wide max of IEEE bits (non-negative doubles) into *acc
+__device__ __forceinline__ void block_max_bits(unsigned long long v, unsigned long long* acc) {
+  __shared__ unsigned long long sm[8];
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+    v = u > v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < 8 ? sm[threadIdx.x] : 0ull;
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+      v = u > v ? u : v;
+    }
+    if (threadIdx.x == 0 && v != 0ull) atomicMax(acc, v);
+  }
+}
+
+// set-up of every problem: F = f, phi = 0 (zero != 0), valid max-norm of f into fbits[p]
+__global__ void __launch_bounds__(256) k_init_b(const BFlat* __restrict__ d, int zero, unsigned long long* __restrict__ fbits) {
+  pdl_wait();
+  const BFlat& e = d[blockIdx.y];
+  unsigned long long v = 0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = e.f[i];
+    e.F[i] = x;
+    if (zero) e.phi[i] = 0.0;
+    if (e.vmask[i]) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x));
+      v = b > v ? b : v;
+    }
+  }
+  block_max_bits(v, fbits + e.p);
+}
+
+// phi += e on the valid cells of every active problem; clears its residual-norm slot
+__global__ void __launch_bounds__(256) k_update_b(const BFlat* __restrict__ d, const int* __restrict__ active,
+                                                  unsigned long long* __restrict__ rbits) {
+  pdl_wait();
+  const BFlat& e = d[blockIdx.y];
+  if (!active[e.p]) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) rbits[e.p] = 0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += (long long)gridDim.x * blockDim.x)
+    if (e.vmask[i]) e.phi[i] += (double)e.e[i];
+}
+
+// valid max-norm of the residual into rbits[p] and its FP32 copy (the next V-cycle's
+// right-hand side) for every active problem
+__global__ void __launch_bounds__(256) k_norm_convert_b(const BFlat* __restrict__ d, const int* __restrict__ active,
+                                                        unsigned long long* __restrict__ rbits) {
+  pdl_wait();
+  const BFlat& e = d[blockIdx.y];
+  if (!active[e.p]) return;
+  unsigned long long v = 0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = e.r[i];
+    e.rin[i] = (float)x;
+    if (e.vmask[i]) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x));
+      v = b > v ? b : v;
+    }
+  }
+  block_max_bits(v, rbits + e.p);
 }
 
 // ------------------------------------------------------------------------ fused coarse V-cycle

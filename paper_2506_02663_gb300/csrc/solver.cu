@@ -933,10 +933,9 @@ inline int coarse_block_m0(const amr_hierarchy* h, size_t& bytes) {
   return m0 < M ? m0 : -1;
 }
 
-template <typename T, int D>
-amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, size_t bytes, const T* b, T* x,
-                        cudaStream_t st) {
-  amr_hierarchy* h = op->h;
+// descriptor of the one-block coarse V-cycle from grid m0 down
+inline CoarseBlock2D make_coarse_block(const amr_operator* op, const amr_solver_params& p, int m0) {
+  const amr_hierarchy* h = op->h;
   const int M = (int)h->mg.size() - 1;
   CoarseBlock2D cb{};
   cb.ng = M - m0 + 1;
@@ -956,18 +955,32 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
     cb.lv[q] = mg_view(h, m0 + q, op->bc);
     cb.ood[q] = p.omega / (op->alpha - 60.0 * op->beta * cb.lv[q].inv12h2);
   }
-  // square pyramids N0, N0/2, ... with N0 = 64 or 48 take the compile-time-size kernel
-  int sq = 0;
+  return cb;
+}
+
+// 64 or 48 when the pyramid from m0 is square N0, N0/2, ... down to the compile-time-size
+// kernel's bottom grid, else 0
+inline int square_pyramid(const amr_operator* op, int m0, int ng) {
+  const amr_hierarchy* h = op->h;
   for (int n0 : {64, 48}) {
     bool ok = true;
-    for (int q = 0; q < cb.ng && ok; ++q) {
+    for (int q = 0; q < ng && ok; ++q) {
       const MgGrid& g = h->mg[m0 + q];
       ok = g.n[0] == (n0 >> q) && g.n[1] == (n0 >> q);
     }
     const int nb = n0 == 64 ? sq_bottom<64, 64>() : sq_bottom<48, 48>();
     const int ngr = 1 + (n0 == 64 ? sq_depth<64, sq_bottom<64, 64>()>() : sq_depth<48, sq_bottom<48, 48>()>());
-    if (ok && cb.ng == ngr && op->nbot == nb * nb) { sq = n0; break; }
+    if (ok && ng == ngr && op->nbot == nb * nb) return n0;
   }
+  return 0;
+}
+
+template <typename T, int D>
+amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, size_t bytes, const T* b, T* x,
+                        cudaStream_t st) {
+  const CoarseBlock2D cb = make_coarse_block(op, p, m0);
+  // square pyramids N0, N0/2, ... with N0 = 64 or 48 take the compile-time-size kernel
+  const int sq = square_pyramid(op, m0, cb.ng);
   cudaEvent_t ev;
   prof_begin(st, &ev);
   if (sq == 64)
@@ -979,7 +992,7 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
   else
     launch(k_mg_coarse2d<T>, 1, dim3(32, 32, 1), bytes, st, cb, b, x, T(op->alpha), T(op->beta), T(p.omega));
   TRY(launch_check());
-  prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * (double)h->mg[m0].n[0] * h->mg[m0].n[1]);  // read f, write x
+  prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * (double)op->h->mg[m0].n[0] * op->h->mg[m0].n[1]);  // read f, write x
   return AMR_OK;
 }
 
@@ -2093,6 +2106,423 @@ amr_status project_T_impl(amr_operator* ppe, const amr_solver_params& p, const i
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// ---------------------------------------------------------------- work-list batch
+// Stopping test of Sec. 7 for every active problem of a work-list batch: records the
+// residual norm, retires converged (or failed) problems, and keeps the while-loop of the
+// captured batch running while any problem is active.
+__global__ void k_check_b(cudaGraphConditionalHandle handle, int use_cond, int n, const unsigned long long* __restrict__ rbits,
+                          const unsigned long long* __restrict__ fbits, double rtol, double atol, int maxv,
+                          DevStats* __restrict__ s, int* __restrict__ active) {
+  pdl_wait();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    if (!active[p]) continue;
+    const double r = __longlong_as_double((long long)rbits[p]);
+    const double fn = __longlong_as_double((long long)fbits[p]);
+    DevStats& st = s[p];
+    const int it = st.iter;
+    if (it < 64) st.hist[it] = r;
+    const double tol = fmax(rtol * fn, atol);
+    int cont = 0;
+    if (!isfinite(r)) st.status = 2;
+    else if (r <= tol) st.status = 0;
+    else if (it >= maxv) st.status = 1;
+    else {
+      cont = 1;
+      st.iter = it + 1;
+    }
+    active[p] = cont;
+    if (cont) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+// A batch of single-level 2-D problems (mixed precision, temporally blocked legs, square
+// coarse pyramids, homogeneous non-Neumann data) solved as one captured graph whose every
+// phase is one launch over a descriptor list.
+struct BatchGroup {  // one launch: entries [off, off + cnt) of a descriptor array
+  int off = 0, cnt = 0, tx = 0, ty = 0, tt = 16;
+};
+struct BatchPlan {
+  std::vector<amr_operator*> ops;
+  std::vector<double*> phi;
+  std::vector<const double*> f;
+  amr_solver_params p{};
+  int n = 0, kmax = 0;
+  std::vector<BatchGroup> down, up;  // per (m, tile) group, down in increasing m, up in decreasing m
+  BatchGroup coarse, resid, flat;
+  BDown* d_down = nullptr;
+  BUp* d_up = nullptr;
+  BCoarse* d_coarse = nullptr;
+  BResid* d_resid = nullptr;
+  BFlat* d_flat = nullptr;
+  int* d_active = nullptr;
+  unsigned long long* d_bits = nullptr;  // rbits[n], fbits[n]
+  DevStats* d_stats = nullptr;
+  DevStats* h_stats = nullptr;  // pinned
+  unsigned long long* h_bits = nullptr;  // pinned copy of rbits, fbits
+  cudaStream_t cs = nullptr, bs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches_pre = 0, launches_body = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaFree(d_down); cudaFree(d_up); cudaFree(d_coarse); cudaFree(d_resid); cudaFree(d_flat);
+    cudaFree(d_active); cudaFree(d_bits); cudaFree(d_stats);
+    if (h_stats) cudaFreeHost(h_stats);
+    if (h_bits) cudaFreeHost(h_bits);
+    if (cs) cudaStreamDestroy(cs);
+    if (bs) cudaStreamDestroy(bs);
+    *this = BatchPlan();
+  }
+};
+
+// levels above the coarse block of op's level-0 pyramid when the batch path applies, else -1
+inline int batch_levels(const amr_operator* op, const amr_solver_params& p) {
+  const amr_hierarchy* h = op->h;
+  if (h->D != 2 || h->L != 1 || h->lev[0].patches.size() != 1 || op->neumann) return -1;
+  if (p.precision != AMR_MIXED || !p.temporal_blocking || p.fuse_coarse || p.nu1 < 1 || p.nu1 > BLK_FX_NU ||
+      p.nu2 < 1 || p.nu2 > BLK_FX_NU)
+    return -1;
+  size_t bytes = 0;
+  const int m0 = coarse_block_m0(h, bytes);
+  if (m0 < 0) return -1;
+  const int M = (int)h->mg.size() - 1;
+  if (!square_pyramid(op, m0, M - m0 + 1)) return -1;
+  for (int m = 0; m < m0; ++m)
+    if (blk_tile(h->mg[m].n) != 16 && blk_tile(h->mg[m].n) != 32) return -1;
+  return m0;
+}
+
+template <typename D>
+amr_status upload(D** dst, const std::vector<D>& v) {
+  if (v.empty()) return AMR_OK;
+  CK(cudaMalloc(dst, v.size() * sizeof(D)));
+  CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(D), cudaMemcpyHostToDevice));
+  return AMR_OK;
+}
+
+// tile edge of a blocked leg in a batch: many grids at once make the legs throughput-bound,
+// where the halo recomputation of a tile (a 36^2 region for 16^2 cells, 52^2 for 32^2) is
+// the cost, so the batch takes 32^2 tiles
+inline int batch_tile(const int*) { return 32; }
+
+// descriptors of every phase, grouped into launches
+amr_status build_batch_lists(BatchPlan& B) {
+  const amr_solver_params& p = B.p;
+  std::vector<BDown> down;
+  std::vector<BUp> up;
+  std::vector<BCoarse> coarse;
+  std::vector<BResid> resid;
+  std::vector<BFlat> flat;
+  std::vector<int> K(B.n);
+  B.kmax = 0;
+  for (int k = 0; k < B.n; ++k) {
+    K[k] = batch_levels(B.ops[k], p);
+    B.kmax = std::max(B.kmax, K[k]);
+  }
+  auto group_of = [](std::vector<BatchGroup>& gs, int off, int cnt, int tx, int ty, int tt) {
+    if (cnt > 0) gs.push_back(BatchGroup{off, cnt, tx, ty, tt});
+  };
+  // down legs m = 0 .. kmax-1 and up legs m = kmax-1 .. 0, each split by tile edge
+  for (int m = 0; m < B.kmax; ++m)
+    for (int tt : {16, 32}) {
+      const int off = (int)down.size();
+      int tx = 0, ty = 0;
+      for (int k = 0; k < B.n; ++k) {
+        if (K[k] <= m) continue;
+        amr_operator* op = B.ops[k];
+        amr_hierarchy* h = op->h;
+        if (batch_tile(h->mg[m].n) != tt) continue;
+        Scratch<float>& S = op->s32;
+        BDown d{};
+        d.p = k;
+        d.tt = tt;
+        d.tiles_x = (h->mg[m].n[0] + tt - 1) / tt;
+        d.tiles_y = (h->mg[m].n[1] + tt - 1) / tt;
+        d.halo = 2 * p.nu1 + 2;
+        d.nu = p.nu1;
+        d.lv = mg_view(h, m, op->bc);
+        d.gp = h->mg[m].patch;
+        d.gcp = h->mg[m + 1].patch;
+        d.b = m == 0 ? S.rin : S.mb[m];
+        d.xo = m == 0 ? S.T1 : S.mt[m];
+        d.bcn = S.mb[m + 1];
+        d.alpha = (float)op->alpha;
+        d.beta = (float)op->beta;
+        d.omega = (float)p.omega;
+        d.ood = (float)(p.omega / (op->alpha - 60.0 * op->beta * d.lv.inv12h2));
+        tx = std::max(tx, d.tiles_x);
+        ty = std::max(ty, d.tiles_y);
+        down.push_back(d);
+      }
+      group_of(B.down, off, (int)down.size() - off, tx, ty, tt);
+    }
+  for (int m = B.kmax - 1; m >= 0; --m)
+    for (int tt : {16, 32}) {
+      const int off = (int)up.size();
+      int tx = 0, ty = 0;
+      for (int k = 0; k < B.n; ++k) {
+        if (K[k] <= m) continue;
+        amr_operator* op = B.ops[k];
+        amr_hierarchy* h = op->h;
+        if (batch_tile(h->mg[m].n) != tt) continue;
+        Scratch<float>& S = op->s32;
+        BUp u{};
+        u.p = k;
+        u.tt = tt;
+        u.tiles_x = (h->mg[m].n[0] + tt - 1) / tt;
+        u.tiles_y = (h->mg[m].n[1] + tt - 1) / tt;
+        u.halo = 2 * p.nu2;
+        u.nu = p.nu2;
+        u.lv = mg_view(h, m, op->bc);
+        u.cv = mg_view(h, m + 1, op->bc);
+        u.gp = h->mg[m].patch;
+        u.gcp = h->mg[m + 1].patch;
+        u.xc = S.mx[m + 1];
+        u.b = m == 0 ? S.rin : S.mb[m];
+        u.xi = m == 0 ? S.T1 : S.mt[m];
+        u.xo = m == 0 ? S.E : S.mx[m];
+        u.alpha = (float)op->alpha;
+        u.beta = (float)op->beta;
+        u.omega = (float)p.omega;
+        u.ood = (float)(p.omega / (op->alpha - 60.0 * op->beta * u.lv.inv12h2));
+        tx = std::max(tx, u.tiles_x);
+        ty = std::max(ty, u.tiles_y);
+        up.push_back(u);
+      }
+      group_of(B.up, off, (int)up.size() - off, tx, ty, tt);
+    }
+  int rtx = 0, rty = 0;
+  long long nmax = 0;
+  for (int k = 0; k < B.n; ++k) {
+    amr_operator* op = B.ops[k];
+    amr_hierarchy* h = op->h;
+    Scratch<float>& S = op->s32;
+    const int m0 = K[k];
+    BCoarse c{};
+    c.p = k;
+    c.cb = make_coarse_block(op, p, m0);
+    c.n0 = square_pyramid(op, m0, c.cb.ng);
+    c.b = m0 == 0 ? S.rin : S.mb[m0];
+    c.x = m0 == 0 ? S.E : S.mx[m0];
+    c.alpha = (float)op->alpha;
+    c.beta = (float)op->beta;
+    c.omega = (float)p.omega;
+    coarse.push_back(c);
+    BResid r{};
+    r.p = k;
+    r.lv = level_view(h, 0, op->bc);
+    r.tiles_x = (r.lv.maxn[0] + BX - 1) / BX;
+    r.tiles_y = (r.lv.maxn[1] + BY - 1) / BY;
+    r.x = B.phi[k];
+    r.f = op->F;
+    r.out = op->Res;
+    r.alpha = op->alpha;
+    r.beta = op->beta;
+    rtx = std::max(rtx, r.tiles_x);
+    rty = std::max(rty, r.tiles_y);
+    resid.push_back(r);
+    BFlat fl{};
+    fl.p = k;
+    fl.n = h->nelems;
+    fl.vmask = h->d_valid;
+    fl.phi = B.phi[k];
+    fl.e = S.E;
+    fl.r = op->Res;
+    fl.rin = S.rin;
+    fl.f = B.f[k];
+    fl.F = op->F;
+    nmax = std::max(nmax, (long long)h->nelems);
+    flat.push_back(fl);
+  }
+  B.coarse = BatchGroup{0, B.n, 0, 0, 0};
+  B.resid = BatchGroup{0, B.n, rtx, rty, 0};
+  B.flat = BatchGroup{0, B.n, (int)std::min<long long>((nmax + 255) / 256, 64), 0, 0};
+  TRY(upload(&B.d_down, down));
+  TRY(upload(&B.d_up, up));
+  TRY(upload(&B.d_coarse, coarse));
+  TRY(upload(&B.d_resid, resid));
+  TRY(upload(&B.d_flat, flat));
+  CK(cudaMalloc(&B.d_active, B.n * sizeof(int)));
+  CK(cudaMalloc(&B.d_bits, 2 * B.n * sizeof(unsigned long long)));
+  CK(cudaMalloc(&B.d_stats, B.n * sizeof(DevStats)));
+  CK(cudaMallocHost(&B.h_stats, B.n * sizeof(DevStats)));
+  CK(cudaMallocHost(&B.h_bits, 2 * B.n * sizeof(unsigned long long)));
+  return AMR_OK;
+}
+
+// one V-cycle of every active problem, the update, the new residuals, their norms and the
+// stopping test (the body of the captured while-loop)
+amr_status batch_body(BatchPlan& B, cudaGraphConditionalHandle handle, cudaStream_t st) {
+  const amr_solver_params& p = B.p;
+  unsigned long long* rbits = B.d_bits;
+  unsigned long long* fbits = B.d_bits + B.n;
+  constexpr int RD16 = 16 + 4 * BLK_FX_NU + 4, RD32 = 32 + 4 * BLK_FX_NU + 4;
+  constexpr int RU16 = 16 + 4 * BLK_FX_NU, RU32 = 32 + 4 * BLK_FX_NU;
+  for (const BatchGroup& g : B.down) {
+    const int rm = g.tt == 16 ? RD16 : RD32;
+    const size_t smem = (size_t)3 * (rm + 2 * NG) * (rm + 2 * NG) * sizeof(float);
+    dim3 grid(g.tx, g.ty, g.cnt);
+    if (g.tt == 16) launch(k_mg_down2d_b<RD16, 16>, grid, dim3(32, 8, 1), smem, st, (const BDown*)(B.d_down + g.off), (const int*)B.d_active);
+    else launch(k_mg_down2d_b<RD32, 32>, grid, dim3(32, 8, 1), smem, st, (const BDown*)(B.d_down + g.off), (const int*)B.d_active);
+    TRY(launch_check());
+  }
+  launch(k_mg_coarse2d_sq_b, B.coarse.cnt, dim3(32, 32, 1), sizeof(float) * std::max(sq_total<64, 64>(), sq_total<48, 48>()), st,
+         (const BCoarse*)B.d_coarse, (const int*)B.d_active);
+  TRY(launch_check());
+  for (const BatchGroup& g : B.up) {
+    const int rm = g.tt == 16 ? RU16 : RU32;
+    const size_t smem = (size_t)3 * (rm + 2 * NG) * (rm + 2 * NG) * sizeof(float);
+    dim3 grid(g.tx, g.ty, g.cnt);
+    if (g.tt == 16) launch(k_mg_up2d_b<RU16, 16>, grid, dim3(32, 8, 1), smem, st, (const BUp*)(B.d_up + g.off), (const int*)B.d_active);
+    else launch(k_mg_up2d_b<RU32, 32>, grid, dim3(32, 8, 1), smem, st, (const BUp*)(B.d_up + g.off), (const int*)B.d_active);
+    TRY(launch_check());
+  }
+  launch(k_update_b, dim3(B.flat.tx, B.n, 1), 256, 0, st, (const BFlat*)B.d_flat, (const int*)B.d_active, rbits);
+  TRY(launch_check());
+  launch(k_resid2d_b<1>, dim3(B.resid.tx, B.resid.ty, B.n), dim3(BX, BY, 1), 0, st, (const BResid*)B.d_resid,
+         (const int*)B.d_active);
+  TRY(launch_check());
+  launch(k_norm_convert_b, dim3(B.flat.tx, B.n, 1), 256, 0, st, (const BFlat*)B.d_flat, (const int*)B.d_active, rbits);
+  TRY(launch_check());
+  launch(k_check_b, 1, 256, 0, st, handle, 1, B.n, (const unsigned long long*)rbits, (const unsigned long long*)fbits,
+         p.rtol, p.atol, p.max_vcycles, B.d_stats, B.d_active);
+  return launch_check();
+}
+
+amr_status build_batch_graph(BatchPlan& B) {
+  const amr_solver_params& p = B.p;
+  CK(cudaStreamCreateWithFlags(&B.cs, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&B.bs, cudaStreamNonBlocking));
+  unsigned long long* rbits = B.d_bits;
+  unsigned long long* fbits = B.d_bits + B.n;
+  cudaStream_t cs = B.cs, bs = B.bs;
+  amr_status result = AMR_OK;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const long long l0 = g_launches.load();
+  do {
+    cudaMemsetAsync(B.d_stats, 0, B.n * sizeof(DevStats), cs);
+    cudaMemsetAsync(B.d_bits, 0, 2 * B.n * sizeof(unsigned long long), cs);
+    cudaMemsetAsync(B.d_active, 1, B.n * sizeof(int), cs);  // nonzero: active
+    launch(k_init_b, dim3(B.flat.tx, B.n, 1), 256, 0, cs, (const BFlat*)B.d_flat, p.zero_initial ? 1 : 0, fbits);
+    if ((result = launch_check()) != AMR_OK) break;
+    launch(k_resid2d_b<1>, dim3(B.resid.tx, B.resid.ty, B.n), dim3(BX, BY, 1), 0, cs, (const BResid*)B.d_resid,
+           (const int*)B.d_active);
+    if ((result = launch_check()) != AMR_OK) break;
+    launch(k_norm_convert_b, dim3(B.flat.tx, B.n, 1), 256, 0, cs, (const BFlat*)B.d_flat, (const int*)B.d_active, rbits);
+    if ((result = launch_check()) != AMR_OK) break;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, cg, 0, 0) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    launch(k_check_b, 1, 256, 0, cs, handle, 1, B.n, (const unsigned long long*)rbits, (const unsigned long long*)fbits,
+           p.rtol, p.atol, p.max_vcycles, B.d_stats, B.d_active);
+    if ((result = launch_check()) != AMR_OK) break;
+    B.launches_pre = g_launches.load() - l0;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &edata, &ndeps) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, cg, deps, edata, ndeps, &cp) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      result = AMR_ERR_CUDA;
+      break;
+    }
+    const long long l1 = g_launches.load();
+    amr_status rb = batch_body(B, handle, bs);
+    B.launches_body = g_launches.load() - l1;
+    cudaGraph_t bout = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(bs, &bout);
+    if (rb != AMR_OK) { result = rb; break; }
+    if (e1 != cudaSuccess) { set_error(std::string("batch body capture: ") + cudaGetErrorString(e1)); result = AMR_ERR_CUDA; break; }
+    if (cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) {
+      result = AMR_ERR_CUDA;
+      break;
+    }
+  } while (false);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  g_launches.store(l0);  // captured launches are counted when the graph runs
+  if (result != AMR_OK) {
+    if (g) cudaGraphDestroy(g);
+    if (std::string(get_error()).empty()) set_error("batch graph capture failed");
+    cudaGetLastError();
+    return result;
+  }
+  if (e2 != cudaSuccess) { set_error(std::string("batch capture: ") + cudaGetErrorString(e2)); return AMR_ERR_CUDA; }
+  const cudaError_t e3 = cudaGraphInstantiate(&B.exec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e3);
+  return AMR_OK;
+}
+
+bool same_params(const amr_solver_params& a, const amr_solver_params& b) {
+  return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.omega == b.omega && a.rtol == b.rtol && a.atol == b.atol &&
+         a.max_vcycles == b.max_vcycles && a.precision == b.precision && a.zero_initial == b.zero_initial &&
+         a.temporal_blocking == b.temporal_blocking && a.fuse_coarse == b.fuse_coarse;
+}
+
+// the batch through the work-list graph; AMR_OK / per-problem status as amr_batch_solve
+amr_status batch_worklist(amr_operator* const* ops, int n, const amr_solver_params& q, double* const* phi,
+                          const double* const* f, amr_solve_stats* stats, int* status, cudaStream_t st) {
+  static std::mutex mu;
+  static BatchPlan plan;
+  std::lock_guard<std::mutex> lock(mu);
+  bool hit = plan.exec && plan.n == n && same_params(plan.p, q);
+  for (int k = 0; hit && k < n; ++k) hit = plan.ops[k] == ops[k] && plan.phi[k] == phi[k] && plan.f[k] == f[k];
+  if (!hit) {
+    plan.release();
+    plan.n = n;
+    plan.p = q;
+    plan.ops.assign(ops, ops + n);
+    plan.phi.assign(phi, phi + n);
+    plan.f.assign(f, f + n);
+    TRY(blk_attrs<float>());
+    CK(cudaFuncSetAttribute(k_mg_coarse2d_sq_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    for (int k = 0; k < n; ++k) TRY(ensure_scratch<float>(ops[k]));
+    amr_status s = build_batch_lists(plan);
+    if (s == AMR_OK) s = build_batch_graph(plan);
+    if (s != AMR_OK) { plan.release(); return s; }
+  }
+  CK(cudaGraphLaunch(plan.exec, st));
+  CK(cudaMemcpyAsync(plan.h_stats, plan.d_stats, n * sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(plan.h_bits, plan.d_bits, 2 * n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  amr_status worst = AMR_OK;
+  long long iters = 0;
+  for (int k = 0; k < n; ++k) {
+    const DevStats& ds = plan.h_stats[k];
+    iters = std::max<long long>(iters, ds.iter);
+    amr_solve_stats loc{};
+    loc.vcycles = ds.iter;
+    for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
+    loc.final_res = ds.hist[std::min(ds.iter, 63)];
+    double fn;
+    std::memcpy(&fn, &plan.h_bits[n + k], sizeof(double));
+    loc.rhs_norm = fn;
+    if (stats) stats[k] = loc;
+    const amr_status sk = ds.status == 0 ? AMR_OK : (ds.status == 2 ? AMR_ERR_NONFINITE : AMR_ERR_NOT_CONVERGED);
+    if (status) status[k] = sk;
+    if (sk != AMR_OK && worst == AMR_OK) {
+      worst = sk;
+      set_error(sk == AMR_ERR_NONFINITE ? "residual is not finite" : "max_vcycles reached");
+    }
+  }
+  g_launches.fetch_add(plan.launches_pre + iters * plan.launches_body);
+  return worst;
+}
+
 }  // namespace
 
 // =================================================================== allocation-free mean-zero
@@ -2505,7 +2935,6 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
   static std::mutex mu;
   static std::vector<cudaStream_t> pool;
   static std::vector<cudaEvent_t> ev;
-  std::lock_guard<std::mutex> lock(mu);
   constexpr int NSTREAM = 16;
   if (pool.empty()) {
     pool.resize(NSTREAM);
@@ -2516,6 +2945,11 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
   cudaStream_t st = S(stream);
   amr_solver_params q = *p;
   q.use_graph = 1;
+  // single-level 2-D problems with blocked legs: one launch per phase over a work list
+  bool worklist = n > 0;
+  for (int k = 0; k < n && worklist; ++k) worklist = batch_levels(ops[k], q) >= 0;
+  if (worklist) return batch_worklist(ops, n, q, phi, f, stats, status, st);
+  std::lock_guard<std::mutex> lock(mu);
   // problems that share a hierarchy share its reduction scratch: same stream, in order
   std::vector<const amr_hierarchy*> hs;
   std::vector<int> sid(n);
