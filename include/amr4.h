@@ -313,11 +313,20 @@ amr_status amr_project_transpose(amr_operator* ppe, const amr_solver_params* p, 
                                  amr_solve_stats* stats, void* stream);
 
 /* Batched solves: n independent problems (each with its own operator; hierarchies may
- * differ, e.g. the uneven sizes of a batch of single-level Helmholtz problems), each solved
- * by its captured CUDA graph (p->use_graph is forced to 1, boundary data homogeneous).  The
- * graphs are launched concurrently on a pool of internal streams forked from ``stream`` and
- * joined back to it; problems that share a hierarchy run one after another on the same
- * stream because they share its reduction scratch.  The call synchronises ``stream``.
+ * differ, e.g. the uneven sizes of a batch of single-level Helmholtz problems; boundary data
+ * homogeneous).  When every problem is a single-level 2-D problem solved in mixed precision
+ * with temporally blocked legs (nu1, nu2 in 1..4, no pure-Neumann operator) whose level-0
+ * pyramid ends in the square one-block coarse V-cycle (64 -> 4 or 48 -> 6: level-0 sizes
+ * 64 * 2^k or 48 * 2^k), the batch runs as one captured CUDA graph (built on the first call,
+ * reused while the operators, fields and parameters stay the same): every phase of the
+ * refinement loop (the down legs of one depth, the coarse V-cycles, the up legs, the update,
+ * the FP64 residual, its norm, the stopping test) is one launch over a descriptor list
+ * covering all problems, and a device-side loop runs until every problem has converged,
+ * problems that have converged skipping their entries.  Otherwise each problem runs its own
+ * captured graph (p->use_graph is forced to 1), launched concurrently on a pool of internal
+ * streams forked from ``stream`` and joined back to it; problems that share a hierarchy then
+ * run one after another on the same stream because they share its reduction scratch.  The
+ * call synchronises ``stream``.
  * stats and status (host arrays of n entries, nullable) receive each problem's statistics
  * and status; the return value is the first non-OK status (AMR_OK if all converged). */
 amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
