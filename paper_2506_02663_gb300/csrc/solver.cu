@@ -2191,8 +2191,6 @@ inline int batch_levels(const amr_operator* op, const amr_solver_params& p) {
   if (m0 < 0) return -1;
   const int M = (int)h->mg.size() - 1;
   if (!square_pyramid(op, m0, M - m0 + 1)) return -1;
-  for (int m = 0; m < m0; ++m)
-    if (blk_tile(h->mg[m].n) != 16 && blk_tile(h->mg[m].n) != 32) return -1;
   return m0;
 }
 
