@@ -1,0 +1,62 @@
+"""Writes the stored expected values under tests/golden/ from the FP64 oracle alone (no
+GPU, no library): ``python tests/golden/make_golden.py``.
+
+ms2d.json: the 64^2 manufactured-solution Poisson problem (phi = sin 2 pi x sin 3 pi y +
+x^2 y on the unit square, Dirichlet face averages, right-hand side = cell averages of the
+Laplacian, the paper's Sec. 3 discretisation): the discrete solution at 32 seeded cells,
+its error norms against the exact cell averages, and the errors and observed orders for
+n = 16, 32, 64, 128 (the fourth-order claim of Sec. 3)."""
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import composite as cp, solve as so  # noqa: E402
+from oracle.hierarchy import Hierarchy  # noqa: E402
+from paper_2506_02663_gb300 import workloads as wl  # noqa: E402  (seeded inputs only)
+
+
+def ms_solution(n):
+    rhs, bc, exact = wl.ms2d(n)
+    H = Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]], bc=[0] * 4)
+    f = cp.new_field(H)
+    f[0][H.levels[0].covered] = rhs.ravel()
+    phi, _, _ = so.solve_direct(H, f, 0.0, 1.0, [bc])
+    sol = phi[0][H.levels[0].covered].reshape(n, n)
+    e = sol - exact
+    h = 1.0 / n
+    return sol, (float(np.sum(np.abs(e)) * h * h), float(math.sqrt(np.sum(e * e) * h * h)), float(np.max(np.abs(e))))
+
+
+def main():
+    n = 64
+    sol, err = ms_solution(n)
+    g = np.random.default_rng(20250603 + 1)
+    cells = g.integers(0, n, size=(32, 2))
+    errs = {m: ms_solution(m)[1] for m in (16, 32, 64, 128)}
+    ms = sorted(errs)
+    orders = {f"{ms[i]}->{ms[i + 1]}": [math.log2(errs[ms[i]][k] / errs[ms[i + 1]][k]) for k in range(3)]
+              for i in range(len(ms) - 1)}
+    out = {
+        "source": "oracle.solve.solve_direct on workloads.ms2d (paper Sec. 3 discretisation, Dirichlet "
+                  "Eq. velBCHomoDiri5th); written by tests/golden/make_golden.py",
+        "n": n,
+        "cells_ij": cells.tolist(),  # (i, j): x index, y index of the n x n interior array [i, j]
+        "phi": [float(sol[i, j]) for i, j in cells],
+        "err_l1_l2_linf": list(err),
+        "errors_by_n": {str(m): list(v) for m, v in errs.items()},
+        "observed_orders_l1_l2_linf": orders,
+    }
+    with open(os.path.join(HERE, "ms2d.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print("wrote ms2d.json")
+
+
+if __name__ == "__main__":
+    main()

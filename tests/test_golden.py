@@ -1,0 +1,32 @@
+"""Stored expected values (tests/golden/, written by tests/golden/make_golden.py from the
+oracle alone): the oracle still reproduces them, and they carry the fourth-order
+convergence Sec. 3 states for the discretisation."""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+
+import make_golden  # noqa: E402
+
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "ms2d.json")))
+
+
+def test_golden_orders_are_fourth_order():
+    """Sec. 3: fourth-order L1 / L2 convergence of the solution error (third-order truncation
+    on the boundary layer leaves the max norm at >= 3.5)."""
+    last = GOLDEN["observed_orders_l1_l2_linf"]["64->128"]
+    assert last[0] > 3.8 and last[1] > 3.8 and last[2] > 3.5, last
+
+
+def test_oracle_reproduces_golden_values():
+    n = GOLDEN["n"]
+    sol, err = make_golden.ms_solution(n)
+    scale = float(np.max(np.abs(sol)))
+    for (i, j), v in zip(GOLDEN["cells_ij"], GOLDEN["phi"]):
+        assert abs(sol[i, j] - v) <= 1e-12 * scale
+    for a, b in zip(err, GOLDEN["err_l1_l2_linf"]):
+        assert abs(a - b) <= 1e-9 * b

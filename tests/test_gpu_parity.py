@@ -618,3 +618,32 @@ def test_blocked_legs_large_tiles(bcw, ab):
     r = cp.residual(H, sols[0], F, alpha, beta)
     rmax = float(np.max(np.abs(r[0][H.levels[0].valid])))
     assert rmax <= 1.5e-10 * max_abs(H, F), rmax / max_abs(H, F)
+
+
+def test_manufactured_solution_matches_golden_values():
+    """The 64^2 manufactured-solution solve on the GPU against the stored oracle values of
+    tests/golden/ms2d.json: sampled cells to 1e-10 of max|phi| and the error norms against
+    the exact cell averages to 1e-4 relative (a 1e-10 |phi| deviation moves norms of about
+    2e-6 by at most that much)."""
+    import json
+    import os
+    amr = _amr()
+    from paper_2506_02663_gb300 import workloads as wl
+    golden = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ms2d.json")))
+    n = golden["n"]
+    rhs, bcd, exact = wl.ms2d(n)
+    gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+    op = amr.Operator(gh, 0.0, 1.0, [0, 0, 0, 0])
+    for precision in (amr.FP64, amr.MIXED):
+        dphi = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        op.solve(dphi, _dev(gh.pack([[rhs]])), bc=_dev(gh.pack_bc([bcd])),
+                 params=amr.default_params(rtol=1e-12, max_vcycles=100, precision=precision))
+        got = gh.unpack(dphi.cpu().numpy())[0][0]
+        scale = float(np.max(np.abs(got)))
+        for (i, j), v in zip(golden["cells_ij"], golden["phi"]):
+            assert abs(got[i, j] - v) <= 1e-10 * scale, (precision, i, j)
+        e = got - exact
+        h = 1.0 / n
+        errs = (np.sum(np.abs(e)) * h * h, np.sqrt(np.sum(e * e) * h * h), np.max(np.abs(e)))
+        for a, b in zip(errs, golden["err_l1_l2_linf"]):
+            assert abs(a - b) <= 1e-4 * b, (precision, a, b)
