@@ -232,6 +232,18 @@ def run_reference(args):
 
 
 # ============================================================================ our arm
+def aggregate(total_ms, dofv_rank, ws, dist=None, device="cpu"):
+    """Whole-job figures of a replicas run: the slowest rank's device time (max over ranks)
+    and value = ws x this rank's DOF x V-cycles / that time (every rank solves the same
+    workload).  ``dist`` is torch.distributed (initialised) or None for one process."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return tmax, ws * dofv_rank / (tmax * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -291,13 +303,8 @@ def run_ours(args):
     clocks = sampler.stop()
     if dist:
         dist.barrier()
-    total_ms = sum(ts)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
     dofv_rank = sum(dof * sum(v) for v in vcs)
-    value = ws * dofv_rank / (tmax * 1e-3)
+    tmax, value = aggregate(sum(ts), dofv_rank, ws, dist, "cuda")
     vc_per_system = [statistics.mean(v[i] for v in vcs) for i in range(len(systems))]
 
     # ---------------- end to end through the C ABI with host buffers
