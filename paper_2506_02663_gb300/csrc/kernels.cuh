@@ -1045,22 +1045,74 @@ __global__ void k_prolong(LevelView fine, LevelView crs, const XferBlock* __rest
   cell_prolong<T, D>(crs, fine.patches[b.fpatch], crs.patches[b.cpatch], gf, xc, xf, xf2);
 }
 
-// 3-D prolongation, one thread per fine cell: += trilinear interpolation of its 2x2x2 coarse
-// stencil, read with 32-bit offsets (cells outside the coarse patch are its stored ghost
-// layers).  In the outermost fine layer, where the stencil leaves the domain, the homogeneous
-// extension enters through per-dimension weights (no per-cell ghost evaluation), so boundary
-// lanes cost a few more loads instead of the generic path.  Interior: cell_prolong's order.
+// 3-D prolongation of one fine cell whose 2x2x2 coarse stencil leaves the domain: the
+// homogeneous extension enters as per-dimension weights over four inward coarse cells (3/4 on
+// the face cell + 1/4 of the layer-1 ghost formula), a tensor product with the usual pairs.
 template <typename T>
+__device__ __forceinline__ void prolong3d_boundary_cell(const LevelView& crs, const PatchDesc& cp, const PatchDesc& fp,
+                                                        const int gf[3], const T* __restrict__ xc, T* __restrict__ xf,
+                                                        T* __restrict__ xf2) {
+  const T* __restrict__ cb = xc + cp.off;
+  const int csy = (int)cp.sy, csz = (int)cp.sz;
+  int ix[3][4];
+  T wx[3][4];
+  int nx[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int par = gf[e] >> 1, sg = (gf[e] & 1) ? 1 : -1;
+    const int lo = e == 0 ? cp.lo[0] : (e == 1 ? cp.lo[1] : cp.lo[2]);
+    const int g2 = par + sg;
+    if (g2 >= 0 && g2 < crs.ndom[e]) {
+      nx[e] = 2;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ix[e][m] = par - lo + (m == 1 ? sg : 0);
+        wx[e][m] = m == 0 ? T(0.75) : (m == 1 ? T(0.25) : T(0));
+      }
+    } else {
+      nx[e] = 4;
+      const int side = g2 < 0 ? 0 : 1, type = crs.bc[2 * e + side];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ix[e][m] = (side == 0 ? m : crs.ndom[e] - 1 - m) - lo;
+        wx[e][m] = T(0.25) * gcoef<T>(type, 0, m) + (m == 0 ? T(0.75) : T(0));
+      }
+    }
+  }
+  T v = T(0);
+#pragma unroll
+  for (int c2 = 0; c2 < 4; ++c2)
+#pragma unroll
+    for (int c1 = 0; c1 < 4; ++c1)
+#pragma unroll
+      for (int c0 = 0; c0 < 4; ++c0)
+        if (c0 < nx[0] && c1 < nx[1] && c2 < nx[2])
+          v += (wx[0][c0] * wx[1][c1] * wx[2][c2]) *
+               cb[(ix[2][c2] + NG) * csz + (ix[1][c1] + NG) * csy + (ix[0][c0] + NG)];
+  const int of = (gf[2] - fp.lo[2] + NG) * (int)fp.sz + (gf[1] - fp.lo[1] + NG) * (int)fp.sy + (gf[0] - fp.lo[0] + NG);
+  xf[fp.off + of] += v;
+  if (xf2 != nullptr) xf2[fp.off + of] += v;
+}
+
+// 3-D prolongation: += trilinear interpolation of each fine cell's 2x2x2 coarse stencil, read
+// with 32-bit offsets (cells outside the coarse patch are its stored ghost layers);
+// cell_prolong's summation order.  A thread takes PZ fine cells along z (large grids: four,
+// independent loads in flight together).  Fine cells whose stencil leaves the domain (the outermost fine layer at a
+// domain face) are done inline when INLINE (small grids), else skipped and left to
+// k_prolong3d_shell, so that no warp of a large grid carries the boundary arithmetic.
+template <typename T, bool INLINE, int PZ>
 __global__ void __launch_bounds__(BX* BY) k_prolong3d(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
-                                                      int nz, const T* __restrict__ xc, T* __restrict__ xf,
+                                                      int nzc, const T* __restrict__ xc, T* __restrict__ xf,
                                                       T* __restrict__ xf2) {
   pdl_wait();
-  const XferBlock b = blocks[blockIdx.z / nz];
-  const int gf[3] = {2 * b.clo[0] + (int)(blockIdx.x * BX + threadIdx.x), 2 * b.clo[1] + (int)(blockIdx.y * BY + threadIdx.y),
-                     2 * b.clo[2] + (int)(blockIdx.z % nz)};
-  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || gf[2] > 2 * b.chi[2] + 1) return;
+  const XferBlock b = blocks[blockIdx.z / nzc];
   const PatchDesc cp = crs.patches[b.cpatch];
   const PatchDesc fp = fine.patches[b.fpatch];
+#pragma unroll
+  for (int qz = 0; qz < PZ; ++qz) {
+  const int gf[3] = {2 * b.clo[0] + (int)(blockIdx.x * BX + threadIdx.x), 2 * b.clo[1] + (int)(blockIdx.y * BY + threadIdx.y),
+                     2 * b.clo[2] + (int)(blockIdx.z % nzc) * PZ + qz};
+  if (gf[0] > 2 * b.chi[0] + 1 || gf[1] > 2 * b.chi[1] + 1 || gf[2] > 2 * b.chi[2] + 1) continue;
   int par[3], sg[3];
   bool inside = true;
 #pragma unroll
@@ -1069,51 +1121,12 @@ __global__ void __launch_bounds__(BX* BY) k_prolong3d(LevelView fine, LevelView 
     sg[e] = (gf[e] & 1) ? 1 : -1;
     inside = inside && par[e] + sg[e] >= 0 && par[e] + sg[e] < crs.ndom[e];
   }
+  if (!inside) {
+    if (INLINE) prolong3d_boundary_cell<T>(crs, cp, fp, gf, xc, xf, xf2);
+    continue;
+  }
   const T* __restrict__ cb = xc + cp.off;
   const int csy = (int)cp.sy, csz = (int)cp.sz;
-  if (!inside) {
-    // tensor product of per-dimension weights: inside the domain the pair (parent 3/4, next
-    // 1/4); where the next coarse cell is outside, the homogeneous layer-1 extension folded
-    // into four inward points from the face (3/4 on the face cell + 1/4 of the ghost formula)
-    int ix[3][4];
-    T wx[3][4];
-    int nx[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const int lo = e == 0 ? cp.lo[0] : (e == 1 ? cp.lo[1] : cp.lo[2]);
-      const int g2 = par[e] + sg[e];
-      if (g2 >= 0 && g2 < crs.ndom[e]) {
-        nx[e] = 2;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          ix[e][m] = par[e] - lo + (m == 1 ? sg[e] : 0);
-          wx[e][m] = m == 0 ? T(0.75) : (m == 1 ? T(0.25) : T(0));
-        }
-      } else {
-        nx[e] = 4;
-        const int side = g2 < 0 ? 0 : 1, type = crs.bc[2 * e + side];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          ix[e][m] = (side == 0 ? m : crs.ndom[e] - 1 - m) - lo;
-          wx[e][m] = T(0.25) * gcoef<T>(type, 0, m) + (m == 0 ? T(0.75) : T(0));
-        }
-      }
-    }
-    T v = T(0);
-#pragma unroll
-    for (int c2 = 0; c2 < 4; ++c2)
-#pragma unroll
-      for (int c1 = 0; c1 < 4; ++c1)
-#pragma unroll
-        for (int c0 = 0; c0 < 4; ++c0)
-          if (c0 < nx[0] && c1 < nx[1] && c2 < nx[2])
-            v += (wx[0][c0] * wx[1][c1] * wx[2][c2]) *
-                 cb[(ix[2][c2] + NG) * csz + (ix[1][c1] + NG) * csy + (ix[0][c0] + NG)];
-    const int of = (gf[2] - fp.lo[2] + NG) * (int)fp.sz + (gf[1] - fp.lo[1] + NG) * (int)fp.sy + (gf[0] - fp.lo[0] + NG);
-    xf[fp.off + of] += v;
-    if (xf2 != nullptr) xf2[fp.off + of] += v;
-    return;
-  }
   const int oc = (par[2] - cp.lo[2] + NG) * csz + (par[1] - cp.lo[1] + NG) * csy + (par[0] - cp.lo[0] + NG);
   const int d0 = sg[0], d1 = sg[1] * csy, d2 = sg[2] * csz;
   T v = T(0);
@@ -1130,6 +1143,43 @@ __global__ void __launch_bounds__(BX* BY) k_prolong3d(LevelView fine, LevelView 
   const int of = (gf[2] - fp.lo[2] + NG) * (int)fp.sz + (gf[1] - fp.lo[1] + NG) * (int)fp.sy + (gf[0] - fp.lo[0] + NG);
   xf[fp.off + of] += v;
   if (xf2 != nullptr) xf2[fp.off + of] += v;
+  }
+}
+
+// The fine cells k_prolong3d<T, false, PZ> skips: the layer at each domain face a block's fine region
+// touches.  blockIdx.y = face 2d + side; a cell on several faces belongs to the face of its
+// lowest dimension, so face (d, side) covers the cells with index 0 or 2 n - 1 along d,
+// the non-boundary indices along the lower dimensions and every index along the higher ones.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong3d_shell(LevelView fine, LevelView crs, const XferBlock* __restrict__ blocks,
+                                                         const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ xf2) {
+  pdl_wait();
+  const XferBlock b = blocks[blockIdx.z];
+  const int d = blockIdx.y >> 1, side = blockIdx.y & 1;
+  int flo[3], fhi[3], blo[3], bhi[3];  // fine region and its non-boundary part per dimension
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    flo[e] = 2 * b.clo[e];
+    fhi[e] = 2 * b.chi[e] + 1;
+    blo[e] = max(flo[e], 1);
+    bhi[e] = min(fhi[e], 2 * crs.ndom[e] - 2);
+  }
+  const int face = side == 0 ? 0 : 2 * crs.ndom[d] - 1;
+  if (face < flo[d] || face > fhi[d]) return;
+  // the two other dimensions, lower one first
+  const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  const int a1 = e1 < d ? blo[e1] : flo[e1], z1 = e1 < d ? bhi[e1] : fhi[e1];
+  const int a2 = e2 < d ? blo[e2] : flo[e2], z2 = e2 < d ? bhi[e2] : fhi[e2];
+  const int n1 = z1 - a1 + 1, n2 = z2 - a2 + 1;
+  if (n1 <= 0 || n2 <= 0) return;
+  const long long cnt = (long long)n1 * n2;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
+    int gf[3];
+    gf[d] = face;
+    gf[e1] = a1 + (int)(t % n1);
+    gf[e2] = a2 + (int)(t / n1);
+    prolong3d_boundary_cell<T>(crs, crs.patches[b.cpatch], fine.patches[b.fpatch], gf, xc, xf, xf2);
+  }
 }
 
 // 2-D prolongation, one thread per coarse cell: its four children += linear interpolation

@@ -471,9 +471,22 @@ amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const Xfe
     // 32-bit offsets inside the padded patches (a 3-D patch beyond 2^31 elements takes the
     // generic kernel)
     const long long fel = (long long)(fine.maxn[0] + 2 * NG + 3) * (fine.maxn[1] + 2 * NG) * (fine.maxn[2] + 2 * NG);
-    if (fel < (1LL << 31) && 2LL * xmax[2] * nblocks <= 65535) {
-      dim3 grid((2 * xmax[0] + BX - 1) / BX, (2 * xmax[1] + BY - 1) / BY, 2 * xmax[2] * nblocks);
-      launch(k_prolong3d<T>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, 2 * xmax[2], xc, xf, xf2);
+    // large grids: four fine cells per thread along z, the face layer in its own launch (a few
+    // blocks per face); small grids: one cell per thread with the face cells inline
+    const bool large = (long long)xmax[0] * xmax[1] * xmax[2] >= 64LL * 64 * 64;
+    const int pz = large ? 4 : 1;
+    const int nzc = (2 * xmax[2] + pz - 1) / pz;
+    if (fel < (1LL << 31) && (long long)nzc * nblocks <= 65535) {
+      dim3 grid((2 * xmax[0] + BX - 1) / BX, (2 * xmax[1] + BY - 1) / BY, nzc * nblocks);
+      if (large) {
+        launch(k_prolong3d<T, false, 4>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, nzc, xc, xf, xf2);
+        if (const amr_status s1 = launch_check(); s1 != AMR_OK) return s1;
+        const long long face = 4LL * std::max({xmax[0] * xmax[1], xmax[1] * xmax[2], xmax[0] * xmax[2]});
+        const unsigned gx = (unsigned)std::min<long long>((face + 255) / 256, 64);
+        launch(k_prolong3d_shell<T>, dim3(gx, 6, nblocks), 256, 0, st, fine, crs, blocks, xc, xf, xf2);
+      } else {
+        launch(k_prolong3d<T, true, 1>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, nzc, xc, xf, xf2);
+      }
     } else {
       const int fy = 2 * xmax[1];
       const int nby = (fy + BY - 1) / BY;
