@@ -1411,21 +1411,21 @@ __device__ __forceinline__ T lap_smem(const T* __restrict__ a, int o, int sy) {
   return (T(16) * s1 - s2 - T(60) * xc) + T(0);
 }
 
-// f(i, j) for every cell of a w x h box of a block (32 x 8 threads).  RM = 0: rows of 32
+// f(i, j) for every cell of a w x h box of a block (rows of 32 threads, NT in all).  RM = 0: rows of 32
 // threads stride over the box; RM > 0 (w, h <= RM, a compile-time bound): one linear pass
 // over RM x RM positions with a fixed trip count, positions outside the box skipped.
-template <int RM, typename F>
+template <int RM, int NT = 256, typename F>
 __device__ __forceinline__ void for_cells(int w, int h, F&& f) {
   if constexpr (RM == 0) {
     for (int j = (int)threadIdx.y; j < h; j += (int)blockDim.y)
       for (int i = (int)threadIdx.x; i < w; i += (int)blockDim.x) f(i, j);
   } else {
-    constexpr int NC = RM * RM, IT = (NC + 255) / 256;
+    constexpr int NC = RM * RM, IT = (NC + NT - 1) / NT;
     const int tid = (int)(threadIdx.x + 32 * threadIdx.y);
 #pragma unroll 2
     for (int k = 0; k < IT; ++k) {
-      const int c = tid + 256 * k;
-      if (NC % 256 == 0 || c < NC) {
+      const int c = tid + NT * k;
+      if (NC % NT == 0 || c < NC) {
         const int i = c % RM, j = c / RM;
         if (i < w && j < h) f(i, j);
       }
@@ -1437,7 +1437,7 @@ __device__ __forceinline__ void for_cells(int w, int h, F&& f) {
 // the region is at most RM x RM (a compile-time bound, shared-memory pitch sy = RM + 4), cell
 // loops have fixed trip counts, and blocks whose region touches no domain face skip the
 // ghost pass and its barrier.
-template <typename T, bool ZERO, int RM = 0>
+template <typename T, bool ZERO, int RM = 0, int NT = 256>
 __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom& tg, const JacobiTable& jt, int sy,
                                             T* cur, T* oth, const T* __restrict__ sb, int nu, T alpha, T beta,
                                             const Team& tm) {
@@ -1455,7 +1455,7 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
         region_ghosts(lv, tg, cur, SY, c0, d0, c1, d1, tm);
         __syncthreads();
       }
-      for_cells<RM>(b0, b1, [&](int i, int j) {
+      for_cells<RM, NT>(b0, b1, [&](int i, int j) {
         if (i < a0 || j < a1) return;
         const int o = (j + NG) * SY + (i + NG);
         const T w = jt_get<T>(jt, jt.kx[i] + 5 * jt.ky[j]);
@@ -1511,7 +1511,7 @@ __device__ __forceinline__ T* smooth_region(const LevelView& lv, const TileGeom&
 // ghosts): nu weighted-Jacobi sweeps from zero, the smoothed x written to xo (and added to
 // xo2 when given), and the residual f - A x restricted (2x2 average) into the coarse
 // right-hand side bcn over the covered coarse cells.  halo = 2 nu + 2.
-template <typename T, int RM = 0, int TILE = 0>
+template <typename T, int RM = 0, int TILE = 0, int NT = 256>
 __device__ __forceinline__ void mg_down2d_body(const LevelView& lv, const PatchDesc& gp, const PatchDesc& gcp, int tx, int ty, int halo,
                                                int nu, const T* __restrict__ b, T* __restrict__ xo, T* __restrict__ xo2,
                                                T* __restrict__ bcn, T alpha, T beta, T omega, T ood) {
@@ -1529,13 +1529,13 @@ __device__ __forceinline__ void mg_down2d_body(const LevelView& lv, const PatchD
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   const T* __restrict__ bg = b + gp.off;
   const int gsy = (int)gp.sy;
-  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
+  for_cells<RM, NT>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = bg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
   __syncthreads();
-  T* cur = smooth_region<T, true, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  T* cur = smooth_region<T, true, RM, NT>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xg = xo + gp.off;
   T* __restrict__ xg2 = xo2 != nullptr ? xo2 + gp.off : nullptr;
-  for_cells<TM>(tg.tw, tg.th, [&](int i, int j) {
+  for_cells<TM, NT>(tg.tw, tg.th, [&](int i, int j) {
     const T v = cur[(tj + j + NG) * sy + ti + i + NG];
     xg[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = v;
     if (xg2 != nullptr) xg2[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] += v;
@@ -1551,7 +1551,7 @@ __device__ __forceinline__ void mg_down2d_body(const LevelView& lv, const PatchD
   const int cw = tg.tw / 2, ch = tg.th / 2;
   const int csy = (int)gcp.sy;
   T* __restrict__ cg = bcn + gcp.off;
-  for_cells<CM>(cw, ch, [&](int ci, int cj) {
+  for_cells<CM, NT>(cw, ch, [&](int ci, int cj) {
     T acc = T(0);
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
@@ -1566,13 +1566,13 @@ __device__ __forceinline__ void mg_down2d_body(const LevelView& lv, const PatchD
   });
 }
 
-template <typename T, int RM = 0, int TILE = 0>
-__global__ void __launch_bounds__(256) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
+template <typename T, int RM = 0, int TILE = 0, int NT = 256>
+__global__ void __launch_bounds__(NT) k_mg_down2d(LevelView lv, PatchDesc gp, PatchDesc gcp, int tx, int ty, int halo,
                                                    int nu, const T* __restrict__ b, T* __restrict__ xo,
                                                    T* __restrict__ xo2, T* __restrict__ bcn, T alpha, T beta, T omega,
                                                    T ood) {
   pdl_wait();
-  mg_down2d_body<T, RM, TILE>(lv, gp, gcp, tx, ty, halo, nu, b, xo, xo2, bcn, alpha, beta, omega, ood);
+  mg_down2d_body<T, RM, TILE, NT>(lv, gp, gcp, tx, ty, halo, nu, b, xo, xo2, bcn, alpha, beta, omega, ood);
 }
 
 // Coarse value at (c0, c1) of a single-patch 2-D grid, at most one cell outside the domain
@@ -1618,7 +1618,7 @@ __device__ __forceinline__ T coarse_ext2d(const T* __restrict__ cg, int csy, con
 // (coarse values outside the domain from the homogeneous extension with corners), then nu
 // weighted-Jacobi sweeps, written to xo (xi != xo: blocks read halos of xi only).
 // halo = 2 nu.
-template <typename T, int RM = 0, int TILE = 0>
+template <typename T, int RM = 0, int TILE = 0, int NT = 256>
 __device__ __forceinline__ void mg_up2d_body(const LevelView& lv, const LevelView& cv, const PatchDesc& gp, const PatchDesc& gcp,
                                              int tx, int ty, int halo, int nu, const T* __restrict__ xc,
                                              const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
@@ -1635,7 +1635,7 @@ __device__ __forceinline__ void mg_up2d_body(const LevelView& lv, const LevelVie
   const T* __restrict__ xg = xi + gp.off;
   const T* __restrict__ cg = xc + gcp.off;
   __shared__ JacobiTable jt;
-  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) {
+  for_cells<RM, NT>(tg.rw, tg.rh, [&](int i, int j) {
       const int og = (tg.r1 + j + NG) * gsy + tg.r0 + i + NG;
       const int os = (j + NG) * sy + i + NG;
       sb[os] = bg[og];
@@ -1665,21 +1665,21 @@ __device__ __forceinline__ void mg_up2d_body(const LevelView& lv, const LevelVie
   const Team tm = block_team();
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   __syncthreads();
-  const T* cur = smooth_region<T, false, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  const T* cur = smooth_region<T, false, RM, NT>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ xw = xo + gp.off;
-  for_cells<TILE>(tg.tw, tg.th, [&](int i, int j) {
+  for_cells<TILE, NT>(tg.tw, tg.th, [&](int i, int j) {
     xw[(tg.j0 + j + NG) * gsy + tg.i0 + i + NG] = cur[(tj + j + NG) * sy + ti + i + NG];
   });
 }
 
-template <typename T, int RM = 0, int TILE = 0>
-__global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
+template <typename T, int RM = 0, int TILE = 0, int NT = 256>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_mg_up2d(LevelView lv, LevelView cv, PatchDesc gp, PatchDesc gcp, int tx,
                                                  int ty, int halo, int nu, const T* __restrict__ xc,
                                                  const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
                                                  T alpha, T beta, T omega, T ood) {
   pdl_wait();
-  mg_up2d_body<T, RM, TILE>(lv, cv, gp, gcp, tx, ty, halo, nu, xc, b, xi, xo, alpha, beta, omega, ood);
+  mg_up2d_body<T, RM, TILE, NT>(lv, cv, gp, gcp, tx, ty, halo, nu, xc, b, xi, xo, alpha, beta, omega, ood);
 }
 
 // Post-smoothing of a single-box AMR level (the correction form's up step): nu weighted-
@@ -1687,8 +1687,8 @@ __global__ void __launch_bounds__(256, 4) k_mg_up2d(LevelView lv, LevelView cv, 
 // correction), zero CF ghosts and physical ghosts by formula, and the result t added to the
 // level's correction e and to the accumulated correction x on the tile.  Only the tile's
 // own e and x cells are read and written (no halo reads of them).  halo = 2 nu.
-template <typename T, int RM = 0, int TILE = 0>
-__global__ void __launch_bounds__(256) k_amr_post2d(LevelView lv, PatchDesc gp, int tx, int ty, int halo, int nu,
+template <typename T, int RM = 0, int TILE = 0, int NT = 256>
+__global__ void __launch_bounds__(NT) k_amr_post2d(LevelView lv, PatchDesc gp, int tx, int ty, int halo, int nu,
                                                     const T* __restrict__ r, T* __restrict__ e, T* __restrict__ x,
                                                     T alpha, T beta, T omega, T ood) {
   pdl_wait();
@@ -1704,13 +1704,13 @@ __global__ void __launch_bounds__(256) k_amr_post2d(LevelView lv, PatchDesc gp, 
   build_jacobi_table<T>(jt, lv, tg, alpha, beta, omega, ood, tm);
   const T* __restrict__ rg = r + gp.off;
   const int gsy = (int)gp.sy;
-  for_cells<RM>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = rg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
+  for_cells<RM, NT>(tg.rw, tg.rh, [&](int i, int j) { sb[(j + NG) * sy + i + NG] = rg[(tg.r1 + j + NG) * gsy + tg.r0 + i + NG]; });
   __syncthreads();
-  const T* cur = smooth_region<T, true, RM>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
+  const T* cur = smooth_region<T, true, RM, NT>(lv, tg, jt, sy, sx, st, sb, nu, alpha, beta, tm);
   const int ti = tg.i0 - tg.r0, tj = tg.j0 - tg.r1;
   T* __restrict__ eg = e + gp.off;
   T* __restrict__ xg = x + gp.off;
-  for_cells<TILE>(tg.tw, tg.th, [&](int i, int j) {
+  for_cells<TILE, NT>(tg.tw, tg.th, [&](int i, int j) {
     const T v = cur[(tj + j + NG) * sy + ti + i + NG];
     const int og = (tg.j0 + j + NG) * gsy + tg.i0 + i + NG;
     eg[og] += v;

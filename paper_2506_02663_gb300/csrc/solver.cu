@@ -888,19 +888,19 @@ size_t blk_smem(const int* n, int halo) {
 constexpr int BLK_FX_NU = 4;
 template <typename T, typename... A>
 void launch_down2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
-  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_down2d<T, 16 + 4 * BLK_FX_NU + 4, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_down2d<T, 16 + 4 * BLK_FX_NU + 4, 16, 512>, grid, dim3(32, 16, 1), smem, st, a...);
   else if (nu <= BLK_FX_NU && tt == 32) launch(k_mg_down2d<T, 32 + 4 * BLK_FX_NU + 4, 32>, grid, dim3(32, 8, 1), smem, st, a...);
   else launch(k_mg_down2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
 }
 template <typename T, typename... A>
 void launch_up2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
-  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_up2d<T, 16 + 4 * BLK_FX_NU, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_mg_up2d<T, 16 + 4 * BLK_FX_NU, 16, 512>, grid, dim3(32, 16, 1), smem, st, a...);
   else if (nu <= BLK_FX_NU && tt == 32) launch(k_mg_up2d<T, 32 + 4 * BLK_FX_NU, 32>, grid, dim3(32, 8, 1), smem, st, a...);
   else launch(k_mg_up2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
 }
 template <typename T, typename... A>
 void launch_post2d(int tt, int nu, dim3 grid, size_t smem, cudaStream_t st, A&&... a) {
-  if (nu <= BLK_FX_NU && tt == 16) launch(k_amr_post2d<T, 16 + 4 * BLK_FX_NU, 16>, grid, dim3(32, 8, 1), smem, st, a...);
+  if (nu <= BLK_FX_NU && tt == 16) launch(k_amr_post2d<T, 16 + 4 * BLK_FX_NU, 16, 512>, grid, dim3(32, 16, 1), smem, st, a...);
   else if (nu <= BLK_FX_NU && tt == 32) launch(k_amr_post2d<T, 32 + 4 * BLK_FX_NU, 32>, grid, dim3(32, 8, 1), smem, st, a...);
   else launch(k_amr_post2d<T>, grid, dim3(32, 8, 1), smem, st, a...);
 }
