@@ -5,7 +5,13 @@ ms2d.json: the 64^2 manufactured-solution Poisson problem (phi = sin 2 pi x sin 
 x^2 y on the unit square, Dirichlet face averages, right-hand side = cell averages of the
 Laplacian, the paper's Sec. 3 discretisation): the discrete solution at 32 seeded cells,
 its error norms against the exact cell averages, and the errors and observed orders for
-n = 16, 32, 64, 128 (the fourth-order claim of Sec. 3)."""
+n = 16, 32, 64, 128 (the fourth-order claim of Sec. 3).
+
+amr2d.json: the bench's two-level workload at 1/8 size (32^2 base, ratio-2 box over
+[0.25, 0.75]^2, Gaussian-bump right-hand side): the composite discrete solution of the
+pure-Neumann PPE after the solvability fix and mean-zero (Sec. 6.3), and of the Helmholtz
+system alpha = 1, beta = -0.25 * 1e-3 / 256 with homogeneous Dirichlet data (Eq. comp. of
+Sec. 5 with AMRCFI ghosts and refluxing), at 24 seeded valid cells of each level."""
 import json
 import math
 import os
@@ -56,6 +62,44 @@ def main():
     with open(os.path.join(HERE, "ms2d.json"), "w") as fh:
         json.dump(out, fh, indent=1)
     print("wrote ms2d.json")
+    amr2d()
+
+
+def amr2d_solutions():
+    dim, n0, boxes, rhs = wl.bumps2d_rhs(scale=8)
+    out = {}
+    for name, bc, alpha, beta in (("ppe", [1] * 4, 0.0, 1.0), ("helmholtz", [0] * 4, 1.0, wl.HELMHOLTZ_BETA)):
+        H = Hierarchy(dim, n0, boxes, bc=bc)
+        F = cp.new_field(H)
+        for l, lev in enumerate(H.levels):
+            for k, (lo, hi) in enumerate(lev.boxes):
+                F[l][lev.box_slice(lo, hi)] = rhs[l][k]
+        if so.is_pure_neumann(H, alpha):
+            F, _ = so.solvability_fix(H, F)
+        phi, _, _ = so.solve_direct(H, F, alpha, beta)
+        if so.is_pure_neumann(H, alpha):
+            phi, _ = so.mean_zero(H, phi)
+        out[name] = (H, phi)
+    return (dim, n0, boxes), out
+
+
+def amr2d():
+    (dim, n0, boxes), sols = amr2d_solutions()
+    g = np.random.default_rng(20250603 + 2)
+    res = {"source": "oracle.solve.solve_direct (+ solvability_fix, mean_zero) on workloads.bumps2d_rhs(scale=8); "
+                     "written by tests/golden/make_golden.py",
+           "n0": list(n0), "boxes": boxes}
+    for name, (H, phi) in sols.items():
+        samples = []
+        for l, lev in enumerate(H.levels):
+            idx = np.argwhere(lev.valid)
+            pick = idx[g.choice(len(idx), size=24, replace=False)]
+            samples += [[l] + [int(v) for v in c] + [float(phi[l][tuple(c)])] for c in pick]
+        res[name] = {"samples_level_index_value": samples,
+                     "max_abs": float(max(np.max(np.abs(phi[l][lev.valid])) for l, lev in enumerate(H.levels)))}
+    with open(os.path.join(HERE, "amr2d.json"), "w") as fh:
+        json.dump(res, fh, indent=1)
+    print("wrote amr2d.json")
 
 
 if __name__ == "__main__":

@@ -30,3 +30,19 @@ def test_oracle_reproduces_golden_values():
         assert abs(sol[i, j] - v) <= 1e-12 * scale
     for a, b in zip(err, GOLDEN["err_l1_l2_linf"]):
         assert abs(a - b) <= 1e-9 * b
+
+
+AMR2D = json.load(open(os.path.join(HERE, "golden", "amr2d.json")))
+
+
+def test_oracle_reproduces_amr2d_golden_values():
+    """The two-level composite solves (coarse-fine ghosts of Sec. 5.2, refluxing, the
+    solvability fix and mean-zero of Sec. 6.3) still give the stored values."""
+    (_, n0, boxes), sols = make_golden.amr2d_solutions()
+    assert list(n0) == AMR2D["n0"]
+    assert json.loads(json.dumps(boxes)) == AMR2D["boxes"]
+    for name, (H, phi) in sols.items():
+        scale = AMR2D[name]["max_abs"]
+        for l, i, j, v in AMR2D[name]["samples_level_index_value"]:
+            assert H.levels[l].valid[i, j]
+            assert abs(phi[l][i, j] - v) <= 1e-12 * scale, (name, l, i, j)
