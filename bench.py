@@ -508,41 +508,77 @@ def _bumps3d_measure(amr, torch, peak, peak_kind, reps=2):
     """The 3-D workload: base 256^3 on [0,1]^3 plus a ratio-2 box over [0.375,0.625]^3
     (128^3 fine cells); RHS = cell averages of seeded Gaussian bumps; one pure-Neumann PPE and
     three Helmholtz solves (gamma=0.25, nu=1e-3, k=1/256, Dirichlet) per step, mixed
-    precision to 1e-10.  The fields (about 150 MB each in FP64) are larger than L2."""
+    precision to 1e-10.  The three velocity components are one amr_batch_solve call (one
+    hierarchy object per component, so that their captured graphs run concurrently); the same
+    step with the components solved one after another is timed beside it.  The backward pass
+    is the four adjoint solves (amr_solve_transpose, mixed precision, same tolerance).  The
+    fields (about 150 MB each in FP64) are larger than L2."""
     from paper_2506_02663_gb300 import workloads as wl
     dim, n0, boxes, rhs = wl.bumps3d_rhs()
     gh = amr.Hierarchy(dim, n0, boxes)
     dof = valid_dof(n0, boxes)
     f = torch.from_numpy(gh.pack(rhs)).cuda()
     ppe = amr.Operator(gh, 0.0, 1.0, [1] * 6)
-    helm = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA, [0] * 6)
+    ghc = [amr.Hierarchy(dim, n0, boxes) for _ in range(3)]
+    helms = [amr.Operator(g, 1.0, wl.HELMHOLTZ_BETA, [0] * 6) for g in ghc]
     phis = [torch.zeros_like(f) for _ in range(4)]
     stream = torch.cuda.current_stream()
     out = {"workload": "bumps3d: 3-D two-level AMR, base 256^3 + ratio-2 box [0.375,0.625]^3 (128^3 fine cells), "
-                       "Gaussian-bump RHS; per step: pure-Neumann PPE + 3 Helmholtz (gamma=0.25, nu=1e-3, k=1/256), "
-                       "each to ||r||_inf <= 1e-10 ||f||_inf",
+                       "Gaussian-bump RHS; per step: pure-Neumann PPE + 3 Helmholtz (gamma=0.25, nu=1e-3, k=1/256) "
+                       "batched in one amr_batch_solve call, each to ||r||_inf <= 1e-10 ||f||_inf",
            "dof_per_system": dof}
-    for name, prec in (("mixed", amr.MIXED), ("fp64", amr.FP64)):
-        p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
 
-        def step():
-            vc = [ppe.solve(phis[0], f, params=p)["vcycles"]]
-            for c in range(3):
-                vc.append(helm.solve(phis[1 + c], f, params=p)["vcycles"])
-            return vc
-        step()
+    def time_step(fn):
+        fn()
         ts, vcs = [], []
         for _ in range(reps):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            vcs.append(step())
+            vcs.append(fn())
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
-        ms = statistics.median(ts)
-        out[name] = {"ms_per_step": ms, "vcycles_per_system": vcs[-1],
-                     "value": dof * sum(vcs[-1]) / (ms * 1e-3), "unit": UNIT}
+        return statistics.median(ts), vcs[-1]
+
+    for name, prec in (("mixed", amr.MIXED), ("fp64", amr.FP64)):
+        p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
+
+        def step():
+            vc = [ppe.solve(phis[0], f, params=p)["vcycles"]]
+            st, status = amr.batch_solve(helms, phis[1:], [f] * 3, params=p)
+            if any(status):
+                raise RuntimeError(f"batched Helmholtz solves: statuses {status}")
+            return vc + [s["vcycles"] for s in st]
+
+        def step_sequential():
+            vc = [ppe.solve(phis[0], f, params=p)["vcycles"]]
+            for c in range(3):
+                vc.append(helms[c].solve(phis[1 + c], f, params=p)["vcycles"])
+            return vc
+        ms, vc = time_step(step)
+        out[name] = {"ms_per_step": ms, "vcycles_per_system": vc,
+                     "value": dof * sum(vc) / (ms * 1e-3), "unit": UNIT}
+        if name == "mixed":
+            ms_seq, vc_seq = time_step(step_sequential)
+            out[name]["components_one_after_another"] = {"ms_per_step": ms_seq, "vcycles_per_system": vc_seq}
+    # backward: the adjoint solves of the step (host-driven refinement loop)
+    pa = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.MIXED, use_graph=0)
+    lam = [torch.zeros_like(f) for _ in range(4)]
+
+    def backward():
+        vc = [ppe.solve_transpose(lam[0], f, params=pa)["vcycles"]]
+        for c in range(3):
+            vc.append(helms[c].solve_transpose(lam[1 + c], f, params=pa)["vcycles"])
+        return vc
+    try:
+        ms_b, vc_b = time_step(backward)
+        out["adjoint_mixed"] = {"ms_per_step": ms_b, "vcycles_per_system": vc_b,
+                                "what": "A^T solves of the PPE (solvability-corrected solve map) and the three "
+                                        "Helmholtz operators, right-hand side f, mixed precision to 1e-10"}
+    except Exception as exc:  # reported, not fatal: the forward numbers stand on their own
+        out["adjoint_mixed"] = {"error": str(exc)[:200]}
+    helm = helms[0]
     # kernel classes of one instrumented mixed step (host-driven loop)
     pp = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.MIXED, use_graph=0)
     amr.profile_enable(True)
@@ -555,7 +591,10 @@ def _bumps3d_measure(amr, torch, peak, peak_kind, reps=2):
     out["classes"] = {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
                       for k, v in classes.items()}
     ppe.close()
-    helm.close()
+    for op in helms:
+        op.close()
+    for g in ghc:
+        g.close()
     gh.close()
     return out
 
