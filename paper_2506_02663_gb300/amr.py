@@ -93,6 +93,7 @@ _sigs = {
     "amr_kernel_launches": [],
     "amr_profile_enable": [C.c_int],
     "amr_set_tile_rows": [C.c_int],
+    "amr_set_fx_residual": [C.c_int],
     "amr_profile_read": [C.c_int, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
 }
 for _n, _a in _sigs.items():
@@ -117,6 +118,12 @@ def set_tile_rows(rows):
     """0: autotuned tile shape per grid; 1, 2, 4: cells per thread along y forced in the tiled
     level-operator kernels (3-D: 2 or 4)."""
     _check(_lib.amr_set_tile_rows(int(rows)), "amr_set_tile_rows")
+
+
+def set_fx_residual(on):
+    """1 (default): the 3-D FP64 residual forms its stencil sums exactly in 64-bit fixed point
+    (falling back to the plain FP64 kernel when a value leaves the frame); 0: plain FP64."""
+    _check(_lib.amr_set_fx_residual(int(on)), "amr_set_fx_residual")
 
 
 def profile_enable(on):

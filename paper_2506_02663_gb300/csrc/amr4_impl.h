@@ -42,6 +42,9 @@ struct LevelView {
   float hf, inv12h2_f, inv12h_f, invh_f;
   double dcorr[6][2];        // Jacobi diagonal correction (x 12 h^2) at distance 0 / 1 from face f
   float dcorr_f[6][2];
+  // device scratch of the fixed-point FP64 residual (two words: largest |x| as IEEE bits,
+  // out-of-frame flag); null for views that are not a hierarchy level
+  unsigned long long* fxs;
 };
 
 void finish_view(LevelView& v);  // fills the precomputed constants from h and bc

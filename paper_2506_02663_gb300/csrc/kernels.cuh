@@ -582,9 +582,11 @@ using zc_slot = std::integral_constant<int, I>;
 template <typename T, int MODE, int R>
 __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
     k_level_op3d_zc(LevelView lv, int ntx, int ntiles, int kc, const T* __restrict__ x, const T* __restrict__ f,
-                    T* __restrict__ out, T alpha, T beta, T omega, const unsigned char* __restrict__ vmask) {
+                    T* __restrict__ out, T alpha, T beta, T omega, const unsigned char* __restrict__ vmask,
+                    const unsigned* __restrict__ gate) {
   using G = ZcGeom<R>;
   pdl_wait();
+  if (gate != nullptr && *gate == 0u) return;  // gated launch: runs only when the flag is set
   __shared__ T sp[2][G::SH * ZC_W];
   __shared__ T wt[125];
   const PatchDesc p = lv.patches[0];
@@ -782,6 +784,249 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
       if (k + 1 < kb) step(k + 1, zc_slot<1>{}, std::false_type{});
     }
   }
+}
+
+// ------------------------------------------------------------------------ 3-D FP64 residual in fixed point
+// GB300 issues FP64 arithmetic at a small fraction of its integer rate, and the FP64 residual
+// of the refinement loop (13 FP64 operations per cell in floating point) is bound by that
+// rate.  Here the sums of the stencil are formed exactly in 64-bit integers: every value of
+// x the stencil reads is rounded once to a fixed-point frame set by the level's largest
+// interior |x| (its leading bit at bit 52), so that T = 16 s1 - s2 - 90 x (Eq. discreteOps:
+// 12 h^2 L x = T) is exact in 64 bits.  Bounds: interior values are below 2^53; a stored ghost
+// value (coarse-fine, copy) must stay below 2^55; a physical ghost value is a fixed
+// combination of interior values (Eqs. velBCHomoDiri5th, Neumann5: at most 11.7 times the
+// largest in layer 1 and 84.4 times in layer 2), and a cell reads at most one ghost per
+// direction, so |T| < (16 (3 * 11.7 + 3) + 3 * 84.4 + 3 + 90) 2^53 < 2^63.
+// T is rounded once to FP64 and r = f - alpha x - (beta / 12 h^2) 2^-S T takes two FP64
+// multiply-adds.  Rounding x to the frame changes it by at most half a unit in the last
+// place of the largest |x|, the size of one FP64 rounding of that value, so the result is as
+// accurate as the floating-point evaluation, whose sums round several times.  A value outside
+// the frame (a stored ghost value more than four times the bound on the interior values, or
+// a non-finite value) sets *flag, and the plain FP64 kernel, launched after this one with
+// that flag as its gate, recomputes the level.
+
+// round(x 2^(1075 - emax)) to the nearest integer (ties away from zero): the frame of a level
+// whose largest |x| has biased exponent emax (so that |x| < 2^(emax - 1022) maps below
+// 2^53); a value of 2^lim * 2^(emax - 1022) or more in magnitude (lim = 2 for stored values,
+// 7 for physical ghost values), or a non-finite one, sets ovf
+__device__ __forceinline__ long long fx_of(double x, int emax, int lim, bool& ovf) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53-bit significand
+  const int sh = e - emax;                                                     // x 2^S = m 2^sh
+  unsigned long long u = 0ull;
+  if (e != 0) {  // zero and subnormal values are below any frame's unit
+    if (sh > lim || e == 0x7ff) ovf = true;
+    else if (sh >= 0) u = m << sh;
+    else if (sh > -54) u = (m + (1ull << (-sh - 1))) >> (-sh);
+  }
+  return (b >> 63) ? -(long long)u : (long long)u;
+}
+
+// a 64-bit integer to FP64, rounded to nearest (ties to even), with integer instructions only
+__device__ __forceinline__ double fx_to_double(long long t) {
+  if (t == 0) return 0.0;
+  const unsigned long long sg = (unsigned long long)t & 0x8000000000000000ull;
+  unsigned long long u = sg ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)u);
+  u <<= lz;                                // leading one at bit 63
+  unsigned long long mant = u >> 11;       // 53 bits, the leading one at bit 52
+  const unsigned rem = (unsigned)(u & 0x7ffull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  // biased exponent 1086 - lz; adding the significand with its leading one to (exponent - 1)
+  // << 52 carries a rounding overflow into the exponent
+  return __longlong_as_double((long long)(sg | ((((unsigned long long)(1085 - lz)) << 52) + mant)));
+}
+
+// largest |x| over the interior cells of a single-patch level, as IEEE bits (non-negative
+// doubles order like their bit patterns), into *acc; block size 256
+__global__ void __launch_bounds__(256) k_absmax_patch(LevelView lv, const double* __restrict__ x,
+                                                      unsigned long long* __restrict__ acc) {
+  pdl_wait();
+  const PatchDesc p = lv.patches[0];
+  const int n0 = p.n[0], n1 = p.n[1], rows = p.n[1] * p.n[2];
+  unsigned long long v = 0ull;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* __restrict__ row = x + p.off + (long long)(r / n1 + NG) * p.sz + (long long)(r % n1 + NG) * p.sy + NG;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(row[i]) & 0x7fffffffffffffffull;
+      v = b > v ? b : v;
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, s);
+    v = u > v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(acc, v);
+}
+
+// The residual f - (alpha x + beta L x) of a z-chunked single-patch 3-D level (same tiles,
+// chunks, halo roles and prefetch distances as k_level_op3d_zc with R = 2), the planes staged
+// as fixed-point integers.  fxs[0]: largest interior |x| (k_absmax_patch); fxs[1]: flag.
+__global__ void __launch_bounds__(ZC_TX* ZC_TY, 2)
+    k_resid3d_fx(LevelView lv, int ntx, int ntiles, int kc, const double* __restrict__ x, const double* __restrict__ f,
+                 double* __restrict__ out, double alpha, double beta) {
+  constexpr int R = 2;
+  using G = ZcGeom<R>;
+  pdl_wait();
+  __shared__ long long sp[2][G::SH * ZC_W];
+  const PatchDesc p = lv.patches[0];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZC_TX + tx;
+  unsigned* __restrict__ flag = reinterpret_cast<unsigned*>(lv.fxs + 1);
+  const int emax = (int)((lv.fxs[0] >> 52) & 0x7ffull);
+  if (emax == 0x7ff || (emax != 0 && emax < 53)) {  // non-finite, or a frame below the normal range
+    if (tid == 0) *flag = 1u;
+    return;
+  }
+  // beta / (12 h^2) 2^-S with S = 1075 - emax (an all-zero interior: every value rounds to 0)
+  const double kT = emax == 0 ? 0.0 : beta * lv.inv12h2 * __longlong_as_double((long long)(emax - 52) << 52);
+  bool ovf = false;
+  const int sy = (int)p.sy, sz = (int)p.sz, nz = p.n[2];
+  const int nzd = lv.ndom[2], lz = p.lo[2];
+  const double* __restrict__ xb = x + p.off;
+  const double* __restrict__ fb = f + p.off;
+  double* __restrict__ ob = out + p.off;
+  int hx = 0, hy = 0;
+  const bool has_halo = tid < G::NH;
+  {
+    const int q = tid;
+    if (q < 2 * ZC_TX) {
+      hy = -2 + q / ZC_TX;
+      hx = q % ZC_TX;
+    } else if (q < 4 * ZC_TX) {
+      hy = G::TH + (q - 2 * ZC_TX) / ZC_TX;
+      hx = q % ZC_TX;
+    } else if (q < G::NH) {
+      const int r = q - 4 * ZC_TX, side = r / (2 * G::TH), c = r & 1;
+      hy = (r % (2 * G::TH)) >> 1;
+      hx = side == 0 ? c - 2 : ZC_TX + c;
+    }
+  }
+  const int hs = (hy + 2) * ZC_W + hx + 2;
+  const int c0 = (ty + 2) * ZC_W + tx + 2;
+  const int tile = blockIdx.x % ntiles, ka = (blockIdx.x / ntiles) * kc, kb = min(nz, ka + kc);
+  if (ka >= kb) return;
+  const int i0 = (tile % ntx) * ZC_TX, j0 = (tile / ntx) * G::TH;
+  const int i = i0 + tx;
+  const int col0 = (i + NG) + (j0 + ty + NG) * sy;
+  const int hli = i0 + hx, hlj = j0 + hy;
+  const int hcol = (hli + NG) + (hlj + NG) * sy;
+  int hsrc = 0, hstep = 0, htype = 0, hlayer = 0;
+  {
+    const int hgi = p.lo[0] + hli, hgj = p.lo[1] + hlj;
+    const int d = (hgi < 0 || hgi >= lv.ndom[0]) ? 0 : ((hgj < 0 || hgj >= lv.ndom[1]) ? 1 : -1);
+    if (has_halo && d >= 0) {
+      const int g = d == 0 ? hgi : hgj, n = lv.ndom[d], side = g < 0 ? 0 : 1;
+      hlayer = (side == 0 ? -g : g - n + 1) - 1;
+      htype = lv.bc[2 * d + side];
+      const int face = (side == 0 ? 0 : n - 1) - p.lo[d] - (d == 0 ? i0 : j0);
+      hsrc = d == 0 ? (hy + 2) * ZC_W + face + 2 : (face + 2) * ZC_W + hx + 2;
+      const int st = d == 0 ? 1 : ZC_W;
+      hstep = side == 0 ? st : -st;
+    }
+  }
+  const bool hload = has_halo && hstep == 0;
+  const bool face_tile = p.lo[0] + i0 == 0 || p.lo[0] + i0 + ZC_TX == lv.ndom[0] || p.lo[1] + j0 == 0 ||
+                         p.lo[1] + j0 + G::TH == lv.ndom[1];
+  auto halo = [&](int k) -> double { return hload ? xb[hcol + (k + NG) * sz] : 0.0; };
+  // frame headroom of the value of plane k (zc_zval): stored inside the domain, else the z
+  // ghost formula
+  auto zlim = [&](int k) -> int { return (lz + k >= 0 && lz + k < nzd) ? 2 : 7; };
+  constexpr int RS = ZC_TY;
+  long long q[R][5];  // x of each column at planes k-2..k+2, fixed point
+  double xd[R][3];    // x at planes k..k+2 as stored (the alpha x term)
+  double xs[2][R], fs[2][R], hv[2];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int col = col0 + r * RS * sy;
+    double d[5];
+    d[0] = zc_zval<double>(xb, col, sz, ka - 2, lz, nzd, lv);
+    d[1] = zc_zval<double>(xb, col, sz, ka - 1, lz, nzd, lv);
+    d[2] = xb[col + (ka + NG) * sz];
+    d[3] = zc_zval<double>(xb, col, sz, ka + 1, lz, nzd, lv);
+    d[4] = zc_zval<double>(xb, col, sz, ka + 2, lz, nzd, lv);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) q[r][m] = fx_of(d[m], emax, zlim(ka - 2 + m), ovf);
+    xd[r][0] = d[2];
+    xd[r][1] = d[3];
+    xd[r][2] = d[4];
+    xs[0][r] = xs[1][r] = 0.0;
+    if (ka + 1 < kb) xs[0][r] = zc_zval<double>(xb, col, sz, ka + 3, lz, nzd, lv);
+    if (ka + 2 < kb) xs[1][r] = zc_zval<double>(xb, col, sz, ka + 4, lz, nzd, lv);
+    fs[0][r] = fb[col + (ka + NG) * sz];
+    fs[1][r] = (ka + 1 < kb) ? fb[col + (ka + 1 + NG) * sz] : 0.0;
+  }
+  hv[0] = hv[1] = 0.0;
+  if (has_halo) {
+    hv[0] = halo(ka);
+    if (ka + 1 < kb) hv[1] = halo(ka + 1);
+  }
+  auto step = [&](int k, auto slot, auto safe) {
+    constexpr int S = decltype(slot)::value;
+    constexpr bool SAFE = decltype(safe)::value;  // planes up to k+5 inside the domain
+    long long* __restrict__ s = sp[S];
+    double fk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      fk[r] = fs[S][r];
+      s[c0 + r * RS * ZC_W] = q[r][2];
+    }
+    if (hload) {
+      s[hs] = fx_of(hv[S], emax, 2, ovf);
+      if (k + 2 < kb) hv[S] = halo(k + 2);
+    }
+    if (k + 2 < kb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) fs[S][r] = fb[col0 + r * RS * sy + (k + 2 + NG) * sz];
+    }
+    __syncthreads();
+    if (face_tile) {
+      // the ghost formula on the staged (fixed-point, so already scaled by 2^S) face cells: the
+      // tile's own interior cells, whose integers are below 2^53 and convert exactly
+      if (hstep != 0) {
+        double v = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) v += gcoef<double>(htype, hlayer, m) * (double)s[hsrc + m * hstep];
+        s[hs] = fx_of(v, 1075, 7, ovf);
+      }
+      __syncthreads();
+    }
+    const int pk = col0 + (k + NG) * sz;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int P = pk + r * RS * sy;
+      const int C = c0 + r * RS * ZC_W;
+      const long long s1 = ((s[C - 1] + s[C + 1]) + (s[C - ZC_W] + s[C + ZC_W])) + (q[r][1] + q[r][3]);
+      const long long s2 = ((s[C - 2] + s[C + 2]) + (s[C - 2 * ZC_W] + s[C + 2 * ZC_W])) + (q[r][0] + q[r][4]);
+      const long long T = s1 * 16 - s2 - q[r][2] * 90;
+      ob[P] = fma(-kT, fx_to_double(T), fma(-alpha, xd[r][0], fk[r]));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      q[r][0] = q[r][1];
+      q[r][1] = q[r][2];
+      q[r][2] = q[r][3];
+      q[r][3] = q[r][4];
+      q[r][4] = fx_of(xs[S][r], emax, zlim(k + 3), ovf);
+      xd[r][0] = xd[r][1];
+      xd[r][1] = xd[r][2];
+      xd[r][2] = xs[S][r];
+      if (k + 3 < kb) {  // q4 of plane k+3
+        if (SAFE) xs[S][r] = xb[col0 + r * RS * sy + (k + 5 + NG) * sz];
+        else xs[S][r] = zc_zval<double>(xb, col0 + r * RS * sy, sz, k + 5, lz, nzd, lv);
+      }
+    }
+  };
+  for (int k = ka; k < kb; k += 2) {
+    if (lz + k + 6 < nzd) {
+      step(k, zc_slot<0>{}, std::true_type{});
+      if (k + 1 < kb) step(k + 1, zc_slot<1>{}, std::true_type{});
+    } else {
+      step(k, zc_slot<0>{}, std::false_type{});
+      if (k + 1 < kb) step(k + 1, zc_slot<1>{}, std::false_type{});
+    }
+  }
+  if (ovf) *flag = 1u;
 }
 
 // ------------------------------------------------------------------------ G and D

@@ -337,12 +337,46 @@ int zc_blocks() {
 // z chunks of the 3-D kernel: as many as one wave holds, at least 4 planes each
 template <typename T, int M, int R>
 void launch_zc(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T O, const unsigned char* vmask,
-               cudaStream_t st) {
+               cudaStream_t st, const unsigned* gate = nullptr) {
   const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * R)), nz = lv.maxn[2];
   const int nch = std::max(1, std::min(zc_blocks<T, M, R>() / ntiles, nz / 4));
   const int kc = (nz + nch - 1) / nch;
   const int G = ntiles * ((nz + kc - 1) / kc);
-  launch(k_level_op3d_zc<T, M, R>, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, A, B, O, vmask);
+  launch(k_level_op3d_zc<T, M, R>, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, A, B, O, vmask,
+         gate);
+}
+
+// FP64 residual of a z-chunked level with the fixed-point stencil sums (k_resid3d_fx): the
+// frame from the level's largest interior |x|, the fixed-point pass, and the plain FP64
+// pass gated on the out-of-frame flag (it exits at once unless a value left the frame)
+std::atomic<int> g_fx_resid{1};  // amr_set_fx_residual
+inline bool fx_eligible(const LevelView& lv) {
+  return lv.fxs != nullptr && g_fx_resid.load(std::memory_order_relaxed) != 0 && zc_eligible(lv, 2);
+}
+int fx_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid3d_fx, ZC_TX * ZC_TY, 0);
+    blocks = std::max(1, nsm * std::max(1, per));
+  }
+  return blocks;
+}
+amr_status launch_resid_fx(const LevelView& lv, const double* x, const double* f, double* out, double alpha,
+                           double beta, cudaStream_t st) {
+  CK(cudaMemsetAsync(lv.fxs, 0, 2 * sizeof(unsigned long long), st));
+  const long long rows = (long long)lv.maxn[1] * lv.maxn[2];
+  launch(k_absmax_patch, (unsigned)std::min<long long>(rows, 152LL * 8), 256, 0, st, lv, x, lv.fxs);
+  const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * 2)), nz = lv.maxn[2];
+  const int nch = std::max(1, std::min(fx_blocks() / ntiles, nz / 4));
+  const int kc = (nz + nch - 1) / nch;
+  const int G = ntiles * ((nz + kc - 1) / kc);
+  launch(k_resid3d_fx, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, alpha, beta);
+  launch_zc<double, OP_RESID, 2>(lv, x, f, out, alpha, beta, 0.0, nullptr, st,
+                                 reinterpret_cast<const unsigned*>(lv.fxs + 1));
+  return AMR_OK;
 }
 
 template <typename T, int D, bool TR = false>
@@ -376,6 +410,13 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
     prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
     return launch_check();
+  }
+  if constexpr (sizeof(T) == 8 && D == 3 && !TR) {
+    if (mode == OP_RESID && bc == nullptr && vmask == nullptr && fx_eligible(lv)) {
+      if (const amr_status s1 = launch_resid_fx(lv, x, f, out, alpha, beta, st); s1 != AMR_OK) return s1;
+      prof_end(st, ev, PC_RESID, 3.0 * sizeof(T) * lv.ncells);
+      return launch_check();
+    }
   }
   if (D == 3 && !TR && bc == nullptr && (vmask == nullptr || mode == OP_RESID) && zc_eligible(lv, 2)) {
     // z-chunked marching path; rows per thread from the autotuner's table
@@ -2649,6 +2690,12 @@ long long amr_kernel_launches(void) { return g_launches.load(std::memory_order_r
 amr_status amr_set_tile_rows(int rows) {
   if (rows != 0 && rows != 1 && rows != 2 && rows != 4) { set_error("tile rows must be 0, 1, 2 or 4"); return AMR_ERR_INVALID_ARG; }
   g_tile_force.store(rows, std::memory_order_relaxed);
+  return AMR_OK;
+}
+
+amr_status amr_set_fx_residual(int on) {
+  if (on != 0 && on != 1) { set_error("fixed-point residual switch must be 0 or 1"); return AMR_ERR_INVALID_ARG; }
+  g_fx_resid.store(on, std::memory_order_relaxed);
   return AMR_OK;
 }
 

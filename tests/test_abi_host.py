@@ -96,3 +96,11 @@ def test_set_tile_rows_validates(amr):
     with pytest.raises(Exception):
         amr.set_tile_rows(3)
     amr.set_tile_rows(0)
+
+
+def test_set_fx_residual_validates(amr):
+    """The fixed-point residual switch accepts 0 and 1 and rejects the rest on the host."""
+    with pytest.raises(Exception):
+        amr.set_fx_residual(2)
+    amr.set_fx_residual(0)
+    amr.set_fx_residual(1)

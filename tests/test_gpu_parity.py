@@ -508,6 +508,92 @@ def test_3d_zchunk_operator_parity(n, rows, tile_rows):
     assert max_diff(H, got, refr) <= 1e-13 * op_scale(H, alpha, beta, X)
 
 
+@pytest.fixture
+def fx_switch():
+    amr = _amr()
+    yield amr.set_fx_residual
+    amr.set_fx_residual(1)
+
+
+def test_3d_fixed_point_residual(fx_switch):
+    """The 3-D FP64 residual with exact fixed-point stencil sums (the default on tile-multiple
+    single-patch levels) against the oracle and the plain FP64 kernel on a 64 x 64 x 40 grid
+    with Dirichlet and Neumann faces: a smooth field that meets the boundary conditions and a
+    rough one (whose layer-2 Dirichlet ghost values reach about 50 times the interior values)
+    both stay in the frame, so the fixed-point result is the one returned (it differs from the
+    plain kernel's in rounding only); phi = 0 (the refinement loop's first residual) gives f
+    exactly."""
+    amr = _amr()
+    n = (64, 64, 40)
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    bc = [0, 1, 0, 0, 1, 0]
+    hi = tuple(v / n[0] for v in n)
+    H = OH(3, n, box, bc=bc, hi=hi)
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    alpha, beta = 1.0, -0.02
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(73)
+    B = _rand_field(H, rng, redundant=False)
+    h = 1.0 / n[0]
+    xc, yc, zc = np.meshgrid(*[(np.arange(m) + 0.5) * h for m in n], indexing="ij")
+    lev = H.levels[0]
+    smooth = np.zeros(lev.shape)
+    smooth[lev.box_slice(*box[0][0])] = (np.sin(0.5 * np.pi * xc) * np.sin(np.pi * yc) *
+                                         np.cos(0.5 * np.pi * zc / hi[2]) * 3.7)
+    cases = {"smooth": [smooth], "rough": _rand_field(H, rng, redundant=False), "zero": [np.zeros(lev.shape)]}
+    for name, X in cases.items():
+        dx, df = _dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B))
+        got = {}
+        for on in (1, 0):
+            fx_switch(on)
+            res = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+            op.residual(dx, df, res)
+            got[on] = res.cpu().numpy()
+        fx_switch(1)
+        ref = cp.apply(H, X, alpha, beta, None)
+        refr = [B[0] - ref[0]]
+        for on in (1, 0):
+            g = from_packed(gh, H, got[on])
+            assert max_diff(H, g, refr) <= 1e-13 * op_scale(H, alpha, beta, X) + 1e-300, (name, on)
+        if name == "zero":
+            assert np.array_equal(got[1], got[0])
+        else:
+            assert not np.array_equal(got[1], got[0]), name
+
+
+def test_3d_fixed_point_residual_fallback(fx_switch):
+    """Two z-chunked levels (base 32 x 32 x 16, a 32 x 16 x 16 fine box) whose fine level
+    holds values a thousand times smaller than the coarse level around it: its coarse-fine
+    ghost values leave the fine level's frame, so the gated FP64 kernel recomputes that level
+    (bit for bit the plain kernel's result), while the base level keeps the fixed-point
+    result; the composite residual matches the oracle either way."""
+    amr = _amr()
+    n0 = (32, 32, 16)
+    boxes = [[((0, 0, 0), (31, 31, 15))], [((16, 16, 8), (47, 31, 23))]]
+    bc = [0, 1, 0, 0, 1, 0]
+    alpha, beta = 1.0, -0.01
+    H = OH(3, n0, boxes, bc=bc, hi=tuple(v / n0[0] for v in n0))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / n0[0])
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(79)
+    X = _rand_field(H, rng)
+    X[1] = X[1] * 1e-3
+    B = _rand_field(H, rng)
+    ref = cp.residual(H, X, B, alpha, beta)
+    got = {}
+    for on in (1, 0):
+        fx_switch(on)
+        res = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        op.residual(_dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B)), res)
+        got[on] = from_packed(gh, H, res.cpu().numpy())
+    fx_switch(1)
+    for on in (1, 0):
+        assert max_diff(H, got[on], ref) <= 1e-13 * op_scale(H, alpha, beta, X), on
+    v0, v1 = H.levels[0].valid, H.levels[1].valid
+    assert np.array_equal(got[1][1][v1], got[0][1][v1])
+    assert not np.array_equal(got[1][0][v0], got[0][0][v0])
+
+
 @pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
 @pytest.mark.parametrize("rows", [2, 4])
 def test_3d_zchunk_two_level_vcycle_and_solve(bcw, ab, rows, tile_rows):
