@@ -361,14 +361,14 @@ amr_status amr_profile_read(int kernel_class, long long* launches, double* total
  * counts as 2 there).  Process-wide; AMR_ERR_INVALID_ARG for any other value. */
 amr_status amr_set_tile_rows(int rows);
 /* FP64 residual of 3-D single-patch levels whose x / y extents are multiples of 32 x 16 (the
- * refinement loop's residual, amr_residual, amr_apply's residual form): on = 1 (the default)
- * forms the stencil sums 16 s1 - s2 - 90 x of Eq. (discreteOps) exactly in 64-bit integers
- * after rounding every value of phi the stencil reads once to a fixed-point frame set by the
- * level's largest interior |phi| (half a unit in the last place of that value at most, the
- * size of one FP64 rounding of it), then r = f - alpha phi - beta/(12 h^2) * sum in FP64;
- * physical ghost values are fixed combinations of interior values and always fit; a stored
- * ghost value (coarse-fine, copy) above four times that bound, or a non-finite value, makes
- * the plain FP64 kernel recompute the level.  Not in the paper: on
+ * refinement loop's residual and amr_residual).  on = 1 (the default): every value of phi
+ * the stencil reads is rounded once to a 64-bit fixed-point frame whose unit is 2^-52 times
+ * the largest interior |phi| rounded down to a power of two (at most half a unit in the last
+ * place of that value, the size of one FP64 rounding of it); the sum 16 s1 - s2 - 90 phi of
+ * Eq. (discreteOps) is then exact in int64, and r = f - alpha phi - beta/(12 h^2) * sum is
+ * formed in FP64.  Physical ghost values are fixed combinations of interior values and
+ * always fit; a stored ghost value (coarse-fine, copy) of 4 * 2^53 units or more, or a
+ * non-finite value, makes the plain FP64 kernel recompute the level.  Not in the paper: on
  * this GPU FP64 arithmetic runs at a small fraction of the integer rate.  on = 0: the plain
  * FP64 kernel always.  Process-wide; AMR_ERR_INVALID_ARG for any other value. */
 amr_status amr_set_fx_residual(int on);
