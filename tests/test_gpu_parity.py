@@ -594,6 +594,30 @@ def test_3d_fixed_point_residual_fallback(fx_switch):
     assert not np.array_equal(got[1][0][v0], got[0][0][v0])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bumps3d_quarter_size_residual_property(precision):
+    """The 3-D workload at a quarter of its size (base 64^3, a 32^3 fine box over
+    [0.375,0.625]^3, Gaussian-bump right-hand side; both levels take the z-chunked kernels
+    and the fixed-point FP64 residual): the PPE and the Helmholtz solves to 1e-10, whose
+    residual, recomputed by the oracle's composite operator, meets the tolerance."""
+    amr = _amr()
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes, rhs = wl.bumps3d_rhs(scale=4)
+    gh = amr.Hierarchy(dim, n0, boxes)
+    f = _dev(gh.pack(rhs))
+    for bc, (alpha, beta) in (([1] * 6, (0.0, 1.0)), ([0] * 6, (1.0, wl.HELMHOLTZ_BETA))):
+        H = OH(dim, n0, boxes, bc=bc)
+        op = amr.Operator(gh, alpha, beta, bc)
+        dphi = torch.zeros_like(f)
+        st = op.solve(dphi, f, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=precision))
+        phi = from_packed(gh, H, dphi.cpu().numpy())
+        F = from_packed(gh, H, f.cpu().numpy())
+        if so.is_pure_neumann(H, alpha):
+            F, _ = so.solvability_fix(H, F)
+        R = cp.residual(H, phi, F, alpha, beta)
+        assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F), (bc[0], max_abs(H, R) / max_abs(H, F), st)
+
+
 @pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
 @pytest.mark.parametrize("rows", [2, 4])
 def test_3d_zchunk_two_level_vcycle_and_solve(bcw, ab, rows, tile_rows):
