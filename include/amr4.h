@@ -6,7 +6,7 @@
  * The library solves the paper's fourth-order finite-volume elliptic systems -- the
  * pure-Neumann pressure Poisson equation and the Helmholtz systems (I - gamma*nu*k*L) of
  * Eq. (GePUP-IMEX b) -- on a block-structured AMR hierarchy (Sec. 5) by geometric
- * multigrid (Sec. 6.4), with every step in hand-written sm_103a CUDA kernels.
+ * multigrid (Sec. 6.5), with every step in hand-written sm_103a CUDA kernels.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -146,7 +146,7 @@ typedef struct {
 
 typedef struct {
   int nu1, nu2;      /* pre/post smoothing sweeps (4, 4: Fig. mg_convergenceRate)        */
-  double omega;      /* weighted-Jacobi weight (2/3, Sec. 6.4)                           */
+  double omega;      /* weighted-Jacobi weight (2/3, Sec. 6.5)                           */
   double rtol, atol; /* stop when ||f - A phi||_inf,valid <= max(rtol*||f||_inf, atol)    */
   int max_vcycles;   /* hard cap on V-cycles (no unbounded device loop exists)            */
   int precision;     /* AMR_FP64, or AMR_MIXED: FP32 V-cycles inside FP64 refinement      */
@@ -166,7 +166,7 @@ typedef struct {
   int vcycles;          /* V-cycles performed                                   */
   double rhs_norm;      /* ||f||_inf over valid cells (after the solvability fix) */
   double final_res;     /* ||f - A phi||_inf over valid cells at exit             */
-  double removed_mean;  /* pure Neumann: constant removed from f (Sec. 6.3)       */
+  double removed_mean;  /* pure Neumann: constant removed from f (Sec. 6.4)       */
   double res_history[64]; /* residual norm before each V-cycle (first 64)         */
 } amr_solve_stats;
 
@@ -209,21 +209,21 @@ amr_status amr_residual(amr_operator* op, double* phi, const double* f, double* 
 
 /* nsweeps weighted-Jacobi sweeps (true diagonal, homogeneous physical ghosts, zero CF
  * ghosts) of level ``level``'s operator on x for right-hand side b (both composite fields;
- * only that level is touched).  Kernel-level entry point of the smoother (Sec. 6.4). */
+ * only that level is touched).  Kernel-level entry point of the smoother (Sec. 6.5). */
 amr_status amr_smooth(amr_operator* op, int level, int nsweeps, double omega, double* x,
                       const double* b, void* stream);
 
-/* One composite V-cycle (Sec. 6.4) in FP64 on phi for right-hand side f. */
+/* One composite V-cycle (Sec. 6.5) in FP64 on phi for right-hand side f. */
 amr_status amr_vcycle(amr_operator* op, const amr_solver_params* p, double* phi, const double* f,
                       const double* bc, void* stream);
 
 /* V-cycles until the max-norm residual test of Sec. 7 passes.  Pure Neumann: f (const)
- * is corrected into an internal copy (Sec. 6.3) and phi is returned with zero h^D-weighted
+ * is corrected into an internal copy (Sec. 6.4) and phi is returned with zero h^D-weighted
  * mean over the valid cells.  stats (host, nullable). */
 amr_status amr_solve(amr_operator* op, const amr_solver_params* p, double* phi, const double* f,
                      const double* bc, amr_solve_stats* stats, void* stream);
 
-/* Sec. 6.3 for the composite PPE: f -= m on every valid cell with
+/* Sec. 6.4 for the composite PPE: f -= m on every valid cell with
  * m * sum_valid h^D = sum_valid h^D f - beta * sum_boundary h^(D-1) g (g = Neumann data in
  * bc, NULL = 0), compensated sums.  *m (host, nullable) receives m.  One component: level
  * 0 is the whole (connected) domain. */
@@ -236,17 +236,21 @@ amr_status amr_mean_zero(amr_hierarchy* h, double* phi, double* mean, void* stre
  * callers that must not allocate device memory at the point of the call -- code running
  * while device memory is fully held by another allocator (a framework's caching pool), or
  * inside a timing- or latency-critical loop where cudaMalloc's implicit device-wide
- * synchronisation is not acceptable.  Same result as amr_mean_zero (same kernels, same
- * fixed-order compensated sums), but its reduction scratch is a fixed file-scope device
- * array inside the library (8192 block partials plus a few scalars, about 128 KiB per GPU
- * that loads the library, held until the process exits) instead of hierarchy-owned memory,
- * and it calls no cudaMalloc, cudaFree or allocating library routine.
+ * synchronisation is not acceptable.  It launches exactly the kernels of amr_mean_zero with
+ * the same launch shapes (average-down, the grid-stride compensated sums with at most 512
+ * blocks per level, the fixed-order final sum, the shift), so the removed mean and the
+ * result are bitwise those of amr_mean_zero; only its reduction scratch differs: a fixed
+ * file-scope device array inside the library (8192 block partials plus a few scalars, about
+ * 128 KiB per GPU that loads the library, held until the process exits) instead of
+ * hierarchy-owned memory.  It calls no cudaMalloc, cudaFree or allocating library routine.
  *   - The hierarchy must already have its device copy (any earlier device call on it, e.g.
- *     amr_operator_create, makes it); otherwise AMR_ERR_INVALID_ARG.
- *   - Hierarchies whose reduction needs more than 8192 blocks are rejected with
- *     AMR_ERR_INVALID_ARG and a message giving the count (nothing is launched).
+ *     amr_operator_create or amr_mean_zero, makes it); otherwise AMR_ERR_INVALID_ARG.
+ *   - Hierarchies whose reduction needs more than 8192 blocks (more than 16 levels of at
+ *     least 131,072 cells) are rejected with AMR_ERR_INVALID_ARG and a message giving the
+ *     count; nothing is launched and phi is unchanged.  amr_mean_zero has the same limit.
  *   - The first call on a device looks up the array's device address with that device
- *     current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     current (cudaGetSymbolAddress); make that first call before any stream capture.  A
+ *     first call on a device whose stream is capturing is refused with AMR_ERR_INVALID_ARG.
  *   - Every call shares the one array and it keeps the last call's contents; each call
  *     writes every slot it reads before reading it.  Calls that overlap on the GPU (on
  *     different streams, or from different threads on the same device) race on the array
@@ -282,7 +286,7 @@ amr_status amr_apply_transpose(amr_operator* op, const double* y, double* out, v
  * with respect to a composite field whose invalid cells are averages is propagated
  * correctly; ghost cells of g are ignored; lambda's invalid cells are set to 0.
  * Pure-Neumann operator (alpha = 0, every face Neumann): the adjoint of the whole solve map
- * of amr_solve (Sec. 6.3 solvability correction, solve, h^D-weighted mean zero).  With
+ * of amr_solve (Sec. 6.4 solvability correction, solve, h^D-weighted mean zero).  With
  * w = h^D on the valid cells it returns the lambda with A^T lambda = g - w (1^T g)/(1^T w)
  * and 1^T lambda = 0 (the null vectors of A are 1 on the right and w on the left);
  * stats->removed_mean receives (1^T g)/(1^T w). */
@@ -337,6 +341,15 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
 amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* phi_host,
                           const double* f_host, const double* bc_host, amr_solve_stats* stats,
                           void* stream);
+
+/* Host-buffer variant of amr_batch_solve (same batching, statistics and return value):
+ * phi_host[k] and f_host[k] are HOST pointers (pinned or pageable) of problem k's composite
+ * fields.  Every f (and phi unless p->zero_initial) is copied into device buffers owned by
+ * the problem's operator (allocated on the first host-buffer call, freed with the
+ * operator), the batch is solved, and every phi is copied back before the call returns.
+ * An operator may appear only once in a call (AMR_ERR_INVALID_ARG otherwise). */
+amr_status amr_batch_solve_host(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi_host,
+                                const double* const* f_host, amr_solve_stats* stats, int* status, void* stream);
 
 void amr_default_params(amr_solver_params* p);
 const char* amr_last_error(void);

@@ -26,6 +26,6 @@ Modules
 ``composite``  Sec. 5.2-5.3: average-down, CF ghost fill, COH-1..4 composite operators,
                refluxing, composite projection (Eq. comp_ProjOp).
 ``solve``      sparse assembly of the composite operator, direct solves, solvability fix
-               (Sec. 6.3), mean-zero, transposes (adjoint).
-``mg``         Sec. 6.4 geometric multigrid (V-cycle with weighted Jacobi, omega = 2/3).
+               (Sec. 6.4), mean-zero, transposes (adjoint).
+``mg``         Sec. 6.5 geometric multigrid (V-cycle with weighted Jacobi, omega = 2/3).
 """

@@ -82,7 +82,7 @@ def neumann_bordered(A, U):
 
 
 def neumann_solve_transpose(H, G, A=None, U=None):
-    """Adjoint of the pure-Neumann solve map f -> phi (Sec. 6.3 solvability correction of f,
+    """Adjoint of the pure-Neumann solve map f -> phi (Sec. 6.4 solvability correction of f,
     bordered solve, h^D-weighted mean zero of phi).
 
     With w = h^D over the unknowns and F = I - 1 w^T / (w^T 1), the forward map is

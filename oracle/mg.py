@@ -1,4 +1,4 @@
-"""Geometric multigrid of Sec. 6.4 (oracle; test infrastructure).
+"""Geometric multigrid of Sec. 6.5 (oracle; test infrastructure).
 
 The paper fixes: restriction by "injection", prolongation by linear interpolation, weighted
 Jacobi with omega = 2/3, 4 pre- and 4 post-smoothing sweeps (Fig. mg_convergenceRate), and

@@ -9,7 +9,7 @@ solve (a library primitive used as one step).  The system is defined as follows:
   unknowns, their values are the average of their children (Eq. AMR_avergingDownToCrse);
 * equations: one per valid cell, the composite operator of COH-1..4 (``composite.apply``);
 * pure Neumann PPE (alpha = 0, all faces Neumann): the right-hand side is first made
-  compatible by the uniform correction of Sec. 6.3 (Eq. correctingFaceAvg applied to the
+  compatible by the uniform correction of Sec. 6.4 (Eq. correctingFaceAvg applied to the
   RHS, as the paragraph after it states for the PPE), and the solution is the one with
   zero h^D-weighted mean over the valid cells (bordered system).
 
@@ -189,7 +189,7 @@ def boundary_flux_sum(H, bc_data):
 
 
 def solvability_fix(H, f, beta=1.0, bc_data=None):
-    """Sec. 6.3 (Eq. correctingFaceAvg, applied to the PPE right-hand side): subtract from
+    """Sec. 6.4 (Eq. correctingFaceAvg, applied to the PPE right-hand side): subtract from
     f on every valid cell the constant m with
         m * sum_valid h^D = sum_valid h^D f - beta * sum_boundary h^(D-1) g.
     Returns (corrected field, m).  One component: the composite domain is connected."""
@@ -245,7 +245,7 @@ def project(Hn, W, bc_w=None):
     W     list of D composite fields (velocity components)
     bc_w  None (homogeneous) or per component a list over levels of Dirichlet face data of w
     D^comp uses Dirichlet ghosts for w (COH-1..4 with refluxing); the right-hand side is made
-    compatible (Sec. 6.3); phi is the mean-zero solution; G^comp uses homogeneous Neumann
+    compatible (Sec. 6.4); phi is the mean-zero solution; G^comp uses homogeneous Neumann
     ghosts and COH-4 on G phi, and no average-down is applied to u afterwards (Lemma
     compositeProjection).  Returns (u components, phi)."""
     D = Hn.D

@@ -77,6 +77,7 @@ _sigs = {
     "amr_solve": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
     "amr_solve_host": [_vp, _P(SolverParams), _vp, _vp, _vp, _P(SolveStats), _vp],
     "amr_batch_solve": [_P(_vp), C.c_int, _P(SolverParams), _P(_vp), _P(_vp), _P(SolveStats), _P(C.c_int), _vp],
+    "amr_batch_solve_host": [_P(_vp), C.c_int, _P(SolverParams), _P(_vp), _P(_vp), _P(SolveStats), _P(C.c_int), _vp],
     "amr_solvability_fix": [_vp, _vp, _vp, _P(C.c_double), _vp],
     "amr_mean_zero": [_vp, _vp, _P(C.c_double), _vp],
     "amr_mean_zero_noalloc": [_vp, _vp, _P(C.c_double), _vp],
@@ -401,6 +402,21 @@ def batch_solve(ops, phis, fs, params=None, stream=None):
     sc = (C.c_int * n)()
     rc = _lib.amr_batch_solve(oa, n, C.byref(p), _ptr_array(phis), _ptr_array(fs), st, sc, _stream(stream))
     _check(rc, "amr_batch_solve", (AMR_OK, AMR_ERR_NOT_CONVERGED))
+    return [stats_dict(st[k]) for k in range(n)], list(sc)
+
+
+def batch_solve_host(ops, phis_host, fs_host, params=None, stream=None):
+    """amr_batch_solve_host: numpy float64 HOST arrays in the composite layout (pinned or
+    pageable); returns (list of stats dicts, list of statuses)."""
+    n = len(ops)
+    p = params or default_params()
+    oa = (_vp * n)(*[op._op.value for op in ops])
+    st = (SolveStats * n)()
+    sc = (C.c_int * n)()
+    ph = (_vp * n)(*[a.ctypes.data for a in phis_host])
+    fh = (_vp * n)(*[a.ctypes.data for a in fs_host])
+    rc = _lib.amr_batch_solve_host(oa, n, C.byref(p), ph, fh, st, sc, _stream(stream))
+    _check(rc, "amr_batch_solve_host", (AMR_OK, AMR_ERR_NOT_CONVERGED))
     return [stats_dict(st[k]) for k in range(n)], list(sc)
 
 

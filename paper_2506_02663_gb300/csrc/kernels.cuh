@@ -174,7 +174,7 @@ __device__ __forceinline__ T diag_sum(const LevelView& lv, const PatchDesc& p, c
 // ------------------------------------------------------------------------ level operator
 // MODE 0: out = alpha x + beta L x
 // MODE 1: out = f - (alpha x + beta L x)
-// MODE 2: out = x + omega (f - A x) / diag        (weighted Jacobi, Sec. 6.4)
+// MODE 2: out = x + omega (f - A x) / diag        (weighted Jacobi, Sec. 6.5)
 // MODE 3: out = omega f / diag                    (first sweep from x = 0)
 enum { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI0 = 3 };
 
@@ -1238,7 +1238,7 @@ __global__ void __launch_bounds__(BX* BY) k_restrict2d_resid(LevelView fine, Lev
 }
 
 // Fine cell gf += cell-centred tensor linear interpolation of the coarse correction
-// (Sec. 6.4 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse values outside
+// (Sec. 6.5 "linear interpolation"; weights 3/4, 1/4 per dimension).  Coarse values outside
 // the domain come from the homogeneous physical extension with corners.
 template <typename T, int D>
 __device__ __forceinline__ void cell_prolong(const LevelView& crs, const PatchDesc& fp, const PatchDesc& cp,
@@ -2902,7 +2902,7 @@ __global__ void k_valid_out(LevelView lv, int nby, const T* __restrict__ w, cons
   out[o] = vmask[o] ? (f != nullptr ? f[o] - w[o] : w[o]) : T(0);
 }
 
-// Transposed prolongation (Sec. 6.4 linear interpolation): every fine cell hands
+// Transposed prolongation (Sec. 6.5 linear interpolation): every fine cell hands
 // w * (y1 + y2) to each coarse cell its interpolation reads (atomic adds); coarse positions
 // outside the domain pass their weight on through the homogeneous extension.
 template <typename T, int D>
@@ -3157,47 +3157,9 @@ __device__ __forceinline__ void dd_add(double& s, double& c, double a, double ac
   two_sum(t, e, s, c);
 }
 
-// Compensated, deterministic partial sums of w * x over valid interior cells: one
-// double-double partial per block, written to part[2*(base + linear block id)].
-template <int D>
-__global__ void k_wsum(LevelView lv, int nby, const double* __restrict__ x, const unsigned char* __restrict__ vmask,
-                       double w, double* __restrict__ part, long long base) {
-  pdl_wait();
-  __shared__ double ss[BX * BY], sc[BX * BY];
-  const PatchDesc p = lv.patches[blockIdx.z];
-  int i, j, k;
-  double s = 0.0, c = 0.0;
-  if (thread_cell<D>(p, nby, i, j, k)) {
-    const long long o = poff(p, i, j, k);
-    if (vmask == nullptr || vmask[o]) {
-      const double prod = w * x[o];
-      const double pe = fma(w, x[o], -prod);  // exact product error
-      s = prod;
-      c = pe;
-    }
-  }
-  const int tid = threadIdx.y * BX + threadIdx.x;
-  ss[tid] = s;
-  sc[tid] = c;
-  __syncthreads();
-  for (int st = BX * BY / 2; st > 0; st >>= 1) {
-    if (tid < st) {
-      double a = ss[tid], ac = sc[tid];
-      dd_add(a, ac, ss[tid + st], sc[tid + st]);
-      ss[tid] = a;
-      sc[tid] = ac;
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    const long long bid = base + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    part[2 * bid] = ss[0];
-    part[2 * bid + 1] = sc[0];
-  }
-}
-
-// Grid-stride variant with a fixed number of blocks per level (deterministic: the cell
-// each thread visits depends only on the launch shape): partial part[2*(base+block)].
+// Compensated, deterministic partial sums of w * x over the valid interior cells of one
+// level, grid-stride with a fixed number of blocks per level (the cell each thread visits
+// depends only on the launch shape): one double-double partial part[2*(base+block)].
 template <int D>
 __global__ void __launch_bounds__(256) k_wsum_gs(LevelView lv, const double* __restrict__ x,
                                                  const unsigned char* __restrict__ vmask, double w,

@@ -1,11 +1,12 @@
 // libamr4 orchestration and C-ABI entry points: composite operators (COH-1..4), the
-// composite V-cycle (Sec. 6.4), solves with the max-norm stopping test (Sec. 7), the
-// solvability fix (Sec. 6.3), the composite projection (Eq. comp_ProjOp) and FP32 V-cycles
+// composite V-cycle (Sec. 6.5), solves with the max-norm stopping test (Sec. 7), the
+// solvability fix (Sec. 6.4), the composite projection (Eq. comp_ProjOp) and FP32 V-cycles
 // inside FP64 iterative refinement.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -89,6 +90,12 @@ namespace {
       set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
       return AMR_ERR_CUDA;                                                            \
     }                                                                                 \
+  } while (0)
+
+#define TRY(...)                         \
+  do {                                   \
+    amr_status s_ = (__VA_ARGS__);       \
+    if (s_ != AMR_OK) return s_;         \
   } while (0)
 
 std::atomic<long long> g_launches{0};  // kernels launched by this library (host count)
@@ -320,18 +327,29 @@ inline bool zc_eligible(const LevelView& lv, int R) {
   return px * (lv.maxn[1] + 2 * NG) * (lv.maxn[2] + 2 * NG) < (1LL << 31);
 }
 
-// one full wave of the z-chunked 3-D kernel: resident blocks per SM x SMs (queried once)
+// One full wave of a kernel on the current device: resident blocks per SM (for the given
+// block size and dynamic shared memory) times the device's SM count, queried once per
+// (device, kernel) pair.
+int wave_blocks(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, kernel});
+  if (it != cache.end()) return it->second;
+  int nsm = 0, per = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  const int blocks = std::max(1, std::max(1, nsm) * std::max(1, per));
+  cache[{dev, kernel}] = blocks;
+  return blocks;
+}
+
+// one full wave of the z-chunked 3-D kernel
 template <typename T, int M, int R>
 int zc_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, nsm = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_level_op3d_zc<T, M, R>, ZC_TX * ZC_TY, 0);
-    blocks = std::max(1, nsm * std::max(1, per));
-  }
-  return blocks;
+  return wave_blocks(reinterpret_cast<const void*>(k_level_op3d_zc<T, M, R>), ZC_TX * ZC_TY, 0);
 }
 
 // z chunks of the 3-D kernel: as many as one wave holds, at least 4 planes each
@@ -353,30 +371,23 @@ std::atomic<int> g_fx_resid{1};  // amr_set_fx_residual
 inline bool fx_eligible(const LevelView& lv) {
   return lv.fxs != nullptr && g_fx_resid.load(std::memory_order_relaxed) != 0 && zc_eligible(lv, 2);
 }
-int fx_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, nsm = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid3d_fx, ZC_TX * ZC_TY, 0);
-    blocks = std::max(1, nsm * std::max(1, per));
-  }
-  return blocks;
-}
+int fx_blocks() { return wave_blocks(reinterpret_cast<const void*>(k_resid3d_fx), ZC_TX * ZC_TY, 0); }
 amr_status launch_resid_fx(const LevelView& lv, const double* x, const double* f, double* out, double alpha,
                            double beta, cudaStream_t st) {
   CK(cudaMemsetAsync(lv.fxs, 0, 2 * sizeof(unsigned long long), st));
   const long long rows = (long long)lv.maxn[1] * lv.maxn[2];
-  launch(k_absmax_patch, (unsigned)std::min<long long>(rows, 152LL * 8), 256, 0, st, lv, x, lv.fxs);
+  const int amax_blocks = wave_blocks(reinterpret_cast<const void*>(k_absmax_patch), 256, 0);
+  launch(k_absmax_patch, (unsigned)std::min<long long>(rows, amax_blocks), 256, 0, st, lv, x, lv.fxs);
+  TRY(launch_check());
   const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * 2)), nz = lv.maxn[2];
   const int nch = std::max(1, std::min(fx_blocks() / ntiles, nz / 4));
   const int kc = (nz + nch - 1) / nch;
   const int G = ntiles * ((nz + kc - 1) / kc);
   launch(k_resid3d_fx, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, alpha, beta);
+  TRY(launch_check());
   launch_zc<double, OP_RESID, 2>(lv, x, f, out, alpha, beta, 0.0, nullptr, st,
                                  reinterpret_cast<const unsigned*>(lv.fxs + 1));
-  return AMR_OK;
+  return launch_check();
 }
 
 template <typename T, int D, bool TR = false>
@@ -593,11 +604,6 @@ amr_status convert(const LevelView& lv, const S* x, T* y, cudaStream_t st) {
   return launch_check();
 }
 
-#define TRY(...)                         \
-  do {                                   \
-    amr_status s_ = (__VA_ARGS__);       \
-    if (s_ != AMR_OK) return s_;         \
-  } while (0)
 
 }  // namespace
 
@@ -1482,6 +1488,25 @@ amr_status maxnorm(amr_hierarchy* h, const T* x, bool use_mask, double* out_host
   return AMR_OK;
 }
 
+// Blocks of the grid-stride weighted sum of one level (k_wsum_gs): one per 256 cells, at
+// most 512; the partials are added in this fixed order, so a given hierarchy always gets
+// the same rounding.
+inline long long wsum_blocks(const LevelView& lv) {
+  return std::min<long long>(512, std::max<long long>(1, ((long long)lv.ncells + 255) / 256));
+}
+
+// The weighted sums keep one partial per block in the hierarchy's 8192-slot scratch: a
+// hierarchy that needs more is rejected before anything is launched.
+inline amr_status wsum_fits(amr_hierarchy* h) {
+  long long nb = 0;
+  for (int l = 0; l < h->L; ++l) nb += wsum_blocks(level_view(h, l, nullptr));
+  if (nb > 8192) {
+    set_error("reduction scratch too small: the hierarchy needs " + std::to_string(nb) + " reduction blocks (8192 max)");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return AMR_OK;
+}
+
 // d_out[0] = sum over valid cells of h^D x (compensated); d_out[1] = boundary flux sum
 template <int D>
 amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* bc_types, double* d_out,
@@ -1489,7 +1514,7 @@ amr_status wsum(amr_hierarchy* h, const double* x, const double* bc, const int* 
   long long base = 0;
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, nullptr);
-    const long long nb = std::min<long long>(512, std::max<long long>(1, ((long long)lv.ncells + 255) / 256));
+    const long long nb = wsum_blocks(lv);
     if (base + nb > 8192) {
       set_error("reduction scratch too small");
       return AMR_ERR_INVALID_ARG;
@@ -1547,6 +1572,7 @@ amr_status shift_all(amr_hierarchy* h, double* x, const double* d_m, bool valid_
 template <int D>
 amr_status solvability_fix_impl(amr_operator* op, double* f, const double* bc, double* m_host, cudaStream_t st) {
   amr_hierarchy* h = op->h;
+  TRY(wsum_fits(h));
   TRY(wsum<D>(h, f, bc, op->bc, h->d_scalar + 2, st));
   launch(k_mean_from_sums, 1, 1, 0, st, h->d_scalar + 2, h->d_scalar + 3, op->beta, valid_volume(h), h->d_scalar + 4);
   TRY(launch_check());
@@ -1561,6 +1587,7 @@ amr_status solvability_fix_impl(amr_operator* op, double* f, const double* bc, d
 
 template <int D>
 amr_status mean_zero_impl(amr_hierarchy* h, double* x, double* mean_host, cudaStream_t st) {
+  TRY(wsum_fits(h));
   TRY(avgdown_all<D>(h, x, st));
   TRY(wsum<D>(h, x, nullptr, nullptr, h->d_scalar + 2, st));
   launch(k_mean_from_sums, 1, 1, 0, st, h->d_scalar + 2, nullptr, 0.0, valid_volume(h), h->d_scalar + 4);
@@ -1575,10 +1602,11 @@ amr_status mean_zero_impl(amr_hierarchy* h, double* x, double* mean_host, cudaSt
 }
 
 // Transpose of the pure-Neumann projector F = I - 1 w^T/(w^T 1) (w = h^D on valid cells; F
-// is both the solvability correction of Sec. 6.3 with homogeneous data and the mean-zero
+// is both the solvability correction of Sec. 6.4 with homogeneous data and the mean-zero
 // step): x <- x - w (1^T x)/(1^T w) on the valid cells.
 template <int D>
 amr_status neumann_fix_T(amr_hierarchy* h, double* x, double* m_host, cudaStream_t st) {
+  TRY(wsum_fits(h));
   TRY(wsum<D>(h, x, nullptr, nullptr, h->d_scalar + 2, st, true));
   launch(k_mean_from_sums, 1, 1, 0, st, h->d_scalar + 2, nullptr, 0.0, valid_volume(h), h->d_scalar + 4);
   TRY(launch_check());
@@ -1706,7 +1734,19 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
 // One V-cycle iteration of the solve loop (V-cycle on op->Res, phi += correction, new
 // residual and its norm), all stream-ordered on st; used inside the captured while-body.
 // grid of the whole-array passes: grid-stride, a few blocks per SM
-inline unsigned flat_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8); }
+// grid-stride element-wise kernels: one block per 256 elements, at most 8 per SM
+inline unsigned flat_blocks(long long n) {
+  static int nsm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int m = (dev >= 0 && dev < 64) ? nsm[dev] : 0;
+  if (m == 0) {
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    m = std::max(1, m);
+    if (dev >= 0 && dev < 64) nsm[dev] = m;
+  }
+  return (unsigned)std::min<long long>((n + 255) / 256, 8LL * m);
+}
 
 // valid-cell max-norm of op->Res into *acc, and (mixed precision) its FP32 copy into rin
 inline amr_status norm_convert(amr_operator* op, int prec, unsigned long long* acc, cudaStream_t st) {
@@ -2590,7 +2630,9 @@ double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once per device
 // with that device current (the host-side name is only a stand-in for the device symbol).
-amr_status noalloc_scratch(double** out) {
+// The lookup may initialise the module on that device, which a stream capture does not
+// allow, so a first call on a device whose stream is capturing is refused.
+amr_status noalloc_scratch(double** out, cudaStream_t st) {
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
@@ -2599,6 +2641,13 @@ amr_status noalloc_scratch(double** out) {
   }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (g_noalloc_addr[dev] == nullptr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      set_error("amr_mean_zero_noalloc: the first call on a device must come before any stream capture (it "
+                "looks up the scratch array's device address)");
+      return AMR_ERR_INVALID_ARG;
+    }
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -2611,32 +2660,32 @@ amr_status noalloc_scratch(double** out) {
   return AMR_OK;
 }
 
+// The same launches as mean_zero_impl (average-down, k_wsum_gs with the wsum() block count
+// per level, k_dd_final, k_mean_from_sums, shift), so the mean and the shifted field are
+// bitwise those of amr_mean_zero; only the partials and scalars live in the fixed array.
 template <int D>
 amr_status mean_zero_noalloc_impl(amr_hierarchy* h, double* x, double* mean_host, cudaStream_t st) {
   // size check before anything is launched
   long long nblocks = 0;
-  for (int l = 0; l < h->L; ++l) {
-    Geo g = geo_of(level_view(h, l, nullptr));
-    nblocks += (long long)g.grid.x * g.grid.y * g.grid.z;
-  }
+  for (int l = 0; l < h->L; ++l) nblocks += wsum_blocks(level_view(h, l, nullptr));
   if (nblocks > NOALLOC_MAX_PARTIALS) {
     set_error("amr_mean_zero_noalloc: hierarchy needs " + std::to_string(nblocks) +
               " reduction blocks, more than the fixed scratch holds (" + std::to_string(NOALLOC_MAX_PARTIALS) + ")");
     return AMR_ERR_INVALID_ARG;
   }
   double* scratch = nullptr;
-  TRY(noalloc_scratch(&scratch));
+  TRY(noalloc_scratch(&scratch, st));
   double* part = scratch;
   double* sums = scratch + 2 * NOALLOC_MAX_PARTIALS;  // [0] weighted sum, [2] mean
   TRY(avgdown_all<D>(h, x, st));
   long long base = 0;
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, nullptr);
-    Geo g = geo_of(lv);
+    const long long nb = wsum_blocks(lv);
     // every block writes its own partial slot, so no slot needs clearing first
-    launch(k_wsum<D>, g.grid, g.block, 0, st, lv, g.nby, x, h->d_valid, std::pow(lv.h, D), part, base);
+    launch(k_wsum_gs<D>, (unsigned)nb, 256, 0, st, lv, x, h->d_valid, std::pow(lv.h, D), part, base);
     TRY(launch_check());
-    base += (long long)g.grid.x * g.grid.y * g.grid.z;
+    base += nb;
   }
   launch(k_dd_final, 1, 256, 0, st, part, base, sums);
   TRY(launch_check());
@@ -3035,6 +3084,42 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
     if (sk != AMR_OK && worst == AMR_OK) worst = sk;
   }
   return worst;
+}
+
+amr_status amr_batch_solve_host(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi_host,
+                                const double* const* f_host, amr_solve_stats* stats, int* status, void* stream) {
+  if (!ops || n < 0 || !phi_host || !f_host) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(check_params(p));
+  for (int k = 0; k < n; ++k) {
+    TRY(check_op(ops[k]));
+    if (!phi_host[k] || !f_host[k]) { set_error("null field in batch"); return AMR_ERR_INVALID_ARG; }
+    for (int j = 0; j < k; ++j)
+      if (ops[j] == ops[k]) { set_error("an operator appears twice in a host-buffer batch"); return AMR_ERR_INVALID_ARG; }
+  }
+  cudaStream_t st = S(stream);
+  std::vector<double*> dphi(n);
+  std::vector<const double*> df(n);
+  for (int k = 0; k < n; ++k) {
+    amr_operator* op = ops[k];
+    if (!op->hphi) TRY(dalloc(&op->hphi, op->h->nelems));
+    if (!op->hf) TRY(dalloc(&op->hf, op->h->nelems));
+  }
+  for (int k = 0; k < n; ++k) {
+    amr_operator* op = ops[k];
+    const size_t bytes = (size_t)op->h->nelems * sizeof(double);
+    CK(cudaMemcpyAsync(op->hf, f_host[k], bytes, cudaMemcpyHostToDevice, st));
+    if (!p->zero_initial) CK(cudaMemcpyAsync(op->hphi, phi_host[k], bytes, cudaMemcpyHostToDevice, st));
+    dphi[k] = op->hphi;
+    df[k] = op->hf;
+  }
+  const amr_status s = amr_batch_solve(ops, n, p, dphi.data(), df.data(), stats, status, stream);
+  if (s != AMR_OK && s != AMR_ERR_NOT_CONVERGED) return s;
+  for (int k = 0; k < n; ++k) {
+    const size_t bytes = (size_t)ops[k]->h->nelems * sizeof(double);
+    CK(cudaMemcpyAsync(phi_host[k], ops[k]->hphi, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return s;
 }
 
 amr_status amr_solvability_fix(amr_operator* op, double* f, const double* bc, double* m, void* stream) {

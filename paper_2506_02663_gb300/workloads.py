@@ -129,8 +129,11 @@ def ms2d(n):
 
 
 # ----------------------------------------------------------------------------- bumps
-def bump_params(workload_id, nbumps=8, dim=2):
-    g = rng(workload_id)
+def bump_params(workload_id, nbumps=8, dim=2, component=0):
+    """Centres, widths and amplitudes of the bumps; ``component`` > 0 draws an independent
+    set (seeded by (SEED0 + workload_id, component)) for the other right-hand sides of one
+    workload, e.g. the velocity components' Helmholtz systems."""
+    g = rng(workload_id) if component == 0 else np.random.default_rng([SEED0 + workload_id, component])
     c = g.uniform(0.0, 1.0, size=(nbumps, dim))
     w = g.uniform(0.03, 0.1, size=nbumps)
     a = g.standard_normal(nbumps)
@@ -175,9 +178,11 @@ def bumps2d_rhs(scale=1):
     return dim, n0, boxes, level_rhs(lambda h, o, s: bumps_cell_averages(p, h, o, s), dim, n0, boxes)
 
 
-def bumps3d_rhs(scale=1):
+def bumps3d_rhs(scale=1, component=0):
+    """Right-hand side of the 3-D workload: component 0 for the pressure Poisson equation,
+    1..3 for the three velocity components' Helmholtz systems (independent bump sets)."""
     dim, n0, boxes = hierarchy_boxes("bumps3d", scale)
-    p = bump_params(5, 8, 3)
+    p = bump_params(5, 8, 3, component)
     return dim, n0, boxes, level_rhs(lambda h, o, s: bumps_cell_averages(p, h, o, s), dim, n0, boxes)
 
 

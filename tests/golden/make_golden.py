@@ -9,9 +9,16 @@ n = 16, 32, 64, 128 (the fourth-order claim of Sec. 3).
 
 amr2d.json: the bench's two-level workload at 1/8 size (32^2 base, ratio-2 box over
 [0.25, 0.75]^2, Gaussian-bump right-hand side): the composite discrete solution of the
-pure-Neumann PPE after the solvability fix and mean-zero (Sec. 6.3), and of the Helmholtz
+pure-Neumann PPE after the solvability fix and mean-zero (Sec. 6.4), and of the Helmholtz
 system alpha = 1, beta = -0.25 * 1e-3 / 256 with homogeneous Dirichlet data (Eq. comp. of
-Sec. 5 with AMRCFI ghosts and refluxing), at 24 seeded valid cells of each level."""
+Sec. 5 with AMRCFI ghosts and refluxing), at 24 seeded valid cells of each level.
+
+amr3d.json: the 3-D workload at 1/8 size (32^3 base, ratio-2 box over [0.375, 0.625]^3,
+i.e. 16^3 fine cells, Gaussian-bump right-hand sides): the composite discrete solution of
+the pure-Neumann PPE (right-hand side component 0) after the solvability fix and mean-zero,
+and of the Helmholtz system of velocity component 1 (alpha = 1, beta = -0.25 * 1e-3 / 256,
+homogeneous Dirichlet), at 24 seeded valid cells of each level.  Each direct solve takes a
+few minutes: ``python tests/golden/make_golden.py amr3d`` writes this file alone."""
 import json
 import math
 import os
@@ -89,6 +96,38 @@ def amr2d():
     res = {"source": "oracle.solve.solve_direct (+ solvability_fix, mean_zero) on workloads.bumps2d_rhs(scale=8); "
                      "written by tests/golden/make_golden.py",
            "n0": list(n0), "boxes": boxes}
+    _write_samples(res, sols, g, "amr2d.json")
+
+
+def amr3d_solutions():
+    out = {}
+    for name, comp, bc, alpha, beta in (("ppe", 0, [1] * 6, 0.0, 1.0),
+                                        ("helmholtz", 1, [0] * 6, 1.0, wl.HELMHOLTZ_BETA)):
+        dim, n0, boxes, rhs = wl.bumps3d_rhs(scale=8, component=comp)
+        H = Hierarchy(dim, n0, boxes, bc=bc)
+        F = cp.new_field(H)
+        for l, lev in enumerate(H.levels):
+            for k, (lo, hi) in enumerate(lev.boxes):
+                F[l][lev.box_slice(lo, hi)] = rhs[l][k]
+        if so.is_pure_neumann(H, alpha):
+            F, _ = so.solvability_fix(H, F)
+        phi, _, _ = so.solve_direct(H, F, alpha, beta)
+        if so.is_pure_neumann(H, alpha):
+            phi, _ = so.mean_zero(H, phi)
+        out[name] = (H, phi)
+    return (dim, n0, boxes), out
+
+
+def amr3d():
+    (dim, n0, boxes), sols = amr3d_solutions()
+    g = np.random.default_rng(20250603 + 5)
+    res = {"source": "oracle.solve.solve_direct (+ solvability_fix, mean_zero) on workloads.bumps3d_rhs(scale=8, "
+                     "component=0 for the PPE, 1 for the Helmholtz system); written by tests/golden/make_golden.py",
+           "n0": list(n0), "boxes": boxes}
+    _write_samples(res, sols, g, "amr3d.json")
+
+
+def _write_samples(res, sols, g, fname):
     for name, (H, phi) in sols.items():
         samples = []
         for l, lev in enumerate(H.levels):
@@ -97,10 +136,14 @@ def amr2d():
             samples += [[l] + [int(v) for v in c] + [float(phi[l][tuple(c)])] for c in pick]
         res[name] = {"samples_level_index_value": samples,
                      "max_abs": float(max(np.max(np.abs(phi[l][lev.valid])) for l, lev in enumerate(H.levels)))}
-    with open(os.path.join(HERE, "amr2d.json"), "w") as fh:
+    with open(os.path.join(HERE, fname), "w") as fh:
         json.dump(res, fh, indent=1)
-    print("wrote amr2d.json")
+    print("wrote", fname)
 
 
 if __name__ == "__main__":
-    main()
+    if sys.argv[1:] == ["amr3d"]:
+        amr3d()
+    else:
+        main()
+        amr3d()

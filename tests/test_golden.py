@@ -37,7 +37,7 @@ AMR2D = json.load(open(os.path.join(HERE, "golden", "amr2d.json")))
 
 def test_oracle_reproduces_amr2d_golden_values():
     """The two-level composite solves (coarse-fine ghosts of Sec. 5.2, refluxing, the
-    solvability fix and mean-zero of Sec. 6.3) still give the stored values."""
+    solvability fix and mean-zero of Sec. 6.4) still give the stored values."""
     (_, n0, boxes), sols = make_golden.amr2d_solutions()
     assert list(n0) == AMR2D["n0"]
     assert json.loads(json.dumps(boxes)) == AMR2D["boxes"]

@@ -171,8 +171,10 @@ def test_projection_chain_gradient_vs_dense_and_fd(name):
 
 def test_projection_chain_full_size_fd():
     """The adjoint2d workload at full size (base 256^2, boxes [0.2,0.8]^2 and [0.35,0.65]^2
-    -> 308^2 and 308^2 fine cells; seeded smoothed N(0,1) forcing, two components):
-    directional derivatives of J from the adjoint agree with central differences to 1e-6."""
+    -> 308^2 and 308^2 fine cells; seeded smoothed N(0,1) forcing, two components): the
+    directional derivative of J from the adjoint agrees with central differences (eps =
+    1e-3) to 1e-6 along 64 seeded random unit directions.  J is quadratic in g, so the
+    central difference is exact up to rounding and the solve tolerance."""
     amr = _amr()
     from oracle.hierarchy import Hierarchy as OH
     from paper_2506_02663_gb300 import workloads as wl
@@ -191,11 +193,15 @@ def test_projection_chain_full_size_fd():
     grads = [x.grad.detach() for x in g]
     rng = np.random.default_rng(229)
     eps = 1e-3
-    for _ in range(2):
+    errs = []
+    for _ in range(64):
         v = [mask * torch.from_numpy(rng.standard_normal(gh.nelems)).cuda() for _ in range(dim)]
+        nrm = float(torch.sqrt(sum(torch.sum(vd * vd) for vd in v)))
+        v = [vd / nrm for vd in v]
         with torch.no_grad():
             jp = J([x.detach() + eps * vd for x, vd in zip(g, v)])
             jm = J([x.detach() - eps * vd for x, vd in zip(g, v)])
         fd = float((jp - jm) / (2 * eps))
         adj = float(sum(torch.sum(gd * vd) for gd, vd in zip(grads, v)))
-        assert abs(fd - adj) <= 1e-6 * abs(fd), (fd, adj)
+        errs.append(abs(fd - adj) / abs(fd))
+    assert max(errs) <= 1e-6, (max(errs), len(errs))

@@ -110,3 +110,42 @@ def test_worklist_batch_large_tiles():
         st = op.solve(x, f, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=amr.MIXED, use_graph=1))
         assert st["vcycles"] == stats[k]["vcycles"]
         assert torch.max(torch.abs(x - phis[k])).item() <= 1e-13 * torch.max(torch.abs(x)).item()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_solve_host_matches_device_batch(precision):
+    """amr_batch_solve_host (host buffers, copies inside the call) gives the device batch's
+    solutions and statistics, on both batch paths: single-level 2-D problems (work list) and
+    two-level 3-D problems (concurrent captured solves)."""
+    from paper_2506_02663_gb300 import amr, workloads as wl
+    p = amr.default_params(rtol=1e-12, max_vcycles=100, precision=precision)
+    cases = []
+    probs = wl.batch2d_problems(nprob=4, sizes=(64, 96))
+    for pr in probs:
+        n = pr["n"]
+        gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+        cases.append((gh, amr.Operator(gh, pr["alpha"], pr["beta"] * 256.0, [0, 0, 0, 0]), gh.pack([[pr["rhs"]]])))
+    for comp in (1, 2):
+        dim, n0, boxes, rhs = wl.bumps3d_rhs(scale=8, component=comp)
+        gh = amr.Hierarchy(dim, n0, boxes)
+        cases.append((gh, amr.Operator(gh, 1.0, -0.01, [0] * 6), gh.pack(rhs)))
+    for group in (cases[:4], cases[4:]):
+        ops = [c[1] for c in group]
+        fs = [torch.from_numpy(c[2]).cuda() for c in group]
+        phis = [torch.zeros_like(f) for f in fs]
+        st_d, status_d = amr.batch_solve(ops, phis, fs, params=p)
+        fh = [torch.from_numpy(c[2]).pin_memory().numpy() for c in group]
+        ph = [np.zeros_like(c[2]) for c in group]  # pageable
+        for _ in range(2):  # the second call reuses the operators' device buffers
+            st_h, status_h = amr.batch_solve_host(ops, ph, fh, params=p)
+            assert status_h == status_d and all(s == 0 for s in status_h)
+            for k in range(len(group)):
+                assert st_h[k]["vcycles"] == st_d[k]["vcycles"]
+                ref = phis[k].cpu().numpy()
+                assert np.max(np.abs(ph[k] - ref)) <= 1e-13 * np.max(np.abs(ref))
+    with pytest.raises(amr.AmrError) as ei:
+        amr.batch_solve_host([cases[0][1], cases[0][1]], [np.zeros_like(cases[0][2])] * 2, [cases[0][2]] * 2, params=p)
+    assert ei.value.status == amr.AMR_ERR_INVALID_ARG
+    for gh, op, _ in cases:
+        op.close()
+        gh.close()

@@ -7,7 +7,7 @@
   exact Laplacian on every valid cell, near the physical boundary too (clipped windows).
 * Pure Neumann: the composite operator annihilates constants and its columns sum to zero
   with the h^D weights (refluxing telescopes the fluxes: the discrete form of the
-  solvability condition of Sec. 6.3).
+  solvability condition of Sec. 6.4).
 * Assembly by coloured probing equals brute-force assembly by unit vectors.
 """
 import itertools
