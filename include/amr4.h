@@ -361,12 +361,18 @@ long long amr_kernel_launches(void);
  * launching stream (0 stops recording).  amr_profile_read() synchronises on the recorded
  * events and returns, for one class, the number of launches, the summed event intervals
  * (ms) and the summed algorithmic bytes.  Classes: 0 weighted-Jacobi sweeps, 1 level
- * residual / apply, 2 restriction and average-down, 3 prolongation, 4 temporally blocked
- * down legs (f read, x and the coarse f written once), 5 temporally blocked up legs (x, f
- * and the coarse correction read once, x written once), 6 one-block coarse V-cycles (f
- * read, x written once). */
+ * residual / apply (FP32; FP64 applications), 2 restriction and average-down, 3
+ * prolongation, 4 temporally blocked down legs (f read, x and the coarse f written once),
+ * 5 temporally blocked up legs (x, f and the coarse correction read once, x written once),
+ * 6 one-block coarse V-cycles (f read, x written once), 7 FP64 level residuals (the
+ * refinement loop's residual: x, f read, r written). */
 amr_status amr_profile_enable(int on);
 amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes);
+/* The same sums over the launches of one class whose grid has between min_cells and
+ * max_cells cells (inclusive; level operators, sweeps and residuals record their grid's cell
+ * count, other classes record 0). */
+amr_status amr_profile_read_range(int kernel_class, double min_cells, double max_cells, long long* launches,
+                                  double* total_ms, double* total_bytes);
 /* Tile shape of the tiled level-operator kernels (not in the paper: a tuning and testing
  * control).  rows = 0 (the default) uses the autotuner's choice per grid; rows = 1, 2 or 4
  * forces that many cells per thread along y in the 2-D kernel, rows = 2 or 4 in the 3-D
@@ -385,6 +391,22 @@ amr_status amr_set_tile_rows(int rows);
  * this GPU FP64 arithmetic runs at a small fraction of the integer rate.  on = 0: the plain
  * FP64 kernel always.  Process-wide; AMR_ERR_INVALID_ARG for any other value. */
 amr_status amr_set_fx_residual(int on);
+/* 3-D level operator of single-patch levels whose x extent is a multiple of 64 cells and whose
+ * y extent is a multiple of 16 (not in the paper: a kernel choice for this GPU).  The
+ * weighted-Jacobi sweeps, residuals and operator applications of such levels can run in a
+ * kernel whose planes of x and f are streamed into shared memory by tensor-map TMA copies
+ * (a producer thread, a warp that writes the physical ghost values into the staged planes,
+ * consumer warps; a ring of slots with mbarriers), or in the z-chunked register-prefetch
+ * kernel; both evaluate the same operations per cell.  on = 1 (the default): the tile
+ * autotuner times both on every such grid and keeps the faster; on = 2: the bulk-copy kernel
+ * wherever eligible; on = 0: never.  Process-wide; AMR_ERR_INVALID_ARG for any other value. */
+amr_status amr_set_bulk_sweep(int on);
+/* The bulk-copy 3-D kernel bounds every wait on its shared-memory pipeline; a wait that runs
+ * out sets a device flag (the kernel then stops without writing its remaining cells).  This
+ * call reads and clears the flag: AMR_ERR_CUDA if it was set since the last check, else
+ * AMR_OK.  Solves check it when they finish (amr_solve and amr_batch_solve return
+ * AMR_ERR_CUDA). */
+amr_status amr_check_kernel_flags(void);
 
 #ifdef __cplusplus
 }

@@ -95,7 +95,10 @@ _sigs = {
     "amr_profile_enable": [C.c_int],
     "amr_set_tile_rows": [C.c_int],
     "amr_set_fx_residual": [C.c_int],
+    "amr_set_bulk_sweep": [C.c_int],
+    "amr_check_kernel_flags": [],
     "amr_profile_read": [C.c_int, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
+    "amr_profile_read_range": [C.c_int, C.c_double, C.c_double, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
 }
 for _n, _a in _sigs.items():
     _f = getattr(_lib, _n)
@@ -112,7 +115,7 @@ def kernel_launches():
     return int(_lib.amr_kernel_launches())
 
 
-KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG, KC_DOWN, KC_UP, KC_COARSE = 0, 1, 2, 3, 4, 5, 6
+KC_JACOBI, KC_RESID, KC_RESTRICT, KC_PROLONG, KC_DOWN, KC_UP, KC_COARSE, KC_RESID64 = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def set_tile_rows(rows):
@@ -127,6 +130,18 @@ def set_fx_residual(on):
     _check(_lib.amr_set_fx_residual(int(on)), "amr_set_fx_residual")
 
 
+def set_bulk_sweep(on):
+    """3-D single-patch levels with x extents a multiple of 64 and y extents a multiple of 16:
+    1 (default) the autotuner picks the bulk-copy (TMA) or the z-chunked level operator per
+    grid; 2 always the bulk-copy kernel; 0 never."""
+    _check(_lib.amr_set_bulk_sweep(int(on)), "amr_set_bulk_sweep")
+
+
+def check_kernel_flags():
+    """Raises AmrError if a bounded pipeline wait of the 3-D kernel ran out since the last check."""
+    _check(_lib.amr_check_kernel_flags(), "amr_check_kernel_flags")
+
+
 def profile_enable(on):
     _check(_lib.amr_profile_enable(1 if on else 0), "amr_profile_enable")
 
@@ -136,6 +151,16 @@ def profile_read(kernel_class):
     ms = C.c_double()
     by = C.c_double()
     _check(_lib.amr_profile_read(kernel_class, C.byref(n), C.byref(ms), C.byref(by)), "amr_profile_read")
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
+def profile_read_range(kernel_class, min_cells, max_cells):
+    """Sums over the recorded launches of one class on grids of min_cells..max_cells cells."""
+    n = C.c_longlong()
+    ms = C.c_double()
+    by = C.c_double()
+    _check(_lib.amr_profile_read_range(kernel_class, float(min_cells), float(max_cells), C.byref(n), C.byref(ms),
+                                       C.byref(by)), "amr_profile_read_range")
     return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
 EXPORTED = tuple(_sigs)

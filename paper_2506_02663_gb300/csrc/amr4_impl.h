@@ -45,6 +45,9 @@ struct LevelView {
   // device scratch of the fixed-point FP64 residual (two words: largest |x| as IEEE bits,
   // out-of-frame flag); null for views that are not a hierarchy level
   unsigned long long* fxs;
+  // host-side copy of the first patch (the only one of a single-patch level): kernels fed by
+  // tensor-map copies need its offset and strides on the host
+  PatchDesc p0;
 };
 
 void finish_view(LevelView& v);  // fills the precomputed constants from h and bc

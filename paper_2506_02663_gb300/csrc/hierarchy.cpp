@@ -652,6 +652,7 @@ LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types) {
     v.bc_pitch[f] = (f < 2 * h->D && lead >= 0) ? L.ndom[lead] : 1;
   }
   v.fxs = h->d_scalar ? reinterpret_cast<unsigned long long*>(h->d_scalar + 8) : nullptr;
+  v.p0 = L.patches.front();
   finish_view(v);
   return v;
 }

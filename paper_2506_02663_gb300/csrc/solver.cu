@@ -13,10 +13,12 @@
 #include <utility>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "amr4_impl.h"
 #include "kernels.cuh"
+#include "sweep3d.cuh"
 
 using namespace amr4;
 
@@ -132,6 +134,28 @@ inline amr_status launch_check() {
   return AMR_OK;
 }
 
+// Bulk-copy 3-D sweep (k_sweep3d) on single-patch levels whose x extent is a multiple of 64
+// and y extent a multiple of the tile height.  amr_set_bulk_sweep: 0 never, 1 (default) where
+// the tile autotuner finds it fastest, 2 wherever eligible.
+std::atomic<int> g_bulk_sweep{1};
+#ifndef SW_TILE_Y
+#define SW_TILE_Y 16
+#endif
+#ifndef SW_ROWS_PER_WARP
+#define SW_ROWS_PER_WARP 2
+#endif
+#ifndef SW_STAGES
+#define SW_STAGES 8
+#endif
+constexpr int SW_TY = SW_TILE_Y, SW_RW = SW_ROWS_PER_WARP, SW_S = SW_STAGES, SW_MINZ = 8;
+inline bool sw_eligible(const LevelView& lv) {
+  if (g_bulk_sweep.load(std::memory_order_relaxed) == 0 || lv.D != 3 || lv.npatch != 1) return false;
+  if (lv.maxn[0] % sw3::TX != 0 || lv.maxn[1] % SW_TY != 0 || lv.maxn[2] < 4) return false;
+  const long long px = ((lv.maxn[0] + 2 * NG) + 3) / 4 * 4;
+  return px * (lv.maxn[1] + 2 * NG) * (lv.maxn[2] + 2 * NG) < (1LL << 31);
+}
+constexpr int TILE_BULK = 8;  // tile-table code of the bulk-copy 3-D kernel
+
 // ---------------------------------------------------------------- tile autotuner
 // Rows per thread of the tiled 2-D kernel and of the z-chunked 3-D kernel, per (dimension,
 // grid cells, value size): filled by autotune_tiles() (CUDA-event timing of each variant on
@@ -148,13 +172,17 @@ std::atomic<int> g_tile_force{0};  // amr_set_tile_rows: 0 = autotuned
 inline int tile_rows_for(const LevelView& lv, size_t tsize) {
   const int forced = g_tile_force.load(std::memory_order_relaxed);
   if (forced) return lv.D == 3 ? std::max(2, forced) : forced;
+  if (lv.D == 3 && g_bulk_sweep.load(std::memory_order_relaxed) == 2 && sw_eligible(lv)) return TILE_BULK;
   const long long key = tile_key(lv, tsize);
   {
     std::lock_guard<std::mutex> lock(g_tile_mu);
     for (const auto& e : g_tile_table)
       if (e.first == key) return e.second;
   }
-  if (lv.D == 3) return 2;
+  if (lv.D == 3) {
+    const int mode = g_bulk_sweep.load(std::memory_order_relaxed);
+    return (sw_eligible(lv) && (mode == 2 || lv.ncells >= 2097152.0)) ? TILE_BULK : 2;
+  }
   return lv.ncells >= 1024.0 * 1024.0 ? 4 : 1;
 }
 
@@ -168,11 +196,13 @@ inline float pick_host<float>(double, float f) { return f; }
 // ---------------------------------------------------------------- bench instrumentation
 // When enabled, launches of the instrumented kernel classes are bracketed with CUDA events
 // on the launching stream; amr_profile_read() sums the event intervals.
-enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_DOWN = 4, PC_UP = 5, PC_COARSE = 6, PC_NCLASS = 7 };
+enum { PC_JACOBI = 0, PC_RESID = 1, PC_RESTRICT = 2, PC_PROLONG = 3, PC_DOWN = 4, PC_UP = 5, PC_COARSE = 6, PC_RESID64 = 7,
+       PC_NCLASS = 8 };
 struct ProfRec {
   cudaEvent_t a, b;
   int cls;
   double bytes;
+  double cells;  // cells of the grid the launch worked on (0: not recorded)
 };
 struct Profiler {
   bool on = false;
@@ -196,11 +226,11 @@ inline void prof_begin(cudaStream_t st, cudaEvent_t* ev) {
   *ev = g_prof.get();
   cudaEventRecord(*ev, st);
 }
-inline void prof_end(cudaStream_t st, cudaEvent_t a, int cls, double bytes) {
+inline void prof_end(cudaStream_t st, cudaEvent_t a, int cls, double bytes, double cells = 0.0) {
   if (a == nullptr) return;
   cudaEvent_t b = g_prof.get();
   cudaEventRecord(b, st);
-  g_prof.recs.push_back({a, b, cls, bytes});
+  g_prof.recs.push_back({a, b, cls, bytes, cells});
 }
 
 template <typename T>
@@ -236,6 +266,7 @@ LevelView mg_view(const amr_hierarchy* h, int m, const int* bc) {
   for (int e = 0; e < 3; ++e) { v.ndom[e] = g.n[e]; v.maxn[e] = g.n[e]; }
   for (int f = 0; f < 6; ++f) { v.bc[f] = bc[f]; v.bc_off[f] = 0; v.bc_pitch[f] = 1; }
   v.ncells = (double)g.n[0] * g.n[1] * g.n[2];
+  v.p0 = g.patch;
   finish_view(v);
   return v;
 }
@@ -364,6 +395,101 @@ void launch_zc(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T 
          gate);
 }
 
+template <typename T, int M>
+constexpr auto sw_kernel() {
+  return k_sweep3d<T, M, SW_TY, SW_RW, SW_S>;
+}
+template <typename T>
+amr_status sw_attrs() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return AMR_OK;
+  CK(cudaFuncSetAttribute(sw_kernel<T, OP_APPLY>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sw3::smem_bytes<T, OP_APPLY, SW_TY, SW_S>()));
+  CK(cudaFuncSetAttribute(sw_kernel<T, OP_RESID>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sw3::smem_bytes<T, OP_RESID, SW_TY, SW_S>()));
+  CK(cudaFuncSetAttribute(sw_kernel<T, OP_JACOBI>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sw3::smem_bytes<T, OP_JACOBI, SW_TY, SW_S>()));
+  CK(cudaFuncSetAttribute(sw_kernel<T, OP_JACOBI0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sw3::smem_bytes<T, OP_JACOBI0, SW_TY, SW_S>()));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return AMR_OK;
+}
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+using TmapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeFn tmap_encoder() {
+  static std::once_flag once;
+  static TmapEncodeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmapEncodeFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a single-patch field over its padded patch (dimensions: row pitch, n_y + 4,
+// n_z + 4), boxes of 68 x rows x 1 values.
+template <typename T>
+amr_status encode_patch_tmap(CUtensorMap* tm, const T* field, const PatchDesc& p, int rows) {
+  const TmapEncodeFn enc = tmap_encoder();
+  if (enc == nullptr) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return AMR_ERR_CUDA;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)p.sy, (cuuint64_t)(p.n[1] + 2 * NG), (cuuint64_t)(p.n[2] + 2 * NG)};
+  const cuuint64_t strides[2] = {(cuuint64_t)p.sy * sizeof(T), (cuuint64_t)p.sz * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)sw3::XW, (cuuint32_t)rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r =
+      enc(tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+          const_cast<T*>(field + p.off), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return AMR_ERR_CUDA;
+  }
+  return AMR_OK;
+}
+
+// tiles of 64 x SW_TY cells; z chunks of at least SW_MINZ planes, as many as one wave holds
+template <typename T, int M>
+amr_status launch_sw(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T O, const unsigned char* vmask,
+                     cudaStream_t st, const unsigned* gate = nullptr) {
+  TRY(sw_attrs<T>());
+  constexpr size_t smem = sw3::smem_bytes<T, M, SW_TY, SW_S>();
+  constexpr int threads = 32 * (SW_TY / SW_RW + 2);
+  CUtensorMap tmx{}, tmf{};
+  if (M != OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmx, x, lv.p0, SW_TY + 4));
+  if (M != OP_APPLY) TRY(encode_patch_tmap<T>(&tmf, f, lv.p0, SW_TY));
+  const int ntx = lv.maxn[0] / sw3::TX, ntiles = ntx * (lv.maxn[1] / SW_TY), nz = lv.maxn[2];
+  const int wave = wave_blocks(reinterpret_cast<const void*>(sw_kernel<T, M>()), threads, smem);
+  const int nch = std::max(1, std::min(wave / ntiles, nz / SW_MINZ));
+  launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, out, A, B, O,
+         vmask, gate);
+  return launch_check();
+}
+
+// Clears and reports the flag that k_sweep3d sets when one of its bounded waits ran out.
+amr_status sweep3d_check_flag() {
+  unsigned v = 0u;
+  CK(cudaMemcpyFromSymbol(&v, g_sweep3d_err, sizeof(unsigned)));
+  if (v != 0u) {
+    const unsigned z = 0u;
+    CK(cudaMemcpyToSymbol(g_sweep3d_err, &z, sizeof(unsigned)));
+    set_error("a bounded pipeline wait of the 3-D sweep kernel ran out (results of that solve are invalid)");
+    return AMR_ERR_CUDA;
+  }
+  return AMR_OK;
+}
+
 // FP64 residual of a z-chunked level with the fixed-point stencil sums (k_resid3d_fx): the
 // frame from the level's largest interior |x|, the fixed-point pass, and the plain FP64
 // pass gated on the out-of-frame flag (it exits at once unless a value left the frame)
@@ -419,15 +545,32 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
     }
 #undef LAUNCH_TILED
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
-    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : (mode == OP_RESID && sizeof(T) == 8) ? PC_RESID64 : PC_RESID,
+             nb * sizeof(T) * lv.ncells, lv.ncells);
     return launch_check();
   }
   if constexpr (sizeof(T) == 8 && D == 3 && !TR) {
     if (mode == OP_RESID && bc == nullptr && vmask == nullptr && fx_eligible(lv)) {
       if (const amr_status s1 = launch_resid_fx(lv, x, f, out, alpha, beta, st); s1 != AMR_OK) return s1;
-      prof_end(st, ev, PC_RESID, 3.0 * sizeof(T) * lv.ncells);
+      prof_end(st, ev, PC_RESID64, 3.0 * sizeof(T) * lv.ncells, lv.ncells);
       return launch_check();
     }
+  }
+  if (D == 3 && !TR && bc == nullptr && (vmask == nullptr || mode == OP_RESID) && sw_eligible(lv) &&
+      tile_rows_for(lv, sizeof(T)) == TILE_BULK) {
+    const T A = T(alpha), B = T(beta), O = T(omega);
+    amr_status s1;
+    switch (mode) {
+      case OP_APPLY: s1 = launch_sw<T, OP_APPLY>(lv, x, f, out, A, B, O, vmask, st); break;
+      case OP_RESID: s1 = launch_sw<T, OP_RESID>(lv, x, f, out, A, B, O, vmask, st); break;
+      case OP_JACOBI: s1 = launch_sw<T, OP_JACOBI>(lv, x, f, out, A, B, O, vmask, st); break;
+      default: s1 = launch_sw<T, OP_JACOBI0>(lv, x, f, out, A, B, O, vmask, st);
+    }
+    if (s1 != AMR_OK) return s1;
+    const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : (mode == OP_RESID && sizeof(T) == 8) ? PC_RESID64 : PC_RESID,
+             nb * sizeof(T) * lv.ncells, lv.ncells);
+    return AMR_OK;
   }
   if (D == 3 && !TR && bc == nullptr && (vmask == nullptr || mode == OP_RESID) && zc_eligible(lv, 2)) {
     // z-chunked marching path; rows per thread from the autotuner's table
@@ -446,7 +589,8 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
     }
 #undef LAUNCH_ZC
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
-    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : (mode == OP_RESID && sizeof(T) == 8) ? PC_RESID64 : PC_RESID,
+             nb * sizeof(T) * lv.ncells, lv.ncells);
     return launch_check();
   }
   if (D == 3 && !TR && bc == nullptr) {
@@ -466,7 +610,8 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
       default: launch(k_level_op3d_march<T, OP_JACOBI0>, grid, block, 0, st, lv, nzc, kz, x, f, out, A, B, O, vmask);
     }
     const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
-    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+    prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : (mode == OP_RESID && sizeof(T) == 8) ? PC_RESID64 : PC_RESID,
+             nb * sizeof(T) * lv.ncells, lv.ncells);
     return launch_check();
   }
   switch (mode) {
@@ -485,7 +630,8 @@ amr_status level_op(int mode, const LevelView& lv, const T* x, const T* f, T* ou
   // algorithmic bytes: Jacobi reads x, f and writes the sweep (the first sweep reads f
   // only); residual reads x, f and writes r; apply reads x and writes the result
   const double nb = mode == OP_JACOBI0 ? 2.0 : (mode == OP_APPLY ? 2.0 : 3.0);
-  prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : PC_RESID, nb * sizeof(T) * lv.ncells);
+  prof_end(st, ev, (mode == OP_JACOBI || mode == OP_JACOBI0) ? PC_JACOBI : (mode == OP_RESID && sizeof(T) == 8) ? PC_RESID64 : PC_RESID,
+             nb * sizeof(T) * lv.ncells, lv.ncells);
   return launch_check();
 }
 
@@ -506,7 +652,7 @@ amr_status restrict_blocks(const LevelView& fine, const LevelView& crs, const Xf
   else
     launch(k_restrict<T, D, false>, grid, block, 0, st, fine, crs, blocks, xf, ff, outc, T(alpha), T(beta), nby);
   const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
-  prof_end(st, ev, PC_RESTRICT, ((resid ? 2.0 : 1.0) * (1 << D) + 1.0) * sizeof(T) * cc);
+  prof_end(st, ev, PC_RESTRICT, ((resid ? 2.0 : 1.0) * (1 << D) + 1.0) * sizeof(T) * cc, cc * (1 << D));
   return launch_check();
 }
 
@@ -547,7 +693,7 @@ amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const Xfe
     }
   }
   const double cc = (double)xmax[0] * xmax[1] * (D == 3 ? xmax[2] : 1) * nblocks;
-  prof_end(st, ev, PC_PROLONG, (1.0 + (1 << D) * (xf2 ? 4.0 : 2.0)) * sizeof(T) * cc);
+  prof_end(st, ev, PC_PROLONG, (1.0 + (1 << D) * (xf2 ? 4.0 : 2.0)) * sizeof(T) * cc, cc * (1 << D));
   return launch_check();
 }
 
@@ -766,7 +912,10 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
   CK(cudaEventCreate(&b));
   for (auto& c : cases) {
     const LevelView& lv = c.lv;
-    if (D == 3 && !zc_eligible(lv, 4)) continue;  // only the 2-row 3-D variant applies
+    std::vector<int> variants = D == 3 ? std::vector<int>{2} : std::vector<int>{1, 2, 4};
+    if (D == 3 && zc_eligible(lv, 4)) variants.push_back(4);
+    if (D == 3 && sw_eligible(lv)) variants.push_back(TILE_BULK);
+    if (variants.size() < 2) continue;  // nothing to choose
     const long long key = tile_key(lv, sizeof(T));
     {
       std::lock_guard<std::mutex> lock(g_tile_mu);
@@ -776,7 +925,6 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
     }
     float best = 1e30f;
     int best_rows = D == 3 ? 2 : 1;
-    const std::vector<int> variants = D == 3 ? std::vector<int>{2, 4} : std::vector<int>{1, 2, 4};
     for (int rows : variants) {
       {
         std::lock_guard<std::mutex> lock(g_tile_mu);
@@ -795,7 +943,8 @@ amr_status autotune_tiles(amr_operator* op, cudaStream_t st) {
         std::lock_guard<std::mutex> lock(g_tile_mu);
         g_tile_table.pop_back();
       }
-      // a larger tile must win by 5 %: timing back-to-back sweeps flatters it (warmer L2)
+      // a larger tile (or the bulk-copy kernel) must win by 5 %: timing back-to-back sweeps
+      // flatters it (warmer L2)
       if (ms < 0.95f * best) { best = ms; best_rows = rows; }
     }
     std::lock_guard<std::mutex> lock(g_tile_mu);
@@ -1873,7 +2022,11 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
   else TRY(ensure_scratch<double>(op));
   CK(cudaMemcpyAsync(op->F, f, bytes, cudaMemcpyDeviceToDevice, st));
-  if (op->neumann) TRY(solvability_fix_impl<D>(op, op->F, bc, nullptr, st));
+  if (op->neumann) {
+    TRY(solvability_fix_impl<D>(op, op->F, bc, nullptr, st));
+    // keep the removed constant (slot 4 is reused by the final mean-zero)
+    CK(cudaMemcpyAsync(h->d_scalar + 6, h->d_scalar + 4, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
   if (p.zero_initial) CK(cudaMemsetAsync(phi, 0, bytes, st));
   TRY(avgdown_all<D>(h, op->F, st));
   TRY(maxnorm_dev<double, D>(h, op->F, reinterpret_cast<unsigned long long*>(h->d_scalar + 5), st));
@@ -1886,11 +2039,12 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
   else TRY(avgdown_all<D>(h, phi, st));
   CK(cudaMemcpyAsync(op->h_stats, op->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(op->h_scal, h->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(op->h_scal, h->d_scalar, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
   return AMR_OK;
 }
 
 amr_status solve_graph_finish(amr_operator* op, amr_solve_stats* stats) {
+  TRY(sweep3d_check_flag());
   const DevStats& ds = *op->h_stats;
   g_launches.fetch_add(op->launches_pre + (long long)ds.iter * op->launches_body);
   amr_solve_stats loc{};
@@ -1898,7 +2052,7 @@ amr_status solve_graph_finish(amr_operator* op, amr_solve_stats* stats) {
   for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
   loc.final_res = ds.hist[std::min(ds.iter, 63)];
   loc.rhs_norm = op->h_scal[5];
-  loc.removed_mean = op->neumann ? op->h_scal[4] : 0.0;
+  loc.removed_mean = op->neumann ? op->h_scal[6] : 0.0;
   if (stats) *stats = loc;
   if (ds.status == 0) return AMR_OK;
   if (ds.status == 2) { set_error("residual is not finite"); return AMR_ERR_NONFINITE; }
@@ -2748,6 +2902,14 @@ amr_status amr_set_fx_residual(int on) {
   return AMR_OK;
 }
 
+amr_status amr_set_bulk_sweep(int on) {
+  if (on < 0 || on > 2) { set_error("bulk-copy sweep switch must be 0, 1 or 2"); return AMR_ERR_INVALID_ARG; }
+  g_bulk_sweep.store(on, std::memory_order_relaxed);
+  return AMR_OK;
+}
+
+amr_status amr_check_kernel_flags(void) { return sweep3d_check_flag(); }
+
 amr_status amr_profile_enable(int on) {
   // events are never reused: a cached instrumented graph keeps recording into its own
   if (on) g_prof.recs.clear();
@@ -2756,11 +2918,16 @@ amr_status amr_profile_enable(int on) {
 }
 
 amr_status amr_profile_read(int kernel_class, long long* launches, double* total_ms, double* total_bytes) {
+  return amr_profile_read_range(kernel_class, 0.0, 1e300, launches, total_ms, total_bytes);
+}
+
+amr_status amr_profile_read_range(int kernel_class, double min_cells, double max_cells, long long* launches,
+                                  double* total_ms, double* total_bytes) {
   if (kernel_class < 0 || kernel_class >= PC_NCLASS) { set_error("bad kernel class"); return AMR_ERR_INVALID_ARG; }
   long long n = 0;
   double ms = 0.0, by = 0.0;
   for (const ProfRec& r : g_prof.recs) {
-    if (r.cls != kernel_class) continue;
+    if (r.cls != kernel_class || r.cells < min_cells || r.cells > max_cells) continue;
     CK(cudaEventSynchronize(r.b));
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, r.a, r.b));

@@ -469,15 +469,24 @@ def tile_rows():
     amr.set_tile_rows(0)
 
 
+@pytest.fixture
+def bulk_sweep():
+    amr = _amr()
+    yield amr.set_bulk_sweep
+    amr.set_bulk_sweep(1)
+
+
 @pytest.mark.parametrize("n", [(64, 48, 40), (64, 64, 40)])
 @pytest.mark.parametrize("rows", [2, 4])
-def test_3d_zchunk_operator_parity(n, rows, tile_rows):
+def test_3d_zchunk_operator_parity(n, rows, tile_rows, bulk_sweep):
     """Single-level grids whose x, y extents are multiples of the z-chunked kernel's tile
     (32 x 16 with two rows per thread, 32 x 32 with four; 48 rows fall back to two), so
     blocks sit at every face and z chunks end inside the grid: three FP64 weighted-Jacobi
-    sweeps, the homogeneous operator and the residual against the oracle."""
+    sweeps, the homogeneous operator and the residual against the oracle (the bulk-copy
+    kernel, which would take these grids, switched off)."""
     amr = _amr()
     tile_rows(rows)
+    bulk_sweep(0)
     box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
     bc = [0, 1, 0, 0, 1, 0]
     H = OH(3, n, box, bc=bc, hi=tuple(v / n[0] for v in n))
@@ -506,6 +515,95 @@ def test_3d_zchunk_operator_parity(n, rows, tile_rows):
     got = from_packed(gh, H, res.cpu().numpy())
     refr = [B[l] - ref[l] for l in range(len(ref))]
     assert max_diff(H, got, refr) <= 1e-13 * op_scale(H, alpha, beta, X)
+
+
+def _level_ops(amr, op, gh, H, X, B):
+    """Three FP64 weighted-Jacobi sweeps, the operator and the residual through the C ABI."""
+    dx = _dev(to_packed(gh, H, X))
+    op.smooth(0, 3, 2.0 / 3.0, dx, _dev(to_packed(gh, H, B)))
+    out = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+    op.apply(_dev(to_packed(gh, H, X)), out)
+    res = torch.zeros_like(out)
+    op.residual(_dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B)), res)
+    return [from_packed(gh, H, t.cpu().numpy()) for t in (dx, out, res)]
+
+
+@pytest.mark.parametrize("n,bc", [((64, 48, 40), [0, 1, 0, 0, 1, 0]), ((128, 32, 16), [1, 0, 1, 1, 0, 1]),
+                                  ((64, 16, 64), [1, 1, 0, 1, 0, 0])])
+def test_3d_bulk_sweep_operator_parity(n, bc, bulk_sweep):
+    """The bulk-copy pipelined 3-D level operator, forced (64 x 16 tiles, z chunks of at least
+    eight planes, ghost values written into the staged planes at every face of both types) on single-level grids with one or two
+    tiles across x and several across y: three FP64 weighted-Jacobi sweeps, the operator and
+    the residual against the oracle, and against the z-chunked kernel (the same operations
+    per cell) to 1e-14."""
+    amr = _amr()
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    H = OH(3, n, box, bc=bc, hi=tuple(v / n[0] for v in n))
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    rng = np.random.default_rng(71)
+    alpha, beta = 1.0, -0.02
+    op = amr.Operator(gh, alpha, beta, bc)
+    X = _rand_field(H, rng, redundant=False)
+    B = _rand_field(H, rng, redundant=False)
+    bulk_sweep(2)
+    got = _level_ops(amr, op, gh, H, X, B)
+    amr.check_kernel_flags()
+    bulk_sweep(0)
+    zc = _level_ops(amr, op, gh, H, X, B)
+    diag = mg.jacobi_diagonal(H, 0, alpha, beta)
+    Xr = X[0].copy()
+    for _ in range(3):
+        Xr = mg.jacobi(H, 0, Xr, B[0], diag, alpha, beta, 2.0 / 3.0)
+    cov = H.levels[0].covered
+    sx = float(np.max(np.abs(Xr[cov])))
+    assert float(np.max(np.abs(got[0][0][cov] - Xr[cov]))) <= 1e-12 * sx
+    assert float(np.max(np.abs(got[0][0][cov] - zc[0][0][cov]))) <= 1e-14 * sx
+    ref = cp.apply(H, X, alpha, beta, None)
+    scale = op_scale(H, alpha, beta, X)
+    assert max_diff(H, got[1], ref) <= 1e-13 * scale
+    assert max_diff(H, got[1], zc[1]) <= 1e-14 * scale
+    refr = [B[l] - ref[l] for l in range(len(ref))]
+    assert max_diff(H, got[2], refr) <= 1e-13 * scale
+    assert max_diff(H, got[2], zc[2]) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
+def test_3d_bulk_sweep_two_level_vcycle_and_solve(bcw, ab, bulk_sweep):
+    """Two-level 3-D hierarchy whose base (64 x 32 x 16, covered cells masked in the residual)
+    and fine box (64 x 32 x 16 fine cells, coarse-fine ghosts stored in the halo) both take
+    the bulk-copy kernel: one FP64 V-cycle against the oracle's V-cycle, then mixed-precision
+    solves to 1e-10 with the bulk-copy and the z-chunked kernels (same V-cycle count, same
+    solution to 1e-12), the residual recomputed by the oracle's composite operator."""
+    amr = _amr()
+    n0 = (64, 32, 16)
+    boxes = [[((0, 0, 0), (63, 31, 15))], [((32, 16, 8), (95, 47, 23))]]
+    bc = [bcw] * 6
+    alpha, beta = ab
+    H = OH(3, n0, boxes, bc=bc, hi=(1.0, 0.5, 0.25))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / 64)
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(73)
+    F = _rand_field(H, rng)
+    if bcw == 1:
+        F, _ = so.solvability_fix(H, F)
+    phi = _rand_field(H, rng)
+    bulk_sweep(2)
+    ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+    dphi = _dev(to_packed(gh, H, phi))
+    df = _dev(to_packed(gh, H, F))
+    op.vcycle(dphi, df)
+    got = from_packed(gh, H, dphi.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref)
+    sols = []
+    for on in (2, 0):
+        bulk_sweep(on)
+        x = torch.zeros_like(df)
+        st = op.solve(x, df, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=1, use_graph=1))
+        sols.append((from_packed(gh, H, x.cpu().numpy()), st["vcycles"]))
+    assert sols[0][1] == sols[1][1]
+    assert max_diff(H, sols[0][0], sols[1][0]) <= 1e-12 * max_abs(H, sols[1][0])
+    R = cp.residual(H, sols[0][0], F, alpha, beta)
+    assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F)
 
 
 @pytest.fixture
