@@ -153,9 +153,13 @@ typedef struct {
   int zero_initial;  /* 1: start from phi = 0; 0: use phi as the initial guess            */
   int use_graph;     /* 1: capture the whole solve as one CUDA graph (device-side loop over
                         V-cycles, no host round trip per V-cycle) and replay it              */
-  int fuse_coarse;   /* 1: run the coarse end of the level-0 V-cycle in one shared-memory
-                        block (same arithmetic as the per-grid kernels); default 0: on GB300
-                        one block is slower than the graph's per-grid launches              */
+  int fuse_coarse;   /* coarse end of the level-0 V-cycle.  0 (default): per-grid launches (in
+                        2-D the one-block square coarse kernel where it applies).  1: one
+                        shared-memory block from the largest grid that fits (generic per-cell
+                        code).  2 (3-D): the grids of at most 32^3 cells as one launch of one
+                        thread-block cluster, phases separated by cluster barriers, same
+                        per-cell arithmetic as the per-grid kernels.  On GB300 both fused
+                        forms are slower than captured per-grid launches.                   */
   int temporal_blocking; /* 1 (default): in forward FP32 V-cycles on 2-D level-0 multigrid grids,
                         each down leg (nu1 sweeps, residual, restriction) and each up leg
                         (prolongation, nu2 sweeps) is one launch over shared-memory tiles

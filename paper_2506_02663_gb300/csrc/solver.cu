@@ -19,6 +19,7 @@
 #include "amr4_impl.h"
 #include "kernels.cuh"
 #include "sweep3d.cuh"
+#include "coarse3d.cuh"
 
 using namespace amr4;
 
@@ -468,12 +469,12 @@ amr_status launch_sw(const LevelView& lv, const T* x, const T* f, T* out, T A, T
   constexpr int threads = 32 * (SW_TY / SW_RW + 2);
   CUtensorMap tmx{}, tmf{};
   if (M != OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmx, x, lv.p0, SW_TY + 4));
-  if (M != OP_APPLY) TRY(encode_patch_tmap<T>(&tmf, f, lv.p0, SW_TY));
+  if (M == OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmf, f, lv.p0, SW_TY));
   const int ntx = lv.maxn[0] / sw3::TX, ntiles = ntx * (lv.maxn[1] / SW_TY), nz = lv.maxn[2];
   const int wave = wave_blocks(reinterpret_cast<const void*>(sw_kernel<T, M>()), threads, smem);
   const int nch = std::max(1, std::min(wave / ntiles, nz / SW_MINZ));
-  launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, out, A, B, O,
-         vmask, gate);
+  launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, f, out, A, B,
+         O, vmask, gate);
   return launch_check();
 }
 
@@ -1205,6 +1206,104 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
   return AMR_OK;
 }
 
+// ---------------------------------------------------------------- cluster coarse V-cycle (3-D)
+// First level-0 multigrid grid from which every grid down to the bottom has at most
+// CC_CELLS cells (and there are at most CC_MAX of them, at least one above the bottom); -1
+// when there is none.
+inline int coarse_cluster_m0(const amr_hierarchy* h) {
+  const int M = (int)h->mg.size() - 1;
+  int m0 = -1;
+  for (int m = M; m >= 0 && M - m + 1 <= CC_MAX; --m) {
+    const MgGrid& g = h->mg[m];
+    if ((long long)g.n[0] * g.n[1] * g.n[2] > CC_CELLS) break;
+    m0 = m;
+  }
+  return m0 < M ? m0 : -1;
+}
+
+// CTAs per cluster: 16 where the device schedules a cluster that large, else 8 (queried
+// once per device and kernel)
+template <typename T, int D, bool TR>
+int coarse_cluster_size() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int cs = 8;
+  if (cudaFuncSetAttribute(k_coarse_cluster<T, D, TR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+      cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(CC_THREADS, 1, 1);
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeClusterDimension;
+    a[0].val.clusterDim.x = 16;
+    a[0].val.clusterDim.y = 1;
+    a[0].val.clusterDim.z = 1;
+    cfg.attrs = a;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cluster<T, D, TR>, &cfg) == cudaSuccess && nclusters >= 1)
+      cs = 16;
+  }
+  cudaGetLastError();
+  cache[dev] = cs;
+  return cs;
+}
+
+template <typename T, int D, bool TR = false>
+amr_status coarse_cluster(amr_operator* op, const amr_solver_params& p, int m0, const T* b, T* x, T* t,
+                          cudaStream_t st) {
+  amr_hierarchy* h = op->h;
+  Scratch<T>& S = scratch<T>(op);
+  const int M = (int)h->mg.size() - 1;
+  CoarseCluster cm{};
+  CoarsePtrs<T> ptr{};
+  cm.ng = M - m0 + 1;
+  cm.nu1 = p.nu1;
+  cm.nu2 = p.nu2;
+  cm.nbot = op->nbot;
+  cm.ldb = op->ldb;
+  cm.minv = TR ? op->d_binvT : op->d_binv;
+  for (int q = 0; q < cm.ng; ++q) {
+    const int m = m0 + q;
+    cm.lv[q] = mg_view(h, m, op->bc);
+    cm.gp[q] = h->mg[m].patch;
+    ptr.x[q] = q == 0 ? x : S.mx[m];
+    ptr.b[q] = q == 0 ? const_cast<T*>(b) : S.mb[m];
+    ptr.t[q] = q == 0 ? t : S.mt[m];
+  }
+  const int cs = coarse_cluster_size<T, D, TR>();
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(CC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, D, TR>, cm, ptr, T(op->alpha), T(op->beta),
+                                           T(p.omega));
+  if (e != cudaSuccess && g_launch_err == cudaSuccess) g_launch_err = e;
+  TRY(launch_check());
+  const MgGrid& g = h->mg[m0];
+  const double cells = (double)g.n[0] * g.n[1] * g.n[2];
+  prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * cells, cells);  // read f, write x of the top grid
+  return AMR_OK;
+}
+static_assert(sizeof(CoarseCluster) + sizeof(CoarsePtrs<double>) < 30000, "kernel parameter block too large");
+
 // ---------------------------------------------------------------- level-0 multigrid
 template <typename T, int D, bool TR = false>
 amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const T* b, T* x, T* t, cudaStream_t st) {
@@ -1212,11 +1311,15 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   Scratch<T>& S = scratch<T>(op);
   const int M = (int)h->mg.size() - 1;
   const LevelView lv = mg_view(h, m, op->bc);
-  if (p.fuse_coarse) {
+  if (p.fuse_coarse == 1) {
     int m0;
     size_t bytes;
     TRY((fused_config<T, D, TR>(op, m0, bytes)));
     if (m == m0) return fused_coarse<T, D, TR>(op, p, m0, bytes, b, x, st);
+  }
+  if constexpr (D == 3) {
+    // fuse_coarse = 2: the coarse end of the pyramid in one cluster launch
+    if (p.fuse_coarse == 2 && m == coarse_cluster_m0(h)) return coarse_cluster<T, D, TR>(op, p, m, b, x, t, st);
   }
   if (m == M) {
     const int n = op->nbot;
@@ -2431,7 +2534,7 @@ struct BatchPlan {
 inline int batch_levels(const amr_operator* op, const amr_solver_params& p) {
   const amr_hierarchy* h = op->h;
   if (h->D != 2 || h->L != 1 || h->lev[0].patches.size() != 1 || op->neumann) return -1;
-  if (p.precision != AMR_MIXED || !p.temporal_blocking || p.fuse_coarse || p.nu1 < 1 || p.nu1 > BLK_FX_NU ||
+  if (p.precision != AMR_MIXED || !p.temporal_blocking || p.fuse_coarse == 1 || p.nu1 < 1 || p.nu1 > BLK_FX_NU ||
       p.nu2 < 1 || p.nu2 > BLK_FX_NU)
     return -1;
   size_t bytes = 0;
@@ -3151,7 +3254,7 @@ amr_status amr_smooth(amr_operator* op, int level, int nsweeps, double omega, do
 
 static amr_status check_params(const amr_solver_params* p) {
   if (!p || p->nu1 < 0 || p->nu2 < 0 || p->max_vcycles < 0 || !(p->omega > 0.0) ||
-      (p->precision != AMR_FP64 && p->precision != AMR_MIXED)) {
+      (p->precision != AMR_FP64 && p->precision != AMR_MIXED) || p->fuse_coarse < 0 || p->fuse_coarse > 2) {
     set_error("bad solver parameters");
     return AMR_ERR_INVALID_ARG;
   }

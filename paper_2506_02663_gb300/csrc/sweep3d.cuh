@@ -7,17 +7,19 @@
 // Design (GB300): a block owns a 64 x TY tile column and marches up z through one chunk of
 // planes.  Three warp roles share a ring of S shared-memory slots, one plane per slot:
 //   * producer (one thread): streams the planes of x (the tile plus its two-cell halo, a
-//     68 x (TY + 4) box of the padded patch) and of f (a 68 x TY box) into the ring with
-//     tensor-map TMA copies (cp.async.bulk.tensor), one per operand and plane, completing on
-//     the slot's "full" mbarrier;
+//     68 x (TY + 4) box of the padded patch) into the ring with tensor-map TMA copies
+//     (cp.async.bulk.tensor), one per plane, completing on the slot's "full" mbarrier (the
+//     first sweep from x = 0, which reads f alone, streams f the same way);
 //   * fixer (one warp, only in blocks that touch a domain face): writes the physical ghost
 //     values (Eqs. velBCHomoDiri5th, Neumann5, homogeneous data -- never stored in global
 //     memory) into the slot's halo columns, halo rows and, at a z face, the ghost planes,
 //     from the staged cells next to the face, then signals the slot's "ready" mbarrier;
 //   * consumers (TY / RW warps; warp w owns RW tile rows, lane l the cells 2l, 2l+1 of a
 //     row): read every neighbour of the 13-point stencil from the ring (planes k-2 .. k+2),
-//     with one 8- or 16-byte shared load per neighbour pair, and store one pair per row.  A
-//     slot is released through its "empty" mbarrier once plane k+2 no longer needs it.
+//     with one 8- or 16-byte shared load per neighbour pair, and store one pair per row; f
+//     is read from global memory two planes ahead into registers, which keeps the slots
+//     small enough for three blocks per SM.  A slot is released through its "empty"
+//     mbarrier once plane k+2 no longer needs it.
 // The consumer loop has no face branch and no block-wide barrier; up to S - 5 planes are in
 // flight per block.  Stored ghost values (coarse-fine, copies) arrive with the halo.  The
 // Jacobi factor comes from the 125-entry distance-class table.
@@ -138,7 +140,7 @@ __host__ __device__ constexpr size_t slot_elems(bool needx, bool needf) {
 
 template <typename T, int MODE, int TY, int S>
 constexpr size_t smem_bytes() {
-  return (size_t)S * slot_elems<TY, T>(MODE != OP_JACOBI0, MODE != OP_APPLY) * sizeof(T) + 3 * S * sizeof(unsigned long long) +
+  return (size_t)S * slot_elems<TY, T>(MODE != OP_JACOBI0, MODE == OP_JACOBI0) * sizeof(T) + 3 * S * sizeof(unsigned long long) +
          128 * sizeof(T);
 }
 
@@ -159,17 +161,18 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 template <typename T, int MODE, int TY, int RW, int S>
 __global__ void __launch_bounds__(32 * (TY / RW + 2))
     k_sweep3d(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf, LevelView lv, int ntx,
-              int ntiles, int nch, T* __restrict__ out, T alpha, T beta, T omega,
+              int ntiles, int nch, const T* __restrict__ f, T* __restrict__ out, T alpha, T beta, T omega,
               const unsigned char* __restrict__ vmask, const unsigned* __restrict__ gate) {
   using namespace sw3;
   using V = typename Pair<T>::V;
   unsigned* err = &g_sweep3d_err;
   constexpr bool NEEDX = MODE != OP_JACOBI0;
   constexpr bool NEEDF = MODE != OP_APPLY;
-  constexpr int NCW = TY / RW;  // consumer warps
-  constexpr int XH = TY + 4;    // slot rows of x
+  constexpr bool FTMA = MODE == OP_JACOBI0;  // f through the ring (else prefetched into registers)
+  constexpr int NCW = TY / RW;               // consumer warps
+  constexpr int XH = TY + 4;                 // slot rows of x
   constexpr int XSZ = NEEDX ? region_elems<T>(XH) : 0;
-  constexpr int SLOT = XSZ + (NEEDF ? region_elems<T>(TY) : 0);
+  constexpr int SLOT = XSZ + (FTMA ? region_elems<T>(TY) : 0);
   static_assert(TY % RW == 0 && S >= 8, "tile rows must split into warps; the ring needs eight slots");
   extern __shared__ __align__(128) unsigned char sw3_smem[];
   T* ring = reinterpret_cast<T*>(sw3_smem);
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
     // ---------------------------------------------------------------- producer (one thread)
     if (lane != 0) return;
     if (NEEDX) tma_prefetch_desc(&tmx);
-    if (NEEDF) tma_prefetch_desc(&tmf);
+    if (FTMA) tma_prefetch_desc(&tmf);
     int q = 0;
     bool ok = true;
     for (; q < np; ++q) {
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
         break;
       }
       const bool ghost = NEEDX && (lz + k < 0 || lz + k >= nzd);  // z ghost plane: the fixer writes it
-      const bool wf = NEEDF && k >= ka && k < kb;
+      const bool wf = FTMA && k >= ka && k < kb;
       if (ghost) {
         mbar_arrive(&full[sl]);
         continue;
@@ -377,11 +380,24 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
     for (int d = 0; d < 4; ++d) pz[d] = ring + (size_t)d * SLOT;
     int s4 = 4, par4 = 0;  // slot and phase parity of plane k+2
     const int rbase = (warp * RW + 2) * XW + c0;
-    for (int k = ka; k < kb; ++k) {
+    // f of the lane's pairs, loaded two planes ahead into two register slots used alternately
+    // (no register with a load in flight is copied)
+    const T* __restrict__ frow =
+        NEEDF ? f + p.off + (long long)(ka + NG) * p.sz + (long long)(j0 + NG + warp * RW) * p.sy + (i0 + c0) : nullptr;
+    V fq[2][RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      fq[0][r] = fq[1][r] = V{T(0), T(0)};
+      if (NEEDF) {
+        fq[0][r] = __ldg(reinterpret_cast<const V*>(frow + r * sy));
+        if (ka + 1 < kb) fq[1][r] = __ldg(reinterpret_cast<const V*>(frow + sz + r * sy));
+      }
+    }
+    auto step = [&](int k, auto slotc) -> bool {
+      constexpr int FS = decltype(slotc)::value;
       pz[4] = ring + (size_t)s4 * SLOT;
-      if (!mbar_wait(&gbar[s4], (unsigned)par4)) { fail(); return; }
+      if (!mbar_wait(&gbar[s4], (unsigned)par4)) return false;
       const T* __restrict__ sx = pz[2];
-      const T* __restrict__ sf = pz[2] + XSZ;
       const int kz25 = 25 * face_class(lz + k, nzd);
 #pragma unroll
       for (int r = 0; r < RW; ++r) {
@@ -403,7 +419,8 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
           o0 = kc0 * xc.x + (kc1 * s1a - kc2 * s2a);
           o1 = kc0 * xc.y + (kc1 * s1b - kc2 * s2b);
         } else {
-          const V fk = ld2<T>(sf + (sr - 2 * XW));
+          const V fk = fq[FS][r];
+          if (k + 2 < kb) fq[FS][r] = __ldg(reinterpret_cast<const V*>(frow + 2 * sz + r * sy));
           const T ra = fma(kc2, s2a, fma(-kc1, s1a, fma(-kc0, xc.x, fk.x)));
           const T rb = fma(kc2, s2b, fma(-kc1, s1b, fma(-kc0, xc.y, fk.y)));
           if (MODE == OP_RESID) {
@@ -433,6 +450,12 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
       }
       orow += sz;
       if (vrow) vrow += sz;
+      if (NEEDF) frow += sz;
+      return true;
+    };
+    for (int k = ka; k < kb; k += 2) {
+      if (!step(k, zc_slot<0>{})) { fail(); return; }
+      if (k + 1 < kb && !step(k + 1, zc_slot<1>{})) { fail(); return; }
     }
   }
 }

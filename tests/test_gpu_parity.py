@@ -568,6 +568,51 @@ def test_3d_bulk_sweep_operator_parity(n, bc, bulk_sweep):
 
 
 @pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
+@pytest.mark.parametrize("n", [(64, 32, 32), (32, 32, 16)])
+@pytest.mark.parametrize("fuse", [2, 0])
+def test_3d_coarse_cluster_vcycle_and_transpose(n, bcw, ab, fuse):
+    """Single-level grids whose multigrid ends in grids of at most 32^3 cells: 64 x 32 x 32
+    (the cluster takes 32 x 16 x 16 -> 16 x 8 x 8 -> 8 x 4 x 4) and 32 x 32 x 16 (the cluster
+    takes the level itself).  fuse_coarse = 2 runs those grids as one cluster launch, 0 as
+    per-grid launches.  One FP64 V-cycle against the oracle's V-cycle; mixed and FP64 solves
+    whose residual the oracle recomputes; and on the smaller grid the adjoint solve, whose
+    level-0 V-cycles take the same path, checked by the residual of the oracle's assembled
+    transposed system."""
+    amr = _amr()
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    bc = [0, 1, 0, 0, 1, 0] if bcw == 0 else [1] * 6
+    alpha, beta = ab
+    H = OH(3, n, box, bc=bc, hi=tuple(v / n[0] for v in n))
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(79)
+    F = _rand_field(H, rng, redundant=False)
+    if so.is_pure_neumann(H, alpha):
+        F, _ = so.solvability_fix(H, F)
+    phi = _rand_field(H, rng, redundant=False)
+    ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+    dphi = _dev(to_packed(gh, H, phi))
+    op.vcycle(dphi, _dev(to_packed(gh, H, F)), params=amr.default_params(fuse_coarse=fuse))
+    got = from_packed(gh, H, dphi.cpu().numpy())
+    assert max_diff(H, got, ref) <= 1e-10 * max_abs(H, ref)
+    for prec in (0, 1):
+        x = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        st = op.solve(x, _dev(to_packed(gh, H, F)), params=amr.default_params(
+            rtol=1e-10, max_vcycles=100, precision=prec, use_graph=1, fuse_coarse=fuse))
+        R = cp.residual(H, from_packed(gh, H, x.cpu().numpy()), F, alpha, beta)
+        assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F), (prec, st)
+    if alpha != 0.0 and n == (32, 32, 16) and fuse == 2:
+        U = so.Unknowns(H)
+        A, _ = so.helmholtz_matrix(H, alpha, beta)
+        g = rng.standard_normal(U.n)
+        dl = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        op.solve_transpose(dl, _dev(to_packed(gh, H, U.scatter(g, fill_invalid=False))),
+                           params=amr.default_params(rtol=1e-12, max_vcycles=100, fuse_coarse=fuse))
+        lam = U.gather(from_packed(gh, H, dl.cpu().numpy()))
+        assert np.max(np.abs(g - A.T @ lam)) <= 2e-12 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("bcw,ab", [(0, (1.0, -0.01)), (1, (0.0, 1.0))])
 def test_3d_bulk_sweep_two_level_vcycle_and_solve(bcw, ab, bulk_sweep):
     """Two-level 3-D hierarchy whose base (64 x 32 x 16, covered cells masked in the residual)
     and fine box (64 x 32 x 16 fine cells, coarse-fine ghosts stored in the halo) both take
