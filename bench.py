@@ -158,9 +158,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _kernel_source_hash():
+def _kernel_source_hash(files=("kernels.cuh", "sweep3d.cuh", "solver.cu")):
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "sweep3d.cuh", "solver.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2506_02663_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -168,13 +168,14 @@ def _kernel_source_hash():
 
 def _traffic(key):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    kernel sources; else None."""
+    sources of that kernel (the entry's ``sources``); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(key)
-        if e and e.get("source_hash") == _kernel_source_hash():
+        if e and e.get("source_hash") == _kernel_source_hash(tuple(e.get("sources", ("kernels.cuh", "sweep3d.cuh",
+                                                                                       "solver.cu")))):
             return e.get("dram_bytes_per_launch")
     except Exception:
         pass

@@ -26,13 +26,16 @@ def test_valid_dof_matches_oracle_valid_regions():
 
 
 def test_traffic_figure_only_for_matching_sources(tmp_path, monkeypatch):
+    """A stored DRAM figure is reported only while the hash of the kernel's own source files
+    (the entry's ``sources``) matches the one recorded at capture time."""
     os.makedirs(tmp_path / "profiles")
-    h = bench._kernel_source_hash()
-    json.dump({"a_w": {"dram_bytes_per_launch": 123.0, "source_hash": h},
-               "b_w": {"dram_bytes_per_launch": 456.0, "source_hash": "0" * 16}},
+    h = bench._kernel_source_hash(("sweep3d.cuh",))
+    json.dump({"a_w": {"dram_bytes_per_launch": 123.0, "sources": ["sweep3d.cuh"], "source_hash": h},
+               "b_w": {"dram_bytes_per_launch": 456.0, "sources": ["sweep3d.cuh"], "source_hash": "0" * 16}},
               open(tmp_path / "profiles" / "traffic.json", "w"))
-    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: h)
+    real = bench._kernel_source_hash
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda files=None: h if tuple(files) == ("sweep3d.cuh",) else real(files))
     assert bench._traffic("a_w") == 123.0
     assert bench._traffic("b_w") is None   # taken on other kernel sources
     assert bench._traffic("c_w") is None   # not captured
