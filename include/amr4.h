@@ -330,7 +330,16 @@ amr_status amr_project_transpose(amr_operator* ppe, const amr_solver_params* p, 
  * refinement loop (the down legs of one depth, the coarse V-cycles, the up legs, the update,
  * the FP64 residual, its norm, the stopping test) is one launch over a descriptor list
  * covering all problems, and a device-side loop runs until every problem has converged,
- * problems that have converged skipping their entries.  Otherwise each problem runs its own
+ * problems that have converged skipping their entries.  When the problems are 3-D, their
+ * hierarchies have one geometry (the same boxes on every level) and their operators are one
+ * operator (alpha, beta, boundary types; not the pure-Neumann PPE) -- e.g. the Helmholtz
+ * systems of the velocity components -- they are solved as one stacked problem: a hierarchy
+ * holding one replica of every patch and work list per problem (built on the first call,
+ * kept with the first operator), one captured graph in which every phase of the V-cycle and
+ * of the refinement loop is one launch over all replicas, a stopping test per replica (a
+ * converged replica's phi is no longer updated; statistics and statuses per problem as for
+ * separate solves; the fields are copied in and out of the stacked arrays inside the call)
+ * when amr_set_stacked_batches(1) is in effect.  Otherwise each problem runs its own
  * captured graph (p->use_graph is forced to 1), launched concurrently on a pool of internal
  * streams forked from ``stream`` and joined back to it; problems that share a hierarchy then
  * run one after another on the same stream because they share its reduction scratch.  The
@@ -411,6 +420,13 @@ amr_status amr_set_bulk_sweep(int on);
  * AMR_OK.  Solves check it when they finish (amr_solve and amr_batch_solve return
  * AMR_ERR_CUDA). */
 amr_status amr_check_kernel_flags(void);
+/* Stacked solves of 3-D batches that share one geometry and one operator in amr_batch_solve
+ * (not in the paper: a launch-count choice).  on = 1: stacked (one launch per phase over all
+ * problems); on = 0 (the default): one captured solve per problem, launched concurrently --
+ * on GB300 the concurrent graphs overlap one problem's latency-bound coarse phases with
+ * another's bandwidth-bound fine phases and measure faster.  Process-wide;
+ * AMR_ERR_INVALID_ARG for any other value. */
+amr_status amr_set_stacked_batches(int on);
 
 #ifdef __cplusplus
 }

@@ -97,6 +97,7 @@ _sigs = {
     "amr_set_fx_residual": [C.c_int],
     "amr_set_bulk_sweep": [C.c_int],
     "amr_check_kernel_flags": [],
+    "amr_set_stacked_batches": [C.c_int],
     "amr_profile_read": [C.c_int, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
     "amr_profile_read_range": [C.c_int, C.c_double, C.c_double, _P(C.c_longlong), _P(C.c_double), _P(C.c_double)],
 }
@@ -135,6 +136,13 @@ def set_bulk_sweep(on):
     1 (default) the autotuner picks the bulk-copy (TMA) or the z-chunked level operator per
     grid; 2 always the bulk-copy kernel; 0 never."""
     _check(_lib.amr_set_bulk_sweep(int(on)), "amr_set_bulk_sweep")
+
+
+def set_stacked_batches(on):
+    """1: 3-D batches of one geometry and one operator are solved as one stacked problem (one
+    launch per phase over all problems); 0 (default): one captured solve per problem,
+    launched concurrently."""
+    _check(_lib.amr_set_stacked_batches(int(on)), "amr_set_stacked_batches")
 
 
 def check_kernel_flags():

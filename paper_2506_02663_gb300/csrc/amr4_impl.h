@@ -48,6 +48,12 @@ struct LevelView {
   // host-side copy of the first patch (the only one of a single-patch level): kernels fed by
   // tensor-map copies need its offset and strides on the host
   PatchDesc p0;
+  // stacked component batches: the level holds ncomp replicas of its patches, replica c at
+  // element offset c * cstride (ncomp = 1, cstride = 0 otherwise); fxs then holds two
+  // words per component
+  int ncomp;
+  long long cstride;
+  const int* active;  // stacked batches: replicas still iterating (nullptr: all)
 };
 
 void finish_view(LevelView& v);  // fills the precomputed constants from h and bc
@@ -126,8 +132,9 @@ struct MgGrid {
   int n[3] = {1, 1, 1};
   double h = 0.0;
   PatchDesc patch{};
-  PatchDesc* d_patch = nullptr;
-  long long nelems = 0;
+  PatchDesc* d_patch = nullptr;  // ncomp replicas of patch, replica c at offset c * cstride
+  long long nelems = 0;          // elements of the grid's arrays (all replicas)
+  long long cstride = 0;         // element stride between replicas
 };
 
 }  // namespace amr4
@@ -159,6 +166,13 @@ struct amr_hierarchy {
   double* d_tz = nullptr;        // G/D transposes: 3 composite fields (allocated on first use)
   bool cfi_const_ready = false;  // AMRCFI weights copied to the device constant banks
   bool on_device = false;
+  // stacked component batch (built by stack_hierarchy): every patch and work list replicated
+  // ncomp times, replica c of the composite layout at element offset c * cstride
+  int ncomp = 1;
+  long long cstride = 0;            // elements of one replica (nelems / ncomp)
+  unsigned long long* d_fxs = nullptr;   // fixed-point residual words, two per component
+  unsigned long long* d_cnorm = nullptr; // per-component residual and right-hand-side norms (IEEE bits)
+  const int* d_active = nullptr;         // stacked batches: replicas still iterating (set by the solve)
 };
 
 namespace amr4 {
@@ -166,6 +180,10 @@ namespace amr4 {
 amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std::string& err);
 void free_hierarchy(amr_hierarchy* h);
 amr_status upload_hierarchy(amr_hierarchy* h, std::string& err);
+// A new hierarchy holding k replicas of h (same geometry): patches, work lists and masks
+// repeated with element offsets c * stride (stride = h's composite length rounded up to 64
+// elements), patch indices shifted per replica; uploaded to the device.
+amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, std::string& err);
 void set_error(const std::string& msg);
 const char* get_error();
 void cfi_weights_exact(int r, std::vector<double>& w);  // [pos][sub][a], 5 x r x 5

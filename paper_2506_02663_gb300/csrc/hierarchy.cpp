@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <stdexcept>
 
@@ -544,6 +545,113 @@ amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std
   return AMR_OK;
 }
 
+// Replicas of a hierarchy for stacked component batches: every field of the stacked
+// hierarchy is k copies of h's composite layout, copy c at element offset c * stride.  Patch
+// indices inside the work lists (AMRCFI source patches, refluxing and transfer patch pairs)
+// are indices within a level, so replica c shifts them by c times the level's patch count;
+// element offsets shift by c * stride.  The level-0 multigrid grids keep one layout each and
+// get k replicas at their own stride.
+amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, std::string& err) {
+  if (k < 1 || h->ncomp != 1) {
+    err = "stack_hierarchy: needs k >= 1 and an unstacked hierarchy";
+    return AMR_ERR_INVALID_ARG;
+  }
+  std::unique_ptr<amr_hierarchy> s(new amr_hierarchy());
+  s->D = h->D;
+  s->r = h->r;
+  for (int e = 0; e < 3; ++e) s->n0[e] = h->n0[e];
+  s->h0 = h->h0;
+  s->L = h->L;
+  s->ncomp = k;
+  const long long stride = (h->nelems + 63) / 64 * 64;
+  s->cstride = stride;
+  s->nelems = stride * k;
+  s->npatch = h->npatch * k;
+  s->bc_off = h->bc_off;
+  s->cfi_w = h->cfi_w;
+  s->lev.resize(h->L);
+  for (int l = 0; l < h->L; ++l) {
+    const LevelHost& A = h->lev[l];
+    LevelHost& B = s->lev[l];
+    const int np = (int)A.patches.size();
+    const int npc = l > 0 ? (int)h->lev[l - 1].patches.size() : 0;  // coarse level's patches
+    const int npf = l + 1 < h->L ? (int)h->lev[l + 1].patches.size() : 0;
+    for (int e = 0; e < 3; ++e) { B.ndom[e] = A.ndom[e]; B.maxn[e] = A.maxn[e]; }
+    B.h = A.h;
+    B.first_patch = A.first_patch * k;
+    const long long w3 = h->D == 3 ? 125 : 25;
+    const long long nside = (long long)A.cfi_side.size() / w3;
+    for (int c = 0; c < k; ++c) {
+      const long long o = c * stride;
+      for (const Box& b : A.boxes) B.boxes.push_back(b);
+      for (PatchDesc p : A.patches) {
+        p.off += o;
+        B.patches.push_back(p);
+      }
+      for (CfiEntry e : A.cfi) {
+        e.dst += o;
+        if (e.src >= 0) e.src += o;
+        else e.src = -1 - (-1 - e.src + c * nside);
+        e.cpatch += c * npc;
+        e.fpatch += c * np;
+        B.cfi.push_back(e);
+      }
+      for (long long v : A.cfi_side) B.cfi_side.push_back(v + o);
+      for (CopyEntry e : A.copy) {
+        e.dst += o;
+        e.src += o;
+        B.copy.push_back(e);
+      }
+      for (RefluxEntry e : A.reflux) {
+        e.coff += o;
+        e.cpatch += c * np;
+        for (int f = 0; f < 6; ++f)
+          if (e.fpatch[f] >= 0) e.fpatch[f] += c * npf;
+        B.reflux.push_back(e);
+      }
+      for (XferBlock x : A.xfer) {
+        x.fpatch += c * npf;
+        x.cpatch += c * np;
+        B.xfer.push_back(x);
+      }
+    }
+    B.dev.xfer_max[0] = A.dev.xfer_max[0];
+    B.dev.xfer_max[1] = A.dev.xfer_max[1];
+    B.dev.xfer_max[2] = A.dev.xfer_max[2];
+  }
+  s->mg = h->mg;
+  for (size_t m = 0; m < s->mg.size(); ++m) {
+    MgGrid& g = s->mg[m];
+    g.d_patch = nullptr;
+    if (m == 0) {
+      g.cstride = stride;
+      g.nelems = stride * k;
+    } else {
+      g.cstride = (h->mg[m].nelems + 63) / 64 * 64;
+      g.nelems = g.cstride * k;
+    }
+  }
+  // valid flags in the order the patches are laid out: level by level, within a level the
+  // replicas one after another
+  {
+    size_t q = 0;
+    for (int l = 0; l < h->L; ++l) {
+      size_t cells = 0;
+      for (const PatchDesc& p : h->lev[l].patches) cells += (size_t)p.n[0] * p.n[1] * p.n[2];
+      for (int c = 0; c < k; ++c)
+        s->im_valid.insert(s->im_valid.end(), h->im_valid.begin() + q, h->im_valid.begin() + q + cells);
+      q += cells;
+    }
+  }
+  const amr_status st = upload_hierarchy(s.get(), err);
+  if (st != AMR_OK) {
+    free_hierarchy(s.get());
+    return st;
+  }
+  *out = s.release();
+  return AMR_OK;
+}
+
 // Device copies of the work lists and masks, made on the first call that needs the GPU
 // (hierarchy creation and the index maps work without one).
 amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
@@ -572,10 +680,16 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
       L.dev.nxfer = (int)L.xfer.size();
     }
     for (auto& g : h->mg) {
-      std::vector<PatchDesc> one{g.patch};
-      g.d_patch = upload(one);
+      std::vector<PatchDesc> reps(h->ncomp, g.patch);
+      for (int c = 0; c < h->ncomp; ++c) reps[c].off = g.patch.off + c * g.cstride;
+      g.d_patch = upload(reps);
     }
     h->d_valid = upload(valid);
+    {
+      std::vector<unsigned long long> z(2 * (size_t)h->ncomp, 0ull);
+      h->d_fxs = upload(z);
+      h->d_cnorm = upload(z);
+    }
     if (cudaMalloc(&h->d_red, sizeof(double) * 2 * 8192) != cudaSuccess) throw std::runtime_error("cudaMalloc failed");
     if (cudaMalloc(&h->d_scalar, sizeof(double) * 16) != cudaSuccess) throw std::runtime_error("cudaMalloc failed");
     if (cudaMallocHost(&h->h_scalar, sizeof(double) * 16) != cudaSuccess) throw std::runtime_error("cudaMallocHost failed");
@@ -600,6 +714,8 @@ void free_hierarchy(amr_hierarchy* h) {
   }
   for (auto& g : h->mg) cudaFree(g.d_patch);
   cudaFree(h->d_valid);
+  cudaFree(h->d_fxs);
+  cudaFree(h->d_cnorm);
   cudaFree(h->d_red);
   cudaFree(h->d_scalar);
   cudaFree(h->d_tz);
@@ -651,8 +767,11 @@ LevelView level_view(const amr_hierarchy* h, int l, const int* bc_types) {
       if (e != d) { lead = e; break; }
     v.bc_pitch[f] = (f < 2 * h->D && lead >= 0) ? L.ndom[lead] : 1;
   }
-  v.fxs = h->d_scalar ? reinterpret_cast<unsigned long long*>(h->d_scalar + 8) : nullptr;
+  v.fxs = h->ncomp > 1 ? h->d_fxs : (h->d_scalar ? reinterpret_cast<unsigned long long*>(h->d_scalar + 8) : nullptr);
   v.p0 = L.patches.front();
+  v.ncomp = h->ncomp;
+  v.cstride = h->cstride;
+  v.active = h->ncomp > 1 ? h->d_active : nullptr;
   finish_view(v);
   return v;
 }

@@ -586,10 +586,13 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
                     const unsigned* __restrict__ gate) {
   using G = ZcGeom<R>;
   pdl_wait();
-  if (gate != nullptr && *gate == 0u) return;  // gated launch: runs only when the flag is set
+  // stacked component batches: the grid holds ncomp equal parts, part c on replica c
+  const int bpc = gridDim.x / lv.ncomp, comp = blockIdx.x / bpc, blk = blockIdx.x % bpc;
+  if (gate != nullptr && gate[4 * comp] == 0u) return;  // gated launch: runs only when the flag is set
+  if (lv.active != nullptr && !lv.active[comp]) return;  // converged replica of a stacked batch
   __shared__ T sp[2][G::SH * ZC_W];
   __shared__ T wt[125];
-  const PatchDesc p = lv.patches[0];
+  const PatchDesc p = lv.patches[comp];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZC_TX + tx;
   const T inv = pick<T>(lv.inv12h2, lv.inv12h2_f);
   if (MODE == OP_JACOBI || MODE == OP_JACOBI0) {
@@ -635,7 +638,7 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
   }
   const int hs = (hy + 2) * ZC_W + hx + 2;
   const int c0 = (ty + 2) * ZC_W + tx + 2;  // shared index of row r: c0 + r * ZC_TY * ZC_W
-  const int tile = blockIdx.x % ntiles, ka = (blockIdx.x / ntiles) * kc, kb = min(nz, ka + kc);
+  const int tile = blk % ntiles, ka = (blk / ntiles) * kc, kb = min(nz, ka + kc);
   __syncthreads();  // weight table
   if (ka >= kb) return;
   const int i0 = (tile % ntx) * ZC_TX, j0 = (tile / ntx) * G::TH;
@@ -843,7 +846,10 @@ __device__ __forceinline__ double fx_to_double(long long t) {
 __global__ void __launch_bounds__(256) k_absmax_patch(LevelView lv, const double* __restrict__ x,
                                                       unsigned long long* __restrict__ acc) {
   pdl_wait();
-  const PatchDesc p = lv.patches[0];
+  // stacked component batches: blockIdx.y = replica, its maximum in acc[2 * replica]
+  if (lv.active != nullptr && !lv.active[blockIdx.y]) return;  // converged replica of a stacked batch
+  const PatchDesc p = lv.patches[blockIdx.y];
+  acc += 2 * blockIdx.y;
   const int n0 = p.n[0], n1 = p.n[1], rows = p.n[1] * p.n[2];
   unsigned long long v = 0ull;
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
@@ -870,10 +876,14 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, 2)
   using G = ZcGeom<R>;
   pdl_wait();
   __shared__ long long sp[2][G::SH * ZC_W];
-  const PatchDesc p = lv.patches[0];
+  // stacked component batches: the grid holds ncomp equal parts, part c on replica c with its
+  // own frame and flag (fxs[2c], fxs[2c + 1])
+  const int bpc = gridDim.x / lv.ncomp, comp = blockIdx.x / bpc, blk = blockIdx.x % bpc;
+  if (lv.active != nullptr && !lv.active[comp]) return;  // converged replica of a stacked batch
+  const PatchDesc p = lv.patches[comp];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZC_TX + tx;
-  unsigned* __restrict__ flag = reinterpret_cast<unsigned*>(lv.fxs + 1);
-  const int emax = (int)((lv.fxs[0] >> 52) & 0x7ffull);
+  unsigned* __restrict__ flag = reinterpret_cast<unsigned*>(lv.fxs + 2 * comp + 1);
+  const int emax = (int)((lv.fxs[2 * comp] >> 52) & 0x7ffull);
   if (emax == 0x7ff || (emax != 0 && emax < 53)) {  // non-finite, or a frame below the normal range
     if (tid == 0) *flag = 1u;
     return;
@@ -904,7 +914,7 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, 2)
   }
   const int hs = (hy + 2) * ZC_W + hx + 2;
   const int c0 = (ty + 2) * ZC_W + tx + 2;
-  const int tile = blockIdx.x % ntiles, ka = (blockIdx.x / ntiles) * kc, kb = min(nz, ka + kc);
+  const int tile = blk % ntiles, ka = (blk / ntiles) * kc, kb = min(nz, ka + kc);
   if (ka >= kb) return;
   const int i0 = (tile % ntx) * ZC_TX, j0 = (tile / ntx) * G::TH;
   const int i = i0 + tx;
@@ -3101,6 +3111,8 @@ __global__ void k_maxnorm(LevelView lv, int nby, const T* __restrict__ x, const 
 //   k_update_valid  phi += X on the valid cells (invalid cells are recomputed by the
 //                   average-down that starts the next composite residual), and clears the
 //                   norm accumulator for that residual.
+//   Stacked component batches: blockIdx.y = replica c over elements [c n, (c + 1) n) (n the
+//   replica stride), its norm in acc[c], its update skipped once active[c] is 0.
 __global__ void __launch_bounds__(256) k_norm_convert(long long n, const double* __restrict__ r,
                                                       const unsigned char* __restrict__ vmask, float* __restrict__ rin,
                                                       unsigned long long* __restrict__ acc) {
@@ -3108,7 +3120,9 @@ __global__ void __launch_bounds__(256) k_norm_convert(long long n, const double*
   __shared__ unsigned long long sm[8];
   unsigned long long v = 0ull;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+  const long long e0 = (long long)blockIdx.y * n;
+  acc += blockIdx.y;
+  for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + n; e += stride) {
     const double x = r[e];
     if (rin != nullptr) rin[e] = (float)x;
     if (vmask[e]) {
@@ -3135,11 +3149,14 @@ __global__ void __launch_bounds__(256) k_norm_convert(long long n, const double*
 template <typename S>
 __global__ void __launch_bounds__(256) k_update_valid(long long n, const S* __restrict__ x, double* __restrict__ phi,
                                                       const unsigned char* __restrict__ vmask,
-                                                      unsigned long long* __restrict__ acc_clear) {
+                                                      unsigned long long* __restrict__ acc_clear,
+                                                      const int* __restrict__ active) {
   pdl_wait();
-  if (acc_clear != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *acc_clear = 0ull;
+  if (acc_clear != nullptr && blockIdx.x == 0 && threadIdx.x == 0) acc_clear[blockIdx.y] = 0ull;
+  if (active != nullptr && !active[blockIdx.y]) return;  // converged replica: phi stays
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+  const long long e0 = (long long)blockIdx.y * n;
+  for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + n; e += stride)
     if (vmask[e]) phi[e] += (double)x[e];
 }
 
@@ -3283,8 +3300,9 @@ __global__ void k_mean_from_sums(const double* __restrict__ sf, const double* __
 // leading n x n block of the inverse of [A 1; 1^T 0] (the constraint right-hand side is 0).
 template <typename T, int D>
 __global__ void k_bottom(const double* __restrict__ minv, int n, int ld, PatchDesc p, const T* __restrict__ b,
-                         T* __restrict__ x) {
+                         T* __restrict__ x, long long cstride) {
   pdl_wait();
+  p.off += blockIdx.x * cstride;  // stacked component batches: one block per replica
   extern __shared__ double sb[];
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const int i = t % p.n[0];

@@ -61,8 +61,11 @@ struct amr_operator {
   double* hf = nullptr;
   double* hbc = nullptr;
   // captured solve (use_graph): one graph = prologue + device-side while loop over V-cycles
-  struct DevStats* d_stats = nullptr;
-  struct DevStats* h_stats = nullptr;  // pinned
+  struct DevStats* d_stats = nullptr;   // one per replica of a stacked component batch
+  struct DevStats* h_stats = nullptr;   // pinned
+  int* d_active = nullptr;              // replicas still iterating (stacked batches)
+  unsigned long long* h_cnorm = nullptr;  // pinned copy of the per-replica norms
+  struct StackCtx* stack = nullptr;       // stacked batch led by this operator (amr_batch_solve)
   double* h_scal = nullptr;            // pinned copy of the hierarchy's device scalars
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -139,6 +142,7 @@ inline amr_status launch_check() {
 // and y extent a multiple of the tile height.  amr_set_bulk_sweep: 0 never, 1 (default) where
 // the tile autotuner finds it fastest, 2 wherever eligible.
 std::atomic<int> g_bulk_sweep{1};
+std::atomic<int> g_stack_batches{0};  // amr_set_stacked_batches
 #ifndef SW_TILE_Y
 #define SW_TILE_Y 16
 #endif
@@ -150,12 +154,14 @@ std::atomic<int> g_bulk_sweep{1};
 #endif
 constexpr int SW_TY = SW_TILE_Y, SW_RW = SW_ROWS_PER_WARP, SW_S = SW_STAGES, SW_MINZ = 8;
 inline bool sw_eligible(const LevelView& lv) {
-  if (g_bulk_sweep.load(std::memory_order_relaxed) == 0 || lv.D != 3 || lv.npatch != 1) return false;
+  if (g_bulk_sweep.load(std::memory_order_relaxed) == 0 || lv.D != 3 || lv.npatch != lv.ncomp) return false;
   if (lv.maxn[0] % sw3::TX != 0 || lv.maxn[1] % SW_TY != 0 || lv.maxn[2] < 4) return false;
   const long long px = ((lv.maxn[0] + 2 * NG) + 3) / 4 * 4;
   return px * (lv.maxn[1] + 2 * NG) * (lv.maxn[2] + 2 * NG) < (1LL << 31);
 }
 constexpr int TILE_BULK = 8;  // tile-table code of the bulk-copy 3-D kernel
+
+void free_stack(amr_operator* op);  // stacked component batches (defined with amr_batch_solve)
 
 // ---------------------------------------------------------------- tile autotuner
 // Rows per thread of the tiled 2-D kernel and of the z-chunked 3-D kernel, per (dimension,
@@ -266,16 +272,28 @@ LevelView mg_view(const amr_hierarchy* h, int m, const int* bc) {
   v.h = g.h;
   for (int e = 0; e < 3; ++e) { v.ndom[e] = g.n[e]; v.maxn[e] = g.n[e]; }
   for (int f = 0; f < 6; ++f) { v.bc[f] = bc[f]; v.bc_off[f] = 0; v.bc_pitch[f] = 1; }
-  v.ncells = (double)g.n[0] * g.n[1] * g.n[2];
+  v.ncells = (double)g.n[0] * g.n[1] * g.n[2] * h->ncomp;
   v.p0 = g.patch;
+  v.npatch = h->ncomp;
+  v.ncomp = h->ncomp;
+  v.cstride = g.cstride;
+  v.active = h->ncomp > 1 ? h->d_active : nullptr;
   finish_view(v);
   return v;
 }
 
 // range [first, end) of a level's elements inside a composite field
-inline void level_range(const amr_hierarchy* h, int l, long long& a, long long& b) {
-  a = h->lev[l].patches.front().off;
-  b = (l + 1 < h->L) ? h->lev[l + 1].patches.front().off : h->nelems;
+inline void level_range(const amr_hierarchy* h, int l, long long& a, long long& b, int comp = 0) {
+  // replica comp of a stacked component batch: its patches are comp * (level's patches per
+  // replica) onwards, its layout ends at (comp + 1) * cstride
+  const int npl = (int)h->lev[l].patches.size() / h->ncomp;
+  a = h->lev[l].patches[(size_t)comp * npl].off;
+  if (l + 1 < h->L) {
+    const int npn = (int)h->lev[l + 1].patches.size() / h->ncomp;
+    b = h->lev[l + 1].patches[(size_t)comp * npn].off;
+  } else {
+    b = h->ncomp > 1 ? (comp + 1) * h->cstride : h->nelems;
+  }
 }
 
 // ---------------------------------------------------------------- host bottom matrix
@@ -353,7 +371,8 @@ bool invert(std::vector<double>& A, int n) {
 // The z-chunked 3-D operator runs on single-patch levels whose x / y extents are multiples of
 // its 32 x 8R tile and whose padded patch has fewer than 2^31 elements (32-bit offsets).
 inline bool zc_eligible(const LevelView& lv, int R) {
-  if (lv.D != 3 || lv.npatch != 1 || lv.maxn[0] % ZC_TX != 0 || lv.maxn[1] % (ZC_TY * R) != 0 || lv.maxn[2] < MIN_BOX)
+  // one patch per component (stacked component batches: ncomp replicas of one patch)
+  if (lv.D != 3 || lv.npatch != lv.ncomp || lv.maxn[0] % ZC_TX != 0 || lv.maxn[1] % (ZC_TY * R) != 0 || lv.maxn[2] < MIN_BOX)
     return false;
   const long long px = ((lv.maxn[0] + 2 * NG) + 3) / 4 * 4;
   return px * (lv.maxn[1] + 2 * NG) * (lv.maxn[2] + 2 * NG) < (1LL << 31);
@@ -389,11 +408,12 @@ template <typename T, int M, int R>
 void launch_zc(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T O, const unsigned char* vmask,
                cudaStream_t st, const unsigned* gate = nullptr) {
   const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * R)), nz = lv.maxn[2];
-  const int nch = std::max(1, std::min(zc_blocks<T, M, R>() / ntiles, nz / 4));
+  const int nc = std::max(1, lv.ncomp);  // stacked component batches: one part of the grid per replica
+  const int nch = std::max(1, std::min(zc_blocks<T, M, R>() / (ntiles * nc), nz / 4));
   const int kc = (nz + nch - 1) / nch;
   const int G = ntiles * ((nz + kc - 1) / kc);
-  launch(k_level_op3d_zc<T, M, R>, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, A, B, O, vmask,
-         gate);
+  launch(k_level_op3d_zc<T, M, R>, G * nc, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, A, B, O,
+         vmask, gate);
 }
 
 template <typename T, int M>
@@ -439,18 +459,23 @@ TmapEncodeFn tmap_encoder() {
 // Tensor map of a single-patch field over its padded patch (dimensions: row pitch, n_y + 4,
 // n_z + 4), boxes of 68 x rows x 1 values.
 template <typename T>
-amr_status encode_patch_tmap(CUtensorMap* tm, const T* field, const PatchDesc& p, int rows) {
+amr_status encode_patch_tmap(CUtensorMap* tm, const T* field, const PatchDesc& p, int rows, int ncomp,
+                             long long cstride) {
   const TmapEncodeFn enc = tmap_encoder();
   if (enc == nullptr) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return AMR_ERR_CUDA;
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)p.sy, (cuuint64_t)(p.n[1] + 2 * NG), (cuuint64_t)(p.n[2] + 2 * NG)};
-  const cuuint64_t strides[2] = {(cuuint64_t)p.sy * sizeof(T), (cuuint64_t)p.sz * sizeof(T)};
-  const cuuint32_t box[3] = {(cuuint32_t)sw3::XW, (cuuint32_t)rows, 1u};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  // dimension 3: the replicas of a stacked component batch (extent 1 otherwise)
+  const long long pz = p.n[2] + 2 * NG;
+  const cuuint64_t dims[4] = {(cuuint64_t)p.sy, (cuuint64_t)(p.n[1] + 2 * NG), (cuuint64_t)pz,
+                              (cuuint64_t)std::max(1, ncomp)};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.sy * sizeof(T), (cuuint64_t)p.sz * sizeof(T),
+                                 (cuuint64_t)(ncomp > 1 ? cstride : p.sz * pz) * sizeof(T)};
+  const cuuint32_t box[4] = {(cuuint32_t)sw3::XW, (cuuint32_t)rows, 1u, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   const CUresult r =
-      enc(tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+      enc(tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
           const_cast<T*>(field + p.off), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -468,13 +493,14 @@ amr_status launch_sw(const LevelView& lv, const T* x, const T* f, T* out, T A, T
   constexpr size_t smem = sw3::smem_bytes<T, M, SW_TY, SW_S>();
   constexpr int threads = 32 * (SW_TY / SW_RW + 2);
   CUtensorMap tmx{}, tmf{};
-  if (M != OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmx, x, lv.p0, SW_TY + 4));
-  if (M == OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmf, f, lv.p0, SW_TY));
+  const int nc = std::max(1, lv.ncomp);  // stacked component batches: one part of the grid per replica
+  if (M != OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmx, x, lv.p0, SW_TY + 4, nc, lv.cstride));
+  if (M == OP_JACOBI0) TRY(encode_patch_tmap<T>(&tmf, f, lv.p0, SW_TY, nc, lv.cstride));
   const int ntx = lv.maxn[0] / sw3::TX, ntiles = ntx * (lv.maxn[1] / SW_TY), nz = lv.maxn[2];
   const int wave = wave_blocks(reinterpret_cast<const void*>(sw_kernel<T, M>()), threads, smem);
-  const int nch = std::max(1, std::min(wave / ntiles, nz / SW_MINZ));
-  launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, f, out, A, B,
-         O, vmask, gate);
+  const int nch = std::max(1, std::min(wave / (ntiles * nc), nz / SW_MINZ));
+  launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch * nc), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, f, out,
+         A, B, O, vmask, gate);
   return launch_check();
 }
 
@@ -501,16 +527,18 @@ inline bool fx_eligible(const LevelView& lv) {
 int fx_blocks() { return wave_blocks(reinterpret_cast<const void*>(k_resid3d_fx), ZC_TX * ZC_TY, 0); }
 amr_status launch_resid_fx(const LevelView& lv, const double* x, const double* f, double* out, double alpha,
                            double beta, cudaStream_t st) {
-  CK(cudaMemsetAsync(lv.fxs, 0, 2 * sizeof(unsigned long long), st));
+  const int nc = std::max(1, lv.ncomp);  // stacked component batches: a frame and a flag per replica
+  CK(cudaMemsetAsync(lv.fxs, 0, 2 * nc * sizeof(unsigned long long), st));
   const long long rows = (long long)lv.maxn[1] * lv.maxn[2];
   const int amax_blocks = wave_blocks(reinterpret_cast<const void*>(k_absmax_patch), 256, 0);
-  launch(k_absmax_patch, (unsigned)std::min<long long>(rows, amax_blocks), 256, 0, st, lv, x, lv.fxs);
+  launch(k_absmax_patch, dim3((unsigned)std::min<long long>(rows, std::max(1, amax_blocks / nc)), nc, 1), 256, 0, st,
+         lv, x, lv.fxs);
   TRY(launch_check());
   const int ntx = lv.maxn[0] / ZC_TX, ntiles = ntx * (lv.maxn[1] / (ZC_TY * 2)), nz = lv.maxn[2];
-  const int nch = std::max(1, std::min(fx_blocks() / ntiles, nz / 4));
+  const int nch = std::max(1, std::min(fx_blocks() / (ntiles * nc), nz / 4));
   const int kc = (nz + nch - 1) / nch;
   const int G = ntiles * ((nz + kc - 1) / kc);
-  launch(k_resid3d_fx, G, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, alpha, beta);
+  launch(k_resid3d_fx, G * nc, dim3(ZC_TX, ZC_TY, 1), 0, st, lv, ntx, ntiles, kc, x, f, out, alpha, beta);
   TRY(launch_check());
   launch_zc<double, OP_RESID, 2>(lv, x, f, out, alpha, beta, 0.0, nullptr, st,
                                  reinterpret_cast<const unsigned*>(lv.fxs + 1));
@@ -1311,7 +1339,7 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   Scratch<T>& S = scratch<T>(op);
   const int M = (int)h->mg.size() - 1;
   const LevelView lv = mg_view(h, m, op->bc);
-  if (p.fuse_coarse == 1) {
+  if (p.fuse_coarse == 1 && h->ncomp == 1) {
     int m0;
     size_t bytes;
     TRY((fused_config<T, D, TR>(op, m0, bytes)));
@@ -1319,11 +1347,13 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   }
   if constexpr (D == 3) {
     // fuse_coarse = 2: the coarse end of the pyramid in one cluster launch
-    if (p.fuse_coarse == 2 && m == coarse_cluster_m0(h)) return coarse_cluster<T, D, TR>(op, p, m, b, x, t, st);
+    if (p.fuse_coarse == 2 && h->ncomp == 1 && m == coarse_cluster_m0(h))
+      return coarse_cluster<T, D, TR>(op, p, m, b, x, t, st);
   }
   if (m == M) {
     const int n = op->nbot;
-    launch(k_bottom<T, D>, 1, 256, n * sizeof(double), st, TR ? op->d_binvT : op->d_binv, n, op->ldb, h->mg[m].patch, b, x);
+    launch(k_bottom<T, D>, h->ncomp, 256, n * sizeof(double), st, TR ? op->d_binvT : op->d_binv, n, op->ldb,
+           h->mg[m].patch, b, x, h->mg[m].cstride);
     return launch_check();
   }
   const LevelView cv = mg_view(h, m + 1, op->bc);
@@ -1360,9 +1390,9 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   }
   TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
-  TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], 1, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
+  TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], h->ncomp, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
   TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
-  TRY(prolong_blocks<T, D>(lv, cv, op->d_mgx[m], 1, xm, S.mx[m + 1], x, (T*)nullptr, st));
+  TRY(prolong_blocks<T, D>(lv, cv, op->d_mgx[m], h->ncomp, xm, S.mx[m + 1], x, (T*)nullptr, st));
   TRY(smooth_from<T, D, TR>(h, 0, lv, b, x, t, p.nu2, op->alpha, op->beta, p.omega, false, st));
   return AMR_OK;
 }
@@ -1606,9 +1636,9 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
   CK(cudaMemsetAsync(S.X, 0, bytes, st));
   CK(cudaMemsetAsync(S.T1, 0, bytes, st));
   CK(cudaMemsetAsync(S.T2, 0, bytes, st));
-  {
+  for (int c = 0; c < h->ncomp; ++c) {
     long long a, b;
-    level_range(h, L, a, b);
+    level_range(h, L, a, b, c);
     CK(cudaMemcpyAsync(S.R + a, r + a, (size_t)(b - a) * sizeof(T), cudaMemcpyDeviceToDevice, st));
   }
   std::vector<LevelView> lv(h->L);
@@ -2000,13 +2030,22 @@ inline unsigned flat_blocks(long long n) {
   return (unsigned)std::min<long long>((n + 255) / 256, 8LL * m);
 }
 
-// valid-cell max-norm of op->Res into *acc, and (mixed precision) its FP32 copy into rin
-inline amr_status norm_convert(amr_operator* op, int prec, unsigned long long* acc, cudaStream_t st) {
+// elements of one replica of a stacked component batch (the whole array otherwise)
+inline long long rep_elems(const amr_hierarchy* h) { return h->ncomp > 1 ? h->cstride : h->nelems; }
+
+// valid-cell max-norm of x into acc[c] for every replica c, and (rin given) x rounded to FP32
+inline amr_status norm_convert_field(amr_operator* op, const double* x, float* rin, unsigned long long* acc,
+                                     cudaStream_t st) {
   amr_hierarchy* h = op->h;
-  float* rin = prec == AMR_MIXED ? op->s32.rin : nullptr;
-  launch(k_norm_convert, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const double*)op->Res,
-         (const unsigned char*)h->d_valid, rin, acc);
+  const long long n = rep_elems(h);
+  launch(k_norm_convert, dim3(flat_blocks(n), h->ncomp, 1), 256, 0, st, n, x, (const unsigned char*)h->d_valid, rin,
+         acc);
   return launch_check();
+}
+
+// valid-cell max-norm of op->Res into acc (per replica), and (mixed precision) its FP32 copy
+inline amr_status norm_convert(amr_operator* op, int prec, unsigned long long* acc, cudaStream_t st) {
+  return norm_convert_field(op, op->Res, prec == AMR_MIXED ? op->s32.rin : nullptr, acc, st);
 }
 
 // One V-cycle iteration of the captured solve loop: V-cycle on the residual (FP32 copy made
@@ -2016,22 +2055,29 @@ template <int D>
 amr_status iteration_body(amr_operator* op, int prec, const amr_solver_params& p, double* phi, const double* bc,
                           cudaStream_t st) {
   amr_hierarchy* h = op->h;
-  unsigned long long* rbits = reinterpret_cast<unsigned long long*>(h->d_scalar);
+  unsigned long long* rbits = h->d_cnorm;
+  const long long n = rep_elems(h);
+  const dim3 grid(flat_blocks(n), h->ncomp, 1);
+  const int* active = h->ncomp > 1 ? op->d_active : nullptr;  // converged replicas keep their phi
   if (prec == AMR_MIXED) {
     Scratch<float>& Sf = op->s32;
     TRY(vcycle_corr<float, D>(op, p, Sf.rin, st));
-    launch(k_update_valid<float>, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const float*)Sf.X, phi,
-           (const unsigned char*)h->d_valid, rbits);
+    launch(k_update_valid<float>, grid, 256, 0, st, n, (const float*)Sf.X, phi, (const unsigned char*)h->d_valid, rbits,
+           active);
   } else {
     Scratch<double>& Sd = op->s64;
     TRY(vcycle_corr<double, D>(op, p, op->Res, st));
-    launch(k_update_valid<double>, flat_blocks(h->nelems), 256, 0, st, (long long)h->nelems, (const double*)Sd.X, phi,
-           (const unsigned char*)h->d_valid, rbits);
+    launch(k_update_valid<double>, grid, 256, 0, st, n, (const double*)Sd.X, phi, (const unsigned char*)h->d_valid,
+           rbits, active);
   }
   TRY(launch_check());
   TRY(composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, st));
   return norm_convert(op, prec, rbits, st);
 }
+
+__global__ void k_check_b(cudaGraphConditionalHandle handle, int use_cond, int n, const unsigned long long* __restrict__ rbits,
+                          const unsigned long long* __restrict__ fbits, double rtol, double atol, int maxv,
+                          DevStats* __restrict__ s, int* __restrict__ active);
 
 template <int D>
 amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* bc) {
@@ -2041,14 +2087,17 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
   if (!op->cap_stream) CK(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
   if (!op->body_stream) CK(cudaStreamCreateWithFlags(&op->body_stream, cudaStreamNonBlocking));
   cudaStream_t cs = op->cap_stream, bs = op->body_stream;
-  unsigned long long* rbits = reinterpret_cast<unsigned long long*>(h->d_scalar);
-  unsigned long long* fbits = reinterpret_cast<unsigned long long*>(h->d_scalar + 5);
+  // per-replica residual and right-hand-side norms (one replica unless a stacked batch)
+  const int nc = h->ncomp;
+  unsigned long long* rbits = h->d_cnorm;
+  unsigned long long* fbits = h->d_cnorm + nc;
   amr_status result = AMR_OK;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   const long long l0 = g_launches.load();
   do {
-    cudaMemsetAsync(op->d_stats, 0, sizeof(DevStats), cs);
-    cudaMemsetAsync(rbits, 0, sizeof(unsigned long long), cs);
+    cudaMemsetAsync(op->d_stats, 0, nc * sizeof(DevStats), cs);
+    cudaMemsetAsync(rbits, 0, nc * sizeof(unsigned long long), cs);
+    if (nc > 1) cudaMemsetAsync(op->d_active, 1, nc * sizeof(int), cs);  // every replica running
     if ((result = composite_op<D>(op, OP_RESID, phi, op->F, op->Res, bc, cs)) != AMR_OK) break;
     if ((result = norm_convert(op, p.precision, rbits, cs)) != AMR_OK) break;
     cudaStreamCaptureStatus cst;
@@ -2056,7 +2105,9 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
     if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
     cudaGraphConditionalHandle handle;
     if (cudaGraphConditionalHandleCreate(&handle, cg, 0, 0) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
-    launch(k_check, 1, 1, 0, cs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+    if (nc > 1) launch(k_check_b, 1, 128, 0, cs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, p.max_vcycles,
+                       op->d_stats, op->d_active);
+    else launch(k_check, 1, 1, 0, cs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
     if ((result = launch_check()) != AMR_OK) break;
     op->launches_pre = g_launches.load() - l0;
     const cudaGraphNode_t* deps = nullptr;
@@ -2078,7 +2129,9 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
     const long long l1 = g_launches.load();
     amr_status rb = iteration_body<D>(op, p.precision, p, phi, bc, bs);
     if (rb == AMR_OK) {
-      launch(k_check, 1, 1, 0, bs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+      if (nc > 1) launch(k_check_b, 1, 128, 0, bs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, p.max_vcycles,
+                         op->d_stats, op->d_active);
+      else launch(k_check, 1, 1, 0, bs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
       rb = launch_check();
     }
     op->launches_body = g_launches.load() - l1;
@@ -2118,9 +2171,12 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   amr_hierarchy* h = op->h;
   const size_t bytes = (size_t)h->nelems * sizeof(double);
   if (!op->d_stats) {
-    TRY(dalloc(&op->d_stats, 1));
-    CK(cudaMallocHost(&op->h_stats, sizeof(DevStats)));
+    const int nc = h->ncomp;
+    TRY(dalloc(&op->d_stats, nc));
+    if (!op->d_active) TRY(dalloc(&op->d_active, nc));
+    CK(cudaMallocHost(&op->h_stats, nc * sizeof(DevStats)));
     CK(cudaMallocHost(&op->h_scal, 8 * sizeof(double)));
+    CK(cudaMallocHost(&op->h_cnorm, 2 * nc * sizeof(unsigned long long)));
   }
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
   else TRY(ensure_scratch<double>(op));
@@ -2132,7 +2188,9 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   }
   if (p.zero_initial) CK(cudaMemsetAsync(phi, 0, bytes, st));
   TRY(avgdown_all<D>(h, op->F, st));
-  TRY(maxnorm_dev<double, D>(h, op->F, reinterpret_cast<unsigned long long*>(h->d_scalar + 5), st));
+  // ||f||_inf over the valid cells of every replica
+  CK(cudaMemsetAsync(h->d_cnorm + h->ncomp, 0, h->ncomp * sizeof(unsigned long long), st));
+  TRY(norm_convert_field(op, op->F, nullptr, h->d_cnorm + h->ncomp, st));
   const bool hit = op->exec && op->g_phi == phi && op->g_bc == bc && op->g_prec == p.precision &&
                    op->g_nu1 == p.nu1 && op->g_nu2 == p.nu2 && op->g_maxv == p.max_vcycles &&
                    op->g_omega == p.omega && op->g_rtol == p.rtol && op->g_atol == p.atol &&
@@ -2141,26 +2199,34 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   CK(cudaGraphLaunch(op->exec, st));
   if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
   else TRY(avgdown_all<D>(h, phi, st));
-  CK(cudaMemcpyAsync(op->h_stats, op->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(op->h_stats, op->d_stats, h->ncomp * sizeof(DevStats), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(op->h_scal, h->d_scalar, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(op->h_cnorm, h->d_cnorm, 2 * h->ncomp * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   return AMR_OK;
 }
 
-amr_status solve_graph_finish(amr_operator* op, amr_solve_stats* stats) {
-  TRY(sweep3d_check_flag());
-  const DevStats& ds = *op->h_stats;
-  g_launches.fetch_add(op->launches_pre + (long long)ds.iter * op->launches_body);
+// Statistics of replica c of a finished captured solve (c = 0 for a single solve).
+amr_status solve_graph_stats(amr_operator* op, int c, amr_solve_stats* stats) {
+  const DevStats& ds = op->h_stats[c];
   amr_solve_stats loc{};
   loc.vcycles = ds.iter;
   for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
   loc.final_res = ds.hist[std::min(ds.iter, 63)];
-  loc.rhs_norm = op->h_scal[5];
+  loc.rhs_norm = __builtin_bit_cast(double, op->h_cnorm[op->h->ncomp + c]);
   loc.removed_mean = op->neumann ? op->h_scal[6] : 0.0;
   if (stats) *stats = loc;
   if (ds.status == 0) return AMR_OK;
   if (ds.status == 2) { set_error("residual is not finite"); return AMR_ERR_NONFINITE; }
   set_error("max_vcycles reached");
   return AMR_ERR_NOT_CONVERGED;
+}
+
+amr_status solve_graph_finish(amr_operator* op, amr_solve_stats* stats) {
+  TRY(sweep3d_check_flag());
+  int most = 0;
+  for (int c = 0; c < op->h->ncomp; ++c) most = std::max(most, op->h_stats[c].iter);
+  g_launches.fetch_add(op->launches_pre + (long long)most * op->launches_body);
+  return solve_graph_stats(op, 0, stats);
 }
 
 template <int D>
@@ -2874,6 +2940,125 @@ amr_status batch_worklist(amr_operator* const* ops, int n, const amr_solver_para
 
 }  // namespace
 
+// =================================================================== stacked component batches
+// A batch of problems that share one 3-D hierarchy geometry and one operator (alpha, beta,
+// boundary types; not the pure-Neumann PPE) -- the Helmholtz systems of the velocity
+// components -- is solved as one problem on a stacked hierarchy that holds one replica of
+// every patch and work list per problem: every phase of the V-cycle and of the refinement
+// loop is one launch over all replicas, the stopping test is per replica (a converged
+// replica's phi is no longer updated; the loop runs until every replica has converged).
+struct StackCtx {
+  std::vector<const amr_operator*> key;
+  amr_hierarchy* hs = nullptr;
+  amr_operator* op = nullptr;
+  double* phi = nullptr;
+  double* f = nullptr;
+};
+
+namespace {
+
+void free_stack(amr_operator* op) {
+  if (!op->stack) return;
+  StackCtx* c = op->stack;
+  cudaFree(c->phi);
+  cudaFree(c->f);
+  amr_operator_destroy(c->op);
+  if (c->hs) {
+    free_hierarchy(c->hs);
+    delete c->hs;
+  }
+  delete c;
+  op->stack = nullptr;
+}
+
+bool same_geometry(const amr_hierarchy* a, const amr_hierarchy* b) {
+  if (a->D != b->D || a->r != b->r || a->L != b->L || a->h0 != b->h0 || a->ncomp != 1 || b->ncomp != 1) return false;
+  for (int e = 0; e < 3; ++e)
+    if (a->n0[e] != b->n0[e]) return false;
+  for (int l = 0; l < a->L; ++l) {
+    const auto& pa = a->lev[l].patches;
+    const auto& pb = b->lev[l].patches;
+    if (pa.size() != pb.size()) return false;
+    for (size_t k = 0; k < pa.size(); ++k)
+      for (int e = 0; e < 3; ++e)
+        if (pa[k].n[e] != pb[k].n[e] || pa[k].lo[e] != pb[k].lo[e]) return false;
+  }
+  return true;
+}
+
+// the problems of a batch can be stacked: 3-D, two or more distinct operators on hierarchies
+// of one geometry, one operator, homogeneous non-Neumann data
+bool stackable(amr_operator* const* ops, int n) {
+  if (n < 2 || ops[0]->h->D != 3 || ops[0]->neumann) return false;
+  for (int k = 0; k < n; ++k) {
+    const amr_operator* a = ops[k];
+    if (a->h->ncomp != 1 || a->alpha != ops[0]->alpha || a->beta != ops[0]->beta || !same_geometry(a->h, ops[0]->h))
+      return false;
+    for (int f = 0; f < 6; ++f)
+      if (a->bc[f] != ops[0]->bc[f]) return false;
+    for (int j = 0; j < k; ++j)
+      if (ops[j] == a) return false;
+  }
+  return true;
+}
+
+amr_status batch_stacked(amr_operator* const* ops, int n, const amr_solver_params& q, double* const* phi,
+                         const double* const* f, amr_solve_stats* stats, int* status, cudaStream_t st) {
+  amr_operator* lead = ops[0];
+  const std::vector<const amr_operator*> key(ops, ops + n);
+  if (!lead->stack || lead->stack->key != key) {
+    free_stack(lead);
+    std::unique_ptr<StackCtx> c(new StackCtx());
+    c->key = key;
+    std::string err;
+    amr_status s1 = stack_hierarchy(lead->h, n, &c->hs, err);
+    if (s1 != AMR_OK) {
+      set_error(err);
+      return s1;
+    }
+    s1 = amr_operator_create(c->hs, lead->alpha, lead->beta, lead->bc, &c->op);
+    if (s1 == AMR_OK) s1 = dalloc(&c->phi, c->hs->nelems);
+    // the per-replica running flags of the captured solve (allocated below on the first
+    // launch) are what the replica kernels test; allocate them now so views can carry them
+    if (s1 == AMR_OK && !c->op->d_active) s1 = dalloc(&c->op->d_active, n);
+    if (s1 == AMR_OK) {
+      if (cudaMemset(c->op->d_active, 1, n * sizeof(int)) != cudaSuccess) s1 = AMR_ERR_CUDA;
+      c->hs->d_active = c->op->d_active;
+    }
+    if (s1 == AMR_OK) s1 = dalloc(&c->f, c->hs->nelems);
+    if (s1 == AMR_OK && (cudaMemset(c->phi, 0, c->hs->nelems * sizeof(double)) != cudaSuccess ||
+                         cudaMemset(c->f, 0, c->hs->nelems * sizeof(double)) != cudaSuccess))
+      s1 = AMR_ERR_CUDA;
+    lead->stack = c.release();
+    if (s1 != AMR_OK) {
+      free_stack(lead);
+      return s1;
+    }
+  }
+  StackCtx* c = lead->stack;
+  const long long one = lead->h->nelems, cs = c->hs->cstride;
+  for (int k = 0; k < n; ++k) {
+    CK(cudaMemcpyAsync(c->f + k * cs, f[k], one * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (!q.zero_initial) CK(cudaMemcpyAsync(c->phi + k * cs, phi[k], one * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  TRY(solve_graph_launch<3>(c->op, q, c->phi, c->f, nullptr, st));
+  for (int k = 0; k < n; ++k)
+    CK(cudaMemcpyAsync(phi[k], c->phi + k * cs, one * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  TRY(sweep3d_check_flag());
+  int most = 0;
+  for (int k = 0; k < n; ++k) most = std::max(most, c->op->h_stats[k].iter);
+  g_launches.fetch_add(c->op->launches_pre + (long long)most * c->op->launches_body);
+  amr_status worst = AMR_OK;
+  for (int k = 0; k < n; ++k) {
+    const amr_status sk = solve_graph_stats(c->op, k, stats ? &stats[k] : nullptr);
+    if (status) status[k] = sk;
+    if (sk != AMR_OK && worst == AMR_OK) worst = sk;
+  }
+  return worst;
+}
+}  // namespace
+
 // =================================================================== allocation-free mean-zero
 // Scratch for amr_mean_zero_noalloc: the block partial sums (one double-double per block) and
 // three scalars live in this file-scope device array instead of hierarchy-owned memory, so
@@ -3012,6 +3197,12 @@ amr_status amr_set_bulk_sweep(int on) {
 }
 
 amr_status amr_check_kernel_flags(void) { return sweep3d_check_flag(); }
+
+amr_status amr_set_stacked_batches(int on) {
+  if (on != 0 && on != 1) { set_error("stacked-batch switch must be 0 or 1"); return AMR_ERR_INVALID_ARG; }
+  g_stack_batches.store(on, std::memory_order_relaxed);
+  return AMR_OK;
+}
 
 amr_status amr_profile_enable(int on) {
   // events are never reused: a cached instrumented graph keeps recording into its own
@@ -3171,15 +3362,19 @@ amr_status amr_operator_create(amr_hierarchy* h, double alpha, double beta, cons
     TRY(dalloc(&op->d_binvT, At.size()));
     CK(cudaMemcpy(op->d_binvT, At.data(), At.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
-  // multigrid transfer blocks
+  // multigrid transfer blocks (one per replica of a stacked component batch)
   for (size_t m = 0; m + 1 < h->mg.size(); ++m) {
-    XferBlock b{};
-    b.fpatch = 0;
-    b.cpatch = 0;
-    for (int q = 0; q < 3; ++q) { b.clo[q] = 0; b.chi[q] = h->mg[m + 1].n[q] - 1; }
+    std::vector<XferBlock> bs(h->ncomp);
+    for (int c = 0; c < h->ncomp; ++c) {
+      XferBlock& b = bs[c];
+      b = XferBlock{};
+      b.fpatch = c;
+      b.cpatch = c;
+      for (int q = 0; q < 3; ++q) { b.clo[q] = 0; b.chi[q] = h->mg[m + 1].n[q] - 1; }
+    }
     XferBlock* d = nullptr;
-    TRY(dalloc(&d, 1));
-    CK(cudaMemcpy(d, &b, sizeof(b), cudaMemcpyHostToDevice));
+    TRY(dalloc(&d, bs.size()));
+    CK(cudaMemcpy(d, bs.data(), bs.size() * sizeof(XferBlock), cudaMemcpyHostToDevice));
     op->d_mgx.push_back(d);
   }
   const size_t ne = (size_t)h->nelems;
@@ -3211,8 +3406,11 @@ void amr_operator_destroy(amr_operator* op) {
   if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
   if (op->body_stream) cudaStreamDestroy(op->body_stream);
   cudaFree(op->d_stats);
+  cudaFree(op->d_active);
   if (op->h_stats) cudaFreeHost(op->h_stats);
   if (op->h_scal) cudaFreeHost(op->h_scal);
+  if (op->h_cnorm) cudaFreeHost(op->h_cnorm);
+  free_stack(op);
   delete op;
 }
 
@@ -3326,6 +3524,9 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
   bool worklist = n > 0;
   for (int k = 0; k < n && worklist; ++k) worklist = batch_levels(ops[k], q) >= 0;
   if (worklist) return batch_worklist(ops, n, q, phi, f, stats, status, st);
+  // one 3-D geometry and operator for every problem: one stacked solve
+  if (g_stack_batches.load(std::memory_order_relaxed) && stackable(ops, n))
+    return batch_stacked(ops, n, q, phi, f, stats, status, st);
   std::lock_guard<std::mutex> lock(mu);
   // problems that share a hierarchy share its reduction scratch: same stream, in order
   std::vector<const amr_hierarchy*> hs;

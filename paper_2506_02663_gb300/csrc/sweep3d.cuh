@@ -82,14 +82,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
   return false;
 }
-// 3-D tiled TMA load of the box at (c0, c1, c2) of the tensor map into shared memory
-// (128-byte aligned), completing its bytes on the mbarrier
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+// 4-D tiled TMA load of the box at (c0, c1, c2, c3) of the tensor map into shared memory
+// (128-byte aligned), completing its bytes on the mbarrier; dimension 3 is the replica of a
+// stacked component batch (extent 1 otherwise)
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
                                           unsigned long long* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* tm) {
@@ -193,9 +194,13 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
       wt[q] = omega / (alpha + beta * inv * acc);
     }
   }
-  const PatchDesc p = lv.p0;
+  // stacked component batches: the grid holds ncomp equal parts, part c on replica c (tensor
+  // coordinate 3 = c; its patch offset for the stores and f)
+  const int bpc = gridDim.x / lv.ncomp, comp = blockIdx.x / bpc, blk = blockIdx.x % bpc;
+  PatchDesc p = lv.p0;
+  p.off += comp * lv.cstride;
   const int nz = p.n[2];
-  const int tile = blockIdx.x % ntiles, chunk = blockIdx.x / ntiles;
+  const int tile = blk % ntiles, chunk = blk / ntiles;
   const int ka = (int)(((long long)chunk * nz) / nch), kb = (int)(((long long)(chunk + 1) * nz) / nch);
   const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
   const int lz = p.lo[2], nzd = lv.ndom[2];
@@ -213,10 +218,13 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
   }
   __syncthreads();
   if (ka >= kb) return;
+  pdl_wait();
+  // converged replica of a stacked batch (the flags are written by the stopping test of the
+  // previous graph phase: read after the wait)
+  if (lv.active != nullptr && !lv.active[comp]) return;
   const int kfirst = NEEDX ? ka - 2 : ka;
   const int np = NEEDX ? (kb - ka) + 4 : (kb - ka);  // planes through the ring
-  pdl_wait();
-  if (gate != nullptr && *gate == 0u) return;  // gated launch: runs only when the flag is set
+  if (gate != nullptr && gate[4 * comp] == 0u) return;  // gated launch: runs only when the flag is set
 
   if (warp == NCW) {
     // ---------------------------------------------------------------- producer (one thread)
@@ -240,8 +248,8 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
       mbar_expect_tx(&full[sl], (unsigned)((NEEDX ? XH * XW : 0) + (wf ? TY * XW : 0)) * (unsigned)sizeof(T));
       T* sx = ring + (size_t)sl * SLOT;
       // padded coordinates: column i0 (cell i0 - 2), row j0 (cell j0 - 2) / j0 + 2, plane k + 2
-      if (NEEDX) tma_load3(sx, &tmx, i0, j0, k + NG, &full[sl]);
-      if (wf) tma_load3(sx + XSZ, &tmf, i0, j0 + NG, k + NG, &full[sl]);
+      if (NEEDX) tma_load4(sx, &tmx, i0, j0, k + NG, comp, &full[sl]);
+      if (wf) tma_load4(sx + XSZ, &tmf, i0, j0 + NG, k + NG, comp, &full[sl]);
     }
     if (!ok) atomicOr(err, 1u);
     // the block must not end while copies into its shared memory are in flight: wait
