@@ -71,6 +71,17 @@ struct CfiEntry {
   int fpatch;         // fine patch (index within its level)
 };
 
+// The 2^D fine CF ghost cells of one coarse parent (ratio 2, one face of one fine patch): they
+// share the parent's 5^D window, so the interpolation runs once per parent, dimension by
+// dimension.  Child c = sub_x + 2 sub_y + 4 sub_z; dst < 0 where a child is absent.
+struct CfiGroup {
+  long long src;     // window origin in its coarse patch, or -1 - index of its side table
+  long long dst[8];  // fine ghost cells
+  int cpatch;
+  signed char pos[3];
+  signed char pad;
+};
+
 struct CopyEntry {
   long long dst;
   long long src;
@@ -102,6 +113,8 @@ struct DeviceLists {
   CfiEntry* cfi = nullptr;
   long long* cfi_side = nullptr;
   long long ncfi = 0;
+  CfiGroup* cfig = nullptr;  // the same ghosts grouped by coarse parent (ratio 2)
+  long long ncfig = 0;
   CopyEntry* copy = nullptr;
   long long ncopy = 0;
   RefluxEntry* reflux = nullptr;
@@ -120,6 +133,7 @@ struct LevelHost {
   PatchDesc* d_patches = nullptr;
   std::vector<CfiEntry> cfi;
   std::vector<long long> cfi_side;
+  std::vector<long long> cfi_key;  // per CF ghost: its coarse parent and face (grouping key)
   std::vector<CopyEntry> copy;
   std::vector<RefluxEntry> reflux;  // this level's coarse cells bordering level+1
   std::vector<XferBlock> xfer;      // this level (coarse) <-> level+1 (fine)

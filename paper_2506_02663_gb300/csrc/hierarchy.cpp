@@ -213,6 +213,35 @@ static T* upload(const std::vector<T>& v) {
   return d;
 }
 
+// CF ghosts grouped by coarse parent (entries with one key): the shared window (origin,
+// coarse patch, position) of the first child, each child's destination at index sub_x +
+// 2 sub_y + 4 sub_z.  Ratio 2 only (no groups otherwise: the per-ghost list is used).
+static std::vector<CfiGroup> cfi_groups(const std::vector<CfiEntry>& cfi, const std::vector<long long>& key, int r,
+                                        int D) {
+  std::vector<CfiGroup> out;
+  if (r != 2 || cfi.empty() || key.size() != cfi.size()) return out;
+  std::vector<size_t> ord(cfi.size());
+  std::iota(ord.begin(), ord.end(), size_t(0));
+  std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return key[a] < key[b]; });
+  for (size_t i = 0; i < ord.size();) {
+    const CfiEntry& e0 = cfi[ord[i]];
+    CfiGroup g{};
+    g.src = e0.src;
+    g.cpatch = e0.cpatch;
+    for (int e = 0; e < 3; ++e) g.pos[e] = e0.pos[e];
+    for (int c = 0; c < 8; ++c) g.dst[c] = -1;
+    size_t j = i;
+    for (; j < ord.size() && key[ord[j]] == key[ord[i]]; ++j) {
+      const CfiEntry& e = cfi[ord[j]];
+      const int c = e.sub[0] + 2 * e.sub[1] + (D == 3 ? 4 * e.sub[2] : 0);
+      g.dst[c] = e.dst;
+    }
+    out.push_back(g);
+    i = j;
+  }
+  return out;
+}
+
 namespace {
 // level lookup over the level's bounding box (+ margin): patch id per cell, -1 outside
 struct LevelMap {
@@ -425,6 +454,12 @@ amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std
                         }
                   }
                   L.cfi.push_back(ce);
+                  {
+                    // grouping key: fine patch, face, coarse parent
+                    long long key = (long long)k * 6 + 2 * d + (g[d] < p.lo[d] ? 0 : 1);
+                    for (int e = D - 1; e >= 0; --e) key = key * C.ndom[e] + (long long)std::floor((double)g[e] / r);
+                    L.cfi_key.push_back(key);
+                  }
                   h->im_cfi_cell.push_back(padded_base + cidx);
                   for (int e = 0; e < D; ++e) {
                     h->im_cfi_start.push_back(start[e]);
@@ -581,6 +616,8 @@ amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, s
     B.first_patch = A.first_patch * k;
     const long long w3 = h->D == 3 ? 125 : 25;
     const long long nside = (long long)A.cfi_side.size() / w3;
+    long long key_span = 1;  // replica c's grouping keys are shifted by c * key_span
+    for (long long key : A.cfi_key) key_span = std::max(key_span, key + 1);
     for (int c = 0; c < k; ++c) {
       const long long o = c * stride;
       for (const Box& b : A.boxes) B.boxes.push_back(b);
@@ -596,6 +633,7 @@ amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, s
         e.fpatch += c * np;
         B.cfi.push_back(e);
       }
+      for (long long key : A.cfi_key) B.cfi_key.push_back(key + c * key_span);
       for (long long v : A.cfi_side) B.cfi_side.push_back(v + o);
       for (CopyEntry e : A.copy) {
         e.dst += o;
@@ -671,6 +709,11 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
       L.d_patches = upload(L.patches);
       L.dev.cfi = upload(L.cfi);
       L.dev.ncfi = (long long)L.cfi.size();
+      {
+        const std::vector<CfiGroup> g = cfi_groups(L.cfi, L.cfi_key, h->r, h->D);
+        L.dev.cfig = upload(g);
+        L.dev.ncfig = (long long)g.size();
+      }
       L.dev.cfi_side = upload(L.cfi_side);
       L.dev.copy = upload(L.copy);
       L.dev.ncopy = (long long)L.copy.size();
@@ -707,6 +750,7 @@ void free_hierarchy(amr_hierarchy* h) {
   for (auto& L : h->lev) {
     cudaFree(L.d_patches);
     cudaFree(L.dev.cfi);
+    cudaFree(L.dev.cfig);
     cudaFree(L.dev.cfi_side);
     cudaFree(L.dev.copy);
     cudaFree(L.dev.reflux);

@@ -814,16 +814,30 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
 // 7 for physical ghost values), or a non-finite one, sets ovf
 __device__ __forceinline__ long long fx_of(double x, int emax, int lim, bool& ovf) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ffull);
-  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53-bit significand
-  const int sh = e - emax;                                                     // x 2^S = m 2^sh
-  unsigned long long u = 0ull;
-  if (e != 0) {  // zero and subnormal values are below any frame's unit
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const int e = (int)((bh >> 20) & 0x7ffu);
+  const int sh = e - emax;  // x 2^S = m 2^sh, m the 53-bit significand
+  unsigned long long u;
+  if (sh <= 0 && sh > -32 && e != 0) {
+    // the common case, values within 2^31 of the frame's largest, in 32-bit halves:
+    // (m + 2^(s-1)) >> s with s = -sh < 32
+    const unsigned s = (unsigned)(-sh);
+    const unsigned mh = (bh & 0xfffffu) | 0x100000u;
+    const unsigned half = (1u << s) >> 1;
+    const unsigned lo = bl + half;
+    const unsigned hi = mh + (lo < bl ? 1u : 0u);
+    u = ((unsigned long long)(hi >> s) << 32) | __funnelshift_r(lo, hi, s);
+  } else {
     if (sh > lim || e == 0x7ff) ovf = true;
-    else if (sh >= 0) u = m << sh;
-    else if (sh > -54) u = (m + (1ull << (-sh - 1))) >> (-sh);
+    // m 2^sh rounded = (m 2^10 + 2^(9 - sh)) >> (10 - sh) for -54 < sh <= lim <= 9 (m 2^10 <
+    // 2^63: the sum does not wrap); zero below that, and for zero and subnormal values, which
+    // lie below any frame's unit
+    const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+    const int r = 10 - sh;
+    const bool keep = e != 0 && sh <= lim && r < 64;
+    u = keep ? ((m << 10) + (1ull << ((r - 1) & 63))) >> (r & 63) : 0ull;
   }
-  return (b >> 63) ? -(long long)u : (long long)u;
+  return (bh >> 31) ? -(long long)u : (long long)u;
 }
 
 // a 64-bit integer to FP64, rounded to nearest (ties to even), with integer instructions only
@@ -852,10 +866,13 @@ __global__ void __launch_bounds__(256) k_absmax_patch(LevelView lv, const double
   acc += 2 * blockIdx.y;
   const int n0 = p.n[0], n1 = p.n[1], rows = p.n[1] * p.n[2];
   unsigned long long v = 0ull;
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+  // one warp per row, eight loads of a lane in flight
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb) {
     const double* __restrict__ row = x + p.off + (long long)(r / n1 + NG) * p.sz + (long long)(r % n1 + NG) * p.sy + NG;
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(row[i]) & 0x7fffffffffffffffull;
+#pragma unroll 8
+    for (int i = lane; i < n0; i += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(row + i)) & 0x7fffffffffffffffull;
       v = b > v ? b : v;
     }
   }
@@ -1009,7 +1026,7 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, 2)
       const long long s1 = ((s[C - 1] + s[C + 1]) + (s[C - ZC_W] + s[C + ZC_W])) + (q[r][1] + q[r][3]);
       const long long s2 = ((s[C - 2] + s[C + 2]) + (s[C - 2 * ZC_W] + s[C + 2 * ZC_W])) + (q[r][0] + q[r][4]);
       const long long T = s1 * 16 - s2 - q[r][2] * 90;
-      ob[P] = fma(-kT, fx_to_double(T), fma(-alpha, xd[r][0], fk[r]));
+      ob[P] = fma(-kT, fx_to_double(T), alpha != 0.0 ? fma(-alpha, xd[r][0], fk[r]) : fk[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -1129,6 +1146,81 @@ __global__ void k_cfi(const CfiEntry* __restrict__ list, long long n, const long
           v += cfiw<T>(b0 + c0) * cfiw<T>(b1 + c1) * (D == 3 ? cfiw<T>(b2 + c2) : T(1)) * xc[s[q]];
   }
   xf[e.dst] = v;
+}
+
+// AMRCFI by coarse parent: one thread evaluates the 2^D children of one parent (the tensor
+// product of the 1-D quartic weights of Sec. 4 over the shared 5^D window) dimension by
+// dimension: per window row the two x sums (one per child column), folded into the two y
+// sums per child row, then into the two z sums: 2 5^D + 4 5^(D-1) + 8 5^(D-2) multiply-adds
+// for 2^D ghosts, instead of 2^D 5^D products and sums.
+template <typename T, int D>
+__global__ void k_cfi_grp(const CfiGroup* __restrict__ list, long long n, const long long* __restrict__ side,
+                          const PatchDesc* __restrict__ cpatches, const T* __restrict__ xc, T* __restrict__ xf,
+                          int zero) {
+  pdl_wait();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CfiGroup& g = list[t];
+  constexpr int NC = D == 3 ? 8 : 4;
+  if (zero) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (g.dst[c] >= 0) xf[g.dst[c]] = T(0);
+    return;
+  }
+  // weight of window cell w for child sub-position a (ratio 2): cfiw((2 pos + a) W + w)
+  const int b0 = 2 * g.pos[0] * CFI_W, b1 = 2 * g.pos[1] * CFI_W, b2 = 2 * g.pos[2] * CFI_W;
+  const long long src = g.src;
+  PatchDesc cp{};
+  if (src >= 0) cp = cpatches[g.cpatch];
+  const long long* s = src >= 0 ? nullptr : side + (-1 - src) * (D == 3 ? 125 : 25);
+  T acc[2][2][2];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c & 1][(c >> 1) & 1][c >> 2] = T(0);
+  for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2) {
+    T by[2][2] = {{T(0), T(0)}, {T(0), T(0)}};  // [x child][y child]
+    for (int c1 = 0; c1 < CFI_W; ++c1) {
+      T v[CFI_W];
+      if (s == nullptr) {
+        const long long row = src + (long long)c1 * cp.sy + (long long)c2 * cp.sz;
+#pragma unroll
+        for (int c0 = 0; c0 < CFI_W; ++c0) v[c0] = xc[row + c0];
+      } else {
+#pragma unroll
+        for (int c0 = 0; c0 < CFI_W; ++c0) v[c0] = xc[s[(c2 * CFI_W + c1) * CFI_W + c0]];
+      }
+      T bx[2] = {T(0), T(0)};
+#pragma unroll
+      for (int c0 = 0; c0 < CFI_W; ++c0) {
+        bx[0] += cfiw<T>(b0 + c0) * v[c0];
+        bx[1] += cfiw<T>(b0 + CFI_W + c0) * v[c0];
+      }
+      const T wy0 = cfiw<T>(b1 + c1), wy1 = cfiw<T>(b1 + CFI_W + c1);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        by[a][0] += wy0 * bx[a];
+        by[a][1] += wy1 * bx[a];
+      }
+    }
+    if (D == 3) {
+      const T wz0 = cfiw<T>(b2 + c2), wz1 = cfiw<T>(b2 + CFI_W + c2);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          acc[a][b][0] += wz0 * by[a][b];
+          acc[a][b][1] += wz1 * by[a][b];
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b][0] = by[a][b];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (g.dst[c] >= 0) xf[g.dst[c]] = acc[c & 1][(c >> 1) & 1][c >> 2];
 }
 
 template <typename T>

@@ -468,4 +468,313 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2))
   }
 }
 
+
+// ------------------------------------------------------------------ FP64 residual, fixed point
+// The refinement loop's FP64 residual r = f - (alpha x + beta L x) on the same single-patch
+// levels, with the stencil sums formed exactly in 64-bit integers as in k_resid3d_fx (frame:
+// the level's largest interior |x|, found by k_absmax_patch, its leading bit at bit 52;
+// T = 16 s1 - s2 - 90 x = 12 h^2 L x 2^S exact; r = f - alpha x - (beta / 12 h^2) 2^-S T by
+// two FP64 multiply-adds).  The planes of x are streamed by the producer as in k_sweep3d;
+// NFW converter warps then rewrite every staged value that the stencil reads as its
+// fixed-point integer, in place (one conversion per staged value instead of one per read),
+// write the physical ghost values of face tiles (x and y: from the converted cells next to
+// the face, rounded to integers; z ghost planes: from the stored cells, rounded to the
+// frame: the same values as k_resid3d_fx), and release the plane to the consumer warps,
+// which read integer neighbour pairs from the ring, f from a second ring of SF slots (one
+// plane of the tile per slot, also filled by the producer) and x itself (for alpha x) from
+// global memory one plane ahead (the plane was just brought into L2 by the copy).
+// The result is bit for bit that of k_resid3d_fx.  A value outside the frame sets the
+// replica's flag (lv.fxs[2 c + 1]), and the plain FP64 kernel launched after this one
+// recomputes the level.
+template <int TY, int RW, int S, int NFW>
+constexpr int rfx_threads() {
+  return 32 * (TY / RW + 1 + NFW);
+}
+constexpr int RFX_SF = 3;  // slots of the f ring
+template <int TY, int S>
+constexpr size_t rfx_smem_bytes() {
+  return ((size_t)S * sw3::region_elems<double>(TY + 4) + (size_t)RFX_SF * sw3::region_elems<double>(TY)) *
+             sizeof(double) +
+         (3 * S + 2 * RFX_SF) * sizeof(unsigned long long);
+}
+
+template <int TY, int RW, int S, int NFW>
+__global__ void __launch_bounds__(rfx_threads<TY, RW, S, NFW>(), 2)
+    k_resid3d_fx_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf, LevelView lv,
+                     int ntx, int ntiles, int nch,
+                     const double* __restrict__ x, const double* __restrict__ f, double* __restrict__ out,
+                     double alpha, double beta) {
+  using namespace sw3;
+  unsigned* err = &g_sweep3d_err;
+  constexpr int NCW = TY / RW;        // consumer warps
+  constexpr int XH = TY + 4;          // slot rows
+  constexpr int SLOT = region_elems<double>(XH);
+  constexpr int SF = RFX_SF, FSLOT = region_elems<double>(TY);
+  constexpr int NFT = 32 * NFW;       // converter threads
+  constexpr int EPL = (XH * XW + NFT - 1) / NFT;  // staged values per converter thread
+  static_assert(TY % RW == 0 && S >= 8 && EPL <= 32, "tile rows must split into warps; eight slots; mask width");
+  extern __shared__ __align__(128) unsigned char sw3_smem[];
+  long long* ring = reinterpret_cast<long long*>(sw3_smem);
+  double* fring = reinterpret_cast<double*>(ring + (size_t)S * SLOT);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(fring + (size_t)SF * FSLOT);
+  unsigned long long* ready = full + S;
+  unsigned long long* empty = ready + S;
+  unsigned long long* ffull = empty + S;
+  unsigned long long* fempty = ffull + SF;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bpc = gridDim.x / lv.ncomp, comp = blockIdx.x / bpc, blk = blockIdx.x % bpc;
+  PatchDesc p = lv.p0;
+  p.off += comp * lv.cstride;
+  const int nz = p.n[2];
+  const int tile = blk % ntiles, chunk = blk / ntiles;
+  const int ka = (int)(((long long)chunk * nz) / nch), kb = (int)(((long long)(chunk + 1) * nz) / nch);
+  const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
+  const int lz = p.lo[2], nzd = lv.ndom[2];
+  const int gx0 = p.lo[0] + i0, gy0 = p.lo[1] + j0;
+  const bool fxl = gx0 == 0, fxh = gx0 + TX == lv.ndom[0], fyl = gy0 == 0, fyh = gy0 + TY == lv.ndom[1];
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&ready[q], NFW);
+      mbar_init(&empty[q], NCW);
+    }
+    for (int q = 0; q < SF; ++q) {
+      mbar_init(&ffull[q], 1);
+      mbar_init(&fempty[q], NCW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (ka >= kb) return;
+  pdl_wait();  // the frame is written by the preceding kernel
+  if (lv.active != nullptr && !lv.active[comp]) return;  // converged replica of a stacked batch
+  unsigned* __restrict__ flag = reinterpret_cast<unsigned*>(lv.fxs + 2 * comp + 1);
+  const int emax = (int)((lv.fxs[2 * comp] >> 52) & 0x7ffull);
+  if (emax == 0x7ff || (emax != 0 && emax < 53)) {  // non-finite, or a frame below the normal range
+    if (tid == 0) *flag = 1u;
+    return;
+  }
+  const int kfirst = ka - 2;
+  const int np = (kb - ka) + 4;  // planes through the ring
+  const int sy = (int)p.sy, sz = (int)p.sz;
+
+  if (warp == NCW) {
+    // ---------------------------------------------------------------- producer (one thread)
+    // x plane q and, from q = 4 on, f plane q - 4 (the plane the consumers take when x plane q
+    // completes their window)
+    if (lane != 0) return;
+    tma_prefetch_desc(&tmx);
+    tma_prefetch_desc(&tmf);
+    int q = 0, nf = 0;  // x planes and f planes issued
+    bool ok = true;
+    for (; q < np; ++q) {
+      const int sl = q % S, use = q / S, k = kfirst + q;
+      if (use > 0 && !mbar_wait(&empty[sl], (unsigned)((use - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      if (lz + k < 0 || lz + k >= nzd) {  // z ghost plane: the converters write it
+        mbar_arrive(&full[sl]);
+      } else {
+        mbar_expect_tx(&full[sl], (unsigned)(XH * XW * sizeof(double)));
+        tma_load4(ring + (size_t)sl * SLOT, &tmx, i0, j0, k + NG, comp, &full[sl]);
+      }
+      const int j = q - 4;
+      if (j >= 0) {
+        const int fs = j % SF, fuse = j / SF;
+        if (fuse > 0 && !mbar_wait(&fempty[fs], (unsigned)((fuse - 1) & 1))) {
+          ok = false;
+          ++q;  // x plane q was issued
+          break;
+        }
+        mbar_expect_tx(&ffull[fs], (unsigned)(TY * XW * sizeof(double)));
+        tma_load4(fring + (size_t)fs * FSLOT, &tmf, i0, j0 + NG, ka + j + NG, comp, &ffull[fs]);
+        ++nf;
+      }
+    }
+    if (!ok) atomicOr(err, 1u);
+    // the block must not end while copies into its shared memory are in flight: wait
+    // (bounded) for the last copies issued into every slot of both rings
+    for (int t = max(0, q - S); t < q; ++t) mbar_wait(&full[t % S], (unsigned)((t / S) & 1));
+    for (int t = max(0, nf - SF); t < nf; ++t) mbar_wait(&ffull[t % SF], (unsigned)((t / SF) & 1));
+    return;
+  }
+
+  if (warp > NCW) {
+    // ---------------------------------------------------------------- converters (NFW warps)
+    const int ft = tid - 32 * (NCW + 1);
+    bool ovf = false;
+    // staged values this thread converts (bit t: value ft + t NFT): not a halo corner (never
+    // read) and not a physical ghost (written from the converted cells afterwards)
+    unsigned cmask = 0u;
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+      const int e = ft + t * NFT;
+      if (e >= XH * XW) continue;
+      const int r = e / XW, c = e % XW;
+      const bool hr = r < 2 || r >= TY + 2, hc = c < 2 || c >= TX + 2;
+      const bool ghost = (c < 2 && fxl) || (c >= TX + 2 && fxh) || (r < 2 && fyl) || (r >= TY + 2 && fyh);
+      if (!(hr && hc) && !ghost) cmask |= 1u << t;
+    }
+    auto fbar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(NFT) : "memory"); };
+    auto slot = [&](int q) -> long long* { return ring + (size_t)(q % S) * SLOT; };
+    // physical ghost value of layer ``layer`` from four converted cells (below 2^53: exact
+    // as FP64), already in frame units, rounded to an integer
+    auto gfx = [&](int type, int layer, long long a0, long long a1, long long a2, long long a3) -> long long {
+      const double v = ghost4<double>(type, layer, (double)a0, (double)a1, (double)a2, (double)a3);
+      return fx_of(v, 1075, 7, ovf);
+    };
+    const bool fxy = fxl || fxh || fyl || fyh;  // block-uniform
+    const double* __restrict__ xb = x + p.off;
+    // Every converter warp passes the same sequence of converter barriers (their number
+    // depends on block-uniform values only), also after a wait ran out: then it skips the
+    // work and the remaining waits, so that no barrier is left waiting for it.
+    bool ok = true;
+    for (int q = 0; q < np; ++q) {
+      const int k = kfirst + q, g = lz + k;
+      long long* sq = slot(q);
+      ok = ok && mbar_wait(&full[q % S], (unsigned)((q / S) & 1));
+      if (g < 0 || g >= nzd) {
+        // z ghost plane over the tile's cells from the four stored planes next to the face
+        // (global memory), rounded to the frame
+        if (ok) {
+          const int side = g < 0 ? 0 : 1, layer = side == 0 ? -g - 1 : g - nzd, type = lv.bc[4 + side];
+          const int k0 = (side == 0 ? 0 : nzd - 1) - lz + NG, dk = side == 0 ? sz : -sz;
+          for (int e = ft; e < TY * TX; e += NFT) {
+            const int ii = e % TX, jj = e / TX;
+            const double* col = xb + (long long)k0 * sz + (long long)(j0 + jj + NG) * sy + (i0 + ii + NG);
+            const double v = ghost4<double>(type, layer, col[0], col[dk], col[2 * dk], col[3 * dk]);
+            sq[(jj + 2) * XW + ii + 2] = fx_of(v, emax, 7, ovf);
+          }
+        }
+      } else {
+        if (ok) {
+          // stored values to integers, in place (each thread rewrites only its own values)
+          const double* sd = reinterpret_cast<const double*>(sq);
+#pragma unroll
+          for (int t = 0; t < EPL; ++t)
+            if ((cmask >> t) & 1u) {
+              const int e = ft + t * NFT;
+              sq[e] = fx_of(sd[e], emax, 2, ovf);
+            }
+        }
+        if (fxy) {
+          fbar();  // every converter's cells of this plane are integers
+          if (ok) {
+            // x and y ghosts (rows / columns of the tile's cells only: the halo corners are
+            // never read)
+            const int txl = lv.bc[0], txh = lv.bc[1], tyl = lv.bc[2], tyh = lv.bc[3];
+            if (fxl || fxh)
+              for (int r = ft + 2; r < TY + 2; r += NFT) {
+                long long* row = sq + r * XW;
+                if (fxl) {
+                  const long long a0 = row[2], a1 = row[3], a2 = row[4], a3 = row[5];
+                  row[1] = gfx(txl, 0, a0, a1, a2, a3);
+                  row[0] = gfx(txl, 1, a0, a1, a2, a3);
+                }
+                if (fxh) {
+                  const long long a0 = row[XW - 3], a1 = row[XW - 4], a2 = row[XW - 5], a3 = row[XW - 6];
+                  row[XW - 2] = gfx(txh, 0, a0, a1, a2, a3);
+                  row[XW - 1] = gfx(txh, 1, a0, a1, a2, a3);
+                }
+              }
+            if (fyl || fyh)
+              for (int c = ft + 2; c < XW - 2; c += NFT) {
+                if (fyl) {
+                  const long long a0 = sq[2 * XW + c], a1 = sq[3 * XW + c], a2 = sq[4 * XW + c], a3 = sq[5 * XW + c];
+                  sq[1 * XW + c] = gfx(tyl, 0, a0, a1, a2, a3);
+                  sq[0 * XW + c] = gfx(tyl, 1, a0, a1, a2, a3);
+                }
+                if (fyh) {
+                  const long long a0 = sq[(TY + 1) * XW + c], a1 = sq[TY * XW + c], a2 = sq[(TY - 1) * XW + c],
+                                  a3 = sq[(TY - 2) * XW + c];
+                  sq[(TY + 2) * XW + c] = gfx(tyh, 0, a0, a1, a2, a3);
+                  sq[(TY + 3) * XW + c] = gfx(tyh, 1, a0, a1, a2, a3);
+                }
+              }
+          }
+        }
+      }
+      fence_proxy_async_smem();  // these generic writes precede the next TMA write of the slot
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready[q % S]);
+    }
+    if (!ok && lane == 0) atomicOr(err, 1u);
+    if (ovf) *flag = 1u;
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  using L2v = longlong2;
+  const double kT = emax == 0 ? 0.0 : beta * lv.inv12h2 * __longlong_as_double((long long)(emax - 52) << 52);
+  const bool has_a = alpha != 0.0;  // block-uniform
+  const int c0 = 2 + 2 * lane;
+  const long long o0 = p.off + (long long)(ka + NG) * p.sz + (long long)(j0 + NG + warp * RW) * p.sy + (i0 + c0);
+  double* __restrict__ orow = out + o0;
+  const double* __restrict__ xrow = x + o0;
+  auto fail = [&]() {
+    if (lane == 0) atomicOr(err, 1u);
+  };
+  for (int q = 0; q < 4; ++q)
+    if (!mbar_wait(&ready[q], 0u)) { fail(); return; }
+  const long long* pz[5];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) pz[d] = ring + (size_t)d * SLOT;
+  int s4 = 4, par4 = 0, fs = 0, fpar = 0;
+  const int rbase = (warp * RW + 2) * XW + c0;
+  const int fbase = warp * RW * XW + c0;
+  double2 xq[RW];
+#pragma unroll
+  for (int r = 0; r < RW; ++r) xq[r] = has_a ? *reinterpret_cast<const double2*>(xrow + r * sy) : make_double2(0.0, 0.0);
+  for (int k = ka; k < kb; ++k) {
+    pz[4] = ring + (size_t)s4 * SLOT;
+    if (!mbar_wait(&ready[s4], (unsigned)par4) || !mbar_wait(&ffull[fs], (unsigned)fpar)) { fail(); return; }
+    const long long* __restrict__ sx = pz[2];
+    const double* __restrict__ sf = fring + (size_t)fs * FSLOT;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const int sr = rbase + r * XW;
+      const L2v xc = *reinterpret_cast<const L2v*>(sx + sr);
+      const L2v xl = *reinterpret_cast<const L2v*>(sx + sr - 2), xr = *reinterpret_cast<const L2v*>(sx + sr + 2);
+      const L2v ym1 = *reinterpret_cast<const L2v*>(sx + sr - XW), ym2 = *reinterpret_cast<const L2v*>(sx + sr - 2 * XW);
+      const L2v yp1 = *reinterpret_cast<const L2v*>(sx + sr + XW), yp2 = *reinterpret_cast<const L2v*>(sx + sr + 2 * XW);
+      const L2v zm2 = *reinterpret_cast<const L2v*>(pz[0] + sr), zm1 = *reinterpret_cast<const L2v*>(pz[1] + sr);
+      const L2v zp1 = *reinterpret_cast<const L2v*>(pz[3] + sr), zp2 = *reinterpret_cast<const L2v*>(pz[4] + sr);
+      // cell 0 of the pair: x neighbours xl.y (-1), xl.x (-2), xc.y (+1), xr.x (+2);
+      // cell 1: xc.x (-1), xl.y (-2), xr.x (+1), xr.y (+2)
+      const long long s1a = ((xl.y + xc.y) + (ym1.x + yp1.x)) + (zm1.x + zp1.x);
+      const long long s2a = ((xl.x + xr.x) + (ym2.x + yp2.x)) + (zm2.x + zp2.x);
+      const long long s1b = ((xc.x + xr.x) + (ym1.y + yp1.y)) + (zm1.y + zp1.y);
+      const long long s2b = ((xl.y + xr.y) + (ym2.y + yp2.y)) + (zm2.y + zp2.y);
+      const long long Ta = s1a * 16 - s2a - xc.x * 90;
+      const long long Tb = s1b * 16 - s2b - xc.y * 90;
+      const double2 fk = *reinterpret_cast<const double2*>(sf + fbase + r * XW);
+      const double2 xk = xq[r];
+      if (has_a && k + 1 < kb) xq[r] = *reinterpret_cast<const double2*>(xrow + sz + r * sy);
+      // (alpha = 0, the pressure Poisson equation: f - 0 x is f, one FP64 operation per cell)
+      const double ra = fma(-kT, fx_to_double(Ta), has_a ? fma(-alpha, xk.x, fk.x) : fk.x);
+      const double rb = fma(-kT, fx_to_double(Tb), has_a ? fma(-alpha, xk.y, fk.y) : fk.y);
+      *reinterpret_cast<double2*>(orow + r * sy) = make_double2(ra, rb);
+    }
+    // plane k-2 of x and plane k of f are no longer read: release their slots
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&empty[(pz[0] - ring) / SLOT]);
+      mbar_arrive(&fempty[fs]);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) pz[d] = pz[d + 1];
+    if (++s4 == S) {
+      s4 = 0;
+      par4 ^= 1;
+    }
+    if (++fs == SF) {
+      fs = 0;
+      fpar ^= 1;
+    }
+    orow += sz;
+    xrow += sz;
+  }
+}
+
 }  // namespace amr4

@@ -28,6 +28,9 @@ SHIMS = r"""
 static long long __double_as_longlong(double x) { long long b; std::memcpy(&b, &x, 8); return b; }
 static double __longlong_as_double(long long b) { double x; std::memcpy(&x, &b, 8); return x; }
 static int __clzll(long long v) { return v == 0 ? 64 : __builtin_clzll((unsigned long long)v); }
+static unsigned __funnelshift_r(unsigned lo, unsigned hi, unsigned s) {
+  return (unsigned)((((unsigned long long)hi << 32) | lo) >> (s & 31));
+}
 """
 
 MAIN = r"""
@@ -53,6 +56,10 @@ int main() {
     if (ovf || (long double)v != r) ++bad;
     bool o = false;
     if (fx_of(mx, emax, 2, o) >= (1LL << 53) || o) ++bad;                 // the maximum maps below 2^53
+    const double y = mx * (1.0 + 2.9 * std::fabs(U(g))) * (U(g) < 0.0 ? -1.0 : 1.0);  // inside the headroom
+    bool oy = false;
+    const long long vy = fx_of(y, emax, 2, oy);
+    if (oy || (long double)vy != std::round(std::ldexp((long double)y, 1075 - emax))) ++bad;
     const double lim2 = std::ldexp(1.0, emax - 1020), lim7 = std::ldexp(1.0, emax - 1015);
     bool a = false, b = false, c = false, d = false;
     fx_of(std::nextafter(lim2, 0.0), emax, 2, a);

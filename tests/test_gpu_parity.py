@@ -658,15 +658,19 @@ def fx_switch():
     amr.set_fx_residual(1)
 
 
-def test_3d_fixed_point_residual(fx_switch):
+@pytest.mark.parametrize("bulk", [0, 2])
+def test_3d_fixed_point_residual(fx_switch, bulk_sweep, bulk):
     """The 3-D FP64 residual with exact fixed-point stencil sums (the default on tile-multiple
     single-patch levels) against the oracle and the plain FP64 kernel on a 64 x 64 x 40 grid
-    with Dirichlet and Neumann faces: a smooth field that meets the boundary conditions and a
-    rough one (whose layer-2 Dirichlet ghost values reach about 50 times the interior values)
-    both stay in the frame, so the fixed-point result is the one returned (it differs from the
-    plain kernel's in rounding only); phi = 0 (the refinement loop's first residual) gives f
-    exactly."""
+    with Dirichlet and Neumann faces, in both forms: the z-chunked kernel (bulk = 0) and the
+    bulk-copy kernel whose converter warps rewrite the staged planes as integers (bulk = 2;
+    five z chunks, so chunks on both z faces and between them).  A smooth field that meets
+    the boundary conditions and a rough one (whose layer-2 Dirichlet ghost values reach about
+    50 times the interior values) both stay in the frame, so the fixed-point result is the
+    one returned (it differs from the plain kernel's in rounding only); phi = 0 (the
+    refinement loop's first residual) gives f exactly."""
     amr = _amr()
+    bulk_sweep(bulk)
     n = (64, 64, 40)
     box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
     bc = [0, 1, 0, 0, 1, 0]
@@ -719,6 +723,71 @@ def test_3d_fixed_point_residual_fallback(fx_switch):
     gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / n0[0])
     op = amr.Operator(gh, alpha, beta, bc)
     rng = np.random.default_rng(79)
+    X = _rand_field(H, rng)
+    X[1] = X[1] * 1e-3
+    B = _rand_field(H, rng)
+    ref = cp.residual(H, X, B, alpha, beta)
+    got = {}
+    for on in (1, 0):
+        fx_switch(on)
+        res = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        op.residual(_dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B)), res)
+        got[on] = from_packed(gh, H, res.cpu().numpy())
+    fx_switch(1)
+    for on in (1, 0):
+        assert max_diff(H, got[on], ref) <= 1e-13 * op_scale(H, alpha, beta, X), on
+    v0, v1 = H.levels[0].valid, H.levels[1].valid
+    assert np.array_equal(got[1][1][v1], got[0][1][v1])
+    assert not np.array_equal(got[1][0][v0], got[0][0][v0])
+
+
+def test_3d_fixed_point_residual_forms_agree(fx_switch, bulk_sweep):
+    """The two fixed-point forms (z-chunked, bulk-copy) on a 128 x 64 x 48 grid with every
+    face type: both within 1e-13 of the oracle's residual, and bit for bit equal (the same
+    frame, the same exact sums, ghost values and multiply-adds)."""
+    amr = _amr()
+    n = (128, 64, 48)
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    bc = [1, 0, 0, 1, 0, 1]
+    hi = tuple(v / n[0] for v in n)
+    H = OH(3, n, box, bc=bc, hi=hi)
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    alpha, beta = 1.0, -0.03
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(83)
+    X = _rand_field(H, rng, redundant=False)
+    B = _rand_field(H, rng, redundant=False)
+    dx, df = _dev(to_packed(gh, H, X)), _dev(to_packed(gh, H, B))
+    got = {}
+    for bulk in (0, 2):
+        bulk_sweep(bulk)
+        res = torch.zeros(gh.nelems, dtype=torch.float64, device="cuda")
+        op.residual(dx, df, res)
+        got[bulk] = from_packed(gh, H, res.cpu().numpy())
+    ref = cp.residual(H, X, B, alpha, beta)
+    scale = op_scale(H, alpha, beta, X)
+    for bulk in (0, 2):
+        assert max_diff(H, got[bulk], ref) <= 1e-13 * scale, bulk
+    assert max_diff(H, got[0], got[2]) == 0.0
+
+
+def test_3d_fixed_point_residual_fallback_bulk(fx_switch, bulk_sweep):
+    """The out-of-frame fallback behind the bulk-copy form: base 64 x 32 x 16 and a 64 x 16 x
+    16 fine box (both bulk-copy levels) whose values are a thousand times smaller than the
+    coarse level around it; its coarse-fine ghost values leave its frame, the converter warps
+    raise the flag and the gated FP64 kernel recomputes the fine level (bit for bit the plain
+    kernel's result), while the base level keeps the fixed-point result; the composite
+    residual matches the oracle either way."""
+    amr = _amr()
+    bulk_sweep(2)
+    n0 = (64, 32, 16)
+    boxes = [[((0, 0, 0), (63, 31, 15))], [((32, 16, 8), (95, 31, 23))]]
+    bc = [0, 1, 1, 0, 0, 1]
+    alpha, beta = 1.0, -0.01
+    H = OH(3, n0, boxes, bc=bc, hi=tuple(v / n0[0] for v in n0))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / n0[0])
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(89)
     X = _rand_field(H, rng)
     X[1] = X[1] * 1e-3
     B = _rand_field(H, rng)
