@@ -789,6 +789,52 @@ __global__ void __launch_bounds__(ZC_TX* ZC_TY, (sizeof(T) == 4 ? 8 : 4) / R)
   }
 }
 
+// ------------------------------------------------------------------------ precision conversions
+// GB300 executes FP64 instructions (conversions to and from FP64 among them) at a small
+// fraction of its integer rate, and the refinement loop converts every cell twice per
+// iteration (the FP32 correction to FP64, the FP64 residual to FP32).  These two helpers do
+// the conversions with integer instructions and give the results of the hardware
+// conversions: FP32 -> FP64 exactly, FP64 -> FP32 rounded to nearest even.  Values outside
+// the normal FP32 range (apart from zero) take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // signed zero
+    return (double)v;
+  }
+  // exponent rebased by 1023 - 127, the 23-bit significand at the top of the 52-bit one
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+__device__ __forceinline__ float f64_to_f32(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
+  if (e >= 897u && e <= 1150u) {  // 2^-126 <= |v| < 2^128
+    // the top 23 of the 52 significand bits, rounded on the 29 below (ties to even); a carry
+    // out of the significand moves the exponent on (to infinity above the largest float)
+    const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    return __uint_as_float(sg | (((e - 896u) << 23) + keep + up));
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(sg);  // signed zero
+  return (float)v;
+}
+// value-type conversion S -> T through the helpers above where one side is FP32
+template <typename T, typename S>
+__device__ __forceinline__ T cvt(S v) {
+  return T(v);
+}
+template <>
+__device__ __forceinline__ double cvt<double, float>(float v) {
+  return f32_to_f64(v);
+}
+template <>
+__device__ __forceinline__ float cvt<float, double>(double v) {
+  return f64_to_f32(v);
+}
+
 // ------------------------------------------------------------------------ 3-D FP64 residual in fixed point
 // GB300 issues FP64 arithmetic at a small fraction of its integer rate, and the FP64 residual
 // of the refinement loop (13 FP64 operations per cell in floating point) is bound by that
@@ -2636,7 +2682,7 @@ __global__ void __launch_bounds__(256) k_update_b(const BFlat* __restrict__ d, c
   if (!active[e.p]) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) rbits[e.p] = 0ull;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += (long long)gridDim.x * blockDim.x)
-    if (e.vmask[i]) e.phi[i] += (double)e.e[i];
+    if (e.vmask[i]) e.phi[i] += f32_to_f64(e.e[i]);
 }
 
 // valid max-norm of the residual into rbits[p] and its FP32 copy (the next V-cycle's
@@ -2649,9 +2695,9 @@ __global__ void __launch_bounds__(256) k_norm_convert_b(const BFlat* __restrict_
   unsigned long long v = 0ull;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += (long long)gridDim.x * blockDim.x) {
     const double x = e.r[i];
-    e.rin[i] = (float)x;
+    e.rin[i] = f64_to_f32(x);
     if (e.vmask[i]) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x));
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
       v = b > v ? b : v;
     }
   }
@@ -3121,7 +3167,7 @@ __global__ void k_axpy(LevelView lv, int nby, const S* __restrict__ x, T* __rest
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
-  const T v = a * T(x[o]);
+  const T v = a * cvt<T, S>(x[o]);
   y[o] += v;
   if (y2 != nullptr) y2[o] += v;
 }
@@ -3133,7 +3179,7 @@ __global__ void k_convert(LevelView lv, int nby, const S* __restrict__ x, T* __r
   int i, j, k;
   if (!thread_cell<D>(p, nby, i, j, k)) return;
   const long long o = poff(p, i, j, k);
-  y[o] = T(x[o]);
+  y[o] = cvt<T, S>(x[o]);
 }
 
 // y[o] += a on interior cells (mask: only valid cells when vmask != null)
@@ -3175,8 +3221,8 @@ __global__ void k_maxnorm(LevelView lv, int nby, const T* __restrict__ x, const 
   if (thread_cell<D>(p, nby, i, j, k)) {
     const long long o = poff(p, i, j, k);
     if (vmask == nullptr || vmask[o]) {
-      const double a = fabs((double)x[o]);
-      v = (unsigned long long)__double_as_longlong(a);
+      const double a = sizeof(T) == 4 ? f32_to_f64((float)x[o]) : (double)x[o];
+      v = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
     }
   }
   for (int s = 16; s > 0; s >>= 1) {
@@ -3216,9 +3262,9 @@ __global__ void __launch_bounds__(256) k_norm_convert(long long n, const double*
   acc += blockIdx.y;
   for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + n; e += stride) {
     const double x = r[e];
-    if (rin != nullptr) rin[e] = (float)x;
+    if (rin != nullptr) rin[e] = f64_to_f32(x);
     if (vmask[e]) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x));
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
       v = b > v ? b : v;
     }
   }
@@ -3249,7 +3295,7 @@ __global__ void __launch_bounds__(256) k_update_valid(long long n, const S* __re
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long e0 = (long long)blockIdx.y * n;
   for (long long e = e0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + n; e += stride)
-    if (vmask[e]) phi[e] += (double)x[e];
+    if (vmask[e]) phi[e] += cvt<double, S>(x[e]);
 }
 
 // Error-free transformation (Knuth's TwoSum).

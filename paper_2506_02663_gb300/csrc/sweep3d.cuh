@@ -160,7 +160,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // nch z chunks (chunk c: planes [c nz / nch, (c + 1) nz / nch), at least four planes each:
 // nch <= nz / 4); block 32 (TY / RW + 2).
 template <typename T, int MODE, int TY, int RW, int S>
-__global__ void __launch_bounds__(32 * (TY / RW + 2))
+__global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  // FP32: three blocks per SM
     k_sweep3d(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf, LevelView lv, int ntx,
               int ntiles, int nch, const T* __restrict__ f, T* __restrict__ out, T alpha, T beta, T omega,
               const unsigned char* __restrict__ vmask, const unsigned* __restrict__ gate) {

@@ -109,3 +109,72 @@ def test_fixed_point_sum_cannot_overflow():
     assert worst < 1024, worst
     # the kernel's comment states the same bound
     assert re.search(r"\(16 \(3 \* 11\.7 \+ 3\) \+ 3 \* 84\.4 \+ 3 \+ 90\) 2\^53 < 2\^63", open(KERNELS).read())
+
+
+CONV_SHIMS = r"""
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#define __device__
+#define __forceinline__ inline
+static long long __double_as_longlong(double x) { long long b; std::memcpy(&b, &x, 8); return b; }
+static unsigned __float_as_uint(float x) { unsigned b; std::memcpy(&b, &x, 4); return b; }
+static float __uint_as_float(unsigned b) { float x; std::memcpy(&x, &b, 4); return x; }
+static double __hiloint2double(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  double x; std::memcpy(&x, &b, 8); return x;
+}
+"""
+
+CONV_MAIN = r"""
+static bool same64(double a, double b) { return std::memcmp(&a, &b, 8) == 0; }
+static bool same32(float a, float b) { return std::memcmp(&a, &b, 4) == 0; }
+int main() {
+  std::mt19937_64 g(20250604);
+  long bad = 0;
+  // FP32 -> FP64: random bit patterns (every class), and the special values
+  for (int it = 0; it < 4000000; ++it) {
+    const float f = __uint_as_float((unsigned)g());
+    if (std::isnan(f)) continue;
+    if (!same64(f32_to_f64(f), (double)f)) ++bad;
+  }
+  for (float f : {0.0f, -0.0f, 1.0f, -1.0f, INFINITY, -INFINITY, 1.17549435e-38f, 1.4e-45f, 3.4028235e38f})
+    if (!same64(f32_to_f64(f), (double)f)) ++bad;
+  // FP64 -> FP32: random doubles over the FP32 range and beyond, exact ties, the range ends
+  std::uniform_int_distribution<int> ex(860, 1180);
+  for (int it = 0; it < 4000000; ++it) {
+    unsigned long long b = g();
+    b = (b & 0x800fffffffffffffull) | ((unsigned long long)ex(g) << 52);
+    if (it % 4 == 1) b = (b & ~0x1fffffffull) | 0x10000000ull;                 // a tie
+    if (it % 4 == 2) b = (b & ~0x1fffffffull) | (g() & 1 ? 0x0fffffffull : 0x10000001ull);
+    double d; std::memcpy(&d, &b, 8);
+    if (!same32(f64_to_f32(d), (float)d)) ++bad;
+  }
+  for (double d : {0.0, -0.0, 1.0, -1.0, (double)INFINITY, -(double)INFINITY, 3.4028235677973366e38, 3.4028235e38 * 1.0000001,
+                   1.1754943508222875e-38, 1.1754942e-38, 1e-45, 1e300, -1e-300})
+    if (!same32(f64_to_f32(d), (float)d)) ++bad;
+  std::printf("bad = %ld\n", bad);
+  return bad != 0;
+}
+"""
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_precision_conversions_match_the_casts(tmp_path):
+    """The integer-instruction FP32 <-> FP64 conversions of the refinement loop (taken
+    verbatim from csrc/kernels.cuh) against the compiler's casts, bit for bit: FP32 -> FP64
+    on random bit patterns of every class; FP64 -> FP32 (round to nearest even) on random
+    doubles from below the smallest normal float to above the largest, exact ties, and the
+    ends of the range (overflow to infinity, subnormal results)."""
+    src = open(KERNELS).read()
+    body = (_extract(src, "__device__ __forceinline__ double f32_to_f64(") +
+            _extract(src, "__device__ __forceinline__ float f64_to_f32("))
+    cpp = tmp_path / "conv.cpp"
+    cpp.write_text(CONV_SHIMS + body + CONV_MAIN)
+    exe = tmp_path / "conv"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe), str(cpp)], check=True,
+                   capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "bad = 0" in r.stdout, r.stdout + r.stderr
