@@ -436,6 +436,8 @@ amr_status sw_attrs() {
                           (int)sw3::smem_bytes<T, OP_JACOBI, SW_TY, SW_S>()));
   CK(cudaFuncSetAttribute(sw_kernel<T, OP_JACOBI0>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sw3::smem_bytes<T, OP_JACOBI0, SW_TY, SW_S>()));
+  CK(cudaFuncSetAttribute(sw_kernel<T, OP_RESTRICT>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sw3::smem_bytes<T, OP_RESTRICT, SW_TY, SW_S>()));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return AMR_OK;
 }
@@ -488,7 +490,8 @@ amr_status encode_patch_tmap(CUtensorMap* tm, const T* field, const PatchDesc& p
 // tiles of 64 x SW_TY cells; z chunks of at least SW_MINZ planes, as many as one wave holds
 template <typename T, int M>
 amr_status launch_sw(const LevelView& lv, const T* x, const T* f, T* out, T A, T B, T O, const unsigned char* vmask,
-                     cudaStream_t st, const unsigned* gate = nullptr) {
+                     cudaStream_t st, const unsigned* gate = nullptr, T* outc = nullptr, const PatchDesc* cpd = nullptr,
+                     long long ccs = 0) {
   TRY(sw_attrs<T>());
   constexpr size_t smem = sw3::smem_bytes<T, M, SW_TY, SW_S>();
   constexpr int threads = 32 * (SW_TY / SW_RW + 2);
@@ -500,7 +503,7 @@ amr_status launch_sw(const LevelView& lv, const T* x, const T* f, T* out, T A, T
   const int wave = wave_blocks(reinterpret_cast<const void*>(sw_kernel<T, M>()), threads, smem);
   const int nch = std::max(1, std::min(wave / (ntiles * nc), nz / SW_MINZ));
   launch(sw_kernel<T, M>(), (unsigned)(ntiles * nch * nc), threads, smem, st, tmx, tmf, lv, ntx, ntiles, nch, f, out,
-         A, B, O, vmask, gate);
+         A, B, O, vmask, gate, outc, cpd != nullptr ? *cpd : PatchDesc{}, ccs);
   return launch_check();
 }
 
@@ -1436,7 +1439,17 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
   }
   TRY(smooth_from_zero<T, D, TR>(h, 0, lv, b, x, t, p.nu1, op->alpha, op->beta, p.omega, false, st));
   const int xm[3] = {h->mg[m + 1].n[0], h->mg[m + 1].n[1], h->mg[m + 1].n[2]};
-  TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], h->ncomp, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
+  if (D == 3 && !TR && sw_eligible(lv) && lv.maxn[2] % 2 == 0 && tile_rows_for(lv, sizeof(T)) == TILE_BULK) {
+    // the residual restriction by the bulk-copy kernel (same arithmetic as k_restrict)
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    TRY(launch_sw<T, OP_RESTRICT>(lv, x, b, (T*)nullptr, T(op->alpha), T(op->beta), T(0), nullptr, st, nullptr,
+                                  S.mb[m + 1], &h->mg[m + 1].patch, h->mg[m + 1].cstride));
+    const double cc = (double)xm[0] * xm[1] * xm[2] * h->ncomp;
+    prof_end(st, ev, PC_RESTRICT, (2.0 * 8 + 1.0) * sizeof(T) * cc, cc * 8);
+  } else {
+    TRY(restrict_blocks<T, D, TR>(lv, cv, op->d_mgx[m], h->ncomp, xm, true, x, b, S.mb[m + 1], op->alpha, op->beta, st));
+  }
   TRY(mg_level0<T, D, TR>(op, p, m + 1, S.mb[m + 1], S.mx[m + 1], S.mt[m + 1], st));
   TRY(prolong_blocks<T, D>(lv, cv, op->d_mgx[m], h->ncomp, xm, S.mx[m + 1], x, (T*)nullptr, st));
   TRY(smooth_from<T, D, TR>(h, 0, lv, b, x, t, p.nu2, op->alpha, op->beta, p.omega, false, st));

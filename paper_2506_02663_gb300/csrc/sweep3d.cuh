@@ -154,8 +154,14 @@ namespace sw3 {
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 }  // namespace sw3
 
+// Residual restriction (multigrid down leg): the residual f - A x of each fine cell, summed
+// over the 2 x 2 x 2 children of every coarse cell in the order and with the arithmetic of
+// cell_restrict, times 1/8, into the coarse grid's right-hand side.
+constexpr int OP_RESTRICT = 4;
+
 // MODE: OP_JACOBI0 (x = 0: out = w f), OP_JACOBI, OP_RESID (vmask: valid cells only),
-// OP_APPLY.  tmx / tmf: tensor maps of x and f over the padded patch (dimensions: pitch,
+// OP_APPLY, OP_RESTRICT (outc: the coarse grid, layout cpd, replica stride ccs; even chunk
+// boundaries; RW = 2, so that a warp's two rows are one coarse row).  tmx / tmf: tensor maps of x and f over the padded patch (dimensions: pitch,
 // n_y + 4, n_z + 4; boxes 68 x (TY + 4) x 1 and 68 x TY x 1).  Grid: ntiles tile columns x
 // nch z chunks (chunk c: planes [c nz / nch, (c + 1) nz / nch), at least four planes each:
 // nch <= nz / 4); block 32 (TY / RW + 2).
@@ -163,7 +169,8 @@ template <typename T, int MODE, int TY, int RW, int S>
 __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  // FP32: three blocks per SM
     k_sweep3d(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf, LevelView lv, int ntx,
               int ntiles, int nch, const T* __restrict__ f, T* __restrict__ out, T alpha, T beta, T omega,
-              const unsigned char* __restrict__ vmask, const unsigned* __restrict__ gate) {
+              const unsigned char* __restrict__ vmask, const unsigned* __restrict__ gate, T* __restrict__ outc,
+              PatchDesc cpd, long long ccs) {
   using namespace sw3;
   using V = typename Pair<T>::V;
   unsigned* err = &g_sweep3d_err;
@@ -175,6 +182,7 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
   constexpr int XSZ = NEEDX ? region_elems<T>(XH) : 0;
   constexpr int SLOT = XSZ + (FTMA ? region_elems<T>(TY) : 0);
   static_assert(TY % RW == 0 && S >= 8, "tile rows must split into warps; the ring needs eight slots");
+  static_assert(MODE != OP_RESTRICT || RW == 2, "restriction: a warp's two rows form one coarse row");
   extern __shared__ __align__(128) unsigned char sw3_smem[];
   T* ring = reinterpret_cast<T*>(sw3_smem);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(sw3_smem + (size_t)S * SLOT * sizeof(T));
@@ -201,7 +209,8 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
   p.off += comp * lv.cstride;
   const int nz = p.n[2];
   const int tile = blk % ntiles, chunk = blk / ntiles;
-  const int ka = (int)(((long long)chunk * nz) / nch), kb = (int)(((long long)(chunk + 1) * nz) / nch);
+  const int ev = MODE == OP_RESTRICT ? ~1 : ~0;  // restriction: chunks of whole plane pairs
+  const int ka = (int)(((long long)chunk * nz) / nch) & ev, kb = (int)(((long long)(chunk + 1) * nz) / nch) & ev;
   const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
   const int lz = p.lo[2], nzd = lv.ndom[2];
   const int gx0 = p.lo[0] + i0, gy0 = p.lo[1] + j0;
@@ -401,6 +410,13 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
         if (ka + 1 < kb) fq[1][r] = __ldg(reinterpret_cast<const V*>(frow + sz + r * sy));
       }
     }
+    // restriction: the coarse cell of the lane (x: its pair, y: the warp's two rows, z: a
+    // plane pair) and the running sum of its children
+    T racc = T(0);
+    T* __restrict__ crow = nullptr;
+    if (MODE == OP_RESTRICT)
+      crow = outc + cpd.off + comp * ccs + (long long)((lz + ka) / 2 - cpd.lo[2] + NG) * cpd.sz +
+             (long long)((gy0 + warp * RW) / 2 - cpd.lo[1] + NG) * cpd.sy + (gx0 / 2 + lane - cpd.lo[0] + NG);
     auto step = [&](int k, auto slotc) -> bool {
       constexpr int FS = decltype(slotc)::value;
       pz[4] = ring + (size_t)s4 * SLOT;
@@ -423,7 +439,17 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
         const T s1b = ((xc.x + xr.x) + (ym1.y + yp1.y)) + (zm1.y + zp1.y);
         const T s2b = ((xl.y + xr.y) + (ym2.y + yp2.y)) + (zm2.y + zp2.y);
         T o0, o1;
-        if (MODE == OP_APPLY) {
+        if (MODE == OP_RESTRICT) {
+          // cell_Lx and cell_restrict: (16 s1 - s2 - 90 x) + 0, f - (alpha x + beta (s inv)),
+          // children summed x fastest, then y, then z
+          const V fk = fq[FS][r];
+          if (k + 2 < kb) fq[FS][r] = __ldg(reinterpret_cast<const V*>(frow + 2 * sz + r * sy));
+          const T sa = (T(16) * s1a - s2a - T(90) * xc.x) + T(0);
+          const T sb = (T(16) * s1b - s2b - T(90) * xc.y) + T(0);
+          racc += fk.x - (alpha * xc.x + beta * (sa * inv));
+          racc += fk.y - (alpha * xc.y + beta * (sb * inv));
+          continue;
+        } else if (MODE == OP_APPLY) {
           o0 = kc0 * xc.x + (kc1 * s1a - kc2 * s2a);
           o1 = kc0 * xc.y + (kc1 * s1b - kc2 * s2b);
         } else {
@@ -446,6 +472,11 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
         } else {
           st2<T>(orow + r * sy, V{o0, o1});
         }
+      }
+      if (MODE == OP_RESTRICT && ((k - ka) & 1)) {  // second plane of the pair: the coarse value
+        *crow = racc * T(0.125);
+        crow += cpd.sz;
+        racc = T(0);
       }
       // plane k-2 is no longer read: release its slot
       __syncwarp();

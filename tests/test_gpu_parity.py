@@ -651,6 +651,41 @@ def test_3d_bulk_sweep_two_level_vcycle_and_solve(bcw, ab, bulk_sweep):
     assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_bulk_restriction_matches_generic(bulk_sweep, precision):
+    """The residual restriction of the multigrid down leg by the bulk-copy kernel (128 x 64 x
+    32 grid with every face type; its next grid 64 x 32 x 16 also takes it): one V-cycle, in
+    FP64 and in the FP32 correction cycle of mixed precision, bit for bit equal to the
+    z-chunked kernels with the generic restriction (same children order and arithmetic), and
+    the FP64 one equal to the oracle's V-cycle to 1e-10."""
+    amr = _amr()
+    n = (128, 64, 32)
+    box = [[((0, 0, 0), tuple(v - 1 for v in n))]]
+    bc = [0, 1, 1, 0, 0, 1]
+    alpha, beta = 1.0, -0.02
+    H = OH(3, n, box, bc=bc, hi=tuple(v / n[0] for v in n))
+    gh = amr.Hierarchy(3, n, box, h0=1.0 / n[0])
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(97)
+    F = _rand_field(H, rng, redundant=False)
+    phi = _rand_field(H, rng, redundant=False)
+    got = {}
+    for on in (2, 0):
+        bulk_sweep(on)
+        dphi = _dev(to_packed(gh, H, phi))
+        if precision == 0:
+            op.vcycle(dphi, _dev(to_packed(gh, H, F)))
+        else:  # two refinement steps, each one FP32 correction V-cycle
+            op.solve(dphi, _dev(to_packed(gh, H, F)), allow_not_converged=True,
+                     params=amr.default_params(rtol=1e-30, max_vcycles=2, precision=1, use_graph=0))
+        got[on] = dphi.cpu().numpy()
+    assert np.array_equal(got[2], got[0])
+    if precision == 0:
+        ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+        g = from_packed(gh, H, got[2])
+        assert max_diff(H, g, ref) <= 1e-10 * max_abs(H, ref)
+
+
 @pytest.fixture
 def fx_switch():
     amr = _amr()
