@@ -1539,6 +1539,98 @@ __global__ void __launch_bounds__(BX* BY) k_prolong3d(LevelView fine, LevelView 
   }
 }
 
+// Prolongation of large 3-D grids by coarse parent: one thread per coarse cell reads the 27
+// coarse values around it once (instead of eight per fine cell) and updates its eight
+// children in x pairs (8-byte loads and stores); each child's value is the same sum, in the
+// same order and with the same weights, as in k_prolong3d.  Children in the outermost fine
+// layer at a domain face are left to k_prolong3d_shell, as in k_prolong3d<T, false, PZ>.
+// Block 32 x 8 coarse cells of one plane; grid.z = coarse plane (+ nzc x transfer block).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong3d_par(LevelView fine, LevelView crs,
+                                                          const XferBlock* __restrict__ blocks, int nzc,
+                                                          const T* __restrict__ xc, T* __restrict__ xf,
+                                                          T* __restrict__ xf2) {
+  using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  pdl_wait();
+  const XferBlock b = blocks[blockIdx.z / nzc];
+  const int g[3] = {b.clo[0] + (int)(blockIdx.x * BX + threadIdx.x), b.clo[1] + (int)(blockIdx.y * BY + threadIdx.y),
+                    b.clo[2] + (int)(blockIdx.z % nzc)};
+  if (g[0] > b.chi[0] || g[1] > b.chi[1] || g[2] > b.chi[2]) return;
+  const PatchDesc cp = crs.patches[b.cpatch];
+  const PatchDesc fp = fine.patches[b.fpatch];
+  // children outside the face layers (fine index 0 or 2 n - 1 along a dimension: the shell's)
+  bool keep[3][2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    keep[e][0] = g[e] > 0;
+    keep[e][1] = g[e] < crs.ndom[e] - 1;
+  }
+  const bool pairx = keep[0][0] && keep[0][1];
+  const int fsy = (int)fp.sy, fsz = (int)fp.sz;
+  const long long of0 = fp.off + (long long)(2 * g[2] - fp.lo[2] + NG) * fsz + (long long)(2 * g[1] - fp.lo[1] + NG) * fsy +
+                        (2 * g[0] - fp.lo[0] + NG);
+  // the fine pairs first, so that their loads are in flight with the coarse ones
+  V2 fv[2][2];
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+      if (pairx) fv[cz][cy] = *reinterpret_cast<const V2*>(xf + of0 + cz * fsz + cy * fsy);
+  const T* __restrict__ cb = xc + cp.off;
+  const int csy = (int)cp.sy, csz = (int)cp.sz;
+  const int oc = (g[2] - cp.lo[2] + NG) * csz + (g[1] - cp.lo[1] + NG) * csy + (g[0] - cp.lo[0] + NG);
+  T c[3][3][3];  // [dz + 1][dy + 1][dx + 1] (padding cells beyond a face only feed skipped children)
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) c[dz][dy][dx] = __ldg(cb + oc + (dz - 1) * csz + (dy - 1) * csy + (dx - 1));
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+      if (!keep[2][cz] || !keep[1][cy]) continue;
+      T v[2];
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int sx = cx ? 1 : -1, sy = cy ? 1 : -1, sz = cz ? 1 : -1;
+        T a = T(0);
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+          for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+            for (int q0 = 0; q0 < 2; ++q0) {
+              const T w = ((T(1) * (q0 == 0 ? T(0.75) : T(0.25))) * (q1 == 0 ? T(0.75) : T(0.25))) *
+                          (q2 == 0 ? T(0.75) : T(0.25));
+              a += w * c[1 + q2 * sz][1 + q1 * sy][1 + q0 * sx];
+            }
+        v[cx] = a;
+      }
+      const long long of = of0 + cz * fsz + cy * fsy;
+      if (pairx) {
+        V2 t = fv[cz][cy];
+        t.x += v[0];
+        t.y += v[1];
+        *reinterpret_cast<V2*>(xf + of) = t;
+        if (xf2 != nullptr) {
+          V2 u = *reinterpret_cast<const V2*>(xf2 + of);
+          u.x += v[0];
+          u.y += v[1];
+          *reinterpret_cast<V2*>(xf2 + of) = u;
+        }
+      } else {
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx)
+          if (keep[0][cx]) {
+            xf[of + cx] += v[cx];
+            if (xf2 != nullptr) xf2[of + cx] += v[cx];
+          }
+      }
+    }
+}
+
 // The fine cells k_prolong3d<T, false, PZ> skips: the layer at each domain face a block's fine region
 // touches.  blockIdx.y = face 2d + side; a cell on several faces belongs to the face of its
 // lowest dimension, so face (d, side) covers the cells with index 0 or 2 n - 1 along d,

@@ -750,7 +750,9 @@ amr_status prolong_blocks(const LevelView& fine, const LevelView& crs, const Xfe
     if (fel < (1LL << 31) && (long long)nzc * nblocks <= 65535) {
       dim3 grid((2 * xmax[0] + BX - 1) / BX, (2 * xmax[1] + BY - 1) / BY, nzc * nblocks);
       if (large) {
-        launch(k_prolong3d<T, false, 4>, grid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, nzc, xc, xf, xf2);
+        // by coarse parent (32 x 8 coarse cells a block, one coarse plane), the face layer by the shell
+        dim3 pgrid((xmax[0] + BX - 1) / BX, (xmax[1] + BY - 1) / BY, xmax[2] * nblocks);
+        launch(k_prolong3d_par<T>, pgrid, dim3(BX, BY, 1), 0, st, fine, crs, blocks, xmax[2], xc, xf, xf2);
         if (const amr_status s1 = launch_check(); s1 != AMR_OK) return s1;
         const long long face = 4LL * std::max({xmax[0] * xmax[1], xmax[1] * xmax[2], xmax[0] * xmax[2]});
         const unsigned gx = (unsigned)std::min<long long>((face + 255) / 256, 64);
