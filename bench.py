@@ -40,6 +40,9 @@ WORKLOAD = ("bumps3d: 3-D two-level AMR, base 256^3 on [0,1]^3 + ratio-2 box [0.
             "nu=1e-3, k=1/256, Dirichlet) batched in one call, RHS = cell averages of seeded Gaussian-bump "
             "sums (one set per system), each to ||r||_inf <= 1e-10 ||f||_inf")
 RTOL = 1e-10
+# FP32 correction cycles per FP64 residual in the mixed-precision solves of the 3-D workload
+# (amr_solver_params.cycles_per_refinement; the iterate equals that of one cycle per step)
+CPR = 2
 
 
 def _args():
@@ -404,7 +407,7 @@ def run_ours(args):
     w = _bumps3d(amr, torch)
     dof = w["dof"]
     prec = amr.MIXED if args.precision == "mixed" else amr.FP64
-    params = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
+    params = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1, cycles_per_refinement=CPR)
 
     for _ in range(args.warmup):
         _step3d(amr, w, params)
@@ -452,7 +455,7 @@ def run_ours(args):
 
     # ---------------- roofline of the dominant kernel, live (instrumented host-driven loop)
     peak, peak_kind = _peaks()
-    prof = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=0)
+    prof = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=0, cycles_per_refinement=CPR)
     amr.profile_enable(True)
     for op, phi, f in zip(ops, w["phis"], w["fs"]):
         op.solve(phi, f, params=prof)
@@ -468,7 +471,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "dof_per_system": dof, "systems": ["ppe", "helmholtz_u", "helmholtz_v",
                                                                              "helmholtz_w"],
-                   "precision": args.precision, "rtol": RTOL, "vcycles_per_system": vc_per_system,
+                   "precision": args.precision, "rtol": RTOL, "cycles_per_refinement": CPR,
+                   "vcycles_per_system": vc_per_system,
                    "l2": "no flush: every input and solution field (about 160 MB in FP64) is larger than the "
                          "129 MB L2",
                    "solve": "one captured CUDA graph per solve (device-side while loop over V-cycles); the three "
@@ -483,7 +487,7 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         other = amr.FP64 if prec == amr.MIXED else amr.MIXED
-        p2 = amr.default_params(rtol=RTOL, max_vcycles=100, precision=other, use_graph=1)
+        p2 = amr.default_params(rtol=RTOL, max_vcycles=100, precision=other, use_graph=1, cycles_per_refinement=CPR)
         _step3d(amr, w, p2)
         ts2, vcs2 = _timed(torch, lambda: _step3d(amr, w, p2), min(args.steps, 3))
         key = "fp64" if prec == amr.MIXED else "mixed"

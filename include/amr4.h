@@ -164,6 +164,14 @@ typedef struct {
                         each down leg (nu1 sweeps, residual, restriction) and each up leg
                         (prolongation, nu2 sweeps) is one launch over shared-memory tiles
                         with halos (same per-cell arithmetic); 0: one launch per sweep    */
+  int cycles_per_refinement; /* mixed precision: FP32 V-cycles per FP64 residual (1..4; 1 by
+                        default).  With c > 1 each refinement step runs c correction cycles,
+                        the later ones on the FP32 composite residual of the correction so far
+                        (in exact arithmetic the same iterate as c steps of one cycle each),
+                        and pays for one FP64 residual, update and norm instead of c.  The
+                        stopping test runs once per step: vcycles is a multiple of c (at most
+                        max_vcycles + c - 1) and res_history holds one entry per step.  The
+                        2-D work-list batch keeps one cycle per step; FP64 solves ignore it. */
 } amr_solver_params;
 
 typedef struct {

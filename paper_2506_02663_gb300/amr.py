@@ -51,7 +51,7 @@ class SolverParams(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("rtol", C.c_double),
                 ("atol", C.c_double), ("max_vcycles", C.c_int), ("precision", C.c_int),
                 ("zero_initial", C.c_int), ("use_graph", C.c_int), ("fuse_coarse", C.c_int),
-                ("temporal_blocking", C.c_int)]
+                ("temporal_blocking", C.c_int), ("cycles_per_refinement", C.c_int)]
 
 
 class SolveStats(C.Structure):

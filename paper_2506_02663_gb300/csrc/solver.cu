@@ -77,6 +77,9 @@ struct amr_operator {
   long long launches_pre = 0, launches_body = 0;
   int g_fuse = -1;
   int g_blk = -1;
+  int g_cpr = 1;                  // cycles per refinement step of the captured solve
+  float* inner_x = nullptr;       // mixed precision, cycles_per_refinement > 1: the correction so far
+  float* inner_r = nullptr;       // and the FP32 composite residual of the correction equation
   int cmg_m0[2][2] = {{-1, -1}, {-1, -1}};  // [transpose][precision 0 = FP32, 1 = FP64]; -1: unset
   size_t cmg_bytes[2][2] = {{0, 0}, {0, 0}};
 };
@@ -1774,42 +1777,42 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
   return AMR_OK;
 }
 
-// ---------------------------------------------------------------- FP64 composite pieces
-template <int D>
-amr_status avgdown_all(amr_hierarchy* h, double* x, cudaStream_t st) {
+// ---------------------------------------------------------------- composite pieces
+// (FP64 in the refinement loop and the projection; FP32 for the inner residual of the
+// mixed-precision correction, see mixed_correction)
+template <int D, typename T>
+amr_status avgdown_all(amr_hierarchy* h, T* x, cudaStream_t st) {
   for (int m = h->L - 2; m >= 0; --m) {
     const DeviceLists& dm = h->lev[m].dev;
     LevelView f = level_view(h, m + 1, nullptr), c = level_view(h, m, nullptr);
-    TRY(restrict_blocks<double, D>(f, c, dm.xfer, dm.nxfer, dm.xfer_max, false, x, (const double*)nullptr, x, 0.0, 0.0,
-                                   st));
+    TRY(restrict_blocks<T, D>(f, c, dm.xfer, dm.nxfer, dm.xfer_max, false, x, (const T*)nullptr, x, 0.0, 0.0, st));
   }
   return AMR_OK;
 }
 
-template <int D>
-amr_status fill_ghosts_all(amr_hierarchy* h, double* x, cudaStream_t st) {
+template <int D, typename T>
+amr_status fill_ghosts_all(amr_hierarchy* h, T* x, cudaStream_t st) {
   TRY(avgdown_all<D>(h, x, st));
   for (int l = 0; l < h->L; ++l) {
-    if (l >= 1) TRY(cfi_fill<double, D>(h, l, x, x, false, st));
-    TRY(copy_fill<double>(h, l, x, st));
+    if (l >= 1) TRY((cfi_fill<T, D>(h, l, x, x, false, st)));
+    TRY(copy_fill<T>(h, l, x, st));
   }
   return AMR_OK;
 }
 
 // out = A^comp x (mode OP_APPLY) or out = f - A^comp x (OP_RESID); covered cells.
-template <int D>
-amr_status composite_op(amr_operator* op, int mode, double* x, const double* f, double* out, const double* bc,
-                        cudaStream_t st) {
+template <int D, typename T>
+amr_status composite_op(amr_operator* op, int mode, T* x, const T* f, T* out, const T* bc, cudaStream_t st) {
   amr_hierarchy* h = op->h;
   TRY(fill_ghosts_all<D>(h, x, st));
   for (int l = 0; l < h->L; ++l) {
     LevelView lv = level_view(h, l, op->bc);
-    TRY(level_op<double, D>(mode, lv, x, f, out, bc, op->alpha, op->beta, 0.0, nullptr, st));
+    TRY((level_op<T, D>(mode, lv, x, f, out, bc, op->alpha, op->beta, 0.0, nullptr, st)));
   }
   for (int l = h->L - 2; l >= 0; --l) {
     LevelView c = level_view(h, l, op->bc), fv = level_view(h, l + 1, op->bc);
-    P3<double> xc{{x, x, x}}, xf{{x, x, x}}, nb{{bc, bc, bc}};
-    TRY(reflux<double, D>(h, l, c, fv, xc, xf, nb, out, mode == OP_APPLY ? op->beta : -op->beta, 0, st));
+    P3<T> xc{{x, x, x}}, xf{{x, x, x}}, nb{{bc, bc, bc}};
+    TRY((reflux<T, D>(h, l, c, fv, xc, xf, nb, out, mode == OP_APPLY ? op->beta : -op->beta, 0, st)));
   }
   TRY(avgdown_all<D>(h, out, st));  // COH-4
   return AMR_OK;
@@ -2016,6 +2019,58 @@ __global__ void k_check(cudaGraphConditionalHandle handle, int use_cond, const u
   if (use_cond) cudaGraphSetConditional(handle, cont);
 }
 
+// ---------------------------------------------------------------- mixed-precision correction
+// cycles_per_refinement (mixed precision only; 1 otherwise) and the cap on refinement steps
+inline int cpr_of(const amr_solver_params& p) { return p.precision == AMR_MIXED ? p.cycles_per_refinement : 1; }
+inline int max_steps(const amr_solver_params& p) { return (p.max_vcycles + cpr_of(p) - 1) / cpr_of(p); }
+
+// the two buffers of the later correction cycles; allocated by the solve entry points before
+// any stream capture begins (allocation is not allowed inside a capture)
+amr_status ensure_inner(amr_operator* op) {
+  if (op->inner_x != nullptr && op->inner_r != nullptr) return AMR_OK;
+  const size_t bytes = (size_t)op->h->nelems * sizeof(float);
+  float* a = nullptr;
+  float* b = nullptr;
+  if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess ||
+      cudaMemset(a, 0, bytes) != cudaSuccess || cudaMemset(b, 0, bytes) != cudaSuccess) {
+    cudaFree(a);
+    cudaFree(b);
+    cudaGetLastError();
+    set_error("allocation of the correction-cycle buffers failed");
+    return AMR_ERR_CUDA;
+  }
+  cudaFree(op->inner_x);
+  cudaFree(op->inner_r);
+  op->inner_x = a;
+  op->inner_r = b;
+  return AMR_OK;
+}
+
+// The FP32 correction of one refinement step into s32.X from the FP32 residual s32.rin:
+// one composite V-cycle, then (cycles_per_refinement > 1) further cycles on the FP32
+// composite residual rin - A X of the correction so far (homogeneous boundary data), each
+// added to it.  The correction so far moves to inner_x and the next cycle writes the other
+// buffer, so no copy is made.
+template <int D>
+amr_status mixed_correction(amr_operator* op, const amr_solver_params& p, cudaStream_t st) {
+  Scratch<float>& S = op->s32;
+  TRY((vcycle_corr<float, D>(op, p, S.rin, st)));
+  if (cpr_of(p) <= 1) return AMR_OK;
+  if (op->inner_x == nullptr || op->inner_r == nullptr) {
+    set_error("correction-cycle buffers were not allocated before the solve");
+    return AMR_ERR_INVALID_ARG;
+  }
+  amr_hierarchy* h = op->h;
+  for (int c = 1; c < cpr_of(p); ++c) {
+    std::swap(S.X, op->inner_x);
+    TRY(composite_op<D>(op, OP_RESID, op->inner_x, (const float*)S.rin, op->inner_r, (const float*)nullptr, st));
+    TRY((vcycle_corr<float, D>(op, p, op->inner_r, st)));
+    for (int l = 0; l < h->L; ++l)
+      TRY((axpy<float, float, D>(level_view(h, l, nullptr), op->inner_x, S.X, (float*)nullptr, 1.0, st)));
+  }
+  return AMR_OK;
+}
+
 // ---------------------------------------------------------------- solve
 template <int D>
 amr_status solve_graph(amr_operator* op, const amr_solver_params& p, double* phi, const double* f, const double* bc,
@@ -2038,6 +2093,7 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
   loc.rhs_norm = fn;
   const double tol = std::max(p.rtol * fn, p.atol);
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  if (cpr_of(p) > 1) TRY(ensure_inner(op));
   else TRY(ensure_scratch<double>(op));
   amr_status result = AMR_ERR_NOT_CONVERGED;
   double res = 0.0;
@@ -2048,7 +2104,7 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
     if (it < 64) loc.res_history[it] = res;
     if (!std::isfinite(res)) { result = AMR_ERR_NONFINITE; set_error("residual is not finite"); break; }
     if (res <= tol) { result = AMR_OK; break; }
-    if (it >= p.max_vcycles) { set_error("max_vcycles reached"); break; }
+    if (it >= max_steps(p)) { set_error("max_vcycles reached"); break; }
     if (g_prof.on) {
       // instrumented run: keep the GPU busy for a moment so that the host queues this
       // V-cycle's launches ahead of execution and the event intervals hold kernels only
@@ -2058,7 +2114,7 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
     if (p.precision == AMR_MIXED) {
       Scratch<float>& S = op->s32;
       for (int l = 0; l < h->L; ++l) TRY(convert<double, float, D>(level_view(h, l, nullptr), op->Res, S.rin, st));
-      TRY(vcycle_corr<float, D>(op, p, S.rin, st));
+      TRY(mixed_correction<D>(op, p, st));
       for (int l = 0; l < h->L; ++l) TRY(axpy<float, double, D>(level_view(h, l, nullptr), S.X, phi, (double*)nullptr, 1.0, st));
     } else {
       Scratch<double>& S = op->s64;
@@ -2066,7 +2122,7 @@ amr_status solve_impl(amr_operator* op, const amr_solver_params& p, double* phi,
       for (int l = 0; l < h->L; ++l) TRY(axpy<double, double, D>(level_view(h, l, nullptr), S.X, phi, (double*)nullptr, 1.0, st));
     }
   }
-  loc.vcycles = it;
+  loc.vcycles = it * (p.precision == AMR_MIXED ? cpr_of(p) : 1);
   loc.final_res = res;
   if (op->neumann && result == AMR_OK) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
   else TRY(avgdown_all<D>(h, phi, st));
@@ -2122,7 +2178,7 @@ amr_status iteration_body(amr_operator* op, int prec, const amr_solver_params& p
   const int* active = h->ncomp > 1 ? op->d_active : nullptr;  // converged replicas keep their phi
   if (prec == AMR_MIXED) {
     Scratch<float>& Sf = op->s32;
-    TRY(vcycle_corr<float, D>(op, p, Sf.rin, st));
+    TRY(mixed_correction<D>(op, p, st));
     launch(k_update_valid<float>, grid, 256, 0, st, n, (const float*)Sf.X, phi, (const unsigned char*)h->d_valid, rbits,
            active);
   } else {
@@ -2166,9 +2222,9 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
     if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
     cudaGraphConditionalHandle handle;
     if (cudaGraphConditionalHandleCreate(&handle, cg, 0, 0) != cudaSuccess) { result = AMR_ERR_CUDA; break; }
-    if (nc > 1) launch(k_check_b, 1, 128, 0, cs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, p.max_vcycles,
+    if (nc > 1) launch(k_check_b, 1, 128, 0, cs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, max_steps(p),
                        op->d_stats, op->d_active);
-    else launch(k_check, 1, 1, 0, cs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+    else launch(k_check, 1, 1, 0, cs, handle, 1, rbits, fbits, p.rtol, p.atol, max_steps(p), op->d_stats);
     if ((result = launch_check()) != AMR_OK) break;
     op->launches_pre = g_launches.load() - l0;
     const cudaGraphNode_t* deps = nullptr;
@@ -2190,9 +2246,9 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
     const long long l1 = g_launches.load();
     amr_status rb = iteration_body<D>(op, p.precision, p, phi, bc, bs);
     if (rb == AMR_OK) {
-      if (nc > 1) launch(k_check_b, 1, 128, 0, bs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, p.max_vcycles,
+      if (nc > 1) launch(k_check_b, 1, 128, 0, bs, handle, 1, nc, rbits, fbits, p.rtol, p.atol, max_steps(p),
                          op->d_stats, op->d_active);
-      else launch(k_check, 1, 1, 0, bs, handle, 1, rbits, fbits, p.rtol, p.atol, p.max_vcycles, op->d_stats);
+      else launch(k_check, 1, 1, 0, bs, handle, 1, rbits, fbits, p.rtol, p.atol, max_steps(p), op->d_stats);
       rb = launch_check();
     }
     op->launches_body = g_launches.load() - l1;
@@ -2221,6 +2277,7 @@ amr_status build_solve_graph(amr_operator* op, const amr_solver_params& p, doubl
   op->g_maxv = p.max_vcycles; op->g_omega = p.omega; op->g_rtol = p.rtol; op->g_atol = p.atol;
   op->g_fuse = p.fuse_coarse;
   op->g_blk = p.temporal_blocking;
+  op->g_cpr = cpr_of(p);
   return AMR_OK;
 }
 
@@ -2240,6 +2297,7 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
     CK(cudaMallocHost(&op->h_cnorm, 2 * nc * sizeof(unsigned long long)));
   }
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  if (cpr_of(p) > 1) TRY(ensure_inner(op));
   else TRY(ensure_scratch<double>(op));
   CK(cudaMemcpyAsync(op->F, f, bytes, cudaMemcpyDeviceToDevice, st));
   if (op->neumann) {
@@ -2255,7 +2313,7 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
   const bool hit = op->exec && op->g_phi == phi && op->g_bc == bc && op->g_prec == p.precision &&
                    op->g_nu1 == p.nu1 && op->g_nu2 == p.nu2 && op->g_maxv == p.max_vcycles &&
                    op->g_omega == p.omega && op->g_rtol == p.rtol && op->g_atol == p.atol &&
-                   op->g_fuse == p.fuse_coarse && op->g_blk == p.temporal_blocking;
+                   op->g_fuse == p.fuse_coarse && op->g_blk == p.temporal_blocking && op->g_cpr == cpr_of(p);
   if (!hit) TRY(build_solve_graph<D>(op, p, phi, bc));
   CK(cudaGraphLaunch(op->exec, st));
   if (op->neumann) TRY(mean_zero_impl<D>(h, phi, nullptr, st));
@@ -2270,7 +2328,7 @@ amr_status solve_graph_launch(amr_operator* op, const amr_solver_params& p, doub
 amr_status solve_graph_stats(amr_operator* op, int c, amr_solve_stats* stats) {
   const DevStats& ds = op->h_stats[c];
   amr_solve_stats loc{};
-  loc.vcycles = ds.iter;
+  loc.vcycles = ds.iter * op->g_cpr;
   for (int i = 0; i < 64 && i <= ds.iter; ++i) loc.res_history[i] = ds.hist[i];
   loc.final_res = ds.hist[std::min(ds.iter, 63)];
   loc.rhs_norm = __builtin_bit_cast(double, op->h_cnorm[op->h->ncomp + c]);
@@ -2313,6 +2371,7 @@ amr_status solve_transpose_impl(amr_operator* op, const amr_solver_params& p, do
   const size_t bytes = (size_t)h->nelems * sizeof(double);
   TRY(ensure_scratch<double>(op));
   if (p.precision == AMR_MIXED) TRY(ensure_scratch<float>(op));
+  if (cpr_of(p) > 1) TRY(ensure_inner(op));
   amr_solve_stats loc{};
   if (p.zero_initial) CK(cudaMemsetAsync(lam, 0, bytes, st));
   // right-hand side: weight on invalid cells (derived data, the average of their children)
@@ -3309,6 +3368,7 @@ void amr_default_params(amr_solver_params* p) {
   p->use_graph = 0;
   p->fuse_coarse = 0;
   p->temporal_blocking = 1;
+  p->cycles_per_refinement = 1;
 }
 
 amr_status amr_hierarchy_create(const amr_hierarchy_desc* desc, amr_hierarchy** out) {
@@ -3460,6 +3520,8 @@ void amr_operator_destroy(amr_operator* op) {
   cudaFree(op->Tmp);
   for (auto p : op->d_mgx) cudaFree(p);
   cudaFree(op->hphi);
+  cudaFree(op->inner_x);
+  cudaFree(op->inner_r);
   cudaFree(op->hf);
   cudaFree(op->hbc);
   if (op->exec) cudaGraphExecDestroy(op->exec);
@@ -3487,7 +3549,7 @@ amr_status amr_fill_ghosts(amr_operator* op, double* phi, const double* bc, void
 amr_status amr_apply(amr_operator* op, double* phi, double* out, const double* bc, void* stream) {
   TRY(check_op(op));
   if (!phi || !out) { set_error("null field"); return AMR_ERR_INVALID_ARG; }
-  TRY(DISPATCH(op->h, composite_op, op, OP_APPLY, phi, nullptr, out, bc, S(stream)));
+  TRY(DISPATCH(op->h, composite_op, op, OP_APPLY, phi, (const double*)nullptr, out, bc, S(stream)));
   return AMR_OK;
 }
 
@@ -3513,7 +3575,8 @@ amr_status amr_smooth(amr_operator* op, int level, int nsweeps, double omega, do
 
 static amr_status check_params(const amr_solver_params* p) {
   if (!p || p->nu1 < 0 || p->nu2 < 0 || p->max_vcycles < 0 || !(p->omega > 0.0) ||
-      (p->precision != AMR_FP64 && p->precision != AMR_MIXED) || p->fuse_coarse < 0 || p->fuse_coarse > 2) {
+      (p->precision != AMR_FP64 && p->precision != AMR_MIXED) || p->fuse_coarse < 0 || p->fuse_coarse > 2 ||
+      p->cycles_per_refinement < 1 || p->cycles_per_refinement > 4) {
     set_error("bad solver parameters");
     return AMR_ERR_INVALID_ARG;
   }
