@@ -1288,6 +1288,70 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
   return AMR_OK;
 }
 
+// ---------------------------------------------------------------- cube coarse V-cycle (3-D)
+// Grid m of the level-0 pyramid starts the compile-time-size cube kernel: it and the grids
+// below are 16^3, 8^3 and the 4^3 bottom, one replica.
+constexpr int CUBE_N0 = 16;
+inline bool cube_pyramid(const amr_operator* op, int m) {
+  const amr_hierarchy* h = op->h;
+  constexpr int ng = cu_ngrids<CUBE_N0>();
+  if (h->D != 3 || h->ncomp != 1 || m + ng != (int)h->mg.size()) return false;
+  for (int q = 0; q < ng; ++q) {
+    const MgGrid& g = h->mg[m + q];
+    for (int e = 0; e < 3; ++e)
+      if (g.n[e] != (CUBE_N0 >> q)) return false;
+  }
+  constexpr int nb = cu_bottom<CUBE_N0, CUBE_N0>();
+  return op->nbot == nb * nb * nb;
+}
+
+template <typename T>
+amr_status cube_coarse(amr_operator* op, const amr_solver_params& p, int m0, const T* b, T* x, cudaStream_t st) {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  constexpr size_t smem = sizeof(T) * cu_total<CUBE_N0, CUBE_N0>();
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+      CK(cudaFuncSetAttribute(k_mg_coarse3d_cube<T, CUBE_N0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done[dev] = true;
+    }
+  }
+  const amr_hierarchy* h = op->h;
+  CubeBlock cb{};
+  cb.nu1 = p.nu1;
+  cb.nu2 = p.nu2;
+  cb.nbot = op->nbot;
+  cb.ldb = op->ldb;
+  cb.minv = op->d_binv;
+  cb.gp = h->mg[m0].patch;
+  const LevelView l0 = mg_view(h, m0, op->bc);
+  for (int f = 0; f < 6; ++f) cb.bcm |= (l0.bc[f] & 1) << f;
+  const float alpha = (float)op->alpha, beta = (float)op->beta, omega = (float)p.omega;
+  cb.alpha = alpha;
+  for (int q = 0; q < cu_ngrids<CUBE_N0>(); ++q) {
+    const LevelView lv = mg_view(h, m0 + q, op->bc);
+    const float inv = lv.inv12h2_f;
+    cb.binv[q] = beta * inv;
+    for (int c = 0; c < 125; ++c) {
+      const int cls[3] = {c % 5, (c / 5) % 5, c / 25};
+      float acc = -90.0f;
+      for (int d = 0; d < 3; ++d)
+        if (cls[d]) acc += lv.dcorr_f[2 * d + (cls[d] - 1) / 2][(cls[d] - 1) % 2];
+      cb.wt[q][c] = omega / (alpha + beta * inv * acc);
+    }
+  }
+  cudaEvent_t ev;
+  prof_begin(st, &ev);
+  launch(k_mg_coarse3d_cube<T, CUBE_N0>, 1, dim3(32, 32, 1), smem, st, cb, b, x);
+  TRY(launch_check());
+  const double cells = (double)CUBE_N0 * CUBE_N0 * CUBE_N0;
+  prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * cells, cells);  // read f, write x
+  return AMR_OK;
+}
+
 // ---------------------------------------------------------------- cluster coarse V-cycle (3-D)
 // First level-0 multigrid grid from which every grid down to the bottom has at most
 // CC_CELLS cells (and there are at most CC_MAX of them, at least one above the bottom); -1
@@ -1403,6 +1467,9 @@ amr_status mg_level0(amr_operator* op, const amr_solver_params& p, int m, const 
     // fuse_coarse = 2: the coarse end of the pyramid in one cluster launch
     if (p.fuse_coarse == 2 && h->ncomp == 1 && m == coarse_cluster_m0(h))
       return coarse_cluster<T, D, TR>(op, p, m, b, x, t, st);
+    // default: a 16^3, 8^3, 4^3 coarse end of an FP32 forward V-cycle in one block
+    if constexpr (sizeof(T) == 4 && !TR)
+      if (p.fuse_coarse == 0 && p.nu1 >= 1 && cube_pyramid(op, m)) return cube_coarse<T>(op, p, m, b, x, st);
   }
   if (m == M) {
     const int n = op->nbot;

@@ -1118,3 +1118,42 @@ def test_amr3d_composite_solves_match_golden_values():
                 assert abs(got[l][i, j, k] - v) <= 1e-10 * scale, (name, precision, l, i, j, k, got[l][i, j, k], v)
         op.close()
         gh.close()
+
+
+@pytest.mark.parametrize("bc,ab", [([0, 1, 1, 0, 0, 1], (1.0, -0.02)), ([0] * 6, (0.0, 1.0))])
+@pytest.mark.parametrize("two_level", [False, True])
+def test_3d_cube_coarse_fp32_vcycle(bc, ab, two_level):
+    """The one-block coarse V-cycle of 3-D pyramids ending 16^3, 8^3, 4^3 (FP32, the default
+    coarse end of such pyramids): one mixed-precision step from zero (one FP32 V-cycle on f)
+    against the oracle's FP64 V-cycle to FP32 accuracy, on a 32^3 base (pyramid 32, 16, 8, 4)
+    alone and with a fine box; then solves to 1e-10 with it and with the cluster coarse end
+    (fuse_coarse = 2): the same V-cycle count (within one), both meeting the tolerance by the
+    oracle's composite residual."""
+    amr = _amr()
+    n0 = (32, 32, 32)
+    boxes = [[((0, 0, 0), (31, 31, 31))]]
+    if two_level:
+        boxes.append([((16, 16, 16), (47, 47, 47))])
+    alpha, beta = ab
+    H = OH(3, n0, boxes, bc=bc, hi=(1.0, 1.0, 1.0))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / 32)
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(103)
+    F = _rand_field(H, rng)
+    df = _dev(to_packed(gh, H, F))
+    x = torch.zeros_like(df)
+    op.solve(x, df, allow_not_converged=True,
+             params=amr.default_params(rtol=1e-30, max_vcycles=1, precision=1, use_graph=0))
+    ref = mg.CompositeMG(H, alpha, beta).vcycle(cp.new_field(H), F)
+    got = from_packed(gh, H, x.cpu().numpy())
+    assert max_diff(H, got, ref) <= 2e-5 * max_abs(H, ref)
+    out = []
+    for fuse in (0, 2):
+        y = torch.zeros_like(df)
+        st = op.solve(y, df, params=amr.default_params(rtol=1e-10, max_vcycles=100, precision=1, use_graph=1,
+                                                         fuse_coarse=fuse))
+        out.append((from_packed(gh, H, y.cpu().numpy()), st["vcycles"]))
+    assert abs(out[0][1] - out[1][1]) <= 1
+    for sol, _ in out:
+        R = cp.residual(H, sol, F, alpha, beta)
+        assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F)
