@@ -683,6 +683,19 @@ def _ms2d_measure(amr, torch, reps=5):
     return out
 
 
+def _batch_golden_errors(hs, phis):
+    """Error of batch solutions against the oracle's stored direct solutions of four problems
+    (tests/golden/batch2d.json): max over the samples relative to max|phi|, worst problem."""
+    with open(os.path.join(ROOT, "tests", "golden", "batch2d.json")) as fh:
+        gold = json.load(fh)
+    worst = 0.0
+    for k, e in gold["problems"].items():
+        per = hs[int(k)].unpack(phis[int(k)].cpu().numpy())[0][0]
+        for i, j, v in e["samples_index_value"]:
+            worst = max(worst, abs(float(per[i - 2, j - 2]) - v) / e["max_abs"])  # oracle arrays carry 2 ghosts
+    return worst
+
+
 def _batch_measure(amr, torch, reps=3):
     """The batch workload: 96 independent single-level Helmholtz problems of uneven sizes
     N in {64,...,512} (seeded), mixed precision to 1e-10, all solved by one amr_batch_solve
@@ -710,7 +723,8 @@ def _batch_measure(amr, torch, reps=3):
         st, status = res[-1]
         vc = sum(pr["n"] ** 2 * s["vcycles"] for pr, s in zip(probs, st))
         out[name] = {"ms_per_batch": statistics.median(ts), "value": vc / (statistics.median(ts) * 1e-3),
-                     "unit": UNIT, "all_converged": all(x == 0 for x in status)}
+                     "unit": UNIT, "all_converged": all(x == 0 for x in status),
+                     "error_vs_stored_oracle": _batch_golden_errors(hs, phis)}
     p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=amr.MIXED, use_graph=1)
 
     def seq():

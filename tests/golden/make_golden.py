@@ -18,7 +18,10 @@ i.e. 16^3 fine cells, Gaussian-bump right-hand sides): the composite discrete so
 the pure-Neumann PPE (right-hand side component 0) after the solvability fix and mean-zero,
 and of the Helmholtz system of velocity component 1 (alpha = 1, beta = -0.25 * 1e-3 / 256,
 homogeneous Dirichlet), at 24 seeded valid cells of each level.  Each direct solve takes a
-few minutes: ``python tests/golden/make_golden.py amr3d`` writes this file alone."""
+few minutes: ``python tests/golden/make_golden.py amr3d`` writes this file alone.
+
+batch2d.json: four problems of the batch workload (``python tests/golden/make_golden.py
+batch2d``), directly solved, 24 seeded cells each."""
 import json
 import math
 import os
@@ -127,6 +130,33 @@ def amr3d():
     _write_samples(res, sols, g, "amr3d.json")
 
 
+def batch2d():
+    """batch2d.json: four problems of the batch workload (the first three of size 64^2 and the
+    first of size 96^2 in its seeded order), each solved directly: 24 seeded cells and
+    max|phi| per problem."""
+    probs = wl.batch2d_problems()
+    picks = [k for k, pr in enumerate(probs) if pr["n"] == 64][:3] + [k for k, pr in enumerate(probs) if pr["n"] == 96][:1]
+    g = np.random.default_rng(20250603 + 3)
+    res = {"source": "oracle.solve.solve_direct on workloads.batch2d_problems() entries (alpha, beta as given, "
+                     "homogeneous Dirichlet); written by tests/golden/make_golden.py", "problems": {}}
+    for k in picks:
+        pr = probs[k]
+        n = pr["n"]
+        H = Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]], bc=[0] * 4)
+        F = cp.new_field(H)
+        F[0][H.levels[0].covered] = pr["rhs"].ravel()
+        phi, _, _ = so.solve_direct(H, F, pr["alpha"], pr["beta"])
+        lev = H.levels[0]
+        idx = np.argwhere(lev.valid)
+        pick = idx[g.choice(len(idx), size=24, replace=False)]
+        res["problems"][str(k)] = {
+            "n": n, "samples_index_value": [[int(v) for v in c] + [float(phi[0][tuple(c)])] for c in pick],
+            "max_abs": float(np.max(np.abs(phi[0][lev.valid])))}
+    with open(os.path.join(HERE, "batch2d.json"), "w") as fh:
+        json.dump(res, fh, indent=1)
+    print("wrote batch2d.json")
+
+
 def _write_samples(res, sols, g, fname):
     for name, (H, phi) in sols.items():
         samples = []
@@ -144,6 +174,9 @@ def _write_samples(res, sols, g, fname):
 if __name__ == "__main__":
     if sys.argv[1:] == ["amr3d"]:
         amr3d()
+    elif sys.argv[1:] == ["batch2d"]:
+        batch2d()
     else:
         main()
+        batch2d()
         amr3d()

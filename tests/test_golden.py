@@ -46,3 +46,26 @@ def test_oracle_reproduces_amr2d_golden_values():
         for l, i, j, v in AMR2D[name]["samples_level_index_value"]:
             assert H.levels[l].valid[i, j]
             assert abs(phi[l][i, j] - v) <= 1e-12 * scale, (name, l, i, j)
+
+
+def test_oracle_reproduces_batch2d_golden_values():
+    """The stored batch-workload solutions (four seeded problems) are reproduced by the
+    oracle's direct solve, and each is the discrete solution: the oracle's residual of the
+    stored problem vanishes to rounding at the sampled cells' level."""
+    from oracle import composite as cp, solve as so
+    from oracle.hierarchy import Hierarchy
+    from paper_2506_02663_gb300 import workloads as wl
+    gold = json.load(open(os.path.join(HERE, "golden", "batch2d.json")))
+    probs = wl.batch2d_problems()
+    for k, e in gold["problems"].items():
+        pr = probs[int(k)]
+        n = pr["n"]
+        assert n == e["n"]
+        H = Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]], bc=[0] * 4)
+        F = cp.new_field(H)
+        F[0][H.levels[0].covered] = pr["rhs"].ravel()
+        phi, _, _ = so.solve_direct(H, F, pr["alpha"], pr["beta"])
+        for s in e["samples_index_value"]:
+            assert abs(phi[0][s[0], s[1]] - s[2]) <= 1e-12 * e["max_abs"]
+        R = cp.residual(H, phi, F, pr["alpha"], pr["beta"])
+        assert np.max(np.abs(R[0][H.levels[0].valid])) <= 1e-9 * np.max(np.abs(F[0][H.levels[0].valid]))

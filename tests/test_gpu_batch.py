@@ -199,3 +199,33 @@ def test_stacked_batch_matches_separate_solves(precision, scale, bulk):
         op.close()
     for gh in ghs:
         gh.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_stored_oracle_solutions(precision):
+    """The four stored problems of the batch workload (tests/golden/batch2d.json: the oracle's
+    direct solutions at seeded cells), solved together by amr_batch_solve to 1e-12: every
+    sample within 1e-10 of max|phi|."""
+    import json
+    import os
+    from paper_2506_02663_gb300 import amr, workloads as wl
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch2d.json")))
+    probs = wl.batch2d_problems()
+    keys = sorted(gold["problems"], key=int)
+    hs, ops, fs = [], [], []
+    for k in keys:
+        pr = probs[int(k)]
+        n = pr["n"]
+        gh = amr.Hierarchy(2, (n, n), [[((0, 0), (n - 1, n - 1))]])
+        hs.append(gh)
+        ops.append(amr.Operator(gh, pr["alpha"], pr["beta"], [0, 0, 0, 0]))
+        fs.append(torch.from_numpy(gh.pack([[pr["rhs"]]])).cuda())
+    phis = [torch.zeros_like(f) for f in fs]
+    stats, status = amr.batch_solve(ops, phis, fs, params=amr.default_params(rtol=1e-12, max_vcycles=100,
+                                                                              precision=precision))
+    assert all(s == 0 for s in status), status
+    for k, gh, x in zip(keys, hs, phis):
+        e = gold["problems"][k]
+        per = gh.unpack(x.cpu().numpy())[0][0]
+        for i, j, v in e["samples_index_value"]:
+            assert abs(float(per[i - 2, j - 2]) - v) <= 1e-10 * e["max_abs"], (k, i, j)
