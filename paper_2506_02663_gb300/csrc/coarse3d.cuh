@@ -184,6 +184,8 @@ struct CubeBlock {
   float wt[4][125];     // omega / diag per grid and distance class kx + 5 ky + 25 kz
   float binv[4];        // beta / (12 h^2) per grid
   float alpha;
+  long long cstride;    // stacked component batches: replica stride of the top grid's arrays
+  const int* active;    // and the replicas still iterating (null for one replica)
 };
 
 template <typename T, int N0>
@@ -383,6 +385,9 @@ template <typename T, int N0>
 __global__ void __launch_bounds__(CU_NT) k_mg_coarse3d_cube(const __grid_constant__ CubeBlock cb,
                                                             const T* __restrict__ b, T* __restrict__ x) {
   pdl_wait();
+  // stacked component batches: block c works on replica c (converged replicas return)
+  const int rep = blockIdx.x;
+  if (cb.active != nullptr && !cb.active[rep]) return;
   extern __shared__ __align__(16) unsigned char cu_smraw[];
   __shared__ double bot[Cu<cu_bottom<N0, N0>()>::E];
   CubeVcycle<T, N0> v;
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(CU_NT) k_mg_coarse3d_cube(const __grid_constan
   v.bot = bot;
   const int tid = threadIdx.x + 32 * threadIdx.y;
   {
-    const T* __restrict__ bg = b + cb.gp.off;
+    const T* __restrict__ bg = b + cb.gp.off + rep * cb.cstride;
     T* bs = v.template B<N0>();
     for (int t = tid; t < N0 * N0 * N0; t += CU_NT) {
       const int i = t % N0, j = (t / N0) % N0, k = t / (N0 * N0);
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(CU_NT) k_mg_coarse3d_cube(const __grid_constan
   }
   __syncthreads();
   const T* res = v.template cycle<N0>();
-  T* __restrict__ xg = x + cb.gp.off;
+  T* __restrict__ xg = x + cb.gp.off + rep * cb.cstride;
   for (int t = tid; t < N0 * N0 * N0; t += CU_NT) {
     const int i = t % N0, j = (t / N0) % N0, k = t / (N0 * N0);
     xg[(k + NG) * cb.gp.sz + (j + NG) * cb.gp.sy + i + NG] = res[CubeVcycle<T, N0>::template at<N0>(i, j, k)];

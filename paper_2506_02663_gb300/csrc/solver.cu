@@ -1290,12 +1290,12 @@ amr_status coarse_block(amr_operator* op, const amr_solver_params& p, int m0, si
 
 // ---------------------------------------------------------------- cube coarse V-cycle (3-D)
 // Grid m of the level-0 pyramid starts the compile-time-size cube kernel: it and the grids
-// below are 16^3, 8^3 and the 4^3 bottom, one replica.
+// below are 16^3, 8^3 and the 4^3 bottom (one block per replica of a stacked batch).
 constexpr int CUBE_N0 = 16;
 inline bool cube_pyramid(const amr_operator* op, int m) {
   const amr_hierarchy* h = op->h;
   constexpr int ng = cu_ngrids<CUBE_N0>();
-  if (h->D != 3 || h->ncomp != 1 || m + ng != (int)h->mg.size()) return false;
+  if (h->D != 3 || m + ng != (int)h->mg.size()) return false;
   for (int q = 0; q < ng; ++q) {
     const MgGrid& g = h->mg[m + q];
     for (int e = 0; e < 3; ++e)
@@ -1329,6 +1329,8 @@ amr_status cube_coarse(amr_operator* op, const amr_solver_params& p, int m0, con
   cb.gp = h->mg[m0].patch;
   const LevelView l0 = mg_view(h, m0, op->bc);
   for (int f = 0; f < 6; ++f) cb.bcm |= (l0.bc[f] & 1) << f;
+  cb.cstride = h->ncomp > 1 ? h->mg[m0].cstride : 0;
+  cb.active = l0.active;
   const float alpha = (float)op->alpha, beta = (float)op->beta, omega = (float)p.omega;
   cb.alpha = alpha;
   for (int q = 0; q < cu_ngrids<CUBE_N0>(); ++q) {
@@ -1345,9 +1347,9 @@ amr_status cube_coarse(amr_operator* op, const amr_solver_params& p, int m0, con
   }
   cudaEvent_t ev;
   prof_begin(st, &ev);
-  launch(k_mg_coarse3d_cube<T, CUBE_N0>, 1, dim3(32, 32, 1), smem, st, cb, b, x);
+  launch(k_mg_coarse3d_cube<T, CUBE_N0>, h->ncomp, dim3(32, 32, 1), smem, st, cb, b, x);
   TRY(launch_check());
-  const double cells = (double)CUBE_N0 * CUBE_N0 * CUBE_N0;
+  const double cells = (double)CUBE_N0 * CUBE_N0 * CUBE_N0 * h->ncomp;
   prof_end(st, ev, PC_COARSE, 2.0 * sizeof(T) * cells, cells);  // read f, write x
   return AMR_OK;
 }
