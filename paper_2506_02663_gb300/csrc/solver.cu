@@ -1780,6 +1780,7 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
   // ---- down
   for (int l = L; l >= 1; --l) {
     const DeviceLists& cl = h->lev[l - 1].dev;
+    bool deferred = false;
     if (blocked_amr_level<T, D>(op, p, l)) {
       // one launch: nu1 sweeps from zero (zero CF ghosts) into E_l, X_l += E_l, and the
       // mean of the fine residual R_l - A_l E_l into R_{l-1} on the covered cells
@@ -1797,9 +1798,8 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
     } else {
       TRY(smooth_from_zero<T, D>(h, l, lv[l], S.R, S.E, S.T1, p.nu1, a_, b_, p.omega, true, st));
       TRY(axpy<T, T, D>(lv[l], S.E, S.X, (T*)nullptr, 1.0, st));
-      // invalid cells of level l-1: mean of the fine residual R_l - A_l E_l (zero CF ghosts)
       TRY(copy_fill<T>(h, l, S.E, st));
-      TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+      deferred = true;  // the fine residual's mean is restricted after the level-(l-1) residual
     }
     // valid cells of level l-1: composite residual r - A^comp X
     for (int m = l - 1; m >= 0; --m) {
@@ -1811,7 +1811,16 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
     TRY(copy_fill<T>(h, l - 1, S.X, st));
     TRY(cfi_fill<T, D>(h, l, S.X, S.X, false, st));
     TRY(copy_fill<T>(h, l, S.X, st));
-    TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, h->d_valid, st));
+    if (deferred) {
+      // every cell of level l-1, then its invalid cells overwritten by the mean of the fine
+      // residual R_l - A_l E_l (zero CF ghosts): the same values as the masked residual
+      // after the restriction, without the mask (the restriction reads neither array the
+      // level-(l-1) residual writes)
+      TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, nullptr, st));
+      TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+    } else {
+      TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, h->d_valid, st));
+    }
     P3<T> xc{{S.X, S.X, S.X}}, xf{{S.X, S.X, S.X}}, nb{{nullptr, nullptr, nullptr}};
     TRY(reflux<T, D>(h, l - 1, lv[l - 1], lv[l], xc, xf, nb, S.R, -b_, 0, st));
   }

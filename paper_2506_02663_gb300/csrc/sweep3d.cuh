@@ -410,6 +410,16 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
         if (ka + 1 < kb) fq[1][r] = __ldg(reinterpret_cast<const V*>(frow + sz + r * sy));
       }
     }
+    // the valid mask of the lane's pairs (masked residual), two planes ahead like f
+    uchar2 mq[2][RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      mq[0][r] = mq[1][r] = make_uchar2(1, 1);
+      if (vrow != nullptr) {
+        mq[0][r] = *reinterpret_cast<const uchar2*>(vrow + r * sy);
+        if (ka + 1 < kb) mq[1][r] = *reinterpret_cast<const uchar2*>(vrow + sz + r * sy);
+      }
+    }
     // restriction: the coarse cell of the lane (x: its pair, y: the warp's two rows, z: a
     // plane pair) and the running sum of its children
     T racc = T(0);
@@ -466,9 +476,16 @@ __global__ void __launch_bounds__(32 * (TY / RW + 2), sizeof(T) == 4 ? 3 : 2)  /
           }
         }
         if (vrow != nullptr) {
-          const unsigned char* vr = vrow + r * sy;
-          if (vr[0]) orow[r * sy] = o0;
-          if (vr[1]) orow[r * sy + 1] = o1;
+          // the pair's two mask bytes in one load; both valid (everywhere outside the region a
+          // finer level covers, and inside it both are invalid): one paired store
+          const uchar2 vm = mq[FS][r];
+          if (k + 2 < kb) mq[FS][r] = *reinterpret_cast<const uchar2*>(vrow + 2 * sz + r * sy);
+          if (vm.x && vm.y) {
+            st2<T>(orow + r * sy, V{o0, o1});
+          } else {
+            if (vm.x) orow[r * sy] = o0;
+            if (vm.y) orow[r * sy + 1] = o1;
+          }
         } else {
           st2<T>(orow + r * sy, V{o0, o1});
         }
