@@ -54,12 +54,13 @@ def _args():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads and the FP64 arm")
-    ap.add_argument("--profile-case", choices=["none", "large", "bench", "single3d", "bumps3d", "bumps2d"],
+    ap.add_argument("--profile-case", choices=["none", "large", "bench", "single3d", "resid64", "bumps3d", "bumps2d"],
                     default="none",
                     help="large: one mixed-precision solve of the single-level 4096^2 case; bench: one warm-up "
                          "and one timed step of the bench workload; bumps2d: the same for the 2-D two-level "
                          "workload; single3d: one mixed-precision V-cycle of a single-level 256^3 Helmholtz "
-                         "problem; bumps3d: the mixed-precision PPE and one Helmholtz solve of the 3-D workload, "
+                         "problem; resid64: three FP64 level residuals of a single-level 256^3 Helmholtz problem; "
+                         "bumps3d: the mixed-precision PPE and one Helmholtz solve of the 3-D workload, "
                          "host-driven loop (all for ncu)")
     return ap.parse_args()
 
@@ -876,6 +877,28 @@ def _profile_single3d(n=256):
     return 0
 
 
+def _profile_resid64(n=256):
+    """Three FP64 level residuals (amr_residual) of a single-level n^3 Helmholtz problem with
+    homogeneous Dirichlet data and seeded random x and f: the fixed-point FP64 residual and its
+    frame pass on a grid whose fields exceed L2 (134 MB per FP64 field; about 1 GB on the
+    device in all)."""
+    import torch
+    from paper_2506_02663_gb300 import amr
+    from paper_2506_02663_gb300 import workloads as wl
+    gh = amr.Hierarchy(3, (n, n, n), [[((0, 0, 0), (n - 1, n - 1, n - 1))]], h0=1.0 / n)
+    op = amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA, [0] * 6)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(gh.nelems, dtype=torch.float64, device="cuda", generator=g)
+    f = torch.randn(gh.nelems, dtype=torch.float64, device="cuda", generator=g)
+    r = torch.zeros_like(x)
+    for _ in range(3):
+        op.residual(x, f, r)
+    torch.cuda.synchronize()
+    amr.check_kernel_flags()
+    print(json.dumps({"profile_case": "resid64", "max_abs_residual": float(r.abs().max())}))
+    return 0
+
+
 def _profile_bumps3d():
     """The 3-D workload's PPE and one Helmholtz solve, mixed precision, host-driven loop."""
     import torch
@@ -943,6 +966,8 @@ def main():
         return _profile_bumps2d()
     if args.profile_case == "single3d":
         return _profile_single3d()
+    if args.profile_case == "resid64":
+        return _profile_resid64()
     if args.profile_case == "bumps3d":
         return _profile_bumps3d()
     if args.impl == "reference":
