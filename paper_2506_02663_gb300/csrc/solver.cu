@@ -1817,7 +1817,19 @@ amr_status vcycle_corr(amr_operator* op, const amr_solver_params& p, const T* r,
       // after the restriction, without the mask (the restriction reads neither array the
       // level-(l-1) residual writes)
       TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, nullptr, st));
-      TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+      if (D == 3 && lv[l - 1].npatch == lv[l - 1].ncomp && sw_eligible(lv[l]) && lv[l].maxn[2] % 2 == 0 &&
+          tile_rows_for(lv[l], sizeof(T)) == TILE_BULK) {
+        // a single-patch fine level over a single-patch coarse level: the bulk-copy
+        // restriction (the arithmetic of k_restrict)
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        TRY((launch_sw<T, OP_RESTRICT>(lv[l], S.E, S.R, (T*)nullptr, T(a_), T(b_), T(0), nullptr, st, nullptr, S.R,
+                                       &lv[l - 1].p0, lv[l - 1].cstride)));
+        const double cc = lv[l].ncells / 8.0;
+        prof_end(st, ev, PC_RESTRICT, (2.0 * 8 + 1.0) * sizeof(T) * cc, cc * 8);
+      } else {
+        TRY(restrict_blocks<T, D>(lv[l], lv[l - 1], cl.xfer, cl.nxfer, cl.xfer_max, true, S.E, S.R, S.R, a_, b_, st));
+      }
     } else {
       TRY(level_op<T, D>(OP_RESID, lv[l - 1], S.X, r, S.R, nullptr, a_, b_, 0.0, h->d_valid, st));
     }

@@ -1157,3 +1157,36 @@ def test_3d_cube_coarse_fp32_vcycle(bc, ab, two_level):
     for sol, _ in out:
         R = cp.residual(H, sol, F, alpha, beta)
         assert max_abs(H, R) <= 1.05e-10 * max_abs(H, F)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_bulk_amr_restriction_matches_generic(bulk_sweep, precision):
+    """The restriction of a single-patch fine level's residual into the coarse level by the
+    bulk-copy kernel (base 64 x 32 x 16, a 64 x 32 x 16 fine box; both levels bulk-copy): one
+    FP64 V-cycle and two mixed refinement steps bit for bit those of the z-chunked kernels with
+    the generic restriction, and the FP64 V-cycle equal to the oracle's to 1e-10."""
+    amr = _amr()
+    n0 = (64, 32, 16)
+    boxes = [[((0, 0, 0), (63, 31, 15))], [((32, 16, 8), (95, 47, 23))]]
+    bc = [0, 1, 0, 0, 1, 0]
+    alpha, beta = 1.0, -0.02
+    H = OH(3, n0, boxes, bc=bc, hi=(1.0, 0.5, 0.25))
+    gh = amr.Hierarchy(3, n0, boxes, h0=1.0 / 64)
+    op = amr.Operator(gh, alpha, beta, bc)
+    rng = np.random.default_rng(107)
+    F = _rand_field(H, rng)
+    phi = _rand_field(H, rng)
+    got = {}
+    for on in (2, 0):
+        bulk_sweep(on)
+        dphi = _dev(to_packed(gh, H, phi))
+        if precision == 0:
+            op.vcycle(dphi, _dev(to_packed(gh, H, F)))
+        else:
+            op.solve(dphi, _dev(to_packed(gh, H, F)), allow_not_converged=True,
+                     params=amr.default_params(rtol=1e-30, max_vcycles=2, precision=1, use_graph=0))
+        got[on] = from_packed(gh, H, dphi.cpu().numpy())
+    assert max_diff(H, got[2], got[0]) == 0.0
+    if precision == 0:
+        ref = mg.CompositeMG(H, alpha, beta).vcycle(phi, F)
+        assert max_diff(H, got[2], ref) <= 1e-10 * max_abs(H, ref)
