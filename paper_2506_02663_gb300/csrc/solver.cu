@@ -3713,8 +3713,21 @@ amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* 
   return s;
 }
 
+// The batch solve; with f_host / phi_host (amr_batch_solve_host, device staging phi / f) the
+// concurrent per-problem path copies each problem's data on its own stream around its solve.
+// The caller of the host form makes f_host, phi_host null for the other paths.
+amr_status batch_solve_impl(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
+                            const double* const* f, amr_solve_stats* stats, int* status, void* stream,
+                            const double* const* f_host = nullptr, double* const* phi_host = nullptr);
+
 amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
                            const double* const* f, amr_solve_stats* stats, int* status, void* stream) {
+  return batch_solve_impl(ops, n, p, phi, f, stats, status, stream);
+}
+
+amr_status batch_solve_impl(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi,
+                            const double* const* f, amr_solve_stats* stats, int* status, void* stream,
+                            const double* const* f_host, double* const* phi_host) {
   if (!ops || n < 0 || !phi || !f) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
   TRY(check_params(p));
   for (int k = 0; k < n; ++k) {
@@ -3734,13 +3747,27 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
   cudaStream_t st = S(stream);
   amr_solver_params q = *p;
   q.use_graph = 1;
-  // single-level 2-D problems with blocked legs: one launch per phase over a work list
+  // single-level 2-D problems with blocked legs: one launch per phase over a work list; one
+  // 3-D geometry and operator for every problem: one stacked solve
   bool worklist = n > 0;
   for (int k = 0; k < n && worklist; ++k) worklist = batch_levels(ops[k], q) >= 0;
-  if (worklist) return batch_worklist(ops, n, q, phi, f, stats, status, st);
-  // one 3-D geometry and operator for every problem: one stacked solve
-  if (g_stack_batches.load(std::memory_order_relaxed) && stackable(ops, n))
-    return batch_stacked(ops, n, q, phi, f, stats, status, st);
+  const bool stacked = !worklist && g_stack_batches.load(std::memory_order_relaxed) && stackable(ops, n);
+  if (worklist || stacked) {
+    // host buffers: all copies in, the batch, all copies out, on the caller's stream
+    for (int k = 0; k < n && f_host != nullptr; ++k) {
+      const size_t bytes = (size_t)ops[k]->h->nelems * sizeof(double);
+      CK(cudaMemcpyAsync(const_cast<double*>(f[k]), f_host[k], bytes, cudaMemcpyHostToDevice, st));
+      if (!q.zero_initial) CK(cudaMemcpyAsync(phi[k], phi_host[k], bytes, cudaMemcpyHostToDevice, st));
+    }
+    const amr_status s = worklist ? batch_worklist(ops, n, q, phi, f, stats, status, st)
+                                  : batch_stacked(ops, n, q, phi, f, stats, status, st);
+    if (phi_host == nullptr || (s != AMR_OK && s != AMR_ERR_NOT_CONVERGED)) return s;
+    for (int k = 0; k < n; ++k)
+      CK(cudaMemcpyAsync(phi_host[k], phi[k], (size_t)ops[k]->h->nelems * sizeof(double), cudaMemcpyDeviceToHost,
+                         st));
+    CK(cudaStreamSynchronize(st));
+    return s;
+  }
   std::lock_guard<std::mutex> lock(mu);
   // problems that share a hierarchy share its reduction scratch: same stream, in order
   std::vector<const amr_hierarchy*> hs;
@@ -3755,7 +3782,16 @@ amr_status amr_batch_solve(amr_operator* const* ops, int n, const amr_solver_par
   for (int i = 0; i < NSTREAM; ++i) CK(cudaStreamWaitEvent(pool[i], ev[NSTREAM], 0));
   for (int k = 0; k < n; ++k) {
     amr_operator* op = ops[k];
-    TRY(DISPATCH(op->h, solve_graph_launch, op, q, phi[k], f[k], nullptr, pool[sid[k]]));
+    cudaStream_t sk = pool[sid[k]];
+    const size_t bytes = (size_t)op->h->nelems * sizeof(double);
+    // host buffers (amr_batch_solve_host): each problem's copies sit on its own stream, so the
+    // copies of one problem overlap the solves of the others
+    if (f_host != nullptr) {
+      CK(cudaMemcpyAsync(const_cast<double*>(f[k]), f_host[k], bytes, cudaMemcpyHostToDevice, sk));
+      if (!q.zero_initial) CK(cudaMemcpyAsync(phi[k], phi_host[k], bytes, cudaMemcpyHostToDevice, sk));
+    }
+    TRY(DISPATCH(op->h, solve_graph_launch, op, q, phi[k], f[k], nullptr, sk));
+    if (phi_host != nullptr) CK(cudaMemcpyAsync(phi_host[k], phi[k], bytes, cudaMemcpyDeviceToHost, sk));
   }
   for (int i = 0; i < NSTREAM; ++i) {
     CK(cudaEventRecord(ev[i], pool[i]));
@@ -3781,29 +3817,19 @@ amr_status amr_batch_solve_host(amr_operator* const* ops, int n, const amr_solve
     for (int j = 0; j < k; ++j)
       if (ops[j] == ops[k]) { set_error("an operator appears twice in a host-buffer batch"); return AMR_ERR_INVALID_ARG; }
   }
-  cudaStream_t st = S(stream);
   std::vector<double*> dphi(n);
   std::vector<const double*> df(n);
   for (int k = 0; k < n; ++k) {
     amr_operator* op = ops[k];
     if (!op->hphi) TRY(dalloc(&op->hphi, op->h->nelems));
     if (!op->hf) TRY(dalloc(&op->hf, op->h->nelems));
-  }
-  for (int k = 0; k < n; ++k) {
-    amr_operator* op = ops[k];
-    const size_t bytes = (size_t)op->h->nelems * sizeof(double);
-    CK(cudaMemcpyAsync(op->hf, f_host[k], bytes, cudaMemcpyHostToDevice, st));
-    if (!p->zero_initial) CK(cudaMemcpyAsync(op->hphi, phi_host[k], bytes, cudaMemcpyHostToDevice, st));
     dphi[k] = op->hphi;
     df[k] = op->hf;
   }
-  const amr_status s = amr_batch_solve(ops, n, p, dphi.data(), df.data(), stats, status, stream);
-  if (s != AMR_OK && s != AMR_ERR_NOT_CONVERGED) return s;
-  for (int k = 0; k < n; ++k) {
-    const size_t bytes = (size_t)ops[k]->h->nelems * sizeof(double);
-    CK(cudaMemcpyAsync(phi_host[k], ops[k]->hphi, bytes, cudaMemcpyDeviceToHost, st));
-  }
-  CK(cudaStreamSynchronize(st));
+  // the copies are issued by the batch itself (per problem and stream where it runs the
+  // problems concurrently), and the call returns once every phi is back on the host
+  const amr_status s = batch_solve_impl(ops, n, p, dphi.data(), df.data(), stats, status, stream, f_host, phi_host);
+  CK(cudaStreamSynchronize(S(stream)));
   return s;
 }
 

@@ -229,3 +229,35 @@ def test_batch_matches_stored_oracle_solutions(precision):
         per = gh.unpack(x.cpu().numpy())[0][0]
         for i, j, v in e["samples_index_value"]:
             assert abs(float(per[i - 2, j - 2]) - v) <= 1e-10 * e["max_abs"], (k, i, j)
+
+
+def test_stacked_batch_host_buffers():
+    """amr_batch_solve_host on the stacked path (three Helmholtz problems of one 3-D geometry,
+    stacked batches on): the copies around the stacked solve give the device batch's
+    solutions and V-cycle counts."""
+    from paper_2506_02663_gb300 import amr, workloads as wl
+    p = amr.default_params(rtol=1e-10, max_vcycles=100, precision=1)
+    ghs, ops, fs = [], [], []
+    for comp in (1, 2, 3):
+        dim, n0, boxes, rhs = wl.bumps3d_rhs(scale=8, component=comp)
+        gh = amr.Hierarchy(dim, n0, boxes)
+        ghs.append(gh)
+        ops.append(amr.Operator(gh, 1.0, wl.HELMHOLTZ_BETA * 64, [0] * 6))
+        fs.append(gh.pack(rhs))
+    amr.set_stacked_batches(1)
+    try:
+        dphis = [torch.zeros(len(f), dtype=torch.float64, device="cuda") for f in fs]
+        st_d, status_d = amr.batch_solve(ops, dphis, [torch.from_numpy(f).cuda() for f in fs], params=p)
+        ph = [np.zeros_like(f) for f in fs]
+        st_h, status_h = amr.batch_solve_host(ops, ph, fs, params=p)
+        assert status_h == status_d and all(s == 0 for s in status_h)
+        for k in range(3):
+            assert st_h[k]["vcycles"] == st_d[k]["vcycles"]
+            ref = dphis[k].cpu().numpy()
+            assert np.max(np.abs(ph[k] - ref)) <= 1e-13 * np.max(np.abs(ref))
+    finally:
+        amr.set_stacked_batches(0)
+    for op in ops:
+        op.close()
+    for gh in ghs:
+        gh.close()
