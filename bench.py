@@ -41,8 +41,16 @@ WORKLOAD = ("bumps3d: 3-D two-level AMR, base 256^3 on [0,1]^3 + ratio-2 box [0.
             "sums (one set per system), each to ||r||_inf <= 1e-10 ||f||_inf")
 RTOL = 1e-10
 # FP32 correction cycles per FP64 residual in the mixed-precision solves of the 3-D workload
-# (amr_solver_params.cycles_per_refinement; the iterate equals that of one cycle per step)
-CPR = 2
+# (amr_solver_params.cycles_per_refinement; the iterate equals that of one cycle per step, so
+# the V-cycle counts stay those of one cycle per step when they divide: PPE 18, Helmholtz 8, 6)
+CPR_PPE = 3
+CPR_HELM = 2
+
+
+def _params3d(amr, prec, use_graph):
+    """Solver parameters of the 3-D step: (PPE, Helmholtz systems)."""
+    return tuple(amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=use_graph,
+                                    cycles_per_refinement=c) for c in (CPR_PPE, CPR_HELM))
 
 
 def _args():
@@ -332,11 +340,12 @@ def _close(w):
         g.close()
 
 
-def _step3d(amr, w, p):
-    """One step: the PPE, then the three Helmholtz components in one batched call."""
+def _step3d(amr, w, pp):
+    """One step: the PPE, then the three Helmholtz components in one batched call; pp = the
+    parameters of the PPE and of the Helmholtz systems."""
     ops, phis, fs = w["ops"], w["phis"], w["fs"]
-    vc = [ops[0].solve(phis[0], fs[0], params=p)["vcycles"]]
-    st, status = amr.batch_solve(ops[1:], phis[1:], fs[1:], params=p)
+    vc = [ops[0].solve(phis[0], fs[0], params=pp[0])["vcycles"]]
+    st, status = amr.batch_solve(ops[1:], phis[1:], fs[1:], params=pp[1])
     if any(status):
         raise RuntimeError(f"batched Helmholtz solves: statuses {status}")
     return vc + [s["vcycles"] for s in st]
@@ -426,7 +435,7 @@ def run_ours(args):
     w = _bumps3d(amr, torch)
     dof = w["dof"]
     prec = amr.MIXED if args.precision == "mixed" else amr.FP64
-    params = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1, cycles_per_refinement=CPR)
+    params = _params3d(amr, prec, 1)
 
     for _ in range(args.warmup):
         _step3d(amr, w, params)
@@ -456,8 +465,8 @@ def run_ours(args):
     ops = w["ops"]
 
     def e2e_step():
-        vc = [ops[0].solve_host(ph[0], fh[0], params=params)["vcycles"]]
-        st, _ = amr.batch_solve_host(ops[1:], ph[1:], fh[1:], params=params)
+        vc = [ops[0].solve_host(ph[0], fh[0], params=params[0])["vcycles"]]
+        st, _ = amr.batch_solve_host(ops[1:], ph[1:], fh[1:], params=params[1])
         return vc + [s["vcycles"] for s in st]
     e2e_step()
     torch.cuda.synchronize()
@@ -474,10 +483,10 @@ def run_ours(args):
 
     # ---------------- roofline of the dominant kernel, live (instrumented host-driven loop)
     peak, peak_kind = _peaks()
-    prof = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=0, cycles_per_refinement=CPR)
+    prof = _params3d(amr, prec, 0)
     amr.profile_enable(True)
-    for op, phi, f in zip(ops, w["phis"], w["fs"]):
-        op.solve(phi, f, params=prof)
+    for k, (op, phi, f) in enumerate(zip(ops, w["phis"], w["fs"])):
+        op.solve(phi, f, params=prof[0 if k == 0 else 1])
     amr.profile_enable(False)
     classes = _class_table(amr, SIZE_BUCKETS)
     roofline = _roofline_entry(classes, peak, peak_kind, "bumps3d")
@@ -490,7 +499,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "dof_per_system": dof, "systems": ["ppe", "helmholtz_u", "helmholtz_v",
                                                                              "helmholtz_w"],
-                   "precision": args.precision, "rtol": RTOL, "cycles_per_refinement": CPR,
+                   "precision": args.precision, "rtol": RTOL,
+                   "cycles_per_refinement": {"ppe": CPR_PPE, "helmholtz": CPR_HELM},
                    "vcycles_per_system": vc_per_system,
                    "l2": "no flush: every input and solution field (about 160 MB in FP64) is larger than the "
                          "129 MB L2",
@@ -506,7 +516,7 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         other = amr.FP64 if prec == amr.MIXED else amr.MIXED
-        p2 = amr.default_params(rtol=RTOL, max_vcycles=100, precision=other, use_graph=1, cycles_per_refinement=CPR)
+        p2 = _params3d(amr, other, 1)
         _step3d(amr, w, p2)
         ts2, vcs2 = _timed(torch, lambda: _step3d(amr, w, p2), min(args.steps, 3))
         key = "fp64" if prec == amr.MIXED else "mixed"
@@ -922,7 +932,7 @@ def _profile_bench(args):
     from paper_2506_02663_gb300 import amr
     w = _bumps3d(amr, torch)
     prec = amr.MIXED if args.precision == "mixed" else amr.FP64
-    p = amr.default_params(rtol=RTOL, max_vcycles=100, precision=prec, use_graph=1)
+    p = _params3d(amr, prec, 1)
     for it in range(2):  # the second step inside the "measured" range
         if it == 1:
             torch.cuda.nvtx.range_push("measured")
