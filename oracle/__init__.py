@@ -28,4 +28,7 @@ Modules
 ``solve``      sparse assembly of the composite operator, direct solves, solvability fix
                (Sec. 6.4), mean-zero, transposes (adjoint).
 ``mg``         Sec. 6.5 geometric multigrid (V-cycle with weighted Jacobi, omega = 2/3).
+``cic``        Sec. 6.3-6.4 interface conditions of the subcycled solves: the time
+               interpolation I^(4) (Eq. timeInterp) and the per-component correction of the
+               interface face averages (Eq. correctingFaceAvg).
 """
