@@ -372,6 +372,56 @@ amr_status amr_solve_host(amr_operator* op, const amr_solver_params* p, double* 
 amr_status amr_batch_solve_host(amr_operator* const* ops, int n, const amr_solver_params* p, double* const* phi_host,
                                 const double* const* f_host, amr_solve_stats* stats, int* status, void* stream);
 
+/* ---- coarse-fine interface conditions of a subcycled level solve ------------------- */
+/* In the subcycled method each refined level l advances with its own time step and reads its
+ * coarse-fine interface data from level l-1 at four equispaced coarse times (Sec. 6.3, steps
+ * CIC-2 and CIC-3).  These calls are the data-parallel part of that: the interface ghosts at
+ * an intermediate time and the corrected interface face averages.  All need 1 <= level <
+ * nlevels on an unstacked hierarchy (AMR_ERR_INVALID_ARG otherwise). */
+
+/* CF ghost cells of `level` at the time t* of Eq. (timeInterp): coarse[i] (i = 0..3; device
+ * composite fields, only level-1 read) hold the data at t_{-i} = t^{l-1} - i k (so coarse[0]
+ * is the latest), k > 0 is the coarse time step and eta = t* - t_{-1} (usually 0 <= eta <=
+ * k).  The printed matrix's columns take the four times in increasing order (its entries are
+ * the cubic Lagrange weights of eta = -2k, -k, 0, k), the reverse of the printed vector, so
+ * printed column j is applied to coarse[3-j]; eta = 0 gives exactly coarse[1] and eta = k
+ * coarse[0].  The printed second row is the eta-derivative of the first, so `rate` receives
+ * d(phi)/dt at t* (multiply by k for the k d(phi)/dt of the equation's left side).  Every
+ * level-`level` ghost cell that AMRCFI fills (Sec. 5.2) receives, in `value`, the AMRCFI
+ * value of the interpolated coarse data, and in `rate` (nullable) that of its time
+ * derivative; no other cell of either field is written.  AMRCFI windows may include coarse
+ * cells covered by `level`: coarse[i] must hold their average-down there, as after
+ * amr_fill_ghosts.  Fails on null fields, k <= 0 or a non-finite k or eta. */
+amr_status amr_cic_ghosts(amr_hierarchy* h, int level, const double* const* coarse, double k, double eta,
+                          double* value, double* rate, void* stream);
+
+/* The coarse-fine interface faces of `level` (faces between a cell of the level's boxes and a
+ * CF ghost cell; one per first-layer CF ghost) and the level's connected components (Sec.
+ * 5.1; numbered in ascending order of their smallest box index in the level's box list).
+ * Host-only, works without a GPU.  Faces are grouped by component.  Two-call pattern: any
+ * output may be NULL.  nfaces / ncomponents: counts; cell (nfaces x dim ints): global index,
+ * at the level, of the interior cell next to each face; face (nfaces): 2 d + side (side 1:
+ * the cell's high face along dimension d, so the outward normal is +e_d; 0: -e_d);
+ * component (nfaces): the face's component. */
+amr_status amr_cic_faces(const amr_hierarchy* h, int level, int* nfaces, int* ncomponents, int* cell, int* face,
+                         int* component);
+
+/* Normal face averages n . <w> on the interface faces of `level`, corrected per connected
+ * component (Sec. 6.4, Eq. correctingFaceAvg).  w[d] (d < dim; device composite fields):
+ * the velocity components, with the level's ghost cells filled (CF ghosts at the wanted time,
+ * e.g. by amr_cic_ghosts; ghosts inside sibling boxes copied, e.g. by amr_fill_ghosts).  Each
+ * face average is Eq. (cell2face) along the normal over the two interior cells and the two
+ * ghost layers.  phys (device, ncomponents doubles, nullable = zeros): for each component,
+ * the sum of the face averages n . <u^b> over its faces on the physical boundary.  Then for
+ * every component c one shift delta_c is added to all its interface faces, so that
+ * -delta_c |faces of c| = (sum of its uncorrected interface averages) + phys[c], i.e. the
+ * corrected interface sum plus phys[c] is zero.  faces (device, nfaces doubles; NULL allowed
+ * when the level has no interface face): the corrected averages in amr_cic_faces order; delta (device, ncomponents doubles, nullable):
+ * the shifts (0 for a component with no interface face).  The per-component sum is a
+ * fixed-order tree (one block per component), so results are deterministic. */
+amr_status amr_cic_face_averages(amr_hierarchy* h, int level, const double* const* w, const double* phys,
+                                 double* faces, double* delta, void* stream);
+
 void amr_default_params(amr_solver_params* p);
 const char* amr_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far (a host-side

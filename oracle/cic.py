@@ -6,20 +6,26 @@ per-component correction of the interface face averages.
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Readings (the printed passage is inconsistent with itself):
-* Eq. (timeInterp) gives a 2 x 4 matrix I^(4)(k, eta) acting on the coarse values at four
-  equispaced times.  Its first row is exactly the cubic Lagrange interpolation with the four
-  columns at eta = -2k, -k, 0, k (in the printed column order): the printed entries put
-  weight 1 on the third column at eta = 0, although the text defines eta from the time of
-  the second column.  The matrix entries win.  Its second row is the eta-derivative of those
-  weights: applied to the four values it gives d(phi)/dt, although the left-hand side names
-  k d(phi)/dt.  The oracle returns the printed rows (value, d/dt) with the nodes in that
-  order; ``time_interp_matrix(..., scaled=True)`` multiplies the second row by k to give
-  the quantity the left-hand side names.
+* Eq. (timeInterp) multiplies a 2 x 4 matrix I^(4)(k, eta) with a vector printed as
+  phi(t_{-0}), ..., phi(t_{-3}), where t_{-i} = t^{l-1} - i k (caption of the interface
+  figure, part (c)) and eta = t* - t_{-1}.  The printed matrix entries are the cubic
+  Lagrange weights of the nodes eta = -2k, -k, 0, k in column order, i.e. of t_{-3},
+  t_{-2}, t_{-1}, t_{-0}: the columns take the times in increasing order, the reverse of the
+  printed vector.  Reading: column j multiplies phi(t_{-(3-j)}); then eta = 0 puts the unit
+  weight on t_{-1}, as the definition of eta requires.  The second printed row is the
+  eta-derivative of the first: applied to the data it gives d(phi)/dt, although the
+  left-hand side names k d(phi)/dt.  ``time_interp_matrix`` returns the printed matrix
+  (columns in printed order, nodes ``time_interp_nodes``); ``coarse_time_weights`` the same
+  rows for the data in the order t_{-0}, t_{-1}, t_{-2}, t_{-3}; ``scaled=True`` multiplies
+  the second row by k.
 * Eq. (correctingFaceAvg): on each connected component c of the level, one shift delta_c of
   every interface face average, with -delta_c |faces_I^c| = sum over the interface faces of
   the uncorrected averages + sum over the physical faces of the given ones.
 """
 import numpy as np
+
+from . import stencil as st
+from .cfi import cfi_values
 
 
 def time_interp_nodes(k):
@@ -60,8 +66,23 @@ def printed_time_interp_matrix(k, eta):
 
 def time_interpolate(values, k, eta, scaled=False):
     """[phi(t*), d(phi)/dt(t*) (times k when scaled)] from the four coarse values (arrays of
-    any equal shape, in column order)."""
+    any equal shape, in the matrix's column order)."""
     M = time_interp_matrix(k, eta, scaled)
+    v = np.stack([np.asarray(a, dtype=np.float64) for a in values])
+    return np.tensordot(M, v, axes=(1, 0))
+
+
+def coarse_time_weights(k, eta, scaled=False):
+    """The rows of I^(4)(k, eta) for the data in the order phi(t_{-0}), phi(t_{-1}),
+    phi(t_{-2}), phi(t_{-3}) with t_{-i} = t^{l-1} - i k and eta = t* - t_{-1}: column j of
+    the printed matrix belongs to t_{-(3-j)}."""
+    return time_interp_matrix(k, eta, scaled)[:, ::-1]
+
+
+def interpolate_coarse_times(values, k, eta, scaled=False):
+    """[phi(t*), d(phi)/dt(t*)] from the data at t_{-0}, t_{-1}, t_{-2}, t_{-3} in that
+    order."""
+    M = coarse_time_weights(k, eta, scaled)
     v = np.stack([np.asarray(a, dtype=np.float64) for a in values])
     return np.tensordot(M, v, axes=(1, 0))
 
@@ -85,3 +106,51 @@ def correct_by_component(interface, component, physical_sums):
         sel = lab == c
         a[sel], deltas[int(c)] = correct_face_averages(a[sel], physical_sums.get(int(c), 0.0))
     return a, deltas
+
+
+def interface_ghost_values(H, coarse_times, l, k, eta):
+    """CIC-2 and CIC-3 on the CF ghost cells of level l: AMRCFI (Sec. 5.2) of each of the four
+    coarse level arrays ``coarse_times`` (level l-1 at t_{-0}, t_{-1}, t_{-2}, t_{-3} in that
+    order; redundant data on covered coarse cells), then Eq. (timeInterp) at t* = t_{-1} +
+    eta.  Returns (cells, value, rate): the array indices of level l's CF ghosts (np.argwhere
+    order), the interpolated values and their time derivatives (the printed second row)."""
+    lev, crs = H.levels[l], H.levels[l - 1]
+    cells = np.argwhere(lev.cf_ghost)
+    g = cells + np.asarray(lev.origin)
+    fine = [cfi_values(c, crs.origin, crs.ndom, g, H.ratio, H.D)[0] for c in coarse_times]
+    value, rate = interpolate_coarse_times(fine, k, eta)
+    return cells, value, rate
+
+
+def interface_faces(H, l):
+    """The coarse-fine interface faces of level l: faces between a cell of the level's boxes
+    and a CF ghost cell.  Returns a list of (cell, d, s, component): the array index of the
+    interior cell, the normal dimension, the side (+1: the cell's high face, outward normal
+    +e_d) and the connected component of the cell's box (Sec. 5.1; components numbered in
+    ascending order of their smallest box index)."""
+    lev = H.levels[l]
+    labels = H.components(l)
+    order = sorted(set(labels))
+    comp_of_box = [order.index(labels[b]) for b in range(len(labels))]
+    out = []
+    for d in range(H.D):
+        for s in (1, -1):
+            for c in np.argwhere(lev.covered):
+                nb = c.copy()
+                nb[d] += s
+                if 0 <= nb[d] < lev.shape[d] and lev.cf_ghost[tuple(nb)]:
+                    out.append((tuple(int(v) for v in c), d, s, comp_of_box[int(lev.patch[tuple(c)])]))
+    return out
+
+
+def interface_face_averages(H, W, l, faces=None):
+    """n . <w> on the interface faces of level l (``W``: the D level-l arrays of the velocity
+    components with their ghosts filled): Eq. (cell2face) on the face along its normal."""
+    faces = interface_faces(H, l) if faces is None else faces
+    out = np.empty(len(faces))
+    for i, (c, d, s, _) in enumerate(faces):
+        lowcell = list(c)
+        if s < 0:
+            lowcell[d] -= 1  # the face is the high face of the cell below it
+        out[i] = s * st.face_value(W[d], H.D, d, tuple(lowcell))
+    return out

@@ -89,6 +89,9 @@ _sigs = {
     "amr_gradient_transpose": [_vp, _P(C.c_int), _P(_vp), _vp, _vp],
     "amr_divergence_transpose": [_vp, _P(C.c_int), _vp, _P(_vp), _vp],
     "amr_project_transpose": [_vp, _P(SolverParams), _P(C.c_int), _P(_vp), _P(_vp), _vp, _P(SolveStats), _vp],
+    "amr_cic_ghosts": [_vp, C.c_int, _P(_vp), C.c_double, C.c_double, _vp, _vp, _vp],
+    "amr_cic_faces": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)],
+    "amr_cic_face_averages": [_vp, C.c_int, _P(_vp), _vp, _vp, _vp, _vp],
     "amr_default_params": [_P(SolverParams)],
     "amr_last_error": [],
     "amr_kernel_launches": [],
@@ -515,3 +518,37 @@ def project(ppe, vel_bc_types, w, u, phi, w_bc=None, params=None, stream=None):
     _check(_lib.amr_project(ppe._op, C.byref(p), bt, _ptr_array(w), wb, _ptr_array(u), _ptr(phi), C.byref(s),
                             _stream(stream)), "amr_project")
     return stats_dict(s)
+
+
+def cic_ghosts(hier, level, coarse, k, eta, value, rate=None, stream=None):
+    """amr_cic_ghosts: the CF ghosts of `level` at t* from the four coarse time levels
+    ``coarse`` (columns of I^(4) in order) into ``value`` and, when given, d/dt into ``rate``."""
+    if len(coarse) != 4:
+        raise ValueError("cic_ghosts needs four coarse time levels")
+    _check(_lib.amr_cic_ghosts(hier.handle, int(level), _ptr_array(coarse), float(k), float(eta), _ptr(value),
+                               _ptr(rate), _stream(stream)), "amr_cic_ghosts")
+
+
+def cic_faces(hier, level):
+    """amr_cic_faces: the interface faces of `level` as numpy arrays: cell (n, dim) global index
+    of the interior cell, face (n,) = 2 d + side, component (n,); and the component count."""
+    nf, nc = C.c_int(), C.c_int()
+    _check(_lib.amr_cic_faces(hier.handle, int(level), C.byref(nf), C.byref(nc), None, None, None), "amr_cic_faces")
+    n, D = nf.value, hier.dim
+    cell = (C.c_int * max(1, n * D))()
+    face = (C.c_int * max(1, n))()
+    comp = (C.c_int * max(1, n))()
+    _check(_lib.amr_cic_faces(hier.handle, int(level), None, None, cell, face, comp), "amr_cic_faces")
+    return {"cell": np.ctypeslib.as_array(cell)[:n * D].reshape(n, D).copy(),
+            "face": np.ctypeslib.as_array(face)[:n].copy(),
+            "component": np.ctypeslib.as_array(comp)[:n].copy(), "ncomponents": nc.value}
+
+
+def cic_face_averages(hier, level, w, faces, phys=None, delta=None, stream=None):
+    """amr_cic_face_averages: corrected normal face averages of the velocity ``w`` (list of dim
+    device fields) on the interface faces of `level` into ``faces``; ``phys`` / ``delta``
+    (device, one double per component) optional."""
+    if len(w) != hier.dim:
+        raise ValueError("cic_face_averages needs one field per dimension")
+    _check(_lib.amr_cic_face_averages(hier.handle, int(level), _ptr_array(w), _ptr(phys), _ptr(faces), _ptr(delta),
+                                      _stream(stream)), "amr_cic_face_averages")

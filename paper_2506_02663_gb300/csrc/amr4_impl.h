@@ -82,6 +82,17 @@ struct CfiGroup {
   signed char pad;
 };
 
+// One coarse-fine interface face of a level (Sec. 6.4, Eq. correctingFaceAvg): the CF ghost
+// of the first layer across it, step = side x the patch stride along the face normal (the
+// interior cell next to the face is ghost - step, the second ghost layer ghost + step), the
+// normal dimension and the side (+1: the interior cell's high face).
+struct CicFace {
+  long long ghost;
+  long long step;
+  int dir;
+  int side;
+};
+
 struct CopyEntry {
   long long dst;
   long long src;
@@ -117,6 +128,10 @@ struct DeviceLists {
   long long ncfig = 0;
   CopyEntry* copy = nullptr;
   long long ncopy = 0;
+  CicFace* cicf = nullptr;  // coarse-fine interface faces, grouped by connected component
+  int* cic_cstart = nullptr;
+  int ncicf = 0;
+  int ncic_comp = 0;
   RefluxEntry* reflux = nullptr;
   long long nreflux = 0;
   XferBlock* xfer = nullptr;  // blocks between this level (coarse) and level+1
@@ -135,6 +150,14 @@ struct LevelHost {
   std::vector<long long> cfi_side;
   std::vector<long long> cfi_key;  // per CF ghost: its coarse parent and face (grouping key)
   std::vector<CopyEntry> copy;
+  // coarse-fine interface faces (one per first-layer CF ghost), grouped by the connected
+  // component of their patch (components in ascending order of their smallest box index);
+  // faces of component c are [cic_cstart[c], cic_cstart[c+1]); cic_cell holds D global
+  // indices per face (the interior cell), cic_comp the component of each face
+  std::vector<CicFace> cicf;
+  std::vector<int> cic_cstart;
+  std::vector<int> cic_cell;
+  std::vector<int> cic_comp;
   std::vector<RefluxEntry> reflux;  // this level's coarse cells bordering level+1
   std::vector<XferBlock> xfer;      // this level (coarse) <-> level+1 (fine)
   DeviceLists dev;

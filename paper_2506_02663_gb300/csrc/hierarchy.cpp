@@ -216,6 +216,36 @@ static T* upload(const std::vector<T>& v) {
 // CF ghosts grouped by coarse parent (entries with one key): the shared window (origin,
 // coarse patch, position) of the first child, each child's destination at index sub_x +
 // 2 sub_y + 4 sub_z.  Ratio 2 only (no groups otherwise: the per-ghost list is used).
+// Orders a level's interface faces by connected component (stable within a component) and
+// records the component ranges; on entry cic_comp holds each face's patch index.
+static void group_cic_faces(LevelHost& L, const std::vector<int>& im_component, int D) {
+  const size_t nb = L.boxes.size();
+  std::vector<int> label(nb), comp_of_label(nb, -1);
+  for (size_t k = 0; k < nb; ++k) label[k] = im_component[L.first_patch + k];
+  int ncomp = 0;
+  for (size_t k = 0; k < nb; ++k)  // labels are the smallest box index of each component
+    if (label[k] == (int)k) comp_of_label[k] = ncomp++;
+  const size_t nf = L.cicf.size();
+  std::vector<int> comp(nf);
+  for (size_t i = 0; i < nf; ++i) comp[i] = comp_of_label[label[L.cic_comp[i]]];
+  std::vector<size_t> ord(nf);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return comp[a] < comp[b]; });
+  std::vector<CicFace> f(nf);
+  std::vector<int> cell(nf * D), cc(nf);
+  for (size_t i = 0; i < nf; ++i) {
+    f[i] = L.cicf[ord[i]];
+    cc[i] = comp[ord[i]];
+    for (int e = 0; e < D; ++e) cell[i * D + e] = L.cic_cell[ord[i] * D + e];
+  }
+  L.cicf.swap(f);
+  L.cic_cell.swap(cell);
+  L.cic_comp.swap(cc);
+  L.cic_cstart.assign(ncomp + 1, 0);
+  for (size_t i = 0; i < nf; ++i) ++L.cic_cstart[L.cic_comp[i] + 1];
+  for (int c = 0; c < ncomp; ++c) L.cic_cstart[c + 1] += L.cic_cstart[c];
+}
+
 static std::vector<CfiGroup> cfi_groups(const std::vector<CfiEntry>& cfi, const std::vector<long long>& key, int r,
                                         int D) {
   std::vector<CfiGroup> out;
@@ -454,6 +484,12 @@ amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std
                         }
                   }
                   L.cfi.push_back(ce);
+                  if (ce.layer == 1 || ce.layer == -1) {  // a coarse-fine interface face
+                    const long long stride = d == 0 ? 1 : (d == 1 ? p.sy : p.sz);
+                    L.cicf.push_back({ce.dst, ce.layer * stride, d, (int)ce.layer});
+                    for (int e = 0; e < D; ++e) L.cic_cell.push_back(e == d ? g[e] - ce.layer : g[e]);
+                    L.cic_comp.push_back((int)k);  // patch for now; component below
+                  }
                   {
                     // grouping key: fine patch, face, coarse parent
                     long long key = (long long)k * 6 + 2 * d + (g[d] < p.lo[d] ? 0 : 1);
@@ -475,6 +511,7 @@ amr_status build_hierarchy(const amr_hierarchy_desc* desc, amr_hierarchy* h, std
           }
       padded_base += cidx;
     }
+    group_cic_faces(L, h->im_component, D);
   }
 
   // ---- reflux lists (COH-3) and transfer blocks ----
@@ -717,6 +754,10 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
       L.dev.cfi_side = upload(L.cfi_side);
       L.dev.copy = upload(L.copy);
       L.dev.ncopy = (long long)L.copy.size();
+      L.dev.cicf = upload(L.cicf);
+      L.dev.ncicf = (int)L.cicf.size();
+      L.dev.cic_cstart = upload(L.cic_cstart);
+      L.dev.ncic_comp = L.cic_cstart.empty() ? 0 : (int)L.cic_cstart.size() - 1;
       L.dev.reflux = upload(L.reflux);
       L.dev.nreflux = (long long)L.reflux.size();
       L.dev.xfer = upload(L.xfer);
@@ -753,6 +794,8 @@ void free_hierarchy(amr_hierarchy* h) {
     cudaFree(L.dev.cfig);
     cudaFree(L.dev.cfi_side);
     cudaFree(L.dev.copy);
+    cudaFree(L.dev.cicf);
+    cudaFree(L.dev.cic_cstart);
     cudaFree(L.dev.reflux);
     cudaFree(L.dev.xfer);
   }

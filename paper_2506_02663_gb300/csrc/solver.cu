@@ -20,6 +20,7 @@
 #include "kernels.cuh"
 #include "sweep3d.cuh"
 #include "coarse3d.cuh"
+#include "cic.cuh"
 
 using namespace amr4;
 
@@ -3351,6 +3352,52 @@ amr_status mean_zero_noalloc_impl(amr_hierarchy* h, double* x, double* mean_host
   }
   return AMR_OK;
 }
+
+// ---------------------------------------------------------------- interface conditions
+// The two rows of I^(4)(k, eta) of Eq. (timeInterp), each entry divided by 6 k^3 (so that
+// eta = 0 gives exactly the unit weight on t_{-1}): row 0 the value weights, row 1 those of
+// the time derivative, for the data at t_{-i} = t^{l-1} - i k in the order i = 0..3.  The
+// printed matrix's columns take the times in increasing order (its entries are the cubic
+// Lagrange weights of eta = -2k, -k, 0, k with eta = t* - t_{-1}), so printed column j
+// belongs to t_{-(3-j)}.
+void cic_weights(double k, double eta, double w[2][4]) {
+  const double e = eta, e2 = eta * eta, e3 = e2 * eta, k2 = k * k, k3 = k2 * k, den = 6.0 * k3;
+  const double m[2][4] = {{(-e3 + k2 * e) / den, (3.0 * e3 + 3.0 * k * e2 - 6.0 * k2 * e) / den,
+                           (-3.0 * e3 - 6.0 * k * e2 + 3.0 * k2 * e + 6.0 * k3) / den,
+                           (e3 + 3.0 * k * e2 + 2.0 * k2 * e) / den},
+                          {(-3.0 * e2 + k2) / den, (9.0 * e2 + 6.0 * k * e - 6.0 * k2) / den,
+                           (-9.0 * e2 - 12.0 * k * e + 3.0 * k2) / den, (3.0 * e2 + 6.0 * k * e + 2.0 * k2) / den}};
+  for (int r = 0; r < 2; ++r)
+    for (int i = 0; i < 4; ++i) w[r][i] = m[r][3 - i];
+}
+
+template <int D>
+amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, double k, double eta, double* v,
+                           double* rate, cudaStream_t st) {
+  const DeviceLists& dl = h->lev[l].dev;
+  if (dl.ncfi == 0) return AMR_OK;
+  CicTimes ct{};
+  for (int i = 0; i < 4; ++i) ct.x[i] = xt[i];
+  cic_weights(k, eta, ct.w);
+  const int nt = 128;
+  if (dl.ncfig > 0)
+    launch(k_cic_grp<D>, (unsigned)((dl.ncfig + nt - 1) / nt), nt, 0, st, dl.cfig, dl.ncfig, dl.cfi_side,
+           h->lev[l - 1].d_patches, ct, v, rate);
+  else
+    launch(k_cic<D>, (unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st, dl.cfi, dl.ncfi, dl.cfi_side,
+           h->lev[l - 1].d_patches, h->r, ct, v, rate);
+  return launch_check();
+}
+
+amr_status cic_faces_impl(amr_hierarchy* h, int l, const double* const* w, const double* phys, double* out,
+                          double* delta, cudaStream_t st) {
+  const DeviceLists& dl = h->lev[l].dev;
+  if (dl.ncic_comp == 0) return AMR_OK;
+  Ptr3 wp{};
+  for (int d = 0; d < h->D; ++d) wp.p[d] = w[d];
+  launch(k_cic_faces, (unsigned)dl.ncic_comp, CIC_FACE_THREADS, 0, st, dl.cicf, dl.cic_cstart, wp, phys, out, delta);
+  return launch_check();
+}
 }  // namespace
 
 // =================================================================== C ABI
@@ -3634,6 +3681,55 @@ amr_status amr_fill_ghosts(amr_operator* op, double* phi, const double* bc, void
   amr_hierarchy* h = op->h;
   TRY(DISPATCH(h, fill_ghosts_all, h, phi, S(stream)));
   return AMR_OK;
+}
+
+static amr_status check_cic_level(const amr_hierarchy* h, int level) {
+  if (!h) { set_error("null hierarchy"); return AMR_ERR_INVALID_ARG; }
+  if (h->ncomp != 1) { set_error("interface conditions need an unstacked hierarchy"); return AMR_ERR_INVALID_ARG; }
+  if (level < 1 || level >= h->L) {
+    set_error("interface conditions: level " + std::to_string(level) + " is not a refined level (1.." +
+              std::to_string(h->L - 1) + ")");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return AMR_OK;
+}
+
+amr_status amr_cic_ghosts(amr_hierarchy* h, int level, const double* const* coarse, double k, double eta,
+                          double* value, double* rate, void* stream) {
+  TRY(check_cic_level(h, level));
+  if (!coarse || !value) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  for (int i = 0; i < 4; ++i)
+    if (!coarse[i]) { set_error("amr_cic_ghosts: null coarse time level"); return AMR_ERR_INVALID_ARG; }
+  if (!(k > 0.0) || !std::isfinite(k) || !std::isfinite(eta)) {
+    set_error("amr_cic_ghosts: needs a finite time step k > 0 and a finite eta");
+    return AMR_ERR_INVALID_ARG;
+  }
+  TRY(ensure_device(h));
+  return DISPATCH(h, cic_ghosts_impl, h, level, coarse, k, eta, value, rate, S(stream));
+}
+
+amr_status amr_cic_faces(const amr_hierarchy* h, int level, int* nfaces, int* ncomponents, int* cell, int* face,
+                         int* component) {
+  TRY(check_cic_level(h, level));
+  const LevelHost& L = h->lev[level];
+  const int nf = (int)L.cicf.size();
+  if (nfaces) *nfaces = nf;
+  if (ncomponents) *ncomponents = L.cic_cstart.empty() ? 0 : (int)L.cic_cstart.size() - 1;
+  if (cell) std::memcpy(cell, L.cic_cell.data(), L.cic_cell.size() * sizeof(int));
+  if (face)
+    for (int i = 0; i < nf; ++i) face[i] = 2 * L.cicf[i].dir + (L.cicf[i].side > 0 ? 1 : 0);
+  if (component) std::memcpy(component, L.cic_comp.data(), L.cic_comp.size() * sizeof(int));
+  return AMR_OK;
+}
+
+amr_status amr_cic_face_averages(amr_hierarchy* h, int level, const double* const* w, const double* phys,
+                                 double* faces, double* delta, void* stream) {
+  TRY(check_cic_level(h, level));
+  if (!w || (!faces && !h->lev[level].cicf.empty())) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  for (int d = 0; d < h->D; ++d)
+    if (!w[d]) { set_error("amr_cic_face_averages: null velocity component"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  return cic_faces_impl(h, level, w, phys, faces, delta, S(stream));
 }
 
 amr_status amr_apply(amr_operator* op, double* phi, double* out, const double* bc, void* stream) {

@@ -58,6 +58,24 @@ def test_time_interpolation_matches_printed_entries(k):
                            rtol=0, atol=1e-12 / k)
 
 
+@pytest.mark.parametrize("k", [0.5, 0.02])
+def test_coarse_time_weights_follow_the_papers_time_labels(k):
+    """With t_{-i} = t0 - i k and eta = t* - t_{-1}, the weights for the data in the order
+    t_{-0}..t_{-3} reproduce every cubic and its derivative at t*, put the unit weight on
+    t_{-1} at eta = 0 and on t_{-0} at eta = k."""
+    rng = np.random.default_rng(23)
+    t0 = 0.8
+    times = [t0 - i * k for i in range(4)]
+    for _ in range(10):
+        p = np.polynomial.Polynomial(rng.standard_normal(4))
+        for eta in (0.0, 0.25 * k, 0.5 * k, k):
+            v, dv = cic.interpolate_coarse_times([p(t) for t in times], k, eta)
+            assert abs(v - p(times[1] + eta)) <= 1e-12 * 10
+            assert abs(dv - p.deriv()(times[1] + eta)) <= 1e-11 * 10 / k
+    assert np.array_equal(cic.coarse_time_weights(k, 0.0)[0], [0.0, 1.0, 0.0, 0.0])
+    assert np.allclose(cic.coarse_time_weights(k, k)[0], [1.0, 0.0, 0.0, 0.0], atol=1e-15)
+
+
 def test_face_correction_enforces_compatibility_per_component():
     """After Eq. (correctingFaceAvg) the interface and physical face sums of every component
     vanish; one uniform shift per component; an already compatible component is unchanged."""
@@ -72,3 +90,80 @@ def test_face_correction_enforces_compatibility_per_component():
         assert abs(np.sum(out[sel]) + phys.get(c, 0.0)) <= 1e-13
         assert np.allclose(out[sel] - a[sel], deltas[c], rtol=0, atol=1e-15)
     assert abs(deltas[2]) <= 1e-15
+
+
+def _two_level(dim=2):
+    from oracle.hierarchy import Hierarchy
+    if dim == 2:
+        return Hierarchy(2, (16, 16), [[((0, 0), (15, 15))], [((8, 8), (23, 23))]], bc=[0] * 4)
+    return Hierarchy(3, (8, 8, 8), [[((0, 0, 0), (7, 7, 7))], [((4, 4, 4), (11, 11, 11))]], bc=[0] * 6)
+
+
+def _coarse_fields(H, rng, n):
+    from oracle import solve as so
+    U = so.Unknowns(H)
+    return [U.scatter(rng.standard_normal(U.n), fill_invalid=True) for _ in range(n)]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interface_ghosts_compose_amrcfi_and_time_interpolation(dim):
+    """Data constant in time give the AMRCFI values of that field and a zero rate; data
+    linear in time (A + t B) give AMRCFI of A + t* B and the rate AMRCFI of B."""
+    from oracle import composite as cp
+    H = _two_level(dim)
+    rng = np.random.default_rng(7)
+    A, B = _coarse_fields(H, rng, 2)
+    k, eta = 0.3, 0.11
+    lev = H.levels[1]
+
+    def amrcfi(F):
+        G = [a.copy() for a in F]
+        cp.fill_cf_ghosts(H, G, 1)
+        return G[1][lev.cf_ghost]
+
+    cells, v, r = cic.interface_ghost_values(H, [A[0]] * 4, 1, k, eta)
+    assert np.array_equal(cells, np.argwhere(lev.cf_ghost))
+    assert np.allclose(v, amrcfi(A), rtol=0, atol=1e-13) and np.allclose(r, 0.0, atol=1e-12)
+    ts = [(1 - i) * k for i in range(4)]  # t_{-i} - t_{-1}, i = 0..3
+    lin = [A[0] + t * B[0] for t in ts]
+    _, v, r = cic.interface_ghost_values(H, lin, 1, k, eta)
+    want = [A[l] + eta * B[l] for l in range(2)]
+    assert np.allclose(v, amrcfi(want), rtol=0, atol=1e-12)
+    assert np.allclose(r, amrcfi(B), rtol=0, atol=1e-11)
+
+
+def test_interface_face_averages_exact_on_cubics_and_divergence_theorem():
+    """Cell averages of w = (f(x), g(y)) with cubic f, g: every interface face average equals
+    s f (or s g) at the face (Eq. cell2face is exact for cubics), and the face sums times the
+    face length equal the integral of div w over the box."""
+    H = _two_level(2)
+    lev = H.levels[1]
+    h = lev.h
+
+    def f(x):
+        return 2.0 * x ** 3 - x ** 2 + 0.5 * x + 1.0
+
+    def F(x):  # antiderivative of f
+        return 0.5 * x ** 4 - x ** 3 / 3.0 + 0.25 * x ** 2 + x
+
+    def g(y):
+        return -y ** 3 + 3.0 * y
+
+    def G(y):
+        return -0.25 * y ** 4 + 1.5 * y ** 2
+
+    i = (np.arange(lev.shape[0]) + lev.origin[0]) * h
+    j = (np.arange(lev.shape[1]) + lev.origin[1]) * h
+    W0 = np.repeat(((F(i + h) - F(i)) / h)[:, None], lev.shape[1], axis=1)
+    W1 = np.repeat(((G(j + h) - G(j)) / h)[None, :], lev.shape[0], axis=0)
+    faces = cic.interface_faces(H, 1)
+    assert len(faces) == 4 * 16
+    vals = cic.interface_face_averages(H, [W0, W1], 1, faces)
+    for (c, d, s, comp), v in zip(faces, vals):
+        assert comp == 0
+        xf = (c[d] + lev.origin[d] + (1 if s > 0 else 0)) * h
+        want = s * (f(xf) if d == 0 else g(xf))
+        assert abs(v - want) <= 1e-13
+    lo, hi = 8 * h, 24 * h
+    flux = (f(hi) - f(lo)) * (hi - lo) + (g(hi) - g(lo)) * (hi - lo)
+    assert abs(np.sum(vals) * h - flux) <= 1e-12
