@@ -62,14 +62,16 @@ def _args():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads and the FP64 arm")
-    ap.add_argument("--profile-case", choices=["none", "large", "bench", "single3d", "resid64", "bumps3d", "bumps2d"],
+    ap.add_argument("--profile-case", choices=["none", "large", "bench", "single3d", "resid64", "bumps3d", "bumps2d",
+                                               "cic3d"],
                     default="none",
                     help="large: one mixed-precision solve of the single-level 4096^2 case; bench: one warm-up "
                          "and one timed step of the bench workload; bumps2d: the same for the 2-D two-level "
                          "workload; single3d: one mixed-precision V-cycle of a single-level 256^3 Helmholtz "
                          "problem; resid64: three FP64 level residuals of a single-level 256^3 Helmholtz problem; "
                          "bumps3d: the mixed-precision PPE and one Helmholtz solve of the 3-D workload, "
-                         "host-driven loop (all for ncu)")
+                         "host-driven loop; cic3d: the interface-condition calls on the 3-D workload's refined "
+                         "level (all for ncu)")
     return ap.parse_args()
 
 
@@ -552,13 +554,28 @@ def run_ours(args):
     return 0
 
 
+# FP64 rate of the GB300 (nominal 1.25 TFLOP/s: 2 FP64 multiply-adds per clock per SM, 152 SMs,
+# 2070 MHz): the bound of the interface-ghost kernels, which are FP64-ALU-bound
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
 def _cic3d_measure(amr, torch, w, peak, peak_kind, reps=20):
     """Interface conditions of the 3-D workload's refined level (the 128^3 box): per velocity
     component the CF ghosts at t* from four coarse times (value and time derivative), then
     the corrected interface face averages of the three components (Sec. 6.3-6.4).  CUDA events
-    around `reps` calls; algorithmic bytes = the coarse cells inside the union of the AMRCFI
-    windows read once per coarse time and component, the ghost values and derivatives written,
-    and four cells read and one value written per interface face."""
+    around `reps` calls, and around `reps` single ghost calls for the roofline.  Bytes =
+    the coarse cells inside the union of the AMRCFI windows read once per coarse time and
+    component, the ghost values and derivatives written, four cells read and one value
+    written per interface face.  Flops of one ghost call = the two time combinations of every
+    window cell (8 multiply-adds) + AMRCFI of the two combinations per coarse parent (2 x
+    (2 x 125 + 4 x 25 + 8 x 5) multiply-adds), 2 flops per multiply-add."""
+    try:
+        return _cic3d_run(amr, torch, w, peak, peak_kind, reps)
+    except Exception as ex:  # the main line must not depend on this extra
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
+def _cic3d_run(amr, torch, w, peak, peak_kind, reps):
     import numpy as np
     gh, op = w["ghs"][0], w["ops"][0]
     n = gh.nelems
@@ -574,9 +591,12 @@ def _cic3d_measure(amr, torch, w, peak, peak_kind, reps=20):
     delta = torch.empty(nc, dtype=torch.float64, device="cuda")
     k, eta = 1.0 / 256.0, 0.5 / 256.0
 
+    def ghosts(d=0):
+        amr.cic_ghosts(gh, 1, coarse, k, eta, vel[d], rate[d])
+
     def call():
         for d in range(3):
-            amr.cic_ghosts(gh, 1, coarse, k, eta, vel[d], rate[d])
+            ghosts(d)
         amr.cic_face_averages(gh, 1, vel, faces, delta=delta)
     for _ in range(3):
         call()
@@ -584,6 +604,7 @@ def _cic3d_measure(amr, torch, w, peak, peak_kind, reps=20):
     l0 = amr.kernel_launches()
     ts, _ = _timed(torch, call, reps)
     launches = (amr.kernel_launches() - l0) // reps
+    tg, _ = _timed(torch, ghosts, reps)
     maps = gh.index_maps()
     starts = maps["cfi_start"]
     ncfi = len(starts)
@@ -592,17 +613,22 @@ def _cic3d_measure(amr, torch, w, peak, peak_kind, reps=20):
         band[starts[:, 0] + o[0], starts[:, 1] + o[1], starts[:, 2] + o[2]] = True
     nband = int(band.sum())
     nbytes = 3 * (4 * nband * 8 + 2 * ncfi * 8) + nf * (4 * 8 + 8)
-    ms = statistics.median(ts)
+    ngroups = ncfi // 8
+    flops = 2.0 * (8 * nband + ngroups * 2 * (2 * 125 + 4 * 25 + 8 * 5))
+    ms, msg = statistics.median(ts), statistics.median(tg)
     gbs = nbytes / (ms * 1e-3) / 1e9
-    # the per-component sum property at full size
+    tf = flops / (msg * 1e-3) / 1e12
     tot = float(faces.sum()) if nf else 0.0
     return {"ms_per_call": ms, "kernel_launches_per_call": launches, "cf_ghosts_per_component": ncfi,
             "coarse_window_cells": nband, "interface_faces": nf, "components": nc,
-            "algorithmic_bytes_per_call": nbytes, "achieved_gbs": gbs,
-            "frac_of_" + peak_kind + "_hbm": gbs / peak,
+            "bytes_per_call": nbytes, "gbs_per_call": gbs,
+            "ghost_call_ms": msg,
+            "roofline": {"bound": "alu", "kernels": "k_cic_combine + k_cic_grp3 (one amr_cic_ghosts call)",
+                         "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "FP64 TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+                         "flops_per_call": flops, "peak_kind": "nominal (2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz)"},
             "corrected_face_sum": tot,
-            "how": "3 x amr_cic_ghosts (value + rate) + amr_cic_face_averages on level 1 of bumps3d, "
-                   "median of CUDA-event times; launch-latency-bound at this size"}
+            "how": "3 x amr_cic_ghosts (value + rate) + amr_cic_face_averages on level 1 of bumps3d, median of "
+                   "CUDA-event times; the ghost kernels are FP64-rate-bound"}
 
 
 def _golden_errors(amr, torch):
@@ -1020,8 +1046,24 @@ def _profile_bumps2d():
     return 0
 
 
+def _profile_cic3d():
+    """The interface-condition calls alone on the 3-D workload's geometry (timed as in the
+    bench's cic3d entry)."""
+    import torch
+    from paper_2506_02663_gb300 import amr
+    from paper_2506_02663_gb300 import workloads as wl
+    dim, n0, boxes = wl.hierarchy_boxes("bumps3d", 1)
+    gh = amr.Hierarchy(dim, n0, boxes)
+    w = {"ghs": [gh], "ops": [amr.Operator(gh, 0.0, 1.0, [1] * 6)]}
+    peak, peak_kind = _peaks()
+    print(json.dumps({"profile_case": "cic3d", **_cic3d_measure(amr, torch, w, peak, peak_kind)}))
+    return 0
+
+
 def main():
     args = _args()
+    if args.profile_case == "cic3d":
+        return _profile_cic3d()
     if args.profile_case == "large":
         return _profile_case()
     if args.profile_case == "bench":

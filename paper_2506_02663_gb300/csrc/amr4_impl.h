@@ -93,6 +93,14 @@ struct CicFace {
   int side;
 };
 
+// A chunk of one component's interface faces [begin, end), one block of the face passes.
+struct CicChunk {
+  int comp;
+  int begin;
+  int end;
+  int pad;
+};
+
 struct CopyEntry {
   long long dst;
   long long src;
@@ -132,6 +140,18 @@ struct DeviceLists {
   int* cic_cstart = nullptr;
   int ncicf = 0;
   int ncic_comp = 0;
+  CicChunk* cic_chunks = nullptr;  // at least one chunk per component
+  int* cic_ccstart = nullptr;      // chunks of component c: [ccstart[c], ccstart[c+1])
+  double* cic_psum = nullptr;      // one partial sum per chunk
+  int ncic_chunks = 0;
+  // 3-D interface ghosts: the distinct coarse cells of the level's AMRCFI windows (field
+  // offsets, ascending) and scratch for their two time combinations, indexed by offset -
+  // cic_base over the coarse level's span; made by the first amr_cic_ghosts call
+  long long* cic_band = nullptr;
+  long long ncic_band = 0;
+  long long cic_base = 0;
+  double* cic_y = nullptr;  // 2 x cic_span doubles
+  long long cic_span = 0;
   RefluxEntry* reflux = nullptr;
   long long nreflux = 0;
   XferBlock* xfer = nullptr;  // blocks between this level (coarse) and level+1
@@ -158,6 +178,8 @@ struct LevelHost {
   std::vector<int> cic_cstart;
   std::vector<int> cic_cell;
   std::vector<int> cic_comp;
+  std::vector<CicChunk> cic_chunks;
+  std::vector<int> cic_ccstart;
   std::vector<RefluxEntry> reflux;  // this level's coarse cells bordering level+1
   std::vector<XferBlock> xfer;      // this level (coarse) <-> level+1 (fine)
   DeviceLists dev;

@@ -244,6 +244,20 @@ static void group_cic_faces(LevelHost& L, const std::vector<int>& im_component, 
   L.cic_cstart.assign(ncomp + 1, 0);
   for (size_t i = 0; i < nf; ++i) ++L.cic_cstart[L.cic_comp[i] + 1];
   for (int c = 0; c < ncomp; ++c) L.cic_cstart[c + 1] += L.cic_cstart[c];
+  // chunks of at most CIC_CHUNK faces, at least one (possibly empty) per component
+  constexpr int CIC_CHUNK = 2048;
+  L.cic_chunks.clear();
+  L.cic_ccstart.assign(1, 0);
+  for (int c = 0; c < ncomp; ++c) {
+    const int b = L.cic_cstart[c], e = L.cic_cstart[c + 1];
+    int q = b;
+    do {
+      const int qe = std::min(e, q + CIC_CHUNK);
+      L.cic_chunks.push_back({c, q, qe, 0});
+      q = qe;
+    } while (q < e);
+    L.cic_ccstart.push_back((int)L.cic_chunks.size());
+  }
 }
 
 static std::vector<CfiGroup> cfi_groups(const std::vector<CfiEntry>& cfi, const std::vector<long long>& key, int r,
@@ -758,6 +772,12 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
       L.dev.ncicf = (int)L.cicf.size();
       L.dev.cic_cstart = upload(L.cic_cstart);
       L.dev.ncic_comp = L.cic_cstart.empty() ? 0 : (int)L.cic_cstart.size() - 1;
+      L.dev.cic_chunks = upload(L.cic_chunks);
+      L.dev.cic_ccstart = upload(L.cic_ccstart);
+      L.dev.ncic_chunks = (int)L.cic_chunks.size();
+      if (!L.cic_chunks.empty() &&
+          cudaMalloc(&L.dev.cic_psum, sizeof(double) * L.cic_chunks.size()) != cudaSuccess)
+        throw std::runtime_error("cudaMalloc failed");
       L.dev.reflux = upload(L.reflux);
       L.dev.nreflux = (long long)L.reflux.size();
       L.dev.xfer = upload(L.xfer);
@@ -796,6 +816,11 @@ void free_hierarchy(amr_hierarchy* h) {
     cudaFree(L.dev.copy);
     cudaFree(L.dev.cicf);
     cudaFree(L.dev.cic_cstart);
+    cudaFree(L.dev.cic_chunks);
+    cudaFree(L.dev.cic_ccstart);
+    cudaFree(L.dev.cic_psum);
+    cudaFree(L.dev.cic_band);
+    cudaFree(L.dev.cic_y);
     cudaFree(L.dev.reflux);
     cudaFree(L.dev.xfer);
   }

@@ -3371,6 +3371,58 @@ void cic_weights(double k, double eta, double w[2][4]) {
     for (int i = 0; i < 4; ++i) w[r][i] = m[r][3 - i];
 }
 
+// The distinct coarse cells of level l's AMRCFI windows and the scratch for their time
+// combinations (3-D, ratio 2), made once per level on the first call that needs them.  The
+// scratch spans the coarse level's patches (2 doubles per element of that span).
+amr_status cic_band(amr_hierarchy* h, int l, cudaStream_t st) {
+  LevelHost& L = h->lev[l];
+  if (L.dev.cic_y) return AMR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("amr_cic_ghosts: the first call for a 3-D level allocates its scratch and must come before any "
+              "stream capture");
+    return AMR_ERR_INVALID_ARG;
+  }
+  const LevelHost& C = h->lev[l - 1];
+  long long lo = -1, hi = 0;
+  for (const PatchDesc& p : C.patches) {
+    lo = lo < 0 ? p.off : std::min(lo, p.off);
+    hi = std::max(hi, p.off + p.sz * (p.n[2] + 2 * NG));
+  }
+  std::vector<unsigned char> mark((size_t)(hi - lo), 0);
+  for (const CfiEntry& e : L.cfi) {
+    if (e.src >= 0) {
+      const PatchDesc& cp = C.patches[e.cpatch];
+      for (int c2 = 0; c2 < CFI_W; ++c2)
+        for (int c1 = 0; c1 < CFI_W; ++c1)
+          for (int c0 = 0; c0 < CFI_W; ++c0) mark[(size_t)(e.src + c0 + c1 * cp.sy + c2 * cp.sz - lo)] = 1;
+    } else {
+      const long long* s = &L.cfi_side[(size_t)(-1 - e.src) * 125];
+      for (int q = 0; q < 125; ++q) mark[(size_t)(s[q] - lo)] = 1;
+    }
+  }
+  std::vector<long long> band;
+  for (size_t i = 0; i < mark.size(); ++i)
+    if (mark[i]) band.push_back(lo + (long long)i);
+  long long* d_band = nullptr;
+  double* d_y = nullptr;
+  if (cudaMalloc(&d_band, sizeof(long long) * std::max<size_t>(band.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&d_y, sizeof(double) * 2 * (size_t)(hi - lo)) != cudaSuccess) {
+    cudaFree(d_band);
+    cudaGetLastError();
+    set_error("amr_cic_ghosts: scratch allocation failed");
+    return AMR_ERR_OOM;
+  }
+  CK(cudaMemcpy(d_band, band.data(), sizeof(long long) * band.size(), cudaMemcpyHostToDevice));
+  L.dev.cic_band = d_band;
+  L.dev.ncic_band = (long long)band.size();
+  L.dev.cic_base = lo;
+  L.dev.cic_span = hi - lo;
+  L.dev.cic_y = d_y;
+  return AMR_OK;
+}
+
 template <int D>
 amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, double k, double eta, double* v,
                            double* rate, cudaStream_t st) {
@@ -3380,7 +3432,17 @@ amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, dou
   for (int i = 0; i < 4; ++i) ct.x[i] = xt[i];
   cic_weights(k, eta, ct.w);
   const int nt = 128;
-  if (dl.ncfig > 0)
+  if (dl.ncfig > 0 && D == 3) {
+    TRY(cic_band(h, l, st));
+    double* y0 = dl.cic_y;
+    double* y1 = rate ? dl.cic_y + dl.cic_span : nullptr;
+    launch(k_cic_combine, (unsigned)((dl.ncic_band + 255) / 256), 256, 0, st, dl.cic_band, dl.ncic_band,
+           dl.cic_base, ct, y0, y1);
+    TRY(launch_check());
+    launch(k_cic_grp3, (unsigned)((dl.ncfig * CIC_LANES + CIC_GRP_THREADS - 1) / CIC_GRP_THREADS),
+           CIC_GRP_THREADS, 0, st, dl.cfig, dl.ncfig, dl.cfi_side, h->lev[l - 1].d_patches, (const double*)y0,
+           (const double*)y1, dl.cic_base, v, rate);
+  } else if (dl.ncfig > 0)
     launch(k_cic_grp<D>, (unsigned)((dl.ncfig + nt - 1) / nt), nt, 0, st, dl.cfig, dl.ncfig, dl.cfi_side,
            h->lev[l - 1].d_patches, ct, v, rate);
   else
@@ -3392,10 +3454,14 @@ amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, dou
 amr_status cic_faces_impl(amr_hierarchy* h, int l, const double* const* w, const double* phys, double* out,
                           double* delta, cudaStream_t st) {
   const DeviceLists& dl = h->lev[l].dev;
-  if (dl.ncic_comp == 0) return AMR_OK;
+  if (dl.ncic_chunks == 0) return AMR_OK;
   Ptr3 wp{};
   for (int d = 0; d < h->D; ++d) wp.p[d] = w[d];
-  launch(k_cic_faces, (unsigned)dl.ncic_comp, CIC_FACE_THREADS, 0, st, dl.cicf, dl.cic_cstart, wp, phys, out, delta);
+  launch(k_cic_faces_sum, (unsigned)dl.ncic_chunks, CIC_FACE_THREADS, 0, st, dl.cicf, dl.cic_chunks, wp, out,
+         dl.cic_psum);
+  TRY(launch_check());
+  launch(k_cic_faces_shift, (unsigned)dl.ncic_chunks, CIC_FACE_THREADS, 0, st, dl.cic_chunks, dl.cic_ccstart,
+         dl.cic_cstart, dl.cic_psum, phys, out, delta);
   return launch_check();
 }
 }  // namespace
