@@ -416,11 +416,37 @@ amr_status amr_cic_faces(const amr_hierarchy* h, int level, int* nfaces, int* nc
  * every component c one shift delta_c is added to all its interface faces, so that
  * -delta_c |faces of c| = (sum of its uncorrected interface averages) + phys[c], i.e. the
  * corrected interface sum plus phys[c] is zero.  faces (device, nfaces doubles; NULL allowed
- * when the level has no interface face): the corrected averages in amr_cic_faces order; delta (device, ncomponents doubles, nullable):
- * the shifts (0 for a component with no interface face).  The per-component sum is a
- * fixed-order tree (one block per component), so results are deterministic. */
+ * when the level has no interface face): the corrected averages in amr_cic_faces order;
+ * delta (device, ncomponents doubles, nullable): the shifts (0 for a component with no
+ * interface face).  Every sum is a fixed-order tree (two passes over chunks of each
+ * component's faces), so results are deterministic. */
 amr_status amr_cic_face_averages(amr_hierarchy* h, int level, const double* const* w, const double* phys,
                                  double* faces, double* delta, void* stream);
+
+/* The level problem of Def. GePUP-E-OneLevel on a connected component of `level` that is a
+ * single box: level l solved alone on that box, with the interface conditions as boundary
+ * data on the box faces that lie on the coarse-fine interface.  Such a component is a
+ * one-level problem whose domain is the box (n0 = hi - lo + 1, h0 = the level's cell size),
+ * so amr_hierarchy_create, amr_operator_create and amr_solve solve it; these two calls give
+ * its geometry and its interface data.  Components of several boxes are rejected with
+ * AMR_ERR_INVALID_ARG (their level problem is not a box problem).
+ *
+ * amr_cic_component_box (host-only): lo[dim], hi[dim] (nullable) the box in the level's
+ * index space; interface_faces[2*dim] (nullable) 1 where face f = 2d+side of the box lies on
+ * the coarse-fine interface, 0 where it lies on the physical boundary. */
+amr_status amr_cic_component_box(const amr_hierarchy* h, int level, int component, int* lo, int* hi,
+                                 int* interface_faces);
+
+/* Face averages <x> (Eq. cell2face along the face normal, over the two interior cells and the
+ * two ghost layers) of the composite field x (device; the level's ghosts filled, CF ghosts at
+ * the wanted time, e.g. by amr_cic_ghosts) on every interface face of a single-box component,
+ * written into bc (device) in the boundary-data layout of the component's one-level box
+ * problem (amr_bc_layout of that hierarchy: faces f = 2d+side in order, each over the box's
+ * cells with dimension d removed, lowest remaining dimension fastest): the Dirichlet data
+ * w = w^I on the interface (Eq. GePUP-localized a).  Slots of faces on the physical boundary
+ * are not written. */
+amr_status amr_cic_interface_bc(amr_hierarchy* h, int level, int component, const double* x, double* bc,
+                                void* stream);
 
 void amr_default_params(amr_solver_params* p);
 const char* amr_last_error(void);

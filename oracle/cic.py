@@ -154,3 +154,50 @@ def interface_face_averages(H, W, l, faces=None):
             lowcell[d] -= 1  # the face is the high face of the cell below it
         out[i] = s * st.face_value(W[d], H.D, d, tuple(lowcell))
     return out
+
+
+def interface_face_values(H, X, l, faces=None):
+    """<x> on the interface faces of level l (``X``: the level-l array of a field with its
+    ghosts filled): Eq. (cell2face) on each face along its normal, no sign."""
+    faces = interface_faces(H, l) if faces is None else faces
+    out = np.empty(len(faces))
+    for i, (c, d, s, _) in enumerate(faces):
+        lowcell = list(c)
+        if s < 0:
+            lowcell[d] -= 1
+        out[i] = st.face_value(X, H.D, d, tuple(lowcell))
+    return out
+
+
+def component_box(H, l, comp):
+    """The level problem of Def. GePUP-E-OneLevel on a component that is one box: (lo, hi,
+    interface flags per face 2d+side: 1 where the box face is interior to the domain, i.e. on
+    the coarse-fine interface).  Raises ValueError for a component of several boxes."""
+    lev = H.levels[l]
+    labels = H.components(l)
+    order = sorted(set(labels))
+    boxes = [b for b in range(len(labels)) if order.index(labels[b]) == comp]
+    if len(boxes) != 1:
+        raise ValueError("component of several boxes")
+    lo, hi = lev.boxes[boxes[0]]
+    flags = []
+    for d in range(H.D):
+        flags += [1 if lo[d] > 0 else 0, 1 if hi[d] < lev.ndom[d] - 1 else 0]
+    return lo, hi, flags
+
+
+def box_interface_bc(H, X, l, comp):
+    """Boundary data of the one-level box problem of a single-box component: for each face
+    f = 2d+side of the box, an array over the box face (remaining dimensions in order) holding
+    the interface face averages <x> (zeros on faces on the physical boundary)."""
+    lo, hi, _ = component_box(H, l, comp)
+    D = H.D
+    n = [hi[e] - lo[e] + 1 for e in range(D)]
+    lev = H.levels[l]
+    data = {2 * d + s: np.zeros(tuple(n[e] for e in range(D) if e != d)) for d in range(D) for s in (0, 1)}
+    faces = [f for f in interface_faces(H, l) if f[3] == comp]
+    vals = interface_face_values(H, X, l, faces)
+    for (c, d, s, _), v in zip(faces, vals):
+        g = [c[e] + lev.origin[e] - lo[e] for e in range(D)]
+        data[2 * d + (1 if s > 0 else 0)][tuple(g[e] for e in range(D) if e != d)] = v
+    return data

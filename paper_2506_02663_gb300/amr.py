@@ -92,6 +92,8 @@ _sigs = {
     "amr_cic_ghosts": [_vp, C.c_int, _P(_vp), C.c_double, C.c_double, _vp, _vp, _vp],
     "amr_cic_faces": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)],
     "amr_cic_face_averages": [_vp, C.c_int, _P(_vp), _vp, _vp, _vp, _vp],
+    "amr_cic_component_box": [_vp, C.c_int, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int)],
+    "amr_cic_interface_bc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp],
     "amr_default_params": [_P(SolverParams)],
     "amr_last_error": [],
     "amr_kernel_launches": [],
@@ -552,3 +554,19 @@ def cic_face_averages(hier, level, w, faces, phys=None, delta=None, stream=None)
         raise ValueError("cic_face_averages needs one field per dimension")
     _check(_lib.amr_cic_face_averages(hier.handle, int(level), _ptr_array(w), _ptr(phys), _ptr(faces), _ptr(delta),
                                       _stream(stream)), "amr_cic_face_averages")
+
+
+def cic_component_box(hier, level, component):
+    """amr_cic_component_box: (lo, hi, interface flags per face 2d+side) of a single-box
+    component of `level`."""
+    D = hier.dim
+    lo, hi, fl = (C.c_int * D)(), (C.c_int * D)(), (C.c_int * (2 * D))()
+    _check(_lib.amr_cic_component_box(hier.handle, int(level), int(component), lo, hi, fl), "amr_cic_component_box")
+    return tuple(lo), tuple(hi), list(fl)
+
+
+def cic_interface_bc(hier, level, component, x, bc, stream=None):
+    """amr_cic_interface_bc: interface face averages of ``x`` into the boundary data ``bc`` of
+    the component's one-level box problem."""
+    _check(_lib.amr_cic_interface_bc(hier.handle, int(level), int(component), _ptr(x), _ptr(bc), _stream(stream)),
+           "amr_cic_interface_bc")

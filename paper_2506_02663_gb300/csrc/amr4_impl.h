@@ -152,6 +152,7 @@ struct DeviceLists {
   long long cic_base = 0;
   double* cic_y = nullptr;  // 2 x cic_span doubles
   long long cic_span = 0;
+  long long* cic_slot = nullptr;  // per face, see LevelHost::cic_slot
   RefluxEntry* reflux = nullptr;
   long long nreflux = 0;
   XferBlock* xfer = nullptr;  // blocks between this level (coarse) and level+1
@@ -180,6 +181,11 @@ struct LevelHost {
   std::vector<int> cic_comp;
   std::vector<CicChunk> cic_chunks;
   std::vector<int> cic_ccstart;
+  // components that are a single box: that box's index (-1 for a component of several
+  // boxes), and per face its slot in the boundary-data layout of the one-level problem whose
+  // domain is the box (-1 for faces of multi-box components)
+  std::vector<int> cic_comp_box;
+  std::vector<long long> cic_slot;
   std::vector<RefluxEntry> reflux;  // this level's coarse cells bordering level+1
   std::vector<XferBlock> xfer;      // this level (coarse) <-> level+1 (fine)
   DeviceLists dev;

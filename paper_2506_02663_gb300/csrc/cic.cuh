@@ -289,4 +289,17 @@ k_cic_faces_shift(const CicChunk* __restrict__ chunks, const int* __restrict__ c
   for (int i = ch.begin + (int)threadIdx.x; i < ch.end; i += CIC_FACE_THREADS) out[i] += d;
 }
 
+// Face averages <x> (Eq. cell2face along the normal, no sign) on the interface faces
+// [begin, end) of one single-box component, into the slots of its box problem's boundary
+// data: the Dirichlet data w = w^I of the component's level problem.
+__global__ void k_cic_face_bc(const CicFace* __restrict__ faces, const long long* __restrict__ slot, int begin,
+                              int end, const double* __restrict__ x, double* __restrict__ out) {
+  pdl_wait();
+  const int i = begin + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= end) return;
+  const CicFace f = faces[i];
+  out[slot[i]] =
+      (7.0 * (x[f.ghost - f.step] + x[f.ghost]) - (x[f.ghost - 2 * f.step] + x[f.ghost + f.step])) * (1.0 / 12.0);
+}
+
 }  // namespace amr4

@@ -244,6 +244,41 @@ static void group_cic_faces(LevelHost& L, const std::vector<int>& im_component, 
   L.cic_cstart.assign(ncomp + 1, 0);
   for (size_t i = 0; i < nf; ++i) ++L.cic_cstart[L.cic_comp[i] + 1];
   for (int c = 0; c < ncomp; ++c) L.cic_cstart[c + 1] += L.cic_cstart[c];
+  // single-box components: per face the slot of its box problem's boundary data (faces f =
+  // 2d + side in order, each over the box's cells with dimension d removed, lowest remaining
+  // dimension fastest)
+  std::vector<int> nbox(ncomp, 0), onebox(ncomp, -1);
+  for (size_t k = 0; k < nb; ++k) {
+    const int c = comp_of_label[label[k]];
+    ++nbox[c];
+    onebox[c] = (int)k;
+  }
+  L.cic_comp_box.assign(ncomp, -1);
+  for (int c = 0; c < ncomp; ++c)
+    if (nbox[c] == 1) L.cic_comp_box[c] = onebox[c];
+  L.cic_slot.assign(nf, -1);
+  for (size_t i = 0; i < nf; ++i) {
+    const int b = L.cic_comp_box[L.cic_comp[i]];
+    if (b < 0) continue;
+    const Box& B = L.boxes[b];
+    int n[3] = {1, 1, 1};
+    for (int e = 0; e < D; ++e) n[e] = B.hi[e] - B.lo[e] + 1;
+    const int d = L.cicf[i].dir, f = 2 * d + (L.cicf[i].side > 0 ? 1 : 0);
+    long long off = 0;
+    for (int f2 = 0; f2 < f; ++f2) {
+      long long cnt = 1;
+      for (int e = 0; e < D; ++e)
+        if (e != f2 / 2) cnt *= n[e];
+      off += cnt;
+    }
+    long long idx = 0, stride = 1;
+    for (int e = 0; e < D; ++e) {
+      if (e == d) continue;
+      idx += (long long)(L.cic_cell[i * D + e] - B.lo[e]) * stride;
+      stride *= n[e];
+    }
+    L.cic_slot[i] = off + idx;
+  }
   // chunks of at most CIC_CHUNK faces, at least one (possibly empty) per component
   constexpr int CIC_CHUNK = 2048;
   L.cic_chunks.clear();
@@ -772,6 +807,7 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
       L.dev.ncicf = (int)L.cicf.size();
       L.dev.cic_cstart = upload(L.cic_cstart);
       L.dev.ncic_comp = L.cic_cstart.empty() ? 0 : (int)L.cic_cstart.size() - 1;
+      L.dev.cic_slot = upload(L.cic_slot);
       L.dev.cic_chunks = upload(L.cic_chunks);
       L.dev.cic_ccstart = upload(L.cic_ccstart);
       L.dev.ncic_chunks = (int)L.cic_chunks.size();
@@ -820,6 +856,7 @@ void free_hierarchy(amr_hierarchy* h) {
     cudaFree(L.dev.cic_ccstart);
     cudaFree(L.dev.cic_psum);
     cudaFree(L.dev.cic_band);
+    cudaFree(L.dev.cic_slot);
     cudaFree(L.dev.cic_y);
     cudaFree(L.dev.reflux);
     cudaFree(L.dev.xfer);

@@ -3788,6 +3788,45 @@ amr_status amr_cic_faces(const amr_hierarchy* h, int level, int* nfaces, int* nc
   return AMR_OK;
 }
 
+amr_status amr_cic_component_box(const amr_hierarchy* h, int level, int component, int* lo, int* hi,
+                                 int* interface_faces) {
+  TRY(check_cic_level(h, level));
+  const LevelHost& L = h->lev[level];
+  if (component < 0 || component >= (int)L.cic_comp_box.size()) {
+    set_error("amr_cic_component_box: component out of range");
+    return AMR_ERR_INVALID_ARG;
+  }
+  const int b = L.cic_comp_box[component];
+  if (b < 0) {
+    set_error("amr_cic_component_box: component " + std::to_string(component) + " of level " + std::to_string(level) +
+              " has several boxes (its level problem is not a box problem)");
+    return AMR_ERR_INVALID_ARG;
+  }
+  const Box& B = L.boxes[b];
+  for (int d = 0; d < h->D; ++d) {
+    if (lo) lo[d] = B.lo[d];
+    if (hi) hi[d] = B.hi[d];
+    if (interface_faces) {
+      interface_faces[2 * d] = B.lo[d] > 0 ? 1 : 0;
+      interface_faces[2 * d + 1] = B.hi[d] < L.ndom[d] - 1 ? 1 : 0;
+    }
+  }
+  return AMR_OK;
+}
+
+amr_status amr_cic_interface_bc(amr_hierarchy* h, int level, int component, const double* x, double* bc,
+                                void* stream) {
+  TRY(amr_cic_component_box(h, level, component, nullptr, nullptr, nullptr));
+  if (!x || !bc) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(h));
+  const LevelHost& L = h->lev[level];
+  const int b = L.cic_cstart[component], e = L.cic_cstart[component + 1];
+  if (e == b) return AMR_OK;
+  const int nt = 256;
+  launch(k_cic_face_bc, (unsigned)((e - b + nt - 1) / nt), nt, 0, S(stream), L.dev.cicf, L.dev.cic_slot, b, e, x, bc);
+  return launch_check();
+}
+
 amr_status amr_cic_face_averages(amr_hierarchy* h, int level, const double* const* w, const double* phys,
                                  double* faces, double* delta, void* stream) {
   TRY(check_cic_level(h, level));

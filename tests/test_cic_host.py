@@ -63,3 +63,27 @@ def test_interface_faces_reject_level_zero(amr):
         amr.cic_faces(h, 0)
     with pytest.raises(amr.AmrError):
         amr.cic_faces(h, 2)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_component_boxes_match_oracle(amr, name):
+    """amr_cic_component_box gives the oracle's box and interface flags for every single-box
+    component and rejects components of several boxes."""
+    from oracle import cic
+    from oracle.hierarchy import Hierarchy
+    dim, n0, boxes = CASES[name]
+    H = Hierarchy(dim, n0, boxes, bc=[0] * (2 * dim))
+    h = amr.Hierarchy(dim, n0, boxes)
+    for l in range(1, len(boxes)):
+        nc = amr.cic_faces(h, l)["ncomponents"]
+        for c in range(nc):
+            try:
+                want = cic.component_box(H, l, c)
+            except ValueError:
+                with pytest.raises(amr.AmrError):
+                    amr.cic_component_box(h, l, c)
+                continue
+            lo, hi, fl = amr.cic_component_box(h, l, c)
+            assert (lo, hi, fl) == (tuple(want[0]), tuple(want[1]), want[2])
+        with pytest.raises(amr.AmrError):
+            amr.cic_component_box(h, l, nc)

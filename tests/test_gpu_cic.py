@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 from oracle import cic, composite as cp, solve as so  # noqa: E402
 from oracle.hierarchy import Hierarchy as OH  # noqa: E402
 
-from _gpu_helpers import to_packed  # noqa: E402
+from _gpu_helpers import from_packed, to_packed  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,7 @@ HIERS = {
     "boundary_box": (2, (16, 16), [[((0, 0), (15, 15))], [((0, 12), (11, 31))]]),
     "three_d_two_components": (3, (12, 12, 12), [[((0, 0, 0), (11, 11, 11))],
                                                  [((2, 2, 2), (7, 7, 7)), ((14, 14, 12), (21, 21, 19))]]),
+    "three_d_box": (3, (16, 16, 16), [[((0, 0, 0), (15, 15, 15))], [((8, 8, 8), (23, 23, 23))]]),
 }
 
 
@@ -273,3 +274,53 @@ def test_full_size_3d_sampled():
         raw = s * st.face_value(P[d], 3, d, tuple(cell))
         assert abs(gf[i] - (raw + dl)) <= 1e-13 * scale
     assert abs(np.sum(gf) + 0.37) <= 1e-12 * scale * nf
+
+
+@pytest.mark.parametrize("name,comp", [("two_components", 1), ("three_d_two_components", 0),
+                                       ("three_d_two_components", 1), ("three_d_box", 0)])
+def test_level_problem_of_a_single_box_component(name, comp):
+    """Def. GePUP-E-OneLevel on a single-box component: CF ghosts at t* from four coarse times
+    (amr_cic_ghosts), their interface face averages as the box problem's Dirichlet data
+    (amr_cic_interface_bc, against the oracle's), then the Helmholtz problem on the box solved
+    by amr_solve against the oracle's direct solve with the oracle's data."""
+    H, gh = _hier(name)
+    amr = _amr()
+    D = H.D
+    rng = np.random.default_rng(41)
+    k, eta = 0.2, 0.05
+    X = _rand(H, rng)
+    Xt = [_rand(H, rng) for _ in range(4)]
+    op = amr.Operator(gh, 0.0, 1.0, [0] * (2 * D))
+    xd = _dev(to_packed(gh, H, X))
+    xtd = [_dev(to_packed(gh, H, F)) for F in Xt]
+    op.fill_ghosts(xd)
+    amr.cic_ghosts(gh, 1, xtd, k, eta, xd, None)
+    lo, hi, flags = amr.cic_component_box(gh, 1, comp)
+    olo, ohi, oflags = cic.component_box(H, 1, comp)
+    assert (lo, hi, flags) == (tuple(olo), tuple(ohi), oflags)
+    n = tuple(hi[e] - lo[e] + 1 for e in range(D))
+    h = H.levels[1].h
+    boxes_b = [[((0,) * D, tuple(v - 1 for v in n))]]
+    gb = amr.Hierarchy(D, n, boxes_b, h0=h)
+    Hb = OH(D, n, boxes_b, bc=[0] * (2 * D), hi=tuple(v * h for v in n))
+    bc = torch.zeros(gb.bc_offsets[-1], dtype=torch.float64, device="cuda")
+    amr.cic_interface_bc(gh, 1, comp, xd, bc)
+    torch.cuda.synchronize()
+    A = [a.copy() for a in X]
+    cp.average_down_all(H, A)
+    cells, v, _ = cic.interface_ghost_values(H, [F[0] for F in Xt], 1, k, eta)
+    A[1][tuple(cells.T)] = v
+    data = cic.box_interface_bc(H, A[1], 1, comp)
+    scale = float(np.max(np.abs(A[1][np.isfinite(A[1])])))  # cells the oracle leaves undefined hold NaN
+    assert np.max(np.abs(bc.cpu().numpy() - gb.pack_bc([data]))) <= 1e-13 * scale
+    alpha, beta = 1.0, -0.01
+    Fb = so.Unknowns(Hb).scatter(rng.standard_normal(so.Unknowns(Hb).n))
+    ref, _, _ = so.solve_direct(Hb, Fb, alpha, beta, bc_data=[data])
+    opb = amr.Operator(gb, alpha, beta, [0] * (2 * D))
+    phi = torch.zeros(gb.nelems, dtype=torch.float64, device="cuda")
+    st = opb.solve(phi, _dev(to_packed(gb, Hb, Fb)), bc=bc,
+                   params=amr.default_params(rtol=1e-12, max_vcycles=60, precision=amr.FP64))
+    assert st["status"] == 0
+    got = from_packed(gb, Hb, phi.cpu().numpy())
+    lev = Hb.levels[0]
+    assert np.max(np.abs(got[0][lev.valid] - ref[0][lev.valid])) <= 1e-10 * np.max(np.abs(ref[0][lev.valid]))

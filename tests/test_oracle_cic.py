@@ -167,3 +167,42 @@ def test_interface_face_averages_exact_on_cubics_and_divergence_theorem():
     lo, hi = 8 * h, 24 * h
     flux = (f(hi) - f(lo)) * (hi - lo) + (g(hi) - g(lo)) * (hi - lo)
     assert abs(np.sum(vals) * h - flux) <= 1e-12
+
+
+def test_box_interface_data_exact_on_cubics():
+    """The boundary data of a single-box component's level problem: cell averages of a cubic
+    p(x, y) give, on every interface face of the box, the exact face average of p at the
+    slot of that face; the multi-box component is rejected."""
+    from oracle.hierarchy import Hierarchy
+    H = Hierarchy(2, (32, 32), [[((0, 0), (31, 31))], [((8, 8), (19, 19)), ((40, 36), (55, 51)),
+                                                       ((20, 8), (27, 15))]], bc=[0] * 4)
+    lev = H.levels[1]
+    h = lev.h
+    with pytest.raises(ValueError):
+        cic.component_box(H, 1, 0)
+    lo, hi, flags = cic.component_box(H, 1, 1)
+    assert (lo, hi, flags) == ((40, 36), (55, 51), [1, 1, 1, 1])
+
+    def avg(F, a):  # cell average over [a, a + h] from the antiderivative F
+        return (F(a + h) - F(a)) / h
+
+    x = (np.arange(lev.shape[0]) + lev.origin[0]) * h
+    y = (np.arange(lev.shape[1]) + lev.origin[1]) * h
+    ax3 = avg(lambda t: t ** 4 / 4, x)
+    ax1 = avg(lambda t: t ** 2 / 2, x)
+    ay2 = avg(lambda t: t ** 3 / 3, y)
+    ay1 = avg(lambda t: t ** 2 / 2, y)
+    X = ax3[:, None] + 2.0 * ax1[:, None] * ay2[None, :] - ay1[None, :]
+    data = cic.box_interface_bc(H, X, 1, 1)
+    n = (16, 16)
+    for d in range(2):
+        for s in (0, 1):
+            arr = data[2 * d + s]
+            xf = (lo[d] + (n[d] if s else 0)) * h  # the face's coordinate
+            t = np.arange(n[1 - d]) + lo[1 - d]
+            tc = t * h
+            if d == 0:  # face x = xf, averaged over y
+                want = xf ** 3 + 2.0 * xf * avg(lambda u: u ** 3 / 3, tc) - avg(lambda u: u ** 2 / 2, tc)
+            else:  # face y = xf, averaged over x
+                want = avg(lambda u: u ** 4 / 4, tc) + 2.0 * avg(lambda u: u ** 2 / 2, tc) * xf ** 2 - xf
+            assert np.allclose(arr, want, rtol=0, atol=1e-12)
