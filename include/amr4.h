@@ -448,6 +448,38 @@ amr_status amr_cic_component_box(const amr_hierarchy* h, int level, int componen
 amr_status amr_cic_interface_bc(amr_hierarchy* h, int level, int component, const double* x, double* bc,
                                 void* stream);
 
+/* ---- regridding ----------------------------------------------------------------------- */
+/* New level boxes from tagged cells (Sec. 5.4, RDM-2 and RDM-3), host-only.  Level
+ * nlevels-1 is built from the tags of level nlevels-2 by the clustering algorithm of Berger
+ * and Rigoutsos; then for l = nlevels-3 .. 0 the tags of level l are united with the boxes of
+ * the new level l+2 coarsened twice and grown by ceil(3 / ratio) cells (clipped to the
+ * domain) and clustered into the new level l+1 -- the growth makes every new level contain
+ * the three-cell margin that AMRCFI windows need around the next finer one (the paper grows
+ * by one cell with ratio 4, which is the same margin), and the clustered boxes are refined
+ * by `ratio`.  Clustering of the tagged cells T of a region (the recursion partitions the
+ * level's domain into disjoint regions at least min_width cells wide): the bounding box of T,
+ * widened inside the region to min_width cells; accepted when |T| >= efficiency x its cells;
+ * otherwise cut in two (both parts at least min_width wide) at a hole of a signature (tags
+ * per slice) closest to the middle of its dimension, else at the inflection point (second
+ * differences of the signature of strictly opposite signs) with the largest jump, else at
+ * the middle of the longest dimension that can be cut; ties go to the cut closest to its
+ * dimension's middle, then the longer dimension, the lower dimension, the lower position;
+ * a box that cannot be cut is accepted.  The result passes amr_hierarchy_create's checks.
+ *   ntags[l], tags[l] (l = 0 .. nlevels-2; host): ntags[l] cells of level l, dim ints each
+ *     (global indices in level l's index space; repeats allowed).
+ *   new_nlevels: levels of the new hierarchy (a level with no box ends it);
+ *   nboxes (nlevels ints, nullable): boxes per new level (nboxes[0] = 1, 0 past the end);
+ *   boxes (nullable): the amr_hierarchy_desc box list (the level-0 domain box first, then
+ *     every new level's boxes: lo[0..dim-1], hi[0..dim-1]), at most max_boxes boxes;
+ *     AMR_ERR_INVALID_ARG when more are needed (call with boxes = NULL for the counts). */
+typedef struct {
+  double efficiency; /* 0 < efficiency <= 1 */
+  int min_width;     /* smallest box width, in cells of the clustered level; >= ceil(4 / ratio) */
+} amr_regrid_params;
+
+amr_status amr_regrid(int dim, int ratio, const int* n0, int nlevels, const int* ntags, const int* const* tags,
+                      const amr_regrid_params* p, int* new_nlevels, int* nboxes, int* boxes, int max_boxes);
+
 void amr_default_params(amr_solver_params* p);
 const char* amr_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far (a host-side

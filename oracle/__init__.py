@@ -29,6 +29,9 @@ Modules
                (Sec. 6.4), mean-zero, transposes (adjoint).
 ``mg``         Sec. 6.5 geometric multigrid (V-cycle with weighted Jacobi, omega = 2/3).
 ``cic``        Sec. 6.3-6.4 interface conditions of the subcycled solves: the time
-               interpolation I^(4) (Eq. timeInterp) and the per-component correction of the
-               interface face averages (Eq. correctingFaceAvg).
+               interpolation I^(4) (Eq. timeInterp), the interface faces and components, the
+               per-component correction of the interface face averages (Eq.
+               correctingFaceAvg), and the boundary data of single-box level problems.
+``regrid``     Sec. 5.4 RDM-2/3: Berger-Rigoutsos clustering of tagged cells into the boxes
+               of a new hierarchy, finest level first.
 """

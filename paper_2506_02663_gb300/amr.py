@@ -54,6 +54,10 @@ class SolverParams(C.Structure):
                 ("temporal_blocking", C.c_int), ("cycles_per_refinement", C.c_int)]
 
 
+class RegridParams(C.Structure):
+    _fields_ = [("efficiency", C.c_double), ("min_width", C.c_int)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("vcycles", C.c_int), ("rhs_norm", C.c_double), ("final_res", C.c_double),
                 ("removed_mean", C.c_double), ("res_history", C.c_double * 64)]
@@ -93,6 +97,8 @@ _sigs = {
     "amr_cic_faces": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)],
     "amr_cic_face_averages": [_vp, C.c_int, _P(_vp), _vp, _vp, _vp, _vp],
     "amr_cic_component_box": [_vp, C.c_int, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int)],
+    "amr_regrid": [C.c_int, C.c_int, _P(C.c_int), C.c_int, _P(C.c_int), _P(_P(C.c_int)), _P(RegridParams),
+                   _P(C.c_int), _P(C.c_int), _P(C.c_int), C.c_int],
     "amr_cic_interface_bc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp],
     "amr_default_params": [_P(SolverParams)],
     "amr_last_error": [],
@@ -570,3 +576,31 @@ def cic_interface_bc(hier, level, component, x, bc, stream=None):
     the component's one-level box problem."""
     _check(_lib.amr_cic_interface_bc(hier.handle, int(level), int(component), _ptr(x), _ptr(bc), _stream(stream)),
            "amr_cic_interface_bc")
+
+
+def regrid(dim, n0, nlevels, tags, efficiency, min_width, ratio=2):
+    """amr_regrid: new boxes per level ([[(lo, hi)], ...], level 0 the domain) from ``tags``
+    (per level 0..nlevels-2: an (n, dim) integer array of tagged cells)."""
+    n0a = (C.c_int * 3)(*(list(n0) + [1] * (3 - dim)))
+    arrs = [np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(-1, dim)) for t in tags]
+    if len(arrs) != nlevels - 1:
+        raise ValueError("regrid needs the tags of levels 0 .. nlevels-2")
+    nt = (C.c_int * max(1, len(arrs)))(*[len(a) for a in arrs])
+    ptrs = (_P(C.c_int) * max(1, len(arrs)))(*[a.ctypes.data_as(_P(C.c_int)) for a in arrs])
+    p = RegridParams(float(efficiency), int(min_width))
+    nl = C.c_int()
+    nb = (C.c_int * nlevels)()
+    _check(_lib.amr_regrid(dim, ratio, n0a, nlevels, nt, ptrs, C.byref(p), C.byref(nl), nb, None, 0), "amr_regrid")
+    total = sum(nb[l] for l in range(nl.value))
+    out = (C.c_int * (2 * dim * total))()
+    _check(_lib.amr_regrid(dim, ratio, n0a, nlevels, nt, ptrs, C.byref(p), C.byref(nl), nb, out, total),
+           "amr_regrid")
+    flat = list(out)
+    levels, q = [], 0
+    for l in range(nl.value):
+        bl = []
+        for _ in range(nb[l]):
+            bl.append((tuple(flat[q:q + dim]), tuple(flat[q + dim:q + 2 * dim])))
+            q += 2 * dim
+        levels.append(bl)
+    return levels

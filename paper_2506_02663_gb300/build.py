@@ -13,7 +13,7 @@ LIB = os.path.join(LIB_DIR, "libamr4.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["solver.cu", "hierarchy.cpp"]
+SOURCES = ["solver.cu", "hierarchy.cpp", "regrid.cpp"]
 
 
 def _nvcc():
