@@ -472,6 +472,29 @@ amr_status amr_cic_interface_bc(amr_hierarchy* h, int level, int component, cons
  *   boxes (nullable): the amr_hierarchy_desc box list (the level-0 domain box first, then
  *     every new level's boxes: lo[0..dim-1], hi[0..dim-1]), at most max_boxes boxes;
  *     AMR_ERR_INVALID_ARG when more are needed (call with boxes = NULL for the counts). */
+/* Data migration after regridding (Sec. 5.4, last paragraph): the composite field old_x of
+ * old_h onto new_x of new_h (device fields; same dimension, ratio and level-0 domain; old_x
+ * and new_x distinct).  Levels in order: every cell of a box of new level l that lies in a
+ * box of old level l takes the old value of that cell (level 0 is copied whole); every other
+ * cell takes the AMRCFI value (Sec. 5.2) from new level l-1, which is complete by then, so
+ * the interpolation source is old data throughout (copied, or itself interpolated from old
+ * data).  Ghost cells of new_x are not written.  The plan (copy blocks, AMRCFI windows) is
+ * built on the host at each call and its device copy freed before returning; the call
+ * synchronises `stream`.  AMR_ERR_NESTING if an AMRCFI window leaves new level l-1. */
+amr_status amr_migrate(amr_hierarchy* old_h, const double* old_x, amr_hierarchy* new_h, double* new_x,
+                       void* stream);
+
+/* The migration plan of one new level (host-only, for inspection and tests; two-call
+ * pattern, every output nullable): nblocks copy blocks as (new patch, old patch, lo[dim],
+ * hi[dim]) in blocks (2 + 2*dim ints each, level index space); ncells interpolated cells:
+ * cells (dim ints each, global index), starts (dim ints each, the window's first coarse
+ * cell), dst (the cell's element offset in new_x), src (the element offset in new_x of the
+ * window's first cell when the window lies in one coarse patch, else -1-k: the window's
+ * 5^dim offsets are side[k*5^dim ...]); nside / side: the side tables. */
+amr_status amr_migrate_plan(const amr_hierarchy* old_h, const amr_hierarchy* new_h, int level, int* nblocks,
+                            int* blocks, long long* ncells, int* cells, int* starts, long long* dst, long long* src,
+                            long long* nside, long long* side);
+
 typedef struct {
   double efficiency; /* 0 < efficiency <= 1 */
   int min_width;     /* smallest box width, in cells of the clustered level; >= ceil(4 / ratio) */

@@ -124,3 +124,30 @@ def regrid(dim, n0, nlevels, tags, efficiency, min_width, ratio=2):
             break
         out.append(new[l])
     return out
+
+
+def migrate(H_old, F_old, H_new):
+    """Data migration (the paragraph after RDM-4): the new composite field (level arrays of
+    H_new).  Levels in order; a cell of a new box inside a box of the old same level takes the
+    old value; any other cell the AMRCFI value (Sec. 5.2) from the new level below, which is
+    complete by then (reading: the interpolation source is the old data as carried onto the
+    new coarser level).  Cells outside the new boxes stay NaN."""
+    from . import composite as cp
+    from .cfi import cfi_values
+    F_new = cp.new_field(H_new, (), np.nan)
+    for l, lev in enumerate(H_new.levels):
+        cells = np.argwhere(lev.covered)
+        g = cells + np.asarray(lev.origin)
+        in_old = np.zeros(len(g), bool)
+        if l < len(H_old.levels):
+            old = H_old.levels[l]
+            a = g - np.asarray(old.origin)
+            ok = np.all((a >= 0) & (a < np.asarray(old.shape)), axis=1)
+            in_old[ok] = old.covered[tuple(a[ok].T)]
+            F_new[l][tuple(cells[in_old].T)] = F_old[l][tuple(a[in_old].T)]
+        rest = ~in_old
+        if rest.any():
+            crs = H_new.levels[l - 1]
+            vals, _ = cfi_values(F_new[l - 1], crs.origin, crs.ndom, g[rest], H_new.ratio, H_new.D)
+            F_new[l][tuple(cells[rest].T)] = vals
+    return F_new

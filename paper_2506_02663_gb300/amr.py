@@ -97,6 +97,9 @@ _sigs = {
     "amr_cic_faces": [_vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)],
     "amr_cic_face_averages": [_vp, C.c_int, _P(_vp), _vp, _vp, _vp, _vp],
     "amr_cic_component_box": [_vp, C.c_int, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int)],
+    "amr_migrate": [_vp, _vp, _vp, _vp, _vp],
+    "amr_migrate_plan": [_vp, _vp, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_longlong), _P(C.c_int), _P(C.c_int),
+                         _P(C.c_longlong), _P(C.c_longlong), _P(C.c_longlong), _P(C.c_longlong)],
     "amr_regrid": [C.c_int, C.c_int, _P(C.c_int), C.c_int, _P(C.c_int), _P(_P(C.c_int)), _P(RegridParams),
                    _P(C.c_int), _P(C.c_int), _P(C.c_int), C.c_int],
     "amr_cic_interface_bc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp],
@@ -604,3 +607,31 @@ def regrid(dim, n0, nlevels, tags, efficiency, min_width, ratio=2):
             q += 2 * dim
         levels.append(bl)
     return levels
+
+
+def migrate(old_hier, old_x, new_hier, new_x, stream=None):
+    """amr_migrate: old_x (composite field of old_hier) onto new_x (of new_hier)."""
+    _check(_lib.amr_migrate(old_hier.handle, _ptr(old_x), new_hier.handle, _ptr(new_x), _stream(stream)),
+           "amr_migrate")
+
+
+def migrate_plan(old_hier, new_hier, level):
+    """amr_migrate_plan of one new level as numpy arrays."""
+    D = new_hier.dim
+    nb, nc, ns = C.c_int(), C.c_longlong(), C.c_longlong()
+    _check(_lib.amr_migrate_plan(old_hier.handle, new_hier.handle, int(level), C.byref(nb), None, C.byref(nc), None,
+                                 None, None, None, C.byref(ns), None), "amr_migrate_plan")
+    blocks = (C.c_int * max(1, nb.value * (2 + 2 * D)))()
+    cells = (C.c_int * max(1, nc.value * D))()
+    starts = (C.c_int * max(1, nc.value * D))()
+    dst = (C.c_longlong * max(1, nc.value))()
+    src = (C.c_longlong * max(1, nc.value))()
+    side = (C.c_longlong * max(1, ns.value))()
+    _check(_lib.amr_migrate_plan(old_hier.handle, new_hier.handle, int(level), None, blocks, None, cells, starts, dst,
+                                 src, None, side), "amr_migrate_plan")
+    n, m = nb.value, nc.value
+    return {"blocks": np.ctypeslib.as_array(blocks)[:n * (2 + 2 * D)].reshape(n, 2 + 2 * D).copy(),
+            "cells": np.ctypeslib.as_array(cells)[:m * D].reshape(m, D).copy(),
+            "starts": np.ctypeslib.as_array(starts)[:m * D].reshape(m, D).copy(),
+            "dst": np.ctypeslib.as_array(dst)[:m].copy(), "src": np.ctypeslib.as_array(src)[:m].copy(),
+            "side": np.ctypeslib.as_array(side)[:ns.value].copy()}

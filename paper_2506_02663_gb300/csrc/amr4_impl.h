@@ -249,6 +249,25 @@ amr_status upload_hierarchy(amr_hierarchy* h, std::string& err);
 // repeated with element offsets c * stride (stride = h's composite length rounded up to 64
 // elements), patch indices shifted per replica; uploaded to the device.
 amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, std::string& err);
+// Data migration after regridding: per level of the new hierarchy, the blocks copied from the
+// old hierarchy's same level (intersections of a new and an old box, level index space) and
+// the AMRCFI entries of the other new cells (windows in the new level l-1; side tables for
+// windows over several patches).
+struct MigrateBlock {
+  int npatch;  // patch of the new level
+  int opatch;  // patch of the old level
+  int lo[3];
+  int hi[3];
+};
+struct MigrateLevel {
+  std::vector<MigrateBlock> blocks;
+  std::vector<CfiEntry> cfi;
+  std::vector<long long> side;
+  std::vector<int> cells;   // dim ints per AMRCFI entry: the new cell (global index)
+  std::vector<int> starts;  // dim ints per AMRCFI entry: the window's first coarse cell
+};
+amr_status migrate_plan(const amr_hierarchy* oh, const amr_hierarchy* nh, std::vector<MigrateLevel>& plan,
+                        std::string& err);
 void set_error(const std::string& msg);
 const char* get_error();
 void cfi_weights_exact(int r, std::vector<double>& w);  // [pos][sub][a], 5 x r x 5

@@ -778,6 +778,107 @@ amr_status stack_hierarchy(const amr_hierarchy* h, int k, amr_hierarchy** out, s
 
 // Device copies of the work lists and masks, made on the first call that needs the GPU
 // (hierarchy creation and the index maps work without one).
+// Data migration plan (Sec. 5.4, last paragraph): the cells of new level l inside a box of
+// old level l are copied (one block per intersecting pair of boxes); every other cell gets
+// the AMRCFI value from new level l-1 (filled before level l), with the window of Sec. 5.2
+// (centred on the parent, slid inward at the physical boundary).  Level 0 is one block.
+amr_status migrate_plan(const amr_hierarchy* oh, const amr_hierarchy* nh, std::vector<MigrateLevel>& plan,
+                        std::string& err) {
+  const int D = nh->D, r = nh->r;
+  if (oh->D != D || oh->r != r || oh->ncomp != 1 || nh->ncomp != 1) {
+    err = "migration: the hierarchies need the same dimension and ratio (and no stacking)";
+    return AMR_ERR_INVALID_ARG;
+  }
+  for (int e = 0; e < D; ++e)
+    if (oh->n0[e] != nh->n0[e]) {
+      err = "migration: the hierarchies need the same level-0 domain";
+      return AMR_ERR_INVALID_ARG;
+    }
+  plan.assign(nh->L, {});
+  for (int l = 0; l < nh->L; ++l) {
+    const LevelHost& N = nh->lev[l];
+    MigrateLevel& M = plan[l];
+    const bool has_old = l < oh->L;
+    LevelMap omap;
+    if (has_old) omap.build(oh->lev[l].boxes, D);
+    for (size_t k = 0; k < N.boxes.size(); ++k) {
+      const Box& nb = N.boxes[k];
+      if (has_old)
+        for (size_t q = 0; q < oh->lev[l].boxes.size(); ++q) {
+          const Box& ob = oh->lev[l].boxes[q];
+          MigrateBlock blk{};
+          blk.npatch = (int)k;
+          blk.opatch = (int)q;
+          bool ok = true;
+          for (int e = 0; e < 3; ++e) { blk.lo[e] = 0; blk.hi[e] = 0; }
+          for (int e = 0; e < D; ++e) {
+            blk.lo[e] = std::max(nb.lo[e], ob.lo[e]);
+            blk.hi[e] = std::min(nb.hi[e], ob.hi[e]);
+            ok = ok && blk.lo[e] <= blk.hi[e];
+          }
+          if (ok) M.blocks.push_back(blk);
+        }
+      if (l == 0) continue;  // level 0 is the domain in both hierarchies
+      const LevelHost& C = nh->lev[l - 1];
+      LevelMap cmap;
+      cmap.build(C.boxes, D);
+      const PatchDesc& p = N.patches[k];
+      int g[3] = {0, 0, 0};
+      for (g[2] = (D == 3 ? nb.lo[2] : 0); g[2] <= (D == 3 ? nb.hi[2] : 0); ++g[2])
+        for (g[1] = nb.lo[1]; g[1] <= nb.hi[1]; ++g[1])
+          for (g[0] = nb.lo[0]; g[0] <= nb.hi[0]; ++g[0]) {
+            if (has_old && omap.at(g) >= 0) continue;
+            CfiEntry ce{};
+            ce.dst = cell_off(p, D, g[0] - p.lo[0], g[1] - p.lo[1], D == 3 ? g[2] - p.lo[2] : 0);
+            ce.fpatch = (int)k;
+            int start[3] = {0, 0, 0};
+            for (int e = 0; e < 3; ++e) { ce.pos[e] = 0; ce.sub[e] = 0; }
+            for (int e = 0; e < D; ++e) {
+              const int par = g[e] / r;  // cells of a box are inside the domain: g >= 0
+              const int s0 = std::min(std::max(par - 2, 0), C.ndom[e] - CFI_W);
+              start[e] = s0;
+              ce.pos[e] = (signed char)(par - s0);
+              ce.sub[e] = (signed char)(g[e] - r * par);
+            }
+            const int cp0 = cmap.at(start);
+            bool single = cp0 >= 0;
+            if (single) {
+              const PatchDesc& cpd = C.patches[cp0];
+              for (int e = 0; e < D; ++e)
+                single = single && start[e] >= cpd.lo[e] && start[e] + CFI_W - 1 <= cpd.lo[e] + cpd.n[e] - 1;
+            }
+            if (single) {
+              const PatchDesc& cpd = C.patches[cp0];
+              ce.cpatch = cp0;
+              ce.src = cell_off(cpd, D, start[0] - cpd.lo[0], start[1] - cpd.lo[1], D == 3 ? start[2] - cpd.lo[2] : 0);
+            } else {
+              ce.cpatch = -1;
+              ce.src = -1 - (long long)(M.side.size() / (D == 3 ? 125 : 25));
+              for (int wz = 0; wz < (D == 3 ? CFI_W : 1); ++wz)
+                for (int wy = 0; wy < CFI_W; ++wy)
+                  for (int wx = 0; wx < CFI_W; ++wx) {
+                    int c[3] = {start[0] + wx, start[1] + wy, D == 3 ? start[2] + wz : 0};
+                    const int q2 = cmap.at(c);
+                    if (q2 < 0) {
+                      err = "migration: an AMRCFI window of new level " + std::to_string(l) + " leaves new level " +
+                            std::to_string(l - 1) + " (the new hierarchy is not properly nested)";
+                      return AMR_ERR_NESTING;
+                    }
+                    const PatchDesc& cpd = C.patches[q2];
+                    M.side.push_back(cell_off(cpd, D, c[0] - cpd.lo[0], c[1] - cpd.lo[1], D == 3 ? c[2] - cpd.lo[2] : 0));
+                  }
+            }
+            M.cfi.push_back(ce);
+            for (int e = 0; e < D; ++e) {
+              M.cells.push_back(g[e]);
+              M.starts.push_back(start[e]);
+            }
+          }
+    }
+  }
+  return AMR_OK;
+}
+
 amr_status upload_hierarchy(amr_hierarchy* h, std::string& err) {
   if (h->on_device) return AMR_OK;
   std::vector<unsigned char> valid(h->nelems, 0);

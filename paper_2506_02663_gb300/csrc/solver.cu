@@ -21,6 +21,7 @@
 #include "sweep3d.cuh"
 #include "coarse3d.cuh"
 #include "cic.cuh"
+#include "migrate.cuh"
 
 using namespace amr4;
 
@@ -3464,6 +3465,79 @@ amr_status cic_faces_impl(amr_hierarchy* h, int l, const double* const* w, const
          dl.cic_cstart, dl.cic_psum, phys, out, delta);
   return launch_check();
 }
+
+// ---------------------------------------------------------------- data migration
+// Device copies of a migration plan, freed when the object goes out of scope.
+struct MigrateDev {
+  std::vector<void*> ptrs;
+  ~MigrateDev() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  amr_status put(const std::vector<T>& v, T** out) {
+    *out = nullptr;
+    if (v.empty()) return AMR_OK;
+    if (cudaMalloc(out, sizeof(T) * v.size()) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("amr_migrate: device allocation failed");
+      return AMR_ERR_OOM;
+    }
+    ptrs.push_back(*out);
+    CK(cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return AMR_OK;
+  }
+};
+
+template <int D>
+amr_status migrate_impl(amr_hierarchy* oh, const double* xo, amr_hierarchy* nh, double* xn, cudaStream_t st) {
+  std::vector<MigrateLevel> plan;
+  std::string err;
+  const amr_status ps = migrate_plan(oh, nh, plan, err);
+  if (ps != AMR_OK) {
+    set_error(err);
+    return ps;
+  }
+  MigrateDev dev;
+  unsigned* bad = nullptr;
+  TRY(dev.put(std::vector<unsigned>(1, 0u), &bad));
+  for (int l = 0; l < nh->L; ++l) {
+    const MigrateLevel& M = plan[l];
+    MigrateBlock* db = nullptr;
+    CfiEntry* dc = nullptr;
+    long long* ds = nullptr;
+    TRY(dev.put(M.blocks, &db));
+    TRY(dev.put(M.cfi, &dc));
+    TRY(dev.put(M.side, &ds));
+    if (!M.blocks.empty()) {
+      long long most = 1;
+      for (const MigrateBlock& b : M.blocks) {
+        long long c = 1;
+        for (int e = 0; e < D; ++e) c *= b.hi[e] - b.lo[e] + 1;
+        most = std::max(most, c);
+      }
+      const unsigned gx = (unsigned)std::min<long long>((most + 255) / 256, 4096);
+      launch(k_migrate_copy<D>, dim3(gx, (unsigned)M.blocks.size(), 1), 256, 0, st, (const MigrateBlock*)db,
+             (const PatchDesc*)nh->lev[l].d_patches, (const PatchDesc*)oh->lev[l].d_patches, xo, oh->nelems, xn,
+             nh->nelems, bad);
+      TRY(launch_check());
+    }
+    if (!M.cfi.empty()) {  // after level l-1 is complete: stream order
+      const int nt = 128;
+      const long long n = (long long)M.cfi.size();
+      launch(k_cfi<double, D>, (unsigned)((n + nt - 1) / nt), nt, 0, st, (const CfiEntry*)dc, n, (const long long*)ds,
+             (const PatchDesc*)nh->lev[l - 1].d_patches, nh->r, (const double*)xn, xn, 0);
+      TRY(launch_check());
+    }
+  }
+  unsigned nbad = 0;
+  CK(cudaMemcpyAsync(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (nbad != 0) {
+    set_error("amr_migrate: " + std::to_string(nbad) + " copy offsets outside a field (skipped)");
+    return AMR_ERR_INVALID_ARG;
+  }
+  return AMR_OK;
+}
 }  // namespace
 
 // =================================================================== C ABI
@@ -3785,6 +3859,52 @@ amr_status amr_cic_faces(const amr_hierarchy* h, int level, int* nfaces, int* nc
   if (face)
     for (int i = 0; i < nf; ++i) face[i] = 2 * L.cicf[i].dir + (L.cicf[i].side > 0 ? 1 : 0);
   if (component) std::memcpy(component, L.cic_comp.data(), L.cic_comp.size() * sizeof(int));
+  return AMR_OK;
+}
+
+amr_status amr_migrate(amr_hierarchy* old_h, const double* old_x, amr_hierarchy* new_h, double* new_x,
+                       void* stream) {
+  if (!old_h || !old_x || !new_h || !new_x) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  if (old_x == new_x) { set_error("amr_migrate: the old and new fields must be different buffers"); return AMR_ERR_INVALID_ARG; }
+  TRY(ensure_device(old_h));
+  TRY(ensure_device(new_h));
+  return DISPATCH(new_h, migrate_impl, old_h, old_x, new_h, new_x, S(stream));
+}
+
+amr_status amr_migrate_plan(const amr_hierarchy* old_h, const amr_hierarchy* new_h, int level, int* nblocks,
+                            int* blocks, long long* ncells, int* cells, int* starts, long long* dst, long long* src,
+                            long long* nside, long long* side) {
+  if (!old_h || !new_h) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
+  if (level < 0 || level >= new_h->L) { set_error("amr_migrate_plan: level out of range"); return AMR_ERR_INVALID_ARG; }
+  std::vector<MigrateLevel> plan;
+  std::string err;
+  const amr_status ps = migrate_plan(old_h, new_h, plan, err);
+  if (ps != AMR_OK) {
+    set_error(err);
+    return ps;
+  }
+  const MigrateLevel& M = plan[level];
+  const int D = new_h->D;
+  if (nblocks) *nblocks = (int)M.blocks.size();
+  if (blocks)
+    for (size_t i = 0; i < M.blocks.size(); ++i) {
+      int* q = blocks + i * (2 + 2 * D);
+      q[0] = M.blocks[i].npatch;
+      q[1] = M.blocks[i].opatch;
+      for (int e = 0; e < D; ++e) {
+        q[2 + e] = M.blocks[i].lo[e];
+        q[2 + D + e] = M.blocks[i].hi[e];
+      }
+    }
+  if (ncells) *ncells = (long long)M.cfi.size();
+  if (cells) std::memcpy(cells, M.cells.data(), M.cells.size() * sizeof(int));
+  if (starts) std::memcpy(starts, M.starts.data(), M.starts.size() * sizeof(int));
+  if (dst)
+    for (size_t i = 0; i < M.cfi.size(); ++i) dst[i] = M.cfi[i].dst;
+  if (src)
+    for (size_t i = 0; i < M.cfi.size(); ++i) src[i] = M.cfi[i].src;
+  if (nside) *nside = (long long)M.side.size();
+  if (side) std::memcpy(side, M.side.data(), M.side.size() * sizeof(long long));
   return AMR_OK;
 }
 
