@@ -377,7 +377,7 @@ amr_status amr_batch_solve_host(amr_operator* const* ops, int n, const amr_solve
  * coarse-fine interface data from level l-1 at four equispaced coarse times (Sec. 6.3, steps
  * CIC-2 and CIC-3).  These calls are the data-parallel part of that: the interface ghosts at
  * an intermediate time and the corrected interface face averages.  All need 1 <= level <
- * nlevels on an unstacked hierarchy (AMR_ERR_INVALID_ARG otherwise). */
+ * nlevels on an unstacked hierarchy of refinement ratio 2 (AMR_ERR_INVALID_ARG otherwise). */
 
 /* CF ghost cells of `level` at the time t* of Eq. (timeInterp): coarse[i] (i = 0..3; device
  * composite fields, only level-1 read) hold the data at t_{-i} = t^{l-1} - i k (so coarse[0]
@@ -474,7 +474,7 @@ amr_status amr_cic_interface_bc(amr_hierarchy* h, int level, int component, cons
  *     AMR_ERR_INVALID_ARG when more are needed (call with boxes = NULL for the counts). */
 /* Data migration after regridding (Sec. 5.4, last paragraph): the composite field old_x of
  * old_h onto new_x of new_h (device fields; same dimension, ratio and level-0 domain; old_x
- * and new_x distinct).  Levels in order: every cell of a box of new level l that lies in a
+ * and new_x distinct; ratio 2).  Levels in order: every cell of a box of new level l that lies in a
  * box of old level l takes the old value of that cell (level 0 is copied whole); every other
  * cell takes the AMRCFI value (Sec. 5.2) from new level l-1, which is complete by then, so
  * the interpolation source is old data throughout (copied, or itself interpolated from old

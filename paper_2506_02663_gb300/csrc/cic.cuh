@@ -3,14 +3,14 @@
 //
 //   k_cic_combine +     the CF ghost cells of level l at an intermediate time t*: AMRCFI of the
 //   k_cic_grp3 (3-D),   level-(l-1) data at four equispaced coarse times, combined by the 2 x 4
-//   k_cic_grp / k_cic   matrix I^(4)(k, eta) of Eq. (timeInterp) into the value at t* and its
-//                       time derivative.  Both maps are linear, so the two time combinations
-//                       of the coarse data are formed first and AMRCFI is applied to them:
-//                       twice the AMRCFI arithmetic instead of four AMRCFI evaluations.  In
-//                       3-D (ratio 2) the combinations are formed once per coarse window cell
-//                       (k_cic_combine) -- the kernels are bound by GB300's FP64 rate, and a
-//                       coarse cell lies in about 24 windows; k_cic_grp / k_cic (2-D, other
-//                       ratios) form them per window cell.
+//   k_cic_grp (2-D)     matrix I^(4)(k, eta) of Eq. (timeInterp) into the value at t* and its
+//                       time derivative (ratio 2).  Both maps are linear, so the two time
+//                       combinations of the coarse data are formed first and AMRCFI is applied
+//                       to them: twice the AMRCFI arithmetic instead of four AMRCFI
+//                       evaluations.  In 3-D the combinations are formed once per coarse window
+//                       cell (k_cic_combine) -- the kernels are bound by GB300's FP64 rate, and
+//                       a coarse cell lies in about 24 windows; k_cic_grp (2-D) forms them per
+//                       window cell.
 //   k_cic_faces_sum /   the normal face averages n . <w> on the level's coarse-fine interface
 //   k_cic_faces_shift   faces (Eq. cell2face along the face normal, from the two interior
 //                       cells and the two CF ghost layers), corrected per connected component
@@ -193,40 +193,6 @@ k_cic_grp3(const CfiGroup* __restrict__ list, long long n, const long long* __re
   }
   out0[dst] = v0;
   if (out1) out1[dst] = v1;
-}
-
-// One thread per CF ghost (any ratio): the full tensor-product window.
-template <int D>
-__global__ void k_cic(const CfiEntry* __restrict__ list, long long n, const long long* __restrict__ side,
-                      const PatchDesc* __restrict__ cpatches, int r, CicTimes ct, double* __restrict__ out0,
-                      double* __restrict__ out1) {
-  pdl_wait();
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const CfiEntry e = list[t];
-  const int b0 = (e.pos[0] * r + e.sub[0]) * CFI_W;
-  const int b1 = (e.pos[1] * r + e.sub[1]) * CFI_W;
-  const int b2 = (e.pos[2] * r + e.sub[2]) * CFI_W;
-  PatchDesc cp{};
-  if (e.src >= 0) cp = cpatches[e.cpatch];
-  const long long* s = e.src >= 0 ? nullptr : side + (-1 - e.src) * (D == 3 ? 125 : 25);
-  double a0 = 0.0, a1 = 0.0;
-  for (int c2 = 0; c2 < (D == 3 ? CFI_W : 1); ++c2)
-    for (int c1 = 0; c1 < CFI_W; ++c1) {
-      const double wr = cfiw<double>(b1 + c1) * (D == 3 ? cfiw<double>(b2 + c2) : 1.0);
-#pragma unroll
-      for (int c0 = 0; c0 < CFI_W; ++c0) {
-        const long long o = s == nullptr ? e.src + (long long)c1 * cp.sy + (long long)c2 * cp.sz + c0
-                                         : s[(c2 * CFI_W + c1) * CFI_W + c0];
-        double va, vb;
-        cic_pair(ct, o, va, vb);
-        const double w = cfiw<double>(b0 + c0) * wr;
-        a0 += w * va;
-        a1 += w * vb;
-      }
-    }
-  out0[e.dst] = a0;
-  if (out1) out1[e.dst] = a1;
 }
 
 constexpr int CIC_FACE_THREADS = 256;

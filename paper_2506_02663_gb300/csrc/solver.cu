@@ -3429,11 +3429,15 @@ amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, dou
                            double* rate, cudaStream_t st) {
   const DeviceLists& dl = h->lev[l].dev;
   if (dl.ncfi == 0) return AMR_OK;
+  if (dl.ncfig == 0) {  // ratio 2 groups every CF ghost by its parent
+    set_error("amr_cic_ghosts: no parent groups for the CF ghosts");
+    return AMR_ERR_INVALID_ARG;
+  }
   CicTimes ct{};
   for (int i = 0; i < 4; ++i) ct.x[i] = xt[i];
   cic_weights(k, eta, ct.w);
   const int nt = 128;
-  if (dl.ncfig > 0 && D == 3) {
+  if (D == 3) {
     TRY(cic_band(h, l, st));
     double* y0 = dl.cic_y;
     double* y1 = rate ? dl.cic_y + dl.cic_span : nullptr;
@@ -3443,12 +3447,10 @@ amr_status cic_ghosts_impl(amr_hierarchy* h, int l, const double* const* xt, dou
     launch(k_cic_grp3, (unsigned)((dl.ncfig * CIC_LANES + CIC_GRP_THREADS - 1) / CIC_GRP_THREADS),
            CIC_GRP_THREADS, 0, st, dl.cfig, dl.ncfig, dl.cfi_side, h->lev[l - 1].d_patches, (const double*)y0,
            (const double*)y1, dl.cic_base, v, rate);
-  } else if (dl.ncfig > 0)
+  } else {
     launch(k_cic_grp<D>, (unsigned)((dl.ncfig + nt - 1) / nt), nt, 0, st, dl.cfig, dl.ncfig, dl.cfi_side,
            h->lev[l - 1].d_patches, ct, v, rate);
-  else
-    launch(k_cic<D>, (unsigned)((dl.ncfi + nt - 1) / nt), nt, 0, st, dl.cfi, dl.ncfi, dl.cfi_side,
-           h->lev[l - 1].d_patches, h->r, ct, v, rate);
+  }
   return launch_check();
 }
 
@@ -3826,6 +3828,7 @@ amr_status amr_fill_ghosts(amr_operator* op, double* phi, const double* bc, void
 static amr_status check_cic_level(const amr_hierarchy* h, int level) {
   if (!h) { set_error("null hierarchy"); return AMR_ERR_INVALID_ARG; }
   if (h->ncomp != 1) { set_error("interface conditions need an unstacked hierarchy"); return AMR_ERR_INVALID_ARG; }
+  if (h->r != 2) { set_error("interface conditions need refinement ratio 2"); return AMR_ERR_INVALID_ARG; }
   if (level < 1 || level >= h->L) {
     set_error("interface conditions: level " + std::to_string(level) + " is not a refined level (1.." +
               std::to_string(h->L - 1) + ")");
@@ -3866,6 +3869,7 @@ amr_status amr_migrate(amr_hierarchy* old_h, const double* old_x, amr_hierarchy*
                        void* stream) {
   if (!old_h || !old_x || !new_h || !new_x) { set_error("null argument"); return AMR_ERR_INVALID_ARG; }
   if (old_x == new_x) { set_error("amr_migrate: the old and new fields must be different buffers"); return AMR_ERR_INVALID_ARG; }
+  if (new_h->r != 2) { set_error("amr_migrate: needs refinement ratio 2"); return AMR_ERR_INVALID_ARG; }
   TRY(ensure_device(old_h));
   TRY(ensure_device(new_h));
   return DISPATCH(new_h, migrate_impl, old_h, old_x, new_h, new_x, S(stream));
