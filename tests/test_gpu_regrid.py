@@ -1,7 +1,7 @@
 """GPU parity of the data migration after regridding (Sec. 5.4, last paragraph) through the C
 ABI against the oracle's migration (oracle/regrid.py): random old fields and quartic cell
-averages (which the migration reproduces exactly on the new hierarchy), within 1e-14 of the
-field's scale."""
+averages (which the migration reproduces exactly on the new hierarchy), within 1e-13 of the
+field's scale (two chained 5^D-term AMRCFI sums in different orders on the two sides)."""
 import numpy as np
 import pytest
 
@@ -43,7 +43,7 @@ def test_migration_matches_oracle(name, kind):
     ref = orr.migrate(Ho, Fo, Hn)
     scale = max(float(np.max(np.abs(F[lev.covered]))) for F, lev in zip(ref, Hn.levels))
     for l, lev in enumerate(Hn.levels):
-        assert np.max(np.abs(got[l][lev.covered] - ref[l][lev.covered])) <= 1e-14 * scale, l
+        assert np.max(np.abs(got[l][lev.covered] - ref[l][lev.covered])) <= 1e-13 * scale, l
     if kind == "quartic":
         exact = _quartic_field(Hn)
         for l, lev in enumerate(Hn.levels):
