@@ -33,5 +33,6 @@ Modules
                per-component correction of the interface face averages (Eq.
                correctingFaceAvg), and the boundary data of single-box level problems.
 ``regrid``     Sec. 5.4 RDM-2/3: Berger-Rigoutsos clustering of tagged cells into the boxes
-               of a new hierarchy, finest level first.
+               of a new hierarchy, finest level first; the data migration after it.
+``convection`` Eq. (convOp): the fourth-order cell-averaged convection operator.
 """
