@@ -11,6 +11,13 @@ batched in one amr_batch_solve call, each to the same tolerance; FP32 V-cycles i
 iterative refinement.  Metric: V-cycle DOF/s = valid cells x V-cycles / time, summed over
 the four systems and all ranks; ms_per_step is the time to the 1e-10 residual of all four.
 
+Besides the line's headline keys, rank 0 reports (unless --no-extras) the step in the other
+precision, the mixed-against-FP64 and stored-oracle errors, the adjoint of the 3-D step,
+the interface conditions of a subcycled level solve on the 3-D workload's refined level
+(``cic3d``: CF ghosts at t* from four coarse times and the corrected interface face
+averages, against the FP64 rate), the regridding clustering on the host (``regrid3d``) and
+the 2-D workloads.
+
 ``python bench.py [--gpus N --steps K --warmup W]``        this library (GB300)
 ``python bench.py --impl reference ...``                    the CPU oracle on the host cores
 Under torchrun (N > 1) every rank solves its own replica (the solve does not shard:
