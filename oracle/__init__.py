@@ -35,4 +35,5 @@ Modules
 ``regrid``     Sec. 5.4 RDM-2/3: Berger-Rigoutsos clustering of tagged cells into the boxes
                of a new hierarchy, finest level first; the data migration after it.
 ``convection`` Eq. (convOp): the fourth-order cell-averaged convection operator.
+``imex``       the ERK-ESDIRK tableau of Eq. (GePUP-IMEX) and one additive Runge-Kutta step.
 """
